@@ -1,0 +1,224 @@
+/*
+ * rann_dd.h -- C ABI of the GB300 (sm_103a) RaNN domain-decomposition solver.
+ *
+ * The method (Shang, Heinlein, Mishra, Wang, "Overlapping Schwarz
+ * preconditioners for randomized neural networks with domain decomposition"):
+ * each overlapping box subdomain Omega_j carries a randomized single-hidden-
+ * layer tanh network Phi_j with fixed uniform weights (Sec. 2, Eq. (net));
+ * the networks are glued by a partition of unity omega_j and a constraining
+ * operator C u = L u + G that enforces the Dirichlet data (Eq. (operator),
+ * (netdd)); collocation gives the block least-squares system H W = F
+ * (Eq. (system)); PCA of each local basis Psi_j reduces H_j to H_j V_{p_j}
+ * (Sec. 4, Eq. (system_new)); the normal equations H^T H W = H^T F are solved
+ * by additive-Schwarz preconditioned CG or restricted-additive-Schwarz
+ * preconditioned GMRES (Sec. 3).  Algorithm 1 lists the steps in this order.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a rann_status; RANN_OK on success.  On error the
+ *    handle is left usable unless the status is RANN_ECUDA (a CUDA error,
+ *    after which the handle should be destroyed).  rann_dd_last_error()
+ *    returns a human-readable message for the last failing call of the
+ *    calling thread.
+ *  - "_dev" pointers are CUDA device pointers to contiguous float64 (or
+ *    int64 where stated) arrays owned by the caller; "_host" pointers are host
+ *    memory owned by the caller.  The handle owns all internal device memory
+ *    (allocated at create/assemble/pca/setup time, released by destroy).
+ *  - All work is enqueued on the CUDA stream given to rann_dd_create and is
+ *    stream-ordered.  Calls that return host data (pca ranks, solver stats,
+ *    inspection getters) synchronise that stream.
+ *  - Calls out of Algorithm 1's order (solve before setup_precond, pca
+ *    before assemble, ...) return RANN_EORDER.
+ *  - No process-global state: handles are independent; a handle must not be
+ *    used from two host threads at once.
+ */
+#ifndef RANN_DD_H
+#define RANN_DD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RANN_OK = 0,
+  RANN_EINVAL = 1,          /* an argument is out of range or inconsistent */
+  RANN_ENOMEM = 2,          /* device or host allocation failed */
+  RANN_ECUDA = 3,           /* a CUDA runtime error */
+  RANN_NOT_CONVERGED = 4,   /* Krylov solve hit maxit; W holds the last iterate */
+  RANN_BREAKDOWN = 5,       /* CG p^T A p <= 0, or NaN/Inf met in a reduction */
+  RANN_LOCAL_SINGULAR = 6,  /* warning: a local Cholesky needed a diagonal shift */
+  RANN_EORDER = 7           /* call made out of Algorithm 1's order */
+} rann_status;
+
+/* PDE operator A of Eq. (1). */
+enum { RANN_OP_POISSON = 0,    /* -Lap u + c0 u                          */
+       RANN_OP_DIFFUSION = 1,  /* -div(a grad u), spatial dims only        */
+       RANN_OP_HEAT = 2 };     /* u_t - nu Lap_x u; last coordinate is t   */
+/* Diffusion coefficient a(x). */
+enum { RANN_COEF_CONST = 0,      /* a = coef_value                                  */
+       RANN_COEF_MULTISCALE = 1, /* a = 2 + sin(2 pi x/eps) sin(2 pi y/eps)        */
+       RANN_COEF_PIECEWISE = 2 };/* a = sum_c coef_vals[c] s_c(x,y), g x g smoothed cells */
+/* G of the constraining operator C u = L u + G (Eq. (operator)). */
+enum { RANN_G_ZERO = 0, RANN_G_SINPROD = 1 /* G = prod_{spatial i} sin(pi x_i) */ };
+/* Subdomain layout. */
+enum { RANN_LAYOUT_CELL = 0,   /* mu_k = (k+1/2)/l, half-width (1/l + overlap)/2 */
+       RANN_LAYOUT_PAPER = 1 };/* mu_k = k/(l-1), half-width (delta/2)/(l-1) (Sec. 5, Ex. 1) */
+/* PCA rank rule (Sec. 4). */
+enum { RANN_PCA_ABS = 0,       /* p_j = #{sigma_k > thr}                            */
+       RANN_PCA_VARIANCE = 1,  /* smallest p: sum_{k<=p} sigma_k^2 >= (1-thr) sum sigma^2 */
+       RANN_PCA_NONE = 2 };    /* p_j = m, V = I                                    */
+/* Schwarz preconditioner kind (Sec. 3). */
+enum { RANN_PREC_NONE = 0, RANN_PREC_AS = 1, RANN_PREC_SAS = 2, RANN_PREC_RAS = 3 };
+
+/*
+ * Problem descriptor: the statement of Eq. (1) with Dirichlet data through
+ * C u = L u + G, the subdomain grid and overlap, the local networks, the
+ * collocation grid.  Host memory, read during rann_dd_create only.
+ *
+ * Collocation points: the cell-centred grid x_q = (q + 1/2)/(sub[i]*pts[i])
+ * per dimension, q = 0 .. sub[i]*pts[i]-1; global point index
+ * g = q_0 + G_0 (q_1 + G_1 q_2) (dimension 0 fastest).
+ * Source: f(x) = f0 + sum_{t < f_terms} fc[t] prod_{spatial i} sin(pi fa[t*dim+i] x_i).
+ * Constraint: L = prod_{spatial i} tanh(x_i/rho) tanh((1-x_i)/rho)
+ *             [* tanh(t/rho) for RANN_OP_HEAT] (Eq. (cons1), (cons2)).
+ * Piecewise coefficient: s_c(x,y) = S(x; c mod g) S(y; c div g) with the
+ * smooth cell indicator S(x; i) = [tanh((x-i/g)/w) - tanh((x-(i+1)/g)/w)]/2,
+ * w = 1/(8g), and the outer edges pushed to -inf/+inf (so sum_c s_c = 1).
+ * Weights: R [J][m][dim] and b [J][m] if given, else drawn from the
+ * SplitMix64 stream `seed` as U[-w_range, w_range] in the order
+ * (subdomain j: R_j in (neuron, dim) order, then b_j).
+ */
+typedef struct {
+  int dim;                 /* 2 or 3 (a space-time problem counts t)          */
+  int op;                  /* RANN_OP_*                                       */
+  double c0;               /* Poisson reaction coefficient                    */
+  double nu;               /* heat diffusivity                                */
+  int coef;                /* RANN_COEF_*                                     */
+  double coef_value;       /* RANN_COEF_CONST value                           */
+  double eps;              /* RANN_COEF_MULTISCALE period                     */
+  int coef_grid;           /* RANN_COEF_PIECEWISE g (<= 8)                    */
+  const double* coef_vals; /* [g*g], cell (cx, cy) at cy*g + cx               */
+  int layout;              /* RANN_LAYOUT_*                                   */
+  int sub[3];              /* subdomains per dimension (l_i)                  */
+  double overlap[3];       /* RANN_LAYOUT_CELL: absolute overlap per dim      */
+  double delta;            /* RANN_LAYOUT_PAPER: overlap ratio delta > 1      */
+  int pts[3];              /* collocation points per subdomain cell per dim   */
+  int neurons;             /* m, 1 .. 1024                                    */
+  double w_range;          /* weights ~ U[-w_range, w_range]                  */
+  uint64_t seed;           /* SplitMix64 stream when R/b are NULL             */
+  const double* R;         /* optional [J][m][dim]                            */
+  const double* b;         /* optional [J][m]                                 */
+  double rho;              /* constraint sharpness                            */
+  int g_kind;              /* RANN_G_*                                        */
+  double f0;               /* constant part of f                              */
+  int f_terms;             /* 0 .. 16                                         */
+  const double* fc;        /* [f_terms]                                       */
+  const double* fa;        /* [f_terms][dim]                                  */
+} rann_dd_desc;
+
+/* Per-solve statistics. */
+typedef struct {
+  int iters;               /* Krylov iterations (inner steps for GMRES)       */
+  double rel_res_true;     /* ||H^T(F - H W)|| / ||H^T F|| recomputed at exit */
+  double rel_res_rec;      /* the solver's own stopping quantity at exit      */
+  double rel_res_prec;     /* ||M^{-1}(b - A W)|| / ||M^{-1} b|| at exit (GMRES) */
+  double ms_solve;         /* device time of the solve                        */
+  int n_shifted;           /* local factors that needed a shift (from setup)  */
+} rann_dd_stats;
+
+typedef struct rann_dd_handle rann_dd_handle;
+
+/* Algorithm 1 steps 1-2: subdomains, collocation grid, networks.  Copies the
+ * descriptor; `cuda_stream` is a cudaStream_t (NULL = legacy default). */
+rann_status rann_dd_create(const rann_dd_desc* desc, void* cuda_stream, rann_dd_handle** out);
+/* Releases all device memory of the handle (stream-ordered, then synchronises). */
+void rann_dd_destroy(rann_dd_handle* h);
+
+/* Sizes: N global collocation points, total block rows sum_j N_j, J, m, and
+ * the current number of unknowns DoF = sum_j p_j (J*m before pca). */
+rann_status rann_dd_sizes(rann_dd_handle* h, int64_t* n_points, int64_t* n_block_rows,
+                          int* J, int* m, int64_t* dof);
+/* Collocation point coordinates into xyz_dev [N][dim]. */
+rann_status rann_dd_points(rann_dd_handle* h, double* xyz_dev);
+
+/* Algorithm 1 steps 3 and 5 (Sec. 2 Eq. (system), Sec. 4 Psi_j): for every
+ * subdomain j and collocation point x in box_j, Psi_j = omega_j Phi_j and
+ * H_j = A[L omega_j Phi_j], float64, kept in the handle. */
+rann_status rann_dd_assemble(rann_dd_handle* h);
+/* F_i = f(x_i) - A[G](x_i) at the N global points into F_dev [N]. */
+rann_status rann_dd_rhs(rann_dd_handle* h, double* F_dev);
+
+/* Algorithm 1 step 4 (Sec. 4, Eq. (pca), (system_new)): eigen-decomposition of
+ * each Gram matrix Psi_j^T Psi_j = V diag(sigma^2) V^T, rank p_j by `mode` and
+ * `thr`, then H_j <- H_j V_{p_j}.  Writes the ranks to ranks_host [J] (may be
+ * NULL).  Synchronises. */
+rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int* ranks_host);
+
+/* Algorithm 1 step 6, preconditioner part (Sec. 3): for every subdomain i the
+ * extended set N(i) (subdomains whose box shares a collocation point with
+ * box_i; overlap_level = 0: {i} only), A_i = R_i H^T H R_i^T assembled from
+ * the neighbour Gram blocks, and its Cholesky factor (float64; a diagonal
+ * shift is applied and counted where a pivot fails).  `kind` is
+ * RANN_PREC_AS / SAS / RAS / NONE and fixes D_i (Sec. 3, Sec. 5).
+ * Returns RANN_LOCAL_SINGULAR (a warning) if any factor was shifted. */
+rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int overlap_level);
+
+/* Algorithm 1 step 6, solve part: preconditioned CG on H^T H W = H^T F
+ * (Sec. 3, Sec. 5 Table 1b/3) from W = 0, stopping when the recursive
+ * ||H^T F - H^T H W|| / ||H^T F|| <= rtol (true residual recomputed at exit).
+ * Needs a symmetric preconditioner (AS or NONE).  F_dev [N], W_dev [DoF]. */
+rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_dev, double* W_dev,
+                                double rtol, int maxit, rann_dd_stats* stats);
+/* Left-preconditioned restarted GMRES(restart) on the normal equations from
+ * W = 0, stopping when ||M^{-1}(H^T F - H^T H W)|| / ||M^{-1} H^T F|| <= rtol
+ * (Sec. 5 Example 1 stopping rule).  Any preconditioner kind. */
+rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* F_dev, double* W_dev,
+                                    double rtol, int restart, int maxit, rann_dd_stats* stats);
+
+/* u_hat(x) = L(x) sum_j omega_j(x) (V_{p_j}^T Phi_j(x)) . W_j + G(x)
+ * (Eq. (netdd), (pca_net)) at n points x_dev [n][dim] (inside [0,1]^dim)
+ * into u_dev [n]. */
+rann_status rann_dd_eval(rann_dd_handle* h, const double* W_dev, const double* x_dev,
+                         int64_t n, double* u_dev);
+
+/* Building blocks of the solve, exposed for tests and composition
+ * (all device vectors float64): y = H x (y_dev [N], x_dev [DoF]);
+ * z = H^T y; z = H^T H x (one fused pass over the blocks); z = M^{-1} r. */
+rann_status rann_dd_matvec(rann_dd_handle* h, const double* x_dev, double* y_dev);
+rann_status rann_dd_matvec_t(rann_dd_handle* h, const double* y_dev, double* z_dev);
+rann_status rann_dd_normal_matvec(rann_dd_handle* h, const double* x_dev, double* z_dev);
+rann_status rann_dd_precond_apply(rann_dd_handle* h, const double* r_dev, double* z_dev);
+
+/* Inspection (synchronising copies to host memory).
+ * which = 0: Psi_j, 1: H_j (both N_j x m, after assemble, before pca);
+ *         2: reduced block B_j = H_j V_{p_j} (N_j x p_j, after pca).
+ * rows_host [N_j] receives the global point index of each row. */
+rann_status rann_dd_block_info(rann_dd_handle* h, int j, int64_t* n_rows, int* n_cols);
+rann_status rann_dd_get_block(rann_dd_handle* h, int j, int which, double* out_host,
+                              int64_t* rows_host);
+/* Eigenvalues sigma^2 (descending, [m]) and the kept V_{p_j} ([m][p_j] row-major). */
+rann_status rann_dd_get_pca(rann_dd_handle* h, int j, double* eig_host, double* V_host);
+
+/* Kernel accounting (tracing for the roofline; the paper has no
+ * counterpart).  Every kernel launch is counted per kernel family together
+ * with its algorithmic bytes and float64 flops (the minimal traffic and
+ * arithmetic of the operation it performs, computed from the sizes); with
+ * profile_enable(h, 1) each launch is also bracketed by CUDA events on the
+ * handle's stream.  profile_enable resets all counters.  profile_get returns,
+ * for family idx = 0, 1, ... (RANN_EINVAL past the last one): its name (a
+ * static string), kernels launched, summed device time in ms (0 unless
+ * profiling was on), summed algorithmic bytes and flops, and its roofline
+ * class (0 = memory-bound, 1 = float64-ALU-bound).  It synchronises the
+ * pending events.  Any output pointer may be NULL. */
+rann_status rann_dd_profile_enable(rann_dd_handle* h, int on);
+rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const char** name, int64_t* launches,
+                                double* ms, double* alg_bytes, double* alg_flops, int* bound);
+
+const char* rann_dd_status_string(rann_status s);
+const char* rann_dd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RANN_DD_H */

@@ -1,0 +1,336 @@
+"""GB300 (sm_103a) RaNN domain-decomposition solver: thin Python binding.
+
+Every step of the method runs in librann_dd.so (hand-written CUDA kernels
+behind the C ABI of include/rann_dd.h); this module only marshals arguments:
+problem descriptors into the C struct, torch CUDA tensors into device
+pointers, and the current torch stream into the library's stream.  There is
+no CPU fallback: if the library is missing, importing the binding raises.
+
+Typical use (Algorithm 1 order):
+
+    s = RannDD(problem)            # steps 1-2: subdomains, grid, networks
+    s.assemble()                   # steps 3, 5: Psi_j and H_j
+    F = s.rhs()                    # F = f - A[G] at the collocation points
+    ranks = s.pca(PCA_VARIANCE, 1e-12)    # step 4
+    s.setup_precond(PREC_RAS)      # step 6: A_i and their factors
+    W, stats = s.solve_gmres_ras(F, rtol=1e-10, restart=50)
+    u = s.eval(W, x)               # u_hat at points x
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "librann_dd.so")
+
+OP_POISSON, OP_DIFFUSION, OP_HEAT = 0, 1, 2
+COEF_CONST, COEF_MULTISCALE, COEF_PIECEWISE = 0, 1, 2
+G_ZERO, G_SINPROD = 0, 1
+LAYOUT_CELL, LAYOUT_PAPER = 0, 1
+PCA_ABS, PCA_VARIANCE, PCA_NONE = 0, 1, 2
+PREC_NONE, PREC_AS, PREC_SAS, PREC_RAS = 0, 1, 2, 3
+PREC_BY_NAME = {"none": PREC_NONE, "as": PREC_AS, "sas": PREC_SAS, "ras": PREC_RAS}
+
+STATUS = {0: "RANN_OK", 1: "RANN_EINVAL", 2: "RANN_ENOMEM", 3: "RANN_ECUDA", 4: "RANN_NOT_CONVERGED",
+          5: "RANN_BREAKDOWN", 6: "RANN_LOCAL_SINGULAR", 7: "RANN_EORDER"}
+OK, EINVAL, ENOMEM, ECUDA, NOT_CONVERGED, BREAKDOWN, LOCAL_SINGULAR, EORDER = range(8)
+
+
+class RannError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("op", ctypes.c_int), ("c0", ctypes.c_double), ("nu", ctypes.c_double),
+        ("coef", ctypes.c_int), ("coef_value", ctypes.c_double), ("eps", ctypes.c_double),
+        ("coef_grid", ctypes.c_int), ("coef_vals", ctypes.POINTER(ctypes.c_double)),
+        ("layout", ctypes.c_int), ("sub", ctypes.c_int * 3), ("overlap", ctypes.c_double * 3),
+        ("delta", ctypes.c_double), ("pts", ctypes.c_int * 3), ("neurons", ctypes.c_int),
+        ("w_range", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("R", ctypes.POINTER(ctypes.c_double)), ("b", ctypes.POINTER(ctypes.c_double)),
+        ("rho", ctypes.c_double), ("g_kind", ctypes.c_int), ("f0", ctypes.c_double),
+        ("f_terms", ctypes.c_int), ("fc", ctypes.POINTER(ctypes.c_double)),
+        ("fa", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_res_true", ctypes.c_double), ("rel_res_rec", ctypes.c_double),
+                ("rel_res_prec", ctypes.c_double), ("ms_solve", ctypes.c_double), ("n_shifted", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_L = ctypes.c_int64
+
+# name -> (restype, argtypes); every entry point declared in include/rann_dd.h
+SIGNATURES = {
+    "rann_dd_create": (_I, [ctypes.POINTER(Desc), _P, ctypes.POINTER(_P)]),
+    "rann_dd_destroy": (None, [_P]),
+    "rann_dd_sizes": (_I, [_P, ctypes.POINTER(_L), ctypes.POINTER(_L), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                           ctypes.POINTER(_L)]),
+    "rann_dd_points": (_I, [_P, _P]),
+    "rann_dd_assemble": (_I, [_P]),
+    "rann_dd_rhs": (_I, [_P, _P]),
+    "rann_dd_pca": (_I, [_P, _I, _D, ctypes.POINTER(_I)]),
+    "rann_dd_setup_precond": (_I, [_P, _I, _I]),
+    "rann_dd_solve_cg_as": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
+    "rann_dd_solve_gmres_ras": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(Stats)]),
+    "rann_dd_eval": (_I, [_P, _P, _P, _L, _P]),
+    "rann_dd_matvec": (_I, [_P, _P, _P]),
+    "rann_dd_matvec_t": (_I, [_P, _P, _P]),
+    "rann_dd_normal_matvec": (_I, [_P, _P, _P]),
+    "rann_dd_precond_apply": (_I, [_P, _P, _P]),
+    "rann_dd_block_info": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_I)]),
+    "rann_dd_get_block": (_I, [_P, _I, _I, _P, _P]),
+    "rann_dd_get_pca": (_I, [_P, _I, _P, _P]),
+    "rann_dd_profile_enable": (_I, [_P, _I]),
+    "rann_dd_profile_get": (_I, [_P, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_L),
+                                 ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "rann_dd_status_string": (ctypes.c_char_p, [_I]),
+    "rann_dd_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads librann_dd.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librann_dd.so not found at {path}: run paper_2412_19207_gb300.build.build() "
+                           "(nvcc, sm_103a) first; there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str, allow=()):
+    if status == OK or status in allow:
+        return status
+    raise RannError(status, f"{what}: {load_library().rann_dd_last_error().decode()}")
+
+
+def _dptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _f64p(a: Optional[np.ndarray]):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_desc(p) -> tuple:
+    """C descriptor from a problem object (rann_inputs.Problem or any object with
+    the same attributes).  Returns (desc, keepalive) -- keep both alive until
+    the handle is created."""
+    d = Desc()
+    keep = []
+    d.dim, d.op, d.c0, d.nu = p.dim, p.op, p.c0, p.nu
+    d.coef, d.coef_value, d.eps, d.coef_grid = p.coef, p.coef_value, p.eps, p.coef_grid
+    arr, ptr = _f64p(p.coef_vals)
+    keep.append(arr)
+    d.coef_vals = ptr
+    d.layout = p.layout
+    for i in range(3):
+        d.sub[i] = int(p.sub[i]) if i < p.dim else 1
+        d.pts[i] = int(p.pts[i]) if i < p.dim else 1
+        d.overlap[i] = float(p.overlap[i]) if i < len(p.overlap) else 0.0
+    d.delta = p.delta
+    d.neurons, d.w_range, d.seed = p.neurons, p.w_range, p.seed
+    R = getattr(p, "R", None)
+    b = getattr(p, "b", None)
+    arr, ptr = _f64p(R)
+    keep.append(arr)
+    d.R = ptr
+    arr, ptr = _f64p(b)
+    keep.append(arr)
+    d.b = ptr
+    d.rho, d.g_kind, d.f0 = p.rho, p.g_kind, p.f0
+    if p.fc is not None:
+        d.f_terms = len(p.fc)
+        arr, ptr = _f64p(p.fc)
+        keep.append(arr)
+        d.fc = ptr
+        fa = np.zeros((len(p.fc), p.dim))
+        fa[:, : np.asarray(p.fa).shape[1]] = np.asarray(p.fa)
+        arr, ptr = _f64p(fa)
+        keep.append(arr)
+        d.fa = ptr
+    else:
+        d.f_terms = 0
+    return d, keep
+
+
+class RannDD:
+    """One problem instance on the current CUDA device and stream."""
+
+    def __init__(self, problem, R: Optional[np.ndarray] = None, b: Optional[np.ndarray] = None, stream=None):
+        import torch
+        lib = load_library()
+        self.problem = problem
+        desc, keep = make_desc(problem)
+        if R is not None:
+            arr, ptr = _f64p(R)
+            keep.append(arr)
+            desc.R = ptr
+            arr, ptr = _f64p(b)
+            keep.append(arr)
+            desc.b = ptr
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.rann_dd_create(ctypes.byref(desc), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+               "rann_dd_create")
+        self._h = h
+        self._lib = lib
+        self.ranks = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rann_dd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- sizes ------------------------------------------------------------
+    def sizes(self):
+        n, rows, dof = _L(), _L(), _L()
+        J, m = _I(), _I()
+        _check(self._lib.rann_dd_sizes(self._h, ctypes.byref(n), ctypes.byref(rows), ctypes.byref(J),
+                                       ctypes.byref(m), ctypes.byref(dof)), "rann_dd_sizes")
+        return {"n_points": n.value, "n_block_rows": rows.value, "J": J.value, "m": m.value, "dof": dof.value}
+
+    def _empty(self, n):
+        import torch
+        return torch.empty(int(n), dtype=torch.float64, device="cuda")
+
+    def points(self):
+        sz = self.sizes()
+        x = self._empty(sz["n_points"] * self.problem.dim)
+        _check(self._lib.rann_dd_points(self._h, _dptr(x)), "rann_dd_points")
+        return x.view(-1, self.problem.dim)
+
+    # -- Algorithm 1 ------------------------------------------------------
+    def assemble(self):
+        _check(self._lib.rann_dd_assemble(self._h), "rann_dd_assemble")
+
+    def rhs(self, out=None):
+        F = out if out is not None else self._empty(self.sizes()["n_points"])
+        _check(self._lib.rann_dd_rhs(self._h, _dptr(F)), "rann_dd_rhs")
+        return F
+
+    def pca(self, mode: int, thr: float):
+        J = self.sizes()["J"]
+        ranks = (ctypes.c_int * J)()
+        _check(self._lib.rann_dd_pca(self._h, mode, thr, ranks), "rann_dd_pca")
+        self.ranks = np.array(ranks[:], dtype=np.int64)
+        return self.ranks
+
+    def setup_precond(self, kind, overlap_level: int = 1) -> int:
+        kind = PREC_BY_NAME[kind] if isinstance(kind, str) else kind
+        return _check(self._lib.rann_dd_setup_precond(self._h, kind, overlap_level), "rann_dd_setup_precond",
+                      allow=(LOCAL_SINGULAR,))
+
+    def solve_cg_as(self, F, rtol=1e-10, maxit=2000, W=None, allow_not_converged=False):
+        W = W if W is not None else self._empty(self.sizes()["dof"])
+        st = Stats()
+        s = self._lib.rann_dd_solve_cg_as(self._h, _dptr(F), _dptr(W), rtol, maxit, ctypes.byref(st))
+        _check(s, "rann_dd_solve_cg_as", allow=(NOT_CONVERGED,) if allow_not_converged else ())
+        return W, st.as_dict() | {"status": STATUS[s]}
+
+    def solve_gmres_ras(self, F, rtol=1e-10, restart=50, maxit=2000, W=None, allow_not_converged=False):
+        W = W if W is not None else self._empty(self.sizes()["dof"])
+        st = Stats()
+        s = self._lib.rann_dd_solve_gmres_ras(self._h, _dptr(F), _dptr(W), rtol, restart, maxit, ctypes.byref(st))
+        _check(s, "rann_dd_solve_gmres_ras", allow=(NOT_CONVERGED,) if allow_not_converged else ())
+        return W, st.as_dict() | {"status": STATUS[s]}
+
+    def eval(self, W, x, out=None):
+        n = x.shape[0]
+        u = out if out is not None else self._empty(n)
+        _check(self._lib.rann_dd_eval(self._h, _dptr(W), _dptr(x), n, _dptr(u)), "rann_dd_eval")
+        return u
+
+    # -- building blocks --------------------------------------------------
+    def matvec(self, x, y=None):
+        y = y if y is not None else self._empty(self.sizes()["n_points"])
+        _check(self._lib.rann_dd_matvec(self._h, _dptr(x), _dptr(y)), "rann_dd_matvec")
+        return y
+
+    def matvec_t(self, y, z=None):
+        z = z if z is not None else self._empty(self.sizes()["dof"])
+        _check(self._lib.rann_dd_matvec_t(self._h, _dptr(y), _dptr(z)), "rann_dd_matvec_t")
+        return z
+
+    def normal_matvec(self, x, z=None):
+        z = z if z is not None else self._empty(self.sizes()["dof"])
+        _check(self._lib.rann_dd_normal_matvec(self._h, _dptr(x), _dptr(z)), "rann_dd_normal_matvec")
+        return z
+
+    def precond_apply(self, r, z=None):
+        z = z if z is not None else self._empty(self.sizes()["dof"])
+        _check(self._lib.rann_dd_precond_apply(self._h, _dptr(r), _dptr(z)), "rann_dd_precond_apply")
+        return z
+
+    # -- kernel accounting ------------------------------------------------
+    def profile(self, on: bool = True):
+        _check(self._lib.rann_dd_profile_enable(self._h, int(on)), "rann_dd_profile_enable")
+
+    def profile_read(self):
+        out = {}
+        i = 0
+        while True:
+            name, n, ms, nb, nf, bd = ctypes.c_char_p(), _L(), _D(), _D(), _D(), _I()
+            if self._lib.rann_dd_profile_get(self._h, i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms),
+                                             ctypes.byref(nb), ctypes.byref(nf), ctypes.byref(bd)) != OK:
+                break
+            out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": nb.value,
+                                        "flops": nf.value, "bound": "alu" if bd.value else "hbm"}
+            i += 1
+        return out
+
+    # -- inspection -------------------------------------------------------
+    def block(self, j: int, which: int):
+        nr, nc = _L(), _I()
+        _check(self._lib.rann_dd_block_info(self._h, j, ctypes.byref(nr), ctypes.byref(nc)), "rann_dd_block_info")
+        cols = self.problem.neurons if which < 2 else nc.value
+        out = np.empty((nr.value, cols))
+        rows = np.empty(nr.value, dtype=np.int64)
+        _check(self._lib.rann_dd_get_block(self._h, j, which, out.ctypes.data, rows.ctypes.data), "rann_dd_get_block")
+        return rows, out
+
+    def pca_of(self, j: int):
+        m = self.problem.neurons
+        eig = np.empty(m)
+        p = int(self.ranks[j])
+        V = np.empty((m, p))
+        _check(self._lib.rann_dd_get_pca(self._h, j, eig.ctypes.data, V.ctypes.data), "rann_dd_get_pca")
+        return eig, V

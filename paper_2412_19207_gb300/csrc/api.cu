@@ -1,0 +1,1139 @@
+// Host runtime and C ABI of librann_dd (see include/rann_dd.h).
+//
+// Owns the geometry (Sec. 5 Example 1: box subdomains, windows; cell-centred
+// collocation grid), the device buffers, the task lists of the batched
+// kernels, and the Krylov drivers (Sec. 3, Sec. 5).  All device work runs on
+// the handle's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+// launchers from the other translation units
+cudaError_t launch_matvec_H2(const ProbDev& P, const SubDev* d_sub, const int* d_cov, int Gmax,
+                             const double* d_B, const double* d_x, double* d_y, int64_t N, cudaStream_t st);
+cudaError_t launch_matvec_HT2(const ProbDev& P, const SubDev* d_sub, int J, const int* d_rtiles,
+                              int nrtiles, const int* d_tile0, const double* d_B, const double* d_y,
+                              double* d_part, double* d_z, int maxP, cudaStream_t st);
+cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, int* d_fail,
+                             const double* d_dmax, cudaStream_t st);
+cudaError_t launch_local_solve(const CholMat* d_mats, int nsets, const int* d_set_ptr, const int* d_set_sub,
+                               const SubDev* d_sub, const int64_t* d_s_off, const double* d_r, double* d_s,
+                               cudaStream_t st);
+cudaError_t launch_schwarz_combine(const SubDev* d_sub, int J, const int* d_inc_ptr, const int* d_inc_set,
+                                   const int* d_inc_pos, const int64_t* d_s_off, const double* d_s, int kind,
+                                   double* d_z, cudaStream_t st);
+cudaError_t launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* d_part,
+                            double* d_out, cudaStream_t st);
+cudaError_t launch_sub_combination(const double* V, int64_t ldv, int nv, const double* d_h, double* w,
+                                   int64_t n, cudaStream_t st);
+cudaError_t launch_add_combination(const double* V, int64_t ldv, int nv, const double* d_y, double* x,
+                                   int64_t n, cudaStream_t st);
+cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t st);
+cudaError_t launch_cg_update(double a, const double* p, const double* q, double* x, double* r, int64_t n,
+                             cudaStream_t st);
+cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, cudaStream_t st);
+cudaError_t launch_assemble_local(const double* d_pairbuf, const int64_t* d_tab, const int* d_tab_ptr,
+                                  const int* d_boff, const int* d_boff_ptr, const CholMat* d_mats, int nsets,
+                                  int maxn, double* d_dmax, cudaStream_t st);
+cudaError_t launch_add_diag(const CholMat* d_mats, const int* d_which, int nwhich, const double* d_shift,
+                            int maxn, cudaStream_t st);
+
+// ------------------------------------------------------------ errors --
+
+static thread_local char g_err[512] = "";
+
+void rann_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+#define CK(expr)                                                                         \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess) {                                                             \
+      rann_set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
+      return _e == cudaErrorMemoryAllocation ? RANN_ENOMEM : RANN_ECUDA;                 \
+    }                                                                                    \
+  } while (0)
+
+#define REQUIRE(cond, status, ...)            \
+  do {                                        \
+    if (!(cond)) {                            \
+      rann_set_error(__VA_ARGS__);            \
+      return status;                          \
+    }                                         \
+  } while (0)
+
+// ---------------------------------------------------- kernel families --
+// Every kernel launch goes through KL(), which counts launches per family and,
+// when profiling is on, brackets the launch with CUDA events on the handle's
+// stream (the times are the device durations of the launches).
+enum KId {
+  K_POINTS, K_ASSEMBLE, K_RHS, K_GRAM, K_SYMM, K_EIG, K_PROJECT, K_PAIRGRAM, K_LOCALASM, K_ADDDIAG,
+  K_CHOL, K_LOCALSOLVE, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL, K_COUNT
+};
+static const char* const KNAMES[K_COUNT] = {
+  "points", "assemble", "rhs", "gram", "symmetrize", "eig", "project", "pair_gram", "local_assemble",
+  "add_diag", "cholesky", "local_solve", "schwarz_combine", "matvec_H", "matvec_HT", "dot", "vector",
+  "eval"};
+
+// Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
+// 1 = float64-ALU-bound (algorithmic flops count).
+static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 0, 0, 0, 0, 0, 0, 1};
+
+struct Prof {
+  bool on = false;
+  int64_t launches[K_COUNT] = {};
+  double ms[K_COUNT] = {};
+  double bytes[K_COUNT] = {};
+  double flops[K_COUNT] = {};
+  struct Pend { int kid; cudaEvent_t a, b; };
+  std::vector<Pend> pending;
+  std::vector<cudaEvent_t> pool;
+};
+
+// ------------------------------------------------------------ handle --
+
+struct rann_dd_handle {
+  cudaStream_t st = nullptr;
+  ProbDev P{};
+  int J = 0, m = 0, dim = 0, Gmax = 0;
+  int64_t N = 0, rows_total = 0;
+  std::vector<SubDev> subs;
+  std::vector<int> cov;
+  std::vector<void*> allocs;
+  // device geometry / weights
+  SubDev* d_sub = nullptr;
+  int* d_cov = nullptr;
+  double* d_R = nullptr;
+  double* d_b = nullptr;
+  int* d_tiles = nullptr;
+  int ntiles = 0;
+  // assembly
+  bool assembled = false;
+  double* d_Psi = nullptr;
+  double* d_H = nullptr;
+  // pca
+  bool reduced = false;
+  double* d_eig = nullptr;
+  double* d_V = nullptr;
+  std::vector<double> eig_host;
+  double* d_B = nullptr;
+  int64_t dof = 0;
+  int maxP = 0;
+  int* d_rtiles = nullptr;
+  int nrtiles = 0;
+  int* d_tile0 = nullptr;
+  double* d_part = nullptr;
+  double* d_yscratch = nullptr;   // N
+  // precond
+  int prec_kind = -1;
+  int n_shifted = 0;
+  int nsets = 0, maxn = 0;
+  std::vector<int> set_ptr, set_sub;
+  CholMat* d_mats = nullptr;
+  int* d_set_ptr = nullptr;
+  int* d_set_sub = nullptr;
+  int* d_inc_ptr = nullptr;
+  int* d_inc_set = nullptr;
+  int* d_inc_pos = nullptr;
+  int64_t* d_s_off = nullptr;
+  double* d_s = nullptr;
+  double* d_Amats = nullptr;
+  double* d_pairbuf = nullptr;
+  // krylov scratch
+  double* d_red = nullptr;     // multidot partials
+  double* d_scal = nullptr;    // small device scalars
+  double* h_scal = nullptr;    // pinned host mirror
+  Prof prof;
+  // algorithmic size aggregates for the kernel accounting
+  double sumNp = 0, sumNm2 = 0, sumNmp = 0, sum_n = 0, sum_n2 = 0, sum_n3 = 0, pair_flops = 0;
+};
+
+static cudaEvent_t prof_event(rann_dd_handle* h) {
+  if (!h->prof.pool.empty()) { cudaEvent_t e = h->prof.pool.back(); h->prof.pool.pop_back(); return e; }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static void prof_resolve(rann_dd_handle* h) {
+  if (h->prof.pending.empty()) return;
+  cudaEventSynchronize(h->prof.pending.back().b);
+  for (auto& p : h->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->prof.ms[p.kid] += ms;
+    h->prof.pool.push_back(p.a);
+    h->prof.pool.push_back(p.b);
+  }
+  h->prof.pending.clear();
+}
+
+// Launch with accounting: nkern kernels, algorithmic bytes and flops of this launch.
+#define KLA(h, kid, nkern, nbytes, nflops, expr)                            \
+  do {                                                                      \
+    cudaEvent_t _a = nullptr, _b = nullptr;                                 \
+    if ((h)->prof.on) { _a = prof_event(h); cudaEventRecord(_a, (h)->st); } \
+    CK(expr);                                                               \
+    (h)->prof.launches[kid] += (nkern);                                     \
+    (h)->prof.bytes[kid] += (double)(nbytes);                               \
+    (h)->prof.flops[kid] += (double)(nflops);                               \
+    if ((h)->prof.on) {                                                     \
+      _b = prof_event(h);                                                   \
+      cudaEventRecord(_b, (h)->st);                                         \
+      (h)->prof.pending.push_back({kid, _a, _b});                           \
+      if ((h)->prof.pending.size() > 4096) prof_resolve(h);                 \
+    }                                                                       \
+  } while (0)
+#define KL(h, kid, nkern, expr) KLA(h, kid, nkern, 0, 0, expr)
+
+static cudaError_t dalloc(rann_dd_handle* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, h->st);
+  if (e == cudaSuccess) h->allocs.push_back(*p);
+  return e;
+}
+
+template <typename T>
+static cudaError_t dupload(rann_dd_handle* h, T** dst, const std::vector<T>& v) {
+  cudaError_t e = dalloc(h, (void**)dst, sizeof(T) * std::max<size_t>(v.size(), 1));
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, h->st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(h->st);   // the host vector may go out of scope
+}
+
+static void dfree(rann_dd_handle* h, void* p) {
+  if (!p) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it != h->allocs.end()) {
+    cudaFreeAsync(p, h->st);
+    h->allocs.erase(it);
+  }
+}
+
+static uint64_t splitmix64_draw(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+extern "C" const char* rann_dd_status_string(rann_status s) {
+  switch (s) {
+    case RANN_OK: return "ok";
+    case RANN_EINVAL: return "invalid argument";
+    case RANN_ENOMEM: return "out of memory";
+    case RANN_ECUDA: return "CUDA error";
+    case RANN_NOT_CONVERGED: return "not converged";
+    case RANN_BREAKDOWN: return "breakdown";
+    case RANN_LOCAL_SINGULAR: return "local factor shifted";
+    case RANN_EORDER: return "call out of order";
+  }
+  return "unknown";
+}
+
+extern "C" const char* rann_dd_last_error(void) { return g_err; }
+
+// ------------------------------------------------------------ create --
+
+extern "C" rann_status rann_dd_create(const rann_dd_desc* d, void* stream, rann_dd_handle** out) {
+  REQUIRE(d && out, RANN_EINVAL, "null descriptor or output");
+  *out = nullptr;
+  REQUIRE(d->dim == 2 || d->dim == 3, RANN_EINVAL, "dim must be 2 or 3");
+  REQUIRE(d->op >= 0 && d->op <= 2, RANN_EINVAL, "bad op");
+  REQUIRE(d->neurons >= 1 && d->neurons <= RANN_MAX_M, RANN_EINVAL, "neurons must be in 1..1024");
+  REQUIRE(d->f_terms >= 0 && d->f_terms <= RANN_MAX_FTERMS, RANN_EINVAL, "f_terms must be in 0..16");
+  REQUIRE(d->f_terms == 0 || (d->fc && d->fa), RANN_EINVAL, "fc/fa missing");
+  REQUIRE(d->rho > 0.0, RANN_EINVAL, "rho must be positive");
+  REQUIRE(d->layout == RANN_LAYOUT_CELL || d->layout == RANN_LAYOUT_PAPER, RANN_EINVAL, "bad layout");
+  REQUIRE(d->g_kind == RANN_G_ZERO || d->g_kind == RANN_G_SINPROD, RANN_EINVAL, "bad g_kind");
+  const int ns = d->op == RANN_OP_HEAT ? d->dim - 1 : d->dim;
+  if (d->op == RANN_OP_DIFFUSION) {
+    REQUIRE(d->coef >= 0 && d->coef <= 2, RANN_EINVAL, "bad coef");
+    REQUIRE(d->coef == RANN_COEF_CONST || ns >= 2, RANN_EINVAL, "x-y coefficients need 2 spatial dims");
+    if (d->coef == RANN_COEF_MULTISCALE) REQUIRE(d->eps > 0.0, RANN_EINVAL, "eps must be positive");
+    if (d->coef == RANN_COEF_PIECEWISE)
+      REQUIRE(d->coef_grid >= 1 && d->coef_grid <= 8 && d->coef_vals, RANN_EINVAL, "coef_grid in 1..8 with values");
+  }
+  for (int i = 0; i < d->dim; ++i) {
+    REQUIRE(d->sub[i] >= 1 && d->pts[i] >= 1, RANN_EINVAL, "sub/pts must be >= 1");
+    REQUIRE((int64_t)d->sub[i] * d->pts[i] <= (1 << 20), RANN_EINVAL, "grid too large");
+    if (d->layout == RANN_LAYOUT_PAPER) REQUIRE(d->sub[i] >= 2 && d->delta > 1.0, RANN_EINVAL, "paper layout needs l >= 2, delta > 1");
+    else REQUIRE(d->overlap[i] >= 0.0, RANN_EINVAL, "overlap must be >= 0");
+  }
+  rann_dd_handle* h = new rann_dd_handle();
+  h->st = (cudaStream_t)stream;
+  ProbDev& P = h->P;
+  P.dim = d->dim; P.ns = ns; P.op = d->op; P.coef = d->coef; P.g_kind = d->g_kind; P.m = d->neurons;
+  P.c0 = d->c0; P.nu = d->nu; P.coef_value = d->coef_value; P.eps = d->eps; P.rho = d->rho; P.f0 = d->f0;
+  P.coef_grid = d->coef_grid;
+  if (d->op == RANN_OP_DIFFUSION && d->coef == RANN_COEF_PIECEWISE)
+    for (int c = 0; c < d->coef_grid * d->coef_grid; ++c) P.coef_vals[c] = d->coef_vals[c];
+  P.f_terms = d->f_terms;
+  for (int t = 0; t < d->f_terms; ++t) {
+    P.fc[t] = d->fc[t];
+    for (int i = 0; i < d->dim; ++i) P.fa[t * d->dim + i] = d->fa[t * d->dim + i];
+  }
+  P.layout = d->layout;
+  h->dim = d->dim; h->m = d->neurons;
+  h->J = 1;
+  h->N = 1;
+  for (int i = 0; i < d->dim; ++i) {
+    P.G[i] = d->sub[i] * d->pts[i];
+    P.nsub[i] = d->sub[i];
+    P.sig[i] = d->layout == RANN_LAYOUT_PAPER ? 0.5 * d->delta / (double)(d->sub[i] - 1)
+                                              : 0.5 * (1.0 / d->sub[i] + d->overlap[i]);
+    h->J *= d->sub[i];
+    h->N *= P.G[i];
+    h->Gmax = std::max(h->Gmax, P.G[i]);
+  }
+  for (int i = d->dim; i < 3; ++i) { P.G[i] = 1; P.nsub[i] = 1; P.sig[i] = 1.0; }
+  // boxes per dim: grid indices strictly inside |x_q - mu_k| < sigma
+  std::vector<std::vector<int>> blo(3), bhi(3);
+  for (int i = 0; i < d->dim; ++i) {
+    blo[i].assign(d->sub[i], -1);
+    bhi[i].assign(d->sub[i], -1);
+    for (int k = 0; k < d->sub[i]; ++k) {
+      double mu = host_mu(d->layout, k, d->sub[i]);
+      for (int q = 0; q < P.G[i]; ++q) {
+        double x = ((double)q + 0.5) / (double)P.G[i];
+        if (std::fabs(x - mu) < P.sig[i]) {
+          if (blo[i][k] < 0) blo[i][k] = q;
+          bhi[i][k] = q + 1;
+        }
+      }
+      if (blo[i][k] < 0) {
+        delete h;
+        rann_set_error("subdomain %d along dim %d holds no collocation point", k, i);
+        return RANN_EINVAL;
+      }
+    }
+  }
+  h->cov.assign((size_t)3 * h->Gmax * 2, 0);
+  for (int i = 0; i < 3; ++i)
+    for (int q = 0; q < h->Gmax; ++q) { h->cov[(i * h->Gmax + q) * 2] = 0; h->cov[(i * h->Gmax + q) * 2 + 1] = 1; }
+  for (int i = 0; i < d->dim; ++i)
+    for (int q = 0; q < P.G[i]; ++q) {
+      int first = -1, cnt = 0;
+      for (int k = 0; k < d->sub[i]; ++k)
+        if (q >= blo[i][k] && q < bhi[i][k]) { if (first < 0) first = k; ++cnt; }
+      h->cov[(i * h->Gmax + q) * 2] = first;
+      h->cov[(i * h->Gmax + q) * 2 + 1] = cnt;
+    }
+  h->subs.resize(h->J);
+  int64_t row0 = 0;
+  for (int j = 0; j < h->J; ++j) {
+    SubDev& S = h->subs[j];
+    memset(&S, 0, sizeof(S));
+    int rem = j;
+    S.N = 1;
+    for (int i = 0; i < 3; ++i) {
+      if (i < d->dim) {
+        S.k[i] = rem % d->sub[i];
+        rem /= d->sub[i];
+        S.lo[i] = blo[i][S.k[i]];
+        S.n[i] = bhi[i][S.k[i]] - blo[i][S.k[i]];
+        S.mu[i] = host_mu(d->layout, S.k[i], d->sub[i]);
+      } else {
+        S.k[i] = 0; S.lo[i] = 0; S.n[i] = 1; S.mu[i] = 0.0;
+      }
+      S.N *= S.n[i];
+    }
+    S.row0 = row0;
+    S.p = h->m;
+    S.P = h->m;
+    row0 += S.N;
+  }
+  h->rows_total = row0;
+  // weights
+  const int m = h->m, dim = d->dim;
+  std::vector<double> R((size_t)h->J * m * dim), b((size_t)h->J * m);
+  if (d->R && d->b) {
+    memcpy(R.data(), d->R, sizeof(double) * R.size());
+    memcpy(b.data(), d->b, sizeof(double) * b.size());
+  } else {
+    const uint64_t per = (uint64_t)m * dim + m;
+    for (int j = 0; j < h->J; ++j)
+      for (uint64_t t = 0; t < per; ++t) {
+        double u = (double)(splitmix64_draw(d->seed, (uint64_t)j * per + t) >> 11) * 0x1.0p-53;
+        double v = -d->w_range + 2.0 * d->w_range * u;
+        if (t < (uint64_t)m * dim) R[(size_t)j * m * dim + t] = v;
+        else b[(size_t)j * m + (t - (uint64_t)m * dim)] = v;
+      }
+  }
+  std::vector<int> tiles;
+  for (int j = 0; j < h->J; ++j)
+    for (int r0 = 0; r0 < h->subs[j].N; r0 += 32) { tiles.push_back(j); tiles.push_back(r0); }
+  h->ntiles = (int)tiles.size() / 2;
+  cudaError_t e;
+  if ((e = dupload(h, &h->d_sub, h->subs)) != cudaSuccess || (e = dupload(h, &h->d_cov, h->cov)) != cudaSuccess ||
+      (e = dupload(h, &h->d_R, R)) != cudaSuccess || (e = dupload(h, &h->d_b, b)) != cudaSuccess ||
+      (e = dupload(h, &h->d_tiles, tiles)) != cudaSuccess ||
+      (e = dalloc(h, (void**)&h->d_red, sizeof(double) * 256 * 130)) != cudaSuccess ||
+      (e = dalloc(h, (void**)&h->d_scal, sizeof(double) * 256)) != cudaSuccess ||
+      (e = cudaMallocHost((void**)&h->h_scal, sizeof(double) * 256)) != cudaSuccess) {
+    rann_set_error("create: %s", cudaGetErrorString(e));
+    rann_dd_destroy(h);
+    return e == cudaErrorMemoryAllocation ? RANN_ENOMEM : RANN_ECUDA;
+  }
+  *out = h;
+  return RANN_OK;
+}
+
+extern "C" void rann_dd_destroy(rann_dd_handle* h) {
+  if (!h) return;
+  for (void* p : h->allocs) cudaFreeAsync(p, h->st);
+  cudaStreamSynchronize(h->st);
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  prof_resolve(h);
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+  delete h;
+}
+
+extern "C" rann_status rann_dd_sizes(rann_dd_handle* h, int64_t* n_points, int64_t* n_block_rows, int* J, int* m,
+                                     int64_t* dof) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  if (n_points) *n_points = h->N;
+  if (n_block_rows) *n_block_rows = h->rows_total;
+  if (J) *J = h->J;
+  if (m) *m = h->m;
+  if (dof) *dof = h->reduced ? h->dof : (int64_t)h->J * h->m;
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_points(rann_dd_handle* h, double* xyz_dev) {
+  REQUIRE(h && xyz_dev, RANN_EINVAL, "null argument");
+  KL(h, K_POINTS, 1, launch_points(h->P, xyz_dev, h->N, h->st));
+  return RANN_OK;
+}
+
+// ---------------------------------------------------------- assemble --
+
+extern "C" rann_status rann_dd_assemble(rann_dd_handle* h) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  const size_t bytes = sizeof(double) * (size_t)h->rows_total * h->m;
+  if (!h->d_Psi) {
+    CK(dalloc(h, (void**)&h->d_Psi, bytes));
+    CK(dalloc(h, (void**)&h->d_H, bytes));
+  }
+  KLA(h, K_ASSEMBLE, 1, 16.0 * h->rows_total * h->m, (double)h->rows_total * h->m * (2 * h->dim + 8), launch_assemble(h->P, h->d_sub, h->d_tiles, h->ntiles, h->d_cov, h->d_R, h->d_b, h->d_Psi, h->d_H, h->st));
+  h->assembled = true;
+  h->reduced = false;
+  h->prec_kind = -1;
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_rhs(rann_dd_handle* h, double* F_dev) {
+  REQUIRE(h && F_dev, RANN_EINVAL, "null argument");
+  KL(h, K_RHS, 1, launch_rhs(h->P, F_dev, h->N, h->st));
+  return RANN_OK;
+}
+
+// --------------------------------------------------------------- pca --
+
+static void push_tiles(std::vector<GemmTask>& out, GemmTask t, bool upper) {
+  for (int tm = 0; tm < t.M; tm += 64)
+    for (int tn = 0; tn < t.N; tn += 64) {
+      if (upper && tn + 64 <= tm) continue;
+      GemmTask x = t;
+      x.tm = tm;
+      x.tn = tn;
+      out.push_back(x);
+    }
+}
+
+extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int* ranks_host) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  REQUIRE(h->assembled, RANN_EORDER, "pca before assemble");
+  REQUIRE(mode >= 0 && mode <= 2, RANN_EINVAL, "bad pca mode");
+  REQUIRE(mode == RANN_PCA_NONE || (thr >= 0.0 && std::isfinite(thr)), RANN_EINVAL, "bad threshold");
+  const int J = h->J, m = h->m;
+  const size_t mm = (size_t)m * m;
+  if (!h->d_V) {
+    CK(dalloc(h, (void**)&h->d_V, sizeof(double) * mm * J));
+    CK(dalloc(h, (void**)&h->d_eig, sizeof(double) * (size_t)m * J));
+  }
+  std::vector<int> info(J, 0);
+  h->eig_host.assign((size_t)m * J, 0.0);
+  h->sumNm2 = 0;
+  for (int j = 0; j < J; ++j) h->sumNm2 += (double)h->subs[j].N * m * (m + 1);
+  // Gram matrices Psi_j^T Psi_j (upper tiles) then eigen-decomposition
+  {
+    std::vector<GemmTask> tasks;
+    for (int j = 0; j < J; ++j) {
+      const SubDev& S = h->subs[j];
+      GemmTask t{};
+      t.A = h->d_Psi + S.row0 * m; t.B = t.A; t.C = h->d_V + mm * j;
+      t.K = S.N; t.M = m; t.N = m; t.lda = m; t.ldb = m; t.ldc = m;
+      push_tiles(tasks, t, true);
+    }
+    GemmTask* d_tasks;
+    CK(dupload(h, &d_tasks, tasks));
+    KLA(h, K_GRAM, 1, 8.0 * h->rows_total * m, h->sumNm2, launch_gemm_tn(d_tasks, (int)tasks.size(), h->st));
+    std::vector<double*> mats(J);
+    std::vector<int> ns(J, m), lds(J, m);
+    for (int j = 0; j < J; ++j) mats[j] = h->d_V + mm * j;
+    double** d_mats; int* d_ns; int* d_lds;
+    CK(dupload(h, &d_mats, mats)); CK(dupload(h, &d_ns, ns)); CK(dupload(h, &d_lds, lds));
+    KL(h, K_SYMM, 1, launch_symmetrize(d_mats, d_ns, d_lds, J, m, h->st));
+    double* d_work; int* d_info;
+    CK(dalloc(h, (void**)&d_work, sizeof(double) * mm * J));
+    CK(dalloc(h, (void**)&d_info, sizeof(int) * J));
+    KLA(h, K_EIG, 1, 24.0 * mm * J, 9.0 * (double)m * mm * J, launch_syevd(h->d_V, m, m, J, h->d_eig, d_work, d_info, h->st));
+    CK(cudaMemcpyAsync(h->eig_host.data(), h->d_eig, sizeof(double) * m * J, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(info.data(), d_info, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    dfree(h, d_tasks); dfree(h, d_mats); dfree(h, d_ns); dfree(h, d_lds); dfree(h, d_work); dfree(h, d_info);
+  }
+  for (int j = 0; j < J; ++j)
+    REQUIRE(info[j] == 0, RANN_ECUDA, "eigen-decomposition of subdomain %d did not converge", j);
+  if (mode == RANN_PCA_NONE) {   // V = I, p = m
+    std::vector<double> I(mm * J, 0.0);
+    for (int j = 0; j < J; ++j)
+      for (int c = 0; c < m; ++c) I[mm * j + (size_t)c * m + c] = 1.0;
+    CK(cudaMemcpyAsync(h->d_V, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  // ranks (Sec. 4): sigma_k = sqrt(max(lambda_k, 0))
+  int64_t woff = 0, boff = 0;
+  h->maxP = 0;
+  for (int j = 0; j < J; ++j) {
+    const double* lam = h->eig_host.data() + (size_t)m * j;
+    int p = m;
+    if (mode == RANN_PCA_ABS) {
+      p = 0;
+      for (int k = 0; k < m; ++k) if (std::sqrt(std::max(lam[k], 0.0)) > thr) ++p;
+    } else if (mode == RANN_PCA_VARIANCE) {
+      double tot = 0.0;
+      for (int k = 0; k < m; ++k) tot += std::max(lam[k], 0.0);
+      double cs = 0.0;
+      p = m;
+      for (int k = 0; k < m; ++k) {
+        cs += std::max(lam[k], 0.0);
+        if (cs >= (1.0 - thr) * tot) { p = k + 1; break; }
+      }
+    }
+    p = std::max(p, 1);
+    SubDev& S = h->subs[j];
+    S.p = p;
+    S.P = p + (p & 1);
+    S.woff = woff;
+    S.boff = boff;
+    woff += p;
+    boff += (int64_t)S.N * S.P;
+    h->maxP = std::max(h->maxP, S.P);
+    if (ranks_host) ranks_host[j] = p;
+  }
+  h->dof = woff;
+  h->sumNp = h->sumNm2 = h->sumNmp = 0;
+  for (int j = 0; j < J; ++j) {
+    const SubDev& S = h->subs[j];
+    h->sumNp += (double)S.N * S.p;
+    h->sumNm2 += (double)S.N * m * (m + 1);
+    h->sumNmp += (double)S.N * m * S.p;
+  }
+  if (h->d_B) dfree(h, h->d_B);
+  CK(dalloc(h, (void**)&h->d_B, sizeof(double) * (size_t)boff));
+  CK(cudaMemsetAsync(h->d_B, 0, sizeof(double) * (size_t)boff, h->st));
+  {
+    std::vector<GemmTask> tasks;
+    for (int j = 0; j < J; ++j) {
+      const SubDev& S = h->subs[j];
+      GemmTask t{};
+      t.A = h->d_H + S.row0 * m; t.B = h->d_V + mm * j; t.C = h->d_B + S.boff;
+      t.K = m; t.M = S.N; t.N = S.p; t.lda = m; t.ldb = m; t.ldc = S.P;
+      push_tiles(tasks, t, false);
+    }
+    GemmTask* d_tasks;
+    CK(dupload(h, &d_tasks, tasks));
+    KLA(h, K_PROJECT, 1, 8.0 * (h->rows_total * (double)m + h->sumNp), 2.0 * h->sumNmp, launch_gemm_nn(d_tasks, (int)tasks.size(), h->st));
+    CK(cudaStreamSynchronize(h->st));
+    dfree(h, d_tasks);
+  }
+  CK(cudaMemcpyAsync(h->d_sub, h->subs.data(), sizeof(SubDev) * J, cudaMemcpyHostToDevice, h->st));
+  // H^T row tiles
+  std::vector<int> rt, t0(J + 1, 0);
+  for (int j = 0; j < J; ++j) {
+    t0[j] = (int)rt.size() / 2;
+    for (int r0 = 0; r0 < h->subs[j].N; r0 += 256) { rt.push_back(j); rt.push_back(r0); }
+  }
+  t0[J] = (int)rt.size() / 2;
+  h->nrtiles = t0[J];
+  if (h->d_rtiles) { dfree(h, h->d_rtiles); dfree(h, h->d_tile0); dfree(h, h->d_part); dfree(h, h->d_yscratch); }
+  CK(dupload(h, &h->d_rtiles, rt));
+  CK(dupload(h, &h->d_tile0, t0));
+  CK(dalloc(h, (void**)&h->d_part, sizeof(double) * (size_t)h->nrtiles * h->maxP));
+  CK(dalloc(h, (void**)&h->d_yscratch, sizeof(double) * (size_t)h->N));
+  CK(cudaStreamSynchronize(h->st));
+  h->reduced = true;
+  h->prec_kind = -1;
+  return RANN_OK;
+}
+
+// ------------------------------------------------------------ matvecs --
+
+extern "C" rann_status rann_dd_matvec(rann_dd_handle* h, const double* x_dev, double* y_dev) {
+  REQUIRE(h && x_dev && y_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->reduced, RANN_EORDER, "matvec before pca");
+  KLA(h, K_MATVEC_H, 1, 8.0 * (h->sumNp + h->N + h->dof), 2.0 * h->sumNp, launch_matvec_H2(h->P, h->d_sub, h->d_cov, h->Gmax, h->d_B, x_dev, y_dev, h->N, h->st));
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_matvec_t(rann_dd_handle* h, const double* y_dev, double* z_dev) {
+  REQUIRE(h && y_dev && z_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->reduced, RANN_EORDER, "matvec before pca");
+  KLA(h, K_MATVEC_HT, 2, 8.0 * (h->sumNp + h->rows_total + h->dof), 2.0 * h->sumNp, launch_matvec_HT2(h->P, h->d_sub, h->J, h->d_rtiles, h->nrtiles, h->d_tile0, h->d_B, y_dev, h->d_part,
+                       z_dev, h->maxP, h->st));
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_normal_matvec(rann_dd_handle* h, const double* x_dev, double* z_dev) {
+  REQUIRE(h && x_dev && z_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->reduced, RANN_EORDER, "matvec before pca");
+  KLA(h, K_MATVEC_H, 1, 8.0 * (h->sumNp + h->N + h->dof), 2.0 * h->sumNp, launch_matvec_H2(h->P, h->d_sub, h->d_cov, h->Gmax, h->d_B, x_dev, h->d_yscratch, h->N, h->st));
+  KLA(h, K_MATVEC_HT, 2, 8.0 * (h->sumNp + h->rows_total + h->dof), 2.0 * h->sumNp, launch_matvec_HT2(h->P, h->d_sub, h->J, h->d_rtiles, h->nrtiles, h->d_tile0, h->d_B, h->d_yscratch,
+                       h->d_part, z_dev, h->maxP, h->st));
+  return RANN_OK;
+}
+
+// ------------------------------------------------------------ precond --
+
+static bool boxes_meet(const SubDev& a, const SubDev& b, int dim) {
+  for (int i = 0; i < dim; ++i)
+    if (std::max(a.lo[i], b.lo[i]) >= std::min(a.lo[i] + a.n[i], b.lo[i] + b.n[i])) return false;
+  return true;
+}
+
+extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int overlap_level) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  REQUIRE(h->reduced, RANN_EORDER, "setup_precond before pca");
+  REQUIRE(kind >= RANN_PREC_NONE && kind <= RANN_PREC_RAS, RANN_EINVAL, "bad preconditioner kind");
+  REQUIRE(overlap_level == 0 || overlap_level == 1, RANN_EINVAL, "overlap_level must be 0 or 1");
+  // release a previous setup
+  for (void* p : {(void*)h->d_mats, (void*)h->d_set_ptr, (void*)h->d_set_sub, (void*)h->d_inc_ptr,
+                  (void*)h->d_inc_set, (void*)h->d_inc_pos, (void*)h->d_s_off, (void*)h->d_s,
+                  (void*)h->d_Amats})
+    dfree(h, p);
+  h->d_mats = nullptr; h->d_Amats = nullptr;
+  h->n_shifted = 0;
+  h->prec_kind = kind;
+  if (kind == RANN_PREC_NONE) return RANN_OK;
+  const int J = h->J, dim = h->dim;
+  const auto& S = h->subs;
+  // extended sets N(i)
+  h->set_ptr.assign(1, 0);
+  h->set_sub.clear();
+  for (int i = 0; i < J; ++i) {
+    for (int k = 0; k < J; ++k)
+      if (overlap_level == 0 ? k == i : boxes_meet(S[i], S[k], dim)) h->set_sub.push_back(k);
+    h->set_ptr.push_back((int)h->set_sub.size());
+  }
+  h->nsets = J;
+  // neighbour pairs (k <= l whose boxes share points) and their Gram blocks B_k^T B_l
+  std::vector<int64_t> pair_off((size_t)J * J, -1);
+  std::vector<GemmTask> tasks;
+  std::vector<int> ridx;
+  std::vector<std::pair<int64_t, int64_t>> ridx_ranges;   // (start in ridx for A rows, for B rows)
+  int64_t pbuf = 0;
+  std::vector<std::pair<int, int>> pairs;
+  for (int i = 0; i < J; ++i)
+    for (int q = h->set_ptr[i]; q < h->set_ptr[i + 1]; ++q)
+      for (int q2 = h->set_ptr[i]; q2 < h->set_ptr[i + 1]; ++q2) {
+        int k = h->set_sub[q], l = h->set_sub[q2];
+        if (k > l || pair_off[(size_t)k * J + l] != -1 || !boxes_meet(S[k], S[l], dim)) continue;
+        pair_off[(size_t)k * J + l] = pbuf;
+        pbuf += (int64_t)S[k].p * S[l].p;
+        pairs.push_back({k, l});
+      }
+  for (auto& pr : pairs) {
+    const SubDev &a = S[pr.first], &b = S[pr.second];
+    int lo[3], hi[3];
+    for (int i = 0; i < 3; ++i) {
+      lo[i] = std::max(a.lo[i], b.lo[i]);
+      hi[i] = std::min(a.lo[i] + a.n[i], b.lo[i] + b.n[i]);
+    }
+    int64_t startA = (int64_t)ridx.size();
+    std::vector<int> rb;
+    for (int q2 = lo[2]; q2 < hi[2]; ++q2)
+      for (int q1 = lo[1]; q1 < hi[1]; ++q1)
+        for (int q0 = lo[0]; q0 < hi[0]; ++q0) {
+          ridx.push_back((q0 - a.lo[0]) + a.n[0] * ((q1 - a.lo[1]) + a.n[1] * (q2 - a.lo[2])));
+          rb.push_back((q0 - b.lo[0]) + b.n[0] * ((q1 - b.lo[1]) + b.n[1] * (q2 - b.lo[2])));
+        }
+    int64_t startB = (int64_t)ridx.size();
+    ridx.insert(ridx.end(), rb.begin(), rb.end());
+    ridx_ranges.push_back({startA, startB});
+  }
+  h->pair_flops = 0;
+  for (size_t t = 0; t < pairs.size(); ++t)
+    h->pair_flops += 2.0 * (double)(ridx_ranges[t].second - ridx_ranges[t].first) * S[pairs[t].first].p *
+                     S[pairs[t].second].p;
+  int* d_ridx;
+  CK(dupload(h, &d_ridx, ridx));
+  CK(dalloc(h, (void**)&h->d_pairbuf, sizeof(double) * (size_t)std::max<int64_t>(pbuf, 1)));
+  for (size_t t = 0; t < pairs.size(); ++t) {
+    const SubDev &a = S[pairs[t].first], &b = S[pairs[t].second];
+    GemmTask g{};
+    g.A = h->d_B + a.boff; g.B = h->d_B + b.boff;
+    g.C = h->d_pairbuf + pair_off[(size_t)pairs[t].first * J + pairs[t].second];
+    g.ia = d_ridx + ridx_ranges[t].first;
+    g.ib = d_ridx + ridx_ranges[t].second;
+    g.K = (int)(ridx_ranges[t].second - ridx_ranges[t].first);
+    g.M = a.p; g.N = b.p; g.lda = a.P; g.ldb = b.P; g.ldc = b.p;
+    push_tiles(tasks, g, false);
+  }
+  GemmTask* d_tasks;
+  CK(dupload(h, &d_tasks, tasks));
+  KLA(h, K_PAIRGRAM, 1, 0, h->pair_flops, launch_gemm_tn(d_tasks, (int)tasks.size(), h->st));
+  // local matrices A_i: table of block sources
+  std::vector<CholMat> mats(J);
+  std::vector<int64_t> tab;      // per (i, a, b): pair offset, or -1; sign bit 1<<62 marks transpose
+  std::vector<int> tab_ptr(1, 0), boffs, boff_ptr(1, 0);
+  int64_t aoff = 0;
+  h->maxn = 0;
+  std::vector<int64_t> s_off(J + 1, 0);
+  for (int i = 0; i < J; ++i) {
+    int n = 0;
+    for (int q = h->set_ptr[i]; q < h->set_ptr[i + 1]; ++q) { boffs.push_back(n); n += S[h->set_sub[q]].p; }
+    boffs.push_back(n);
+    boff_ptr.push_back((int)boffs.size());
+    mats[i].n = n; mats[i].ld = n;
+    mats[i].A = reinterpret_cast<double*>(aoff);   // patched below
+    aoff += (int64_t)n * n;
+    s_off[i + 1] = s_off[i] + n;
+    h->maxn = std::max(h->maxn, n);
+    for (int q = h->set_ptr[i]; q < h->set_ptr[i + 1]; ++q)
+      for (int q2 = h->set_ptr[i]; q2 < h->set_ptr[i + 1]; ++q2) {
+        int k = h->set_sub[q], l = h->set_sub[q2];
+        int64_t off = k <= l ? pair_off[(size_t)k * J + l] : pair_off[(size_t)l * J + k];
+        if (off >= 0 && k > l) off |= (int64_t)1 << 62;
+        tab.push_back(off);
+      }
+    tab_ptr.push_back((int)tab.size());
+  }
+  CK(dalloc(h, (void**)&h->d_Amats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
+  h->sum_n = h->sum_n2 = h->sum_n3 = 0;
+  for (int i = 0; i < J; ++i) {
+    const double n = mats[i].n;
+    h->sum_n += n; h->sum_n2 += n * n; h->sum_n3 += n * n * n;
+  }
+  for (int i = 0; i < J; ++i) mats[i].A = h->d_Amats + reinterpret_cast<int64_t>(mats[i].A);
+  int64_t* d_tab; int *d_tab_ptr, *d_boffs, *d_boff_ptr; double* d_dmax; int* d_fail;
+  CK(dupload(h, &d_tab, tab)); CK(dupload(h, &d_tab_ptr, tab_ptr));
+  CK(dupload(h, &d_boffs, boffs)); CK(dupload(h, &d_boff_ptr, boff_ptr));
+  CK(dupload(h, &h->d_mats, mats));
+  CK(dalloc(h, (void**)&d_dmax, sizeof(double) * J));
+  CK(dalloc(h, (void**)&d_fail, sizeof(int) * J));
+  KLA(h, K_LOCALASM, 2, 8.0 * h->sum_n2, 0, launch_assemble_local(h->d_pairbuf, d_tab, d_tab_ptr, d_boffs, d_boff_ptr, h->d_mats, J, h->maxn, d_dmax, h->st));
+  // Cholesky with shift-and-retry for failed pivots
+  std::vector<int> fail(J, 0);
+  std::vector<int> active(J);
+  std::iota(active.begin(), active.end(), 0);
+  std::vector<double> dmax(J);
+  CK(cudaMemcpyAsync(dmax.data(), d_dmax, sizeof(double) * J, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  std::vector<int> shifted(J, 0);
+  for (int attempt = 0; attempt < 6 && !active.empty(); ++attempt) {
+    std::vector<CholMat> am;
+    std::vector<double> adm;
+    for (int i : active) { am.push_back(mats[i]); adm.push_back(dmax[i]); }
+    CholMat* d_am; double* d_adm;
+    CK(dupload(h, &d_am, am)); CK(dupload(h, &d_adm, adm));
+    int amax = 0;
+    double chol_flops = 0.0;
+    for (auto& c : am) { amax = std::max(amax, c.n); chol_flops += (double)c.n * c.n * c.n / 3.0; }
+    CK(cudaMemsetAsync(d_fail, 0, sizeof(int) * J, h->st));
+    for (int c0 = 0; c0 < amax; c0 += 32)
+      KLA(h, K_CHOL, (amax - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0, launch_chol_step(d_am, (int)am.size(), amax, c0, d_fail, d_adm, h->st));
+    std::vector<int> f(am.size());
+    CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * am.size(), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    std::vector<int> next;
+    for (size_t t = 0; t < am.size(); ++t) if (f[t]) next.push_back(active[t]);
+    dfree(h, d_am); dfree(h, d_adm);
+    if (next.empty()) break;
+    // rebuild the failed matrices and add a growing diagonal shift
+    std::vector<CholMat> fm;
+    std::vector<int> which;
+    std::vector<double> shift;
+    for (int i : next) {
+      shifted[i] = 1;
+      which.push_back((int)fm.size());
+      fm.push_back(mats[i]);
+      shift.push_back(dmax[i] * std::pow(10.0, -14 + 2 * attempt));
+    }
+    // reassemble all (cheap relative to the factorisation), then shift the failed ones
+    KLA(h, K_LOCALASM, 2, 8.0 * h->sum_n2, 0, launch_assemble_local(h->d_pairbuf, d_tab, d_tab_ptr, d_boffs, d_boff_ptr, h->d_mats, J, h->maxn, d_dmax, h->st));
+    CholMat* d_fm; int* d_which; double* d_shift;
+    CK(dupload(h, &d_fm, fm)); CK(dupload(h, &d_which, which)); CK(dupload(h, &d_shift, shift));
+    KL(h, K_ADDDIAG, 1, launch_add_diag(d_fm, d_which, (int)which.size(), d_shift, h->maxn, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    dfree(h, d_fm); dfree(h, d_which); dfree(h, d_shift);
+    // the successful ones were overwritten by the reassembly: refactor everything still needed
+    active.clear();
+    for (int i = 0; i < J; ++i) active.push_back(i);
+    if (attempt == 5) { rann_set_error("local Cholesky failed after shifts"); return RANN_ECUDA; }
+  }
+  for (int i = 0; i < J; ++i) h->n_shifted += shifted[i];
+  // incidence lists for the combine step: sets containing each subdomain, with its block offset
+  std::vector<int> inc_ptr(1, 0), inc_set, inc_pos;
+  for (int k = 0; k < J; ++k) {
+    for (int i = 0; i < J; ++i) {
+      int pos = 0;
+      for (int q = h->set_ptr[i]; q < h->set_ptr[i + 1]; ++q) {
+        if (h->set_sub[q] == k) { inc_set.push_back(i); inc_pos.push_back(pos); }
+        pos += S[h->set_sub[q]].p;
+      }
+    }
+    inc_ptr.push_back((int)inc_set.size());
+  }
+  CK(dupload(h, &h->d_set_ptr, h->set_ptr)); CK(dupload(h, &h->d_set_sub, h->set_sub));
+  CK(dupload(h, &h->d_inc_ptr, inc_ptr)); CK(dupload(h, &h->d_inc_set, inc_set)); CK(dupload(h, &h->d_inc_pos, inc_pos));
+  CK(dupload(h, &h->d_s_off, s_off));
+  CK(dalloc(h, (void**)&h->d_s, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
+  dfree(h, d_ridx); dfree(h, d_tasks); dfree(h, d_tab); dfree(h, d_tab_ptr); dfree(h, d_boffs); dfree(h, d_boff_ptr);
+  dfree(h, d_dmax); dfree(h, d_fail); dfree(h, h->d_pairbuf);
+  h->d_pairbuf = nullptr;
+  CK(cudaStreamSynchronize(h->st));
+  return h->n_shifted ? RANN_LOCAL_SINGULAR : RANN_OK;
+}
+
+static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z) {
+  if (h->prec_kind == RANN_PREC_NONE) {
+    CK(cudaMemcpyAsync(z, r, sizeof(double) * h->dof, cudaMemcpyDeviceToDevice, h->st));
+    return RANN_OK;
+  }
+  KLA(h, K_LOCALSOLVE, 1, 8.0 * (h->sum_n2 + 4.0 * h->sum_n), 2.0 * h->sum_n2, launch_local_solve(h->d_mats, h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub, h->d_s_off, r, h->d_s, h->st));
+  KLA(h, K_COMBINE, 1, 8.0 * (h->sum_n + h->dof), 0, launch_schwarz_combine(h->d_sub, h->J, h->d_inc_ptr, h->d_inc_set, h->d_inc_pos, h->d_s_off, h->d_s,
+                            h->prec_kind, z, h->st));
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_precond_apply(rann_dd_handle* h, const double* r_dev, double* z_dev) {
+  REQUIRE(h && r_dev && z_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "precond_apply before setup_precond");
+  return prec_apply(h, r_dev, z_dev);
+}
+
+// -------------------------------------------------------------- solves --
+
+static rann_status dot_host(rann_dd_handle* h, const double* x, const double* y, int64_t n, double* out) {
+  KLA(h, K_DOT, 2, 16.0 * n, 2.0 * n, launch_multidot(x, 0, 1, y, n, h->d_red, h->d_scal, h->st));
+  CK(cudaMemcpyAsync(h->h_scal, h->d_scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  *out = h->h_scal[0];
+  return RANN_OK;
+}
+
+#define TRY(x) do { rann_status _s = (x); if (_s != RANN_OK) return _s; } while (0)
+
+struct Workspace {
+  rann_dd_handle* h;
+  std::vector<double*> bufs;
+  ~Workspace() { for (double* p : bufs) dfree(h, p); }
+  double* get(size_t n) {
+    double* p = nullptr;
+    if (dalloc(h, (void**)&p, sizeof(double) * std::max<size_t>(n, 1)) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return p;
+  }
+};
+
+extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
+                                           int maxit, rann_dd_stats* stats) {
+  REQUIRE(h && F_dev && W_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve before setup_precond");
+  REQUIRE(h->prec_kind == RANN_PREC_AS || h->prec_kind == RANN_PREC_NONE, RANN_EINVAL,
+          "CG needs a symmetric preconditioner (AS or none)");
+  REQUIRE(rtol > 0 && maxit >= 0, RANN_EINVAL, "bad rtol/maxit");
+  const int64_t n = h->dof;
+  Workspace ws{h, {}};
+  double *b = ws.get(n), *r = ws.get(n), *z = ws.get(n), *p = ws.get(n), *q = ws.get(n);
+  REQUIRE(b && r && z && p && q, RANN_ENOMEM, "workspace allocation failed");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, h->st));
+  TRY(rann_dd_matvec_t(h, F_dev, b));
+  CK(cudaMemsetAsync(W_dev, 0, sizeof(double) * n, h->st));
+  CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  double bb, rz, rel = 1.0;
+  TRY(dot_host(h, b, b, n, &bb));
+  const double bnorm = std::sqrt(bb);
+  rann_status st = RANN_NOT_CONVERGED;
+  int it = 0;
+  if (!(bnorm > 0.0)) { st = std::isfinite(bb) ? RANN_OK : RANN_BREAKDOWN; rel = 0.0; }
+  else {
+    TRY(prec_apply(h, r, z));
+    CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+    TRY(dot_host(h, r, z, n, &rz));
+    while (it < maxit) {
+      TRY(rann_dd_normal_matvec(h, p, q));
+      double pq;
+      TRY(dot_host(h, p, q, n, &pq));
+      if (!(pq > 0.0) || !std::isfinite(pq)) { st = RANN_BREAKDOWN; break; }
+      double alpha = rz / pq;
+      KLA(h, K_VEC, 1, 40.0 * n, 4.0 * n, launch_cg_update(alpha, p, q, W_dev, r, n, h->st));
+      ++it;
+      double rr;
+      TRY(dot_host(h, r, r, n, &rr));
+      rel = std::sqrt(rr) / bnorm;
+      if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
+      if (rel <= rtol) { st = RANN_OK; break; }
+      TRY(prec_apply(h, r, z));
+      double rz2;
+      TRY(dot_host(h, r, z, n, &rz2));
+      KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, z, rz2 / rz, p, n, h->st));
+      rz = rz2;
+    }
+  }
+  // true residual
+  double tr = 0.0;
+  TRY(rann_dd_normal_matvec(h, W_dev, q));
+  KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b, -1.0, q, n, h->st));
+  TRY(dot_host(h, q, q, n, &tr));
+  CK(cudaEventRecord(e1, h->st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  if (stats) {
+    stats->iters = it;
+    stats->rel_res_true = bnorm > 0 ? std::sqrt(tr) / bnorm : 0.0;
+    stats->rel_res_rec = rel;
+    stats->rel_res_prec = -1.0;
+    stats->ms_solve = ms;
+    stats->n_shifted = h->n_shifted;
+  }
+  if (st == RANN_NOT_CONVERGED) rann_set_error("CG reached maxit=%d at rel. residual %.3e", maxit, rel);
+  return st;
+}
+
+extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
+                                               int restart, int maxit, rann_dd_stats* stats) {
+  REQUIRE(h && F_dev && W_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve before setup_precond");
+  REQUIRE(rtol > 0 && maxit >= 0 && restart >= 1 && restart <= 120, RANN_EINVAL, "bad rtol/restart/maxit");
+  const int64_t n = h->dof;
+  const int k = restart;
+  Workspace ws{h, {}};
+  double *b = ws.get(n), *t = ws.get(n), *V = ws.get((size_t)(k + 1) * n), *hv = ws.get(2 * (k + 2));
+  REQUIRE(b && t && V && hv, RANN_ENOMEM, "workspace allocation failed");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, h->st));
+  TRY(rann_dd_matvec_t(h, F_dev, b));
+  CK(cudaMemsetAsync(W_dev, 0, sizeof(double) * n, h->st));
+  // ||M^{-1} b||
+  TRY(prec_apply(h, b, V));
+  double mbb;
+  TRY(dot_host(h, V, V, n, &mbb));
+  const double mbnorm = std::sqrt(mbb);
+  std::vector<double> Hm((size_t)(k + 1) * k), cs(k), sn(k), g(k + 1), y(k), hcol(2 * (k + 2));
+  int it = 0;
+  double rel = 1.0;
+  rann_status st = RANN_NOT_CONVERGED;
+  if (!(mbnorm > 0.0)) { st = std::isfinite(mbb) ? RANN_OK : RANN_BREAKDOWN; rel = 0.0; }
+  while (st == RANN_NOT_CONVERGED && it < maxit) {
+    // r = M^{-1}(b - A x)
+    TRY(rann_dd_normal_matvec(h, W_dev, t));
+    KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b, -1.0, t, n, h->st));
+    TRY(prec_apply(h, t, V));
+    double bb;
+    TRY(dot_host(h, V, V, n, &bb));
+    double beta = std::sqrt(bb);
+    rel = beta / mbnorm;
+    if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
+    if (rel <= rtol) { st = RANN_OK; break; }
+    KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_copy(1.0 / beta, V, V, n, h->st));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < k && it < maxit; ++j) {
+      double* w = V + (size_t)(j + 1) * n;
+      TRY(rann_dd_normal_matvec(h, V + (size_t)j * n, t));
+      TRY(prec_apply(h, t, w));
+      // classical Gram-Schmidt, twice
+      for (int pass = 0; pass < 2; ++pass) {
+        KLA(h, K_DOT, 2, 8.0 * n * (j + 2), 2.0 * n * (j + 1), launch_multidot(V, n, j + 1, w, n, h->d_red, hv + pass * (k + 2), h->st));
+        KLA(h, K_VEC, 1, 8.0 * n * (j + 3), 2.0 * n * (j + 1), launch_sub_combination(V, n, j + 1, hv + pass * (k + 2), w, n, h->st));
+      }
+      CK(cudaMemcpyAsync(hcol.data(), hv, sizeof(double) * hcol.size(), cudaMemcpyDeviceToHost, h->st));
+      double ww;
+      TRY(dot_host(h, w, w, n, &ww));   // synchronises, so hcol is valid
+      std::vector<double> hj(j + 2);
+      for (int i = 0; i <= j; ++i) hj[i] = hcol[i] + hcol[(k + 2) + i];
+      hj[j + 1] = std::sqrt(ww);
+      if (hj[j + 1] > 0.0) KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_copy(1.0 / hj[j + 1], w, w, n, h->st));
+      for (int i = 0; i < j; ++i) {
+        double a = cs[i] * hj[i] + sn[i] * hj[i + 1];
+        hj[i + 1] = -sn[i] * hj[i] + cs[i] * hj[i + 1];
+        hj[i] = a;
+      }
+      double den = std::hypot(hj[j], hj[j + 1]);
+      if (den == 0.0) { cs[j] = 1.0; sn[j] = 0.0; } else { cs[j] = hj[j] / den; sn[j] = hj[j + 1] / den; }
+      hj[j] = cs[j] * hj[j] + sn[j] * hj[j + 1];
+      hj[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) Hm[(size_t)i * k + j] = hj[i];
+      ++it;
+      jdone = j + 1;
+      rel = std::fabs(g[j + 1]) / mbnorm;
+      if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
+      if (rel <= rtol || hj[j] == 0.0) break;
+    }
+    if (st == RANN_BREAKDOWN) break;
+    for (int i = jdone - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int q = i + 1; q < jdone; ++q) s -= Hm[(size_t)i * k + q] * y[q];
+      y[i] = Hm[(size_t)i * k + i] != 0.0 ? s / Hm[(size_t)i * k + i] : 0.0;
+    }
+    CK(cudaMemcpyAsync(hv, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, h->st));
+    KLA(h, K_VEC, 1, 8.0 * n * (jdone + 2), 2.0 * n * jdone, launch_add_combination(V, n, jdone, hv, W_dev, n, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (rel <= rtol) {
+      // confirm with the explicit preconditioned residual
+      TRY(rann_dd_normal_matvec(h, W_dev, t));
+      KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b, -1.0, t, n, h->st));
+      TRY(prec_apply(h, t, V));
+      double rr;
+      TRY(dot_host(h, V, V, n, &rr));
+      rel = std::sqrt(rr) / mbnorm;
+      if (rel <= rtol) st = RANN_OK;
+    }
+  }
+  double precrel = rel;
+  double bb2, tr;
+  TRY(dot_host(h, b, b, n, &bb2));
+  TRY(rann_dd_normal_matvec(h, W_dev, t));
+  KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b, -1.0, t, n, h->st));
+  TRY(dot_host(h, t, t, n, &tr));
+  CK(cudaEventRecord(e1, h->st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  if (stats) {
+    stats->iters = it;
+    stats->rel_res_true = bb2 > 0 ? std::sqrt(tr / bb2) : 0.0;
+    stats->rel_res_rec = precrel;
+    stats->rel_res_prec = precrel;
+    stats->ms_solve = ms;
+    stats->n_shifted = h->n_shifted;
+  }
+  if (st == RANN_NOT_CONVERGED) rann_set_error("GMRES reached maxit=%d at rel. residual %.3e", maxit, rel);
+  return st;
+}
+
+// ---------------------------------------------------------------- eval --
+
+extern "C" rann_status rann_dd_eval(rann_dd_handle* h, const double* W_dev, const double* x_dev, int64_t n,
+                                    double* u_dev) {
+  REQUIRE(h && W_dev && (n == 0 || (x_dev && u_dev)), RANN_EINVAL, "null argument");
+  REQUIRE(n >= 0, RANN_EINVAL, "negative n");
+  REQUIRE(h->reduced, RANN_EORDER, "eval before pca");
+  const int J = h->J, m = h->m;
+  double* d_U;
+  CK(dalloc(h, (void**)&d_U, sizeof(double) * (size_t)J * m));
+  std::vector<GemmTask> tasks;
+  for (int j = 0; j < J; ++j) {
+    const SubDev& S = h->subs[j];
+    GemmTask t{};
+    t.A = h->d_V + (size_t)m * m * j; t.B = W_dev + S.woff; t.C = d_U + (size_t)m * j;
+    t.K = S.p; t.M = m; t.N = 1; t.lda = m; t.ldb = 1; t.ldc = 1;
+    push_tiles(tasks, t, false);
+  }
+  GemmTask* d_tasks;
+  CK(dupload(h, &d_tasks, tasks));
+  KL(h, K_EVAL, 1, launch_gemm_nn(d_tasks, (int)tasks.size(), h->st));
+  KL(h, K_EVAL, 1, launch_eval(h->P, h->d_sub, h->d_R, h->d_b, d_U, x_dev, n, u_dev, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  dfree(h, d_tasks);
+  dfree(h, d_U);
+  return RANN_OK;
+}
+
+// ---------------------------------------------------------- inspection --
+
+extern "C" rann_status rann_dd_block_info(rann_dd_handle* h, int j, int64_t* n_rows, int* n_cols) {
+  REQUIRE(h && j >= 0 && j < h->J, RANN_EINVAL, "bad subdomain index");
+  if (n_rows) *n_rows = h->subs[j].N;
+  if (n_cols) *n_cols = h->reduced ? h->subs[j].p : h->m;
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_get_block(rann_dd_handle* h, int j, int which, double* out_host,
+                                         int64_t* rows_host) {
+  REQUIRE(h && j >= 0 && j < h->J, RANN_EINVAL, "bad subdomain index");
+  REQUIRE(which >= 0 && which <= 2, RANN_EINVAL, "bad block kind");
+  const SubDev& S = h->subs[j];
+  if (rows_host) {
+    int64_t r = 0;
+    for (int a2 = 0; a2 < S.n[2]; ++a2)
+      for (int a1 = 0; a1 < S.n[1]; ++a1)
+        for (int a0 = 0; a0 < S.n[0]; ++a0)
+          rows_host[r++] = (S.lo[0] + a0) + (int64_t)h->P.G[0] * ((S.lo[1] + a1) + (int64_t)h->P.G[1] * (S.lo[2] + a2));
+  }
+  if (!out_host) return RANN_OK;
+  if (which < 2) {
+    REQUIRE(h->assembled, RANN_EORDER, "get_block before assemble");
+    const double* src = (which == 0 ? h->d_Psi : h->d_H) + S.row0 * h->m;
+    CK(cudaMemcpyAsync(out_host, src, sizeof(double) * (size_t)S.N * h->m, cudaMemcpyDeviceToHost, h->st));
+  } else {
+    REQUIRE(h->reduced, RANN_EORDER, "get_block(B) before pca");
+    CK(cudaMemcpy2DAsync(out_host, sizeof(double) * S.p, h->d_B + S.boff, sizeof(double) * S.P,
+                         sizeof(double) * S.p, S.N, cudaMemcpyDeviceToHost, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_get_pca(rann_dd_handle* h, int j, double* eig_host, double* V_host) {
+  REQUIRE(h && j >= 0 && j < h->J, RANN_EINVAL, "bad subdomain index");
+  REQUIRE(h->reduced, RANN_EORDER, "get_pca before pca");
+  const int m = h->m;
+  if (eig_host) memcpy(eig_host, h->eig_host.data() + (size_t)m * j, sizeof(double) * m);
+  if (V_host) {
+    CK(cudaMemcpy2DAsync(V_host, sizeof(double) * h->subs[j].p, h->d_V + (size_t)m * m * j, sizeof(double) * m,
+                         sizeof(double) * h->subs[j].p, m, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  return RANN_OK;
+}
+
+// ----------------------------------------------------------- profiling --
+
+extern "C" rann_status rann_dd_profile_enable(rann_dd_handle* h, int on) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  prof_resolve(h);
+  for (int k = 0; k < K_COUNT; ++k) {
+    h->prof.launches[k] = 0; h->prof.ms[k] = 0.0; h->prof.bytes[k] = 0.0; h->prof.flops[k] = 0.0;
+  }
+  h->prof.on = on != 0;
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const char** name, int64_t* launches,
+                                           double* ms, double* alg_bytes, double* alg_flops, int* bound) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  if (idx < 0 || idx >= K_COUNT) return RANN_EINVAL;
+  prof_resolve(h);
+  if (name) *name = KNAMES[idx];
+  if (launches) *launches = h->prof.launches[idx];
+  if (ms) *ms = h->prof.ms[idx];
+  if (alg_bytes) *alg_bytes = h->prof.bytes[idx];
+  if (alg_flops) *alg_flops = h->prof.flops[idx];
+  if (bound) *bound = KBOUND[idx];
+  return RANN_OK;
+}

@@ -1,0 +1,91 @@
+// Internal declarations shared by the CUDA translation units of librann_dd.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "rann_dd.h"
+
+#define RANN_MAX_DIM 3
+#define RANN_MAX_FTERMS 16
+#define RANN_MAX_COEF 64
+#define RANN_MAX_M 1024
+#define RANN_PI 3.141592653589793238462643383279502884
+
+// Problem constants, passed by value to the kernels.
+struct ProbDev {
+  int dim, ns, op, coef, g_kind, m;
+  double c0, nu, coef_value, eps, rho, f0;
+  int coef_grid;
+  double coef_vals[RANN_MAX_COEF];
+  int f_terms;
+  double fc[RANN_MAX_FTERMS];
+  double fa[RANN_MAX_FTERMS * RANN_MAX_DIM];
+  int G[RANN_MAX_DIM];       // global grid points per dim
+  int nsub[RANN_MAX_DIM];    // subdomains per dim
+  double sig[RANN_MAX_DIM];  // half-width per dim
+  int layout;
+};
+
+// Per-subdomain block descriptor (device copy).
+struct SubDev {
+  int k[RANN_MAX_DIM];       // multi-index of the subdomain
+  int lo[RANN_MAX_DIM];      // first global grid index of box_j per dim
+  int n[RANN_MAX_DIM];       // box extent per dim
+  double mu[RANN_MAX_DIM];   // centre per dim
+  int N;                     // rows = prod n
+  int p;                     // PCA rank
+  int P;                     // padded row length of B_j (p rounded up to 2)
+  int pad_;
+  int64_t row0;              // offset of block j in the unreduced row storage (rows)
+  int64_t woff;              // offset of W_j
+  int64_t boff;              // offset of B_j in the reduced storage (doubles)
+};
+
+// Host-side helpers (api.cu).
+void rann_set_error(const char* fmt, ...);
+
+static inline double host_mu(int layout, int k, int l) {
+  return layout == RANN_LAYOUT_PAPER ? (double)k / (double)(l - 1) : ((double)k + 0.5) / (double)l;
+}
+
+// ---- kernel launchers (defined in the .cu files) ----
+// assembly.cu
+cudaError_t launch_assemble(const ProbDev& P, const SubDev* d_sub, const int* d_tiles, int ntiles,
+                            const int* d_cov, const double* d_R, const double* d_b,
+                            double* d_Psi, double* d_H, cudaStream_t st);
+cudaError_t launch_rhs(const ProbDev& P, double* d_F, int64_t N, cudaStream_t st);
+cudaError_t launch_points(const ProbDev& P, double* d_xyz, int64_t N, cudaStream_t st);
+cudaError_t launch_eval(const ProbDev& P, const SubDev* d_sub, const double* d_R, const double* d_b,
+                        const double* d_U, const double* d_x, int64_t n, double* d_u,
+                        cudaStream_t st);
+
+// dense.cu -- batched float64 dense kernels
+struct GemmTask {            // one output tile of one batched product
+  const double* A;           // TN: A is K x M (row-major, lda); NN: A is M x K
+  const double* B;           // TN: B is K x N; NN: B is K x N
+  double* C;                 // M x N (ldc)
+  const int* ia;             // TN only: optional row gather for A (K entries)
+  const int* ib;             // TN only: optional row gather for B
+  int K, M, N, lda, ldb, ldc;
+  int tm, tn;                // tile origin (row, col) in C
+  int upper_only;            // TN symmetric: skip tiles strictly below the diagonal
+  int pad_;
+};
+cudaError_t launch_gemm_tn(const GemmTask* d_tasks, int ntasks, cudaStream_t st);
+cudaError_t launch_gemm_nn(const GemmTask* d_tasks, int ntasks, cudaStream_t st);
+cudaError_t launch_symmetrize(double* const* d_mats, const int* d_n, const int* d_ld, int nmat,
+                              int maxn, cudaStream_t st);
+
+// eig.cu -- batched symmetric eigen-decomposition (float64)
+cudaError_t launch_syevd(double* d_A, int m, int lda_stride, int batch, double* d_w, double* d_work,
+                         int* d_info, cudaStream_t st);
+
+// chol.cu -- batched uneven Cholesky and triangular solves
+struct CholMat {
+  double* A;                 // n x n row-major (lower triangle used)
+  int n;
+  int ld;
+};

@@ -1,0 +1,137 @@
+// Vector kernels for the Krylov solvers (PCG and GMRES on the normal
+// equations, Sec. 3/5), float64.  Reductions are deterministic: a fixed grid
+// writes per-block partial sums, one block adds them in index order.
+#include "common.cuh"
+
+namespace {
+
+constexpr int RB = 256;     // reduction blocks
+constexpr int RT = 256;     // threads per reduction block
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v) {
+  __shared__ double red[RT / 32];
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < RT / 32) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;   // valid in thread 0
+}
+
+// partial[b * nv + i] = sum over block b's range of V[i] . w  (V rows of length n)
+__global__ void __launch_bounds__(RT) multidot_partial(const double* __restrict__ V, int64_t ldv, int nv,
+                                                       const double* __restrict__ w, int64_t n,
+                                                       double* __restrict__ part) {
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t t0 = blockIdx.x * chunk, t1 = min(n, t0 + chunk);
+  for (int i = 0; i < nv; ++i) {
+    double s = 0.0;
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) s = fma(V[i * ldv + t], w[t], s);
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x * nv + i] = s;
+  }
+}
+
+__global__ void multidot_final(const double* __restrict__ part, int nb, int nv, double* __restrict__ out) {
+  int i = threadIdx.x;
+  if (i >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[b * nv + i];
+  out[i] = s;
+}
+
+// w -= sum_i h[i] V[i]
+__global__ void sub_combination(const double* __restrict__ V, int64_t ldv, int nv,
+                                const double* __restrict__ h, double* __restrict__ w, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[t];
+    for (int i = 0; i < nv; ++i) s = fma(-h[i], V[i * ldv + t], s);
+    w[t] = s;
+  }
+}
+
+// y = a * x + b * y
+__global__ void axpby_kernel(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    y[t] = fma(a, x[t], b * y[t]);
+}
+
+// x += a p ; r -= a q
+__global__ void cg_update_kernel(double a, const double* __restrict__ p, const double* __restrict__ q,
+                                 double* __restrict__ x, double* __restrict__ r, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    x[t] = fma(a, p[t], x[t]);
+    r[t] = fma(-a, q[t], r[t]);
+  }
+}
+
+__global__ void scale_copy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    y[t] = a * x[t];
+}
+
+// x += V^T y for GMRES: x[t] += sum_i y[i] V[i][t]
+__global__ void add_combination(const double* __restrict__ V, int64_t ldv, int nv,
+                                const double* __restrict__ y, double* __restrict__ x, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    double s = x[t];
+    for (int i = 0; i < nv; ++i) s = fma(y[i], V[i * ldv + t], s);
+    x[t] = s;
+  }
+}
+
+inline unsigned grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (unsigned)(g > 1216 ? 1216 : (g < 1 ? 1 : g));
+}
+
+}  // namespace
+
+cudaError_t launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t n,
+                            double* d_part, double* d_out, cudaStream_t st) {
+  multidot_partial<<<RB, RT, 0, st>>>(V, ldv, nv, w, n, d_part);
+  multidot_final<<<1, 128, 0, st>>>(d_part, RB, nv, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const double* x, const double* y, int64_t n, double* d_part, double* d_out,
+                       cudaStream_t st) {
+  return launch_multidot(x, 0, 1, y, n, d_part, d_out, st);
+}
+
+cudaError_t launch_sub_combination(const double* V, int64_t ldv, int nv, const double* d_h, double* w,
+                                   int64_t n, cudaStream_t st) {
+  sub_combination<<<grid_for(n), 256, 0, st>>>(V, ldv, nv, d_h, w, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_combination(const double* V, int64_t ldv, int nv, const double* d_y, double* x,
+                                   int64_t n, cudaStream_t st) {
+  add_combination<<<grid_for(n), 256, 0, st>>>(V, ldv, nv, d_y, x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t st) {
+  axpby_kernel<<<grid_for(n), 256, 0, st>>>(a, x, b, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(double a, const double* p, const double* q, double* x, double* r, int64_t n,
+                             cudaStream_t st) {
+  cg_update_kernel<<<grid_for(n), 256, 0, st>>>(a, p, q, x, r, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, cudaStream_t st) {
+  scale_copy_kernel<<<grid_for(n), 256, 0, st>>>(a, x, y, n);
+  return cudaGetLastError();
+}

@@ -1,0 +1,290 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Inputs are the seeded synthetic problems of rann_inputs; both sides receive
+the same hidden weights.  Tolerances:
+  * assembly, right-hand side: entrywise, 1e-12 relative to the block's max
+    (float64 arithmetic with a different but exact-derivative formulation);
+  * PCA: identical ranks (unless the oracle flags a singular value within 1e-6
+    of the cut), eigenvalues sigma_k^2 within 64 m eps lambda_max (the
+    backward error of a Gram eigen-decomposition), Eckart-Young optimality of
+    the kept subspace;
+  * block products: 1e-13 relative (same matrix, different summation order);
+  * solves: the least-squares residual ||H W - F|| equals the oracle's
+    direct-QR minimum to 1e-8 ||F||, and u_hat matches the oracle's u_hat at
+    test points to a per-problem bound (see SOLVE_TOL).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import rann_inputs as ri
+from oracle import assembly as asm
+from oracle import solver as sv
+
+SMALL = ["poisson2d_2x2", "multiscale2d", "heat3d", "poisson3d", "piecewise2d", "example1"]
+# u_hat parity bound per problem at rtol = 1e-10 (relative L2 at test points).
+# The Krylov iterates stop at a relative residual of 1e-10 on normal equations
+# with condition numbers 1e8..1e14, so u_hat is determined only to about
+# kappa(H^T H)^(1/2) * rtol; the bounds are that estimate with a margin.
+SOLVE_TOL = {"poisson2d_2x2": 1e-6, "multiscale2d": 1e-5, "heat3d": 1e-8, "poisson3d": 1e-8,
+             "piecewise2d": 1e-3, "example1": 1e-8}
+
+
+@pytest.fixture(scope="session")
+def g():
+    from paper_2412_19207_gb300 import build
+    build.build()
+    import paper_2412_19207_gb300 as pkg
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    return pkg
+
+
+_cache = {}
+
+
+def pipeline(g, name):
+    """GPU handle after assemble/rhs/pca, and the oracle system, for a small config."""
+    if name in _cache:
+        return _cache[name]
+    p = ri.config(name, small=True)
+    R, b = ri.weights(p)
+    s = g.RannDD(p, R, b)
+    s.assemble()
+    F = s.rhs()
+    blocks = [s.block(j, 0) + (s.block(j, 1)[1],) for j in range(p.J)]
+    ranks = s.pca(p.pca_mode, p.pca_thr)
+    S = sv.build_system(p, R, b)
+    _cache[name] = (p, s, F, blocks, ranks, S)
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_rhs_parity(g, name):
+    p, s, F, *_ = pipeline(g, name)
+    Fo = asm.rhs(p)
+    np.testing.assert_allclose(F.cpu().numpy(), Fo, rtol=0, atol=1e-13 * max(1.0, np.abs(Fo).max()))
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_assembly_parity(g, name):
+    p, s, F, blocks, *_ = pipeline(g, name)
+    R, b = ri.weights(p)
+    for j in range(p.J):
+        rows, Psi, H = blocks[j]
+        ro, Po, Ho = asm.block(p, R, b, j)
+        np.testing.assert_array_equal(rows, ro)
+        np.testing.assert_allclose(Psi, Po, rtol=0, atol=1e-12 * np.abs(Po).max())
+        np.testing.assert_allclose(H, Ho, rtol=0, atol=1e-12 * np.abs(Ho).max())
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_pca_parity(g, name):
+    p, s, F, blocks, ranks, S = pipeline(g, name)
+    for j in range(p.J):
+        pc = S.pcas[j]
+        if not pc.borderline:
+            assert ranks[j] == pc.rank, (j, ranks[j], pc.rank)
+        eig, V = s.pca_of(j)
+        lam_o = pc.sigma ** 2
+        lam_o = np.concatenate([lam_o, np.zeros(p.neurons - lam_o.shape[0])])
+        tol = 64 * p.neurons * 2.2e-16 * lam_o[0]
+        np.testing.assert_allclose(eig, lam_o, rtol=0, atol=tol)
+        np.testing.assert_allclose(V.T @ V, np.eye(V.shape[1]), atol=1e-11)
+        Psi = blocks[j][1]
+        resid = np.linalg.norm(Psi - Psi @ V @ V.T) ** 2
+        tail = np.sum(pc.sigma[ranks[j]:] ** 2)
+        assert abs(resid - tail) <= 1e-8 * tail + 256 * p.neurons * 2.2e-16 * lam_o[0]
+
+
+def _gpu_system(p, s, ranks):
+    """Dense H from the GPU's own reduced blocks (for kernel-level checks)."""
+    rows, Bs = [], []
+    for j in range(p.J):
+        r, B = s.block(j, 2)
+        rows.append(r)
+        Bs.append(B)
+    offs = np.concatenate([[0], np.cumsum(ranks)])
+    N = p.n_points()
+    H = np.zeros((N, int(offs[-1])))
+    for j in range(p.J):
+        H[rows[j], offs[j]:offs[j + 1]] = Bs[j]
+    return rows, Bs, offs, H
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_block_products(g, name):
+    p, s, F, blocks, ranks, S = pipeline(g, name)
+    _, _, _, H = _gpu_system(p, s, ranks)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(H.shape[1])
+    y = rng.standard_normal(H.shape[0])
+    xd, yd = torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda")
+    for got, want in [(s.matvec(xd), H @ x), (s.matvec_t(yd), H.T @ y), (s.normal_matvec(xd), H.T @ (H @ x))]:
+        got = got.cpu().numpy()
+        assert np.linalg.norm(got - want) <= 1e-13 * np.linalg.norm(want) * np.sqrt(H.shape[1])
+
+
+@pytest.mark.parametrize("name,kind", [("multiscale2d", "as"), ("multiscale2d", "sas"), ("multiscale2d", "ras"),
+                                       ("heat3d", "ras"), ("poisson3d", "as"), ("example1", "sas")])
+def test_precond_parity(g, name, kind):
+    """M^{-1} r of the GPU against the oracle's QR-based Schwarz operator built
+    on the same (GPU) reduced blocks; tolerance kappa(A_i) * eps."""
+    p, s, F, blocks, ranks, S = pipeline(g, name)
+    rows, Bs, offs, H = _gpu_system(p, s, ranks)
+    Sg = sv.System(p, S.R, S.b, rows, Bs, S.pcas, S.F, offs.astype(np.int64))
+    M = sv.schwarz(Sg, kind)
+    kappa = max(np.linalg.cond(sv.local_matrix(Sg, ks)) for ks in M.sets)
+    s.setup_precond(kind)
+    r = np.random.default_rng(2).standard_normal(Sg.dof)
+    z = s.precond_apply(torch.tensor(r, device="cuda")).cpu().numpy()
+    zo = M.apply(r)
+    assert np.linalg.norm(z - zo) <= max(1e-12, 1e3 * kappa * 2.2e-16) * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_solve_parity(g, name):
+    p, s, F, blocks, ranks, S = pipeline(g, name)
+    kind = p.precond
+    s.setup_precond(kind)
+    if p.solver == "cg_as" and kind in ("as", "none"):
+        W, st = s.solve_cg_as(F, 1e-10, 3000)
+        sol = sv.solve(S, "cg", sv.schwarz(S, kind), 1e-10, p.restart, 3000)
+    else:
+        W, st = s.solve_gmres_ras(F, 1e-10, p.restart, 3000)
+        sol = sv.solve(S, "gmres", sv.schwarz(S, kind), 1e-10, p.restart, 3000)
+    assert st["status"] == "RANN_OK"
+    qr = sv.solve_qr(S)
+    res = np.linalg.norm(s.matvec(W).cpu().numpy() - S.F)
+    assert abs(res - qr.res_ls) <= 1e-8 * np.linalg.norm(S.F)
+    X = ri.test_points(p, 21 if p.dim == 2 else 9)
+    ug = s.eval(W, torch.tensor(X, device="cuda")).cpu().numpy()
+    uo = sv.evaluate(S, sol.W, X)
+    assert np.linalg.norm(ug - uo) <= SOLVE_TOL[name] * np.linalg.norm(uo)
+    # the constraint makes u_hat = G exactly on the boundary
+    Xb = ri.boundary_points(p, 7)
+    ub = s.eval(W, torch.tensor(Xb, device="cuda")).cpu().numpy()
+    np.testing.assert_array_equal(ub, asm.constraint_G(p, asm._coords(Xb, -1)).a)
+
+
+def test_eval_kernel_parity(g):
+    """u_hat of the GPU and of the oracle for the same W and the same (GPU) basis."""
+    p, s, F, blocks, ranks, S = pipeline(g, "heat3d")
+    W = np.random.default_rng(5).standard_normal(int(ranks.sum()))
+    pcas = [sv.PCA(S.pcas[j].sigma, s.pca_of(j)[1], int(ranks[j]), False) for j in range(p.J)]
+    Sg = sv.System(p, S.R, S.b, S.rows, S.B, pcas, S.F, np.concatenate([[0], np.cumsum(ranks)]))
+    X = np.random.default_rng(6).random((500, p.dim))
+    ug = s.eval(torch.tensor(W, device="cuda"), torch.tensor(X, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(ug, sv.evaluate(Sg, W, X), rtol=0, atol=1e-12 * np.abs(ug).max())
+
+
+@pytest.mark.parametrize("name,solver", [("poisson2d_2x2", "cg"), ("poisson3d", "cg"), ("poisson2d_2x2", "gmres")])
+def test_one_iteration_on_2x2(g, name, solver):
+    """Tables 2 and 3: with J = 2^d every extended set holds all unknowns and
+    the AS-preconditioned solve stops after one iteration."""
+    p = ri.config(name, small=(name == "poisson3d"))
+    s = g.RannDD(p)
+    s.assemble()
+    F = s.rhs()
+    s.pca(p.pca_mode, p.pca_thr)
+    s.setup_precond("as")
+    if solver == "cg":
+        _, st = s.solve_cg_as(F, 1e-10, 10)
+    else:
+        _, st = s.solve_gmres_ras(F, 1e-10, 10, 10)
+    assert st["iters"] == 1 and st["status"] == "RANN_OK"
+
+
+def test_determinism(g):
+    p = ri.config("multiscale2d", small=True)
+    out = []
+    for _ in range(2):
+        s = g.RannDD(p)
+        s.assemble()
+        F = s.rhs()
+        s.pca(p.pca_mode, p.pca_thr)
+        s.setup_precond("ras")
+        W, _ = s.solve_gmres_ras(F, 1e-10, 50, 500)
+        out.append(W.cpu().numpy())
+        s.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_seed_path_matches_input_generator(g):
+    """Weights drawn inside the library from the seed equal rann_inputs' draws."""
+    p = ri.config("heat3d", small=True)
+    a, b = g.RannDD(p), g.RannDD(p, *ri.weights(p))
+    a.assemble()
+    b.assemble()
+    for j in (0, p.J - 1):
+        np.testing.assert_array_equal(a.block(j, 1)[1], b.block(j, 1)[1])
+
+
+def test_order_and_argument_errors(g):
+    p = ri.config("poisson2d_2x2", small=True)
+    s = g.RannDD(p)
+    with pytest.raises(g.RannError) as e:
+        s.pca(g.PCA_VARIANCE, 1e-12)
+    assert e.value.status == g.EORDER
+    s.assemble()
+    F = s.rhs()
+    with pytest.raises(g.RannError) as e:
+        s.setup_precond("as")
+    assert e.value.status == g.EORDER
+    s.pca(g.PCA_VARIANCE, 1e-12)
+    with pytest.raises(g.RannError) as e:
+        s.solve_cg_as(F)
+    assert e.value.status == g.EORDER
+    with pytest.raises(g.RannError) as e:
+        s.setup_precond(9)
+    assert e.value.status == g.EINVAL
+    s.setup_precond("ras")
+    with pytest.raises(g.RannError) as e:
+        s.solve_cg_as(F)          # RAS is not symmetric
+    assert e.value.status == g.EINVAL
+    with pytest.raises(g.RannError) as e:
+        s.solve_gmres_ras(F, restart=0)
+    assert e.value.status == g.EINVAL
+    W, st = s.solve_gmres_ras(F, 1e-10, 50, 0, allow_not_converged=True)
+    assert st["status"] == "RANN_NOT_CONVERGED"
+    Z = torch.zeros_like(F)
+    W, st = s.solve_gmres_ras(Z, 1e-10, 50, 10)
+    assert st["status"] == "RANN_OK" and float(W.abs().max()) == 0.0
+    # empty evaluation is a no-op
+    s.eval(W, torch.empty((0, p.dim), dtype=torch.float64, device="cuda"),
+           torch.empty(0, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("variant", ["single_subdomain", "pca_none", "restart_1", "block_jacobi", "wide_net"])
+def test_degenerate_cases(g, variant):
+    if variant == "single_subdomain":
+        p = ri.Problem(name="one", dim=2, op=ri.OP_POISSON, sub=(1, 1), pts=(16, 16), neurons=24, w_range=1.0,
+                       seed=7, overlap=(0.0, 0.0), rho=0.5, fc=np.array([2 * np.pi ** 2]), fa=np.ones((1, 2)),
+                       pca_mode=ri.PCA_ABS, pca_thr=1e-3)
+    elif variant == "wide_net":      # m > N_j: rank-deficient Gram matrices, m at the 1024 cap
+        p = ri.config("poisson2d_2x2", small=True)
+        p.neurons, p.pts = 1024, (6, 6)
+    else:
+        p = ri.config("multiscale2d", small=True)
+    mode = ri.PCA_NONE if variant == "pca_none" else p.pca_mode
+    s = g.RannDD(p)
+    s.assemble()
+    F = s.rhs()
+    ranks = s.pca(mode, p.pca_thr)
+    S = sv.build_system(p)
+    if variant != "pca_none":
+        assert list(ranks) == [pc.rank for pc in S.pcas]
+    s.setup_precond("as", 0 if variant == "block_jacobi" else 1)
+    if variant == "restart_1":
+        W, st = s.solve_gmres_ras(F, 1e-10, 1, 20000, allow_not_converged=True)
+        assert st["iters"] > 0
+        return
+    W, st = s.solve_cg_as(F, 1e-10, 5000)
+    assert st["status"] == "RANN_OK"
+    if variant == "pca_none":
+        return
+    qr = sv.solve_qr(S)
+    res = np.linalg.norm(s.matvec(W).cpu().numpy() - S.F)
+    assert abs(res - qr.res_ls) <= 1e-8 * np.linalg.norm(S.F)
