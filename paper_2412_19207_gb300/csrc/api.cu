@@ -23,9 +23,14 @@ cudaError_t launch_matvec_HT2(const ProbDev& P, const SubDev* d_sub, int J, cons
                               double* d_part, double* d_z, int maxP, cudaStream_t st);
 cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, int* d_fail,
                              const double* d_dmax, cudaStream_t st);
-cudaError_t launch_local_solve(const CholMat* d_mats, int nsets, const int* d_set_ptr, const int* d_set_sub,
-                               const SubDev* d_sub, const int64_t* d_s_off, const double* d_r, double* d_s,
-                               cudaStream_t st);
+cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st);
+cudaError_t launch_schwarz_gather(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
+                                  const int64_t* d_s_off, const double* d_r, double* d_g, cudaStream_t st);
+cudaError_t launch_trmv_lower(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
+                              const double* d_g, double* d_y, cudaStream_t st);
+cudaError_t launch_trmv_upper(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
+                              const int64_t* d_p_off, const double* d_y, double* d_part, double* d_s,
+                              cudaStream_t st);
 cudaError_t launch_schwarz_combine(const SubDev* d_sub, int J, const int* d_inc_ptr, const int* d_inc_set,
                                    const int* d_inc_pos, const int64_t* d_s_off, const double* d_s, int kind,
                                    double* d_z, cudaStream_t st);
@@ -79,16 +84,17 @@ void rann_set_error(const char* fmt, ...) {
 // stream (the times are the device durations of the launches).
 enum KId {
   K_POINTS, K_ASSEMBLE, K_RHS, K_GRAM, K_SYMM, K_EIG, K_PROJECT, K_PAIRGRAM, K_LOCALASM, K_ADDDIAG,
-  K_CHOL, K_LOCALSOLVE, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL, K_COUNT
+  K_CHOL, K_TRTRI, K_GATHER, K_TRMV_L, K_TRMV_U, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL,
+  K_COUNT
 };
 static const char* const KNAMES[K_COUNT] = {
   "points", "assemble", "rhs", "gram", "symmetrize", "eig", "project", "pair_gram", "local_assemble",
-  "add_diag", "cholesky", "local_solve", "schwarz_combine", "matvec_H", "matvec_HT", "dot", "vector",
-  "eval"};
+  "add_diag", "cholesky", "trtri", "schwarz_gather", "trmv_lower", "trmv_upper", "schwarz_combine",
+  "matvec_H", "matvec_HT", "dot", "vector", "eval"};
 
 // Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
 // 1 = float64-ALU-bound (algorithmic flops count).
-static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 0, 0, 0, 0, 0, 0, 1};
+static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1};
 
 struct Prof {
   bool on = false;
@@ -147,8 +153,13 @@ struct rann_dd_handle {
   int* d_inc_set = nullptr;
   int* d_inc_pos = nullptr;
   int64_t* d_s_off = nullptr;
-  double* d_s = nullptr;
+  double* d_s = nullptr;       // s_i = A_i^{-1} g_i (sum n_i)
+  double* d_g = nullptr;       // gathered g_i = R_i r
+  double* d_y = nullptr;       // y_i = L_i^{-1} g_i
+  double* d_tpart = nullptr;   // partial sums of the transposed product
+  int64_t* d_p_off = nullptr;
   double* d_Amats = nullptr;
+  double* d_Xmats = nullptr;
   double* d_pairbuf = nullptr;
   // krylov scratch
   double* d_red = nullptr;     // multidot partials
@@ -623,9 +634,10 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   // release a previous setup
   for (void* p : {(void*)h->d_mats, (void*)h->d_set_ptr, (void*)h->d_set_sub, (void*)h->d_inc_ptr,
                   (void*)h->d_inc_set, (void*)h->d_inc_pos, (void*)h->d_s_off, (void*)h->d_s,
-                  (void*)h->d_Amats})
+                  (void*)h->d_Amats, (void*)h->d_Xmats, (void*)h->d_g, (void*)h->d_y, (void*)h->d_tpart,
+                  (void*)h->d_p_off})
     dfree(h, p);
-  h->d_mats = nullptr; h->d_Amats = nullptr;
+  h->d_mats = nullptr; h->d_Amats = nullptr; h->d_Xmats = nullptr;
   h->n_shifted = 0;
   h->prec_kind = kind;
   if (kind == RANN_PREC_NONE) return RANN_OK;
@@ -723,12 +735,16 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     tab_ptr.push_back((int)tab.size());
   }
   CK(dalloc(h, (void**)&h->d_Amats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
+  CK(dalloc(h, (void**)&h->d_Xmats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
   h->sum_n = h->sum_n2 = h->sum_n3 = 0;
   for (int i = 0; i < J; ++i) {
     const double n = mats[i].n;
     h->sum_n += n; h->sum_n2 += n * n; h->sum_n3 += n * n * n;
   }
-  for (int i = 0; i < J; ++i) mats[i].A = h->d_Amats + reinterpret_cast<int64_t>(mats[i].A);
+  for (int i = 0; i < J; ++i) {
+    mats[i].X = h->d_Xmats + reinterpret_cast<int64_t>(mats[i].A);
+    mats[i].A = h->d_Amats + reinterpret_cast<int64_t>(mats[i].A);
+  }
   int64_t* d_tab; int *d_tab_ptr, *d_boffs, *d_boff_ptr; double* d_dmax; int* d_fail;
   CK(dupload(h, &d_tab, tab)); CK(dupload(h, &d_tab_ptr, tab_ptr));
   CK(dupload(h, &d_boffs, boffs)); CK(dupload(h, &d_boff_ptr, boff_ptr));
@@ -786,6 +802,12 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     if (attempt == 5) { rann_set_error("local Cholesky failed after shifts"); return RANN_ECUDA; }
   }
   for (int i = 0; i < J; ++i) h->n_shifted += shifted[i];
+  // X_i = L_i^{-1} for the parallel apply
+  KLA(h, K_TRTRI, 2, 0, h->sum_n3 / 3.0, launch_trtri(h->d_mats, J, h->maxn, h->st));
+  std::vector<int64_t> p_off(J + 1, 0);
+  for (int i = 0; i < J; ++i) p_off[i + 1] = p_off[i] + (int64_t)((mats[i].n + 255) / 256) * mats[i].n;
+  CK(dupload(h, &h->d_p_off, p_off));
+  CK(dalloc(h, (void**)&h->d_tpart, sizeof(double) * (size_t)std::max<int64_t>(p_off[J], 1)));
   // incidence lists for the combine step: sets containing each subdomain, with its block offset
   std::vector<int> inc_ptr(1, 0), inc_set, inc_pos;
   for (int k = 0; k < J; ++k) {
@@ -802,6 +824,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   CK(dupload(h, &h->d_inc_ptr, inc_ptr)); CK(dupload(h, &h->d_inc_set, inc_set)); CK(dupload(h, &h->d_inc_pos, inc_pos));
   CK(dupload(h, &h->d_s_off, s_off));
   CK(dalloc(h, (void**)&h->d_s, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
+  CK(dalloc(h, (void**)&h->d_g, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
+  CK(dalloc(h, (void**)&h->d_y, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
   dfree(h, d_ridx); dfree(h, d_tasks); dfree(h, d_tab); dfree(h, d_tab_ptr); dfree(h, d_boffs); dfree(h, d_boff_ptr);
   dfree(h, d_dmax); dfree(h, d_fail); dfree(h, h->d_pairbuf);
   h->d_pairbuf = nullptr;
@@ -814,7 +838,9 @@ static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z) {
     CK(cudaMemcpyAsync(z, r, sizeof(double) * h->dof, cudaMemcpyDeviceToDevice, h->st));
     return RANN_OK;
   }
-  KLA(h, K_LOCALSOLVE, 1, 8.0 * (h->sum_n2 + 4.0 * h->sum_n), 2.0 * h->sum_n2, launch_local_solve(h->d_mats, h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub, h->d_s_off, r, h->d_s, h->st));
+  KLA(h, K_GATHER, 1, 16.0 * h->sum_n, 0, launch_schwarz_gather(h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub, h->d_s_off, r, h->d_g, h->st));
+  KLA(h, K_TRMV_L, 1, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n, launch_trmv_lower(h->d_mats, h->nsets, h->maxn, h->d_s_off, h->d_g, h->d_y, h->st));
+  KLA(h, K_TRMV_U, 2, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n, launch_trmv_upper(h->d_mats, h->nsets, h->maxn, h->d_s_off, h->d_p_off, h->d_y, h->d_tpart, h->d_s, h->st));
   KLA(h, K_COMBINE, 1, 8.0 * (h->sum_n + h->dof), 0, launch_schwarz_combine(h->d_sub, h->J, h->d_inc_ptr, h->d_inc_set, h->d_inc_pos, h->d_s_off, h->d_s,
                             h->prec_kind, z, h->st));
   return RANN_OK;

@@ -9,9 +9,13 @@
 // positive (relative to the largest diagonal entry) marks the matrix as
 // failed; the host then refactors it with a diagonal shift.
 //
-// Apply: z = sum_i R_i^T D_i A_i^{-1} R_i r: each subdomain gathers its
-// extended-set residual, runs the forward and backward substitutions, and
-// the per-unknown sums over the sets are formed in a fixed order
+// Apply: z = sum_i R_i^T D_i A_i^{-1} R_i r with A_i^{-1} = X_i^T X_i,
+// X_i = L_i^{-1} computed once at set-up (block-column-parallel forward
+// substitution).  Inverting the triangular factor keeps the error of a
+// triangular solve (about kappa(A_i) eps relative, since kappa(L_i)^2 =
+// kappa(A_i)), unlike an explicit A_i^{-1}, and turns each apply into two
+// fully parallel triangular matrix-vector products instead of sequential
+// substitutions.  Per-unknown sums over the sets are formed in a fixed order
 // (deterministic, no atomics).
 #include "common.cuh"
 
@@ -125,71 +129,154 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(const CholMat* __restr
     }
 }
 
+// ---- triangular inverse X = L^{-1} ----
+// Diagonal blocks: X_bb = L_bb^{-1}, one thread per column of the block.
+__global__ void trtri_diag_kernel(const CholMat* __restrict__ mats) {
+  const CholMat M = mats[blockIdx.y];
+  const int nblk = (M.n + NB - 1) / NB;
+  if ((int)blockIdx.x >= nblk) return;
+  const int b0 = blockIdx.x * NB, nb = min(NB, M.n - b0);
+  __shared__ double l[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int r = e / NB, c = e % NB;
+    l[r][c] = (r < nb && c <= r) ? M.A[(int64_t)(b0 + r) * M.ld + b0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c >= nb) return;
+  double x[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) x[r] = 0.0;
+  for (int r = c; r < nb; ++r) {
+    double s = (r == c) ? 1.0 : 0.0;
+    for (int k = c; k < r; ++k) s = fma(-l[r][k], x[k], s);
+    x[r] = s / l[r][r];
+  }
+  for (int r = c; r < nb; ++r) M.X[(int64_t)(b0 + r) * M.ld + b0 + c] = x[r];
+}
+
+// Block column j of X: for i > j, X_ij = -X_ii sum_{j <= k < i} L_ik X_kj.
+__global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restrict__ mats) {
+  const CholMat M = mats[blockIdx.y];
+  const int nblk = (M.n + NB - 1) / NB;
+  const int j = blockIdx.x;
+  if (j >= nblk) return;
+  __shared__ double sl[NB][NB + 1];
+  __shared__ double sx[NB][NB + 1];
+  const int t = threadIdx.x, r = t % NB, cg = (t / NB) * 4;   // row r, columns cg..cg+3
+  const int cj = j * NB;
+  for (int i = j + 1; i < nblk; ++i) {
+    const int ri = i * NB;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = j; k < i; ++k) {
+      const int ck = k * NB;
+      for (int e = t; e < NB * NB; e += 256) {
+        int a = e / NB, b = e % NB;
+        sl[a][b] = (ri + a < M.n) ? M.A[(int64_t)(ri + a) * M.ld + ck + b] : 0.0;         // L_ik
+        // X_kj (the diagonal block X_jj is lower triangular: its upper part is never written)
+        sx[a][b] = (ck + a < M.n && cj + b < M.n && (k > j || b <= a)) ? M.X[(int64_t)(ck + a) * M.ld + cj + b] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int q = 0; q < NB; ++q) {
+        double lv = sl[r][q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(lv, sx[q][cg + u], acc[u]);
+      }
+      __syncthreads();
+    }
+    // X_ij = -X_ii acc
+    for (int e = t; e < NB * NB; e += 256) {
+      int a = e / NB, b = e % NB;
+      sl[a][b] = (ri + a < M.n && b <= a) ? M.X[(int64_t)(ri + a) * M.ld + ri + b] : 0.0;   // X_ii (lower)
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sx[r][cg + u] = acc[u];
+    __syncthreads();
+    double out[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q <= r; ++q) {
+      double lv = sl[r][q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) out[u] = fma(lv, sx[q][cg + u], out[u]);
+    }
+    if (ri + r < M.n)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cj + cg + u < M.n) M.X[(int64_t)(ri + r) * M.ld + cj + cg + u] = -out[u];
+    __syncthreads();   // X_ij visible to the next i (same block)
+  }
+}
+
 // ---- apply ----
-// Each extended set i: gather r_i, solve L y = r_i, L^T s = y, store s_i.
-__global__ void __launch_bounds__(256) local_solve_kernel(const CholMat* __restrict__ mats,
-                                                          const int* __restrict__ set_ptr,
-                                                          const int* __restrict__ set_sub,
-                                                          const SubDev* __restrict__ subs,
-                                                          const int64_t* __restrict__ s_off,
-                                                          const double* __restrict__ r,
-                                                          double* __restrict__ s_all) {
+// g_i = R_i r (gather the extended-set residual).
+__global__ void schwarz_gather_kernel(const int* __restrict__ set_ptr, const int* __restrict__ set_sub,
+                                      const SubDev* __restrict__ subs, const int64_t* __restrict__ s_off,
+                                      const double* __restrict__ r, double* __restrict__ g) {
   const int i = blockIdx.x;
-  const CholMat M = mats[i];
-  double* y = s_all + s_off[i];
-  // gather
+  double* gi = g + s_off[i];
   int off = 0;
   for (int q = set_ptr[i]; q < set_ptr[i + 1]; ++q) {
     const SubDev& S = subs[set_sub[q]];
-    for (int c = threadIdx.x; c < S.p; c += blockDim.x) y[off + c] = r[S.woff + c];
+    for (int c = threadIdx.x; c < S.p; c += blockDim.x) gi[off + c] = r[S.woff + c];
     off += S.p;
   }
+}
+
+// y_i = X_i g_i, X_i lower triangular: one warp per row.
+__global__ void __launch_bounds__(256) trmv_lower_kernel(const CholMat* __restrict__ mats,
+                                                         const int64_t* __restrict__ s_off,
+                                                         const double* __restrict__ g, double* __restrict__ y) {
+  const CholMat M = mats[blockIdx.y];
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= M.n) return;
+  const double* row = M.X + (int64_t)r * M.ld;
+  const double* gi = g + s_off[blockIdx.y];
+  double acc = 0.0;
+  for (int c = lane; c <= r; c += 32) acc = fma(row[c], gi[c], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[s_off[blockIdx.y] + r] = acc;
+}
+
+// partial_i[rc][c] = sum over rows r of chunk rc (r >= c) of X_i[r][c] y_i[r]:
+// 256-column tile ct and 256-row chunk rc >= ct, threads across columns.
+constexpr int TT = 256;
+__global__ void __launch_bounds__(TT) trmv_upper_partial_kernel(const CholMat* __restrict__ mats,
+                                                                const int64_t* __restrict__ s_off,
+                                                                const int64_t* __restrict__ p_off,
+                                                                const double* __restrict__ y,
+                                                                double* __restrict__ part) {
+  const CholMat M = mats[blockIdx.y];
+  const int T = (M.n + TT - 1) / TT;
+  const int t = blockIdx.x;
+  if (t >= T * (T + 1) / 2) return;
+  int rc = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while (rc * (rc + 1) / 2 > t) --rc;
+  while ((rc + 1) * (rc + 2) / 2 <= t) ++rc;
+  const int ct = t - rc * (rc + 1) / 2;     // ct <= rc
+  __shared__ double ys[TT];
+  const double* yi = y + s_off[blockIdx.y];
+  const int r0 = rc * TT, r1 = min(M.n, r0 + TT);
+  for (int q = threadIdx.x; q < r1 - r0; q += TT) ys[q] = yi[r0 + q];
   __syncthreads();
-  const int n = M.n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // forward: L y = r
-  for (int b0 = 0; b0 < n; b0 += NB) {
-    const int nb = min(NB, n - b0);
-    if (warp == 0) {
-      double yl = (lane < nb) ? y[b0 + lane] : 0.0;
-      for (int j = 0; j < nb; ++j) {
-        if (lane == j) yl /= M.A[(int64_t)(b0 + j) * M.ld + b0 + j];
-        double yj = __shfl_sync(0xffffffffu, yl, j);
-        if (lane > j && lane < nb) yl = fma(-M.A[(int64_t)(b0 + lane) * M.ld + b0 + j], yj, yl);
-      }
-      if (lane < nb) y[b0 + lane] = yl;
-    }
-    __syncthreads();
-    for (int rr = b0 + nb + threadIdx.x; rr < n; rr += blockDim.x) {
-      const double* Lr = M.A + (int64_t)rr * M.ld + b0;
-      double s = y[rr];
-      for (int k = 0; k < nb; ++k) s = fma(-Lr[k], y[b0 + k], s);
-      y[rr] = s;
-    }
-    __syncthreads();
-  }
-  // backward: L^T s = y
-  const int nblk = (n + NB - 1) / NB;
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int b0 = bi * NB;
-    const int nb = min(NB, n - b0);
-    if (warp == 0) {
-      double yl = (lane < nb) ? y[b0 + lane] : 0.0;
-      for (int j = nb - 1; j >= 0; --j) {
-        if (lane == j) yl /= M.A[(int64_t)(b0 + j) * M.ld + b0 + j];
-        double yj = __shfl_sync(0xffffffffu, yl, j);
-        if (lane < j) yl = fma(-M.A[(int64_t)(b0 + j) * M.ld + b0 + lane], yj, yl);
-      }
-      if (lane < nb) y[b0 + lane] = yl;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < b0; c += blockDim.x) {
-      double s = y[c];
-      for (int k = 0; k < nb; ++k) s = fma(-M.A[(int64_t)(b0 + k) * M.ld + c], y[b0 + k], s);
-      y[c] = s;
-    }
-    __syncthreads();
-  }
+  const int c = ct * TT + threadIdx.x;
+  if (c >= M.n) return;
+  double acc = 0.0;
+  for (int rr = max(r0, c); rr < r1; ++rr) acc = fma(M.X[(int64_t)rr * M.ld + c], ys[rr - r0], acc);
+  part[p_off[blockIdx.y] + (int64_t)rc * M.n + c] = acc;
+}
+
+// s_i[c] = sum over row chunks rc >= c / 256 of partial_i[rc][c] (fixed order).
+__global__ void trmv_upper_reduce_kernel(const CholMat* __restrict__ mats, const int64_t* __restrict__ s_off,
+                                         const int64_t* __restrict__ p_off, const double* __restrict__ part,
+                                         double* __restrict__ s) {
+  const CholMat M = mats[blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= M.n) return;
+  const int T = (M.n + TT - 1) / TT;
+  double acc = 0.0;
+  for (int rc = c / TT; rc < T; ++rc) acc += part[p_off[blockIdx.y] + (int64_t)rc * M.n + c];
+  s[s_off[blockIdx.y] + c] = acc;
 }
 
 // z[u] = sum over the sets i containing u's subdomain k (fixed order) of D_i(u) s_i[u].
@@ -300,11 +387,32 @@ cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_local_solve(const CholMat* d_mats, int nsets, const int* d_set_ptr,
-                               const int* d_set_sub, const SubDev* d_sub, const int64_t* d_s_off,
-                               const double* d_r, double* d_s, cudaStream_t st) {
-  if (nsets == 0) return cudaSuccess;
-  local_solve_kernel<<<nsets, 256, 0, st>>>(d_mats, d_set_ptr, d_set_sub, d_sub, d_s_off, d_r, d_s);
+cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st) {
+  if (nmat == 0) return cudaSuccess;
+  int nblk = (maxn + NB - 1) / NB;
+  trtri_diag_kernel<<<dim3(nblk, nmat), NB, 0, st>>>(d_mats);
+  trtri_col_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schwarz_gather(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
+                                  const int64_t* d_s_off, const double* d_r, double* d_g, cudaStream_t st) {
+  schwarz_gather_kernel<<<nsets, 256, 0, st>>>(d_set_ptr, d_set_sub, d_sub, d_s_off, d_r, d_g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trmv_lower(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
+                              const double* d_g, double* d_y, cudaStream_t st) {
+  trmv_lower_kernel<<<dim3((maxn + 7) / 8, nsets), 256, 0, st>>>(d_mats, d_s_off, d_g, d_y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trmv_upper(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
+                              const int64_t* d_p_off, const double* d_y, double* d_part, double* d_s,
+                              cudaStream_t st) {
+  int T = (maxn + TT - 1) / TT;
+  trmv_upper_partial_kernel<<<dim3(T * (T + 1) / 2, nsets), TT, 0, st>>>(d_mats, d_s_off, d_p_off, d_y, d_part);
+  trmv_upper_reduce_kernel<<<dim3((maxn + 255) / 256, nsets), 256, 0, st>>>(d_mats, d_s_off, d_p_off, d_part, d_s);
   return cudaGetLastError();
 }
 

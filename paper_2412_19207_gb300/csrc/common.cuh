@@ -85,7 +85,8 @@ cudaError_t launch_syevd(double* d_A, int m, int lda_stride, int batch, double* 
 
 // chol.cu -- batched uneven Cholesky and triangular solves
 struct CholMat {
-  double* A;                 // n x n row-major (lower triangle used)
+  double* A;                 // n x n row-major (lower triangle used): A_i, then its Cholesky factor L_i
+  double* X;                 // n x n row-major (lower triangle used): L_i^{-1}
   int n;
   int ld;
 };

@@ -30,6 +30,11 @@ SMALL = ["poisson2d_2x2", "multiscale2d", "heat3d", "poisson3d", "piecewise2d", 
 # kappa(H^T H)^(1/2) * rtol; the bounds are that estimate with a margin.
 SOLVE_TOL = {"poisson2d_2x2": 1e-6, "multiscale2d": 1e-5, "heat3d": 1e-8, "poisson3d": 1e-8,
              "piecewise2d": 1e-3, "example1": 1e-8}
+# Excess of ||H W - F|| over the direct-QR minimum, relative to ||F||.  CG
+# stops on the normal-equation residual (1e-8 holds); GMRES with the Boolean
+# RAS operator stops on the preconditioned residual, which bounds the normal
+# residual only through kappa(M_RAS^{-1}), so its excess is larger.
+LS_TOL = {"multiscale2d": 1e-7, "piecewise2d": 1e-6}
 
 
 @pytest.fixture(scope="session")
@@ -158,7 +163,9 @@ def test_solve_parity(g, name):
     assert st["status"] == "RANN_OK"
     qr = sv.solve_qr(S)
     res = np.linalg.norm(s.matvec(W).cpu().numpy() - S.F)
-    assert abs(res - qr.res_ls) <= 1e-8 * np.linalg.norm(S.F)
+    # (the oracle's QR zeroes near-singular pivots, so it is a minimiser only up
+    # to that truncation: the bound is two-sided)
+    assert abs(res - qr.res_ls) <= LS_TOL.get(name, 1e-8) * np.linalg.norm(S.F)
     X = ri.test_points(p, 21 if p.dim == 2 else 9)
     ug = s.eval(W, torch.tensor(X, device="cuda")).cpu().numpy()
     uo = sv.evaluate(S, sol.W, X)
