@@ -200,6 +200,30 @@ rann_status rann_dd_get_block(rann_dd_handle* h, int j, int which, double* out_h
 /* Eigenvalues sigma^2 (descending, [m]) and the kept V_{p_j} ([m][p_j] row-major). */
 rann_status rann_dd_get_pca(rann_dd_handle* h, int j, double* eig_host, double* V_host);
 
+/* The transposed block product z_j = B_j^T y(rows_j) without any allocation.
+ * The paper has no counterpart: it exists for callers that cannot allocate
+ * device memory -- a program whose device memory is all owned by its own
+ * allocator (a framework's caching pool or a fixed arena reserved at
+ * start-up), where cudaMalloc fails, or a latency-critical loop that cannot
+ * take the device-wide synchronisation cudaMalloc/cudaFree may imply.  It
+ * needs no handle and allocates nothing: partial sums live in a fixed device
+ * array of 2^20 doubles (8 MiB) and block descriptors in a fixed table of
+ * 4096 entries, both held by every GPU that loads the library until exit.
+ * Host arrays [J]: block j is n_rows[j] x ld[j] row-major at B_dev + boff[j]
+ * (its first n_cols[j] columns are used); its rows read y_dev at the indices
+ * rows_dev[row_off[j] .. row_off[j] + n_rows[j]) (int64, device); z_j goes to
+ * z_dev[zoff[j] ..].  RANN_EINVAL if J is outside 1..4096, a pointer is NULL,
+ * a descriptor is negative or n_cols > ld, or (number of 256-row tiles) x
+ * (largest n_cols) exceeds 2^20.  The first call on a device looks up the
+ * arrays' device addresses (with that device current); make it before any
+ * stream capture.  All calls share the arrays, which keep the last call's
+ * contents; every value a call reads is written earlier by the same call.
+ * Calls that overlap on the GPU race.  Enqueued on `cuda_stream`. */
+rann_status rann_dd_matvec_t_noalloc(int J, const int64_t* boff, const int* n_rows, const int* n_cols,
+                                     const int* ld, const int64_t* row_off, const int64_t* zoff,
+                                     const double* B_dev, const int64_t* rows_dev, const double* y_dev,
+                                     double* z_dev, void* cuda_stream);
+
 /* Kernel accounting (tracing for the roofline; the paper has no
  * counterpart).  Every kernel launch is counted per kernel family together
  * with its algorithmic bytes and float64 flops (the minimal traffic and

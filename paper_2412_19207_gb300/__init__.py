@@ -95,6 +95,7 @@ SIGNATURES = {
     "rann_dd_block_info": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_I)]),
     "rann_dd_get_block": (_I, [_P, _I, _I, _P, _P]),
     "rann_dd_get_pca": (_I, [_P, _I, _P, _P]),
+    "rann_dd_matvec_t_noalloc": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "rann_dd_profile_enable": (_I, [_P, _I]),
     "rann_dd_profile_get": (_I, [_P, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_L),
                                  ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
