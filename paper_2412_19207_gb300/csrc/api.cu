@@ -475,7 +475,7 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     CK(dalloc(h, (void**)&h->d_V, sizeof(double) * mm * J));
     CK(dalloc(h, (void**)&h->d_eig, sizeof(double) * (size_t)m * J));
   }
-  std::vector<int> info(J, 0);
+  std::vector<int> info(J, 0), dev_ranks(J, m);
   h->eig_host.assign((size_t)m * J, 0.0);
   h->sumNm2 = 0;
   for (int j = 0; j < J; ++j) h->sumNm2 += (double)h->subs[j].N * m * (m + 1);
@@ -498,14 +498,20 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     double** d_mats; int* d_ns; int* d_lds;
     CK(dupload(h, &d_mats, mats)); CK(dupload(h, &d_ns, ns)); CK(dupload(h, &d_lds, lds));
     KL(h, K_SYMM, 1, launch_symmetrize(d_mats, d_ns, d_lds, J, m, h->st));
-    double* d_work; int* d_info;
-    CK(dalloc(h, (void**)&d_work, sizeof(double) * mm * J));
+    double* d_work; int* d_info; int* d_ranks;
+    CK(dalloc(h, (void**)&d_work, sizeof(double) * (size_t)syevd_work_doubles(m) * J));
     CK(dalloc(h, (void**)&d_info, sizeof(int) * J));
-    KLA(h, K_EIG, 1, 24.0 * mm * J, 9.0 * (double)m * mm * J, launch_syevd(h->d_V, m, m, J, h->d_eig, d_work, d_info, h->st));
+    CK(dalloc(h, (void**)&d_ranks, sizeof(int) * J));
+    // algorithmic flops: tridiagonal reduction 4/3 m^3 per matrix (the eigenvector work depends on p_j
+    // and is added below once the ranks are known)
+    KLA(h, K_EIG, 1, 24.0 * mm * J, 4.0 / 3.0 * (double)m * mm * J,
+        launch_syevd(h->d_V, m, J, h->d_eig, d_work, d_info, d_ranks, mode, thr, h->st));
     CK(cudaMemcpyAsync(h->eig_host.data(), h->d_eig, sizeof(double) * m * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(info.data(), d_info, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(dev_ranks.data(), d_ranks, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     dfree(h, d_tasks); dfree(h, d_mats); dfree(h, d_ns); dfree(h, d_lds); dfree(h, d_work); dfree(h, d_info);
+    dfree(h, d_ranks);
   }
   for (int j = 0; j < J; ++j)
     REQUIRE(info[j] == 0, RANN_ECUDA, "eigen-decomposition of subdomain %d did not converge", j);
@@ -520,22 +526,10 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   int64_t woff = 0, boff = 0;
   h->maxP = 0;
   for (int j = 0; j < J; ++j) {
-    const double* lam = h->eig_host.data() + (size_t)m * j;
-    int p = m;
-    if (mode == RANN_PCA_ABS) {
-      p = 0;
-      for (int k = 0; k < m; ++k) if (std::sqrt(std::max(lam[k], 0.0)) > thr) ++p;
-    } else if (mode == RANN_PCA_VARIANCE) {
-      double tot = 0.0;
-      for (int k = 0; k < m; ++k) tot += std::max(lam[k], 0.0);
-      double cs = 0.0;
-      p = m;
-      for (int k = 0; k < m; ++k) {
-        cs += std::max(lam[k], 0.0);
-        if (cs >= (1.0 - thr) * tot) { p = k + 1; break; }
-      }
-    }
-    p = std::max(p, 1);
+    // the eigensolver applied the rank rule (it forms only the kept eigenvectors)
+    const int p = dev_ranks[j];
+    REQUIRE(p >= 1 && p <= m, RANN_ECUDA, "eigensolver returned rank %d for subdomain %d", p, j);
+    h->prof.flops[K_EIG] += 2.0 * (double)m * m * p + 4.0 * (double)m * p * p;
     SubDev& S = h->subs[j];
     S.p = p;
     S.P = p + (p & 1);

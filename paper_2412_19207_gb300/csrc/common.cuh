@@ -80,8 +80,11 @@ cudaError_t launch_symmetrize(double* const* d_mats, const int* d_n, const int* 
                               int maxn, cudaStream_t st);
 
 // eig.cu -- batched symmetric eigen-decomposition (float64)
-cudaError_t launch_syevd(double* d_A, int m, int lda_stride, int batch, double* d_w, double* d_work,
-                         int* d_info, cudaStream_t st);
+// Eigenpairs of `batch` m x m symmetric matrices; ranks by the PCA rule (mode, thr);
+// d_work holds batch * syevd_work_doubles(m) doubles.
+int64_t syevd_work_doubles(int m);
+cudaError_t launch_syevd(double* d_A, int m, int batch, double* d_w, double* d_work, int* d_info, int* d_ranks,
+                         int mode, double thr, cudaStream_t st);
 
 // chol.cu -- batched uneven Cholesky and triangular solves
 struct CholMat {

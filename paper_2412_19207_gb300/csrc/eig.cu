@@ -1,57 +1,71 @@
-// Batched symmetric eigen-decomposition in float64, one thread block per matrix.
+// Batched symmetric eigen-decomposition in float64 for the PCA (Sec. 4,
+// Eq. (pca)): the right singular vectors and singular values of Psi_j are the
+// eigenpairs of G_j = Psi_j^T Psi_j = V diag(sigma^2) V^T.  One thread block
+// per matrix; only the p_j kept eigenvectors are formed.
 //
-// Sec. 4 (Eq. (pca)): the PCA of Psi_j needs its right singular vectors and
-// singular values; they are the eigenpairs of the Gram matrix
-// Psi_j^T Psi_j = V diag(sigma^2) V^T.  Steps (Golub & Van Loan, Ch. 8):
-//   1. Householder tridiagonalisation A = Q T Q^T (reflectors kept in A);
-//   2. Q accumulated backwards from the reflectors;
-//   3. implicit QL iteration with Wilkinson shifts on T (the tql2 scheme of
-//      Bowdler, Martin, Reinsch & Wilkinson, 1968), its plane rotations
-//      applied to the eigenvector rows;
-//   4. eigenpairs sorted by descending eigenvalue.
-// Output: w[m] descending, and A overwritten by V (row-major, column c = the
-// eigenvector of w[c]).  info[b] != 0 if QL did not converge in 60 sweeps for
-// some eigenvalue.
+//   1. Householder tridiagonalisation G = Q T Q^T (Golub & Van Loan 8.3.1),
+//      reflectors kept in the rows of G; the symmetric rank-2 update is done
+//      once per lower element and mirrored, so the matrix stays exactly
+//      symmetric.
+//   2. Eigenvalues of T by implicit QL with Wilkinson shifts (the tql1 scheme
+//      of Bowdler, Martin, Reinsch & Wilkinson, 1968), no vectors.
+//   3. Eigenvalues sorted descending; the rank rule of Sec. 4 gives p_j.
+//   4. Eigenvectors of T for the p_j largest eigenvalues by inverse iteration
+//      (tridiagonal LU with partial pivoting, two solves; Wilkinson, The
+//      Algebraic Eigenvalue Problem, Ch. 9), one thread per vector, then
+//      classical Gram-Schmidt applied twice in descending order.
+//   5. Back-transformation V = Q Z, one warp per vector.
+// Output: w[m] descending; ranks[b] = p_j; G overwritten by V (row-major
+// m x m, column c = eigenvector c for c < p_j, zero beyond); info[b] != 0 if
+// QL did not converge in 100 sweeps for some eigenvalue.
 #include "common.cuh"
 
 namespace {
 
-constexpr int NT = 256;
+constexpr int NT = 512;
+constexpr int NW = NT / 32;
 
 __device__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
   if (threadIdx.x == 0) {
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    double s = 0.0;
+    for (int w = 0; w < NW; ++w) s += red[w];
     red[32] = s;
   }
   __syncthreads();
   return red[32];
 }
 
+// Deterministic start vector for inverse iteration, entries in [-0.5, 1.5).
+__device__ __forceinline__ double start_entry(int i, int k) {
+  unsigned h = (unsigned)i * 2654435761u ^ ((unsigned)k * 40503u + 0x9E3779B9u);
+  h ^= h >> 15;
+  h *= 2246822519u;
+  h ^= h >> 13;
+  return (double)(h & 2047u) / 1024.0 - 0.5;
+}
+
 __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int m, int64_t stride,
-                                                  double* __restrict__ wall,
-                                                  double* __restrict__ Zall,
-                                                  int* __restrict__ info) {
+                                                  double* __restrict__ wall, double* __restrict__ work_all,
+                                                  int64_t work_stride, int* __restrict__ info,
+                                                  int* __restrict__ ranks, int mode, double thr) {
   extern __shared__ double sm[];
-  double* v = sm;              // [m]
-  double* w = v + m;           // [m]
-  double* d = w + m;           // [m]
-  double* e = d + m;           // [m]
-  double* beta = e + m;        // [m]
-  double* rc = beta + m;       // [m] rotation cos
-  double* rs = rc + m;         // [m] rotation sin
-  int* ri = (int*)(rs + m);    // [m] rotation index
-  int* perm = ri + m;          // [m]
+  double* v = sm;              // [m] reflector / QL diagonal copy
+  double* w = v + m;           // [m] symmetric product / QL off-diagonal copy
+  double* d = w + m;           // [m] tridiagonal diagonal (later: Gram-Schmidt coefficients)
+  double* e = d + m;           // [m] tridiagonal off-diagonal
+  double* beta = e + m;        // [m] reflector scalars
+  double* ev = beta + m;       // [m] eigenvalues, descending
   __shared__ double red[33];
-  __shared__ int nrot, ql_fail, done;
   __shared__ double tnorm;
+  __shared__ int ql_fail, prank;
   double* A = Aall + blockIdx.x * stride;
-  double* Zt = Zall + blockIdx.x * stride;   // eigenvectors as rows
-  const int tid = threadIdx.x;
+  double* Z = work_all + blockIdx.x * work_stride;   // rows: eigenvectors
+  double* LU = Z + (int64_t)m * m;                   // 5 m NT doubles, [i][thread]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   // ---- 1. tridiagonalisation ----
   for (int k = 0; k + 2 < m; ++k) {
@@ -62,40 +76,44 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
       v[c] = x;
       loc += x * x;
     }
-    double sig2 = block_sum(loc, red);
-    double sigma = sqrt(sig2);
-    double x0 = v[0];
-    double alpha = (x0 >= 0.0) ? -sigma : sigma;
-    double bt = 0.0;
-    if (sigma > 0.0) bt = 1.0 / (sig2 + fabs(x0) * sigma);   // 2 / (v^T v)
+    const double sig2 = block_sum(loc, red);
+    const double sigma = sqrt(sig2);
+    const double x0 = v[0];
+    const double alpha = (x0 >= 0.0) ? -sigma : sigma;
+    const double bt = (sigma > 0.0) ? 1.0 / (sig2 + fabs(x0) * sigma) : 0.0;   // 2 / (v^T v)
     __syncthreads();
     if (tid == 0) { v[0] = x0 - alpha; d[k] = A[(int64_t)k * m + k]; e[k] = alpha; beta[k] = bt; }
     __syncthreads();
     if (bt != 0.0) {
-      // p = bt * A' v  (A' = A[k+1:, k+1:], read by columns for coalescing)
       double pv = 0.0;
-      for (int r = tid; r < n1; r += NT) {
+      for (int r = tid; r < n1; r += NT) {   // p = bt A' v, A' read by columns (coalesced over r)
         double s = 0.0;
-        for (int c = 0; c < n1; ++c) s = fma(A[(int64_t)(k + 1 + c) * m + k + 1 + r], v[c], s);
+        const double* col = A + (int64_t)(k + 1) * m + k + 1 + r;
+        for (int c = 0; c < n1; ++c) s = fma(col[(int64_t)c * m], v[c], s);
         s *= bt;
         w[r] = s;
-        pv += s * v[r];
+        pv = fma(s, v[r], pv);
       }
-      double K = 0.5 * bt * block_sum(pv, red);
-      for (int r = tid; r < n1; r += NT) w[r] = w[r] - K * v[r];
+      const double K = 0.5 * bt * block_sum(pv, red);
+      for (int r = tid; r < n1; r += NT) w[r] = fma(-K, v[r], w[r]);
       __syncthreads();
-      // A' -= v w^T + w v^T (evaluated symmetrically so that A stays exactly symmetric)
-      for (int64_t e2 = tid; e2 < (int64_t)n1 * n1; e2 += NT) {
-        int r = (int)(e2 / n1), c = (int)(e2 % n1);
-        double s = __dadd_rn(__dmul_rn(v[r], w[c]), __dmul_rn(w[r], v[c]));
-        int64_t idx = (int64_t)(k + 1 + r) * m + k + 1 + c;
-        A[idx] = __dsub_rn(A[idx], s);
+      // A' -= v w^T + w v^T: each lower element once, mirrored to the upper one
+      for (int rr = warp; rr < n1; rr += NW) {
+        double* row = A + (int64_t)(k + 1 + rr) * m + k + 1;
+        const double vr = v[rr], wr = w[rr];
+        for (int cc = lane; cc <= rr; cc += 32) {
+          double s = fma(-vr, w[cc], fma(-wr, v[cc], row[cc]));
+          row[cc] = s;
+          if (cc != rr) A[(int64_t)(k + 1 + cc) * m + k + 1 + rr] = s;
+        }
       }
     }
     __syncthreads();
     for (int c = tid; c < n1; c += NT) A[(int64_t)k * m + k + 1 + c] = v[c];   // keep the reflector
     __syncthreads();
   }
+
+  // ---- 2. eigenvalues of T: implicit QL without vectors (one thread) ----
   if (tid == 0) {
     if (m >= 2) {
       d[m - 2] = A[(int64_t)(m - 2) * m + m - 2];
@@ -105,130 +123,207 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
     d[m - 1] = A[(int64_t)(m - 1) * m + m - 1];
     e[m - 1] = 0.0;
     beta[m - 1] = 0.0;
-    ql_fail = 0;
     double t = 0.0;
-    for (int i = 0; i < m; ++i) t = fmax(t, fabs(d[i]) + fabs(e[i]));
+    for (int i = 0; i < m; ++i) { t = fmax(t, fabs(d[i]) + fabs(e[i])); v[i] = d[i]; w[i] = e[i]; }
     tnorm = t;
-  }
-  __syncthreads();
-
-  // ---- 2. Q = H_0 H_1 ... H_{m-3}, accumulated backwards into Zt (as Q, then transposed) ----
-  for (int64_t e2 = tid; e2 < (int64_t)m * m; e2 += NT) Zt[e2] = ((e2 / m) == (e2 % m)) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int k = m - 3; k >= 0; --k) {
-    const int n1 = m - k - 1;
-    const double bt = beta[k];
-    if (bt == 0.0) continue;
-    for (int c = tid; c < n1; c += NT) v[c] = A[(int64_t)k * m + k + 1 + c];
-    __syncthreads();
-    for (int c = tid; c < n1; c += NT) {   // column k+1+c of Q
-      double t = 0.0;
-      for (int r = 0; r < n1; ++r) t = fma(v[r], Zt[(int64_t)(k + 1 + r) * m + k + 1 + c], t);
-      t *= bt;
-      for (int r = 0; r < n1; ++r) {
-        int64_t idx = (int64_t)(k + 1 + r) * m + k + 1 + c;
-        Zt[idx] = fma(-t, v[r], Zt[idx]);
-      }
-    }
-    __syncthreads();
-  }
-  // transpose in place: Zt[c][r] = Q[r][c]
-  for (int64_t e2 = tid; e2 < (int64_t)m * m; e2 += NT) {
-    int r = (int)(e2 / m), c = (int)(e2 % m);
-    if (r < c) {
-      double a = Zt[(int64_t)r * m + c], b = Zt[(int64_t)c * m + r];
-      Zt[(int64_t)r * m + c] = b;
-      Zt[(int64_t)c * m + r] = a;
-    }
-  }
-  __syncthreads();
-
-  // ---- 3. implicit QL on (d, e); rotations of each sweep applied to rows of Zt ----
-  for (int l = 0; l < m; ++l) {
-    int iter = 0;
-    while (true) {
-      if (tid == 0) {
+    int fail = 0;
+    for (int l = 0; l < m; ++l) {
+      int iter = 0;
+      while (true) {
         int mm = l;
         for (; mm < m - 1; ++mm) {
-          double dd = fabs(d[mm]) + fabs(d[mm + 1]);
-          if (fabs(e[mm]) <= 2.2e-16 * dd || fabs(e[mm]) <= 2.2e-16 * tnorm) break;
+          double dd = fabs(v[mm]) + fabs(v[mm + 1]);
+          if (fabs(w[mm]) <= 2.2e-16 * dd || fabs(w[mm]) <= 2.2e-16 * t) break;
         }
-        nrot = 0;
-        if (mm == l) {
-          done = 1;
-        } else if (iter >= 100) {
-          done = 1;
-          ql_fail = 1;
-        } else {
-          done = 0;
-          double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-          double r = hypot(g, 1.0);
-          g = d[mm] - d[l] + e[l] / (g + copysign(r, g));
-          double s = 1.0, c = 1.0, p = 0.0;
-          int i = mm - 1;
-          bool early = false;
-          for (; i >= l; --i) {
-            double f = s * e[i], b = c * e[i];
-            r = hypot(f, g);
-            e[i + 1] = r;
-            if (r == 0.0) { d[i + 1] -= p; e[mm] = 0.0; early = true; break; }
-            s = f / r; c = g / r;
-            g = d[i + 1] - p;
-            r = (d[i] - g) * s + 2.0 * c * b;
-            p = s * r;
-            d[i + 1] = g + p;
-            g = c * r - b;
-            rc[nrot] = c; rs[nrot] = s; ri[nrot] = i; ++nrot;
-          }
-          if (!early) { d[l] -= p; e[l] = g; e[mm] = 0.0; }
+        if (mm == l) break;
+        if (iter++ >= 100) { fail = 1; break; }
+        double g = (v[l + 1] - v[l]) / (2.0 * w[l]);
+        double r = hypot(g, 1.0);
+        g = v[mm] - v[l] + w[l] / (g + copysign(r, g));
+        double s = 1.0, c = 1.0, p = 0.0;
+        bool early = false;
+        for (int i = mm - 1; i >= l; --i) {
+          double f = s * w[i], b = c * w[i];
+          r = hypot(f, g);
+          w[i + 1] = r;
+          if (r == 0.0) { v[i + 1] -= p; w[mm] = 0.0; early = true; break; }
+          s = f / r; c = g / r;
+          g = v[i + 1] - p;
+          r = (v[i] - g) * s + 2.0 * c * b;
+          p = s * r;
+          v[i + 1] = g + p;
+          g = c * r - b;
         }
+        if (!early) { v[l] -= p; w[l] = g; w[mm] = 0.0; }
       }
-      __syncthreads();
-      const int dn = done, nr = nrot;
-      __syncthreads();   // all threads hold done/nrot before thread 0 rewrites them
-      if (dn) break;
-      ++iter;
-      for (int r = tid; r < m; r += NT) {
-        for (int q = 0; q < nr; ++q) {
-          int i = ri[q];
-          double c = rc[q], s = rs[q];
-          double a = Zt[(int64_t)i * m + r], b = Zt[(int64_t)(i + 1) * m + r];
-          Zt[(int64_t)(i + 1) * m + r] = fma(s, a, c * b);
-          Zt[(int64_t)i * m + r] = fma(c, a, -s * b);
-        }
-      }
-      __syncthreads();
     }
-  }
-
-  // ---- 4. sort descending; V[r][c] = Zt[perm[c]][r] back into A ----
-  if (tid == 0) {
-    for (int c = 0; c < m; ++c) perm[c] = c;
-    for (int c = 0; c < m; ++c) {
-      int best = c;
-      for (int q = c + 1; q < m; ++q) if (d[perm[q]] > d[perm[best]]) best = q;
-      int t = perm[c]; perm[c] = perm[best]; perm[best] = t;
-    }
-    info[blockIdx.x] = ql_fail;
+    ql_fail = fail;
   }
   __syncthreads();
-  for (int c = tid; c < m; c += NT) wall[(int64_t)blockIdx.x * m + c] = d[perm[c]];
+
+  // ---- 3. sort descending (rank of each eigenvalue; ties by index) ----
+  for (int t = tid; t < m; t += NT) {
+    const double x = v[t];
+    int rk = 0;
+    for (int j = 0; j < m; ++j) rk += (v[j] > x) || (v[j] == x && j < t);
+    ev[rk] = x;
+  }
+  __syncthreads();
+  // ---- rank rule (Sec. 4) ----
+  if (tid == 0) {
+    int p = m;
+    if (mode == RANN_PCA_ABS) {
+      p = 0;
+      for (int k = 0; k < m; ++k) if (sqrt(fmax(ev[k], 0.0)) > thr) ++p;
+    } else if (mode == RANN_PCA_VARIANCE) {
+      double tot = 0.0;
+      for (int k = 0; k < m; ++k) tot += fmax(ev[k], 0.0);
+      double cs = 0.0;
+      for (int k = 0; k < m; ++k) {
+        cs += fmax(ev[k], 0.0);
+        if (cs >= (1.0 - thr) * tot) { p = k + 1; break; }
+      }
+    }
+    prank = max(p, 1);
+  }
+  __syncthreads();
+  const int p = prank;
+
+  // ---- 4. eigenvectors of T by inverse iteration ----
+  const double tolp = 2.2e-16 * tnorm + 1e-300;
+  double* u0 = LU;
+  double* u1 = LU + (int64_t)m * NT;
+  double* u2 = LU + 2 * (int64_t)m * NT;
+  double* ml = LU + 3 * (int64_t)m * NT;
+  double* xv = LU + 4 * (int64_t)m * NT;
+  for (int k0 = 0; k0 < p; k0 += NT) {
+    const int k = k0 + tid;
+    if (k < p) {
+      const double lam = ev[k];
+      // LU of T - lam I with partial pivoting.  A row swap at step i is coded
+      // in the multiplier as -(mult + 4) (|mult| <= 1 either way).
+      double cd = d[0] - lam, cs = (m > 1) ? e[0] : 0.0;
+      for (int i = 0; i + 1 < m; ++i) {
+        const double sub = e[i];
+        const double nd = d[i + 1] - lam, ns = (i + 2 < m) ? e[i + 1] : 0.0;
+        double mult, a0, a1, a2;
+        const bool swap = fabs(sub) > fabs(cd);
+        if (!swap) {
+          if (fabs(cd) < tolp) cd = (cd < 0.0) ? -tolp : tolp;
+          mult = sub / cd;
+          a0 = cd; a1 = cs; a2 = 0.0;
+          cd = nd - mult * cs;
+          cs = ns;
+        } else {
+          mult = cd / sub;
+          a0 = sub; a1 = nd; a2 = ns;
+          cd = cs - mult * nd;
+          cs = -mult * ns;
+        }
+        u0[(int64_t)i * NT + tid] = a0;
+        u1[(int64_t)i * NT + tid] = a1;
+        u2[(int64_t)i * NT + tid] = a2;
+        ml[(int64_t)i * NT + tid] = swap ? -(mult + 4.0) : mult;
+      }
+      if (fabs(cd) < tolp) cd = (cd < 0.0) ? -tolp : tolp;
+      u0[(int64_t)(m - 1) * NT + tid] = cd;
+      for (int i = 0; i < m; ++i) xv[(int64_t)i * NT + tid] = start_entry(i, k);
+      for (int it = 0; it < 2; ++it) {
+        for (int i = 0; i + 1 < m; ++i) {      // apply the row swaps and L^{-1}
+          double mc = ml[(int64_t)i * NT + tid];
+          double xi = xv[(int64_t)i * NT + tid], xn = xv[(int64_t)(i + 1) * NT + tid];
+          if (mc <= -3.0) {
+            mc = -mc - 4.0;
+            const double tmp = xi; xi = xn; xn = tmp;
+          }
+          xv[(int64_t)i * NT + tid] = xi;
+          xv[(int64_t)(i + 1) * NT + tid] = xn - mc * xi;
+        }
+        double x1 = 0.0, x2 = 0.0, amax = 0.0;
+        for (int i = m - 1; i >= 0; --i) {      // U^{-1}
+          double s = xv[(int64_t)i * NT + tid];
+          if (i + 1 < m) s -= u1[(int64_t)i * NT + tid] * x1;
+          if (i + 2 < m) s -= u2[(int64_t)i * NT + tid] * x2;
+          const double xi = s / u0[(int64_t)i * NT + tid];
+          xv[(int64_t)i * NT + tid] = xi;
+          x2 = x1;
+          x1 = xi;
+          amax = fmax(amax, fabs(xi));
+        }
+        const double sc = (amax > 0.0 && amax < 1e300) ? 1.0 / amax : 1.0;
+        for (int i = 0; i < m; ++i) xv[(int64_t)i * NT + tid] *= sc;
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < m; ++i) { const double x = xv[(int64_t)i * NT + tid]; nrm = fma(x, x, nrm); }
+      const double inv = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
+      for (int i = 0; i < m; ++i) Z[(int64_t)k * m + i] = xv[(int64_t)i * NT + tid] * inv;
+    }
+  }
+  __syncthreads();
+  // ---- classical Gram-Schmidt, twice, in descending order ----
+  for (int k = 1; k < p; ++k) {
+    double* zk = Z + (int64_t)k * m;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = tid; j < k; j += NT) {
+        const double* zj = Z + (int64_t)j * m;
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s = fma(zj[i], zk[i], s);
+        d[j] = s;
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += NT) {
+        double s = zk[i];
+        for (int j = 0; j < k; ++j) s = fma(-d[j], Z[(int64_t)j * m + i], s);
+        zk[i] = s;
+      }
+      __syncthreads();
+    }
+    double loc = 0.0;
+    for (int i = tid; i < m; i += NT) loc = fma(zk[i], zk[i], loc);
+    const double nn = block_sum(loc, red);
+    const double inv = (nn > 0.0) ? 1.0 / sqrt(nn) : 0.0;
+    for (int i = tid; i < m; i += NT) zk[i] *= inv;
+    __syncthreads();
+  }
+  // ---- 5. back-transformation V = H_0 H_1 ... H_{m-3} Z, one warp per vector ----
+  for (int c = warp; c < p; c += NW) {
+    double* z = Z + (int64_t)c * m;
+    for (int k = m - 3; k >= 0; --k) {
+      const double bt = beta[k];
+      if (bt == 0.0) continue;
+      const double* vk = A + (int64_t)k * m + k + 1;
+      double s = 0.0;
+      for (int i = lane; i < m - k - 1; i += 32) s = fma(vk[i], z[k + 1 + i], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      s *= bt;
+      for (int i = lane; i < m - k - 1; i += 32) z[k + 1 + i] = fma(-s, vk[i], z[k + 1 + i]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // ---- output ----
+  for (int c = tid; c < m; c += NT) wall[(int64_t)blockIdx.x * m + c] = ev[c];
   for (int64_t e2 = tid; e2 < (int64_t)m * m; e2 += NT) {
-    int r = (int)(e2 / m), c = (int)(e2 % m);
-    A[e2] = Zt[(int64_t)perm[c] * m + r];
+    const int r = (int)(e2 / m), c = (int)(e2 % m);
+    A[e2] = (c < p) ? Z[(int64_t)c * m + r] : 0.0;
+  }
+  if (tid == 0) {
+    info[blockIdx.x] = ql_fail;
+    ranks[blockIdx.x] = p;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_syevd(double* d_A, int m, int /*lda_stride*/, int batch, double* d_w,
-                         double* d_work, int* d_info, cudaStream_t st) {
+int64_t syevd_work_doubles(int m) { return (int64_t)m * m + 5 * (int64_t)m * NT; }
+
+cudaError_t launch_syevd(double* d_A, int m, int batch, double* d_w, double* d_work, int* d_info, int* d_ranks,
+                         int mode, double thr, cudaStream_t st) {
   if (batch == 0) return cudaSuccess;
-  size_t smem = sizeof(double) * 8 * (size_t)m + sizeof(int) * 2 * (size_t)m;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  syev_kernel<<<batch, NT, smem, st>>>(d_A, m, (int64_t)m * m, d_w, d_work, d_info);
+  const size_t smem = sizeof(double) * 6 * (size_t)m;
+  cudaError_t e = cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  syev_kernel<<<batch, NT, smem, st>>>(d_A, m, (int64_t)m * m, d_w, d_work, syevd_work_doubles(m), d_info,
+                                       d_ranks, mode, thr);
   return cudaGetLastError();
 }
