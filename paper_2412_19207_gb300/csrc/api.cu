@@ -24,6 +24,20 @@ cudaError_t launch_matvec_HT2(const ProbDev& P, const SubDev* d_sub, int J, cons
 cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, int* d_fail,
                              const double* d_dmax, cudaStream_t st);
 cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st);
+cudaError_t launch_split(const double* d_x, float2* d_x2, int64_t n, cudaStream_t st);
+cudaError_t launch_rowdot_df(const SubDev* d_sub, const int* d_rtiles, int nrtiles, const float2* d_B2,
+                             const float2* d_x2, float2* d_yp, cudaStream_t st);
+cudaError_t launch_matvec_HT_df(const ProbDev& P, const SubDev* d_sub, int J, const int* d_rtiles, int nrtiles,
+                                const int* d_tile0, const int* d_cov, int Gmax, const float2* d_B2,
+                                const float2* d_yp, double* d_part, double* d_z, int maxP, cudaStream_t st);
+cudaError_t launch_split_lower(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st);
+cudaError_t launch_schwarz_gather_df(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
+                                     const int64_t* d_s_off, const double* d_r, float2* d_g2, cudaStream_t st);
+cudaError_t launch_trmv_lower_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
+                                 const float2* d_g2, float2* d_y2, cudaStream_t st);
+cudaError_t launch_trmv_upper_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
+                                 const int64_t* d_p_off, const float2* d_y2, double* d_part, double* d_s,
+                                 cudaStream_t st);
 cudaError_t launch_schwarz_gather(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
                                   const int64_t* d_s_off, const double* d_r, double* d_g, cudaStream_t st);
 cudaError_t launch_trmv_lower(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
@@ -85,16 +99,18 @@ void rann_set_error(const char* fmt, ...) {
 enum KId {
   K_POINTS, K_ASSEMBLE, K_RHS, K_GRAM, K_SYMM, K_EIG, K_PROJECT, K_PAIRGRAM, K_LOCALASM, K_ADDDIAG,
   K_CHOL, K_TRTRI, K_GATHER, K_TRMV_L, K_TRMV_U, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL,
-  K_COUNT
+  K_SPLIT, K_MATVEC_H_DF, K_MATVEC_HT_DF, K_GATHER_DF, K_TRMV_L_DF, K_TRMV_U_DF, K_COUNT
 };
 static const char* const KNAMES[K_COUNT] = {
   "points", "assemble", "rhs", "gram", "symmetrize", "eig", "project", "pair_gram", "local_assemble",
   "add_diag", "cholesky", "trtri", "schwarz_gather", "trmv_lower", "trmv_upper", "schwarz_combine",
-  "matvec_H", "matvec_HT", "dot", "vector", "eval"};
+  "matvec_H", "matvec_HT", "dot", "vector", "eval", "split_df32", "matvec_H_df32", "matvec_HT_df32",
+  "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32"};
 
 // Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
 // 1 = float64-ALU-bound (algorithmic flops count).
-static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1};
+static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1,
+                                     0, 0, 0, 0, 0, 0};
 
 struct Prof {
   bool on = false;
@@ -141,6 +157,10 @@ struct rann_dd_handle {
   int* d_tile0 = nullptr;
   double* d_part = nullptr;
   double* d_yscratch = nullptr;   // N
+  float2* d_B2 = nullptr;         // reduced blocks as double-float pairs (inner Krylov operator)
+  float2* d_x2 = nullptr;         // DoF
+  float2* d_y2 = nullptr;         // N
+  int inner_df = 1;               // inner Krylov iterations in double-float
   // precond
   int prec_kind = -1;
   int n_shifted = 0;
@@ -160,6 +180,9 @@ struct rann_dd_handle {
   int64_t* d_p_off = nullptr;
   double* d_Amats = nullptr;
   double* d_Xmats = nullptr;
+  float2* d_X2mats = nullptr;
+  float2* d_g2 = nullptr;
+  float2* d_ys2 = nullptr;
   double* d_pairbuf = nullptr;
   // krylov scratch
   double* d_red = nullptr;     // multidot partials
@@ -575,7 +598,14 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   }
   t0[J] = (int)rt.size() / 2;
   h->nrtiles = t0[J];
-  if (h->d_rtiles) { dfree(h, h->d_rtiles); dfree(h, h->d_tile0); dfree(h, h->d_part); dfree(h, h->d_yscratch); }
+  if (h->d_rtiles) {
+    dfree(h, h->d_rtiles); dfree(h, h->d_tile0); dfree(h, h->d_part); dfree(h, h->d_yscratch);
+    dfree(h, h->d_B2); dfree(h, h->d_x2); dfree(h, h->d_y2);
+  }
+  CK(dalloc(h, (void**)&h->d_B2, sizeof(float2) * (size_t)std::max<int64_t>(boff, 1)));
+  CK(dalloc(h, (void**)&h->d_x2, sizeof(float2) * (size_t)std::max<int64_t>(h->dof, 1)));
+  CK(dalloc(h, (void**)&h->d_y2, sizeof(float2) * (size_t)std::max<int64_t>(h->rows_total, 1)));
+  KLA(h, K_SPLIT, 1, 16.0 * boff, 0, launch_split(h->d_B, h->d_B2, boff, h->st));
   CK(dupload(h, &h->d_rtiles, rt));
   CK(dupload(h, &h->d_tile0, t0));
   CK(dalloc(h, (void**)&h->d_part, sizeof(double) * (size_t)h->nrtiles * h->maxP));
@@ -612,6 +642,18 @@ extern "C" rann_status rann_dd_normal_matvec(rann_dd_handle* h, const double* x_
   return RANN_OK;
 }
 
+// Inner-iteration operator: z = H^T H x with double-float blocks.
+static rann_status normal_matvec_fast(rann_dd_handle* h, const double* x, double* z) {
+  KLA(h, K_SPLIT, 1, 24.0 * h->dof, 0, launch_split(x, h->d_x2, h->dof, h->st));
+  // y_j = B_j x_j row by row (per block), then z_j = B_j^T y with y summed over the blocks holding each point
+  KLA(h, K_MATVEC_H_DF, 1, 8.0 * (h->sumNp + h->rows_total + h->dof), 2.0 * h->sumNp,
+      launch_rowdot_df(h->d_sub, h->d_rtiles, h->nrtiles, h->d_B2, h->d_x2, h->d_y2, h->st));
+  KLA(h, K_MATVEC_HT_DF, 2, 8.0 * (h->sumNp + 2.0 * h->rows_total + h->dof), 2.0 * h->sumNp,
+      launch_matvec_HT_df(h->P, h->d_sub, h->J, h->d_rtiles, h->nrtiles, h->d_tile0, h->d_cov, h->Gmax, h->d_B2,
+                          h->d_y2, h->d_part, z, h->maxP, h->st));
+  return RANN_OK;
+}
+
 // ------------------------------------------------------------ precond --
 
 static bool boxes_meet(const SubDev& a, const SubDev& b, int dim) {
@@ -629,9 +671,9 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   for (void* p : {(void*)h->d_mats, (void*)h->d_set_ptr, (void*)h->d_set_sub, (void*)h->d_inc_ptr,
                   (void*)h->d_inc_set, (void*)h->d_inc_pos, (void*)h->d_s_off, (void*)h->d_s,
                   (void*)h->d_Amats, (void*)h->d_Xmats, (void*)h->d_g, (void*)h->d_y, (void*)h->d_tpart,
-                  (void*)h->d_p_off})
+                  (void*)h->d_p_off, (void*)h->d_X2mats, (void*)h->d_g2, (void*)h->d_ys2})
     dfree(h, p);
-  h->d_mats = nullptr; h->d_Amats = nullptr; h->d_Xmats = nullptr;
+  h->d_mats = nullptr; h->d_Amats = nullptr; h->d_Xmats = nullptr; h->d_X2mats = nullptr;
   h->n_shifted = 0;
   h->prec_kind = kind;
   if (kind == RANN_PREC_NONE) return RANN_OK;
@@ -730,6 +772,7 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   }
   CK(dalloc(h, (void**)&h->d_Amats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
   CK(dalloc(h, (void**)&h->d_Xmats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
+  CK(dalloc(h, (void**)&h->d_X2mats, sizeof(float2) * (size_t)std::max<int64_t>(aoff, 1)));
   h->sum_n = h->sum_n2 = h->sum_n3 = 0;
   for (int i = 0; i < J; ++i) {
     const double n = mats[i].n;
@@ -737,6 +780,7 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   }
   for (int i = 0; i < J; ++i) {
     mats[i].X = h->d_Xmats + reinterpret_cast<int64_t>(mats[i].A);
+    mats[i].X2 = h->d_X2mats + reinterpret_cast<int64_t>(mats[i].A);
     mats[i].A = h->d_Amats + reinterpret_cast<int64_t>(mats[i].A);
   }
   int64_t* d_tab; int *d_tab_ptr, *d_boffs, *d_boff_ptr; double* d_dmax; int* d_fail;
@@ -798,6 +842,7 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   for (int i = 0; i < J; ++i) h->n_shifted += shifted[i];
   // X_i = L_i^{-1} for the parallel apply
   KLA(h, K_TRTRI, 2, 0, h->sum_n3 / 3.0, launch_trtri(h->d_mats, J, h->maxn, h->st));
+  KLA(h, K_SPLIT, 1, 6.0 * h->sum_n2, 0, launch_split_lower(h->d_mats, J, h->maxn, h->st));
   std::vector<int64_t> p_off(J + 1, 0);
   for (int i = 0; i < J; ++i) p_off[i + 1] = p_off[i] + (int64_t)((mats[i].n + 255) / 256) * mats[i].n;
   CK(dupload(h, &h->d_p_off, p_off));
@@ -820,6 +865,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   CK(dalloc(h, (void**)&h->d_s, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
   CK(dalloc(h, (void**)&h->d_g, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
   CK(dalloc(h, (void**)&h->d_y, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
+  CK(dalloc(h, (void**)&h->d_g2, sizeof(float2) * (size_t)std::max<int64_t>(s_off[J], 1)));
+  CK(dalloc(h, (void**)&h->d_ys2, sizeof(float2) * (size_t)std::max<int64_t>(s_off[J], 1)));
   dfree(h, d_ridx); dfree(h, d_tasks); dfree(h, d_tab); dfree(h, d_tab_ptr); dfree(h, d_boffs); dfree(h, d_boff_ptr);
   dfree(h, d_dmax); dfree(h, d_fail); dfree(h, h->d_pairbuf);
   h->d_pairbuf = nullptr;
@@ -827,9 +874,21 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   return h->n_shifted ? RANN_LOCAL_SINGULAR : RANN_OK;
 }
 
-static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z) {
+static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, bool fast = false) {
   if (h->prec_kind == RANN_PREC_NONE) {
     CK(cudaMemcpyAsync(z, r, sizeof(double) * h->dof, cudaMemcpyDeviceToDevice, h->st));
+    return RANN_OK;
+  }
+  if (fast) {
+    KLA(h, K_GATHER_DF, 1, 16.0 * h->sum_n, 0,
+        launch_schwarz_gather_df(h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub, h->d_s_off, r, h->d_g2, h->st));
+    KLA(h, K_TRMV_L_DF, 1, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n,
+        launch_trmv_lower_df(h->d_mats, h->nsets, h->maxn, h->d_s_off, h->d_g2, h->d_ys2, h->st));
+    KLA(h, K_TRMV_U_DF, 2, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n,
+        launch_trmv_upper_df(h->d_mats, h->nsets, h->maxn, h->d_s_off, h->d_p_off, h->d_ys2, h->d_tpart, h->d_s,
+                             h->st));
+    KLA(h, K_COMBINE, 1, 8.0 * (h->sum_n + h->dof), 0, launch_schwarz_combine(h->d_sub, h->J, h->d_inc_ptr,
+        h->d_inc_set, h->d_inc_pos, h->d_s_off, h->d_s, h->prec_kind, z, h->st));
     return RANN_OK;
   }
   KLA(h, K_GATHER, 1, 16.0 * h->sum_n, 0, launch_schwarz_gather(h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub, h->d_s_off, r, h->d_g, h->st));
@@ -849,7 +908,7 @@ extern "C" rann_status rann_dd_precond_apply(rann_dd_handle* h, const double* r_
 // -------------------------------------------------------------- solves --
 
 static rann_status dot_host(rann_dd_handle* h, const double* x, const double* y, int64_t n, double* out) {
-  KLA(h, K_DOT, 2, 16.0 * n, 2.0 * n, launch_multidot(x, 0, 1, y, n, h->d_red, h->d_scal, h->st));
+  KLA(h, K_DOT, 1, 16.0 * n, 2.0 * n, launch_multidot(x, 0, 1, y, n, h->d_red, h->d_scal, h->st));
   CK(cudaMemcpyAsync(h->h_scal, h->d_scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   *out = h->h_scal[0];
@@ -870,6 +929,19 @@ struct Workspace {
   }
 };
 
+// The Krylov iterations apply the operator and the preconditioner with
+// double-float data (A_in, M_in); every residual that decides a restart or the
+// exit is recomputed with the float64 operator (A_64).  The loop between two
+// float64 residuals is one step of iterative refinement, so the returned W
+// solves the float64 normal equations to rtol.  With inner_df = 0 both are
+// float64.
+static rann_status op_inner(rann_dd_handle* h, const double* x, double* z) {
+  return h->inner_df ? normal_matvec_fast(h, x, z) : rann_dd_normal_matvec(h, x, z);
+}
+static rann_status prec_inner(rann_dd_handle* h, const double* r, double* z) {
+  return prec_apply(h, r, z, h->inner_df != 0);
+}
+
 extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
                                            int maxit, rann_dd_stats* stats) {
   REQUIRE(h && F_dev && W_dev, RANN_EINVAL, "null argument");
@@ -887,41 +959,60 @@ extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_de
   TRY(rann_dd_matvec_t(h, F_dev, b));
   CK(cudaMemsetAsync(W_dev, 0, sizeof(double) * n, h->st));
   CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  double bb, rz, rel = 1.0;
+  double bb;
   TRY(dot_host(h, b, b, n, &bb));
   const double bnorm = std::sqrt(bb);
   rann_status st = RANN_NOT_CONVERGED;
   int it = 0;
-  if (!(bnorm > 0.0)) { st = std::isfinite(bb) ? RANN_OK : RANN_BREAKDOWN; rel = 0.0; }
-  else {
-    TRY(prec_apply(h, r, z));
+  double rel = 1.0, true_rel = 1.0;
+  if (!(bnorm > 0.0)) {
+    st = std::isfinite(bb) ? RANN_OK : RANN_BREAKDOWN;
+    rel = true_rel = 0.0;
+  } else {
+    // Preconditioned CG; when the recursive residual has dropped by 1e-4 since
+    // the last float64 residual (or reaches rtol), the float64 residual
+    // b - A W replaces it and decides convergence (residual replacement: the
+    // search direction is kept).
+    double rz, rr;
+    TRY(prec_inner(h, r, z));
     CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
     TRY(dot_host(h, r, z, n, &rz));
-    while (it < maxit) {
-      TRY(rann_dd_normal_matvec(h, p, q));
+    while (true) {
+      if (it >= maxit) {
+        TRY(rann_dd_normal_matvec(h, W_dev, q));
+        CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+        KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(-1.0, q, 1.0, r, n, h->st));
+        TRY(dot_host(h, r, r, n, &rr));
+        true_rel = std::sqrt(rr) / bnorm;
+        if (true_rel <= rtol) st = RANN_OK;
+        break;
+      }
+      TRY(op_inner(h, p, q));
       double pq;
       TRY(dot_host(h, p, q, n, &pq));
       if (!(pq > 0.0) || !std::isfinite(pq)) { st = RANN_BREAKDOWN; break; }
-      double alpha = rz / pq;
+      const double alpha = rz / pq;
       KLA(h, K_VEC, 1, 40.0 * n, 4.0 * n, launch_cg_update(alpha, p, q, W_dev, r, n, h->st));
       ++it;
-      double rr;
       TRY(dot_host(h, r, r, n, &rr));
       rel = std::sqrt(rr) / bnorm;
       if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
-      if (rel <= rtol) { st = RANN_OK; break; }
-      TRY(prec_apply(h, r, z));
+      if (rel <= std::max(rtol, 1e-4 * true_rel)) {
+        TRY(rann_dd_normal_matvec(h, W_dev, q));
+        CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+        KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(-1.0, q, 1.0, r, n, h->st));
+        TRY(dot_host(h, r, r, n, &rr));
+        true_rel = std::sqrt(rr) / bnorm;
+        if (true_rel <= rtol) { st = RANN_OK; break; }
+        rel = true_rel;
+      }
+      TRY(prec_inner(h, r, z));
       double rz2;
       TRY(dot_host(h, r, z, n, &rz2));
       KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, z, rz2 / rz, p, n, h->st));
       rz = rz2;
     }
   }
-  // true residual
-  double tr = 0.0;
-  TRY(rann_dd_normal_matvec(h, W_dev, q));
-  KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b, -1.0, q, n, h->st));
-  TRY(dot_host(h, q, q, n, &tr));
   CK(cudaEventRecord(e1, h->st));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -929,13 +1020,13 @@ extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_de
   cudaEventDestroy(e0); cudaEventDestroy(e1);
   if (stats) {
     stats->iters = it;
-    stats->rel_res_true = bnorm > 0 ? std::sqrt(tr) / bnorm : 0.0;
+    stats->rel_res_true = true_rel;
     stats->rel_res_rec = rel;
     stats->rel_res_prec = -1.0;
     stats->ms_solve = ms;
     stats->n_shifted = h->n_shifted;
   }
-  if (st == RANN_NOT_CONVERGED) rann_set_error("CG reached maxit=%d at rel. residual %.3e", maxit, rel);
+  if (st == RANN_NOT_CONVERGED) rann_set_error("CG reached maxit=%d at rel. residual %.3e", maxit, true_rel);
   return st;
 }
 
@@ -955,7 +1046,7 @@ extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* 
   TRY(rann_dd_matvec_t(h, F_dev, b));
   CK(cudaMemsetAsync(W_dev, 0, sizeof(double) * n, h->st));
   // ||M^{-1} b||
-  TRY(prec_apply(h, b, V));
+  TRY(prec_inner(h, b, V));
   double mbb;
   TRY(dot_host(h, V, V, n, &mbb));
   const double mbnorm = std::sqrt(mbb);
@@ -964,29 +1055,38 @@ extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* 
   double rel = 1.0;
   rann_status st = RANN_NOT_CONVERGED;
   if (!(mbnorm > 0.0)) { st = std::isfinite(mbb) ? RANN_OK : RANN_BREAKDOWN; rel = 0.0; }
-  while (st == RANN_NOT_CONVERGED && it < maxit) {
-    // r = M^{-1}(b - A x)
-    TRY(rann_dd_normal_matvec(h, W_dev, t));
-    KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b, -1.0, t, n, h->st));
-    TRY(prec_apply(h, t, V));
+  bool first = true;
+  while (st == RANN_NOT_CONVERGED) {
+    // r = M^{-1}(b - A W) with the float64 operator (W = 0 on the first cycle)
+    if (first) {
+      CK(cudaMemcpyAsync(t, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+    } else {
+      TRY(rann_dd_normal_matvec(h, W_dev, t));
+      KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b, -1.0, t, n, h->st));
+    }
+    first = false;
+    TRY(prec_inner(h, t, V));
     double bb;
     TRY(dot_host(h, V, V, n, &bb));
-    double beta = std::sqrt(bb);
+    const double beta = std::sqrt(bb);
     rel = beta / mbnorm;
     if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
     if (rel <= rtol) { st = RANN_OK; break; }
+    if (it >= maxit) break;
     KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_copy(1.0 / beta, V, V, n, h->st));
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jdone = 0;
     for (int j = 0; j < k && it < maxit; ++j) {
       double* w = V + (size_t)(j + 1) * n;
-      TRY(rann_dd_normal_matvec(h, V + (size_t)j * n, t));
-      TRY(prec_apply(h, t, w));
+      TRY(op_inner(h, V + (size_t)j * n, t));
+      TRY(prec_inner(h, t, w));
       // classical Gram-Schmidt, twice
       for (int pass = 0; pass < 2; ++pass) {
-        KLA(h, K_DOT, 2, 8.0 * n * (j + 2), 2.0 * n * (j + 1), launch_multidot(V, n, j + 1, w, n, h->d_red, hv + pass * (k + 2), h->st));
-        KLA(h, K_VEC, 1, 8.0 * n * (j + 3), 2.0 * n * (j + 1), launch_sub_combination(V, n, j + 1, hv + pass * (k + 2), w, n, h->st));
+        KLA(h, K_DOT, 1, 8.0 * n * (j + 2), 2.0 * n * (j + 1),
+            launch_multidot(V, n, j + 1, w, n, h->d_red, hv + pass * (k + 2), h->st));
+        KLA(h, K_VEC, 1, 8.0 * n * (j + 3), 2.0 * n * (j + 1),
+            launch_sub_combination(V, n, j + 1, hv + pass * (k + 2), w, n, h->st));
       }
       CK(cudaMemcpyAsync(hcol.data(), hv, sizeof(double) * hcol.size(), cudaMemcpyDeviceToHost, h->st));
       double ww;
@@ -1015,23 +1115,15 @@ extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* 
     }
     if (st == RANN_BREAKDOWN) break;
     for (int i = jdone - 1; i >= 0; --i) {
-      double s = g[i];
-      for (int q = i + 1; q < jdone; ++q) s -= Hm[(size_t)i * k + q] * y[q];
-      y[i] = Hm[(size_t)i * k + i] != 0.0 ? s / Hm[(size_t)i * k + i] : 0.0;
+      double sacc = g[i];
+      for (int q = i + 1; q < jdone; ++q) sacc -= Hm[(size_t)i * k + q] * y[q];
+      y[i] = Hm[(size_t)i * k + i] != 0.0 ? sacc / Hm[(size_t)i * k + i] : 0.0;
     }
     CK(cudaMemcpyAsync(hv, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, h->st));
-    KLA(h, K_VEC, 1, 8.0 * n * (jdone + 2), 2.0 * n * jdone, launch_add_combination(V, n, jdone, hv, W_dev, n, h->st));
+    KLA(h, K_VEC, 1, 8.0 * n * (jdone + 2), 2.0 * n * jdone,
+        launch_add_combination(V, n, jdone, hv, W_dev, n, h->st));
     CK(cudaStreamSynchronize(h->st));
-    if (rel <= rtol) {
-      // confirm with the explicit preconditioned residual
-      TRY(rann_dd_normal_matvec(h, W_dev, t));
-      KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b, -1.0, t, n, h->st));
-      TRY(prec_apply(h, t, V));
-      double rr;
-      TRY(dot_host(h, V, V, n, &rr));
-      rel = std::sqrt(rr) / mbnorm;
-      if (rel <= rtol) st = RANN_OK;
-    }
+    // the next cycle recomputes the residual in float64 and decides convergence
   }
   double precrel = rel;
   double bb2, tr;
@@ -1054,6 +1146,13 @@ extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* 
   }
   if (st == RANN_NOT_CONVERGED) rann_set_error("GMRES reached maxit=%d at rel. residual %.3e", maxit, rel);
   return st;
+}
+
+extern "C" rann_status rann_dd_set_inner_precision(rann_dd_handle* h, int mode) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  REQUIRE(mode == 0 || mode == 1, RANN_EINVAL, "inner precision mode must be 0 (float64) or 1 (double-float)");
+  h->inner_df = mode;
+  return RANN_OK;
 }
 
 // ---------------------------------------------------------------- eval --

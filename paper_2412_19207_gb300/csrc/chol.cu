@@ -18,6 +18,7 @@
 // substitutions.  Per-unknown sums over the sets are formed in a fixed order
 // (deterministic, no atomics).
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace {
 
@@ -354,7 +355,134 @@ __global__ void add_diag_kernel(const CholMat* __restrict__ mats, const int* __r
   for (int r = threadIdx.x; r < M.n; r += blockDim.x) M.A[(int64_t)r * M.ld + r] += s;
 }
 
+// ---- double-float apply (the inner Krylov preconditioner) ----
+
+__global__ void schwarz_gather_df_kernel(const int* __restrict__ set_ptr, const int* __restrict__ set_sub,
+                                         const SubDev* __restrict__ subs, const int64_t* __restrict__ s_off,
+                                         const double* __restrict__ r, float2* __restrict__ g2) {
+  const int i = blockIdx.x;
+  float2* gi = g2 + s_off[i];
+  int off = 0;
+  for (int q = set_ptr[i]; q < set_ptr[i + 1]; ++q) {
+    const SubDev& S = subs[set_sub[q]];
+    for (int c = threadIdx.x; c < S.p; c += blockDim.x) gi[off + c] = df_split(r[S.woff + c]);
+    off += S.p;
+  }
+}
+
+// y2 = X2 g2 (lower triangular) in double-float: one warp per row, four
+// independent accumulator chains per lane.
+__global__ void __launch_bounds__(256) trmv_lower_df_kernel(const CholMat* __restrict__ mats,
+                                                            const int64_t* __restrict__ s_off,
+                                                            const float2* __restrict__ g2, float2* __restrict__ y2) {
+  const CholMat M = mats[blockIdx.y];
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= M.n) return;
+  const float2* row = M.X2 + (int64_t)r * M.ld;
+  const float2* gi = g2 + s_off[blockIdx.y];
+  float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+  int c = lane, cnt = 0;
+  for (; c + 96 <= r; c += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) df_mac(h[u], l[u], row[c + 32 * u], gi[c + 32 * u]);
+    if ((++cnt & 7) == 0)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) df_renorm(h[u], l[u]);
+  }
+  for (int u = 0; c <= r; c += 32, ++u) df_mac(h[u & 3], l[u & 3], row[c], gi[c]);
+  df_add(h[0], l[0], h[1], l[1]);
+  df_add(h[2], l[2], h[3], l[3]);
+  df_add(h[0], l[0], h[2], l[2]);
+  df_warp_sum(h[0], l[0]);
+  if (lane == 0) y2[s_off[blockIdx.y] + r] = make_float2(h[0], l[0]);
+}
+
+// partial_i[rc][c] = sum over the rows of 256-row chunk rc (r >= c) of X2[r][c] y2[r]:
+// 64 columns x 4 row groups per block, two chains per thread, row groups added
+// in shared memory.  Block (ct, rc) with ct the 64-column tile; only chunks
+// that reach the lower triangle of the tile do work.
+__global__ void __launch_bounds__(256) trmv_upper_df_partial_kernel(const CholMat* __restrict__ mats,
+                                                                    const int64_t* __restrict__ s_off,
+                                                                    const int64_t* __restrict__ p_off,
+                                                                    const float2* __restrict__ y2,
+                                                                    double* __restrict__ part) {
+  const CholMat M = mats[blockIdx.z];
+  const int ct = blockIdx.x, rc = blockIdx.y;
+  const int c0 = ct * 64, r0 = rc * TT;
+  if (c0 >= M.n || r0 >= M.n || rc < c0 / TT) return;
+  const int r1 = min(M.n, r0 + TT);
+  __shared__ float2 ys[TT];
+  __shared__ float2 red[4][64];
+  const float2* yi = y2 + s_off[blockIdx.z];
+  for (int q = threadIdx.x; q < r1 - r0; q += 256) ys[q] = yi[r0 + q];
+  __syncthreads();
+  const int cx = threadIdx.x & 63, rg = threadIdx.x >> 6;
+  const int c = c0 + cx;
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+  if (c < M.n) {
+    int rr = max(r0, c);
+    rr += (rg - (rr - r0)) & 3;                       // first row of this group (rows = rg mod 4)
+    int cnt = 0;
+    for (; rr + 4 < r1; rr += 8) {
+      df_mac(h0, l0, M.X2[(int64_t)rr * M.ld + c], ys[rr - r0]);
+      df_mac(h1, l1, M.X2[(int64_t)(rr + 4) * M.ld + c], ys[rr + 4 - r0]);
+      if ((++cnt & 7) == 0) { df_renorm(h0, l0); df_renorm(h1, l1); }
+    }
+    if (rr < r1) df_mac(h0, l0, M.X2[(int64_t)rr * M.ld + c], ys[rr - r0]);
+    df_add(h0, l0, h1, l1);
+  }
+  red[rg][cx] = make_float2(h0, l0);
+  __syncthreads();
+  if (rg == 0 && c < M.n) {
+    float h = red[0][cx].x, l = red[0][cx].y;
+    for (int g = 1; g < 4; ++g) df_add(h, l, red[g][cx].x, red[g][cx].y);
+    part[p_off[blockIdx.z] + (int64_t)rc * M.n + c] = df_to_double(h, l);
+  }
+}
+
+// X2 = split(X) on the lower triangles.
+__global__ void split_lower_kernel(const CholMat* __restrict__ mats) {
+  const CholMat M = mats[blockIdx.y];
+  const int64_t tot = (int64_t)M.n * M.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / M.n), c = (int)(e % M.n);
+    if (c <= r) M.X2[(int64_t)r * M.ld + c] = df_split(M.X[(int64_t)r * M.ld + c]);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_split_lower(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st) {
+  if (nmat == 0) return cudaSuccess;
+  int64_t tot = (int64_t)maxn * maxn;
+  int gx = (int)((tot + 255) / 256);
+  if (gx > 2048) gx = 2048;
+  split_lower_kernel<<<dim3(gx, nmat), 256, 0, st>>>(d_mats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schwarz_gather_df(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
+                                     const int64_t* d_s_off, const double* d_r, float2* d_g2, cudaStream_t st) {
+  schwarz_gather_df_kernel<<<nsets, 256, 0, st>>>(d_set_ptr, d_set_sub, d_sub, d_s_off, d_r, d_g2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trmv_lower_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
+                                 const float2* d_g2, float2* d_y2, cudaStream_t st) {
+  trmv_lower_df_kernel<<<dim3((maxn + 7) / 8, nsets), 256, 0, st>>>(d_mats, d_s_off, d_g2, d_y2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trmv_upper_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
+                                 const int64_t* d_p_off, const float2* d_y2, double* d_part, double* d_s,
+                                 cudaStream_t st) {
+  int T = (maxn + TT - 1) / TT;
+  trmv_upper_df_partial_kernel<<<dim3((maxn + 63) / 64, T, nsets), 256, 0, st>>>(d_mats, d_s_off, d_p_off, d_y2,
+                                                                                 d_part);
+  trmv_upper_reduce_kernel<<<dim3((maxn + 255) / 256, nsets), 256, 0, st>>>(d_mats, d_s_off, d_p_off, d_part, d_s);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_assemble_local(const double* d_pairbuf, const int64_t* d_tab, const int* d_tab_ptr,
                                   const int* d_boff, const int* d_boff_ptr, const CholMat* d_mats, int nsets,

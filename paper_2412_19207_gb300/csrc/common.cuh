@@ -90,6 +90,7 @@ cudaError_t launch_syevd(double* d_A, int m, int batch, double* d_w, double* d_w
 struct CholMat {
   double* A;                 // n x n row-major (lower triangle used): A_i, then its Cholesky factor L_i
   double* X;                 // n x n row-major (lower triangle used): L_i^{-1}
+  float2* X2;                // L_i^{-1} as double-float pairs (same layout)
   int n;
   int ld;
 };

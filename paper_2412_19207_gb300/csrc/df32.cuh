@@ -1,0 +1,62 @@
+// Double-float ("df32") arithmetic: a value is an unevaluated sum hi + lo of
+// two float32 numbers with |lo| <= ulp(hi)/2, about 48 significant bits.
+// Error-free transformations (Dekker, "A floating-point technique for
+// extending the available precision", 1971; Knuth TAOCP Vol. 2, two-sum):
+//   two_sum(a, b) = (s, e) with s = fl(a + b), a + b = s + e exactly;
+//   a*b = p + e exactly with p = fl(a*b), e = fma(a, b, -p).
+// GB300 runs float32 at 70x its float64 rate, so the memory-bound solve
+// kernels use df32 (float32 FMA pipe) instead of float64 FMAs.  Operands are
+// stored pre-split (8 bytes per element, as float64 would be).
+// Every operation uses the _rn intrinsics so that the compiler cannot fuse
+// or reassociate the error-free sequences.
+#pragma once
+#include <cuda_runtime.h>
+
+__device__ __forceinline__ float2 df_split(double a) {
+  const float h = __double2float_rn(a);
+  return make_float2(h, __double2float_rn(a - (double)h));
+}
+
+__device__ __forceinline__ double df_to_double(float h, float l) { return (double)h + (double)l; }
+
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// (sh, sl) += a * x, a and x double-floats; sl collects all low-order terms.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float2 a, float2 x) {
+  const float p = __fmul_rn(a.x, x.x);
+  const float e = __fmaf_rn(a.x, x.x, -p);
+  float t, e2;
+  df_two_sum(sh, p, t, e2);
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e, e2), __fmaf_rn(a.x, x.y, __fmul_rn(a.y, x.x))));
+}
+
+// Fold the low part into the high part (fast two-sum, |sh| >= |sl| not required
+// for the exactness of the sum, only for normalisation).
+__device__ __forceinline__ void df_renorm(float& sh, float& sl) {
+  float s, e;
+  df_two_sum(sh, sl, s, e);
+  sh = s;
+  sl = e;
+}
+
+// (ah, al) += (bh, bl)
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  df_two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  df_two_sum(s, e, ah, al);
+}
+
+// Warp-wide double-float sum (result valid in every lane).
+__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add(h, l, oh, ol);
+  }
+}

@@ -1,11 +1,10 @@
 // Vector kernels for the Krylov solvers (PCG and GMRES on the normal
-// equations, Sec. 3/5), float64.  Reductions are deterministic: a fixed grid
-// writes per-block partial sums, one block adds them in index order.
+// equations, Sec. 3/5), float64.  Reductions are deterministic: each dot
+// product is one block reduction with a fixed summation order.
 #include "common.cuh"
 
 namespace {
 
-constexpr int RB = 256;     // reduction blocks
 constexpr int RT = 256;     // threads per reduction block
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -27,26 +26,17 @@ __device__ double block_sum(double v) {
   return s;   // valid in thread 0
 }
 
-// partial[b * nv + i] = sum over block b's range of V[i] . w  (V rows of length n)
-__global__ void __launch_bounds__(RT) multidot_partial(const double* __restrict__ V, int64_t ldv, int nv,
-                                                       const double* __restrict__ w, int64_t n,
-                                                       double* __restrict__ part) {
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t t0 = blockIdx.x * chunk, t1 = min(n, t0 + chunk);
-  for (int i = 0; i < nv; ++i) {
-    double s = 0.0;
-    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) s = fma(V[i * ldv + t], w[t], s);
-    s = block_sum(s);
-    if (threadIdx.x == 0) part[blockIdx.x * nv + i] = s;
-  }
-}
-
-__global__ void multidot_final(const double* __restrict__ part, int nb, int nv, double* __restrict__ out) {
-  int i = threadIdx.x;
-  if (i >= nv) return;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[b * nv + i];
-  out[i] = s;
+// out[i] = V[i] . w, block i (vectors of Krylov length; fixed summation order)
+__global__ void __launch_bounds__(RT) multidot_rows(const double* __restrict__ V, int64_t ldv,
+                                                    const double* __restrict__ w, int64_t n,
+                                                    double* __restrict__ out) {
+  const double* v = V + blockIdx.x * ldv;
+  double s0 = 0.0, s1 = 0.0;
+  int64_t t = threadIdx.x;
+  for (; t + RT < n; t += 2 * RT) { s0 = fma(v[t], w[t], s0); s1 = fma(v[t + RT], w[t + RT], s1); }
+  if (t < n) s0 = fma(v[t], w[t], s0);
+  const double s = block_sum(s0 + s1);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
 // w -= sum_i h[i] V[i]
@@ -98,8 +88,8 @@ inline unsigned grid_for(int64_t n) {
 
 cudaError_t launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t n,
                             double* d_part, double* d_out, cudaStream_t st) {
-  multidot_partial<<<RB, RT, 0, st>>>(V, ldv, nv, w, n, d_part);
-  multidot_final<<<1, 128, 0, st>>>(d_part, RB, nv, d_out);
+  // one block per vector: out[i] = V[i] . w, one deterministic block reduction each
+  multidot_rows<<<nv, RT, 0, st>>>(V, ldv, w, n, d_out);
   return cudaGetLastError();
 }
 

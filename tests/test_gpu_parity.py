@@ -301,3 +301,31 @@ def test_degenerate_cases(g, variant):
     qr = sv.solve_qr(S)
     res = np.linalg.norm(s.matvec(W).cpu().numpy() - S.F)
     assert abs(res - qr.res_ls) <= LS_TOL.get("multiscale2d", 1e-8) * np.linalg.norm(S.F)
+
+
+@pytest.mark.parametrize("name,solver,kind", [("multiscale2d", "gmres", "sas"), ("poisson3d", "cg", "as"),
+                                              ("heat3d", "gmres", "ras"), ("piecewise2d", "cg", "as")])
+def test_inner_precision_modes_reach_the_same_solution(g, name, solver, kind):
+    """Double-float inner iterations with float64 residuals (mode 1) and pure
+    float64 (mode 0) both reach rtol on the float64 normal equations and give
+    the same u_hat to the solve tolerance."""
+    p = ri.config(name, small=True)
+    s = g.RannDD(p)
+    s.assemble()
+    F = s.rhs()
+    s.pca(p.pca_mode, p.pca_thr)
+    s.setup_precond(kind)
+    X = torch.tensor(ri.test_points(p, 15 if p.dim == 2 else 7), device="cuda")
+    out = []
+    for mode in (0, 1):
+        s.set_inner_precision(mode)
+        if solver == "cg":
+            W, st = s.solve_cg_as(F, 1e-10, 5000)
+            assert st["rel_res_true"] <= 1e-10
+        else:
+            W, st = s.solve_gmres_ras(F, 1e-10, 50, 5000)
+            assert st["rel_res_prec"] <= 1e-10
+        out.append((s.eval(W, X).cpu().numpy(), st))
+    (u0, s0), (u1, s1) = out
+    assert np.linalg.norm(u1 - u0) <= SOLVE_TOL[name] * np.linalg.norm(u0)
+    assert s1["iters"] <= 2 * s0["iters"] + 10
