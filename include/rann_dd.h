@@ -176,15 +176,18 @@ rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_dev, double* 
 rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* F_dev, double* W_dev,
                                     double rtol, int restart, int maxit, rann_dd_stats* stats);
 
-/* Arithmetic of the Krylov iterations (not of the residuals that decide
- * restarts and convergence, which are always float64): mode 1 (default)
- * applies H^T H and M^{-1} with the reduced blocks and the factors stored as
- * double-float pairs (float32 hi + lo, about 48 significant bits) -- on GB300
- * float32 runs at 70x the float64 rate, so these memory-bound products then
- * stream at HBM speed; the float64 residual at every restart makes the solve
- * an iterative refinement that converges to the float64 solution.  Mode 0
- * uses float64 throughout.  Takes effect at the next solve. */
-rann_status rann_dd_set_inner_precision(rann_dd_handle* h, int mode);
+/* Precision policy.  Mode 1 (default): the work that only shapes the
+ * preconditioner or the Krylov iterates -- the neighbour Gram blocks of A_i,
+ * the Cholesky trailing updates, L_i^{-1}, and every operator and
+ * preconditioner application inside the Krylov iterations -- runs in
+ * double-float (float32 hi + lo pairs, about 48 significant bits; GB300
+ * executes float32 at 70x its float64 rate), while the PCA, the reduced
+ * blocks B_j and every residual that decides a restart or convergence stay
+ * float64, so the solve is an iterative refinement converging to the float64
+ * solution.  Mode 0: float64 throughout (needed where the preconditioner must
+ * be exact to float64 rounding, e.g. the unreduced system with PCA off).
+ * Affects the next setup_precond and solve. */
+rann_status rann_dd_set_precision(rann_dd_handle* h, int mode);
 
 /* u_hat(x) = L(x) sum_j omega_j(x) (V_{p_j}^T Phi_j(x)) . W_j + G(x)
  * (Eq. (netdd), (pca_net)) at n points x_dev [n][dim] (inside [0,1]^dim)

@@ -88,7 +88,7 @@ SIGNATURES = {
     "rann_dd_solve_cg_as": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
     "rann_dd_solve_gmres_ras": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(Stats)]),
     "rann_dd_eval": (_I, [_P, _P, _P, _L, _P]),
-    "rann_dd_set_inner_precision": (_I, [_P, _I]),
+    "rann_dd_set_precision": (_I, [_P, _I]),
     "rann_dd_matvec": (_I, [_P, _P, _P]),
     "rann_dd_matvec_t": (_I, [_P, _P, _P]),
     "rann_dd_normal_matvec": (_I, [_P, _P, _P]),
@@ -275,9 +275,10 @@ class RannDD:
         _check(s, "rann_dd_solve_gmres_ras", allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return W, st.as_dict() | {"status": STATUS[s]}
 
-    def set_inner_precision(self, mode: int):
-        """1: Krylov iterations in double-float (default); 0: float64."""
-        _check(self._lib.rann_dd_set_inner_precision(self._h, mode), "rann_dd_set_inner_precision")
+    def set_precision(self, mode: int):
+        """1 (default): double-float preconditioner set-up and Krylov iterations with
+        float64 residuals; 0: float64 throughout.  Affects the next setup/solve."""
+        _check(self._lib.rann_dd_set_precision(self._h, mode), "rann_dd_set_precision")
 
     def eval(self, W, x, out=None):
         n = x.shape[0]

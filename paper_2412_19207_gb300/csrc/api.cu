@@ -22,8 +22,8 @@ cudaError_t launch_matvec_HT2(const ProbDev& P, const SubDev* d_sub, int J, cons
                               int nrtiles, const int* d_tile0, const double* d_B, const double* d_y,
                               double* d_part, double* d_z, int maxP, cudaStream_t st);
 cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, int* d_fail,
-                             const double* d_dmax, cudaStream_t st);
-cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st);
+                             const double* d_dmax, int df, cudaStream_t st);
+cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, int df, cudaStream_t st);
 cudaError_t launch_split(const double* d_x, float2* d_x2, int64_t n, cudaStream_t st);
 cudaError_t launch_rowdot_df(const SubDev* d_sub, const int* d_rtiles, int nrtiles, const float2* d_B2,
                              const float2* d_x2, float2* d_yp, cudaStream_t st);
@@ -160,7 +160,7 @@ struct rann_dd_handle {
   float2* d_B2 = nullptr;         // reduced blocks as double-float pairs (inner Krylov operator)
   float2* d_x2 = nullptr;         // DoF
   float2* d_y2 = nullptr;         // N
-  int inner_df = 1;               // inner Krylov iterations in double-float
+  int inner_df = 1;               // precision mode: 1 = double-float preconditioner set-up and inner iterations
   // precond
   int prec_kind = -1;
   int n_shifted = 0;
@@ -733,7 +733,15 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   for (size_t t = 0; t < pairs.size(); ++t) {
     const SubDev &a = S[pairs[t].first], &b = S[pairs[t].second];
     GemmTask g{};
-    g.A = h->d_B + a.boff; g.B = h->d_B + b.boff;
+    // mode 1: the double-float copies of the blocks (same offsets) -- the Gram blocks of A_i only
+    // shape the preconditioner
+    if (h->inner_df) {
+      g.A = reinterpret_cast<const double*>(h->d_B2 + a.boff);
+      g.B = reinterpret_cast<const double*>(h->d_B2 + b.boff);
+    } else {
+      g.A = h->d_B + a.boff;
+      g.B = h->d_B + b.boff;
+    }
     g.C = h->d_pairbuf + pair_off[(size_t)pairs[t].first * J + pairs[t].second];
     g.ia = d_ridx + ridx_ranges[t].first;
     g.ib = d_ridx + ridx_ranges[t].second;
@@ -743,7 +751,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   }
   GemmTask* d_tasks;
   CK(dupload(h, &d_tasks, tasks));
-  KLA(h, K_PAIRGRAM, 1, 0, h->pair_flops, launch_gemm_tn(d_tasks, (int)tasks.size(), h->st));
+  if (h->inner_df) KLA(h, K_PAIRGRAM, 1, 0, h->pair_flops, launch_gemm_tn_df(d_tasks, (int)tasks.size(), h->st));
+  else KLA(h, K_PAIRGRAM, 1, 0, h->pair_flops, launch_gemm_tn(d_tasks, (int)tasks.size(), h->st));
   // local matrices A_i: table of block sources
   std::vector<CholMat> mats(J);
   std::vector<int64_t> tab;      // per (i, a, b): pair offset, or -1; sign bit 1<<62 marks transpose
@@ -809,7 +818,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     for (auto& c : am) { amax = std::max(amax, c.n); chol_flops += (double)c.n * c.n * c.n / 3.0; }
     CK(cudaMemsetAsync(d_fail, 0, sizeof(int) * J, h->st));
     for (int c0 = 0; c0 < amax; c0 += 32)
-      KLA(h, K_CHOL, (amax - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0, launch_chol_step(d_am, (int)am.size(), amax, c0, d_fail, d_adm, h->st));
+      KLA(h, K_CHOL, (amax - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
+          launch_chol_step(d_am, (int)am.size(), amax, c0, d_fail, d_adm, h->inner_df, h->st));
     std::vector<int> f(am.size());
     CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * am.size(), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -841,7 +851,7 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   }
   for (int i = 0; i < J; ++i) h->n_shifted += shifted[i];
   // X_i = L_i^{-1} for the parallel apply
-  KLA(h, K_TRTRI, 2, 0, h->sum_n3 / 3.0, launch_trtri(h->d_mats, J, h->maxn, h->st));
+  KLA(h, K_TRTRI, 2, 0, h->sum_n3 / 3.0, launch_trtri(h->d_mats, J, h->maxn, h->inner_df, h->st));
   KLA(h, K_SPLIT, 1, 6.0 * h->sum_n2, 0, launch_split_lower(h->d_mats, J, h->maxn, h->st));
   std::vector<int64_t> p_off(J + 1, 0);
   for (int i = 0; i < J; ++i) p_off[i + 1] = p_off[i] + (int64_t)((mats[i].n + 255) / 256) * mats[i].n;
@@ -1148,9 +1158,9 @@ extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* 
   return st;
 }
 
-extern "C" rann_status rann_dd_set_inner_precision(rann_dd_handle* h, int mode) {
+extern "C" rann_status rann_dd_set_precision(rann_dd_handle* h, int mode) {
   REQUIRE(h, RANN_EINVAL, "null handle");
-  REQUIRE(mode == 0 || mode == 1, RANN_EINVAL, "inner precision mode must be 0 (float64) or 1 (double-float)");
+  REQUIRE(mode == 0 || mode == 1, RANN_EINVAL, "precision mode must be 0 (float64) or 1 (double-float)");
   h->inner_df = mode;
   return RANN_OK;
 }

@@ -87,8 +87,147 @@ __global__ void trsm_panel_kernel(const CholMat* __restrict__ mats, int c0) {
   for (int j = 0; j < NB; ++j) row[j] = x[j];
 }
 
-// A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles.
+// A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles.  The rank-32
+// product is accumulated in double-float (the panel is split on load) and
+// subtracted in float64: the trailing updates carry most of the Cholesky
+// flops, and their ~1e-14 relative accuracy only affects the preconditioner.
 __global__ void __launch_bounds__(256) syrk_update_kernel(const CholMat* __restrict__ mats, int c0) {
+  const CholMat M = mats[blockIdx.y];
+  const int s0 = c0 + NB;
+  if (M.n <= s0) return;
+  const int T = (M.n - s0 + 63) / 64;
+  const int t = blockIdx.x;
+  if (t >= T * (T + 1) / 2) return;
+  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while (ti * (ti + 1) / 2 > t) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  const int tj = t - ti * (ti + 1) / 2;
+  const int r0 = s0 + ti * 64, q0 = s0 + tj * 64;
+  __shared__ float2 sa[NB][65];
+  __shared__ float2 sb[NB][65];
+  for (int e = threadIdx.x; e < 64 * NB; e += 256) {
+    int rr = e / NB, k = e % NB;
+    int r = r0 + rr, q = q0 + rr;
+    sa[k][rr] = (r < M.n) ? df_split(M.A[(int64_t)r * M.ld + c0 + k]) : make_float2(0.f, 0.f);
+    sb[k][rr] = (q < M.n) ? df_split(M.A[(int64_t)q * M.ld + c0 + k]) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float ah[4][4], al[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { ah[p][q] = 0.f; al[p][q] = 0.f; }
+#pragma unroll 4
+  for (int k = 0; k < NB; ++k) {
+    float2 a[4], b[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) { a[p] = sa[k][ty + 16 * p]; b[p] = sb[k][tx + 16 * p]; }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) df_mac(ah[p][q], al[p][q], a[p], b[q]);
+    if ((k & 15) == 15)
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) df_renorm(ah[p][q], al[p][q]);
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int r = r0 + ty + 16 * p, c = q0 + tx + 16 * q;
+      if (r < M.n && c <= r) M.A[(int64_t)r * M.ld + c] -= df_to_double(ah[p][q], al[p][q]);
+    }
+}
+
+// ---- triangular inverse X = L^{-1} ----
+// Diagonal blocks: X_bb = L_bb^{-1}, one thread per column of the block.
+__global__ void trtri_diag_kernel(const CholMat* __restrict__ mats) {
+  const CholMat M = mats[blockIdx.y];
+  const int nblk = (M.n + NB - 1) / NB;
+  if ((int)blockIdx.x >= nblk) return;
+  const int b0 = blockIdx.x * NB, nb = min(NB, M.n - b0);
+  __shared__ double l[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int r = e / NB, c = e % NB;
+    l[r][c] = (r < nb && c <= r) ? M.A[(int64_t)(b0 + r) * M.ld + b0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c >= nb) return;
+  double x[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) x[r] = 0.0;
+  for (int r = c; r < nb; ++r) {
+    double s = (r == c) ? 1.0 : 0.0;
+    for (int k = c; k < r; ++k) s = fma(-l[r][k], x[k], s);
+    x[r] = s / l[r][r];
+  }
+  for (int r = c; r < nb; ++r) M.X[(int64_t)(b0 + r) * M.ld + b0 + c] = x[r];
+}
+
+// Block column j of X: for i > j, X_ij = -X_ii sum_{j <= k < i} L_ik X_kj,
+// the products accumulated in double-float (operands split on load), X_ij
+// stored in float64.
+__global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restrict__ mats) {
+  const CholMat M = mats[blockIdx.y];
+  const int nblk = (M.n + NB - 1) / NB;
+  const int j = blockIdx.x;
+  if (j >= nblk) return;
+  __shared__ float2 sl[NB][NB + 1];
+  __shared__ float2 sx[NB][NB + 1];
+  const int t = threadIdx.x, r = t % NB, cg = (t / NB) * 4;   // row r, columns cg..cg+3
+  const int cj = j * NB;
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int i = j + 1; i < nblk; ++i) {
+    const int ri = i * NB;
+    float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = j; k < i; ++k) {
+      const int ck = k * NB;
+      for (int e = t; e < NB * NB; e += 256) {
+        int a = e / NB, b = e % NB;
+        sl[a][b] = (ri + a < M.n) ? df_split(M.A[(int64_t)(ri + a) * M.ld + ck + b]) : zero;   // L_ik
+        // X_kj (the diagonal block X_jj is lower triangular: its upper part is never written)
+        sx[a][b] = (ck + a < M.n && cj + b < M.n && (k > j || b <= a))
+                       ? df_split(M.X[(int64_t)(ck + a) * M.ld + cj + b]) : zero;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int q = 0; q < NB; ++q) {
+        const float2 lv = sl[r][q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) df_mac(ah[u], al[u], lv, sx[q][cg + u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) df_renorm(ah[u], al[u]);
+      __syncthreads();
+    }
+    // X_ij = -X_ii acc
+    for (int e = t; e < NB * NB; e += 256) {
+      int a = e / NB, b = e % NB;
+      sl[a][b] = (ri + a < M.n && b <= a) ? df_split(M.X[(int64_t)(ri + a) * M.ld + ri + b]) : zero;   // X_ii
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sx[r][cg + u] = make_float2(ah[u], al[u]);
+    __syncthreads();
+    float oh[4] = {0.f, 0.f, 0.f, 0.f}, ol[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q <= r; ++q) {
+      const float2 lv = sl[r][q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) df_mac(oh[u], ol[u], lv, sx[q][cg + u]);
+    }
+    if (ri + r < M.n)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cj + cg + u < M.n) M.X[(int64_t)(ri + r) * M.ld + cj + cg + u] = -df_to_double(oh[u], ol[u]);
+    __syncthreads();   // X_ij visible to the next i (same block)
+  }
+}
+
+// Float64 variant of the trailing update (precision mode 0).
+__global__ void __launch_bounds__(256) syrk_update_f64_kernel(const CholMat* __restrict__ mats, int c0) {
   const CholMat M = mats[blockIdx.y];
   const int s0 = c0 + NB;
   if (M.n <= s0) return;
@@ -130,41 +269,15 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(const CholMat* __restr
     }
 }
 
-// ---- triangular inverse X = L^{-1} ----
-// Diagonal blocks: X_bb = L_bb^{-1}, one thread per column of the block.
-__global__ void trtri_diag_kernel(const CholMat* __restrict__ mats) {
-  const CholMat M = mats[blockIdx.y];
-  const int nblk = (M.n + NB - 1) / NB;
-  if ((int)blockIdx.x >= nblk) return;
-  const int b0 = blockIdx.x * NB, nb = min(NB, M.n - b0);
-  __shared__ double l[NB][NB + 1];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e % NB;
-    l[r][c] = (r < nb && c <= r) ? M.A[(int64_t)(b0 + r) * M.ld + b0 + c] : 0.0;
-  }
-  __syncthreads();
-  const int c = threadIdx.x;
-  if (c >= nb) return;
-  double x[NB];
-#pragma unroll
-  for (int r = 0; r < NB; ++r) x[r] = 0.0;
-  for (int r = c; r < nb; ++r) {
-    double s = (r == c) ? 1.0 : 0.0;
-    for (int k = c; k < r; ++k) s = fma(-l[r][k], x[k], s);
-    x[r] = s / l[r][r];
-  }
-  for (int r = c; r < nb; ++r) M.X[(int64_t)(b0 + r) * M.ld + b0 + c] = x[r];
-}
-
-// Block column j of X: for i > j, X_ij = -X_ii sum_{j <= k < i} L_ik X_kj.
-__global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restrict__ mats) {
+// Float64 variant of the block-column triangular inverse (precision mode 0).
+__global__ void __launch_bounds__(256) trtri_col_f64_kernel(const CholMat* __restrict__ mats) {
   const CholMat M = mats[blockIdx.y];
   const int nblk = (M.n + NB - 1) / NB;
   const int j = blockIdx.x;
   if (j >= nblk) return;
   __shared__ double sl[NB][NB + 1];
   __shared__ double sx[NB][NB + 1];
-  const int t = threadIdx.x, r = t % NB, cg = (t / NB) * 4;   // row r, columns cg..cg+3
+  const int t = threadIdx.x, r = t % NB, cg = (t / NB) * 4;
   const int cj = j * NB;
   for (int i = j + 1; i < nblk; ++i) {
     const int ri = i * NB;
@@ -173,8 +286,7 @@ __global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restric
       const int ck = k * NB;
       for (int e = t; e < NB * NB; e += 256) {
         int a = e / NB, b = e % NB;
-        sl[a][b] = (ri + a < M.n) ? M.A[(int64_t)(ri + a) * M.ld + ck + b] : 0.0;         // L_ik
-        // X_kj (the diagonal block X_jj is lower triangular: its upper part is never written)
+        sl[a][b] = (ri + a < M.n) ? M.A[(int64_t)(ri + a) * M.ld + ck + b] : 0.0;
         sx[a][b] = (ck + a < M.n && cj + b < M.n && (k > j || b <= a)) ? M.X[(int64_t)(ck + a) * M.ld + cj + b] : 0.0;
       }
       __syncthreads();
@@ -186,10 +298,9 @@ __global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restric
       }
       __syncthreads();
     }
-    // X_ij = -X_ii acc
     for (int e = t; e < NB * NB; e += 256) {
       int a = e / NB, b = e % NB;
-      sl[a][b] = (ri + a < M.n && b <= a) ? M.X[(int64_t)(ri + a) * M.ld + ri + b] : 0.0;   // X_ii (lower)
+      sl[a][b] = (ri + a < M.n && b <= a) ? M.X[(int64_t)(ri + a) * M.ld + ri + b] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) sx[r][cg + u] = acc[u];
@@ -204,7 +315,7 @@ __global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restric
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (cj + cg + u < M.n) M.X[(int64_t)(ri + r) * M.ld + cj + cg + u] = -out[u];
-    __syncthreads();   // X_ij visible to the next i (same block)
+    __syncthreads();
   }
 }
 
@@ -504,22 +615,24 @@ cudaError_t launch_add_diag(const CholMat* d_mats, const int* d_which, int nwhic
 }
 
 cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, int* d_fail,
-                             const double* d_dmax, cudaStream_t st) {
+                             const double* d_dmax, int df, cudaStream_t st) {
   potrf_diag_kernel<<<nmat, 256, 0, st>>>(d_mats, c0, d_fail, d_dmax);
   int rest = maxn - c0 - NB;
   if (rest > 0) {
     trsm_panel_kernel<<<dim3((rest + 127) / 128, nmat), 128, 0, st>>>(d_mats, c0);
     int T = (rest + 63) / 64;
-    syrk_update_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
+    if (df) syrk_update_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
+    else syrk_update_f64_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st) {
+cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, int df, cudaStream_t st) {
   if (nmat == 0) return cudaSuccess;
   int nblk = (maxn + NB - 1) / NB;
   trtri_diag_kernel<<<dim3(nblk, nmat), NB, 0, st>>>(d_mats);
-  trtri_col_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
+  if (df) trtri_col_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
+  else trtri_col_f64_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
   return cudaGetLastError();
 }
 

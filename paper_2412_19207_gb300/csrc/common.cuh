@@ -76,6 +76,7 @@ struct GemmTask {            // one output tile of one batched product
 };
 cudaError_t launch_gemm_tn(const GemmTask* d_tasks, int ntasks, cudaStream_t st);
 cudaError_t launch_gemm_nn(const GemmTask* d_tasks, int ntasks, cudaStream_t st);
+cudaError_t launch_gemm_tn_df(const GemmTask* d_tasks, int ntasks, cudaStream_t st);
 cudaError_t launch_symmetrize(double* const* d_mats, const int* d_n, const int* d_ld, int nmat,
                               int maxn, cudaStream_t st);
 

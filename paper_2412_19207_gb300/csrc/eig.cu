@@ -8,7 +8,9 @@
 //      once per lower element and mirrored, so the matrix stays exactly
 //      symmetric.
 //   2. Eigenvalues of T by implicit QL with Wilkinson shifts (the tql1 scheme
-//      of Bowdler, Martin, Reinsch & Wilkinson, 1968), no vectors.
+//      of Bowdler, Martin, Reinsch & Wilkinson, 1968), no vectors; each plane
+//      rotation takes one reciprocal square root (the chase is one thread's
+//      dependent chain, so its latency per step bounds this phase).
 //   3. Eigenvalues sorted descending; the rank rule of Sec. 4 gives p_j.
 //   4. Eigenvectors of T for the p_j largest eigenvalues by inverse iteration
 //      (tridiagonal LU with partial pivoting, two solves; Wilkinson, The
@@ -144,10 +146,15 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
         bool early = false;
         for (int i = mm - 1; i >= l; --i) {
           double f = s * w[i], b = c * w[i];
-          r = hypot(f, g);
+          // plane rotation from one reciprocal square root: r = |(f, g)|,
+          // s = f / r, c = g / r (|f|, |g| <= |T|, so f^2 + g^2 cannot overflow;
+          // an underflow to zero is the r == 0 deflation)
+          const double t2 = fma(f, f, g * g);
+          if (t2 == 0.0) { w[i + 1] = 0.0; v[i + 1] -= p; w[mm] = 0.0; early = true; break; }
+          const double ri = rsqrt(t2);
+          r = t2 * ri;
           w[i + 1] = r;
-          if (r == 0.0) { v[i + 1] -= p; w[mm] = 0.0; early = true; break; }
-          s = f / r; c = g / r;
+          s = f * ri; c = g * ri;
           g = v[i + 1] - p;
           r = (v[i] - g) * s + 2.0 * c * b;
           p = s * r;
