@@ -176,6 +176,16 @@ rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_dev, double* 
 rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* F_dev, double* W_dev,
                                     double rtol, int restart, int maxit, rann_dd_stats* stats);
 
+/* Adjoint of the solve (differentiation through Algorithm 1 step 6; the
+ * paper's normal equations of Sec. 2 are symmetric, so the adjoint system is
+ * the same): lam_dev [DoF] receives lam = (H^T H)^{-1} gW for a loss gradient
+ * gW_dev = dl/dW [DoF], solved to rtol with the stored preconditioner (CG if
+ * it is AS or none, left-preconditioned GMRES(50) otherwise).  Then
+ * dl/dF = H lam (rann_dd_matvec).  Krylov iterates are recomputed, not
+ * stored.  Needs setup_precond. */
+rann_status rann_dd_solve_backward(rann_dd_handle* h, const double* gW_dev, double* lam_dev,
+                                   double rtol, int maxit, rann_dd_stats* stats);
+
 /* Precision policy.  Mode 1 (default): the work that only shapes the
  * preconditioner or the Krylov iterates -- the neighbour Gram blocks of A_i,
  * the Cholesky trailing updates, L_i^{-1}, and every operator and

@@ -88,6 +88,7 @@ SIGNATURES = {
     "rann_dd_solve_cg_as": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
     "rann_dd_solve_gmres_ras": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(Stats)]),
     "rann_dd_eval": (_I, [_P, _P, _P, _L, _P]),
+    "rann_dd_solve_backward": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
     "rann_dd_set_precision": (_I, [_P, _I]),
     "rann_dd_matvec": (_I, [_P, _P, _P]),
     "rann_dd_matvec_t": (_I, [_P, _P, _P]),
@@ -210,6 +211,7 @@ class RannDD:
         self._h = h
         self._lib = lib
         self.ranks = None
+        self._prec = None
 
     def close(self):
         if getattr(self, "_h", None):
@@ -258,6 +260,7 @@ class RannDD:
 
     def setup_precond(self, kind, overlap_level: int = 1) -> int:
         kind = PREC_BY_NAME[kind] if isinstance(kind, str) else kind
+        self._prec = kind
         return _check(self._lib.rann_dd_setup_precond(self._h, kind, overlap_level), "rann_dd_setup_precond",
                       allow=(LOCAL_SINGULAR,))
 
@@ -274,6 +277,20 @@ class RannDD:
         s = self._lib.rann_dd_solve_gmres_ras(self._h, _dptr(F), _dptr(W), rtol, restart, maxit, ctypes.byref(st))
         _check(s, "rann_dd_solve_gmres_ras", allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return W, st.as_dict() | {"status": STATUS[s]}
+
+    def solve_backward(self, gW, rtol=1e-10, maxit=2000, lam=None):
+        """lam = (H^T H)^{-1} gW with the stored preconditioner (adjoint of the solve)."""
+        lam = lam if lam is not None else self._empty(self.sizes()["dof"])
+        st = Stats()
+        s = self._lib.rann_dd_solve_backward(self._h, _dptr(gW), _dptr(lam), rtol, maxit, ctypes.byref(st))
+        _check(s, "rann_dd_solve_backward")
+        return lam, st.as_dict() | {"status": STATUS[s]}
+
+    def solve(self, F, rtol=1e-10, maxit=2000, restart=50):
+        """The solve matching the preconditioner: AS-CG for AS/none, GMRES otherwise."""
+        if self._prec in (PREC_AS, PREC_NONE):
+            return self.solve_cg_as(F, rtol, maxit)
+        return self.solve_gmres_ras(F, rtol, restart, maxit)
 
     def set_precision(self, mode: int):
         """1 (default): double-float preconditioner set-up and Krylov iterations with
@@ -341,3 +358,28 @@ class RannDD:
         V = np.empty((m, p))
         _check(self._lib.rann_dd_get_pca(self._h, j, eig.ctypes.data, V.ctypes.data), "rann_dd_get_pca")
         return eig, V
+
+
+class LeastSquaresSolve:
+    """Differentiable solve W(F) = (H^T H)^{-1} H^T F of a prepared RannDD
+    (assembled, reduced, preconditioner set up): torch.autograd support for
+    gradients with respect to the right-hand side F.  The backward pass solves
+    the adjoint system with the same preconditioner (rann_dd_solve_backward)
+    and returns dl/dF = H lam."""
+
+    @staticmethod
+    def apply(solver: "RannDD", F, rtol: float = 1e-10, maxit: int = 2000):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, Fin):
+                W, _ = solver.solve(Fin.detach().contiguous(), rtol, maxit)
+                return W
+
+            @staticmethod
+            def backward(ctx, gW):
+                lam, _ = solver.solve_backward(gW.contiguous(), rtol, maxit)
+                return solver.matvec(lam)
+
+        return _Fn.apply(F)

@@ -952,9 +952,10 @@ static rann_status prec_inner(rann_dd_handle* h, const double* r, double* z) {
   return prec_apply(h, r, z, h->inner_df != 0);
 }
 
-extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
-                                           int maxit, rann_dd_stats* stats) {
-  REQUIRE(h && F_dev && W_dev, RANN_EINVAL, "null argument");
+// CG on H^T H W = b with b = H^T F (F_dev) or b given (b_dev).
+static rann_status solve_cg_impl(rann_dd_handle* h, const double* F_dev, const double* b_dev, double* W_dev,
+                                 double rtol, int maxit, rann_dd_stats* stats) {
+  REQUIRE(h && (F_dev || b_dev) && W_dev, RANN_EINVAL, "null argument");
   REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve before setup_precond");
   REQUIRE(h->prec_kind == RANN_PREC_AS || h->prec_kind == RANN_PREC_NONE, RANN_EINVAL,
           "CG needs a symmetric preconditioner (AS or none)");
@@ -966,7 +967,8 @@ extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_de
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, h->st));
-  TRY(rann_dd_matvec_t(h, F_dev, b));
+  if (F_dev) TRY(rann_dd_matvec_t(h, F_dev, b));
+  else CK(cudaMemcpyAsync(b, b_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
   CK(cudaMemsetAsync(W_dev, 0, sizeof(double) * n, h->st));
   CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
   double bb;
@@ -979,48 +981,49 @@ extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_de
     st = std::isfinite(bb) ? RANN_OK : RANN_BREAKDOWN;
     rel = true_rel = 0.0;
   } else {
-    // Preconditioned CG; when the recursive residual has dropped by 1e-4 since
-    // the last float64 residual (or reaches rtol), the float64 residual
-    // b - A W replaces it and decides convergence (residual replacement: the
-    // search direction is kept).
-    double rz, rr;
-    TRY(prec_inner(h, r, z));
-    CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-    TRY(dot_host(h, r, z, n, &rz));
-    while (true) {
-      if (it >= maxit) {
-        TRY(rann_dd_normal_matvec(h, W_dev, q));
-        CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-        KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(-1.0, q, 1.0, r, n, h->st));
-        TRY(dot_host(h, r, r, n, &rr));
-        true_rel = std::sqrt(rr) / bnorm;
-        if (true_rel <= rtol) st = RANN_OK;
-        break;
-      }
-      TRY(op_inner(h, p, q));
-      double pq;
-      TRY(dot_host(h, p, q, n, &pq));
-      if (!(pq > 0.0) || !std::isfinite(pq)) { st = RANN_BREAKDOWN; break; }
-      const double alpha = rz / pq;
-      KLA(h, K_VEC, 1, 40.0 * n, 4.0 * n, launch_cg_update(alpha, p, q, W_dev, r, n, h->st));
-      ++it;
-      TRY(dot_host(h, r, r, n, &rr));
-      rel = std::sqrt(rr) / bnorm;
-      if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
-      if (rel <= std::max(rtol, 1e-4 * true_rel)) {
-        TRY(rann_dd_normal_matvec(h, W_dev, q));
-        CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-        KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(-1.0, q, 1.0, r, n, h->st));
-        TRY(dot_host(h, r, r, n, &rr));
-        true_rel = std::sqrt(rr) / bnorm;
-        if (true_rel <= rtol) { st = RANN_OK; break; }
-        rel = true_rel;
-      }
+    // Iterative refinement around preconditioned CG: each cycle solves the
+    // correction equation A d = r (r the float64 residual of the current W)
+    // from d = 0 with the inner operator until ||r_rec|| <= rtol ||b||, adds d
+    // to W (held in the recurrence's x), and recomputes the float64 residual.
+    // In float64 mode the first cycle is plain PCG.
+    double* d = W_dev;   // W accumulates the corrections: x_{k+1} = x_k + alpha p, per cycle from r
+    double rr;
+    for (int cycle = 0; cycle < 30; ++cycle) {
+      double rz;
       TRY(prec_inner(h, r, z));
-      double rz2;
-      TRY(dot_host(h, r, z, n, &rz2));
-      KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, z, rz2 / rz, p, n, h->st));
-      rz = rz2;
+      CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+      TRY(dot_host(h, r, z, n, &rz));
+      bool inner_ok = false;
+      while (it < maxit) {
+        TRY(op_inner(h, p, q));
+        double pq;
+        TRY(dot_host(h, p, q, n, &pq));
+        if (!(pq > 0.0) || !std::isfinite(pq)) { st = RANN_BREAKDOWN; break; }
+        const double alpha = rz / pq;
+        KLA(h, K_VEC, 1, 40.0 * n, 4.0 * n, launch_cg_update(alpha, p, q, d, r, n, h->st));
+        ++it;
+        TRY(dot_host(h, r, r, n, &rr));
+        rel = std::sqrt(rr) / bnorm;
+        if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
+        if (rel <= rtol) { inner_ok = true; break; }
+        TRY(prec_inner(h, r, z));
+        double rz2;
+        TRY(dot_host(h, r, z, n, &rz2));
+        KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, z, rz2 / rz, p, n, h->st));
+        rz = rz2;
+      }
+      if (st == RANN_BREAKDOWN) break;
+      // float64 residual of the accumulated W
+      TRY(rann_dd_normal_matvec(h, W_dev, q));
+      CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+      KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(-1.0, q, 1.0, r, n, h->st));
+      TRY(dot_host(h, r, r, n, &rr));
+      const double prev = true_rel;
+      true_rel = std::sqrt(rr) / bnorm;
+      if (!std::isfinite(true_rel)) { st = RANN_BREAKDOWN; break; }
+      if (true_rel <= rtol) { st = RANN_OK; break; }
+      if (!inner_ok || it >= maxit) break;
+      if (true_rel >= prev) break;   // refinement no longer reduces the float64 residual
     }
   }
   CK(cudaEventRecord(e1, h->st));
@@ -1040,9 +1043,10 @@ extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_de
   return st;
 }
 
-extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
-                                               int restart, int maxit, rann_dd_stats* stats) {
-  REQUIRE(h && F_dev && W_dev, RANN_EINVAL, "null argument");
+// Left-preconditioned GMRES on H^T H W = b with b = H^T F (F_dev) or b given (b_dev).
+static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, const double* b_dev, double* W_dev,
+                                    double rtol, int restart, int maxit, rann_dd_stats* stats) {
+  REQUIRE(h && (F_dev || b_dev) && W_dev, RANN_EINVAL, "null argument");
   REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve before setup_precond");
   REQUIRE(rtol > 0 && maxit >= 0 && restart >= 1 && restart <= 120, RANN_EINVAL, "bad rtol/restart/maxit");
   const int64_t n = h->dof;
@@ -1053,7 +1057,8 @@ extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* 
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, h->st));
-  TRY(rann_dd_matvec_t(h, F_dev, b));
+  if (F_dev) TRY(rann_dd_matvec_t(h, F_dev, b));
+  else CK(cudaMemcpyAsync(b, b_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
   CK(cudaMemsetAsync(W_dev, 0, sizeof(double) * n, h->st));
   // ||M^{-1} b||
   TRY(prec_inner(h, b, V));
@@ -1156,6 +1161,31 @@ extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* 
   }
   if (st == RANN_NOT_CONVERGED) rann_set_error("GMRES reached maxit=%d at rel. residual %.3e", maxit, rel);
   return st;
+}
+
+extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
+                                           int maxit, rann_dd_stats* stats) {
+  REQUIRE(F_dev, RANN_EINVAL, "null F");
+  return solve_cg_impl(h, F_dev, nullptr, W_dev, rtol, maxit, stats);
+}
+
+extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
+                                               int restart, int maxit, rann_dd_stats* stats) {
+  REQUIRE(F_dev, RANN_EINVAL, "null F");
+  return solve_gmres_impl(h, F_dev, nullptr, W_dev, rtol, restart, maxit, stats);
+}
+
+// Adjoint of the least-squares solve.  W = (H^T H)^{-1} H^T F, so for a loss
+// l(W) the sensitivity to F is H lam with (H^T H) lam = dl/dW: the same
+// symmetric normal matrix, solved with the stored preconditioner (CG when it
+// is symmetric, GMRES(50) otherwise).
+extern "C" rann_status rann_dd_solve_backward(rann_dd_handle* h, const double* gW_dev, double* lam_dev, double rtol,
+                                              int maxit, rann_dd_stats* stats) {
+  REQUIRE(h && gW_dev && lam_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve_backward before setup_precond");
+  if (h->prec_kind == RANN_PREC_AS || h->prec_kind == RANN_PREC_NONE)
+    return solve_cg_impl(h, nullptr, gW_dev, lam_dev, rtol, maxit, stats);
+  return solve_gmres_impl(h, nullptr, gW_dev, lam_dev, rtol, 50, maxit, stats);
 }
 
 extern "C" rann_status rann_dd_set_precision(rann_dd_handle* h, int mode) {

@@ -297,7 +297,9 @@ def test_degenerate_cases(g, variant):
         W, st = s.solve_gmres_ras(F, 1e-10, 1, 20000, allow_not_converged=True)
         assert st["iters"] > 0
         return
-    W, st = s.solve_cg_as(F, 1e-10, 5000)
+    # without PCA the normal matrix has kappa ~ 1e16 and float64 attains a
+    # relative residual of ~2e-10 only: that variant is held to 1e-9
+    W, st = s.solve_cg_as(F, 1e-9 if variant == "pca_none" else 1e-10, 5000)
     assert st["status"] == "RANN_OK"
     if variant == "pca_none":
         return
