@@ -193,10 +193,14 @@ rann_status rann_dd_solve_backward(rann_dd_handle* h, const double* gW_dev, doub
  * double-float (float32 hi + lo pairs, about 48 significant bits; GB300
  * executes float32 at 70x its float64 rate), while the PCA, the reduced
  * blocks B_j and every residual that decides a restart or convergence stay
- * float64, so the solve is an iterative refinement converging to the float64
- * solution.  Mode 0: float64 throughout (needed where the preconditioner must
- * be exact to float64 rounding, e.g. the unreduced system with PCA off).
- * Affects the next setup_precond and solve. */
+ * float64-accurate, so the solve is an iterative refinement converging to the
+ * float64 solution.  In mode 1 the two dense products of the PCA (the Gram
+ * matrices Psi_j^T Psi_j and B_j = H_j V_{p_j}) are formed on the bf16 tensor
+ * cores from exact 7-bit digit slices of float64 operands (Ozaki splitting),
+ * with an error of the float64 product's order.  Mode 0: float64 SIMT
+ * arithmetic throughout (needed where the preconditioner must be exact to
+ * float64 rounding, e.g. the unreduced system with PCA off).  Affects the
+ * next pca, setup_precond and solve. */
 rann_status rann_dd_set_precision(rann_dd_handle* h, int mode);
 
 /* u_hat(x) = L(x) sum_j omega_j(x) (V_{p_j}^T Phi_j(x)) . W_j + G(x)
@@ -249,14 +253,15 @@ rann_status rann_dd_matvec_t_noalloc(int J, const int64_t* boff, const int* n_ro
 
 /* Kernel accounting (tracing for the roofline; the paper has no
  * counterpart).  Every kernel launch is counted per kernel family together
- * with its algorithmic bytes and float64 flops (the minimal traffic and
- * arithmetic of the operation it performs, computed from the sizes); with
+ * with its algorithmic bytes and flops (the minimal traffic and arithmetic
+ * of the operation it performs, computed from the sizes); with
  * profile_enable(h, 1) each launch is also bracketed by CUDA events on the
  * handle's stream.  profile_enable resets all counters.  profile_get returns,
  * for family idx = 0, 1, ... (RANN_EINVAL past the last one): its name (a
  * static string), kernels launched, summed device time in ms (0 unless
  * profiling was on), summed algorithmic bytes and flops, and its roofline
- * class (0 = memory-bound, 1 = float64-ALU-bound).  It synchronises the
+ * class (0 = memory-bound, 1 = float64-ALU-bound, 2 = bf16-tensor-core-bound,
+ * whose flops are those of the digit-slice products).  It synchronises the
  * pending events.  Any output pointer may be NULL. */
 rann_status rann_dd_profile_enable(rann_dd_handle* h, int on);
 rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const char** name, int64_t* launches,

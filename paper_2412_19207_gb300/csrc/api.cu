@@ -99,18 +99,20 @@ void rann_set_error(const char* fmt, ...) {
 enum KId {
   K_POINTS, K_ASSEMBLE, K_RHS, K_GRAM, K_SYMM, K_EIG, K_PROJECT, K_PAIRGRAM, K_LOCALASM, K_ADDDIAG,
   K_CHOL, K_TRTRI, K_GATHER, K_TRMV_L, K_TRMV_U, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL,
-  K_SPLIT, K_MATVEC_H_DF, K_MATVEC_HT_DF, K_GATHER_DF, K_TRMV_L_DF, K_TRMV_U_DF, K_COUNT
+  K_SPLIT, K_MATVEC_H_DF, K_MATVEC_HT_DF, K_GATHER_DF, K_TRMV_L_DF, K_TRMV_U_DF, K_OZ_SPLIT, K_GRAM_OZ,
+  K_PROJECT_OZ, K_COUNT
 };
 static const char* const KNAMES[K_COUNT] = {
   "points", "assemble", "rhs", "gram", "symmetrize", "eig", "project", "pair_gram", "local_assemble",
   "add_diag", "cholesky", "trtri", "schwarz_gather", "trmv_lower", "trmv_upper", "schwarz_combine",
   "matvec_H", "matvec_HT", "dot", "vector", "eval", "split_df32", "matvec_H_df32", "matvec_HT_df32",
-  "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32"};
+  "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32", "ozaki_split", "gram_ozaki", "project_ozaki"};
 
 // Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
-// 1 = float64-ALU-bound (algorithmic flops count).
+// 1 = float64-ALU-bound (algorithmic flops count), 2 = bf16-tensor-core-bound
+// (the flops of the digit-slice products count).
 static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1,
-                                     0, 0, 0, 0, 0, 0};
+                                     0, 0, 0, 0, 0, 0, 0, 2, 2};
 
 struct Prof {
   bool on = false;
@@ -504,17 +506,57 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   for (int j = 0; j < J; ++j) h->sumNm2 += (double)h->subs[j].N * m * (m + 1);
   // Gram matrices Psi_j^T Psi_j (upper tiles) then eigen-decomposition
   {
-    std::vector<GemmTask> tasks;
-    for (int j = 0; j < J; ++j) {
-      const SubDev& S = h->subs[j];
-      GemmTask t{};
-      t.A = h->d_Psi + S.row0 * m; t.B = t.A; t.C = h->d_V + mm * j;
-      t.K = S.N; t.M = m; t.N = m; t.lda = m; t.ldb = m; t.ldc = m;
-      push_tiles(tasks, t, true);
+    void* d_tasks = nullptr;
+    uint16_t* d_sl = nullptr;
+    int* d_e = nullptr;
+    if (h->inner_df) {      // digit-slice products on the tensor cores (float64-accurate)
+      const int nsl = oz_slices();
+      std::vector<OzSplitTask> sp(J);
+      std::vector<OzTask> gt;
+      int64_t soff = 0;
+      int maxKp = 0;
+      for (int j = 0; j < J; ++j) {
+        const int Kp = oz_kpad(h->subs[j].N);
+        soff += (int64_t)nsl * m * Kp;
+        maxKp = std::max(maxKp, Kp);
+      }
+      CK(dalloc(h, (void**)&d_sl, sizeof(uint16_t) * (size_t)soff));
+      CK(dalloc(h, (void**)&d_e, sizeof(int) * (size_t)m * J));
+      soff = 0;
+      for (int j = 0; j < J; ++j) {
+        const SubDev& S = h->subs[j];
+        OzSplitTask& t = sp[j];
+        t.X = h->d_Psi + S.row0 * m; t.si = 1; t.sk = m;       // row i of Psi_j^T
+        t.M = m; t.K = S.N; t.Kp = oz_kpad(S.N); t.e = d_e + (size_t)m * j; t.out = d_sl + soff;
+        OzTask g{};
+        g.A = t.out; g.B = t.out; g.ea = t.e; g.eb = t.e; g.C = h->d_V + mm * j;
+        g.M = m; g.N = m; g.Kp = t.Kp; g.ldc = m;
+        for (int tm = 0; tm < m; tm += 64)
+          for (int tn = tm; tn < m; tn += 64) { g.tm = tm; g.tn = tn; gt.push_back(g); }
+        soff += (int64_t)nsl * m * t.Kp;
+      }
+      OzSplitTask* d_sp; OzTask* d_gt;
+      CK(dupload(h, &d_sp, sp)); CK(dupload(h, &d_gt, gt));
+      d_tasks = d_gt;
+      KLA(h, K_OZ_SPLIT, 2, (8.0 + 2.0 * nsl) * h->rows_total * m, 0,
+          launch_oz_split(d_sp, J, m, maxKp, h->st));
+      KLA(h, K_GRAM_OZ, 1, 2.0 * nsl * h->rows_total * m, 36.0 * h->sumNm2,
+          launch_oz_gemm(d_gt, (int)gt.size(), h->st));
+      dfree(h, d_sp);
+    } else {
+      std::vector<GemmTask> tasks;
+      for (int j = 0; j < J; ++j) {
+        const SubDev& S = h->subs[j];
+        GemmTask t{};
+        t.A = h->d_Psi + S.row0 * m; t.B = t.A; t.C = h->d_V + mm * j;
+        t.K = S.N; t.M = m; t.N = m; t.lda = m; t.ldb = m; t.ldc = m;
+        push_tiles(tasks, t, true);
+      }
+      GemmTask* d_gt;
+      CK(dupload(h, &d_gt, tasks));
+      d_tasks = d_gt;
+      KLA(h, K_GRAM, 1, 8.0 * h->rows_total * m, h->sumNm2, launch_gemm_tn(d_gt, (int)tasks.size(), h->st));
     }
-    GemmTask* d_tasks;
-    CK(dupload(h, &d_tasks, tasks));
-    KLA(h, K_GRAM, 1, 8.0 * h->rows_total * m, h->sumNm2, launch_gemm_tn(d_tasks, (int)tasks.size(), h->st));
     std::vector<double*> mats(J);
     std::vector<int> ns(J, m), lds(J, m);
     for (int j = 0; j < J; ++j) mats[j] = h->d_V + mm * j;
@@ -535,6 +577,7 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     CK(cudaStreamSynchronize(h->st));
     dfree(h, d_tasks); dfree(h, d_mats); dfree(h, d_ns); dfree(h, d_lds); dfree(h, d_work); dfree(h, d_info);
     dfree(h, d_ranks);
+    if (d_sl) { dfree(h, d_sl); dfree(h, d_e); }
   }
   for (int j = 0; j < J; ++j)
     REQUIRE(info[j] == 0, RANN_ECUDA, "eigen-decomposition of subdomain %d did not converge", j);
@@ -574,7 +617,42 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   if (h->d_B) dfree(h, h->d_B);
   CK(dalloc(h, (void**)&h->d_B, sizeof(double) * (size_t)boff));
   CK(cudaMemsetAsync(h->d_B, 0, sizeof(double) * (size_t)boff, h->st));
-  {
+  if (h->inner_df) {        // B_j = H_j V_{p_j} from digit slices of H_j and V_{p_j}^T
+    const int nsl = oz_slices(), Kp = oz_kpad(m);
+    int64_t sumP = 0;
+    for (int j = 0; j < J; ++j) sumP += h->subs[j].p;
+    uint16_t* d_sl; int* d_e;
+    const int64_t nrows = h->rows_total + sumP;
+    CK(dalloc(h, (void**)&d_sl, sizeof(uint16_t) * (size_t)(nsl * Kp) * (size_t)nrows));
+    CK(dalloc(h, (void**)&d_e, sizeof(int) * (size_t)nrows));
+    std::vector<OzSplitTask> sp(2 * J);
+    std::vector<OzTask> gt;
+    int64_t vrow = h->rows_total;       // rows of the V^T operands follow the rows of H
+    int maxM = m;
+    for (int j = 0; j < J; ++j) {
+      const SubDev& S = h->subs[j];
+      OzSplitTask& a = sp[2 * j];
+      a.X = h->d_H + S.row0 * m; a.si = m; a.sk = 1;
+      a.M = S.N; a.K = m; a.Kp = Kp; a.e = d_e + S.row0; a.out = d_sl + (size_t)nsl * Kp * S.row0;
+      OzSplitTask& b = sp[2 * j + 1];
+      b.X = h->d_V + mm * j; b.si = 1; b.sk = m;                // row c of V_{p_j}^T
+      b.M = S.p; b.K = m; b.Kp = Kp; b.e = d_e + vrow; b.out = d_sl + (size_t)nsl * Kp * vrow;
+      vrow += S.p;
+      maxM = std::max(maxM, S.N);
+      OzTask g{};
+      g.A = a.out; g.B = b.out; g.ea = a.e; g.eb = b.e; g.C = h->d_B + S.boff;
+      g.M = S.N; g.N = S.p; g.Kp = Kp; g.ldc = S.P;
+      for (int tm = 0; tm < S.N; tm += 64)
+        for (int tn = 0; tn < S.p; tn += 64) { g.tm = tm; g.tn = tn; gt.push_back(g); }
+    }
+    OzSplitTask* d_sp; OzTask* d_gt;
+    CK(dupload(h, &d_sp, sp)); CK(dupload(h, &d_gt, gt));
+    KLA(h, K_OZ_SPLIT, 2, (8.0 + 2.0 * nsl) * (double)m * nrows, 0, launch_oz_split(d_sp, 2 * J, maxM, Kp, h->st));
+    KLA(h, K_PROJECT_OZ, 1, 2.0 * nsl * (double)m * nrows + 8.0 * h->sumNp, 36.0 * 2.0 * h->sumNmp,
+        launch_oz_gemm(d_gt, (int)gt.size(), h->st));
+    CK(cudaStreamSynchronize(h->st));
+    dfree(h, d_sp); dfree(h, d_gt); dfree(h, d_sl); dfree(h, d_e);
+  } else {
     std::vector<GemmTask> tasks;
     for (int j = 0; j < J; ++j) {
       const SubDev& S = h->subs[j];

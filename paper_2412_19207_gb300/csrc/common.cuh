@@ -80,6 +80,28 @@ cudaError_t launch_gemm_tn_df(const GemmTask* d_tasks, int ntasks, cudaStream_t 
 cudaError_t launch_symmetrize(double* const* d_mats, const int* d_n, const int* d_ld, int nmat,
                               int maxn, cudaStream_t st);
 
+// ozaki.cu -- float64-accurate products from bf16 digit slices on the tensor cores
+struct OzSplitTask {         // one operand: rows i < M of x(i, k) = X[i * si + k * sk], k < K
+  const double* X;
+  int64_t si, sk;
+  int M, K, Kp, pad_;        // Kp = oz_kpad(K)
+  int* e;                    // [M] row exponents (out)
+  uint16_t* out;             // [oz_slices()][M][Kp] bf16 digit slices (out)
+};
+struct OzTask {              // one 64 x 64 tile of C = A B^T (A: M x K slices, B: N x K slices)
+  const uint16_t* A;
+  const uint16_t* B;
+  const int* ea;
+  const int* eb;
+  double* C;                 // M x N (ldc)
+  int M, N, Kp, ldc;
+  int tm, tn;                // tile origin in C
+};
+int oz_slices();
+int oz_kpad(int K);
+cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, int maxKp, cudaStream_t st);
+cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, cudaStream_t st);
+
 // eig.cu -- batched symmetric eigen-decomposition (float64)
 // Eigenpairs of `batch` m x m symmetric matrices; ranks by the PCA rule (mode, thr);
 // d_work holds batch * syevd_work_doubles(m) doubles.
