@@ -570,7 +570,7 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     // algorithmic flops: tridiagonal reduction 4/3 m^3 per matrix (the eigenvector work depends on p_j
     // and is added below once the ranks are known)
     KLA(h, K_EIG, 1, 24.0 * mm * J, 4.0 / 3.0 * (double)m * mm * J,
-        launch_syevd(h->d_V, m, J, h->d_eig, d_work, d_info, d_ranks, mode, thr, h->st));
+        launch_syevd(h->d_V, m, J, h->d_eig, d_work, d_info, d_ranks, mode, thr, h->inner_df, h->st));
     CK(cudaMemcpyAsync(h->eig_host.data(), h->d_eig, sizeof(double) * m * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(info.data(), d_info, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(dev_ranks.data(), d_ranks, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));

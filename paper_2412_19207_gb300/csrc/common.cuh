@@ -104,10 +104,11 @@ cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, cudaStream_t st);
 
 // eig.cu -- batched symmetric eigen-decomposition (float64)
 // Eigenpairs of `batch` m x m symmetric matrices; ranks by the PCA rule (mode, thr);
-// d_work holds batch * syevd_work_doubles(m) doubles.
+// eigenvalues by bisection (bisect = 1) or QL (0); d_work holds
+// batch * syevd_work_doubles(m) doubles.
 int64_t syevd_work_doubles(int m);
 cudaError_t launch_syevd(double* d_A, int m, int batch, double* d_w, double* d_work, int* d_info, int* d_ranks,
-                         int mode, double thr, cudaStream_t st);
+                         int mode, double thr, int bisect, cudaStream_t st);
 
 // chol.cu -- batched uneven Cholesky and triangular solves
 struct CholMat {

@@ -7,11 +7,18 @@
 //      reflectors kept in the rows of G; the symmetric rank-2 update is done
 //      once per lower element and mirrored, so the matrix stays exactly
 //      symmetric.
-//   2. Eigenvalues of T by implicit QL with Wilkinson shifts (the tql1 scheme
-//      of Bowdler, Martin, Reinsch & Wilkinson, 1968), no vectors; each plane
-//      rotation takes one reciprocal square root (the chase is one thread's
-//      dependent chain, so its latency per step bounds this phase).
-//   3. Eigenvalues sorted descending; the rank rule of Sec. 4 gives p_j.
+//   2. Eigenvalues of T.  Fast path: bisection on Sturm counts, one thread
+//      per eigenvalue (Barth, Martin & Wilkinson, 1967; Kahan's LDL^T count):
+//      T is scaled by a power of two to norm <= 1; 48 halvings use LDL^T
+//      pivot counts in double-float arithmetic (float32 pipe), then the
+//      bracket is widened, re-verified and halved 10 more times with float64
+//      counts from the division-free three-term recurrence of the leading
+//      principal minors (rescaled by powers of two every 8 steps), so each
+//      eigenvalue ends within ~2^-52 ||T|| like a float64 QL.  Reference
+//      path (precision mode 0): implicit QL with Wilkinson shifts (the tql1
+//      scheme of Bowdler, Martin, Reinsch & Wilkinson, 1968), no vectors,
+//      one thread's dependent chain.
+//   3. Eigenvalues in descending order; the rank rule of Sec. 4 gives p_j.
 //   4. Eigenvectors of T for the p_j largest eigenvalues by inverse iteration
 //      (tridiagonal LU with partial pivoting, two solves; Wilkinson, The
 //      Algebraic Eigenvalue Problem, Ch. 9), one thread per vector, then
@@ -21,6 +28,7 @@
 // m x m, column c = eigenvector c for c < p_j, zero beyond); info[b] != 0 if
 // QL did not converge in 100 sweeps for some eigenvalue.
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace {
 
@@ -50,10 +58,78 @@ __device__ __forceinline__ double start_entry(int i, int k) {
   return (double)(h & 2047u) / 1024.0 - 0.5;
 }
 
+constexpr float PIV_DF = 0x1p-60f;   // pivot floor of the scaled LDL^T counts
+constexpr double PIV_64 = 0x1p-60;
+
+// (ah, al) - (bh, bl) in double-float
+__device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, float& rh, float& rl) {
+  float s, e;
+  df_two_sum(ah, -bh, s, e);
+  e = __fadd_rn(e, __fsub_rn(al, bl));
+  df_two_sum(s, e, rh, rl);
+}
+
+// Number of eigenvalues of the scaled T below sigma: negative pivots of
+// T - sigma I = L D L^T, q_0 = d_0 - sigma, q_i = d_i - sigma - e_{i-1}^2 / q_{i-1},
+// in double-float (d = dh + dl, e^2 = eh + el); a pivot below PIV_DF in
+// magnitude is replaced by -PIV_DF.
+__device__ int sturm_count_df(const float* __restrict__ dh, const float* __restrict__ dl,
+                              const float* __restrict__ eh, const float* __restrict__ el, int m,
+                              double sigma) {
+  const float2 sg = df_split(sigma);
+  float qh, ql;
+  df_diff(dh[0], dl[0], sg.x, sg.y, qh, ql);
+  if (fabsf(qh) < PIV_DF) { qh = -PIV_DF; ql = 0.f; }
+  int cnt = qh < 0.f;
+  for (int i = 1; i < m; ++i) {
+    float ah, al;
+    df_diff(dh[i], dl[i], sg.x, sg.y, ah, al);
+    // t = e^2 / q: quotient, exact residual, one correction
+    const float x = __fdividef(eh[i - 1], qh);
+    const float ph = __fmul_rn(x, qh);
+    const float pe = __fmaf_rn(x, qh, -ph);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(eh[i - 1], ph), pe), __fsub_rn(el[i - 1], __fmul_rn(x, ql)));
+    const float c = __fdividef(r, qh);
+    float th, tl;
+    df_two_sum(x, c, th, tl);
+    df_diff(ah, al, th, tl, qh, ql);
+    if (fabsf(qh) < PIV_DF) { qh = -PIV_DF; ql = 0.f; }
+    cnt += qh < 0.f;
+  }
+  return cnt;
+}
+
+// The same count in float64 from the leading principal minors
+// p_{i+1} = (d_i - sigma) p_i - e_{i-1}^2 p_{i-1} (a sign change between p_i and
+// p_{i+1} is a negative pivot q_i = p_{i+1} / p_i; an exact zero becomes
+// q_i = -PIV_64).  Both minors are rescaled by the power of two that brings the
+// larger to [1, 2) every 8 steps (|d_i - sigma| + e_{i-1}^2 <= 4, so 8 steps
+// grow them by at most 2^16).
+__device__ int sturm_count_f64(const double* __restrict__ ds, const double* __restrict__ e2s, int m,
+                               double sigma) {
+  double p0 = 1.0, p1 = ds[0] - sigma;
+  if (p1 == 0.0) p1 = -PIV_64;
+  int cnt = __double2hiint(p1) < 0;
+  for (int i = 1; i < m; ++i) {
+    double p2 = fma(ds[i] - sigma, p1, -e2s[i - 1] * p0);
+    if (((__double2hiint(p2) & 0x7fffffff) | __double2loint(p2)) == 0) p2 = -PIV_64 * p1;
+    cnt += (__double2hiint(p2) ^ __double2hiint(p1)) < 0;
+    p0 = p1;
+    p1 = p2;
+    if ((i & 7) == 0) {
+      const int E = max((__double2hiint(p0) >> 20) & 0x7ff, (__double2hiint(p1) >> 20) & 0x7ff);
+      const double f = __hiloint2double((2046 - E) << 20, 0);   // 2^(1023 - E), E <= 2045 here
+      p0 *= f;
+      p1 *= f;
+    }
+  }
+  return cnt;
+}
+
 __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int m, int64_t stride,
                                                   double* __restrict__ wall, double* __restrict__ work_all,
                                                   int64_t work_stride, int* __restrict__ info,
-                                                  int* __restrict__ ranks, int mode, double thr) {
+                                                  int* __restrict__ ranks, int mode, double thr, int bisect) {
   extern __shared__ double sm[];
   double* v = sm;              // [m] reflector / QL diagonal copy
   double* w = v + m;           // [m] symmetric product / QL off-diagonal copy
@@ -61,6 +137,13 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
   double* e = d + m;           // [m] tridiagonal off-diagonal
   double* beta = e + m;        // [m] reflector scalars
   double* ev = beta + m;       // [m] eigenvalues, descending
+  double* ds = ev + m;         // [m] bisection: scaled diagonal
+  double* e2s = ds + m;        // [m] bisection: scaled squared off-diagonal
+  float* dh = reinterpret_cast<float*>(e2s + m);   // [m] x 4: double-float copies of ds, e2s
+  float* dl = dh + m;
+  float* eh = dl + m;
+  float* el = eh + m;
+  __shared__ double gbounds[3];
   __shared__ double red[33];
   __shared__ double tnorm;
   __shared__ int ql_fail, prank;
@@ -115,7 +198,7 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
     __syncthreads();
   }
 
-  // ---- 2. eigenvalues of T: implicit QL without vectors (one thread) ----
+  // ---- 2. eigenvalues of T ----
   if (tid == 0) {
     if (m >= 2) {
       d[m - 2] = A[(int64_t)(m - 2) * m + m - 2];
@@ -125,9 +208,56 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
     d[m - 1] = A[(int64_t)(m - 1) * m + m - 1];
     e[m - 1] = 0.0;
     beta[m - 1] = 0.0;
-    double t = 0.0;
-    for (int i = 0; i < m; ++i) { t = fmax(t, fabs(d[i]) + fabs(e[i])); v[i] = d[i]; w[i] = e[i]; }
+    double t = 0.0, gl = 0.0, gu = 0.0;
+    for (int i = 0; i < m; ++i) {
+      t = fmax(t, fabs(d[i]) + fabs(e[i]));
+      v[i] = d[i];
+      w[i] = e[i];
+      const double rad = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0);   // Gershgorin discs
+      gl = (i == 0) ? d[i] - rad : fmin(gl, d[i] - rad);
+      gu = (i == 0) ? d[i] + rad : fmax(gu, d[i] + rad);
+    }
     tnorm = t;
+    gbounds[0] = gl;
+    gbounds[1] = gu;
+    ql_fail = 0;
+  }
+  __syncthreads();
+  if (bisect) {
+    // scale T by 2^-sc (exact) so that its norm is at most 1
+    const int sc = (tnorm > 0.0) ? ilogb(tnorm) + 1 : 0;
+    for (int i = tid; i < m; i += NT) {
+      const double di = ldexp(d[i], -sc), ei = ldexp(e[i], -sc);
+      ds[i] = di;
+      e2s[i] = ei * ei;
+      const float2 a = df_split(di), b = df_split(ei * ei);
+      dh[i] = a.x; dl[i] = a.y; eh[i] = b.x; el[i] = b.y;
+    }
+    __syncthreads();
+    const double glo = ldexp(gbounds[0], -sc) - 0x1p-40, ghi = ldexp(gbounds[1], -sc) + 0x1p-40;
+    for (int k = tid; k < m; k += NT) {          // k-th smallest eigenvalue
+      double lo = glo, hi = ghi;
+      for (int it = 0; it < 48; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count_df(dh, dl, eh, el, m, mid) > k) hi = mid; else lo = mid;
+      }
+      // float64 polish: widen, re-verify the bracket with float64 counts, halve
+      double wd = 0x1p-44;
+      lo -= wd;
+      for (int r = 0; r < 40 && lo > glo && sturm_count_f64(ds, e2s, m, lo) > k; ++r) { wd *= 2.0; lo = fmax(lo - wd, glo); }
+      wd = 0x1p-44;
+      hi += wd;
+      for (int r = 0; r < 40 && hi < ghi && sturm_count_f64(ds, e2s, m, hi) <= k; ++r) { wd *= 2.0; hi = fmin(hi + wd, ghi); }
+      for (int it = 0; it < 10; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (sturm_count_f64(ds, e2s, m, mid) > k) hi = mid; else lo = mid;
+      }
+      ev[m - 1 - k] = ldexp(0.5 * (lo + hi), sc);
+    }
+  } else if (tid == 0) {
+    // implicit QL without vectors (one thread)
+    const double t = tnorm;
     int fail = 0;
     for (int l = 0; l < m; ++l) {
       int iter = 0;
@@ -168,14 +298,16 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
   }
   __syncthreads();
 
-  // ---- 3. sort descending (rank of each eigenvalue; ties by index) ----
-  for (int t = tid; t < m; t += NT) {
-    const double x = v[t];
-    int rk = 0;
-    for (int j = 0; j < m; ++j) rk += (v[j] > x) || (v[j] == x && j < t);
-    ev[rk] = x;
+  // ---- 3. QL path: sort descending (rank of each eigenvalue; ties by index) ----
+  if (!bisect) {
+    for (int t = tid; t < m; t += NT) {
+      const double x = v[t];
+      int rk = 0;
+      for (int j = 0; j < m; ++j) rk += (v[j] > x) || (v[j] == x && j < t);
+      ev[rk] = x;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // ---- rank rule (Sec. 4) ----
   if (tid == 0) {
     int p = m;
@@ -325,12 +457,12 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
 int64_t syevd_work_doubles(int m) { return (int64_t)m * m + 5 * (int64_t)m * NT; }
 
 cudaError_t launch_syevd(double* d_A, int m, int batch, double* d_w, double* d_work, int* d_info, int* d_ranks,
-                         int mode, double thr, cudaStream_t st) {
+                         int mode, double thr, int bisect, cudaStream_t st) {
   if (batch == 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * 6 * (size_t)m;
+  const size_t smem = sizeof(double) * 10 * (size_t)m;
   cudaError_t e = cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   syev_kernel<<<batch, NT, smem, st>>>(d_A, m, (int64_t)m * m, d_w, d_work, syevd_work_doubles(m), d_info,
-                                       d_ranks, mode, thr);
+                                       d_ranks, mode, thr, bisect);
   return cudaGetLastError();
 }
