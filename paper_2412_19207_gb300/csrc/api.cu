@@ -100,19 +100,19 @@ enum KId {
   K_POINTS, K_ASSEMBLE, K_RHS, K_GRAM, K_SYMM, K_EIG, K_PROJECT, K_PAIRGRAM, K_LOCALASM, K_ADDDIAG,
   K_CHOL, K_TRTRI, K_GATHER, K_TRMV_L, K_TRMV_U, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL,
   K_SPLIT, K_MATVEC_H_DF, K_MATVEC_HT_DF, K_GATHER_DF, K_TRMV_L_DF, K_TRMV_U_DF, K_OZ_SPLIT, K_GRAM_OZ,
-  K_PROJECT_OZ, K_COUNT
+  K_PROJECT_OZ, K_EIG_VAL, K_EIG_VEC, K_EIG_ORTH, K_EIG_BACK, K_COUNT
 };
 static const char* const KNAMES[K_COUNT] = {
-  "points", "assemble", "rhs", "gram", "symmetrize", "eig", "project", "pair_gram", "local_assemble",
+  "points", "assemble", "rhs", "gram", "symmetrize", "eig_tridiag", "project", "pair_gram", "local_assemble",
   "add_diag", "cholesky", "trtri", "schwarz_gather", "trmv_lower", "trmv_upper", "schwarz_combine",
   "matvec_H", "matvec_HT", "dot", "vector", "eval", "split_df32", "matvec_H_df32", "matvec_HT_df32",
-  "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32", "ozaki_split", "gram_ozaki", "project_ozaki"};
+  "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32", "ozaki_split", "gram_ozaki", "project_ozaki", "eig_values", "eig_vectors", "eig_orth", "eig_back"};
 
 // Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
 // 1 = float64-ALU-bound (algorithmic flops count), 2 = bf16-tensor-core-bound
 // (the flops of the digit-slice products count).
 static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1,
-                                     0, 0, 0, 0, 0, 0, 0, 2, 2};
+                                     0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1};
 
 struct Prof {
   bool on = false;
@@ -567,10 +567,15 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     CK(dalloc(h, (void**)&d_work, sizeof(double) * (size_t)syevd_work_doubles(m) * J));
     CK(dalloc(h, (void**)&d_info, sizeof(int) * J));
     CK(dalloc(h, (void**)&d_ranks, sizeof(int) * J));
-    // algorithmic flops: tridiagonal reduction 4/3 m^3 per matrix (the eigenvector work depends on p_j
-    // and is added below once the ranks are known)
-    KLA(h, K_EIG, 1, 24.0 * mm * J, 4.0 / 3.0 * (double)m * mm * J,
-        launch_syevd(h->d_V, m, J, h->d_eig, d_work, d_info, d_ranks, mode, thr, h->inner_df, h->st));
+    // algorithmic flops: tridiagonal reduction 4/3 m^3 per matrix; eigenvalues: the float64 Sturm
+    // counts of the bisection (12 per eigenvalue, 3 flops per step; the double-float counts run on the
+    // float32 pipe); the eigenvector work depends on p_j and is added below once the ranks are known
+    SyevBatch sb{h->d_V, m, J, h->d_eig, d_work, d_info, d_ranks, mode, thr, h->inner_df};
+    KLA(h, K_EIG, 1, 24.0 * mm * J, 4.0 / 3.0 * (double)m * mm * J, launch_syev_phase(sb, 0, h->st));
+    KLA(h, K_EIG_VAL, 1, 0, h->inner_df ? 36.0 * mm * J : 0.0, launch_syev_phase(sb, 1, h->st));
+    KLA(h, K_EIG_VEC, 1, 0, 0, launch_syev_phase(sb, 2, h->st));
+    KLA(h, K_EIG_ORTH, 1, 0, 0, launch_syev_phase(sb, 3, h->st));
+    KLA(h, K_EIG_BACK, 2, 0, 0, launch_syev_phase(sb, 4, h->st));
     CK(cudaMemcpyAsync(h->eig_host.data(), h->d_eig, sizeof(double) * m * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(info.data(), d_info, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(dev_ranks.data(), d_ranks, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
@@ -595,7 +600,9 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     // the eigensolver applied the rank rule (it forms only the kept eigenvectors)
     const int p = dev_ranks[j];
     REQUIRE(p >= 1 && p <= m, RANN_ECUDA, "eigensolver returned rank %d for subdomain %d", p, j);
-    h->prof.flops[K_EIG] += 2.0 * (double)m * m * p + 4.0 * (double)m * p * p;
+    h->prof.flops[K_EIG_VEC] += 25.0 * (double)m * p;       // tridiagonal LU and two solves
+    h->prof.flops[K_EIG_ORTH] += 4.0 * (double)m * p * p;   // two Gram-Schmidt passes
+    h->prof.flops[K_EIG_BACK] += 2.0 * (double)m * m * p;   // m - 2 reflectors per vector
     SubDev& S = h->subs[j];
     S.p = p;
     S.P = p + (p & 1);

@@ -103,12 +103,24 @@ cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, in
 cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, cudaStream_t st);
 
 // eig.cu -- batched symmetric eigen-decomposition (float64)
-// Eigenpairs of `batch` m x m symmetric matrices; ranks by the PCA rule (mode, thr);
-// eigenvalues by bisection (bisect = 1) or QL (0); d_work holds
-// batch * syevd_work_doubles(m) doubles.
+// Eigenpairs of `batch` m x m symmetric matrices A; ranks by the PCA rule (mode, thr);
+// eigenvalues by bisection (bisect = 1) or QL (0); work holds
+// batch * syevd_work_doubles(m) doubles.  Phases 0..4 (tridiagonalisation,
+// eigenvalues, rank rule + inverse iteration, Gram-Schmidt, back-transformation
+// + output) run in this order on one stream.
+struct SyevBatch {
+  double* A;
+  int m, batch;
+  double* w;                 // [batch][m] eigenvalues, descending
+  double* work;
+  int* info;
+  int* ranks;
+  int mode;
+  double thr;
+  int bisect;
+};
 int64_t syevd_work_doubles(int m);
-cudaError_t launch_syevd(double* d_A, int m, int batch, double* d_w, double* d_work, int* d_info, int* d_ranks,
-                         int mode, double thr, int bisect, cudaStream_t st);
+cudaError_t launch_syev_phase(const SyevBatch& b, int phase, cudaStream_t st);
 
 // chol.cu -- batched uneven Cholesky and triangular solves
 struct CholMat {

@@ -1,12 +1,13 @@
 // Batched symmetric eigen-decomposition in float64 for the PCA (Sec. 4,
 // Eq. (pca)): the right singular vectors and singular values of Psi_j are the
-// eigenpairs of G_j = Psi_j^T Psi_j = V diag(sigma^2) V^T.  One thread block
-// per matrix; only the p_j kept eigenvectors are formed.
+// eigenpairs of G_j = Psi_j^T Psi_j = V diag(sigma^2) V^T.  Only the p_j
+// kept eigenvectors are formed.  Five kernels per batch (one phase each;
+// grids span the batch and, where the phase is parallel over eigenpairs,
+// parts of each matrix):
 //
-//   1. Householder tridiagonalisation G = Q T Q^T (Golub & Van Loan 8.3.1),
-//      reflectors kept in the rows of G; the symmetric rank-2 update is done
-//      once per lower element and mirrored, so the matrix stays exactly
-//      symmetric.
+//   1. Householder tridiagonalisation G = Q T Q^T (Golub & Van Loan 8.3.1)
+//      on the lower triangle by a cluster of blocks per matrix; reflectors
+//      kept in the upper rows of G.
 //   2. Eigenvalues of T.  Fast path: bisection on Sturm counts, one thread
 //      per eigenvalue (Barth, Martin & Wilkinson, 1967; Kahan's LDL^T count):
 //      T is scaled by a power of two to norm <= 1; 48 halvings use LDL^T
@@ -23,10 +24,16 @@
 //      (tridiagonal LU with partial pivoting, two solves; Wilkinson, The
 //      Algebraic Eigenvalue Problem, Ch. 9), one thread per vector, then
 //      classical Gram-Schmidt applied twice in descending order.
-//   5. Back-transformation V = Q Z, one warp per vector.
+//   5. Back-transformation V = Q Z, one warp per vector, and the transposed
+//      copy of V into G.
 // Output: w[m] descending; ranks[b] = p_j; G overwritten by V (row-major
 // m x m, column c = eigenvector c for c < p_j, zero beyond); info[b] != 0 if
 // QL did not converge in 100 sweeps for some eigenvalue.
+// Work area per matrix (doubles): Z [m][m] (rows: eigenvectors of T), the
+// inverse-iteration LU [5][m][m] (entry i of vector k at [i][k]), d, e, beta
+// [m] each, and 4 scalars (||T||, Gershgorin bounds).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "df32.cuh"
 
@@ -126,38 +133,54 @@ __device__ int sturm_count_f64(const double* __restrict__ ds, const double* __re
   return cnt;
 }
 
-__global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int m, int64_t stride,
-                                                  double* __restrict__ wall, double* __restrict__ work_all,
-                                                  int64_t work_stride, int* __restrict__ info,
-                                                  int* __restrict__ ranks, int mode, double thr, int bisect) {
-  extern __shared__ double sm[];
-  double* v = sm;              // [m] reflector / QL diagonal copy
-  double* w = v + m;           // [m] symmetric product / QL off-diagonal copy
-  double* d = w + m;           // [m] tridiagonal diagonal (later: Gram-Schmidt coefficients)
-  double* e = d + m;           // [m] tridiagonal off-diagonal
-  double* beta = e + m;        // [m] reflector scalars
-  double* ev = beta + m;       // [m] eigenvalues, descending
-  double* ds = ev + m;         // [m] bisection: scaled diagonal
-  double* e2s = ds + m;        // [m] bisection: scaled squared off-diagonal
-  float* dh = reinterpret_cast<float*>(e2s + m);   // [m] x 4: double-float copies of ds, e2s
-  float* dl = dh + m;
-  float* eh = dl + m;
-  float* el = eh + m;
-  __shared__ double gbounds[3];
-  __shared__ double red[33];
-  __shared__ double tnorm;
-  __shared__ int ql_fail, prank;
-  double* A = Aall + blockIdx.x * stride;
-  double* Z = work_all + blockIdx.x * work_stride;   // rows: eigenvectors
-  double* LU = Z + (int64_t)m * m;                   // 5 m NT doubles, [i][thread]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// Per-matrix work layout.
+struct SyevWork {
+  double *Z, *LU, *d, *e, *beta, *meta;
+  __device__ SyevWork(double* base, int m) {
+    Z = base;
+    LU = Z + (int64_t)m * m;
+    d = LU + 5 * (int64_t)m * m;
+    e = d + m;
+    beta = e + m;
+    meta = beta + m;            // [0] ||T||_inf-like bound, [1] [2] Gershgorin bounds
+  }
+};
 
-  // ---- 1. tridiagonalisation ----
+// ---- 1. tridiagonalisation, one cluster of TC blocks per matrix ----
+// Only the lower triangle of the trailing matrix A' is kept.  Per column k:
+// every block forms the same reflector v from column k; the symmetric
+// product A' v is accumulated from the lower rows (each row c, loaded once,
+// adds v_c A'[c][0..c] to the result and contributes its dot product with v
+// to entry c); rows are dealt cyclically to the TC x NW warps of the cluster,
+// the per-block partial sums are exchanged through distributed shared memory
+// and added in a fixed order (so every block holds the identical w); then the
+// cluster applies A' -= v w^T + w v^T to the lower rows, dealt the same way.
+// Each lane holds SL columns (lane + 32 t), so a row's loads are all in flight
+// at once.
+constexpr int TC = 2;          // blocks per matrix (cluster size; one block per SM at 512 threads)
+
+template <int SL>
+__global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ Aall, int m,
+                                                          double* __restrict__ work_all, int64_t work_stride) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double sm[];
+  double* v = sm;              // [m] reflector
+  double* w = v + m;           // [m] symmetric product
+  double* wl = w + m;          // [m] this block's partial product (read by the cluster)
+  double* part = wl + m;       // [NW][m] per-warp partials
+  __shared__ double red[33];
+  const int mat = blockIdx.x / TC;
+  const int rank = (int)cluster.block_rank();
+  double* A = Aall + (int64_t)mat * m * m;
+  SyevWork W(work_all + mat * work_stride, m);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gw = rank * NW + warp;             // warp index within the cluster
   for (int k = 0; k + 2 < m; ++k) {
     const int n1 = m - k - 1;
     double loc = 0.0;
     for (int c = tid; c < n1; c += NT) {
-      double x = A[(int64_t)k * m + k + 1 + c];   // row k == column k by symmetry
+      const double x = A[(int64_t)(k + 1 + c) * m + k];   // column k, lower part
       v[c] = x;
       loc += x * x;
     }
@@ -167,75 +190,156 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
     const double alpha = (x0 >= 0.0) ? -sigma : sigma;
     const double bt = (sigma > 0.0) ? 1.0 / (sig2 + fabs(x0) * sigma) : 0.0;   // 2 / (v^T v)
     __syncthreads();
-    if (tid == 0) { v[0] = x0 - alpha; d[k] = A[(int64_t)k * m + k]; e[k] = alpha; beta[k] = bt; }
+    if (tid == 0) {
+      v[0] = x0 - alpha;
+      if (rank == 0) { W.d[k] = A[(int64_t)k * m + k]; W.e[k] = alpha; W.beta[k] = bt; }
+    }
     __syncthreads();
     if (bt != 0.0) {
-      double pv = 0.0;
-      for (int r = tid; r < n1; r += NT) {   // p = bt A' v, A' read by columns (coalesced over r)
+      double* Ak = A + (int64_t)(k + 1) * m + (k + 1);       // A'[c][j] = Ak[c * m + j]
+      double acc[SL];
+#pragma unroll
+      for (int t = 0; t < SL; ++t) acc[t] = 0.0;
+      for (int c = gw; c < n1; c += TC * NW) {
+        const double* R = Ak + (int64_t)c * m;
+        const int tmax = c >> 5;               // last slot holding part of row c (warp-uniform)
+        double x[SL];
+#pragma unroll
+        for (int t = 0; t < SL; ++t) {
+          if (t > tmax) break;
+          x[t] = (lane + 32 * t <= c) ? R[lane + 32 * t] : 0.0;
+        }
+        const double vc = v[c];
+        double dot = 0.0;
+#pragma unroll
+        for (int t = 0; t < SL; ++t) {
+          if (t > tmax) break;
+          const int j = lane + 32 * t;
+          acc[t] = fma(vc, x[t], acc[t]);
+          dot = fma(x[t], (j < c) ? v[j] : 0.0, dot);
+        }
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+#pragma unroll
+        for (int t = 0; t < SL; ++t)
+          if (lane + 32 * t == c) acc[t] += dot;
+      }
+#pragma unroll
+      for (int t = 0; t < SL; ++t)
+        if (lane + 32 * t < n1) part[warp * m + lane + 32 * t] = acc[t];
+      __syncthreads();
+      for (int j = tid; j < n1; j += NT) {
         double s = 0.0;
-        const double* col = A + (int64_t)(k + 1) * m + k + 1 + r;
-        for (int c = 0; c < n1; ++c) s = fma(col[(int64_t)c * m], v[c], s);
+        for (int q = 0; q < NW; ++q) s += part[q * m + j];
+        wl[j] = s;
+      }
+      cluster.sync();                          // partials visible to the cluster
+      double pv = 0.0;
+      for (int j = tid; j < n1; j += NT) {
+        double s = 0.0;
+        for (int q = 0; q < TC; ++q) s += cluster.map_shared_rank(wl, q)[j];
         s *= bt;
-        w[r] = s;
-        pv = fma(s, v[r], pv);
+        w[j] = s;
+        pv = fma(s, v[j], pv);
       }
       const double K = 0.5 * bt * block_sum(pv, red);
-      for (int r = tid; r < n1; r += NT) w[r] = fma(-K, v[r], w[r]);
+      for (int j = tid; j < n1; j += NT) w[j] = fma(-K, v[j], w[j]);
       __syncthreads();
-      // A' -= v w^T + w v^T: each lower element once, mirrored to the upper one
-      for (int rr = warp; rr < n1; rr += NW) {
-        double* row = A + (int64_t)(k + 1 + rr) * m + k + 1;
+      // A' -= v w^T + w v^T on the lower rows
+      for (int rr = gw; rr < n1; rr += TC * NW) {
+        double* R = Ak + (int64_t)rr * m;
+        const int tmax = rr >> 5;
+        double x[SL];
+#pragma unroll
+        for (int t = 0; t < SL; ++t) {
+          if (t > tmax) break;
+          x[t] = (lane + 32 * t <= rr) ? R[lane + 32 * t] : 0.0;
+        }
         const double vr = v[rr], wr = w[rr];
-        for (int cc = lane; cc <= rr; cc += 32) {
-          double s = fma(-vr, w[cc], fma(-wr, v[cc], row[cc]));
-          row[cc] = s;
-          if (cc != rr) A[(int64_t)(k + 1 + cc) * m + k + 1 + rr] = s;
+#pragma unroll
+        for (int t = 0; t < SL; ++t) {
+          if (t > tmax) break;
+          const int j = lane + 32 * t;
+          if (j <= rr) R[j] = fma(-vr, w[j], fma(-wr, v[j], x[t]));
         }
       }
     }
-    __syncthreads();
-    for (int c = tid; c < n1; c += NT) A[(int64_t)k * m + k + 1 + c] = v[c];   // keep the reflector
-    __syncthreads();
+    if (rank == 0)
+      for (int c = tid; c < n1; c += NT) A[(int64_t)k * m + k + 1 + c] = v[c];   // keep the reflector (upper part)
+    cluster.sync();                            // updates visible before the next column; wl free again
   }
-
-  // ---- 2. eigenvalues of T ----
-  if (tid == 0) {
+  if (rank == 0 && tid == 0) {
     if (m >= 2) {
-      d[m - 2] = A[(int64_t)(m - 2) * m + m - 2];
-      e[m - 2] = A[(int64_t)(m - 1) * m + m - 2];
-      beta[m - 2] = 0.0;
+      W.d[m - 2] = A[(int64_t)(m - 2) * m + m - 2];
+      W.e[m - 2] = A[(int64_t)(m - 1) * m + m - 2];
+      W.beta[m - 2] = 0.0;
     }
-    d[m - 1] = A[(int64_t)(m - 1) * m + m - 1];
-    e[m - 1] = 0.0;
-    beta[m - 1] = 0.0;
+    W.d[m - 1] = A[(int64_t)(m - 1) * m + m - 1];
+    W.e[m - 1] = 0.0;
+    W.beta[m - 1] = 0.0;
     double t = 0.0, gl = 0.0, gu = 0.0;
     for (int i = 0; i < m; ++i) {
-      t = fmax(t, fabs(d[i]) + fabs(e[i]));
-      v[i] = d[i];
-      w[i] = e[i];
-      const double rad = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0);   // Gershgorin discs
-      gl = (i == 0) ? d[i] - rad : fmin(gl, d[i] - rad);
-      gu = (i == 0) ? d[i] + rad : fmax(gu, d[i] + rad);
+      const double di = W.d[i], ei = W.e[i], ep = (i > 0) ? W.e[i - 1] : 0.0;
+      t = fmax(t, fabs(di) + fabs(ei));
+      const double rad = fabs(ei) + fabs(ep);   // Gershgorin discs
+      gl = (i == 0) ? di - rad : fmin(gl, di - rad);
+      gu = (i == 0) ? di + rad : fmax(gu, di + rad);
     }
-    tnorm = t;
-    gbounds[0] = gl;
-    gbounds[1] = gu;
-    ql_fail = 0;
+    W.meta[0] = t;
+    W.meta[1] = gl;
+    W.meta[2] = gu;
   }
-  __syncthreads();
+}
+
+template <int SL>
+cudaError_t launch_tridiag(double* A, int m, int batch, double* work, int64_t ws, cudaStream_t st) {
+  const int smem = (int)(sizeof(double) * (size_t)(3 + NW) * m);
+  cudaError_t e = cudaFuncSetAttribute(syev_tridiag_kernel<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(batch * TC);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = TC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, syev_tridiag_kernel<SL>, A, m, work, ws);
+}
+
+// ---- 2. eigenvalues, grid (matrix, part of the spectrum) ----
+constexpr int VT = 128;        // threads (eigenvalues) per block of the bisection
+__global__ void __launch_bounds__(VT) syev_values_kernel(int m, double* __restrict__ work_all, int64_t work_stride,
+                                                         double* __restrict__ wall, int* __restrict__ info,
+                                                         int bisect) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  SyevWork W(work_all + blockIdx.x * work_stride, m);
+  double* ev = wall + blockIdx.x * (int64_t)m;
+  const double tnorm = W.meta[0];
   if (bisect) {
+    double* ds = sm;             // [m] scaled diagonal
+    double* e2s = ds + m;        // [m] scaled squared off-diagonal
+    float* dh = reinterpret_cast<float*>(e2s + m);   // [m] x 4: double-float copies of ds, e2s
+    float* dl = dh + m;
+    float* eh = dl + m;
+    float* el = eh + m;
     // scale T by 2^-sc (exact) so that its norm is at most 1
     const int sc = (tnorm > 0.0) ? ilogb(tnorm) + 1 : 0;
-    for (int i = tid; i < m; i += NT) {
-      const double di = ldexp(d[i], -sc), ei = ldexp(e[i], -sc);
+    for (int i = tid; i < m; i += VT) {
+      const double di = ldexp(W.d[i], -sc), ei = ldexp(W.e[i], -sc);
       ds[i] = di;
       e2s[i] = ei * ei;
       const float2 a = df_split(di), b = df_split(ei * ei);
       dh[i] = a.x; dl[i] = a.y; eh[i] = b.x; el[i] = b.y;
     }
     __syncthreads();
-    const double glo = ldexp(gbounds[0], -sc) - 0x1p-40, ghi = ldexp(gbounds[1], -sc) + 0x1p-40;
-    for (int k = tid; k < m; k += NT) {          // k-th smallest eigenvalue
+    const double glo = ldexp(W.meta[1], -sc) - 0x1p-40, ghi = ldexp(W.meta[2], -sc) + 0x1p-40;
+    const int k = blockIdx.y * VT + tid;          // k-th smallest eigenvalue
+    if (k < m) {
       double lo = glo, hi = ghi;
       for (int it = 0; it < 48; ++it) {
         const double mid = 0.5 * (lo + hi);
@@ -255,8 +359,17 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
       }
       ev[m - 1 - k] = ldexp(0.5 * (lo + hi), sc);
     }
-  } else if (tid == 0) {
-    // implicit QL without vectors (one thread)
+    if (blockIdx.y == 0 && tid == 0) info[blockIdx.x] = 0;
+    return;
+  }
+  // reference path: implicit QL without vectors (one thread), then a rank sort
+  if (blockIdx.y != 0) return;
+  double* v = sm;
+  double* w = v + m;
+  __shared__ int ql_fail;
+  for (int i = tid; i < m; i += VT) { v[i] = W.d[i]; w[i] = W.e[i]; }
+  __syncthreads();
+  if (tid == 0) {
     const double t = tnorm;
     int fail = 0;
     for (int l = 0; l < m; ++l) {
@@ -297,109 +410,129 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
     ql_fail = fail;
   }
   __syncthreads();
+  for (int t = tid; t < m; t += VT) {       // descending (rank of each eigenvalue; ties by index)
+    const double x = v[t];
+    int rk = 0;
+    for (int j = 0; j < m; ++j) rk += (v[j] > x) || (v[j] == x && j < t);
+    ev[rk] = x;
+  }
+  if (tid == 0) info[blockIdx.x] = ql_fail;
+}
 
-  // ---- 3. QL path: sort descending (rank of each eigenvalue; ties by index) ----
-  if (!bisect) {
-    for (int t = tid; t < m; t += NT) {
-      const double x = v[t];
-      int rk = 0;
-      for (int j = 0; j < m; ++j) rk += (v[j] > x) || (v[j] == x && j < t);
-      ev[rk] = x;
+// PCA rank of Sec. 4 from the descending eigenvalues sigma_k^2 (at least 1).
+__device__ int pca_rank_rule(const double* ev, int m, int mode, double thr) {
+  int p = m;
+  if (mode == RANN_PCA_ABS) {
+    p = 0;
+    for (int k = 0; k < m; ++k) if (sqrt(fmax(ev[k], 0.0)) > thr) ++p;
+  } else if (mode == RANN_PCA_VARIANCE) {
+    double tot = 0.0;
+    for (int k = 0; k < m; ++k) tot += fmax(ev[k], 0.0);
+    double cs = 0.0;
+    for (int k = 0; k < m; ++k) {
+      cs += fmax(ev[k], 0.0);
+      if (cs >= (1.0 - thr) * tot) { p = k + 1; break; }
     }
-    __syncthreads();
   }
-  // ---- rank rule (Sec. 4) ----
+  return max(p, 1);
+}
+
+// ---- 3./4. rank rule and inverse iteration, grid (matrix, part of the vectors) ----
+__global__ void __launch_bounds__(VT) syev_vectors_kernel(int m, double* __restrict__ work_all, int64_t work_stride,
+                                                          const double* __restrict__ wall, int* __restrict__ ranks,
+                                                          int mode, double thr) {
+  extern __shared__ double sm[];
+  double* d = sm;
+  double* e = d + m;
+  __shared__ int prank;
+  const int tid = threadIdx.x;
+  SyevWork W(work_all + blockIdx.x * work_stride, m);
+  const double* ev = wall + blockIdx.x * (int64_t)m;
   if (tid == 0) {
-    int p = m;
-    if (mode == RANN_PCA_ABS) {
-      p = 0;
-      for (int k = 0; k < m; ++k) if (sqrt(fmax(ev[k], 0.0)) > thr) ++p;
-    } else if (mode == RANN_PCA_VARIANCE) {
-      double tot = 0.0;
-      for (int k = 0; k < m; ++k) tot += fmax(ev[k], 0.0);
-      double cs = 0.0;
-      for (int k = 0; k < m; ++k) {
-        cs += fmax(ev[k], 0.0);
-        if (cs >= (1.0 - thr) * tot) { p = k + 1; break; }
-      }
-    }
-    prank = max(p, 1);
+    prank = pca_rank_rule(ev, m, mode, thr);
+    if (blockIdx.y == 0) ranks[blockIdx.x] = prank;
   }
+  for (int i = tid; i < m; i += VT) { d[i] = W.d[i]; e[i] = W.e[i]; }
   __syncthreads();
   const int p = prank;
-
-  // ---- 4. eigenvectors of T by inverse iteration ----
-  const double tolp = 2.2e-16 * tnorm + 1e-300;
-  double* u0 = LU;
-  double* u1 = LU + (int64_t)m * NT;
-  double* u2 = LU + 2 * (int64_t)m * NT;
-  double* ml = LU + 3 * (int64_t)m * NT;
-  double* xv = LU + 4 * (int64_t)m * NT;
-  for (int k0 = 0; k0 < p; k0 += NT) {
-    const int k = k0 + tid;
-    if (k < p) {
-      const double lam = ev[k];
-      // LU of T - lam I with partial pivoting.  A row swap at step i is coded
-      // in the multiplier as -(mult + 4) (|mult| <= 1 either way).
-      double cd = d[0] - lam, cs = (m > 1) ? e[0] : 0.0;
-      for (int i = 0; i + 1 < m; ++i) {
-        const double sub = e[i];
-        const double nd = d[i + 1] - lam, ns = (i + 2 < m) ? e[i + 1] : 0.0;
-        double mult, a0, a1, a2;
-        const bool swap = fabs(sub) > fabs(cd);
-        if (!swap) {
-          if (fabs(cd) < tolp) cd = (cd < 0.0) ? -tolp : tolp;
-          mult = sub / cd;
-          a0 = cd; a1 = cs; a2 = 0.0;
-          cd = nd - mult * cs;
-          cs = ns;
-        } else {
-          mult = cd / sub;
-          a0 = sub; a1 = nd; a2 = ns;
-          cd = cs - mult * nd;
-          cs = -mult * ns;
-        }
-        u0[(int64_t)i * NT + tid] = a0;
-        u1[(int64_t)i * NT + tid] = a1;
-        u2[(int64_t)i * NT + tid] = a2;
-        ml[(int64_t)i * NT + tid] = swap ? -(mult + 4.0) : mult;
-      }
+  const int k = blockIdx.y * VT + tid;
+  if (k >= p) return;
+  const double tolp = 2.2e-16 * W.meta[0] + 1e-300;
+  const int64_t mm = (int64_t)m * m;
+  double* u0 = W.LU + k;                 // entry i at [i * m]
+  double* u1 = u0 + mm;
+  double* u2 = u1 + mm;
+  double* ml = u2 + mm;
+  double* xv = ml + mm;
+  const double lam = ev[k];
+  // LU of T - lam I with partial pivoting.  A row swap at step i is coded
+  // in the multiplier as -(mult + 4) (|mult| <= 1 either way).
+  double cd = d[0] - lam, cs = (m > 1) ? e[0] : 0.0;
+  for (int i = 0; i + 1 < m; ++i) {
+    const double sub = e[i];
+    const double nd = d[i + 1] - lam, ns = (i + 2 < m) ? e[i + 1] : 0.0;
+    double mult, a0, a1, a2;
+    const bool swap = fabs(sub) > fabs(cd);
+    if (!swap) {
       if (fabs(cd) < tolp) cd = (cd < 0.0) ? -tolp : tolp;
-      u0[(int64_t)(m - 1) * NT + tid] = cd;
-      for (int i = 0; i < m; ++i) xv[(int64_t)i * NT + tid] = start_entry(i, k);
-      for (int it = 0; it < 2; ++it) {
-        for (int i = 0; i + 1 < m; ++i) {      // apply the row swaps and L^{-1}
-          double mc = ml[(int64_t)i * NT + tid];
-          double xi = xv[(int64_t)i * NT + tid], xn = xv[(int64_t)(i + 1) * NT + tid];
-          if (mc <= -3.0) {
-            mc = -mc - 4.0;
-            const double tmp = xi; xi = xn; xn = tmp;
-          }
-          xv[(int64_t)i * NT + tid] = xi;
-          xv[(int64_t)(i + 1) * NT + tid] = xn - mc * xi;
-        }
-        double x1 = 0.0, x2 = 0.0, amax = 0.0;
-        for (int i = m - 1; i >= 0; --i) {      // U^{-1}
-          double s = xv[(int64_t)i * NT + tid];
-          if (i + 1 < m) s -= u1[(int64_t)i * NT + tid] * x1;
-          if (i + 2 < m) s -= u2[(int64_t)i * NT + tid] * x2;
-          const double xi = s / u0[(int64_t)i * NT + tid];
-          xv[(int64_t)i * NT + tid] = xi;
-          x2 = x1;
-          x1 = xi;
-          amax = fmax(amax, fabs(xi));
-        }
-        const double sc = (amax > 0.0 && amax < 1e300) ? 1.0 / amax : 1.0;
-        for (int i = 0; i < m; ++i) xv[(int64_t)i * NT + tid] *= sc;
-      }
-      double nrm = 0.0;
-      for (int i = 0; i < m; ++i) { const double x = xv[(int64_t)i * NT + tid]; nrm = fma(x, x, nrm); }
-      const double inv = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
-      for (int i = 0; i < m; ++i) Z[(int64_t)k * m + i] = xv[(int64_t)i * NT + tid] * inv;
+      mult = sub / cd;
+      a0 = cd; a1 = cs; a2 = 0.0;
+      cd = nd - mult * cs;
+      cs = ns;
+    } else {
+      mult = cd / sub;
+      a0 = sub; a1 = nd; a2 = ns;
+      cd = cs - mult * nd;
+      cs = -mult * ns;
     }
+    u0[(int64_t)i * m] = a0;
+    u1[(int64_t)i * m] = a1;
+    u2[(int64_t)i * m] = a2;
+    ml[(int64_t)i * m] = swap ? -(mult + 4.0) : mult;
   }
-  __syncthreads();
-  // ---- classical Gram-Schmidt, twice, in descending order ----
+  if (fabs(cd) < tolp) cd = (cd < 0.0) ? -tolp : tolp;
+  u0[(int64_t)(m - 1) * m] = cd;
+  for (int i = 0; i < m; ++i) xv[(int64_t)i * m] = start_entry(i, k);
+  for (int it = 0; it < 2; ++it) {
+    for (int i = 0; i + 1 < m; ++i) {      // apply the row swaps and L^{-1}
+      double mc = ml[(int64_t)i * m];
+      double xi = xv[(int64_t)i * m], xn = xv[(int64_t)(i + 1) * m];
+      if (mc <= -3.0) {
+        mc = -mc - 4.0;
+        const double tmp = xi; xi = xn; xn = tmp;
+      }
+      xv[(int64_t)i * m] = xi;
+      xv[(int64_t)(i + 1) * m] = xn - mc * xi;
+    }
+    double x1 = 0.0, x2 = 0.0, amax = 0.0;
+    for (int i = m - 1; i >= 0; --i) {      // U^{-1}
+      double s = xv[(int64_t)i * m];
+      if (i + 1 < m) s -= u1[(int64_t)i * m] * x1;
+      if (i + 2 < m) s -= u2[(int64_t)i * m] * x2;
+      const double xi = s / u0[(int64_t)i * m];
+      xv[(int64_t)i * m] = xi;
+      x2 = x1;
+      x1 = xi;
+      amax = fmax(amax, fabs(xi));
+    }
+    const double sc = (amax > 0.0 && amax < 1e300) ? 1.0 / amax : 1.0;
+    for (int i = 0; i < m; ++i) xv[(int64_t)i * m] *= sc;
+  }
+  double nrm = 0.0;
+  for (int i = 0; i < m; ++i) { const double x = xv[(int64_t)i * m]; nrm = fma(x, x, nrm); }
+  const double inv = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
+  for (int i = 0; i < m; ++i) W.Z[(int64_t)k * m + i] = xv[(int64_t)i * m] * inv;
+}
+
+// ---- 4. classical Gram-Schmidt, twice, in descending order; one block per matrix ----
+__global__ void __launch_bounds__(NT) syev_orth_kernel(int m, double* __restrict__ work_all, int64_t work_stride,
+                                                       const int* __restrict__ ranks) {
+  __shared__ double red[33];
+  extern __shared__ double sm[];
+  double* coef = sm;           // [m]
+  SyevWork W(work_all + blockIdx.x * work_stride, m);
+  double* Z = W.Z;
+  const int p = ranks[blockIdx.x], tid = threadIdx.x;
   for (int k = 1; k < p; ++k) {
     double* zk = Z + (int64_t)k * m;
     for (int pass = 0; pass < 2; ++pass) {
@@ -407,12 +540,12 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
         const double* zj = Z + (int64_t)j * m;
         double s = 0.0;
         for (int i = 0; i < m; ++i) s = fma(zj[i], zk[i], s);
-        d[j] = s;
+        coef[j] = s;
       }
       __syncthreads();
       for (int i = tid; i < m; i += NT) {
         double s = zk[i];
-        for (int j = 0; j < k; ++j) s = fma(-d[j], Z[(int64_t)j * m + i], s);
+        for (int j = 0; j < k; ++j) s = fma(-coef[j], Z[(int64_t)j * m + i], s);
         zk[i] = s;
       }
       __syncthreads();
@@ -424,45 +557,102 @@ __global__ void __launch_bounds__(NT) syev_kernel(double* __restrict__ Aall, int
     for (int i = tid; i < m; i += NT) zk[i] *= inv;
     __syncthreads();
   }
-  // ---- 5. back-transformation V = H_0 H_1 ... H_{m-3} Z, one warp per vector ----
-  for (int c = warp; c < p; c += NW) {
-    double* z = Z + (int64_t)c * m;
-    for (int k = m - 3; k >= 0; --k) {
-      const double bt = beta[k];
-      if (bt == 0.0) continue;
-      const double* vk = A + (int64_t)k * m + k + 1;
-      double s = 0.0;
-      for (int i = lane; i < m - k - 1; i += 32) s = fma(vk[i], z[k + 1 + i], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      s *= bt;
-      for (int i = lane; i < m - k - 1; i += 32) z[k + 1 + i] = fma(-s, vk[i], z[k + 1 + i]);
-      __syncwarp();
-    }
+}
+
+// ---- 5. back-transformation V = H_0 H_1 ... H_{m-3} Z, one warp per vector ----
+constexpr int BW = 8;          // warps (vectors) per block
+__global__ void __launch_bounds__(BW * 32) syev_back_kernel(const double* __restrict__ Aall, int m,
+                                                            double* __restrict__ work_all, int64_t work_stride,
+                                                            const int* __restrict__ ranks) {
+  SyevWork W(work_all + blockIdx.x * work_stride, m);
+  const double* A = Aall + blockIdx.x * (int64_t)m * m;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.y * BW + (threadIdx.x >> 5);
+  if (c >= ranks[blockIdx.x]) return;
+  double* z = W.Z + (int64_t)c * m;
+  for (int k = m - 3; k >= 0; --k) {
+    const double bt = W.beta[k];
+    if (bt == 0.0) continue;
+    const double* vk = A + (int64_t)k * m + k + 1;
+    double s = 0.0;
+    for (int i = lane; i < m - k - 1; i += 32) s = fma(vk[i], z[k + 1 + i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    s *= bt;
+    for (int i = lane; i < m - k - 1; i += 32) z[k + 1 + i] = fma(-s, vk[i], z[k + 1 + i]);
+    __syncwarp();
+  }
+}
+
+// G <- V: column c of G is eigenvector c (c < p), zero beyond; 32 x 32 tiles.
+__global__ void __launch_bounds__(256) syev_output_kernel(double* __restrict__ Aall, int m,
+                                                          const double* __restrict__ work_all, int64_t work_stride,
+                                                          const int* __restrict__ ranks) {
+  __shared__ double tile[32][33];
+  const double* Z = work_all + blockIdx.z * work_stride;
+  double* A = Aall + blockIdx.z * (int64_t)m * m;
+  const int p = ranks[blockIdx.z];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    const int a = e & 31, b = e >> 5;      // read Z[c0 + b][r0 + a]
+    const int c = c0 + b, r = r0 + a;
+    tile[b][a] = (c < p && r < m) ? Z[(int64_t)c * m + r] : 0.0;
   }
   __syncthreads();
-  // ---- output ----
-  for (int c = tid; c < m; c += NT) wall[(int64_t)blockIdx.x * m + c] = ev[c];
-  for (int64_t e2 = tid; e2 < (int64_t)m * m; e2 += NT) {
-    const int r = (int)(e2 / m), c = (int)(e2 % m);
-    A[e2] = (c < p) ? Z[(int64_t)c * m + r] : 0.0;
-  }
-  if (tid == 0) {
-    info[blockIdx.x] = ql_fail;
-    ranks[blockIdx.x] = p;
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    const int a = e & 31, b = e >> 5;      // write A[r0 + b][c0 + a]
+    const int r = r0 + b, c = c0 + a;
+    if (r < m && c < m) A[(int64_t)r * m + c] = tile[a][b];
   }
 }
 
 }  // namespace
 
-int64_t syevd_work_doubles(int m) { return (int64_t)m * m + 5 * (int64_t)m * NT; }
+int64_t syevd_work_doubles(int m) { return 6 * (int64_t)m * m + 3 * (int64_t)m + 8; }
 
-cudaError_t launch_syevd(double* d_A, int m, int batch, double* d_w, double* d_work, int* d_info, int* d_ranks,
-                         int mode, double thr, int bisect, cudaStream_t st) {
-  if (batch == 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * 10 * (size_t)m;
-  cudaError_t e = cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  syev_kernel<<<batch, NT, smem, st>>>(d_A, m, (int64_t)m * m, d_w, d_work, syevd_work_doubles(m), d_info,
-                                       d_ranks, mode, thr, bisect);
+cudaError_t launch_syev_phase(const SyevBatch& b, int phase, cudaStream_t st) {
+  if (b.batch == 0) return cudaSuccess;
+  const int m = b.m;
+  const int64_t ws = syevd_work_doubles(m);
+  cudaError_t e = cudaSuccess;
+  switch (phase) {
+    case 0: {
+      const int sl = (m - 1 + 31) / 32;       // 32-column slots of the longest row
+      if (sl <= 4) e = launch_tridiag<4>(b.A, m, b.batch, b.work, ws, st);
+      else if (sl <= 8) e = launch_tridiag<8>(b.A, m, b.batch, b.work, ws, st);
+      else if (sl <= 12) e = launch_tridiag<12>(b.A, m, b.batch, b.work, ws, st);
+      else if (sl <= 16) e = launch_tridiag<16>(b.A, m, b.batch, b.work, ws, st);
+      else if (sl <= 24) e = launch_tridiag<24>(b.A, m, b.batch, b.work, ws, st);
+      else e = launch_tridiag<32>(b.A, m, b.batch, b.work, ws, st);
+      if (e != cudaSuccess) return e;
+      break;
+    }
+    case 1: {
+      const int smem = (int)(sizeof(double) * 4 * m);
+      if ((e = cudaFuncSetAttribute(syev_values_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+        return e;
+      syev_values_kernel<<<dim3(b.batch, b.bisect ? (m + VT - 1) / VT : 1), VT, smem, st>>>(m, b.work, ws, b.w,
+                                                                                          b.info, b.bisect);
+      break;
+    }
+    case 2: {
+      const int smem = (int)(sizeof(double) * 2 * m);
+      syev_vectors_kernel<<<dim3(b.batch, (m + VT - 1) / VT), VT, smem, st>>>(m, b.work, ws, b.w, b.ranks, b.mode,
+                                                                             b.thr);
+      break;
+    }
+    case 3: {
+      const int smem = (int)(sizeof(double) * m);
+      syev_orth_kernel<<<b.batch, NT, smem, st>>>(m, b.work, ws, b.ranks);
+      break;
+    }
+    case 4: {
+      syev_back_kernel<<<dim3(b.batch, (m + BW - 1) / BW), BW * 32, 0, st>>>(b.A, m, b.work, ws, b.ranks);
+      const int nt = (m + 31) / 32;
+      syev_output_kernel<<<dim3(nt, nt, b.batch), 256, 0, st>>>(b.A, m, b.work, ws, b.ranks);
+      break;
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
