@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
   double* v = sm;              // [m] reflector
   double* w = v + m;           // [m] symmetric product
   double* wl = w + m;          // [m] this block's partial product (read by the cluster)
-  double* part = wl + m;       // [NW][m] per-warp partials
+  double* wdot = wl + m;       // [m] dot products of the rows this block owns
+  double* part = wdot + m;     // [NW][m] per-warp partials
   __shared__ double red[33];
   const int mat = blockIdx.x / TC;
   const int rank = (int)cluster.block_rank();
@@ -219,9 +220,7 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
           dot = fma(x[t], (j < c) ? v[j] : 0.0, dot);
         }
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-#pragma unroll
-        for (int t = 0; t < SL; ++t)
-          if (lane + 32 * t == c) acc[t] += dot;
+        if (lane == 0) wdot[c] = dot;          // row c belongs to this warp alone
       }
 #pragma unroll
       for (int t = 0; t < SL; ++t)
@@ -230,6 +229,7 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
       for (int j = tid; j < n1; j += NT) {
         double s = 0.0;
         for (int q = 0; q < NW; ++q) s += part[q * m + j];
+        if ((j % (TC * NW)) / NW == rank) s += wdot[j];   // dot of a row this block owns
         wl[j] = s;
       }
       cluster.sync();                          // partials visible to the cluster
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
 
 template <int SL>
 cudaError_t launch_tridiag(double* A, int m, int batch, double* work, int64_t ws, cudaStream_t st) {
-  const int smem = (int)(sizeof(double) * (size_t)(3 + NW) * m);
+  const int smem = (int)(sizeof(double) * (size_t)(4 + NW) * m);
   cudaError_t e = cudaFuncSetAttribute(syev_tridiag_kernel<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -525,36 +525,51 @@ __global__ void __launch_bounds__(VT) syev_vectors_kernel(int m, double* __restr
 }
 
 // ---- 4. classical Gram-Schmidt, twice, in descending order; one block per matrix ----
+// z_k is staged in shared memory; the k coefficients z_j . z_k are one warp
+// each (lanes over the entries, coalesced rows, fixed-order shuffle sum), and
+// the subtraction z_k -= sum_j c_j z_j is one thread per entry.
 __global__ void __launch_bounds__(NT) syev_orth_kernel(int m, double* __restrict__ work_all, int64_t work_stride,
                                                        const int* __restrict__ ranks) {
   __shared__ double red[33];
   extern __shared__ double sm[];
   double* coef = sm;           // [m]
+  double* zs = coef + m;       // [m] current vector
   SyevWork W(work_all + blockIdx.x * work_stride, m);
   double* Z = W.Z;
-  const int p = ranks[blockIdx.x], tid = threadIdx.x;
+  const int p = ranks[blockIdx.x], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int k = 1; k < p; ++k) {
     double* zk = Z + (int64_t)k * m;
+    for (int i = tid; i < m; i += NT) zs[i] = zk[i];
+    __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
-      for (int j = tid; j < k; j += NT) {
+      for (int j = warp; j < k; j += NW) {
         const double* zj = Z + (int64_t)j * m;
-        double s = 0.0;
-        for (int i = 0; i < m; ++i) s = fma(zj[i], zk[i], s);
-        coef[j] = s;
+        double s0 = 0.0, s1 = 0.0;
+        int i = lane;
+        for (; i + 32 < m; i += 64) { s0 = fma(zj[i], zs[i], s0); s1 = fma(zj[i + 32], zs[i + 32], s1); }
+        if (i < m) s0 = fma(zj[i], zs[i], s0);
+        double s = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) coef[j] = s;
       }
       __syncthreads();
       for (int i = tid; i < m; i += NT) {
-        double s = zk[i];
-        for (int j = 0; j < k; ++j) s = fma(-coef[j], Z[(int64_t)j * m + i], s);
-        zk[i] = s;
+        double s0 = zs[i], s1 = 0.0;
+        int j = 0;
+        for (; j + 1 < k; j += 2) {
+          s0 = fma(-coef[j], Z[(int64_t)j * m + i], s0);
+          s1 = fma(-coef[j + 1], Z[(int64_t)(j + 1) * m + i], s1);
+        }
+        if (j < k) s0 = fma(-coef[j], Z[(int64_t)j * m + i], s0);
+        zs[i] = s0 + s1;
       }
       __syncthreads();
     }
     double loc = 0.0;
-    for (int i = tid; i < m; i += NT) loc = fma(zk[i], zk[i], loc);
+    for (int i = tid; i < m; i += NT) loc = fma(zs[i], zs[i], loc);
     const double nn = block_sum(loc, red);
     const double inv = (nn > 0.0) ? 1.0 / sqrt(nn) : 0.0;
-    for (int i = tid; i < m; i += NT) zk[i] *= inv;
+    for (int i = tid; i < m; i += NT) zk[i] = zs[i] * inv;
     __syncthreads();
   }
 }
@@ -641,7 +656,7 @@ cudaError_t launch_syev_phase(const SyevBatch& b, int phase, cudaStream_t st) {
       break;
     }
     case 3: {
-      const int smem = (int)(sizeof(double) * m);
+      const int smem = (int)(sizeof(double) * 2 * m);
       syev_orth_kernel<<<b.batch, NT, smem, st>>>(m, b.work, ws, b.ranks);
       break;
     }
