@@ -25,11 +25,13 @@ cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, 
                              const double* d_dmax, int df, cudaStream_t st);
 cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, int df, cudaStream_t st);
 cudaError_t launch_split(const double* d_x, float2* d_x2, int64_t n, cudaStream_t st);
-cudaError_t launch_rowdot_df(const SubDev* d_sub, const int* d_rtiles, int nrtiles, const float2* d_B2,
-                             const float2* d_x2, float2* d_yp, cudaStream_t st);
+cudaError_t launch_split_pad(const SubDev* d_sub, int J, const double* d_x, float2* d_x2p, cudaStream_t st);
+cudaError_t launch_rowdot_df(const SubDev* d_sub, const int* d_rtiles, int nrtiles, int tile_rows,
+                             const float2* d_B2, const float2* d_x2p, float2* d_yp, cudaStream_t st);
 cudaError_t launch_matvec_HT_df(const ProbDev& P, const SubDev* d_sub, int J, const int* d_rtiles, int nrtiles,
-                                const int* d_tile0, const int* d_cov, int Gmax, const float2* d_B2,
+                                int tile_rows, const int* d_tile0, const int* d_cov, int Gmax, const float2* d_B2,
                                 const float2* d_yp, double* d_part, double* d_z, int maxP, cudaStream_t st);
+constexpr int DF_TILE_ROWS = 128;  // rows per block of the direct-load double-float matvec
 cudaError_t launch_split_lower(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st);
 cudaError_t launch_schwarz_gather_df(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
                                      const int64_t* d_s_off, const double* d_r, float2* d_g2, cudaStream_t st);
@@ -100,19 +102,20 @@ enum KId {
   K_POINTS, K_ASSEMBLE, K_RHS, K_GRAM, K_SYMM, K_EIG, K_PROJECT, K_PAIRGRAM, K_LOCALASM, K_ADDDIAG,
   K_CHOL, K_TRTRI, K_GATHER, K_TRMV_L, K_TRMV_U, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL,
   K_SPLIT, K_MATVEC_H_DF, K_MATVEC_HT_DF, K_GATHER_DF, K_TRMV_L_DF, K_TRMV_U_DF, K_OZ_SPLIT, K_GRAM_OZ,
-  K_PROJECT_OZ, K_EIG_VAL, K_EIG_VEC, K_EIG_ORTH, K_EIG_BACK, K_COUNT
+  K_PROJECT_OZ, K_EIG_VAL, K_EIG_VEC, K_EIG_ORTH, K_EIG_BACK, K_GRAMROWS, K_GRAMOP,
+  K_COUNT
 };
 static const char* const KNAMES[K_COUNT] = {
   "points", "assemble", "rhs", "gram", "symmetrize", "eig_tridiag", "project", "pair_gram", "local_assemble",
   "add_diag", "cholesky", "trtri", "schwarz_gather", "trmv_lower", "trmv_upper", "schwarz_combine",
   "matvec_H", "matvec_HT", "dot", "vector", "eval", "split_df32", "matvec_H_df32", "matvec_HT_df32",
-  "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32", "ozaki_split", "gram_ozaki", "project_ozaki", "eig_values", "eig_vectors", "eig_orth", "eig_back"};
+  "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32", "ozaki_split", "gram_ozaki", "project_ozaki", "eig_values", "eig_vectors", "eig_orth", "eig_back", "gram_rows", "gramop_df32"};
 
 // Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
 // 1 = float64-ALU-bound (algorithmic flops count), 2 = bf16-tensor-core-bound
 // (the flops of the digit-slice products count).
 static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1,
-                                     0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1};
+                                     0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1, 0, 0};
 
 struct Prof {
   bool on = false;
@@ -160,8 +163,21 @@ struct rann_dd_handle {
   double* d_part = nullptr;
   double* d_yscratch = nullptr;   // N
   float2* d_B2 = nullptr;         // reduced blocks as double-float pairs (inner Krylov operator)
-  float2* d_x2 = nullptr;         // DoF
-  float2* d_y2 = nullptr;         // N
+  float2* d_x2 = nullptr;         // sum_j P_j: x as double-float pairs, each block's part 16-byte aligned
+  float2* d_y2 = nullptr;         // rows_total: per-block row products B_j x_j
+  int* d_dtiles = nullptr;        // (block, first row) tiles of the direct-load double-float matvec
+  int ndtiles = 0;
+  int* d_dtile0 = nullptr;
+  double* d_dpart = nullptr;
+  int nsm = 1;
+  // normal matrix as block rows (inner operator of precision mode 1, built by setup_precond)
+  bool gram_ready = false;
+  GramRows gram{};
+  std::vector<void*> gram_allocs;
+  int* d_gtile = nullptr;
+  int ngtile = 0;
+  double gram_entries = 0;        // sum_k p_k n_k
+  int gram_maxn2 = 0;
   int inner_df = 1;               // precision mode: 1 = double-float preconditioner set-up and inner iterations
   // precond
   int prec_kind = -1;
@@ -231,6 +247,7 @@ static void prof_resolve(rann_dd_handle* h) {
     }                                                                       \
   } while (0)
 #define KL(h, kid, nkern, expr) KLA(h, kid, nkern, 0, 0, expr)
+#define TRY(x) do { rann_status _s = (x); if (_s != RANN_OK) return _s; } while (0)
 
 static cudaError_t dalloc(rann_dd_handle* h, void** p, size_t bytes) {
   *p = nullptr;
@@ -310,6 +327,11 @@ extern "C" rann_status rann_dd_create(const rann_dd_desc* d, void* stream, rann_
   }
   rann_dd_handle* h = new rann_dd_handle();
   h->st = (cudaStream_t)stream;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (h->nsm < 1) h->nsm = 1;
+  }
   ProbDev& P = h->P;
   P.dim = d->dim; P.ns = ns; P.op = d->op; P.coef = d->coef; P.g_kind = d->g_kind; P.m = d->neurons;
   P.c0 = d->c0; P.nu = d->nu; P.coef_value = d->coef_value; P.eps = d->eps; P.rho = d->rho; P.f0 = d->f0;
@@ -595,6 +617,7 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   }
   // ranks (Sec. 4): sigma_k = sqrt(max(lambda_k, 0))
   int64_t woff = 0, boff = 0;
+  int poff = 0;
   h->maxP = 0;
   for (int j = 0; j < J; ++j) {
     // the eigensolver applied the rank rule (it forms only the kept eigenvectors)
@@ -608,8 +631,10 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     S.P = p + (p & 1);
     S.woff = woff;
     S.boff = boff;
+    S.poff = poff;
     woff += p;
     boff += (int64_t)S.N * S.P;
+    poff += S.P;
     h->maxP = std::max(h->maxP, S.P);
     if (ranks_host) ranks_host[j] = p;
   }
@@ -683,13 +708,25 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   }
   t0[J] = (int)rt.size() / 2;
   h->nrtiles = t0[J];
+  std::vector<int> dft, dft0(J + 1, 0);
+  for (int j = 0; j < J; ++j) {
+    dft0[j] = (int)dft.size() / 2;
+    for (int r0 = 0; r0 < h->subs[j].N; r0 += DF_TILE_ROWS) { dft.push_back(j); dft.push_back(r0); }
+  }
+  dft0[J] = (int)dft.size() / 2;
+  h->ndtiles = dft0[J];
   if (h->d_rtiles) {
     dfree(h, h->d_rtiles); dfree(h, h->d_tile0); dfree(h, h->d_part); dfree(h, h->d_yscratch);
     dfree(h, h->d_B2); dfree(h, h->d_x2); dfree(h, h->d_y2);
+    dfree(h, h->d_dtiles); dfree(h, h->d_dtile0); dfree(h, h->d_dpart);
   }
   CK(dalloc(h, (void**)&h->d_B2, sizeof(float2) * (size_t)std::max<int64_t>(boff, 1)));
-  CK(dalloc(h, (void**)&h->d_x2, sizeof(float2) * (size_t)std::max<int64_t>(h->dof, 1)));
+  CK(dalloc(h, (void**)&h->d_x2, sizeof(float2) * (size_t)std::max(poff, 1)));
   CK(dalloc(h, (void**)&h->d_y2, sizeof(float2) * (size_t)std::max<int64_t>(h->rows_total, 1)));
+  CK(dupload(h, &h->d_dtiles, dft));
+  CK(dupload(h, &h->d_dtile0, dft0));
+  CK(dalloc(h, (void**)&h->d_dpart, sizeof(double) * (size_t)std::max(h->ndtiles, 1) * h->maxP));
+
   KLA(h, K_SPLIT, 1, 16.0 * boff, 0, launch_split(h->d_B, h->d_B2, boff, h->st));
   CK(dupload(h, &h->d_rtiles, rt));
   CK(dupload(h, &h->d_tile0, t0));
@@ -729,13 +766,19 @@ extern "C" rann_status rann_dd_normal_matvec(rann_dd_handle* h, const double* x_
 
 // Inner-iteration operator: z = H^T H x with double-float blocks.
 static rann_status normal_matvec_fast(rann_dd_handle* h, const double* x, double* z) {
-  KLA(h, K_SPLIT, 1, 24.0 * h->dof, 0, launch_split(x, h->d_x2, h->dof, h->st));
+  if (h->gram_ready) {
+    // z_k = sum_l G_kl x_l from the block rows of H^T H
+    KLA(h, K_GRAMOP, 1, 8.0 * (h->gram_entries + h->dof), 2.0 * h->gram_entries,
+        launch_gram_matvec(h->gram, h->J, h->d_gtile, h->ngtile, h->gram_maxn2, x, z, h->st));
+    return RANN_OK;
+  }
   // y_j = B_j x_j row by row (per block), then z_j = B_j^T y with y summed over the blocks holding each point
+  KLA(h, K_SPLIT, 1, 24.0 * h->dof, 0, launch_split_pad(h->d_sub, h->J, x, h->d_x2, h->st));
   KLA(h, K_MATVEC_H_DF, 1, 8.0 * (h->sumNp + h->rows_total + h->dof), 2.0 * h->sumNp,
-      launch_rowdot_df(h->d_sub, h->d_rtiles, h->nrtiles, h->d_B2, h->d_x2, h->d_y2, h->st));
+      launch_rowdot_df(h->d_sub, h->d_dtiles, h->ndtiles, DF_TILE_ROWS, h->d_B2, h->d_x2, h->d_y2, h->st));
   KLA(h, K_MATVEC_HT_DF, 2, 8.0 * (h->sumNp + 2.0 * h->rows_total + h->dof), 2.0 * h->sumNp,
-      launch_matvec_HT_df(h->P, h->d_sub, h->J, h->d_rtiles, h->nrtiles, h->d_tile0, h->d_cov, h->Gmax, h->d_B2,
-                          h->d_y2, h->d_part, z, h->maxP, h->st));
+      launch_matvec_HT_df(h->P, h->d_sub, h->J, h->d_dtiles, h->ndtiles, DF_TILE_ROWS, h->d_dtile0, h->d_cov,
+                          h->Gmax, h->d_B2, h->d_y2, h->d_dpart, z, h->maxP, h->st));
   return RANN_OK;
 }
 
@@ -745,6 +788,60 @@ static bool boxes_meet(const SubDev& a, const SubDev& b, int dim) {
   for (int i = 0; i < dim; ++i)
     if (std::max(a.lo[i], b.lo[i]) >= std::min(a.lo[i] + a.n[i], b.lo[i] + b.n[i])) return false;
   return true;
+}
+
+// Block rows R_k = [G_kl]_l of H^T H in double-float from the pair Gram buffer.
+static rann_status build_gram_rows(rann_dd_handle* h, const std::vector<int64_t>& pair_off) {
+  const int J = h->J;
+  const auto& S = h->subs;
+  for (int k = 0; k < J; ++k) {     // the row kernel stages at most GRAM_MAX_NBR neighbour segments
+    int nq = 0;
+    for (int l = 0; l < J; ++l) nq += (k <= l ? pair_off[(size_t)k * J + l] : pair_off[(size_t)l * J + k]) >= 0;
+    if (nq > GRAM_MAX_NBR) return RANN_OK;
+  }
+  std::vector<int> p(J), n2(J), nptr(1, 0), nl, ncol, ntr, poff(J);
+  std::vector<int64_t> roff(J), woff(J), noff;
+  std::vector<int> gt;
+  int64_t ro = 0;
+  int maxp = 0, maxn2 = 0;
+  h->gram_entries = 0;
+  for (int k = 0; k < J; ++k) {
+    int col = 0;
+    for (int l = 0; l < J; ++l) {
+      const int64_t off = k <= l ? pair_off[(size_t)k * J + l] : pair_off[(size_t)l * J + k];
+      if (off < 0) continue;
+      nl.push_back(l); ncol.push_back(col); noff.push_back(off); ntr.push_back(k > l ? 1 : 0);
+      col += S[l].P;
+      h->gram_entries += (double)S[k].p * S[l].p;
+    }
+    nptr.push_back((int)nl.size());
+    p[k] = S[k].p;
+    n2[k] = col;
+    roff[k] = ro; woff[k] = S[k].woff; poff[k] = S[k].poff;
+    ro += (int64_t)p[k] * n2[k];
+    maxp = std::max(maxp, p[k]);
+    maxn2 = std::max(maxn2, n2[k]);
+    for (int c0 = 0; c0 < p[k]; c0 += GRAM_TILE_ROWS) { gt.push_back(k); gt.push_back(c0); }
+  }
+  auto up = [&](auto** dst, const auto& v) -> cudaError_t {
+    cudaError_t e = dupload(h, dst, v);
+    if (e == cudaSuccess) h->gram_allocs.push_back((void*)*dst);
+    return e;
+  };
+  int *d_p, *d_n2, *d_nptr, *d_nl, *d_ncol, *d_ntr, *d_poff;
+  int64_t *d_roff, *d_woff, *d_noff;
+  CK(up(&d_p, p)); CK(up(&d_n2, n2)); CK(up(&d_nptr, nptr)); CK(up(&d_nl, nl)); CK(up(&d_ncol, ncol));
+  CK(up(&d_ntr, ntr)); CK(up(&d_roff, roff)); CK(up(&d_poff, poff)); CK(up(&d_woff, woff)); CK(up(&d_noff, noff));
+  CK(up(&h->d_gtile, gt));
+  h->ngtile = (int)gt.size() / 2;
+  h->gram_maxn2 = maxn2;
+  float2* d_R2;
+  CK(dalloc(h, (void**)&d_R2, sizeof(float2) * (size_t)std::max<int64_t>(ro, 2)));
+  h->gram_allocs.push_back(d_R2);
+  h->gram = GramRows{d_p, d_n2, d_roff, d_poff, d_woff, d_nptr, d_nl, d_ncol, d_noff, d_ntr, d_R2};
+  KLA(h, K_GRAMROWS, 1, 16.0 * (double)ro, 0, launch_gramrows_build(h->gram, h->d_pairbuf, J, maxp, maxn2, h->st));
+  h->gram_ready = true;
+  return RANN_OK;
 }
 
 extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int overlap_level) {
@@ -759,6 +856,9 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
                   (void*)h->d_p_off, (void*)h->d_X2mats, (void*)h->d_g2, (void*)h->d_ys2})
     dfree(h, p);
   h->d_mats = nullptr; h->d_Amats = nullptr; h->d_Xmats = nullptr; h->d_X2mats = nullptr;
+  for (void* p : h->gram_allocs) dfree(h, p);
+  h->gram_allocs.clear();
+  h->gram_ready = false;
   h->n_shifted = 0;
   h->prec_kind = kind;
   if (kind == RANN_PREC_NONE) return RANN_OK;
@@ -780,15 +880,14 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   std::vector<std::pair<int64_t, int64_t>> ridx_ranges;   // (start in ridx for A rows, for B rows)
   int64_t pbuf = 0;
   std::vector<std::pair<int, int>> pairs;
-  for (int i = 0; i < J; ++i)
-    for (int q = h->set_ptr[i]; q < h->set_ptr[i + 1]; ++q)
-      for (int q2 = h->set_ptr[i]; q2 < h->set_ptr[i + 1]; ++q2) {
-        int k = h->set_sub[q], l = h->set_sub[q2];
-        if (k > l || pair_off[(size_t)k * J + l] != -1 || !boxes_meet(S[k], S[l], dim)) continue;
-        pair_off[(size_t)k * J + l] = pbuf;
-        pbuf += (int64_t)S[k].p * S[l].p;
-        pairs.push_back({k, l});
-      }
+  // every pair of boxes that meet (the blocks of H^T H; the local matrices A_i use those inside N(i))
+  for (int k = 0; k < J; ++k)
+    for (int l = k; l < J; ++l) {
+      if (!boxes_meet(S[k], S[l], dim)) continue;
+      pair_off[(size_t)k * J + l] = pbuf;
+      pbuf += (int64_t)S[k].p * S[l].p;
+      pairs.push_back({k, l});
+    }
   for (auto& pr : pairs) {
     const SubDev &a = S[pr.first], &b = S[pr.second];
     int lo[3], hi[3];
@@ -838,6 +937,7 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   CK(dupload(h, &d_tasks, tasks));
   if (h->inner_df) KLA(h, K_PAIRGRAM, 1, 0, h->pair_flops, launch_gemm_tn_df(d_tasks, (int)tasks.size(), h->st));
   else KLA(h, K_PAIRGRAM, 1, 0, h->pair_flops, launch_gemm_tn(d_tasks, (int)tasks.size(), h->st));
+  if (h->inner_df) TRY(build_gram_rows(h, pair_off));
   // local matrices A_i: table of block sources
   std::vector<CholMat> mats(J);
   std::vector<int64_t> tab;      // per (i, a, b): pair offset, or -1; sign bit 1<<62 marks transpose
@@ -1010,7 +1110,6 @@ static rann_status dot_host(rann_dd_handle* h, const double* x, const double* y,
   return RANN_OK;
 }
 
-#define TRY(x) do { rann_status _s = (x); if (_s != RANN_OK) return _s; } while (0)
 
 struct Workspace {
   rann_dd_handle* h;

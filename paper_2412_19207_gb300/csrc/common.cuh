@@ -38,11 +38,12 @@ struct SubDev {
   int N;                     // rows = prod n
   int p;                     // PCA rank
   int P;                     // padded row length of B_j (p rounded up to 2)
-  int pad_;
+  int poff;                  // offset of x_j in the padded (P_j-aligned) vector copy
   int64_t row0;              // offset of block j in the unreduced row storage (rows)
   int64_t woff;              // offset of W_j
   int64_t boff;              // offset of B_j in the reduced storage (doubles)
 };
+
 
 // Host-side helpers (api.cu).
 void rann_set_error(const char* fmt, ...);
@@ -101,6 +102,27 @@ int oz_slices();
 int oz_kpad(int K);
 cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, int maxKp, cudaStream_t st);
 cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, cudaStream_t st);
+
+// gramop.cu -- the normal matrix as double-float block rows R_k = [G_kl]_l
+constexpr int GRAM_TILE_ROWS = 8;    // rows of R_k per block of the row-dot kernel (one warp each)
+constexpr int GRAM_MAX_NBR = 27;     // most neighbours of a block row (3^3); more falls back to B^T (B x)
+struct GramRows {                    // device arrays
+  const int* p;                      // [J] p_k
+  const int* n2;                     // [J] row length of R_k: sum of P_l over its neighbours
+  const int64_t* roff;               // [J] offset of R_k in R2 (float2 units, even)
+  const int* poff;                   // [J] offset of x_k in the padded double-float copy of x
+  const int64_t* woff;               // [J] offset of x_k in x
+  const int* nbr_ptr;                // [J + 1] neighbour lists (boxes that meet box k, increasing l)
+  const int* nbr_l;                  // neighbour index l
+  const int* nbr_col;                // first column of block l in R_k (block l spans P_l columns)
+  const int64_t* nbr_off;            // offset of the stored Gram block of the pair in the pair buffer
+  const int* nbr_tr;                 // 1: stored as G_lk (p_l x p_k), read transposed
+  float2* R2;
+};
+cudaError_t launch_gramrows_build(const GramRows& g, const double* d_pairbuf, int J, int maxp, int maxn2,
+                                  cudaStream_t st);
+cudaError_t launch_gram_matvec(const GramRows& g, int J, const int* d_rtile, int nrtile, int maxn2,
+                               const double* d_x, double* d_z, cudaStream_t st);
 
 // eig.cu -- batched symmetric eigen-decomposition (float64)
 // Eigenpairs of `batch` m x m symmetric matrices A; ranks by the PCA rule (mode, thr);

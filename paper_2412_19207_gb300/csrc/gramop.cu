@@ -1,0 +1,106 @@
+// The normal matrix H^T H (Eq. (system_new), Sec. 3) as block rows for the
+// inner Krylov iterations: block k of z = H^T H x is
+//   z_k = sum_{l : box_l meets box_k} G_kl x_l,   G_kl = B_k^T B_l over the shared points,
+// the same Gram blocks the Schwarz local matrices A_i are assembled from.
+// Each block row R_k = [G_kl]_l (p_k rows; neighbour l, in increasing l,
+// spans P_l = p_l rounded up to even columns, zero-padded) is stored once in
+// double-float, so one application reads sum_k p_k n_k entries instead of B
+// twice and its rows (~3^d p entries) stream in full 16-byte loads.
+#include "common.cuh"
+#include "df32.cuh"
+
+namespace {
+
+// R2[roff_k + c * n2_k + col] from the pair buffer (k <= l stored p_k x p_l
+// row-major); neighbour l occupies P_l columns (zero beyond p_l).
+__global__ void gramrows_build_kernel(const GramRows g, const double* __restrict__ pairbuf, int k0) {
+  const int k = k0 + blockIdx.y;
+  const int p = g.p[k], n2 = g.n2[k];
+  const int64_t tot = (int64_t)p * n2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / n2), col = (int)(e % n2);
+    double v = 0.0;
+    for (int q = g.nbr_ptr[k]; q < g.nbr_ptr[k + 1]; ++q) {
+      const int c0 = g.nbr_col[q], pl = g.p[g.nbr_l[q]];
+      if (col >= c0 && col < c0 + pl + (pl & 1)) {
+        const int cc = col - c0;
+        const int64_t off = g.nbr_off[q];
+        if (cc < pl) v = g.nbr_tr[q] ? pairbuf[off + (int64_t)cc * p + c] : pairbuf[off + (int64_t)c * pl + cc];
+        break;
+      }
+    }
+    g.R2[g.roff[k] + e] = df_split(v);
+  }
+}
+
+// z[woff_k + c] = R_k[c, :] . [x_l]_l for GRAM_TILE_ROWS rows of block k: the
+// neighbours' entries of x are split into double-float pairs and staged in
+// shared memory in one flat pass (a small table maps each 16-byte column pair
+// to its neighbour), then one warp per row with 16-byte loads and two chains
+// per lane.
+__global__ void __launch_bounds__(256) gram_rowdot_kernel(const GramRows g, const int* __restrict__ rtile,
+                                                          const double* __restrict__ x, double* __restrict__ z) {
+  extern __shared__ float4 xs[];
+  __shared__ int seg_c4[GRAM_MAX_NBR + 1], seg_p[GRAM_MAX_NBR];
+  __shared__ int64_t seg_w[GRAM_MAX_NBR];
+  const int k = rtile[2 * blockIdx.x], c0 = rtile[2 * blockIdx.x + 1];
+  const int p = g.p[k], n4 = g.n2[k] >> 1;
+  const int q0 = g.nbr_ptr[k], nq = g.nbr_ptr[k + 1] - q0;
+  if (threadIdx.x < nq) {
+    const int l = g.nbr_l[q0 + threadIdx.x];
+    seg_c4[threadIdx.x] = g.nbr_col[q0 + threadIdx.x] >> 1;
+    seg_p[threadIdx.x] = g.p[l];
+    seg_w[threadIdx.x] = g.woff[l];
+  }
+  if (threadIdx.x == 0) seg_c4[nq] = n4;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+    int q = 0;
+    while (q + 1 < nq && seg_c4[q + 1] <= i) ++q;
+    const int e = 2 * (i - seg_c4[q]);
+    const double* xl = x + seg_w[q];
+    const float2 a = df_split(xl[e]);
+    const float2 b = (e + 1 < seg_p[q]) ? df_split(xl[e + 1]) : make_float2(0.f, 0.f);
+    xs[i] = make_float4(a.x, a.y, b.x, b.y);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = c0 + warp;
+  if (c >= min(c0 + GRAM_TILE_ROWS, p)) return;
+  const float4* row = reinterpret_cast<const float4*>(g.R2 + g.roff[k] + (int64_t)c * g.n2[k]);
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+#pragma unroll 16
+  for (int i = lane; i < n4; i += 32) {
+    const float4 a = row[i], xv = xs[i];
+    df_mac(h0, l0, make_float2(a.x, a.y), make_float2(xv.x, xv.y));
+    df_mac(h1, l1, make_float2(a.z, a.w), make_float2(xv.z, xv.w));
+  }
+  df_add(h0, l0, h1, l1);
+  df_warp_sum(h0, l0);
+  if (lane == 0) z[g.woff[k] + c] = df_to_double(h0, l0);
+}
+
+}  // namespace
+
+cudaError_t launch_gramrows_build(const GramRows& g, const double* d_pairbuf, int J, int maxp, int maxn2,
+                                  cudaStream_t st) {
+  if (J == 0) return cudaSuccess;
+  const int64_t per = (int64_t)maxp * maxn2;
+  const int gx = (int)std::min<int64_t>((per + 255) / 256, 1024);
+  for (int k0 = 0; k0 < J; k0 += 65535) {
+    gramrows_build_kernel<<<dim3(gx, std::min(J - k0, 65535)), 256, 0, st>>>(g, d_pairbuf, k0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_gram_matvec(const GramRows& g, int J, const int* d_rtile, int nrtile, int maxn2,
+                               const double* d_x, double* d_z, cudaStream_t st) {
+  if (J == 0) return cudaSuccess;
+  const int smem = (int)(sizeof(float2) * (size_t)maxn2);
+  cudaError_t e = cudaFuncSetAttribute(gram_rowdot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  gram_rowdot_kernel<<<nrtile, 32 * GRAM_TILE_ROWS, smem, st>>>(g, d_rtile, d_x, d_z);
+  return cudaGetLastError();
+}

@@ -12,7 +12,7 @@
 
 namespace {
 
-constexpr int HT_ROWS = 256;    // rows per H^T chunk
+constexpr int HT_ROWS = 256;    // rows per H^T chunk (and the most rows of a double-float tile)
 
 __global__ void matvec_H_kernel(ProbDev P, const SubDev* __restrict__ subs, const int* __restrict__ cov,
                                 int Gmax, const double* __restrict__ B, const double* __restrict__ x,
@@ -94,51 +94,64 @@ __global__ void split_kernel(const double* __restrict__ x, float2* __restrict__ 
 }
 
 // Per-block row products in double-float: yp[row0_j + r] = B_j[r, :] . x_j
-// (the contribution of block j to y at its r-th point).  One warp handles four
-// consecutive rows at once so that each lane keeps four independent loads in
-// flight; rows are contiguous, so every load is coalesced.
+// (the contribution of block j to y at its r-th point).  x_j is staged in
+// shared memory; a quarter warp (8 lanes) handles one row with 16-byte loads
+// (two double-float entries; rows have even length P_j and start 16-byte
+// aligned), four rows per warp, and sums its lanes with three shuffles.
 __global__ void __launch_bounds__(256) rowdot_df_kernel(const SubDev* __restrict__ subs,
-                                                        const int* __restrict__ rtiles,
+                                                        const int* __restrict__ rtiles, int tile_rows,
                                                         const float2* __restrict__ B2,
-                                                        const float2* __restrict__ x2,
+                                                        const float2* __restrict__ x2p,
                                                         float2* __restrict__ yp) {
+  __shared__ float4 xs[RANN_MAX_M / 2];
   const int j = rtiles[2 * blockIdx.x], r0 = rtiles[2 * blockIdx.x + 1];
   const SubDev& S = subs[j];
-  const int nr = min(HT_ROWS, S.N - r0);
+  const int nr = min(tile_rows, S.N - r0);
+  const int P2 = S.P >> 1;
+  const float4* xj = reinterpret_cast<const float4*>(x2p + S.poff);
+  for (int c = threadIdx.x; c < P2; c += blockDim.x) xs[c] = xj[c];
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float2* xj = x2 + S.woff;
-  for (int rb = warp * 4; rb < nr; rb += 32) {      // 8 warps x 4 rows = 32 rows per sweep
-    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
-    const float2* row = B2 + S.boff + (int64_t)(r0 + rb) * S.P;
-    for (int c = lane; c < S.p; c += 32) {
-      const float2 xv = xj[c];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (rb + u < nr) df_mac(h[u], l[u], row[(int64_t)u * S.P + c], xv);
+  const int q = lane >> 3, sl = lane & 7;
+  for (int rb = warp * 4; rb < nr; rb += 32) {      // 8 warps x 4 rows per sweep
+    const int row = rb + q;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    if (row < nr) {
+      const float4* rp = reinterpret_cast<const float4*>(B2 + S.boff + (int64_t)(r0 + row) * S.P);
+#pragma unroll 4
+      for (int c = sl; c < P2; c += 8) {
+        const float4 b = rp[c];
+        const float4 xv = xs[c];
+        df_mac(h0, l0, make_float2(b.x, b.y), make_float2(xv.x, xv.y));
+        df_mac(h1, l1, make_float2(b.z, b.w), make_float2(xv.z, xv.w));
+      }
+      df_add(h0, l0, h1, l1);
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      df_warp_sum(h[u], l[u]);
-      if (lane == 0 && rb + u < nr) yp[S.row0 + r0 + rb + u] = make_float2(h[u], l[u]);
+    for (int o = 4; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h0, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, l0, o);
+      df_add(h0, l0, oh, ol);
     }
+    if (sl == 0 && row < nr) yp[S.row0 + r0 + row] = make_float2(h0, l0);
   }
 }
 
 // Partial z_j over one 256-row chunk of B_j in double-float: y at each row is
 // first summed from the row products of every block holding that point; then
-// 64 column lanes x 4 row groups accumulate with two independent chains each,
-// and the row groups are added in shared memory.  Partials stored as float64.
+// each thread owns one column pair (16-byte loads) and a row group, with two
+// independent chains, and the row groups are added in a fixed order in shared
+// memory.  Partials stored as float64.
 __global__ void __launch_bounds__(256) matvec_HT_df_partial_kernel(ProbDev P, const SubDev* __restrict__ subs,
-                                                                   const int* __restrict__ rtiles,
+                                                                   const int* __restrict__ rtiles, int tile_rows,
                                                                    const int* __restrict__ cov, int Gmax,
                                                                    const float2* __restrict__ B2,
                                                                    const float2* __restrict__ yp,
                                                                    double* __restrict__ part, int maxP) {
   const int j = rtiles[2 * blockIdx.x], r0 = rtiles[2 * blockIdx.x + 1];
   const SubDev& S = subs[j];
-  const int nr = min(HT_ROWS, S.N - r0);
+  const int nr = min(tile_rows, S.N - r0);
   __shared__ float2 yl[HT_ROWS];
-  __shared__ float2 red[4][64];
+  __shared__ float4 red[256];
   const int d = P.dim;
   for (int t = threadIdx.x; t < nr; t += blockDim.x) {
     const int r = r0 + t;
@@ -164,33 +177,66 @@ __global__ void __launch_bounds__(256) matvec_HT_df_partial_kernel(ProbDev P, co
     yl[t] = make_float2(yh, yl2);
   }
   __syncthreads();
-  const int cx = threadIdx.x & 63, rg = threadIdx.x >> 6;
-  for (int c0 = 0; c0 < S.p; c0 += 64) {
-    const int c = c0 + cx;
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    if (c < S.p) {
-      const float2* col = B2 + S.boff + (int64_t)r0 * S.P + c;
+  const int P2 = S.P >> 1;
+  const int P2c = min(P2, 256);                  // column pairs per sweep
+  const int G = 256 / P2c;                       // row groups
+  const int cp = threadIdx.x % P2c, rg = threadIdx.x / P2c;
+  for (int c0 = 0; c0 < P2; c0 += P2c) {
+    const int c2 = c0 + cp;
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;   // columns 2 c2 (a) and 2 c2 + 1 (b), chain 0
+    float e0 = 0.f, e1 = 0.f, f0 = 0.f, f1 = 0.f;   // chain 1
+    if (rg < G && c2 < P2) {
+      const float4* col = reinterpret_cast<const float4*>(B2 + S.boff + (int64_t)r0 * S.P) + c2;
       int t = rg, cnt = 0;
-      for (; t + 4 < nr; t += 8) {
-        df_mac(h0, l0, col[(int64_t)t * S.P], yl[t]);
-        df_mac(h1, l1, col[(int64_t)(t + 4) * S.P], yl[t + 4]);
-        if ((++cnt & 7) == 0) { df_renorm(h0, l0); df_renorm(h1, l1); }
+      for (; t + G < nr; t += 2 * G) {
+        const float4 u = col[(int64_t)t * P2], w = col[(int64_t)(t + G) * P2];
+        const float2 yu = yl[t], yw = yl[t + G];
+        df_mac(a0, a1, make_float2(u.x, u.y), yu);
+        df_mac(b0, b1, make_float2(u.z, u.w), yu);
+        df_mac(e0, e1, make_float2(w.x, w.y), yw);
+        df_mac(f0, f1, make_float2(w.z, w.w), yw);
+        if ((++cnt & 7) == 0) { df_renorm(a0, a1); df_renorm(b0, b1); df_renorm(e0, e1); df_renorm(f0, f1); }
       }
-      if (t < nr) df_mac(h0, l0, col[(int64_t)t * S.P], yl[t]);
-      df_add(h0, l0, h1, l1);
+      if (t < nr) {
+        const float4 u = col[(int64_t)t * P2];
+        df_mac(a0, a1, make_float2(u.x, u.y), yl[t]);
+        df_mac(b0, b1, make_float2(u.z, u.w), yl[t]);
+      }
+      df_add(a0, a1, e0, e1);
+      df_add(b0, b1, f0, f1);
     }
-    red[rg][cx] = make_float2(h0, l0);
+    red[threadIdx.x] = make_float4(a0, a1, b0, b1);
     __syncthreads();
-    if (rg == 0 && c < S.p) {
-      float h = red[0][cx].x, l = red[0][cx].y;
-      for (int g = 1; g < 4; ++g) df_add(h, l, red[g][cx].x, red[g][cx].y);
-      part[(int64_t)blockIdx.x * maxP + c] = df_to_double(h, l);
+    if (rg == 0 && c2 < P2) {
+      float ah = red[cp].x, al = red[cp].y, bh = red[cp].z, bl = red[cp].w;
+      for (int g = 1; g < G; ++g) {
+        const float4 v = red[g * P2c + cp];
+        df_add(ah, al, v.x, v.y);
+        df_add(bh, bl, v.z, v.w);
+      }
+      if (2 * c2 < S.p) part[(int64_t)blockIdx.x * maxP + 2 * c2] = df_to_double(ah, al);
+      if (2 * c2 + 1 < S.p) part[(int64_t)blockIdx.x * maxP + 2 * c2 + 1] = df_to_double(bh, bl);
     }
     __syncthreads();
   }
 }
 
+// x2p[poff_j + c] = split(x[woff_j + c]) for c < p_j, zero up to P_j (each
+// block's part 16-byte aligned for the row products).
+__global__ void split_pad_kernel(const SubDev* __restrict__ subs, const double* __restrict__ x,
+                                 float2* __restrict__ x2p) {
+  const SubDev& S = subs[blockIdx.x];
+  for (int c = threadIdx.x; c < S.P; c += blockDim.x)
+    x2p[S.poff + c] = (c < S.p) ? df_split(x[S.woff + c]) : make_float2(0.f, 0.f);
+}
+
 }  // namespace
+
+cudaError_t launch_split_pad(const SubDev* d_sub, int J, const double* d_x, float2* d_x2p, cudaStream_t st) {
+  if (J == 0) return cudaSuccess;
+  split_pad_kernel<<<J, 256, 0, st>>>(d_sub, d_x, d_x2p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_split(const double* d_x, float2* d_x2, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
@@ -199,18 +245,19 @@ cudaError_t launch_split(const double* d_x, float2* d_x2, int64_t n, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_rowdot_df(const SubDev* d_sub, const int* d_rtiles, int nrtiles, const float2* d_B2,
-                             const float2* d_x2, float2* d_yp, cudaStream_t st) {
+cudaError_t launch_rowdot_df(const SubDev* d_sub, const int* d_rtiles, int nrtiles, int tile_rows,
+                             const float2* d_B2, const float2* d_x2p, float2* d_yp, cudaStream_t st) {
   if (nrtiles == 0) return cudaSuccess;
-  rowdot_df_kernel<<<nrtiles, 256, 0, st>>>(d_sub, d_rtiles, d_B2, d_x2, d_yp);
+  rowdot_df_kernel<<<nrtiles, 256, 0, st>>>(d_sub, d_rtiles, tile_rows, d_B2, d_x2p, d_yp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_matvec_HT_df(const ProbDev& P, const SubDev* d_sub, int J, const int* d_rtiles, int nrtiles,
-                                const int* d_tile0, const int* d_cov, int Gmax, const float2* d_B2,
+                                int tile_rows, const int* d_tile0, const int* d_cov, int Gmax, const float2* d_B2,
                                 const float2* d_yp, double* d_part, double* d_z, int maxP, cudaStream_t st) {
   if (nrtiles == 0) return cudaSuccess;
-  matvec_HT_df_partial_kernel<<<nrtiles, 256, 0, st>>>(P, d_sub, d_rtiles, d_cov, Gmax, d_B2, d_yp, d_part, maxP);
+  matvec_HT_df_partial_kernel<<<nrtiles, 256, 0, st>>>(P, d_sub, d_rtiles, tile_rows, d_cov, Gmax, d_B2, d_yp,
+                                                       d_part, maxP);
   matvec_HT_final_kernel<<<J, 256, 0, st>>>(d_sub, d_tile0, d_part, maxP, d_z);
   return cudaGetLastError();
 }
