@@ -1146,8 +1146,14 @@ static rann_status solve_cg_impl(rann_dd_handle* h, const double* F_dev, const d
   REQUIRE(rtol > 0 && maxit >= 0, RANN_EINVAL, "bad rtol/maxit");
   const int64_t n = h->dof;
   Workspace ws{h, {}};
-  double *b = ws.get(n), *r = ws.get(n), *z = ws.get(n), *p = ws.get(n), *q = ws.get(n);
-  REQUIRE(b && r && z && p && q, RANN_ENOMEM, "workspace allocation failed");
+  double *b = ws.get(n), *r = ws.get(n), *z = ws.get(n), *p = ws.get(n), *q = ws.get(n), *cgs = ws.get(8);
+  REQUIRE(b && r && z && p && q && cgs, RANN_ENOMEM, "workspace allocation failed");
+  struct Events {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~Events() { for (auto x : e) if (x) cudaEventDestroy(x); }
+  } evh;
+  cudaEvent_t* evs = evh.e;
+  for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, h->st));
@@ -1172,31 +1178,45 @@ static rann_status solve_cg_impl(rann_dd_handle* h, const double* F_dev, const d
     // In float64 mode the first cycle is plain PCG.
     double* d = W_dev;   // W accumulates the corrections: x_{k+1} = x_k + alpha p, per cycle from r
     double rr;
+    // CG scalars on the device; the host stays at most two steps ahead and
+    // stops enqueueing once the device reports done
+    CgDev sd{};
+    sd.pq = cgs; sd.rr = cgs + 1; sd.rz = cgs + 2; sd.rel = cgs + 4;
+    sd.done = reinterpret_cast<int*>(cgs + 5);
+    sd.it = sd.done + 1;
+    int* hdone = reinterpret_cast<int*>(h->h_scal + 128);
     for (int cycle = 0; cycle < 30; ++cycle) {
-      double rz;
       TRY(prec_inner(h, r, z));
       CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-      TRY(dot_host(h, r, z, n, &rz));
-      bool inner_ok = false;
-      while (it < maxit) {
+      KLA(h, K_DOT, 1, 16.0 * n, 2.0 * n, launch_multidot(r, 0, 1, z, n, h->d_red, sd.rz, h->st));
+      CK(cudaMemsetAsync(sd.done, 0, 2 * sizeof(int), h->st));
+      *hdone = 0;
+      const int kmax = maxit - it;
+      int ph = 0;
+      for (int i = 0; i < kmax; ++i) {
+        if (i >= 2) {
+          CK(cudaEventSynchronize(evs[(i - 2) % 3]));
+          if (*(volatile int*)hdone) break;
+        }
         TRY(op_inner(h, p, q));
-        double pq;
-        TRY(dot_host(h, p, q, n, &pq));
-        if (!(pq > 0.0) || !std::isfinite(pq)) { st = RANN_BREAKDOWN; break; }
-        const double alpha = rz / pq;
-        KLA(h, K_VEC, 1, 40.0 * n, 4.0 * n, launch_cg_update(alpha, p, q, d, r, n, h->st));
-        ++it;
-        TRY(dot_host(h, r, r, n, &rr));
-        rel = std::sqrt(rr) / bnorm;
-        if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
-        if (rel <= rtol) { inner_ok = true; break; }
+        KLA(h, K_DOT, 1, 16.0 * n, 2.0 * n, launch_multidot(p, 0, 1, q, n, h->d_red, sd.pq, h->st));
+        KLA(h, K_VEC, 1, 40.0 * n, 4.0 * n, launch_cg_update_dev(p, q, d, r, n, sd, ph, h->st));
+        KLA(h, K_DOT, 1, 8.0 * n, 2.0 * n, launch_multidot(r, 0, 1, r, n, h->d_red, sd.rr, h->st));
+        KLA(h, K_VEC, 1, 0, 0, launch_cg_check(sd, bnorm, rtol, h->st));
         TRY(prec_inner(h, r, z));
-        double rz2;
-        TRY(dot_host(h, r, z, n, &rz2));
-        KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, z, rz2 / rz, p, n, h->st));
-        rz = rz2;
+        KLA(h, K_DOT, 1, 16.0 * n, 2.0 * n, launch_multidot(r, 0, 1, z, n, h->d_red, sd.rz + (ph ^ 1), h->st));
+        KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_cg_direction(z, p, n, sd, ph, h->st));
+        ph ^= 1;
+        CK(cudaMemcpyAsync(hdone, sd.done, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaEventRecord(evs[i % 3], h->st));
       }
-      if (st == RANN_BREAKDOWN) break;
+      int dv[2];
+      CK(cudaMemcpyAsync(dv, sd.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaMemcpyAsync(&rel, sd.rel, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      it += dv[1];
+      const bool inner_ok = dv[0] == 1;
+      if (dv[0] == 2) { st = RANN_BREAKDOWN; break; }
       // float64 residual of the accumulated W
       TRY(rann_dd_normal_matvec(h, W_dev, q));
       CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
@@ -1237,7 +1257,28 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
   const int k = restart;
   Workspace ws{h, {}};
   double *b = ws.get(n), *t = ws.get(n), *V = ws.get((size_t)(k + 1) * n), *hv = ws.get(2 * (k + 2));
-  REQUIRE(b && t && V && hv, RANN_ENOMEM, "workspace allocation failed");
+  const size_t nstate = (size_t)(k + 1) * k + 2 * k + (k + 1) + 3 * (k + 2) + 4;
+  double* state = ws.get(nstate);
+  REQUIRE(b && t && V && hv && state, RANN_ENOMEM, "workspace allocation failed");
+  GmresDev sd{};
+  sd.H = state;
+  sd.cs = sd.H + (size_t)(k + 1) * k;
+  sd.sn = sd.cs + k;
+  sd.g = sd.sn + k;
+  sd.hv = sd.g + (k + 1);
+  sd.hcol = sd.hv + 2 * (k + 2);
+  sd.ww = sd.hcol + (k + 2);
+  sd.inv = sd.ww + 1;
+  sd.rel = sd.inv + 1;
+  sd.done = reinterpret_cast<int*>(sd.rel + 1);      // two ints in the last double
+  sd.jdone = sd.done + 1;
+  int* hdone = reinterpret_cast<int*>(h->h_scal + 128);
+  struct Events {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~Events() { for (auto x : e) if (x) cudaEventDestroy(x); }
+  } evh;
+  cudaEvent_t* evs = evh.e;
+  for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, h->st));
@@ -1249,7 +1290,7 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
   double mbb;
   TRY(dot_host(h, V, V, n, &mbb));
   const double mbnorm = std::sqrt(mbb);
-  std::vector<double> Hm((size_t)(k + 1) * k), cs(k), sn(k), g(k + 1), y(k), hcol(2 * (k + 2));
+  std::vector<double> Hm((size_t)(k + 1) * k), g(k + 1), y(k);
   int it = 0;
   double rel = 1.0;
   rann_status st = RANN_NOT_CONVERGED;
@@ -1273,46 +1314,46 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
     if (rel <= rtol) { st = RANN_OK; break; }
     if (it >= maxit) break;
     KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_copy(1.0 / beta, V, V, n, h->st));
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int jdone = 0;
-    for (int j = 0; j < k && it < maxit; ++j) {
+    // Arnoldi steps with the Givens bookkeeping on the device; the host stays at
+    // most two steps ahead and stops enqueueing once the device reports done
+    CK(cudaMemsetAsync(sd.g, 0, sizeof(double) * (k + 1), h->st));
+    CK(cudaMemcpyAsync(sd.g, &beta, sizeof(double), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemsetAsync(sd.done, 0, 2 * sizeof(int), h->st));
+    *hdone = 0;
+    const int jmax = std::min(k, maxit - it);
+    for (int j = 0; j < jmax; ++j) {
+      if (j >= 2) {
+        CK(cudaEventSynchronize(evs[(j - 2) % 3]));
+        if (*(volatile int*)hdone) break;
+      }
       double* w = V + (size_t)(j + 1) * n;
       TRY(op_inner(h, V + (size_t)j * n, t));
       TRY(prec_inner(h, t, w));
       // classical Gram-Schmidt, twice
       for (int pass = 0; pass < 2; ++pass) {
         KLA(h, K_DOT, 1, 8.0 * n * (j + 2), 2.0 * n * (j + 1),
-            launch_multidot(V, n, j + 1, w, n, h->d_red, hv + pass * (k + 2), h->st));
+            launch_multidot(V, n, j + 1, w, n, h->d_red, sd.hv + pass * (k + 2), h->st));
         KLA(h, K_VEC, 1, 8.0 * n * (j + 3), 2.0 * n * (j + 1),
-            launch_sub_combination(V, n, j + 1, hv + pass * (k + 2), w, n, h->st));
+            launch_sub_combination(V, n, j + 1, sd.hv + pass * (k + 2), w, n, h->st));
       }
-      CK(cudaMemcpyAsync(hcol.data(), hv, sizeof(double) * hcol.size(), cudaMemcpyDeviceToHost, h->st));
-      double ww;
-      TRY(dot_host(h, w, w, n, &ww));   // synchronises, so hcol is valid
-      std::vector<double> hj(j + 2);
-      for (int i = 0; i <= j; ++i) hj[i] = hcol[i] + hcol[(k + 2) + i];
-      hj[j + 1] = std::sqrt(ww);
-      if (hj[j + 1] > 0.0) KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_copy(1.0 / hj[j + 1], w, w, n, h->st));
-      for (int i = 0; i < j; ++i) {
-        double a = cs[i] * hj[i] + sn[i] * hj[i + 1];
-        hj[i + 1] = -sn[i] * hj[i] + cs[i] * hj[i + 1];
-        hj[i] = a;
-      }
-      double den = std::hypot(hj[j], hj[j + 1]);
-      if (den == 0.0) { cs[j] = 1.0; sn[j] = 0.0; } else { cs[j] = hj[j] / den; sn[j] = hj[j + 1] / den; }
-      hj[j] = cs[j] * hj[j] + sn[j] * hj[j + 1];
-      hj[j + 1] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      for (int i = 0; i <= j; ++i) Hm[(size_t)i * k + j] = hj[i];
-      ++it;
-      jdone = j + 1;
-      rel = std::fabs(g[j + 1]) / mbnorm;
-      if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
-      if (rel <= rtol || hj[j] == 0.0) break;
+      KLA(h, K_DOT, 1, 8.0 * n, 2.0 * n, launch_multidot(w, 0, 1, w, n, h->d_red, sd.ww, h->st));
+      KLA(h, K_VEC, 1, 0, 0, launch_gmres_givens(sd, j, k, mbnorm, rtol, h->st));
+      KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_dev(w, sd.inv, n, h->st));
+      CK(cudaMemcpyAsync(hdone, sd.done, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaEventRecord(evs[j % 3], h->st));
     }
-    if (st == RANN_BREAKDOWN) break;
+    int dj[2];
+    CK(cudaMemcpyAsync(dj, sd.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&rel, sd.rel, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const int jdone = dj[1];
+    it += jdone;
+    if (jdone == 0) rel = beta / mbnorm;
+    if (dj[0] == 2) { st = RANN_BREAKDOWN; break; }
+    if (jdone == 0) break;
+    CK(cudaMemcpyAsync(Hm.data(), sd.H, sizeof(double) * (size_t)jdone * k, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(g.data(), sd.g, sizeof(double) * jdone, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
     for (int i = jdone - 1; i >= 0; --i) {
       double sacc = g[i];
       for (int q = i + 1; q < jdone; ++q) sacc -= Hm[(size_t)i * k + q] * y[q];

@@ -493,15 +493,17 @@ __global__ void __launch_bounds__(256) trmv_lower_df_kernel(const CholMat* __res
   const float2* row = M.X2 + (int64_t)r * M.ld;
   const float2* gi = g2 + s_off[blockIdx.y];
   float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
-  int c = lane, cnt = 0;
-  for (; c + 96 <= r; c += 128) {
+  constexpr int U = 8;                                   // independent loads in flight per lane
+  for (int c0 = lane; c0 <= r; c0 += 32 * U) {
+    float2 a[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) df_mac(h[u], l[u], row[c + 32 * u], gi[c + 32 * u]);
-    if ((++cnt & 7) == 0)
+    for (int u = 0; u < U; ++u) a[u] = (c0 + 32 * u <= r) ? row[c0 + 32 * u] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) df_renorm(h[u], l[u]);
+    for (int u = 0; u < U; ++u) {
+      if (c0 + 32 * u > r) break;
+      df_mac(h[u & 3], l[u & 3], a[u], gi[c0 + 32 * u]);
+    }
   }
-  for (int u = 0; c <= r; c += 32, ++u) df_mac(h[u & 3], l[u & 3], row[c], gi[c]);
   df_add(h[0], l[0], h[1], l[1]);
   df_add(h[2], l[2], h[3], l[3]);
   df_add(h[0], l[0], h[2], l[2]);
@@ -534,13 +536,19 @@ __global__ void __launch_bounds__(256) trmv_upper_df_partial_kernel(const CholMa
   if (c < M.n) {
     int rr = max(r0, c);
     rr += (rg - (rr - r0)) & 3;                       // first row of this group (rows = rg mod 4)
-    int cnt = 0;
-    for (; rr + 4 < r1; rr += 8) {
-      df_mac(h0, l0, M.X2[(int64_t)rr * M.ld + c], ys[rr - r0]);
-      df_mac(h1, l1, M.X2[(int64_t)(rr + 4) * M.ld + c], ys[rr + 4 - r0]);
-      if ((++cnt & 7) == 0) { df_renorm(h0, l0); df_renorm(h1, l1); }
+    constexpr int U = 8;                              // rows loaded ahead per thread
+    for (; rr < r1; rr += 4 * U) {
+      float2 a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        a[u] = (rr + 4 * u < r1) ? M.X2[(int64_t)(rr + 4 * u) * M.ld + c] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; u += 2) {
+        if (rr + 4 * u >= r1) break;
+        df_mac(h0, l0, a[u], ys[rr + 4 * u - r0]);
+        if (rr + 4 * u + 4 < r1) df_mac(h1, l1, a[u + 1], ys[rr + 4 * u + 4 - r0]);
+      }
     }
-    if (rr < r1) df_mac(h0, l0, M.X2[(int64_t)rr * M.ld + c], ys[rr - r0]);
     df_add(h0, l0, h1, l1);
   }
   red[rg][cx] = make_float2(h0, l0);

@@ -103,6 +103,36 @@ int oz_kpad(int K);
 cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, int maxKp, cudaStream_t st);
 cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, cudaStream_t st);
 
+// krylov.cu -- device-resident state of one GMRES cycle
+struct GmresDev {
+  double* H;                 // [k + 1][k] rotated Hessenberg matrix (row-major, ld k)
+  double* cs;                // [k] Givens cosines
+  double* sn;                // [k] Givens sines
+  double* g;                 // [k + 1] rotated right-hand side (g_0 = beta)
+  double* hv;                // [2][k + 2] coefficients of the two Gram-Schmidt passes
+  double* hcol;              // [k + 2] scratch column
+  double* ww;                // ||w||^2 after the passes
+  double* inv;               // 1 / h_{j+1,j}
+  double* rel;               // residual estimate of the last step
+  int* done;                 // 0 running, 1 converged or lucky breakdown, 2 non-finite
+  int* jdone;                // steps that entered the Hessenberg matrix
+};
+cudaError_t launch_gmres_givens(const GmresDev& s, int j, int k, double mbnorm, double rtol, cudaStream_t st);
+// device-resident scalars of preconditioned CG (rz ping-pongs between two slots)
+struct CgDev {
+  double* pq;
+  double* rr;
+  double* rz;                // [2]
+  double* rel;
+  int* done;                 // 0 running, 1 converged, 2 breakdown
+  int* it;                   // updates made
+};
+cudaError_t launch_cg_update_dev(const double* p, const double* q, double* x, double* r, int64_t n, const CgDev& s,
+                                 int ph, cudaStream_t st);
+cudaError_t launch_cg_check(const CgDev& s, double bnorm, double rtol, cudaStream_t st);
+cudaError_t launch_cg_direction(const double* z, double* p, int64_t n, const CgDev& s, int ph, cudaStream_t st);
+cudaError_t launch_scale_dev(double* y, const double* a, int64_t n, cudaStream_t st);
+
 // gramop.cu -- the normal matrix as double-float block rows R_k = [G_kl]_l
 constexpr int GRAM_TILE_ROWS = 8;    // rows of R_k per block of the row-dot kernel (one warp each)
 constexpr int GRAM_MAX_NBR = 27;     // most neighbours of a block row (3^3); more falls back to B^T (B x)

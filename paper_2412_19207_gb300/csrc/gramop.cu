@@ -69,11 +69,18 @@ __global__ void __launch_bounds__(256) gram_rowdot_kernel(const GramRows g, cons
   if (c >= min(c0 + GRAM_TILE_ROWS, p)) return;
   const float4* row = reinterpret_cast<const float4*>(g.R2 + g.roff[k] + (int64_t)c * g.n2[k]);
   float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-#pragma unroll 16
-  for (int i = lane; i < n4; i += 32) {
-    const float4 a = row[i], xv = xs[i];
-    df_mac(h0, l0, make_float2(a.x, a.y), make_float2(xv.x, xv.y));
-    df_mac(h1, l1, make_float2(a.z, a.w), make_float2(xv.z, xv.w));
+  constexpr int U = 8;                         // independent 16-byte loads in flight per lane
+  for (int i0 = lane; i0 < n4; i0 += 32 * U) {
+    float4 a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = (i0 + 32 * u < n4) ? row[i0 + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (i0 + 32 * u >= n4) break;
+      const float4 xv = xs[i0 + 32 * u];
+      df_mac(h0, l0, make_float2(a[u].x, a[u].y), make_float2(xv.x, xv.y));
+      df_mac(h1, l1, make_float2(a[u].z, a[u].w), make_float2(xv.z, xv.w));
+    }
   }
   df_add(h0, l0, h1, l1);
   df_warp_sum(h0, l0);

@@ -79,6 +79,83 @@ __global__ void add_combination(const double* __restrict__ V, int64_t ldv, int n
   }
 }
 
+// One Arnoldi step's bookkeeping on the device (Saad & Schultz's GMRES with
+// Givens rotations): column j of the Hessenberg matrix from the two
+// Gram-Schmidt passes and ||w||, the earlier rotations applied, a new rotation
+// zeroing h_{j+1,j}, the residual estimate |g_{j+1}| / ||M^{-1} b||, and the
+// scale 1 / h_{j+1,j} that normalises the next basis vector.  The cycle stops
+// (done = 1) at the tolerance or a lucky breakdown, done = 2 on a non-finite
+// estimate; a step after done changes nothing.  One thread.
+__global__ void gmres_givens_kernel(GmresDev s, int j, int k, double mbnorm, double rtol) {
+  if (*s.done) { *s.inv = 0.0; return; }
+  double* hj = s.hcol;                       // [k + 2] scratch
+  for (int i = 0; i <= j; ++i) hj[i] = s.hv[i] + s.hv[(k + 2) + i];
+  const double nrm = sqrt(*s.ww);
+  hj[j + 1] = nrm;
+  *s.inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double a = s.cs[i] * hj[i] + s.sn[i] * hj[i + 1];
+    hj[i + 1] = -s.sn[i] * hj[i] + s.cs[i] * hj[i + 1];
+    hj[i] = a;
+  }
+  const double den = hypot(hj[j], hj[j + 1]);
+  if (den == 0.0) { s.cs[j] = 1.0; s.sn[j] = 0.0; } else { s.cs[j] = hj[j] / den; s.sn[j] = hj[j + 1] / den; }
+  hj[j] = s.cs[j] * hj[j] + s.sn[j] * hj[j + 1];
+  hj[j + 1] = 0.0;
+  s.g[j + 1] = -s.sn[j] * s.g[j];
+  s.g[j] = s.cs[j] * s.g[j];
+  for (int i = 0; i <= j; ++i) s.H[(int64_t)i * k + j] = hj[i];
+  const double rel = fabs(s.g[j + 1]) / mbnorm;
+  *s.rel = rel;
+  *s.jdone = j + 1;
+  if (!isfinite(rel)) *s.done = 2;
+  else if (rel <= rtol || hj[j] == 0.0) *s.done = 1;
+}
+
+// y *= *a (a device scalar)
+__global__ void scale_dev_kernel(double* __restrict__ y, const double* __restrict__ a, int64_t n) {
+  const double f = *a;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    y[t] *= f;
+}
+
+// Preconditioned CG steps with the scalars on the device (Hestenes & Stiefel):
+// x += alpha p, r -= alpha q with alpha = (r.z) / (p.q); a step after done
+// (converged, breakdown) changes nothing.  done = 2 when p.q is not positive
+// and finite.
+__global__ void cg_update_dev_kernel(const double* __restrict__ p, const double* __restrict__ q,
+                                     double* __restrict__ x, double* __restrict__ r, int64_t n, CgDev s, int ph) {
+  if (*s.done) return;
+  const double pq = *s.pq, rz = s.rz[ph];
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *s.done = 2;
+    return;
+  }
+  const double alpha = rz / pq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    x[t] = fma(alpha, p[t], x[t]);
+    r[t] = fma(-alpha, q[t], r[t]);
+  }
+}
+
+// After an update: count it and test ||r|| / ||b|| (one thread).
+__global__ void cg_check_kernel(CgDev s, double bnorm, double rtol) {
+  if (*s.done) return;
+  const double rel = sqrt(*s.rr) / bnorm;
+  *s.rel = rel;
+  *s.it += 1;
+  if (!isfinite(rel)) *s.done = 2;
+  else if (rel <= rtol) *s.done = 1;
+}
+
+// p = z + (rz_new / rz_old) p
+__global__ void cg_direction_kernel(const double* __restrict__ z, double* __restrict__ p, int64_t n, CgDev s, int ph) {
+  if (*s.done) return;
+  const double beta = s.rz[ph ^ 1] / s.rz[ph];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    p[t] = fma(beta, p[t], z[t]);
+}
+
 inline unsigned grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   return (unsigned)(g > 1216 ? 1216 : (g < 1 ? 1 : g));
@@ -123,5 +200,31 @@ cudaError_t launch_cg_update(double a, const double* p, const double* q, double*
 
 cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, cudaStream_t st) {
   scale_copy_kernel<<<grid_for(n), 256, 0, st>>>(a, x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_givens(const GmresDev& s, int j, int k, double mbnorm, double rtol, cudaStream_t st) {
+  gmres_givens_kernel<<<1, 1, 0, st>>>(s, j, k, mbnorm, rtol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_dev(double* y, const double* a, int64_t n, cudaStream_t st) {
+  scale_dev_kernel<<<grid_for(n), 256, 0, st>>>(y, a, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update_dev(const double* p, const double* q, double* x, double* r, int64_t n, const CgDev& s,
+                                 int ph, cudaStream_t st) {
+  cg_update_dev_kernel<<<grid_for(n), 256, 0, st>>>(p, q, x, r, n, s, ph);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_check(const CgDev& s, double bnorm, double rtol, cudaStream_t st) {
+  cg_check_kernel<<<1, 1, 0, st>>>(s, bnorm, rtol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_direction(const double* z, double* p, int64_t n, const CgDev& s, int ph, cudaStream_t st) {
+  cg_direction_kernel<<<grid_for(n), 256, 0, st>>>(z, p, n, s, ph);
   return cudaGetLastError();
 }
