@@ -261,7 +261,9 @@ rann_status rann_dd_matvec_t_noalloc(int J, const int64_t* boff, const int* n_ro
  * static string), kernels launched, summed device time in ms (0 unless
  * profiling was on), summed algorithmic bytes and flops, and its roofline
  * class (0 = memory-bound, 1 = float64-ALU-bound, 2 = bf16-tensor-core-bound,
- * whose flops are those of the digit-slice products).  It synchronises the
+ * whose flops are those of the digit-slice products, 3 = double-float
+ * arithmetic on the float32 pipe, float64-equivalent flops; the class of a
+ * family can depend on the precision mode).  It synchronises the
  * pending events.  Any output pointer may be NULL. */
 rann_status rann_dd_profile_enable(rann_dd_handle* h, int on);
 rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const char** name, int64_t* launches,

@@ -125,6 +125,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     return lib
 
 
+BOUND_NAMES = {0: "hbm", 1: "alu", 2: "tensor", 3: "alu_df32"}
+
+
 def _check(status: int, what: str, allow=()):
     if status == OK or status in allow:
         return status
@@ -329,6 +332,9 @@ class RannDD:
         _check(self._lib.rann_dd_profile_enable(self._h, int(on)), "rann_dd_profile_enable")
 
     def profile_read(self):
+        """Per kernel family: launches, device ms, algorithmic bytes and flops, and
+        the roofline class ("hbm", "alu" = float64 pipe, "tensor" = bf16 digit-slice
+        products, "alu_df32" = double-float on the float32 pipe)."""
         out = {}
         i = 0
         while True:
@@ -337,7 +343,7 @@ class RannDD:
                                              ctypes.byref(nb), ctypes.byref(nf), ctypes.byref(bd)) != OK:
                 break
             out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": nb.value,
-                                        "flops": nf.value, "bound": "alu" if bd.value else "hbm"}
+                                        "flops": nf.value, "bound": BOUND_NAMES.get(bd.value, "alu")}
             i += 1
         return out
 

@@ -113,9 +113,13 @@ static const char* const KNAMES[K_COUNT] = {
 
 // Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
 // 1 = float64-ALU-bound (algorithmic flops count), 2 = bf16-tensor-core-bound
-// (the flops of the digit-slice products count).
+// (the flops of the digit-slice products count), 3 = double-float arithmetic
+// on the float32 pipe (float64-equivalent flops count; the families marked in
+// KDF below run that way in precision mode 1).
 static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1,
                                      0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1, 0, 0};
+
+static bool family_is_df(int k) { return k == K_PAIRGRAM || k == K_CHOL || k == K_TRTRI; }
 
 struct Prof {
   bool on = false;
@@ -1252,7 +1256,8 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
                                     double rtol, int restart, int maxit, rann_dd_stats* stats) {
   REQUIRE(h && (F_dev || b_dev) && W_dev, RANN_EINVAL, "null argument");
   REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve before setup_precond");
-  REQUIRE(rtol > 0 && maxit >= 0 && restart >= 1 && restart <= 120, RANN_EINVAL, "bad rtol/restart/maxit");
+  REQUIRE(rtol > 0 && maxit >= 0 && restart >= 1 && restart <= GMRES_MAX_RESTART, RANN_EINVAL,
+          "bad rtol/restart/maxit");
   const int64_t n = h->dof;
   const int k = restart;
   Workspace ws{h, {}};
@@ -1518,6 +1523,6 @@ extern "C" rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const cha
   if (ms) *ms = h->prof.ms[idx];
   if (alg_bytes) *alg_bytes = h->prof.bytes[idx];
   if (alg_flops) *alg_flops = h->prof.flops[idx];
-  if (bound) *bound = KBOUND[idx];
+  if (bound) *bound = (h->inner_df && family_is_df(idx)) ? 3 : KBOUND[idx];
   return RANN_OK;
 }

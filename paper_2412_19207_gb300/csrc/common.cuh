@@ -104,6 +104,7 @@ cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, in
 cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, cudaStream_t st);
 
 // krylov.cu -- device-resident state of one GMRES cycle
+constexpr int GMRES_MAX_RESTART = 120;
 struct GmresDev {
   double* H;                 // [k + 1][k] rotated Hessenberg matrix (row-major, ld k)
   double* cs;                // [k] Givens cosines

@@ -85,31 +85,45 @@ __global__ void add_combination(const double* __restrict__ V, int64_t ldv, int n
 // zeroing h_{j+1,j}, the residual estimate |g_{j+1}| / ||M^{-1} b||, and the
 // scale 1 / h_{j+1,j} that normalises the next basis vector.  The cycle stops
 // (done = 1) at the tolerance or a lucky breakdown, done = 2 on a non-finite
-// estimate; a step after done changes nothing.  One thread.
-__global__ void gmres_givens_kernel(GmresDev s, int j, int k, double mbnorm, double rtol) {
-  if (*s.done) { *s.inv = 0.0; return; }
-  double* hj = s.hcol;                       // [k + 2] scratch
-  for (int i = 0; i <= j; ++i) hj[i] = s.hv[i] + s.hv[(k + 2) + i];
-  const double nrm = sqrt(*s.ww);
-  hj[j + 1] = nrm;
-  *s.inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-  for (int i = 0; i < j; ++i) {
-    const double a = s.cs[i] * hj[i] + s.sn[i] * hj[i + 1];
-    hj[i + 1] = -s.sn[i] * hj[i] + s.cs[i] * hj[i + 1];
-    hj[i] = a;
+// estimate; a step after done changes nothing.  The column and the rotations
+// are staged in shared memory; one thread runs the rotation chain.
+__global__ void __launch_bounds__(128) gmres_givens_kernel(GmresDev s, int j, int k, double mbnorm, double rtol) {
+  __shared__ double hj[GMRES_MAX_RESTART + 2], cs[GMRES_MAX_RESTART], sn[GMRES_MAX_RESTART];
+  __shared__ int skip;
+  const int t = threadIdx.x;
+  if (t == 0) skip = *s.done;
+  // the column from the two passes and the earlier rotations, loaded in parallel
+  for (int i = t; i <= j; i += blockDim.x) hj[i] = s.hv[i] + s.hv[(k + 2) + i];
+  for (int i = t; i < j; i += blockDim.x) { cs[i] = s.cs[i]; sn[i] = s.sn[i]; }
+  __syncthreads();
+  if (skip) { if (t == 0) *s.inv = 0.0; return; }
+  if (t == 0) {
+    const double nrm = sqrt(*s.ww);
+    hj[j + 1] = nrm;
+    *s.inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int i = 0; i < j; ++i) {
+      const double a = cs[i] * hj[i] + sn[i] * hj[i + 1];
+      hj[i + 1] = -sn[i] * hj[i] + cs[i] * hj[i + 1];
+      hj[i] = a;
+    }
+    const double den = hypot(hj[j], hj[j + 1]);
+    double c = 1.0, sj = 0.0;
+    if (den != 0.0) { c = hj[j] / den; sj = hj[j + 1] / den; }
+    s.cs[j] = c;
+    s.sn[j] = sj;
+    hj[j] = c * hj[j] + sj * hj[j + 1];
+    hj[j + 1] = 0.0;
+    const double gj = s.g[j];
+    s.g[j + 1] = -sj * gj;
+    s.g[j] = c * gj;
+    const double rel = fabs(s.g[j + 1]) / mbnorm;
+    *s.rel = rel;
+    *s.jdone = j + 1;
+    if (!isfinite(rel)) *s.done = 2;
+    else if (rel <= rtol || hj[j] == 0.0) *s.done = 1;
   }
-  const double den = hypot(hj[j], hj[j + 1]);
-  if (den == 0.0) { s.cs[j] = 1.0; s.sn[j] = 0.0; } else { s.cs[j] = hj[j] / den; s.sn[j] = hj[j + 1] / den; }
-  hj[j] = s.cs[j] * hj[j] + s.sn[j] * hj[j + 1];
-  hj[j + 1] = 0.0;
-  s.g[j + 1] = -s.sn[j] * s.g[j];
-  s.g[j] = s.cs[j] * s.g[j];
-  for (int i = 0; i <= j; ++i) s.H[(int64_t)i * k + j] = hj[i];
-  const double rel = fabs(s.g[j + 1]) / mbnorm;
-  *s.rel = rel;
-  *s.jdone = j + 1;
-  if (!isfinite(rel)) *s.done = 2;
-  else if (rel <= rtol || hj[j] == 0.0) *s.done = 1;
+  __syncthreads();
+  for (int i = t; i <= j; i += blockDim.x) s.H[(int64_t)i * k + j] = hj[i];
 }
 
 // y *= *a (a device scalar)
@@ -204,7 +218,7 @@ cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, c
 }
 
 cudaError_t launch_gmres_givens(const GmresDev& s, int j, int k, double mbnorm, double rtol, cudaStream_t st) {
-  gmres_givens_kernel<<<1, 1, 0, st>>>(s, j, k, mbnorm, rtol);
+  gmres_givens_kernel<<<1, 128, 0, st>>>(s, j, k, mbnorm, rtol);
   return cudaGetLastError();
 }
 
