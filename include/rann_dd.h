@@ -211,7 +211,9 @@ rann_status rann_dd_eval(rann_dd_handle* h, const double* W_dev, const double* x
 
 /* Building blocks of the solve, exposed for tests and composition
  * (all device vectors float64): y = H x (y_dev [N], x_dev [DoF]);
- * z = H^T y; z = H^T H x (one fused pass over the blocks); z = M^{-1} r. */
+ * z = H^T y; z = H^T H x (float64, B^T (B x)); z = M^{-1} r with the stored
+ * local factors (double-float after a set-up in precision mode 1, float64
+ * after one in mode 0). */
 rann_status rann_dd_matvec(rann_dd_handle* h, const double* x_dev, double* y_dev);
 rann_status rann_dd_matvec_t(rann_dd_handle* h, const double* y_dev, double* z_dev);
 rann_status rann_dd_normal_matvec(rann_dd_handle* h, const double* x_dev, double* z_dev);

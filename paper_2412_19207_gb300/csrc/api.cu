@@ -201,6 +201,8 @@ struct rann_dd_handle {
   double* d_tpart = nullptr;   // partial sums of the transposed product
   int64_t* d_p_off = nullptr;
   double* d_Amats = nullptr;
+  float2* d_A2mats = nullptr;     // double-float A_i / L_i (precision mode 1 set-up)
+  bool prec_df = false;           // the set-up kept only double-float factors
   double* d_Xmats = nullptr;
   float2* d_X2mats = nullptr;
   float2* d_g2 = nullptr;
@@ -857,9 +859,9 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   for (void* p : {(void*)h->d_mats, (void*)h->d_set_ptr, (void*)h->d_set_sub, (void*)h->d_inc_ptr,
                   (void*)h->d_inc_set, (void*)h->d_inc_pos, (void*)h->d_s_off, (void*)h->d_s,
                   (void*)h->d_Amats, (void*)h->d_Xmats, (void*)h->d_g, (void*)h->d_y, (void*)h->d_tpart,
-                  (void*)h->d_p_off, (void*)h->d_X2mats, (void*)h->d_g2, (void*)h->d_ys2})
+                  (void*)h->d_p_off, (void*)h->d_X2mats, (void*)h->d_g2, (void*)h->d_ys2, (void*)h->d_A2mats})
     dfree(h, p);
-  h->d_mats = nullptr; h->d_Amats = nullptr; h->d_Xmats = nullptr; h->d_X2mats = nullptr;
+  h->d_mats = nullptr; h->d_Amats = nullptr; h->d_Xmats = nullptr; h->d_X2mats = nullptr; h->d_A2mats = nullptr;
   for (void* p : h->gram_allocs) dfree(h, p);
   h->gram_allocs.clear();
   h->gram_ready = false;
@@ -968,8 +970,14 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
       }
     tab_ptr.push_back((int)tab.size());
   }
-  CK(dalloc(h, (void**)&h->d_Amats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
-  CK(dalloc(h, (void**)&h->d_Xmats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
+  // precision mode 1 keeps A_i, L_i and L_i^{-1} in double-float only
+  h->prec_df = h->inner_df != 0;
+  if (h->prec_df) {
+    CK(dalloc(h, (void**)&h->d_A2mats, sizeof(float2) * (size_t)std::max<int64_t>(aoff, 1)));
+  } else {
+    CK(dalloc(h, (void**)&h->d_Amats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
+    CK(dalloc(h, (void**)&h->d_Xmats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
+  }
   CK(dalloc(h, (void**)&h->d_X2mats, sizeof(float2) * (size_t)std::max<int64_t>(aoff, 1)));
   h->sum_n = h->sum_n2 = h->sum_n3 = 0;
   for (int i = 0; i < J; ++i) {
@@ -977,9 +985,17 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     h->sum_n += n; h->sum_n2 += n * n; h->sum_n3 += n * n * n;
   }
   for (int i = 0; i < J; ++i) {
-    mats[i].X = h->d_Xmats + reinterpret_cast<int64_t>(mats[i].A);
-    mats[i].X2 = h->d_X2mats + reinterpret_cast<int64_t>(mats[i].A);
-    mats[i].A = h->d_Amats + reinterpret_cast<int64_t>(mats[i].A);
+    const int64_t o = reinterpret_cast<int64_t>(mats[i].A);
+    mats[i].X2 = h->d_X2mats + o;
+    if (h->prec_df) {
+      mats[i].A2 = h->d_A2mats + o;
+      mats[i].A = nullptr;
+      mats[i].X = nullptr;
+    } else {
+      mats[i].A2 = nullptr;
+      mats[i].A = h->d_Amats + o;
+      mats[i].X = h->d_Xmats + o;
+    }
   }
   int64_t* d_tab; int *d_tab_ptr, *d_boffs, *d_boff_ptr; double* d_dmax; int* d_fail;
   CK(dupload(h, &d_tab, tab)); CK(dupload(h, &d_tab_ptr, tab_ptr));
@@ -1008,7 +1024,7 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     CK(cudaMemsetAsync(d_fail, 0, sizeof(int) * J, h->st));
     for (int c0 = 0; c0 < amax; c0 += 32)
       KLA(h, K_CHOL, (amax - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
-          launch_chol_step(d_am, (int)am.size(), amax, c0, d_fail, d_adm, h->inner_df, h->st));
+          launch_chol_step(d_am, (int)am.size(), amax, c0, d_fail, d_adm, h->prec_df, h->st));
     std::vector<int> f(am.size());
     CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * am.size(), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -1040,8 +1056,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   }
   for (int i = 0; i < J; ++i) h->n_shifted += shifted[i];
   // X_i = L_i^{-1} for the parallel apply
-  KLA(h, K_TRTRI, 2, 0, h->sum_n3 / 3.0, launch_trtri(h->d_mats, J, h->maxn, h->inner_df, h->st));
-  KLA(h, K_SPLIT, 1, 6.0 * h->sum_n2, 0, launch_split_lower(h->d_mats, J, h->maxn, h->st));
+  KLA(h, K_TRTRI, h->prec_df ? 1 : 2, 0, h->sum_n3 / 3.0, launch_trtri(h->d_mats, J, h->maxn, h->prec_df, h->st));
+  if (!h->prec_df) KLA(h, K_SPLIT, 1, 6.0 * h->sum_n2, 0, launch_split_lower(h->d_mats, J, h->maxn, h->st));
   std::vector<int64_t> p_off(J + 1, 0);
   for (int i = 0; i < J; ++i) p_off[i + 1] = p_off[i] + (int64_t)((mats[i].n + 255) / 256) * mats[i].n;
   CK(dupload(h, &h->d_p_off, p_off));
@@ -1101,7 +1117,8 @@ static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, boo
 extern "C" rann_status rann_dd_precond_apply(rann_dd_handle* h, const double* r_dev, double* z_dev) {
   REQUIRE(h && r_dev && z_dev, RANN_EINVAL, "null argument");
   REQUIRE(h->prec_kind >= 0, RANN_EORDER, "precond_apply before setup_precond");
-  return prec_apply(h, r_dev, z_dev);
+  // a precision mode 1 set-up keeps only the double-float factors
+  return prec_apply(h, r_dev, z_dev, h->prec_df);
 }
 
 // -------------------------------------------------------------- solves --
@@ -1137,7 +1154,7 @@ static rann_status op_inner(rann_dd_handle* h, const double* x, double* z) {
   return h->inner_df ? normal_matvec_fast(h, x, z) : rann_dd_normal_matvec(h, x, z);
 }
 static rann_status prec_inner(rann_dd_handle* h, const double* r, double* z) {
-  return prec_apply(h, r, z, h->inner_df != 0);
+  return prec_apply(h, r, z, h->inner_df != 0 || h->prec_df);
 }
 
 // CG on H^T H W = b with b = H^T F (F_dev) or b given (b_dev).

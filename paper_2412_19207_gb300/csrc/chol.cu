@@ -87,11 +87,95 @@ __global__ void trsm_panel_kernel(const CholMat* __restrict__ mats, int c0) {
   for (int j = 0; j < NB; ++j) row[j] = x[j];
 }
 
-// A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles.  The rank-32
-// product is accumulated in double-float (the panel is split on load) and
-// subtracted in float64: the trailing updates carry most of the Cholesky
-// flops, and their ~1e-14 relative accuracy only affects the preconditioner.
-__global__ void __launch_bounds__(256) syrk_update_kernel(const CholMat* __restrict__ mats, int c0) {
+// ---- double-float resident factorisation (precision mode 1) ----
+// A_i, L_i and L_i^{-1} stay double-float (A2, X2): the 32 x 32 diagonal
+// block is factored in float64 (converted on load and store) together with
+// its inverse, which goes to the diagonal block of X2; the panel is then
+// L21 = A21 L11^{-T} as a double-float product with that inverse, and the
+// trailing update A22 -= L21 L21^T and the block-column inverse run on the
+// float32 pipe with no conversions.
+
+// Diagonal block c0 of A2: L11 (float64 Cholesky, pivots checked as in the
+// float64 path) back to A2, L11^{-1} (one thread per column) to X2.
+__global__ void potrf_diag_df_kernel(const CholMat* __restrict__ mats, int c0, int* __restrict__ fail,
+                                     const double* __restrict__ dmax) {
+  const CholMat M = mats[blockIdx.x];
+  if (M.n <= c0) return;
+  const int nb = min(NB, M.n - c0);
+  __shared__ double a[NB][NB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int r = e / nb, c = e % nb;
+    const float2 v = M.A2[(int64_t)(c0 + r) * M.ld + c0 + c];
+    a[r][c] = df_to_double(v.x, v.y);
+  }
+  __syncthreads();
+  const double tol = 1e-15 * dmax[blockIdx.x];
+  for (int j = 0; j < nb; ++j) {
+    if (threadIdx.x == 0) {
+      double piv = a[j][j];
+      if (!(piv > tol)) {
+        fail[blockIdx.x] = 1;
+        piv = fmax(fabs(piv), tol > 0.0 ? tol : 1e-300);
+      }
+      a[j][j] = sqrt(piv);
+    }
+    __syncthreads();
+    for (int r = j + 1 + threadIdx.x; r < nb; r += blockDim.x) a[r][j] /= a[j][j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+      const int r = e / nb, c = e % nb;
+      if (c > j && r >= c) a[r][c] -= a[r][j] * a[c][j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int r = e / nb, c = e % nb;
+    if (r >= c) M.A2[(int64_t)(c0 + r) * M.ld + c0 + c] = df_split(a[r][c]);
+  }
+  const int c = threadIdx.x;
+  if (c < nb) {
+    double x[NB];
+    for (int r = c; r < nb; ++r) {
+      double sacc = (r == c) ? 1.0 : 0.0;
+      for (int k = c; k < r; ++k) sacc = fma(-a[r][k], x[k], sacc);
+      x[r] = sacc / a[r][r];
+      M.X2[(int64_t)(c0 + r) * M.ld + c0 + c] = df_split(x[r]);
+    }
+  }
+}
+
+// L21 = A21 L11^{-T}: row r of the panel times the stored inverse block, one
+// thread per row, in double-float.
+__global__ void __launch_bounds__(128) trsm_panel_df_kernel(const CholMat* __restrict__ mats, int c0) {
+  const CholMat M = mats[blockIdx.y];
+  if (M.n <= c0 + NB) return;
+  __shared__ float2 li[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    li[r][c] = (c <= r) ? M.X2[(int64_t)(c0 + r) * M.ld + c0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int r = c0 + NB + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= M.n) return;
+  float2* row = M.A2 + (int64_t)r * M.ld + c0;
+  float ah[NB], al[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) { ah[j] = 0.f; al[j] = 0.f; }
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const float2 xk = row[k];
+#pragma unroll
+    for (int j = k; j < NB; ++j) df_mac(ah[j], al[j], xk, li[j][k]);
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    df_renorm(ah[j], al[j]);
+    row[j] = make_float2(ah[j], al[j]);
+  }
+}
+
+// A22 -= L21 L21^T on the lower triangle of A2, 64 x 64 tiles, double-float.
+__global__ void __launch_bounds__(256) syrk_update_df_kernel(const CholMat* __restrict__ mats, int c0) {
   const CholMat M = mats[blockIdx.y];
   const int s0 = c0 + NB;
   if (M.n <= s0) return;
@@ -106,10 +190,10 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(const CholMat* __restr
   __shared__ float2 sa[NB][65];
   __shared__ float2 sb[NB][65];
   for (int e = threadIdx.x; e < 64 * NB; e += 256) {
-    int rr = e / NB, k = e % NB;
-    int r = r0 + rr, q = q0 + rr;
-    sa[k][rr] = (r < M.n) ? df_split(M.A[(int64_t)r * M.ld + c0 + k]) : make_float2(0.f, 0.f);
-    sb[k][rr] = (q < M.n) ? df_split(M.A[(int64_t)q * M.ld + c0 + k]) : make_float2(0.f, 0.f);
+    const int rr = e / NB, k = e % NB;
+    const int r = r0 + rr, q = q0 + rr;
+    sa[k][rr] = (r < M.n) ? M.A2[(int64_t)r * M.ld + c0 + k] : make_float2(0.f, 0.f);
+    sb[k][rr] = (q < M.n) ? M.A2[(int64_t)q * M.ld + c0 + k] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -137,8 +221,12 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(const CholMat* __restr
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      int r = r0 + ty + 16 * p, c = q0 + tx + 16 * q;
-      if (r < M.n && c <= r) M.A[(int64_t)r * M.ld + c] -= df_to_double(ah[p][q], al[p][q]);
+      const int r = r0 + ty + 16 * p, c = q0 + tx + 16 * q;
+      if (r < M.n && c <= r) {
+        float2 v = M.A2[(int64_t)r * M.ld + c];
+        df_add(v.x, v.y, -ah[p][q], -al[p][q]);
+        M.A2[(int64_t)r * M.ld + c] = v;
+      }
     }
 }
 
@@ -168,10 +256,10 @@ __global__ void trtri_diag_kernel(const CholMat* __restrict__ mats) {
   for (int r = c; r < nb; ++r) M.X[(int64_t)(b0 + r) * M.ld + b0 + c] = x[r];
 }
 
-// Block column j of X: for i > j, X_ij = -X_ii sum_{j <= k < i} L_ik X_kj,
-// the products accumulated in double-float (operands split on load), X_ij
-// stored in float64.
-__global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restrict__ mats) {
+// Block column j of X2 = L^{-1} (double-float, L from A2): for i > j,
+// X_ij = -X_ii sum_{j <= k < i} L_ik X_kj; the diagonal blocks X_ii were
+// written by the factorisation.
+__global__ void __launch_bounds__(256) trtri_col_df_kernel(const CholMat* __restrict__ mats) {
   const CholMat M = mats[blockIdx.y];
   const int nblk = (M.n + NB - 1) / NB;
   const int j = blockIdx.x;
@@ -187,11 +275,11 @@ __global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restric
     for (int k = j; k < i; ++k) {
       const int ck = k * NB;
       for (int e = t; e < NB * NB; e += 256) {
-        int a = e / NB, b = e % NB;
-        sl[a][b] = (ri + a < M.n) ? df_split(M.A[(int64_t)(ri + a) * M.ld + ck + b]) : zero;   // L_ik
+        const int a = e / NB, b = e % NB;
+        sl[a][b] = (ri + a < M.n) ? M.A2[(int64_t)(ri + a) * M.ld + ck + b] : zero;   // L_ik
         // X_kj (the diagonal block X_jj is lower triangular: its upper part is never written)
-        sx[a][b] = (ck + a < M.n && cj + b < M.n && (k > j || b <= a))
-                       ? df_split(M.X[(int64_t)(ck + a) * M.ld + cj + b]) : zero;
+        sx[a][b] = (ck + a < M.n && cj + b < M.n && (k > j || b <= a)) ? M.X2[(int64_t)(ck + a) * M.ld + cj + b]
+                                                                       : zero;
       }
       __syncthreads();
 #pragma unroll 8
@@ -206,8 +294,8 @@ __global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restric
     }
     // X_ij = -X_ii acc
     for (int e = t; e < NB * NB; e += 256) {
-      int a = e / NB, b = e % NB;
-      sl[a][b] = (ri + a < M.n && b <= a) ? df_split(M.X[(int64_t)(ri + a) * M.ld + ri + b]) : zero;   // X_ii
+      const int a = e / NB, b = e % NB;
+      sl[a][b] = (ri + a < M.n && b <= a) ? M.X2[(int64_t)(ri + a) * M.ld + ri + b] : zero;   // X_ii
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) sx[r][cg + u] = make_float2(ah[u], al[u]);
@@ -220,8 +308,11 @@ __global__ void __launch_bounds__(256) trtri_col_kernel(const CholMat* __restric
     }
     if (ri + r < M.n)
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (cj + cg + u < M.n) M.X[(int64_t)(ri + r) * M.ld + cj + cg + u] = -df_to_double(oh[u], ol[u]);
+      for (int u = 0; u < 4; ++u) {
+        if (cj + cg + u >= M.n) continue;
+        df_renorm(oh[u], ol[u]);
+        M.X2[(int64_t)(ri + r) * M.ld + cj + cg + u] = make_float2(-oh[u], -ol[u]);
+      }
     __syncthreads();   // X_ij visible to the next i (same block)
   }
 }
@@ -440,6 +531,10 @@ __global__ void assemble_local_kernel(const double* __restrict__ pairbuf, const 
       v = tr ? pairbuf[off + (int64_t)(c - bo[b]) * pa + (r - bo[a])]
              : pairbuf[off + (int64_t)(r - bo[a]) * pb + (c - bo[b])];
     }
+    if (M.A2) {
+      M.A2[(int64_t)r * M.ld + c] = df_split(v);
+      continue;
+    }
     M.A[(int64_t)r * M.ld + c] = v;
   }
 }
@@ -447,7 +542,12 @@ __global__ void assemble_local_kernel(const double* __restrict__ pairbuf, const 
 __global__ void dmax_kernel(const CholMat* __restrict__ mats, double* __restrict__ dmax) {
   const CholMat M = mats[blockIdx.x];
   double v = 0.0;
-  for (int r = threadIdx.x; r < M.n; r += blockDim.x) v = fmax(v, M.A[(int64_t)r * M.ld + r]);
+  for (int r = threadIdx.x; r < M.n; r += blockDim.x) {
+    double d;
+    if (M.A2) { const float2 a = M.A2[(int64_t)r * M.ld + r]; d = df_to_double(a.x, a.y); }
+    else d = M.A[(int64_t)r * M.ld + r];
+    v = fmax(v, d);
+  }
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
   __shared__ double red[8];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -463,7 +563,16 @@ __global__ void add_diag_kernel(const CholMat* __restrict__ mats, const int* __r
                                 const double* __restrict__ shift) {
   const CholMat M = mats[which[blockIdx.x]];
   const double s = shift[blockIdx.x];
-  for (int r = threadIdx.x; r < M.n; r += blockDim.x) M.A[(int64_t)r * M.ld + r] += s;
+  const float2 s2 = df_split(s);
+  for (int r = threadIdx.x; r < M.n; r += blockDim.x) {
+    if (M.A2) {
+      float2 a = M.A2[(int64_t)r * M.ld + r];
+      df_add(a.x, a.y, s2.x, s2.y);
+      M.A2[(int64_t)r * M.ld + r] = a;
+    } else {
+      M.A[(int64_t)r * M.ld + r] += s;
+    }
+  }
 }
 
 // ---- double-float apply (the inner Krylov preconditioner) ----
@@ -624,13 +733,20 @@ cudaError_t launch_add_diag(const CholMat* d_mats, const int* d_which, int nwhic
 
 cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, int* d_fail,
                              const double* d_dmax, int df, cudaStream_t st) {
-  potrf_diag_kernel<<<nmat, 256, 0, st>>>(d_mats, c0, d_fail, d_dmax);
-  int rest = maxn - c0 - NB;
-  if (rest > 0) {
-    trsm_panel_kernel<<<dim3((rest + 127) / 128, nmat), 128, 0, st>>>(d_mats, c0);
-    int T = (rest + 63) / 64;
-    if (df) syrk_update_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
-    else syrk_update_f64_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
+  const int rest = maxn - c0 - NB;
+  const int T = (rest + 63) / 64;
+  if (df) {
+    potrf_diag_df_kernel<<<nmat, NB * 8, 0, st>>>(d_mats, c0, d_fail, d_dmax);
+    if (rest > 0) {
+      trsm_panel_df_kernel<<<dim3((rest + 127) / 128, nmat), 128, 0, st>>>(d_mats, c0);
+      syrk_update_df_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
+    }
+  } else {
+    potrf_diag_kernel<<<nmat, 256, 0, st>>>(d_mats, c0, d_fail, d_dmax);
+    if (rest > 0) {
+      trsm_panel_kernel<<<dim3((rest + 127) / 128, nmat), 128, 0, st>>>(d_mats, c0);
+      syrk_update_f64_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
+    }
   }
   return cudaGetLastError();
 }
@@ -638,9 +754,12 @@ cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, 
 cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, int df, cudaStream_t st) {
   if (nmat == 0) return cudaSuccess;
   int nblk = (maxn + NB - 1) / NB;
-  trtri_diag_kernel<<<dim3(nblk, nmat), NB, 0, st>>>(d_mats);
-  if (df) trtri_col_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
-  else trtri_col_f64_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
+  if (df) {            // the diagonal blocks of X2 come from the factorisation
+    trtri_col_df_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
+  } else {
+    trtri_diag_kernel<<<dim3(nblk, nmat), NB, 0, st>>>(d_mats);
+    trtri_col_f64_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
+  }
   return cudaGetLastError();
 }
 

@@ -177,9 +177,10 @@ cudaError_t launch_syev_phase(const SyevBatch& b, int phase, cudaStream_t st);
 
 // chol.cu -- batched uneven Cholesky and triangular solves
 struct CholMat {
-  double* A;                 // n x n row-major (lower triangle used): A_i, then its Cholesky factor L_i
-  double* X;                 // n x n row-major (lower triangle used): L_i^{-1}
+  double* A;                 // n x n row-major (lower triangle used): A_i, then its Cholesky factor L_i (float64 mode)
+  double* X;                 // n x n row-major (lower triangle used): L_i^{-1} (float64 mode)
   float2* X2;                // L_i^{-1} as double-float pairs (same layout)
+  float2* A2;                // double-float A_i, then L_i (precision mode 1; null in float64 mode)
   int n;
   int ld;
 };
