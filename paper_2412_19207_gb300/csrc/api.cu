@@ -102,14 +102,15 @@ enum KId {
   K_POINTS, K_ASSEMBLE, K_RHS, K_GRAM, K_SYMM, K_EIG, K_PROJECT, K_PAIRGRAM, K_LOCALASM, K_ADDDIAG,
   K_CHOL, K_TRTRI, K_GATHER, K_TRMV_L, K_TRMV_U, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL,
   K_SPLIT, K_MATVEC_H_DF, K_MATVEC_HT_DF, K_GATHER_DF, K_TRMV_L_DF, K_TRMV_U_DF, K_OZ_SPLIT, K_GRAM_OZ,
-  K_PROJECT_OZ, K_EIG_VAL, K_EIG_VEC, K_EIG_ORTH, K_EIG_BACK, K_GRAMROWS, K_GRAMOP,
+  K_PROJECT_OZ, K_EIG_VAL, K_EIG_VEC, K_EIG_ORTH, K_EIG_BACK, K_GRAMROWS, K_GRAMOP, K_PAIRGRAM_OZ,
   K_COUNT
 };
 static const char* const KNAMES[K_COUNT] = {
   "points", "assemble", "rhs", "gram", "symmetrize", "eig_tridiag", "project", "pair_gram", "local_assemble",
   "add_diag", "cholesky", "trtri", "schwarz_gather", "trmv_lower", "trmv_upper", "schwarz_combine",
   "matvec_H", "matvec_HT", "dot", "vector", "eval", "split_df32", "matvec_H_df32", "matvec_HT_df32",
-  "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32", "ozaki_split", "gram_ozaki", "project_ozaki", "eig_values", "eig_vectors", "eig_orth", "eig_back", "gram_rows", "gramop_df32"};
+  "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32", "ozaki_split", "gram_ozaki", "project_ozaki", "eig_values", "eig_vectors", "eig_orth", "eig_back", "gram_rows", "gramop_df32",
+  "pair_gram_ozaki"};
 
 // Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
 // 1 = float64-ALU-bound (algorithmic flops count), 2 = bf16-tensor-core-bound
@@ -117,7 +118,7 @@ static const char* const KNAMES[K_COUNT] = {
 // on the float32 pipe (float64-equivalent flops count; the families marked in
 // KDF below run that way in precision mode 1).
 static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1,
-                                     0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1, 0, 0};
+                                     0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1, 0, 0, 2};
 
 static bool family_is_df(int k) { return k == K_PAIRGRAM || k == K_CHOL || k == K_TRTRI; }
 
@@ -212,6 +213,8 @@ struct rann_dd_handle {
   double* d_red = nullptr;     // multidot partials
   double* d_scal = nullptr;    // small device scalars
   double* h_scal = nullptr;    // pinned host mirror
+  char* h_stage = nullptr;     // pinned staging arena of the uploads
+  size_t stage_cap = 0, stage_used = 0;
   Prof prof;
   // algorithmic size aggregates for the kernel accounting
   double sumNp = 0, sumNm2 = 0, sumNmp = 0, sum_n = 0, sum_n2 = 0, sum_n3 = 0, pair_flops = 0;
@@ -263,13 +266,35 @@ static cudaError_t dalloc(rann_dd_handle* h, void** p, size_t bytes) {
   return e;
 }
 
+// Host-to-device uploads go through a pinned staging arena, so they are
+// asynchronous and the host can keep enqueueing; a region is reused only after
+// the stream has been synchronised (stream_sync resets the arena).
+static cudaError_t stream_sync(rann_dd_handle* h) {
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e == cudaSuccess) h->stage_used = 0;
+  return e;
+}
+
 template <typename T>
 static cudaError_t dupload(rann_dd_handle* h, T** dst, const std::vector<T>& v) {
   cudaError_t e = dalloc(h, (void**)dst, sizeof(T) * std::max<size_t>(v.size(), 1));
-  if (e != cudaSuccess) return e;
-  if (!v.empty()) e = cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, h->st);
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(h->st);   // the host vector may go out of scope
+  if (e != cudaSuccess || v.empty()) return e;
+  const size_t bytes = sizeof(T) * v.size(), need = (bytes + 255) & ~(size_t)255;
+  if (h->stage_used + need > h->stage_cap) {
+    if ((e = stream_sync(h)) != cudaSuccess) return e;
+    if (need > h->stage_cap) {
+      if (h->h_stage) cudaFreeHost(h->h_stage);
+      h->h_stage = nullptr;
+      h->stage_cap = 0;
+      const size_t cap = std::max<size_t>(need, (size_t)16 << 20);
+      if ((e = cudaMallocHost((void**)&h->h_stage, cap)) != cudaSuccess) return e;
+      h->stage_cap = cap;
+    }
+  }
+  memcpy(h->h_stage + h->stage_used, v.data(), bytes);
+  e = cudaMemcpyAsync(*dst, h->h_stage + h->stage_used, bytes, cudaMemcpyHostToDevice, h->st);
+  h->stage_used += need;
+  return e;
 }
 
 static void dfree(rann_dd_handle* h, void* p) {
@@ -460,6 +485,7 @@ extern "C" void rann_dd_destroy(rann_dd_handle* h) {
   for (void* p : h->allocs) cudaFreeAsync(p, h->st);
   cudaStreamSynchronize(h->st);
   if (h->h_scal) cudaFreeHost(h->h_scal);
+  if (h->h_stage) cudaFreeHost(h->h_stage);
   prof_resolve(h);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   delete h;
@@ -607,7 +633,7 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     CK(cudaMemcpyAsync(h->eig_host.data(), h->d_eig, sizeof(double) * m * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(info.data(), d_info, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(dev_ranks.data(), d_ranks, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    CK(stream_sync(h));
     dfree(h, d_tasks); dfree(h, d_mats); dfree(h, d_ns); dfree(h, d_lds); dfree(h, d_work); dfree(h, d_info);
     dfree(h, d_ranks);
     if (d_sl) { dfree(h, d_sl); dfree(h, d_e); }
@@ -619,7 +645,7 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     for (int j = 0; j < J; ++j)
       for (int c = 0; c < m; ++c) I[mm * j + (size_t)c * m + c] = 1.0;
     CK(cudaMemcpyAsync(h->d_V, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    CK(stream_sync(h));
   }
   // ranks (Sec. 4): sigma_k = sqrt(max(lambda_k, 0))
   int64_t woff = 0, boff = 0;
@@ -688,7 +714,6 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     KLA(h, K_OZ_SPLIT, 2, (8.0 + 2.0 * nsl) * (double)m * nrows, 0, launch_oz_split(d_sp, 2 * J, maxM, Kp, h->st));
     KLA(h, K_PROJECT_OZ, 1, 2.0 * nsl * (double)m * nrows + 8.0 * h->sumNp, 36.0 * 2.0 * h->sumNmp,
         launch_oz_gemm(d_gt, (int)gt.size(), h->st));
-    CK(cudaStreamSynchronize(h->st));
     dfree(h, d_sp); dfree(h, d_gt); dfree(h, d_sl); dfree(h, d_e);
   } else {
     std::vector<GemmTask> tasks;
@@ -702,7 +727,6 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     GemmTask* d_tasks;
     CK(dupload(h, &d_tasks, tasks));
     KLA(h, K_PROJECT, 1, 8.0 * (h->rows_total * (double)m + h->sumNp), 2.0 * h->sumNmp, launch_gemm_nn(d_tasks, (int)tasks.size(), h->st));
-    CK(cudaStreamSynchronize(h->st));
     dfree(h, d_tasks);
   }
   CK(cudaMemcpyAsync(h->d_sub, h->subs.data(), sizeof(SubDev) * J, cudaMemcpyHostToDevice, h->st));
@@ -738,7 +762,6 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   CK(dupload(h, &h->d_tile0, t0));
   CK(dalloc(h, (void**)&h->d_part, sizeof(double) * (size_t)h->nrtiles * h->maxP));
   CK(dalloc(h, (void**)&h->d_yscratch, sizeof(double) * (size_t)h->N));
-  CK(cudaStreamSynchronize(h->st));
   h->reduced = true;
   h->prec_kind = -1;
   return RANN_OK;
@@ -920,29 +943,77 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   int* d_ridx;
   CK(dupload(h, &d_ridx, ridx));
   CK(dalloc(h, (void**)&h->d_pairbuf, sizeof(double) * (size_t)std::max<int64_t>(pbuf, 1)));
-  for (size_t t = 0; t < pairs.size(); ++t) {
-    const SubDev &a = S[pairs[t].first], &b = S[pairs[t].second];
-    GemmTask g{};
-    // mode 1: the double-float copies of the blocks (same offsets) -- the Gram blocks of A_i only
-    // shape the preconditioner
-    if (h->inner_df) {
-      g.A = reinterpret_cast<const double*>(h->d_B2 + a.boff);
-      g.B = reinterpret_cast<const double*>(h->d_B2 + b.boff);
-    } else {
+  if (h->inner_df) {
+    // G_kl from digit slices of the gathered operands on the tensor cores (float64-accurate);
+    // a diagonal pair splits its one operand once
+    const int nsl = oz_slices();
+    std::vector<OzSplitTask> sp;
+    std::vector<int> spa(pairs.size()), spb(pairs.size());
+    int64_t soff = 0, eoff = 0;
+    int maxM = 1, maxKp = 32;
+    auto operand = [&](int k, int64_t start, int K) {
+      OzSplitTask o{};
+      o.X = h->d_B + S[k].boff; o.si = 1; o.sk = S[k].P;
+      o.gather = d_ridx + start;
+      o.M = S[k].p; o.K = K; o.Kp = oz_kpad(K);
+      o.e = reinterpret_cast<int*>(eoff);                    // patched below
+      o.out = reinterpret_cast<uint16_t*>(soff);
+      soff += (int64_t)nsl * o.M * o.Kp;
+      eoff += o.M;
+      maxM = std::max(maxM, o.M);
+      maxKp = std::max(maxKp, o.Kp);
+      sp.push_back(o);
+      return (int)sp.size() - 1;
+    };
+    for (size_t t = 0; t < pairs.size(); ++t) {
+      const int K = (int)(ridx_ranges[t].second - ridx_ranges[t].first);
+      spa[t] = operand(pairs[t].first, ridx_ranges[t].first, K);
+      spb[t] = pairs[t].first == pairs[t].second ? spa[t] : operand(pairs[t].second, ridx_ranges[t].second, K);
+    }
+    uint16_t* d_sl; int* d_e;
+    CK(dalloc(h, (void**)&d_sl, sizeof(uint16_t) * (size_t)std::max<int64_t>(soff, 1)));
+    CK(dalloc(h, (void**)&d_e, sizeof(int) * (size_t)std::max<int64_t>(eoff, 1)));
+    for (auto& o : sp) {
+      o.e = d_e + reinterpret_cast<int64_t>(o.e);
+      o.out = d_sl + reinterpret_cast<int64_t>(o.out);
+    }
+    std::vector<OzTask> gt;
+    for (size_t t = 0; t < pairs.size(); ++t) {
+      const OzSplitTask &a = sp[spa[t]], &b = sp[spb[t]];
+      OzTask g{};
+      g.A = a.out; g.B = b.out; g.ea = a.e; g.eb = b.e;
+      g.C = h->d_pairbuf + pair_off[(size_t)pairs[t].first * J + pairs[t].second];
+      g.M = a.M; g.N = b.M; g.Kp = a.Kp; g.ldc = b.M;
+      for (int tm = 0; tm < g.M; tm += 64)
+        for (int tn = 0; tn < g.N; tn += 64) { g.tm = tm; g.tn = tn; gt.push_back(g); }
+    }
+    OzSplitTask* d_sp; OzTask* d_gt;
+    CK(dupload(h, &d_sp, sp)); CK(dupload(h, &d_gt, gt));
+    double split_entries = 0;
+    for (auto& o : sp) split_entries += (double)o.M * o.K;
+    KLA(h, K_OZ_SPLIT, 2, (8.0 + 2.0 * nsl) * split_entries, 0,
+        launch_oz_split(d_sp, (int)sp.size(), maxM, maxKp, h->st));
+    KLA(h, K_PAIRGRAM_OZ, 1, 2.0 * nsl * split_entries, 36.0 * h->pair_flops,
+        launch_oz_gemm(d_gt, (int)gt.size(), h->st));
+    dfree(h, d_sp); dfree(h, d_gt); dfree(h, d_sl); dfree(h, d_e);
+  } else {
+    for (size_t t = 0; t < pairs.size(); ++t) {
+      const SubDev &a = S[pairs[t].first], &b = S[pairs[t].second];
+      GemmTask g{};
       g.A = h->d_B + a.boff;
       g.B = h->d_B + b.boff;
+      g.C = h->d_pairbuf + pair_off[(size_t)pairs[t].first * J + pairs[t].second];
+      g.ia = d_ridx + ridx_ranges[t].first;
+      g.ib = d_ridx + ridx_ranges[t].second;
+      g.K = (int)(ridx_ranges[t].second - ridx_ranges[t].first);
+      g.M = a.p; g.N = b.p; g.lda = a.P; g.ldb = b.P; g.ldc = b.p;
+      push_tiles(tasks, g, false);
     }
-    g.C = h->d_pairbuf + pair_off[(size_t)pairs[t].first * J + pairs[t].second];
-    g.ia = d_ridx + ridx_ranges[t].first;
-    g.ib = d_ridx + ridx_ranges[t].second;
-    g.K = (int)(ridx_ranges[t].second - ridx_ranges[t].first);
-    g.M = a.p; g.N = b.p; g.lda = a.P; g.ldb = b.P; g.ldc = b.p;
-    push_tiles(tasks, g, false);
+    GemmTask* d_tasks;
+    CK(dupload(h, &d_tasks, tasks));
+    KLA(h, K_PAIRGRAM, 1, 0, h->pair_flops, launch_gemm_tn(d_tasks, (int)tasks.size(), h->st));
+    dfree(h, d_tasks);
   }
-  GemmTask* d_tasks;
-  CK(dupload(h, &d_tasks, tasks));
-  if (h->inner_df) KLA(h, K_PAIRGRAM, 1, 0, h->pair_flops, launch_gemm_tn_df(d_tasks, (int)tasks.size(), h->st));
-  else KLA(h, K_PAIRGRAM, 1, 0, h->pair_flops, launch_gemm_tn(d_tasks, (int)tasks.size(), h->st));
   if (h->inner_df) TRY(build_gram_rows(h, pair_off));
   // local matrices A_i: table of block sources
   std::vector<CholMat> mats(J);
@@ -1004,35 +1075,31 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   CK(dalloc(h, (void**)&d_dmax, sizeof(double) * J));
   CK(dalloc(h, (void**)&d_fail, sizeof(int) * J));
   KLA(h, K_LOCALASM, 2, 8.0 * h->sum_n2, 0, launch_assemble_local(h->d_pairbuf, d_tab, d_tab_ptr, d_boffs, d_boff_ptr, h->d_mats, J, h->maxn, d_dmax, h->st));
-  // Cholesky with shift-and-retry for failed pivots
-  std::vector<int> fail(J, 0);
-  std::vector<int> active(J);
-  std::iota(active.begin(), active.end(), 0);
-  std::vector<double> dmax(J);
-  CK(cudaMemcpyAsync(dmax.data(), d_dmax, sizeof(double) * J, cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
+  // Cholesky with shift-and-retry for failed pivots: every attempt factors all
+  // J matrices (a retry reassembles them all); the largest diagonal entries
+  // stay on the device and reach the host only when a shift is needed
+  std::vector<double> dmax;
   std::vector<int> shifted(J, 0);
-  for (int attempt = 0; attempt < 6 && !active.empty(); ++attempt) {
-    std::vector<CholMat> am;
-    std::vector<double> adm;
-    for (int i : active) { am.push_back(mats[i]); adm.push_back(dmax[i]); }
-    CholMat* d_am; double* d_adm;
-    CK(dupload(h, &d_am, am)); CK(dupload(h, &d_adm, adm));
-    int amax = 0;
-    double chol_flops = 0.0;
-    for (auto& c : am) { amax = std::max(amax, c.n); chol_flops += (double)c.n * c.n * c.n / 3.0; }
+  double chol_flops = 0.0;
+  for (int i = 0; i < J; ++i) chol_flops += (double)mats[i].n * mats[i].n * mats[i].n / 3.0;
+  for (int attempt = 0; attempt < 6; ++attempt) {
     CK(cudaMemsetAsync(d_fail, 0, sizeof(int) * J, h->st));
-    for (int c0 = 0; c0 < amax; c0 += 32)
-      KLA(h, K_CHOL, (amax - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
-          launch_chol_step(d_am, (int)am.size(), amax, c0, d_fail, d_adm, h->prec_df, h->st));
-    std::vector<int> f(am.size());
-    CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * am.size(), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    for (int c0 = 0; c0 < h->maxn; c0 += 32)
+      KLA(h, K_CHOL, (h->maxn - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
+          launch_chol_step(h->d_mats, J, h->maxn, c0, d_fail, d_dmax, h->prec_df, h->st));
+    std::vector<int> f(J);
+    CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
+    CK(stream_sync(h));
     std::vector<int> next;
-    for (size_t t = 0; t < am.size(); ++t) if (f[t]) next.push_back(active[t]);
-    dfree(h, d_am); dfree(h, d_adm);
+    for (int i = 0; i < J; ++i) if (f[i]) next.push_back(i);
     if (next.empty()) break;
-    // rebuild the failed matrices and add a growing diagonal shift
+    if (attempt == 5) { rann_set_error("local Cholesky failed after shifts"); return RANN_ECUDA; }
+    if (dmax.empty()) {
+      dmax.resize(J);
+      CK(cudaMemcpyAsync(dmax.data(), d_dmax, sizeof(double) * J, cudaMemcpyDeviceToHost, h->st));
+      CK(stream_sync(h));
+    }
+    // rebuild all matrices and add a growing diagonal shift to the failed ones
     std::vector<CholMat> fm;
     std::vector<int> which;
     std::vector<double> shift;
@@ -1042,17 +1109,11 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
       fm.push_back(mats[i]);
       shift.push_back(dmax[i] * std::pow(10.0, -14 + 2 * attempt));
     }
-    // reassemble all (cheap relative to the factorisation), then shift the failed ones
     KLA(h, K_LOCALASM, 2, 8.0 * h->sum_n2, 0, launch_assemble_local(h->d_pairbuf, d_tab, d_tab_ptr, d_boffs, d_boff_ptr, h->d_mats, J, h->maxn, d_dmax, h->st));
     CholMat* d_fm; int* d_which; double* d_shift;
     CK(dupload(h, &d_fm, fm)); CK(dupload(h, &d_which, which)); CK(dupload(h, &d_shift, shift));
     KL(h, K_ADDDIAG, 1, launch_add_diag(d_fm, d_which, (int)which.size(), d_shift, h->maxn, h->st));
-    CK(cudaStreamSynchronize(h->st));
     dfree(h, d_fm); dfree(h, d_which); dfree(h, d_shift);
-    // the successful ones were overwritten by the reassembly: refactor everything still needed
-    active.clear();
-    for (int i = 0; i < J; ++i) active.push_back(i);
-    if (attempt == 5) { rann_set_error("local Cholesky failed after shifts"); return RANN_ECUDA; }
   }
   for (int i = 0; i < J; ++i) h->n_shifted += shifted[i];
   // X_i = L_i^{-1} for the parallel apply
@@ -1082,10 +1143,10 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   CK(dalloc(h, (void**)&h->d_y, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
   CK(dalloc(h, (void**)&h->d_g2, sizeof(float2) * (size_t)std::max<int64_t>(s_off[J], 1)));
   CK(dalloc(h, (void**)&h->d_ys2, sizeof(float2) * (size_t)std::max<int64_t>(s_off[J], 1)));
-  dfree(h, d_ridx); dfree(h, d_tasks); dfree(h, d_tab); dfree(h, d_tab_ptr); dfree(h, d_boffs); dfree(h, d_boff_ptr);
+  dfree(h, d_ridx); dfree(h, d_tab); dfree(h, d_tab_ptr); dfree(h, d_boffs); dfree(h, d_boff_ptr);
   dfree(h, d_dmax); dfree(h, d_fail); dfree(h, h->d_pairbuf);
   h->d_pairbuf = nullptr;
-  CK(cudaStreamSynchronize(h->st));
+  CK(stream_sync(h));
   return h->n_shifted ? RANN_LOCAL_SINGULAR : RANN_OK;
 }
 
@@ -1126,7 +1187,7 @@ extern "C" rann_status rann_dd_precond_apply(rann_dd_handle* h, const double* r_
 static rann_status dot_host(rann_dd_handle* h, const double* x, const double* y, int64_t n, double* out) {
   KLA(h, K_DOT, 1, 16.0 * n, 2.0 * n, launch_multidot(x, 0, 1, y, n, h->d_red, h->d_scal, h->st));
   CK(cudaMemcpyAsync(h->h_scal, h->d_scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
+  CK(stream_sync(h));
   *out = h->h_scal[0];
   return RANN_OK;
 }
@@ -1234,7 +1295,7 @@ static rann_status solve_cg_impl(rann_dd_handle* h, const double* F_dev, const d
       int dv[2];
       CK(cudaMemcpyAsync(dv, sd.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
       CK(cudaMemcpyAsync(&rel, sd.rel, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-      CK(cudaStreamSynchronize(h->st));
+      CK(stream_sync(h));
       it += dv[1];
       const bool inner_ok = dv[0] == 1;
       if (dv[0] == 2) { st = RANN_BREAKDOWN; break; }
@@ -1367,7 +1428,7 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
     int dj[2];
     CK(cudaMemcpyAsync(dj, sd.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(&rel, sd.rel, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    CK(stream_sync(h));
     const int jdone = dj[1];
     it += jdone;
     if (jdone == 0) rel = beta / mbnorm;
@@ -1375,7 +1436,7 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
     if (jdone == 0) break;
     CK(cudaMemcpyAsync(Hm.data(), sd.H, sizeof(double) * (size_t)jdone * k, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(g.data(), sd.g, sizeof(double) * jdone, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    CK(stream_sync(h));
     for (int i = jdone - 1; i >= 0; --i) {
       double sacc = g[i];
       for (int q = i + 1; q < jdone; ++q) sacc -= Hm[(size_t)i * k + q] * y[q];
@@ -1384,7 +1445,7 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
     CK(cudaMemcpyAsync(hv, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, h->st));
     KLA(h, K_VEC, 1, 8.0 * n * (jdone + 2), 2.0 * n * jdone,
         launch_add_combination(V, n, jdone, hv, W_dev, n, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    CK(stream_sync(h));
     // the next cycle recomputes the residual in float64 and decides convergence
   }
   double precrel = rel;
@@ -1464,7 +1525,7 @@ extern "C" rann_status rann_dd_eval(rann_dd_handle* h, const double* W_dev, cons
   CK(dupload(h, &d_tasks, tasks));
   KL(h, K_EVAL, 1, launch_gemm_nn(d_tasks, (int)tasks.size(), h->st));
   KL(h, K_EVAL, 1, launch_eval(h->P, h->d_sub, h->d_R, h->d_b, d_U, x_dev, n, u_dev, h->st));
-  CK(cudaStreamSynchronize(h->st));
+  CK(stream_sync(h));
   dfree(h, d_tasks);
   dfree(h, d_U);
   return RANN_OK;
@@ -1501,7 +1562,7 @@ extern "C" rann_status rann_dd_get_block(rann_dd_handle* h, int j, int which, do
     CK(cudaMemcpy2DAsync(out_host, sizeof(double) * S.p, h->d_B + S.boff, sizeof(double) * S.P,
                          sizeof(double) * S.p, S.N, cudaMemcpyDeviceToHost, h->st));
   }
-  CK(cudaStreamSynchronize(h->st));
+  CK(stream_sync(h));
   return RANN_OK;
 }
 
@@ -1513,7 +1574,7 @@ extern "C" rann_status rann_dd_get_pca(rann_dd_handle* h, int j, double* eig_hos
   if (V_host) {
     CK(cudaMemcpy2DAsync(V_host, sizeof(double) * h->subs[j].p, h->d_V + (size_t)m * m * j, sizeof(double) * m,
                          sizeof(double) * h->subs[j].p, m, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    CK(stream_sync(h));
   }
   return RANN_OK;
 }

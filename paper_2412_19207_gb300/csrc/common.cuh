@@ -82,8 +82,9 @@ cudaError_t launch_symmetrize(double* const* d_mats, const int* d_n, const int* 
                               int maxn, cudaStream_t st);
 
 // ozaki.cu -- float64-accurate products from bf16 digit slices on the tensor cores
-struct OzSplitTask {         // one operand: rows i < M of x(i, k) = X[i * si + k * sk], k < K
+struct OzSplitTask {         // one operand: rows i < M of x(i, k) = X[i * si + g(k) * sk], k < K
   const double* X;
+  const int* gather;         // g(k) = gather[k], or k when null
   int64_t si, sk;
   int M, K, Kp, pad_;        // Kp = oz_kpad(K)
   int* e;                    // [M] row exponents (out)

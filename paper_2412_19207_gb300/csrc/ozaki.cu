@@ -1,10 +1,11 @@
 // Float64-accurate products on the bf16 tensor cores (Ozaki splitting).
 //
 // GB300 executes float64 at 1/70 of its float32 rate while its bf16 tensor
-// cores run ~1500x faster than float64, so the two dense float64
-// contractions of the PCA -- the Gram matrices Psi_j^T Psi_j (Sec. 4) and the
-// reduced blocks H_j V_{p_j} (Eq. (system_new)) -- are formed from exact
-// integer digit slices:
+// cores run ~1500x faster than float64, so the dense float64 contractions --
+// the Gram matrices Psi_j^T Psi_j of the PCA (Sec. 4), the reduced blocks
+// H_j V_{p_j} (Eq. (system_new)) and the neighbour Gram blocks B_k^T B_l of
+// the Schwarz matrices (Sec. 3; operands gathered to the shared rows) -- are
+// formed from exact integer digit slices:
 //   * each row i of an operand is scaled by 2^{-e_i} (e_i = ceil(log2 max_k |x_ik|)),
 //     rounded to the 56-bit fixed-point integer X = round(x 2^{56 - e_i}) and
 //     written in balanced base 128, x = 2^{e_i} sum_{q=1}^{8} d_q 2^{-7q} + O(2^{e_i - 57}),
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const OzSplitTask* __rest
   const int a = threadIdx.x & 31, b = threadIdx.x >> 5;
   const long long* X = reinterpret_cast<const long long*>(t.X);
   const long long ABS = 0x7FFFFFFFFFFFFFFFll;
-  if (t.sk == 1) {      // rows contiguous in k: warp b owns rows i0 + b + 8c, lanes stride k
+  if (t.sk == 1 && !t.gather) {   // rows contiguous in k: warp b owns rows i0 + b + 8c, lanes stride k
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int i = i0 + b + 8 * c;
@@ -68,7 +69,10 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const OzSplitTask* __rest
     const int i = i0 + a;
     long long mx = 0;
     if (i < t.M)
-      for (int k = b; k < t.K; k += 8) mx = max(mx, X[(int64_t)i * t.si + (int64_t)k * t.sk] & ABS);
+      for (int k = b; k < t.K; k += 8) {
+        const int64_t kk = t.gather ? t.gather[k] : k;
+        mx = max(mx, X[(int64_t)i * t.si + kk * t.sk] & ABS);
+      }
     red[b][a] = mx;
     __syncthreads();
     if (b == 0) {
@@ -94,12 +98,14 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitTask* __rest
   if (i0 >= t.M || k0 >= t.Kp) return;
   __shared__ long long tile[32][33];
   const long long* X = reinterpret_cast<const long long*>(t.X);
-  const bool kfast = (t.sk == 1);
+  const bool kfast = (t.sk == 1 && !t.gather);
   for (int e = threadIdx.x; e < 1024; e += 256) {
     const int a = e & 31, b = e >> 5;
     const int ii = kfast ? b : a, kk = kfast ? a : b;
     const int i = i0 + ii, k = k0 + kk;
-    tile[ii][kk] = (i < t.M && k < t.K) ? X[(int64_t)i * t.si + (int64_t)k * t.sk] : 0ll;
+    long long v = 0;
+    if (i < t.M && k < t.K) v = X[(int64_t)i * t.si + (int64_t)(t.gather ? t.gather[k] : k) * t.sk];
+    tile[ii][kk] = v;
   }
   __syncthreads();
   const int64_t slice = (int64_t)t.M * t.Kp;
