@@ -360,7 +360,17 @@ extern "C" rann_status rann_dd_create(const rann_dd_desc* d, void* stream, rann_
   h->st = (cudaStream_t)stream;
   {
     int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+      // keep freed stream-ordered allocations cached in this process's default
+      // pool (by default they return to the driver at every synchronisation,
+      // and the large per-call buffers are then mapped again each time)
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+    }
     if (h->nsm < 1) h->nsm = 1;
   }
   ProbDev& P = h->P;
