@@ -218,7 +218,7 @@ def bench_ours(args, rank, world):
         "matvec": {"normal_rows_df32": gbps(["gramop_df32"]),
                    "H_f64": gbps(["matvec_H"]), "HT_f64": gbps(["matvec_HT"]),
                    "H_df32": gbps(["matvec_H_df32"]), "HT_df32": gbps(["matvec_HT_df32"]),
-                   "schwarz_apply_df32": gbps(["trmv_lower_df32", "trmv_upper_df32"])},
+                   "schwarz_apply_df32": gbps(["schwarz_apply_df32", "trmv_lower_df32", "trmv_upper_df32"])},
         "kernels": kernels,
         "gpu_launches": int(launches) * args.steps,
         "gpu_launches_per_step": int(launches),

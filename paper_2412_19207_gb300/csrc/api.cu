@@ -35,6 +35,12 @@ constexpr int DF_TILE_ROWS = 128;  // rows per block of the direct-load double-f
 cudaError_t launch_split_lower(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st);
 cudaError_t launch_schwarz_gather_df(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
                                      const int64_t* d_s_off, const double* d_r, float2* d_g2, cudaStream_t st);
+int schwarz_apply_rows();
+int schwarz_apply_max_subs();
+cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
+                                    const int* d_set_sub, const SubDev* d_sub, const double* d_r,
+                                    const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
+                                    cudaStream_t st);
 cudaError_t launch_trmv_lower_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
                                  const float2* d_g2, float2* d_y2, cudaStream_t st);
 cudaError_t launch_trmv_upper_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
@@ -102,7 +108,7 @@ enum KId {
   K_POINTS, K_ASSEMBLE, K_RHS, K_GRAM, K_SYMM, K_EIG, K_PROJECT, K_PAIRGRAM, K_LOCALASM, K_ADDDIAG,
   K_CHOL, K_TRTRI, K_GATHER, K_TRMV_L, K_TRMV_U, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL,
   K_SPLIT, K_MATVEC_H_DF, K_MATVEC_HT_DF, K_GATHER_DF, K_TRMV_L_DF, K_TRMV_U_DF, K_OZ_SPLIT, K_GRAM_OZ,
-  K_PROJECT_OZ, K_EIG_VAL, K_EIG_VEC, K_EIG_ORTH, K_EIG_BACK, K_GRAMROWS, K_GRAMOP, K_PAIRGRAM_OZ,
+  K_PROJECT_OZ, K_EIG_VAL, K_EIG_VEC, K_EIG_ORTH, K_EIG_BACK, K_GRAMROWS, K_GRAMOP, K_PAIRGRAM_OZ, K_SCHWARZ_DF,
   K_COUNT
 };
 static const char* const KNAMES[K_COUNT] = {
@@ -110,7 +116,7 @@ static const char* const KNAMES[K_COUNT] = {
   "add_diag", "cholesky", "trtri", "schwarz_gather", "trmv_lower", "trmv_upper", "schwarz_combine",
   "matvec_H", "matvec_HT", "dot", "vector", "eval", "split_df32", "matvec_H_df32", "matvec_HT_df32",
   "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32", "ozaki_split", "gram_ozaki", "project_ozaki", "eig_values", "eig_vectors", "eig_orth", "eig_back", "gram_rows", "gramop_df32",
-  "pair_gram_ozaki"};
+  "pair_gram_ozaki", "schwarz_apply_df32"};
 
 // Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
 // 1 = float64-ALU-bound (algorithmic flops count), 2 = bf16-tensor-core-bound
@@ -118,7 +124,7 @@ static const char* const KNAMES[K_COUNT] = {
 // on the float32 pipe (float64-equivalent flops count; the families marked in
 // KDF below run that way in precision mode 1).
 static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1,
-                                     0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1, 0, 0, 2};
+                                     0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1, 0, 0, 2, 0};
 
 static bool family_is_df(int k) { return k == K_PAIRGRAM || k == K_CHOL || k == K_TRTRI; }
 
@@ -203,6 +209,9 @@ struct rann_dd_handle {
   int64_t* d_p_off = nullptr;
   double* d_Amats = nullptr;
   float2* d_A2mats = nullptr;     // double-float A_i / L_i (precision mode 1 set-up)
+  int64_t* d_p_off32 = nullptr;   // per set: offset of its 32-row-block partial sums
+  int max_set_size = 0;           // most subdomains in one extended set
+  double* d_tpart32 = nullptr;
   bool prec_df = false;           // the set-up kept only double-float factors
   double* d_Xmats = nullptr;
   float2* d_X2mats = nullptr;
@@ -892,7 +901,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   for (void* p : {(void*)h->d_mats, (void*)h->d_set_ptr, (void*)h->d_set_sub, (void*)h->d_inc_ptr,
                   (void*)h->d_inc_set, (void*)h->d_inc_pos, (void*)h->d_s_off, (void*)h->d_s,
                   (void*)h->d_Amats, (void*)h->d_Xmats, (void*)h->d_g, (void*)h->d_y, (void*)h->d_tpart,
-                  (void*)h->d_p_off, (void*)h->d_X2mats, (void*)h->d_g2, (void*)h->d_ys2, (void*)h->d_A2mats})
+                  (void*)h->d_p_off, (void*)h->d_X2mats, (void*)h->d_g2, (void*)h->d_ys2, (void*)h->d_A2mats,
+                  (void*)h->d_p_off32, (void*)h->d_tpart32})
     dfree(h, p);
   h->d_mats = nullptr; h->d_Amats = nullptr; h->d_Xmats = nullptr; h->d_X2mats = nullptr; h->d_A2mats = nullptr;
   for (void* p : h->gram_allocs) dfree(h, p);
@@ -912,6 +922,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     h->set_ptr.push_back((int)h->set_sub.size());
   }
   h->nsets = J;
+  h->max_set_size = 0;
+  for (int i = 0; i < J; ++i) h->max_set_size = std::max(h->max_set_size, h->set_ptr[i + 1] - h->set_ptr[i]);
   // neighbour pairs (k <= l whose boxes share points) and their Gram blocks B_k^T B_l
   std::vector<int64_t> pair_off((size_t)J * J, -1);
   std::vector<GemmTask> tasks;
@@ -1133,6 +1145,13 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   for (int i = 0; i < J; ++i) p_off[i + 1] = p_off[i] + (int64_t)((mats[i].n + 255) / 256) * mats[i].n;
   CK(dupload(h, &h->d_p_off, p_off));
   CK(dalloc(h, (void**)&h->d_tpart, sizeof(double) * (size_t)std::max<int64_t>(p_off[J], 1)));
+  {
+    const int ar = schwarz_apply_rows();
+    std::vector<int64_t> p32(J + 1, 0);
+    for (int i = 0; i < J; ++i) p32[i + 1] = p32[i] + (int64_t)((mats[i].n + ar - 1) / ar) * mats[i].n;
+    CK(dupload(h, &h->d_p_off32, p32));
+    CK(dalloc(h, (void**)&h->d_tpart32, sizeof(double) * (size_t)std::max<int64_t>(p32[J], 1)));
+  }
   // incidence lists for the combine step: sets containing each subdomain, with its block offset
   std::vector<int> inc_ptr(1, 0), inc_set, inc_pos;
   for (int k = 0; k < J; ++k) {
@@ -1165,7 +1184,7 @@ static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, boo
     CK(cudaMemcpyAsync(z, r, sizeof(double) * h->dof, cudaMemcpyDeviceToDevice, h->st));
     return RANN_OK;
   }
-  if (fast) {
+  if (fast && h->max_set_size > schwarz_apply_max_subs()) {   // the fused kernel stages a bounded set
     KLA(h, K_GATHER_DF, 1, 16.0 * h->sum_n, 0,
         launch_schwarz_gather_df(h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub, h->d_s_off, r, h->d_g2, h->st));
     KLA(h, K_TRMV_L_DF, 1, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n,
@@ -1173,6 +1192,14 @@ static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, boo
     KLA(h, K_TRMV_U_DF, 2, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n,
         launch_trmv_upper_df(h->d_mats, h->nsets, h->maxn, h->d_s_off, h->d_p_off, h->d_ys2, h->d_tpart, h->d_s,
                              h->st));
+  } else if (fast) {
+    // s_i = X_i^T X_i R_i r with X_i = L_i^{-1} read from HBM once (fused, with the gather)
+    KLA(h, K_SCHWARZ_DF, 2, 4.0 * (h->sum_n2 + h->sum_n) + 8.0 * h->sum_n + 8.0 * h->dof,
+        2.0 * (h->sum_n2 + h->sum_n),
+        launch_schwarz_apply_df(h->d_mats, h->nsets, h->maxn, h->d_set_ptr, h->d_set_sub, h->d_sub, r, h->d_s_off,
+                                h->d_p_off32, h->d_tpart32, h->d_s, h->st));
+  }
+  if (fast) {
     KLA(h, K_COMBINE, 1, 8.0 * (h->sum_n + h->dof), 0, launch_schwarz_combine(h->d_sub, h->J, h->d_inc_ptr,
         h->d_inc_set, h->d_inc_pos, h->d_s_off, h->d_s, h->prec_kind, z, h->st));
     return RANN_OK;

@@ -669,6 +669,111 @@ __global__ void __launch_bounds__(256) trmv_upper_df_partial_kernel(const CholMa
   }
 }
 
+// Fused double-float apply s_i = X_i^T (X_i g_i), g_i = R_i r, for 32-row
+// blocks of X_i: the block's y rows are formed from the rows just loaded, and
+// the same rows (re-read from L2) give the block's share of X_i^T y, so X_i
+// crosses HBM once per apply.  part[rb][c] holds the share of row block rb;
+// schwarz_reduce32_kernel adds them in a fixed order.  The set's residual
+// entries are split to double-float and staged in shared memory in one flat
+// pass (a small table maps each column to its subdomain).
+constexpr int AR = 32;             // rows per block of the fused apply
+constexpr int AMAX_SUB = 27;       // most subdomains in an extended set (3^3)
+constexpr int ANT = 512;           // threads per block of the fused apply
+__global__ void __launch_bounds__(ANT, 2) schwarz_apply_df_kernel(const CholMat* __restrict__ mats,
+                                                               const int* __restrict__ set_ptr,
+                                                               const int* __restrict__ set_sub,
+                                                               const SubDev* __restrict__ subs,
+                                                               const double* __restrict__ r,
+                                                               const int64_t* __restrict__ p_off32,
+                                                               double* __restrict__ part) {
+  extern __shared__ float2 gs[];
+  __shared__ float2 ys[AR];
+  __shared__ int seg_c[AMAX_SUB + 1], seg_p[AMAX_SUB];
+  __shared__ int64_t seg_w[AMAX_SUB];
+  const int i = blockIdx.y;
+  const CholMat M = mats[i];
+  const int nb = (M.n + AR - 1) / AR;
+  if ((int)blockIdx.x >= nb) return;
+  const int rb = nb - 1 - (int)blockIdx.x;            // the long bottom row blocks start first
+  const int r0 = rb * AR;
+  const int r1 = min(M.n, r0 + AR);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q0 = set_ptr[i], nq = set_ptr[i + 1] - q0;
+  if (tid == 0) {
+    int c = 0;
+    for (int q = 0; q < nq; ++q) {
+      const SubDev& S = subs[set_sub[q0 + q]];
+      seg_c[q] = c; seg_p[q] = S.p; seg_w[q] = S.woff;
+      c += S.p;
+    }
+    seg_c[nq] = c;
+  }
+  __syncthreads();
+  for (int c = tid; c < r1; c += blockDim.x) {       // columns < r1 are all this block uses
+    int q = 0;
+    while (q + 1 < nq && seg_c[q + 1] <= c) ++q;
+    gs[c] = df_split(r[seg_w[q] + (c - seg_c[q])]);
+  }
+  if (tid < AR) ys[tid] = make_float2(0.f, 0.f);
+  __syncthreads();
+  // y rows: one warp per row, eight independent loads per lane in flight
+  for (int rr = warp; rr < r1 - r0; rr += ANT / 32) {
+    const int row = r0 + rr;
+    const float2* xr = M.X2 + (int64_t)row * M.ld;
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+    constexpr int U = 8;
+    for (int c0 = lane; c0 <= row; c0 += 32 * U) {
+      float2 a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) a[u] = (c0 + 32 * u <= row) ? xr[c0 + 32 * u] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c0 + 32 * u > row) break;
+        df_mac(h[u & 3], l[u & 3], a[u], gs[c0 + 32 * u]);
+      }
+    }
+    df_add(h[0], l[0], h[1], l[1]);
+    df_add(h[2], l[2], h[3], l[3]);
+    df_add(h[0], l[0], h[2], l[2]);
+    df_warp_sum(h[0], l[0]);
+    if (lane == 0) ys[rr] = make_float2(h[0], l[0]);
+  }
+  __syncthreads();
+  // the block's share of X^T y: thread per column, the block's rows r >= c
+  for (int c = tid; c < r1; c += blockDim.x) {
+    // eight of the block's rows of column c in flight at a time (rows r < c are zero in X)
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    for (int q = max(0, c - r0) & ~7; q < r1 - r0; q += 8) {
+      float2 a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int row = r0 + q + u;
+        a[u] = (row < r1 && row >= c) ? M.X2[(int64_t)row * M.ld + c] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        df_mac(h0, l0, a[u], ys[q + u]);
+        df_mac(h1, l1, a[u + 1], ys[q + u + 1]);
+      }
+    }
+    df_add(h0, l0, h1, l1);
+    part[p_off32[i] + (int64_t)rb * M.n + c] = df_to_double(h0, l0);
+  }
+}
+
+// s_i[c] = sum over the row blocks rb >= c / 32 of part[rb][c] (fixed order).
+__global__ void schwarz_reduce32_kernel(const CholMat* __restrict__ mats, const int64_t* __restrict__ s_off,
+                                        const int64_t* __restrict__ p_off32, const double* __restrict__ part,
+                                        double* __restrict__ s) {
+  const CholMat M = mats[blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= M.n) return;
+  const int nb = (M.n + AR - 1) / AR;
+  double acc = 0.0;
+  for (int rb = c / AR; rb < nb; ++rb) acc += part[p_off32[blockIdx.y] + (int64_t)rb * M.n + c];
+  s[s_off[blockIdx.y] + c] = acc;
+}
+
 // X2 = split(X) on the lower triangles.
 __global__ void split_lower_kernel(const CholMat* __restrict__ mats) {
   const CholMat M = mats[blockIdx.y];
@@ -791,5 +896,22 @@ cudaError_t launch_schwarz_combine(const SubDev* d_sub, int J, const int* d_inc_
   if (J == 0) return cudaSuccess;
   schwarz_combine_kernel<<<J, 256, 0, st>>>(d_sub, J, d_inc_ptr, d_inc_set, d_inc_pos, d_s_off, d_s,
                                              kind, d_z);
+  return cudaGetLastError();
+}
+
+int schwarz_apply_rows() { return AR; }
+int schwarz_apply_max_subs() { return AMAX_SUB; }
+
+cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
+                                    const int* d_set_sub, const SubDev* d_sub, const double* d_r,
+                                    const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
+                                    cudaStream_t st) {
+  if (nsets == 0) return cudaSuccess;
+  const int smem = (int)(sizeof(float2) * (size_t)maxn);
+  cudaError_t e = cudaFuncSetAttribute(schwarz_apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  schwarz_apply_df_kernel<<<dim3((maxn + AR - 1) / AR, nsets), ANT, smem, st>>>(d_mats, d_set_ptr, d_set_sub, d_sub,
+                                                                               d_r, d_p_off32, d_part);
+  schwarz_reduce32_kernel<<<dim3((maxn + 255) / 256, nsets), 256, 0, st>>>(d_mats, d_s_off, d_p_off32, d_part, d_s);
   return cudaGetLastError();
 }
