@@ -13,6 +13,11 @@ baseline use this package; the product path never does.
   * gmres: left-preconditioned restarted GMRES(k) with modified Gram-Schmidt
     and Givens rotations (Saad Alg. 9.4), stopping on
     ||M^{-1}(b - A x)|| / ||M^{-1} b|| (Sec. 5, Example 1 stopping rule).
+  * cgs, bicg: the two CG variants of Sec. 5 (Table 1b) -- conjugate
+    gradient squared (Sonneveld 1989) and biconjugate gradients (Fletcher
+    1976), preconditioned as in Barrett et al., "Templates for the Solution of
+    Linear Systems" (1994), Figs. 2.9 and 2.8; BiCG also applies A^T and M^T.
+    Both stop on ||b - A x|| / ||b||.
 No LAPACK: every factorisation here is written out.
 """
 from __future__ import annotations
@@ -163,5 +168,94 @@ def gmres(apply_A, b: np.ndarray, apply_M=None, rtol=1e-10, restart=50, maxit=10
             y[i] = (g[i] - Hh[i, i + 1:jdone] @ y[i + 1:]) / Hh[i, i] if Hh[i, i] != 0.0 else 0.0
         x = x + V[:jdone].T @ y
         if hist[-1] <= rtol:
+            break
+    return x, it, hist
+
+
+def cgs(apply_A, b: np.ndarray, apply_M=None, rtol=1e-10, maxit=1000):
+    """Preconditioned conjugate gradient squared from x0 = 0 (shadow residual
+    r~ = r_0); returns (x, iters, history of ||r||/||b||)."""
+    M = apply_M if apply_M else (lambda v: v.copy())
+    x = np.zeros_like(b)
+    r = b.copy()
+    rt = r.copy()
+    bnorm = np.linalg.norm(b)
+    hist = [1.0]
+    if bnorm == 0.0:
+        return x, 0, hist
+    rho_prev = 1.0
+    u = p = q = None
+    it = 0
+    while it < maxit:
+        rho = rt @ r
+        if rho == 0.0:
+            break
+        if it == 0:
+            u = r.copy()
+            p = u.copy()
+        else:
+            beta = rho / rho_prev
+            u = r + beta * q
+            p = u + beta * (q + beta * p)
+        ph = M(p)
+        vh = apply_A(ph)
+        sigma = rt @ vh
+        if sigma == 0.0:
+            break
+        alpha = rho / sigma
+        q = u - alpha * vh
+        uh = M(u + q)
+        x = x + alpha * uh
+        r = r - alpha * apply_A(uh)
+        rho_prev = rho
+        it += 1
+        rel = np.linalg.norm(r) / bnorm
+        hist.append(rel)
+        if rel <= rtol:
+            break
+    return x, it, hist
+
+
+def bicg(apply_A, apply_AT, b: np.ndarray, apply_M=None, apply_MT=None, rtol=1e-10, maxit=1000):
+    """Preconditioned biconjugate gradients from x0 = 0 (shadow residual
+    r~ = r_0); returns (x, iters, history of ||r||/||b||)."""
+    M = apply_M if apply_M else (lambda v: v.copy())
+    MT = apply_MT if apply_MT else (lambda v: v.copy())
+    x = np.zeros_like(b)
+    r = b.copy()
+    rt = r.copy()
+    bnorm = np.linalg.norm(b)
+    hist = [1.0]
+    if bnorm == 0.0:
+        return x, 0, hist
+    rho_prev = 1.0
+    p = pt = None
+    it = 0
+    while it < maxit:
+        z = M(r)
+        zt = MT(rt)
+        rho = z @ rt
+        if rho == 0.0:
+            break
+        if it == 0:
+            p, pt = z.copy(), zt.copy()
+        else:
+            beta = rho / rho_prev
+            p = z + beta * p
+            pt = zt + beta * pt
+        q = apply_A(p)
+        qt = apply_AT(pt)
+        sigma = pt @ q
+        if sigma == 0.0:
+            break
+        alpha = rho / sigma
+        x = x + alpha * p
+        r = r - alpha * q
+        rt = rt - alpha * qt
+        rho_prev = rho
+        it += 1
+        rel = np.linalg.norm(r) / bnorm
+        hist.append(rel)
+        if rel <= rtol:
             break
     return x, it, hist

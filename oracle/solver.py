@@ -140,6 +140,14 @@ class Schwarz:
             z[ix] += self.D[i] * s
         return z
 
+    def apply_t(self, r: np.ndarray) -> np.ndarray:
+        """M^T r = sum_i R_i^T A_i^{-T} D_i R_i r (A_i symmetric: A_i^{-T} = A_i^{-1})."""
+        z = np.zeros_like(r)
+        for i, ix in enumerate(self.idx):
+            V, beta, P = self.qr[i]
+            z[ix] += la.back_substitute(P, la.apply_qt(V, beta, self.D[i] * r[ix]))
+        return z
+
 
 def extended_sets(S: System, overlap_level: int = 1) -> List[List[int]]:
     p = S.problem
@@ -201,6 +209,11 @@ def solve(S: System, solver: str, precond: Optional[Schwarz], rtol=1e-10,
         W, it, hist = la.pcg(S.normal, bvec, M, rtol, maxit)
     elif solver == "gmres":
         W, it, hist = la.gmres(S.normal, bvec, M, rtol, restart, maxit)
+    elif solver == "cgs":
+        W, it, hist = la.cgs(S.normal, bvec, M, rtol, maxit)
+    elif solver == "bicg":
+        MT = precond.apply_t if precond is not None else None
+        W, it, hist = la.bicg(S.normal, S.normal, bvec, M, MT, rtol, maxit)   # H^T H is symmetric
     else:
         raise ValueError(solver)
     res = S.F - S.H(W)

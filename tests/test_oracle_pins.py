@@ -357,6 +357,54 @@ def test_cg_exact_in_n_steps():
     assert it == 3
 
 
+def test_cgs_and_bicg_against_dense_solve():
+    """The CG variants of Sec. 5 (Table 1b) reach the direct solution on an SPD
+    system (with a Jacobi preconditioner) and on a nonsymmetric one."""
+    rng = np.random.default_rng(31)
+    n = 30
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(1, 50, n)) @ Q.T
+    b = rng.standard_normal(n)
+    Dinv = 1.0 / np.diag(A)
+    xs = np.linalg.solve(A, b)
+    x, it, _ = la.cgs(lambda v: A @ v, b, lambda v: Dinv * v, 1e-12, 200)
+    np.testing.assert_allclose(x, xs, rtol=1e-9)
+    x, it, _ = la.bicg(lambda v: A @ v, lambda v: A.T @ v, b, lambda v: Dinv * v, lambda v: Dinv * v, 1e-12, 200)
+    np.testing.assert_allclose(x, xs, rtol=1e-9)
+    N = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.3
+    xn = np.linalg.solve(N, b)
+    x, _, _ = la.cgs(lambda v: N @ v, b, None, 1e-12, 200)
+    np.testing.assert_allclose(x, xn, rtol=1e-8)
+    x, _, _ = la.bicg(lambda v: N @ v, lambda v: N.T @ v, b, None, None, 1e-12, 200)
+    np.testing.assert_allclose(x, xn, rtol=1e-8)
+
+
+def test_bicg_needs_the_transposed_preconditioner():
+    """BiCG's shadow sequence uses M^T: with a nonsymmetric M it finishes in at
+    most n steps (finite termination), and M in place of M^T breaks that."""
+    rng = np.random.default_rng(32)
+    n = 24
+    N = np.eye(n) * 3 + rng.standard_normal((n, n)) * 0.4
+    Mm = np.linalg.inv(np.tril(N))                       # nonsymmetric approximate inverse
+    b = rng.standard_normal(n)
+    _, it, hist = la.bicg(lambda v: N @ v, lambda v: N.T @ v, b, lambda v: Mm @ v, lambda v: Mm.T @ v, 1e-10, 3 * n)
+    assert hist[-1] <= 1e-10 and it <= n + 2
+    _, it2, hist2 = la.bicg(lambda v: N @ v, lambda v: N.T @ v, b, lambda v: Mm @ v, lambda v: Mm @ v, 1e-10, n + 2)
+    assert hist2[-1] > 1e-10
+
+
+def test_cgs_terminates_with_few_distinct_eigenvalues():
+    """With 3 distinct eigenvalues the Krylov space closes after 3 steps; CGS,
+    which squares the CG polynomial, reaches the solution in at most 3."""
+    rng = np.random.default_rng(33)
+    Q, _ = np.linalg.qr(rng.standard_normal((20, 20)))
+    A = Q @ np.diag([1.0] * 7 + [3.0] * 7 + [10.0] * 6) @ Q.T
+    b = rng.standard_normal(20)
+    x, it, _ = la.cgs(lambda v: A @ v, b, None, 1e-11, 50)
+    assert it <= 3
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9)
+
+
 # ------------------------------------------------------------- Schwarz --
 
 @pytest.mark.parametrize("kind", ["ras", "sas"])
@@ -369,6 +417,20 @@ def test_restricted_partition_of_identity(kind):
     for ix, D in zip(M.idx, M.D):
         np.add.at(total, ix, D)
     np.testing.assert_allclose(total, 1.0, rtol=1e-15)
+
+
+@pytest.mark.parametrize("kind", ["as", "sas", "ras"])
+def test_schwarz_transpose_is_the_adjoint(kind):
+    """M^T = sum_i R_i^T A_i^{-1} D_i R_i: <M^T r, s> = <r, M s> (D_i moves to the input side)."""
+    p = ri.config("multiscale2d", small=True)
+    S = sv.build_system(p)
+    M = sv.schwarz(S, kind)
+    rng = np.random.default_rng(5)
+    r, s = rng.standard_normal(S.dof), rng.standard_normal(S.dof)
+    lhs, rhs = M.apply_t(r) @ s, r @ M.apply(s)
+    assert abs(lhs - rhs) <= 1e-8 * np.linalg.norm(M.apply_t(r)) * np.linalg.norm(s)
+    if kind != "as":   # not symmetric: M^T differs from M
+        assert np.linalg.norm(M.apply_t(r) - M.apply(r)) > 1e-6 * np.linalg.norm(M.apply(r))
 
 
 def test_local_matrix_is_restricted_normal_matrix():
@@ -420,9 +482,20 @@ def test_krylov_matches_direct_least_squares():
     p = ri.config("multiscale2d", small=True)
     S = sv.build_system(p)
     qr = sv.solve_qr(S)
-    for kind, solver in [("as", "cg"), ("sas", "gmres")]:
+    for kind, solver in [("as", "cg"), ("sas", "gmres"), ("as", "cgs"), ("sas", "cgs"), ("ras", "cgs"),
+                         ("as", "bicg"), ("sas", "bicg")]:
         sol = sv.solve(S, solver, sv.schwarz(S, kind), 1e-10, 50, 3000)
-        assert abs(sol.res_ls - qr.res_ls) <= 1e-8 * np.linalg.norm(S.F)
+        assert abs(sol.res_ls - qr.res_ls) <= 1e-8 * np.linalg.norm(S.F), (kind, solver)
+
+
+@pytest.mark.parametrize("solver", ["cgs", "bicg"])
+def test_cg_variants_one_iteration_on_2x2(solver):
+    """With M_AS^{-1} H^T H = J I on J = 2x2 (Table 2), any Krylov method is done
+    after one step; Table 1b's variants included."""
+    p = ri.config("poisson2d_2x2")
+    S = sv.build_system(p)
+    sol = sv.solve(S, solver, sv.schwarz(S, "as"), 1e-8)
+    assert sol.iters == 1
 
 
 def test_manufactured_solution_accuracy():
