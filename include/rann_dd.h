@@ -175,6 +175,18 @@ rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_dev, double* 
  * (Sec. 5 Example 1 stopping rule).  Any preconditioner kind. */
 rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* F_dev, double* W_dev,
                                     double rtol, int restart, int maxit, rann_dd_stats* stats);
+/* The CG variants of Sec. 5 (Table 1b) on the normal equations from W = 0,
+ * with any preconditioner kind: conjugate gradient squared (Sonneveld) and
+ * biconjugate gradients (Fletcher; its shadow sequence applies A^T = A and
+ * M^{-T}), both preconditioned as in Barrett et al., Templates (1994), and
+ * both stopping when ||H^T F - H^T H W|| / ||H^T F|| <= rtol (the float64
+ * residual; the recurrences run as iterative refinement like CG).  Returns
+ * RANN_BREAKDOWN when a recurrence scalar vanishes or is not finite.
+ * F_dev [N], W_dev [DoF]. */
+rann_status rann_dd_solve_cgs(rann_dd_handle* h, const double* F_dev, double* W_dev,
+                              double rtol, int maxit, rann_dd_stats* stats);
+rann_status rann_dd_solve_bicg(rann_dd_handle* h, const double* F_dev, double* W_dev,
+                               double rtol, int maxit, rann_dd_stats* stats);
 
 /* Adjoint of the solve (differentiation through Algorithm 1 step 6; the
  * paper's normal equations of Sec. 2 are symmetric, so the adjoint system is
@@ -218,6 +230,9 @@ rann_status rann_dd_matvec(rann_dd_handle* h, const double* x_dev, double* y_dev
 rann_status rann_dd_matvec_t(rann_dd_handle* h, const double* y_dev, double* z_dev);
 rann_status rann_dd_normal_matvec(rann_dd_handle* h, const double* x_dev, double* z_dev);
 rann_status rann_dd_precond_apply(rann_dd_handle* h, const double* r_dev, double* z_dev);
+/* z = M^{-T} r = sum_i R_i^T A_i^{-1} D_i R_i r (the transposed Schwarz
+ * preconditioner of Sec. 3; equals M^{-1} for AS). */
+rann_status rann_dd_precond_apply_t(rann_dd_handle* h, const double* r_dev, double* z_dev);
 
 /* Inspection (synchronising copies to host memory).
  * which = 0: Psi_j, 1: H_j (both N_j x m, after assemble, before pca);

@@ -87,6 +87,8 @@ SIGNATURES = {
     "rann_dd_setup_precond": (_I, [_P, _I, _I]),
     "rann_dd_solve_cg_as": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
     "rann_dd_solve_gmres_ras": (_I, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(Stats)]),
+    "rann_dd_solve_cgs": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
+    "rann_dd_solve_bicg": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
     "rann_dd_eval": (_I, [_P, _P, _P, _L, _P]),
     "rann_dd_solve_backward": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
     "rann_dd_set_precision": (_I, [_P, _I]),
@@ -94,6 +96,7 @@ SIGNATURES = {
     "rann_dd_matvec_t": (_I, [_P, _P, _P]),
     "rann_dd_normal_matvec": (_I, [_P, _P, _P]),
     "rann_dd_precond_apply": (_I, [_P, _P, _P]),
+    "rann_dd_precond_apply_t": (_I, [_P, _P, _P]),
     "rann_dd_block_info": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_I)]),
     "rann_dd_get_block": (_I, [_P, _I, _I, _P, _P]),
     "rann_dd_get_pca": (_I, [_P, _I, _P, _P]),
@@ -281,6 +284,21 @@ class RannDD:
         _check(s, "rann_dd_solve_gmres_ras", allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return W, st.as_dict() | {"status": STATUS[s]}
 
+    def _solve_variant(self, fn, F, rtol, maxit, W, allow_not_converged):
+        W = W if W is not None else self._empty(self.sizes()["dof"])
+        st = Stats()
+        s = getattr(self._lib, fn)(self._h, _dptr(F), _dptr(W), rtol, maxit, ctypes.byref(st))
+        _check(s, fn, allow=(NOT_CONVERGED,) if allow_not_converged else ())
+        return W, st.as_dict() | {"status": STATUS[s]}
+
+    def solve_cgs(self, F, rtol=1e-10, maxit=2000, W=None, allow_not_converged=False):
+        """Conjugate gradient squared on the normal equations (Sec. 5, Table 1b)."""
+        return self._solve_variant("rann_dd_solve_cgs", F, rtol, maxit, W, allow_not_converged)
+
+    def solve_bicg(self, F, rtol=1e-10, maxit=2000, W=None, allow_not_converged=False):
+        """Biconjugate gradients on the normal equations (Sec. 5, Table 1b)."""
+        return self._solve_variant("rann_dd_solve_bicg", F, rtol, maxit, W, allow_not_converged)
+
     def solve_backward(self, gW, rtol=1e-10, maxit=2000, lam=None):
         """lam = (H^T H)^{-1} gW with the stored preconditioner (adjoint of the solve)."""
         lam = lam if lam is not None else self._empty(self.sizes()["dof"])
@@ -325,6 +343,11 @@ class RannDD:
     def precond_apply(self, r, z=None):
         z = z if z is not None else self._empty(self.sizes()["dof"])
         _check(self._lib.rann_dd_precond_apply(self._h, _dptr(r), _dptr(z)), "rann_dd_precond_apply")
+        return z
+
+    def precond_apply_t(self, r, z=None):
+        z = z if z is not None else self._empty(self.sizes()["dof"])
+        _check(self._lib.rann_dd_precond_apply_t(self._h, _dptr(r), _dptr(z)), "rann_dd_precond_apply_t")
         return z
 
     # -- kernel accounting ------------------------------------------------

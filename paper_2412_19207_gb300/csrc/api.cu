@@ -34,20 +34,22 @@ cudaError_t launch_matvec_HT_df(const ProbDev& P, const SubDev* d_sub, int J, co
 constexpr int DF_TILE_ROWS = 128;  // rows per block of the direct-load double-float matvec
 cudaError_t launch_split_lower(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st);
 cudaError_t launch_schwarz_gather_df(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
-                                     const int64_t* d_s_off, const double* d_r, float2* d_g2, cudaStream_t st);
+                                     const int64_t* d_s_off, const double* d_r, float2* d_g2, int wkind,
+                                     const int* d_inc_ptr, cudaStream_t st);
 int schwarz_apply_rows();
 int schwarz_apply_max_subs();
 cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
                                     const int* d_set_sub, const SubDev* d_sub, const double* d_r,
                                     const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
-                                    cudaStream_t st);
+                                    int wkind, const int* d_inc_ptr, cudaStream_t st);
 cudaError_t launch_trmv_lower_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
                                  const float2* d_g2, float2* d_y2, cudaStream_t st);
 cudaError_t launch_trmv_upper_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
                                  const int64_t* d_p_off, const float2* d_y2, double* d_part, double* d_s,
                                  cudaStream_t st);
 cudaError_t launch_schwarz_gather(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
-                                  const int64_t* d_s_off, const double* d_r, double* d_g, cudaStream_t st);
+                                  const int64_t* d_s_off, const double* d_r, double* d_g, int wkind,
+                                  const int* d_inc_ptr, cudaStream_t st);
 cudaError_t launch_trmv_lower(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
                               const double* d_g, double* d_y, cudaStream_t st);
 cudaError_t launch_trmv_upper(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
@@ -1179,14 +1181,20 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   return h->n_shifted ? RANN_LOCAL_SINGULAR : RANN_OK;
 }
 
-static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, bool fast = false) {
+// z = M^{-1} r, or with transpose z = M^{-T} r = sum_i R_i^T A_i^{-1} D_i R_i r
+// (D_i moves to the gather, the combine sums unweighted).
+static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, bool fast = false,
+                              bool transpose = false) {
   if (h->prec_kind == RANN_PREC_NONE) {
     CK(cudaMemcpyAsync(z, r, sizeof(double) * h->dof, cudaMemcpyDeviceToDevice, h->st));
     return RANN_OK;
   }
+  const int wkind = transpose ? h->prec_kind : RANN_PREC_AS;
+  const int ckind = transpose ? RANN_PREC_AS : h->prec_kind;
   if (fast && h->max_set_size > schwarz_apply_max_subs()) {   // the fused kernel stages a bounded set
     KLA(h, K_GATHER_DF, 1, 16.0 * h->sum_n, 0,
-        launch_schwarz_gather_df(h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub, h->d_s_off, r, h->d_g2, h->st));
+        launch_schwarz_gather_df(h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub, h->d_s_off, r, h->d_g2, wkind,
+                                 h->d_inc_ptr, h->st));
     KLA(h, K_TRMV_L_DF, 1, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n,
         launch_trmv_lower_df(h->d_mats, h->nsets, h->maxn, h->d_s_off, h->d_g2, h->d_ys2, h->st));
     KLA(h, K_TRMV_U_DF, 2, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n,
@@ -1197,18 +1205,19 @@ static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, boo
     KLA(h, K_SCHWARZ_DF, 2, 4.0 * (h->sum_n2 + h->sum_n) + 8.0 * h->sum_n + 8.0 * h->dof,
         2.0 * (h->sum_n2 + h->sum_n),
         launch_schwarz_apply_df(h->d_mats, h->nsets, h->maxn, h->d_set_ptr, h->d_set_sub, h->d_sub, r, h->d_s_off,
-                                h->d_p_off32, h->d_tpart32, h->d_s, h->st));
+                                h->d_p_off32, h->d_tpart32, h->d_s, wkind, h->d_inc_ptr, h->st));
   }
   if (fast) {
     KLA(h, K_COMBINE, 1, 8.0 * (h->sum_n + h->dof), 0, launch_schwarz_combine(h->d_sub, h->J, h->d_inc_ptr,
-        h->d_inc_set, h->d_inc_pos, h->d_s_off, h->d_s, h->prec_kind, z, h->st));
+        h->d_inc_set, h->d_inc_pos, h->d_s_off, h->d_s, ckind, z, h->st));
     return RANN_OK;
   }
-  KLA(h, K_GATHER, 1, 16.0 * h->sum_n, 0, launch_schwarz_gather(h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub, h->d_s_off, r, h->d_g, h->st));
+  KLA(h, K_GATHER, 1, 16.0 * h->sum_n, 0, launch_schwarz_gather(h->nsets, h->d_set_ptr, h->d_set_sub, h->d_sub,
+                                                                 h->d_s_off, r, h->d_g, wkind, h->d_inc_ptr, h->st));
   KLA(h, K_TRMV_L, 1, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n, launch_trmv_lower(h->d_mats, h->nsets, h->maxn, h->d_s_off, h->d_g, h->d_y, h->st));
   KLA(h, K_TRMV_U, 2, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n, launch_trmv_upper(h->d_mats, h->nsets, h->maxn, h->d_s_off, h->d_p_off, h->d_y, h->d_tpart, h->d_s, h->st));
   KLA(h, K_COMBINE, 1, 8.0 * (h->sum_n + h->dof), 0, launch_schwarz_combine(h->d_sub, h->J, h->d_inc_ptr, h->d_inc_set, h->d_inc_pos, h->d_s_off, h->d_s,
-                            h->prec_kind, z, h->st));
+                            ckind, z, h->st));
   return RANN_OK;
 }
 
@@ -1364,6 +1373,160 @@ static rann_status solve_cg_impl(rann_dd_handle* h, const double* F_dev, const d
   }
   if (st == RANN_NOT_CONVERGED) rann_set_error("CG reached maxit=%d at rel. residual %.3e", maxit, true_rel);
   return st;
+}
+
+static rann_status prec_inner_t(rann_dd_handle* h, const double* r, double* z) {
+  return prec_apply(h, r, z, h->inner_df != 0 || h->prec_df, true);
+}
+
+// The CG variants of Sec. 5 (Table 1b) on H^T H W = H^T F: conjugate gradient
+// squared (Sonneveld) and biconjugate gradients (Fletcher; the shadow
+// sequence uses A^T = A and M^{-T}), preconditioned as in Barrett et al.,
+// Templates (1994), shadow residual = the cycle's initial residual.  Like CG,
+// each cycle solves the correction equation with the inner operator and
+// preconditioner until ||r_rec|| <= rtol ||b|| and then recomputes the float64
+// residual; the exit is on ||b - H^T H W|| / ||b||.
+static rann_status solve_variant_impl(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol, int maxit,
+                                      rann_dd_stats* stats, bool bicg) {
+  REQUIRE(h && F_dev && W_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve before setup_precond");
+  REQUIRE(rtol > 0 && maxit >= 0, RANN_EINVAL, "bad rtol/maxit");
+  const int64_t n = h->dof;
+  Workspace ws{h, {}};
+  double *b = ws.get(n), *r = ws.get(n), *rr = ws.get(n), *rt = ws.get(n), *u = ws.get(n), *pv = ws.get(n),
+         *q = ws.get(n), *ph = ws.get(n), *vh = ws.get(n), *t = ws.get(n), *t2 = ws.get(n);
+  REQUIRE(b && r && rr && rt && u && pv && q && ph && vh && t && t2, RANN_ENOMEM, "workspace allocation failed");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, h->st));
+  TRY(rann_dd_matvec_t(h, F_dev, b));
+  CK(cudaMemsetAsync(W_dev, 0, sizeof(double) * n, h->st));
+  CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  double bb;
+  TRY(dot_host(h, b, b, n, &bb));
+  const double bnorm = std::sqrt(bb);
+  rann_status st = RANN_NOT_CONVERGED;
+  int it = 0;
+  double rel = 1.0, true_rel = 1.0;
+  auto copy = [&](double* dst, const double* src) {
+    return cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
+  };
+  auto axpby = [&](double a, const double* x, double c, double* y) -> rann_status {
+    KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(a, x, c, y, n, h->st));
+    return RANN_OK;
+  };
+  if (!(bnorm > 0.0)) {
+    st = std::isfinite(bb) ? RANN_OK : RANN_BREAKDOWN;
+    rel = true_rel = 0.0;
+  } else {
+    for (int cycle = 0; cycle < 30; ++cycle) {
+      CK(copy(rr, r));
+      CK(copy(rt, r));
+      double rho_prev = 1.0;
+      bool inner_ok = false, first = true;
+      while (it < maxit) {
+        double rho, sigma, r2;
+        if (!bicg) {
+          // CGS: rho = r~.r; u = r + beta q; p = u + beta (q + beta p)
+          TRY(dot_host(h, rt, rr, n, &rho));
+          if (!(rho != 0.0) || !std::isfinite(rho)) { st = RANN_BREAKDOWN; break; }
+          if (first) {
+            CK(copy(u, rr)); CK(copy(pv, rr));
+          } else {
+            const double beta = rho / rho_prev;
+            CK(copy(u, rr)); TRY(axpby(beta, q, 1.0, u));
+            CK(copy(t, q)); TRY(axpby(beta, pv, 1.0, t));
+            TRY(axpby(1.0, u, beta, t));                  // t = u + beta (q + beta p)
+            CK(copy(pv, t));
+          }
+          TRY(prec_inner(h, pv, ph));
+          TRY(op_inner(h, ph, vh));
+          TRY(dot_host(h, rt, vh, n, &sigma));
+          if (!(sigma != 0.0) || !std::isfinite(sigma)) { st = RANN_BREAKDOWN; break; }
+          const double alpha = rho / sigma;
+          CK(copy(q, u)); TRY(axpby(-alpha, vh, 1.0, q));   // q = u - alpha A M p
+          CK(copy(t, u)); TRY(axpby(1.0, q, 1.0, t));       // t = u + q
+          TRY(prec_inner(h, t, ph));                          // u^ = M (u + q)
+          TRY(axpby(alpha, ph, 1.0, W_dev));
+          TRY(op_inner(h, ph, t2));
+          TRY(axpby(-alpha, t2, 1.0, rr));
+        } else {
+          // BiCG: z = M r, z~ = M^T r~, rho = z.r~; p = z + beta p, p~ = z~ + beta p~
+          TRY(prec_inner(h, rr, ph));
+          TRY(prec_inner_t(h, rt, vh));
+          TRY(dot_host(h, ph, rt, n, &rho));
+          if (!(rho != 0.0) || !std::isfinite(rho)) { st = RANN_BREAKDOWN; break; }
+          if (first) {
+            CK(copy(pv, ph)); CK(copy(u, vh));
+          } else {
+            const double beta = rho / rho_prev;
+            TRY(axpby(1.0, ph, beta, pv));
+            TRY(axpby(1.0, vh, beta, u));                    // u holds p~
+          }
+          TRY(op_inner(h, pv, q));
+          TRY(op_inner(h, u, t));                             // A^T p~ = A p~ (H^T H is symmetric)
+          TRY(dot_host(h, u, q, n, &sigma));
+          if (!(sigma != 0.0) || !std::isfinite(sigma)) { st = RANN_BREAKDOWN; break; }
+          const double alpha = rho / sigma;
+          TRY(axpby(alpha, pv, 1.0, W_dev));
+          TRY(axpby(-alpha, q, 1.0, rr));
+          TRY(axpby(-alpha, t, 1.0, rt));
+        }
+        first = false;
+        rho_prev = rho;
+        ++it;
+        TRY(dot_host(h, rr, rr, n, &r2));
+        rel = std::sqrt(r2) / bnorm;
+        if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
+        if (rel <= rtol) { inner_ok = true; break; }
+      }
+      if (st == RANN_BREAKDOWN) break;
+      // float64 residual of the accumulated W
+      TRY(rann_dd_normal_matvec(h, W_dev, q));
+      CK(copy(r, b));
+      TRY(axpby(-1.0, q, 1.0, r));
+      double rr2;
+      TRY(dot_host(h, r, r, n, &rr2));
+      const double prev = true_rel;
+      true_rel = std::sqrt(rr2) / bnorm;
+      if (!std::isfinite(true_rel)) { st = RANN_BREAKDOWN; break; }
+      if (true_rel <= rtol) { st = RANN_OK; break; }
+      if (!inner_ok || it >= maxit) break;
+      if (true_rel >= prev) break;   // refinement no longer reduces the float64 residual
+    }
+  }
+  CK(cudaEventRecord(e1, h->st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  if (stats) {
+    stats->iters = it;
+    stats->rel_res_true = true_rel;
+    stats->rel_res_rec = rel;
+    stats->rel_res_prec = -1.0;
+    stats->ms_solve = ms;
+    stats->n_shifted = h->n_shifted;
+  }
+  if (st == RANN_NOT_CONVERGED)
+    rann_set_error("%s reached maxit=%d at rel. residual %.3e", bicg ? "BiCG" : "CGS", maxit, true_rel);
+  return st;
+}
+
+extern "C" rann_status rann_dd_solve_cgs(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
+                                         int maxit, rann_dd_stats* stats) {
+  return solve_variant_impl(h, F_dev, W_dev, rtol, maxit, stats, false);
+}
+
+extern "C" rann_status rann_dd_solve_bicg(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
+                                          int maxit, rann_dd_stats* stats) {
+  return solve_variant_impl(h, F_dev, W_dev, rtol, maxit, stats, true);
+}
+
+extern "C" rann_status rann_dd_precond_apply_t(rann_dd_handle* h, const double* r_dev, double* z_dev) {
+  REQUIRE(h && r_dev && z_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "precond_apply_t before setup_precond");
+  return prec_apply(h, r_dev, z_dev, h->prec_df, true);
 }
 
 // Left-preconditioned GMRES on H^T H W = b with b = H^T F (F_dev) or b given (b_dev).

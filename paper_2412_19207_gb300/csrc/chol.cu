@@ -411,16 +411,26 @@ __global__ void __launch_bounds__(256) trtri_col_f64_kernel(const CholMat* __res
 }
 
 // ---- apply ----
+// Weight of subdomain k's entries in set i when D_i moves to the input side
+// (the transposed apply M^T = sum_i R_i^T A_i^{-1} D_i R_i): 0 = none.
+__device__ __forceinline__ double input_weight(int wkind, int k, int i, const int* __restrict__ inc_ptr) {
+  if (wkind == RANN_PREC_SAS) return 1.0 / (double)(inc_ptr[k + 1] - inc_ptr[k]);
+  if (wkind == RANN_PREC_RAS) return k == i ? 1.0 : 0.0;
+  return 1.0;
+}
+
 // g_i = R_i r (gather the extended-set residual).
 __global__ void schwarz_gather_kernel(const int* __restrict__ set_ptr, const int* __restrict__ set_sub,
                                       const SubDev* __restrict__ subs, const int64_t* __restrict__ s_off,
-                                      const double* __restrict__ r, double* __restrict__ g) {
+                                      const double* __restrict__ r, double* __restrict__ g, int wkind,
+                                      const int* __restrict__ inc_ptr) {
   const int i = blockIdx.x;
   double* gi = g + s_off[i];
   int off = 0;
   for (int q = set_ptr[i]; q < set_ptr[i + 1]; ++q) {
     const SubDev& S = subs[set_sub[q]];
-    for (int c = threadIdx.x; c < S.p; c += blockDim.x) gi[off + c] = r[S.woff + c];
+    const double w = input_weight(wkind, set_sub[q], i, inc_ptr);
+    for (int c = threadIdx.x; c < S.p; c += blockDim.x) gi[off + c] = w * r[S.woff + c];
     off += S.p;
   }
 }
@@ -579,13 +589,15 @@ __global__ void add_diag_kernel(const CholMat* __restrict__ mats, const int* __r
 
 __global__ void schwarz_gather_df_kernel(const int* __restrict__ set_ptr, const int* __restrict__ set_sub,
                                          const SubDev* __restrict__ subs, const int64_t* __restrict__ s_off,
-                                         const double* __restrict__ r, float2* __restrict__ g2) {
+                                         const double* __restrict__ r, float2* __restrict__ g2, int wkind,
+                                         const int* __restrict__ inc_ptr) {
   const int i = blockIdx.x;
   float2* gi = g2 + s_off[i];
   int off = 0;
   for (int q = set_ptr[i]; q < set_ptr[i + 1]; ++q) {
     const SubDev& S = subs[set_sub[q]];
-    for (int c = threadIdx.x; c < S.p; c += blockDim.x) gi[off + c] = df_split(r[S.woff + c]);
+    const double w = input_weight(wkind, set_sub[q], i, inc_ptr);
+    for (int c = threadIdx.x; c < S.p; c += blockDim.x) gi[off + c] = df_split(w * r[S.woff + c]);
     off += S.p;
   }
 }
@@ -685,11 +697,13 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_df_kernel(const CholMat*
                                                                const SubDev* __restrict__ subs,
                                                                const double* __restrict__ r,
                                                                const int64_t* __restrict__ p_off32,
-                                                               double* __restrict__ part) {
+                                                               double* __restrict__ part, int wkind,
+                                                               const int* __restrict__ inc_ptr) {
   extern __shared__ float2 gs[];
   __shared__ float2 ys[AR];
   __shared__ int seg_c[AMAX_SUB + 1], seg_p[AMAX_SUB];
   __shared__ int64_t seg_w[AMAX_SUB];
+  __shared__ double seg_d[AMAX_SUB];
   const int i = blockIdx.y;
   const CholMat M = mats[i];
   const int nb = (M.n + AR - 1) / AR;
@@ -704,6 +718,7 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_df_kernel(const CholMat*
     for (int q = 0; q < nq; ++q) {
       const SubDev& S = subs[set_sub[q0 + q]];
       seg_c[q] = c; seg_p[q] = S.p; seg_w[q] = S.woff;
+      seg_d[q] = input_weight(wkind, set_sub[q0 + q], i, inc_ptr);
       c += S.p;
     }
     seg_c[nq] = c;
@@ -712,7 +727,7 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_df_kernel(const CholMat*
   for (int c = tid; c < r1; c += blockDim.x) {       // columns < r1 are all this block uses
     int q = 0;
     while (q + 1 < nq && seg_c[q + 1] <= c) ++q;
-    gs[c] = df_split(r[seg_w[q] + (c - seg_c[q])]);
+    gs[c] = df_split(seg_d[q] * r[seg_w[q] + (c - seg_c[q])]);
   }
   if (tid < AR) ys[tid] = make_float2(0.f, 0.f);
   __syncthreads();
@@ -796,8 +811,9 @@ cudaError_t launch_split_lower(const CholMat* d_mats, int nmat, int maxn, cudaSt
 }
 
 cudaError_t launch_schwarz_gather_df(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
-                                     const int64_t* d_s_off, const double* d_r, float2* d_g2, cudaStream_t st) {
-  schwarz_gather_df_kernel<<<nsets, 256, 0, st>>>(d_set_ptr, d_set_sub, d_sub, d_s_off, d_r, d_g2);
+                                     const int64_t* d_s_off, const double* d_r, float2* d_g2, int wkind,
+                                     const int* d_inc_ptr, cudaStream_t st) {
+  schwarz_gather_df_kernel<<<nsets, 256, 0, st>>>(d_set_ptr, d_set_sub, d_sub, d_s_off, d_r, d_g2, wkind, d_inc_ptr);
   return cudaGetLastError();
 }
 
@@ -869,8 +885,9 @@ cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, int df, cuda
 }
 
 cudaError_t launch_schwarz_gather(int nsets, const int* d_set_ptr, const int* d_set_sub, const SubDev* d_sub,
-                                  const int64_t* d_s_off, const double* d_r, double* d_g, cudaStream_t st) {
-  schwarz_gather_kernel<<<nsets, 256, 0, st>>>(d_set_ptr, d_set_sub, d_sub, d_s_off, d_r, d_g);
+                                  const int64_t* d_s_off, const double* d_r, double* d_g, int wkind,
+                                  const int* d_inc_ptr, cudaStream_t st) {
+  schwarz_gather_kernel<<<nsets, 256, 0, st>>>(d_set_ptr, d_set_sub, d_sub, d_s_off, d_r, d_g, wkind, d_inc_ptr);
   return cudaGetLastError();
 }
 
@@ -905,13 +922,14 @@ int schwarz_apply_max_subs() { return AMAX_SUB; }
 cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
                                     const int* d_set_sub, const SubDev* d_sub, const double* d_r,
                                     const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
-                                    cudaStream_t st) {
+                                    int wkind, const int* d_inc_ptr, cudaStream_t st) {
   if (nsets == 0) return cudaSuccess;
   const int smem = (int)(sizeof(float2) * (size_t)maxn);
   cudaError_t e = cudaFuncSetAttribute(schwarz_apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   schwarz_apply_df_kernel<<<dim3((maxn + AR - 1) / AR, nsets), ANT, smem, st>>>(d_mats, d_set_ptr, d_set_sub, d_sub,
-                                                                               d_r, d_p_off32, d_part);
+                                                                               d_r, d_p_off32, d_part, wkind,
+                                                                               d_inc_ptr);
   schwarz_reduce32_kernel<<<dim3((maxn + 255) / 256, nsets), 256, 0, st>>>(d_mats, d_s_off, d_p_off32, d_part, d_s);
   return cudaGetLastError();
 }
