@@ -224,6 +224,7 @@ struct rann_dd_handle {
   double* d_red = nullptr;     // multidot partials
   double* d_scal = nullptr;    // small device scalars
   double* h_scal = nullptr;    // pinned host mirror
+  int* d_ozerr = nullptr;      // non-zero once a tensor-core product pipeline timed out
   char* h_stage = nullptr;     // pinned staging arena of the uploads
   size_t stage_cap = 0, stage_used = 0;
   Prof prof;
@@ -492,6 +493,8 @@ extern "C" rann_status rann_dd_create(const rann_dd_desc* d, void* stream, rann_
       (e = dupload(h, &h->d_tiles, tiles)) != cudaSuccess ||
       (e = dalloc(h, (void**)&h->d_red, sizeof(double) * 256 * 130)) != cudaSuccess ||
       (e = dalloc(h, (void**)&h->d_scal, sizeof(double) * 256)) != cudaSuccess ||
+      (e = dalloc(h, (void**)&h->d_ozerr, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->d_ozerr, 0, sizeof(int), h->st)) != cudaSuccess ||
       (e = cudaMallocHost((void**)&h->h_scal, sizeof(double) * 256)) != cudaSuccess) {
     rann_set_error("create: %s", cudaGetErrorString(e));
     rann_dd_destroy(h);
@@ -604,20 +607,22 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
         t.X = h->d_Psi + S.row0 * m; t.si = 1; t.sk = m;       // row i of Psi_j^T
         t.M = m; t.K = S.N; t.Kp = oz_kpad(S.N); t.e = d_e + (size_t)m * j; t.out = d_sl + soff;
         OzTask g{};
-        g.A = t.out; g.B = t.out; g.ea = t.e; g.eb = t.e; g.C = h->d_V + mm * j;
+        g.ia = j; g.ib = j; g.ea = t.e; g.eb = t.e; g.C = h->d_V + mm * j;
         g.M = m; g.N = m; g.Kp = t.Kp; g.ldc = m;
-        for (int tm = 0; tm < m; tm += 64)
-          for (int tn = tm; tn < m; tn += 64) { g.tm = tm; g.tn = tn; gt.push_back(g); }
+        for (int tm = 0; tm < m; tm += OZ_TILE_M)      // tiles meeting the upper triangle
+          for (int tn = tm; tn < m; tn += OZ_TILE_N) { g.tm = tm; g.tn = tn; gt.push_back(g); }
         soff += (int64_t)nsl * m * t.Kp;
       }
-      OzSplitTask* d_sp; OzTask* d_gt;
-      CK(dupload(h, &d_sp, sp)); CK(dupload(h, &d_gt, gt));
+      std::vector<OzMap> maps;
+      CK(oz_encode_maps(sp, maps));
+      OzSplitTask* d_sp; OzTask* d_gt; OzMap* d_maps;
+      CK(dupload(h, &d_sp, sp)); CK(dupload(h, &d_gt, gt)); CK(dupload(h, &d_maps, maps));
       d_tasks = d_gt;
       KLA(h, K_OZ_SPLIT, 2, (8.0 + 2.0 * nsl) * h->rows_total * m, 0,
           launch_oz_split(d_sp, J, m, maxKp, h->st));
       KLA(h, K_GRAM_OZ, 1, 2.0 * nsl * h->rows_total * m, 36.0 * h->sumNm2,
-          launch_oz_gemm(d_gt, (int)gt.size(), h->st));
-      dfree(h, d_sp);
+          launch_oz_gemm(d_gt, (int)gt.size(), d_maps, h->d_ozerr, h->st));
+      dfree(h, d_sp); dfree(h, d_maps);
     } else {
       std::vector<GemmTask> tasks;
       for (int j = 0; j < J; ++j) {
@@ -654,7 +659,10 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     CK(cudaMemcpyAsync(h->eig_host.data(), h->d_eig, sizeof(double) * m * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(info.data(), d_info, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(dev_ranks.data(), d_ranks, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
+    int ozerr = 0;
+    CK(cudaMemcpyAsync(&ozerr, h->d_ozerr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(stream_sync(h));
+    REQUIRE(ozerr == 0, RANN_ECUDA, "tensor-core Gram product: pipeline wait %d timed out", ozerr);
     dfree(h, d_tasks); dfree(h, d_mats); dfree(h, d_ns); dfree(h, d_lds); dfree(h, d_work); dfree(h, d_info);
     dfree(h, d_ranks);
     if (d_sl) { dfree(h, d_sl); dfree(h, d_e); }
@@ -725,17 +733,19 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
       vrow += S.p;
       maxM = std::max(maxM, S.N);
       OzTask g{};
-      g.A = a.out; g.B = b.out; g.ea = a.e; g.eb = b.e; g.C = h->d_B + S.boff;
+      g.ia = 2 * j; g.ib = 2 * j + 1; g.ea = a.e; g.eb = b.e; g.C = h->d_B + S.boff;
       g.M = S.N; g.N = S.p; g.Kp = Kp; g.ldc = S.P;
-      for (int tm = 0; tm < S.N; tm += 64)
-        for (int tn = 0; tn < S.p; tn += 64) { g.tm = tm; g.tn = tn; gt.push_back(g); }
+      for (int tm = 0; tm < S.N; tm += OZ_TILE_M)
+        for (int tn = 0; tn < S.p; tn += OZ_TILE_N) { g.tm = tm; g.tn = tn; gt.push_back(g); }
     }
-    OzSplitTask* d_sp; OzTask* d_gt;
-    CK(dupload(h, &d_sp, sp)); CK(dupload(h, &d_gt, gt));
+    std::vector<OzMap> maps;
+    CK(oz_encode_maps(sp, maps));
+    OzSplitTask* d_sp; OzTask* d_gt; OzMap* d_maps;
+    CK(dupload(h, &d_sp, sp)); CK(dupload(h, &d_gt, gt)); CK(dupload(h, &d_maps, maps));
     KLA(h, K_OZ_SPLIT, 2, (8.0 + 2.0 * nsl) * (double)m * nrows, 0, launch_oz_split(d_sp, 2 * J, maxM, Kp, h->st));
     KLA(h, K_PROJECT_OZ, 1, 2.0 * nsl * (double)m * nrows + 8.0 * h->sumNp, 36.0 * 2.0 * h->sumNmp,
-        launch_oz_gemm(d_gt, (int)gt.size(), h->st));
-    dfree(h, d_sp); dfree(h, d_gt); dfree(h, d_sl); dfree(h, d_e);
+        launch_oz_gemm(d_gt, (int)gt.size(), d_maps, h->d_ozerr, h->st));
+    dfree(h, d_sp); dfree(h, d_gt); dfree(h, d_maps); dfree(h, d_sl); dfree(h, d_e);
   } else {
     std::vector<GemmTask> tasks;
     for (int j = 0; j < J; ++j) {
@@ -1005,21 +1015,23 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     for (size_t t = 0; t < pairs.size(); ++t) {
       const OzSplitTask &a = sp[spa[t]], &b = sp[spb[t]];
       OzTask g{};
-      g.A = a.out; g.B = b.out; g.ea = a.e; g.eb = b.e;
+      g.ia = spa[t]; g.ib = spb[t]; g.ea = a.e; g.eb = b.e;
       g.C = h->d_pairbuf + pair_off[(size_t)pairs[t].first * J + pairs[t].second];
       g.M = a.M; g.N = b.M; g.Kp = a.Kp; g.ldc = b.M;
-      for (int tm = 0; tm < g.M; tm += 64)
-        for (int tn = 0; tn < g.N; tn += 64) { g.tm = tm; g.tn = tn; gt.push_back(g); }
+      for (int tm = 0; tm < g.M; tm += OZ_TILE_M)
+        for (int tn = 0; tn < g.N; tn += OZ_TILE_N) { g.tm = tm; g.tn = tn; gt.push_back(g); }
     }
-    OzSplitTask* d_sp; OzTask* d_gt;
-    CK(dupload(h, &d_sp, sp)); CK(dupload(h, &d_gt, gt));
+    std::vector<OzMap> maps;
+    CK(oz_encode_maps(sp, maps));
+    OzSplitTask* d_sp; OzTask* d_gt; OzMap* d_maps;
+    CK(dupload(h, &d_sp, sp)); CK(dupload(h, &d_gt, gt)); CK(dupload(h, &d_maps, maps));
     double split_entries = 0;
     for (auto& o : sp) split_entries += (double)o.M * o.K;
     KLA(h, K_OZ_SPLIT, 2, (8.0 + 2.0 * nsl) * split_entries, 0,
         launch_oz_split(d_sp, (int)sp.size(), maxM, maxKp, h->st));
     KLA(h, K_PAIRGRAM_OZ, 1, 2.0 * nsl * split_entries, 36.0 * h->pair_flops,
-        launch_oz_gemm(d_gt, (int)gt.size(), h->st));
-    dfree(h, d_sp); dfree(h, d_gt); dfree(h, d_sl); dfree(h, d_e);
+        launch_oz_gemm(d_gt, (int)gt.size(), d_maps, h->d_ozerr, h->st));
+    dfree(h, d_sp); dfree(h, d_gt); dfree(h, d_maps); dfree(h, d_sl); dfree(h, d_e);
   } else {
     for (size_t t = 0; t < pairs.size(); ++t) {
       const SubDev &a = S[pairs[t].first], &b = S[pairs[t].second];
@@ -1112,8 +1124,11 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
       KLA(h, K_CHOL, (h->maxn - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
           launch_chol_step(h->d_mats, J, h->maxn, c0, d_fail, d_dmax, h->prec_df, h->st));
     std::vector<int> f(J);
+    int ozerr = 0;
     CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&ozerr, h->d_ozerr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(stream_sync(h));
+    REQUIRE(ozerr == 0, RANN_ECUDA, "tensor-core product (projection / pair Gram): pipeline wait %d timed out", ozerr);
     std::vector<int> next;
     for (int i = 0; i < J; ++i) if (f[i]) next.push_back(i);
     if (next.empty()) break;

@@ -88,11 +88,12 @@ struct OzSplitTask {         // one operand: rows i < M of x(i, k) = X[i * si + 
   int64_t si, sk;
   int M, K, Kp, pad_;        // Kp = oz_kpad(K)
   int* e;                    // [M] row exponents (out)
-  uint16_t* out;             // [oz_slices()][M][Kp] bf16 digit slices (out)
+  uint16_t* out;             // [oz_slices()][Kp/8][M][8] bf16 digit slices (out), 16-byte aligned
 };
-struct OzTask {              // one 64 x 64 tile of C = A B^T (A: M x K slices, B: N x K slices)
-  const uint16_t* A;
-  const uint16_t* B;
+constexpr int OZ_TILE_M = 128, OZ_TILE_N = 64;   // C tile of one block (rows of A x rows of B)
+struct alignas(64) OzMap { unsigned char bytes[128]; };   // a TMA tensor map of one operand's slices
+struct OzTask {              // one OZ_TILE_M x OZ_TILE_N tile of C = A B^T (A: M x K slices, B: N x K slices)
+  int ia, ib;                // split operands of A and B (their tensor maps: maps[2 ia], maps[2 ib + 1])
   const int* ea;
   const int* eb;
   double* C;                 // M x N (ldc)
@@ -101,8 +102,13 @@ struct OzTask {              // one 64 x 64 tile of C = A B^T (A: M x K slices, 
 };
 int oz_slices();
 int oz_kpad(int K);
+// Host: the two TMA tensor maps (A role, B role) of each operand's slices,
+// from the device addresses in ops[].out (no device work).
+cudaError_t oz_encode_maps(const std::vector<OzSplitTask>& ops, std::vector<OzMap>& maps);
 cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, int maxKp, cudaStream_t st);
-cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, cudaStream_t st);
+// d_maps: device copy of oz_encode_maps' output (64-byte aligned); d_err: set
+// non-zero if a pipeline wait timed out (the tile is then not written).
+cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, const OzMap* d_maps, int* d_err, cudaStream_t st);
 
 // krylov.cu -- device-resident state of one GMRES cycle
 constexpr int GMRES_MAX_RESTART = 120;

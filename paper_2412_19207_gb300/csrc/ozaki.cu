@@ -15,30 +15,42 @@
 //     The 36 slice products of the weight groups s = 2..9 are kept (the rest
 //     lie below 2^-63 relative); the products of one group accumulate on the
 //     tensor cores in float32, exact because every partial sum over a
-//     256-long k chunk is an integer below 2^24 (group 9 peaks at
-//     256 * 40960 < 2^24); at the end of a chunk the eight group sums are
-//     joined exactly in two 46-bit integers, hi = sum_{s<=5} c_s 128^{5-s} and
-//     lo = sum_{s>=6} c_s 128^{9-s}, which enter the float64 accumulator as
-//     hi 2^-35 + lo 2^-63 (two roundings per chunk).
+//     256-long k chunk is an integer below 2^24 (group s = g + 2 is bounded
+//     by 256 * 4096 (g + 3) for g >= 1 and by 2^22 for g = 0); at the end of
+//     a chunk the eight group sums are joined exactly in integers,
+//     hi = sum_{s<=5} c_s 128^{5-s} and lo = sum_{s>=6} c_s 128^{9-s}, which
+//     accumulate over the chunks without rounding (exact for K < 2^17); the
+//     tile ends with the single rounding of hi 2^-35 + lo 2^-63 to float64.
 // The error is a few units of 2^-53 K max_k|a_ik| max_k|b_jk|, the float64
 // bound.  The scheme is that of Ozaki, Ogita, Oishi & Rump, "Error-free
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 59 (2012).
+//
+// Blackwell mapping of one 128 x 64 tile of C: the eight group accumulators
+// (8 x 64 float32 columns) fill the 512 columns of tensor memory; a 4-stage
+// ring of k steps of 16 is filled by 4-D TMA boxes (all eight slices of the
+// tile's 128 A rows and 64 B rows, landing in the no-swizzle K-major
+// core-matrix layout); one thread issues the 36 tcgen05.mma of a k step; eight
+// warps drain the accumulators to the integer chunk sums through tcgen05.ld.
 #include "common.cuh"
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 namespace {
 
-constexpr int OZ_Q = 8;            // digit slices per operand
-constexpr int OZ_SMAX = 9;         // largest weight group q + r kept
-constexpr int OZ_NG = OZ_SMAX - 1; // weight groups s = 2..9
-constexpr int OZ_CHUNK = 256;      // k span of one exact float32 accumulation
-constexpr int OZ_TM = 64, OZ_TN = 64, OZ_TK = 32;
-constexpr int OZ_THREADS = 512;    // 16 warps, each a 16 x 16 sub-tile
-constexpr int OZ_LDW = OZ_TK / 2 + 4;   // shared row length in 32-bit words (2 bf16 each; padded)
-constexpr int OZ_ROWS = 2 * OZ_Q * OZ_TM;           // staged rows: A_1..A_8 then B_1..B_8
-constexpr int OZ_STAGE_WORDS = OZ_ROWS * OZ_LDW;    // one k step (80 KB)
-static_assert(OZ_CHUNK % OZ_TK == 0, "chunk must be a multiple of the k step");
-static_assert(OZ_TM == OZ_TN, "A and B tiles share the staging layout");
+constexpr int OZ_Q = 8;             // digit slices per operand
+constexpr int OZ_NG = 8;            // weight groups s = 2..9 (g = s - 2 = q + r, zero-based)
+constexpr int OZ_TK = 16;           // k of one stage (one tcgen05.mma step)
+constexpr int OZ_CHUNK_STEPS = 16;  // 256 k per exact float32 accumulation
+constexpr int OZ_STAGES = 4;
+constexpr int OZ_A_BYTES = OZ_Q * OZ_TILE_M * OZ_TK * 2;   // 32 KB
+constexpr int OZ_B_BYTES = OZ_Q * OZ_TILE_N * OZ_TK * 2;   // 16 KB
+constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024; // + alignment slack
+constexpr int OZ_DRAIN_WARPS = 8;   // warps 2..9: lane quarter w % 4, column half (w - 2) / 4
+constexpr int OZ_THREADS = 32 * (2 + OZ_DRAIN_WARPS);
+constexpr long long OZ_WAIT_CYCLES = 2000000000ll;          // ~1 s: a wait this long is a fault
+static_assert(OZ_NG * OZ_TILE_N == 512, "the group accumulators fill tensor memory");
 
 __device__ __forceinline__ uint16_t bf16_of_small_int(int d) {
   // |d| <= 128: exactly representable in bf16 (8 significant bits); the bf16
@@ -90,8 +102,9 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const OzSplitTask* __rest
   }
 }
 
-// Digit slices of a 32 x 32 tile: slice q of row i at out[q * M * Kp + i * Kp + k],
-// zero for k >= K (padding up to Kp).
+// Digit slices of a 32 x 32 tile.  Slice q of row i, column k sits at
+// out[q M Kp + ((k / 8) M + i) 8 + k % 8] (8 k of a row contiguous, then the
+// rows, then the groups of 8 k, then the slices), zero for k >= K.
 __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitTask* __restrict__ tasks) {
   const OzSplitTask t = tasks[blockIdx.z];
   const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
@@ -110,7 +123,8 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitTask* __rest
   __syncthreads();
   const int64_t slice = (int64_t)t.M * t.Kp;
   for (int e = threadIdx.x; e < 1024; e += 256) {
-    const int kk = e & 31, ii = e >> 5;
+    // a warp covers 8 k x 4 rows: 64 contiguous bytes of every slice
+    const int k8 = e & 7, ii = (e >> 3) & 31, kk = (e >> 8) * 8 + k8;
     const int i = i0 + ii, k = k0 + kk;
     if (i >= t.M) continue;
     // X = round(|x| 2^{56 - e_i}) with the sign of x, from the float64 fields
@@ -124,7 +138,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitTask* __rest
       else if (sh > -60) v = (mant + (1ll << (-sh - 1))) >> (-sh);
       if (bits < 0) v = -v;
     }
-    uint16_t* o = t.out + (int64_t)i * t.Kp + k;
+    uint16_t* o = t.out + ((int64_t)(k >> 3) * t.M + i) * 8 + k8;
 #pragma unroll
     for (int q = OZ_Q - 1; q >= 1; --q) {            // balanced base-128 digits, least significant first
       const long long d = ((v + 64) & 127) - 64;
@@ -135,136 +149,287 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitTask* __rest
   }
 }
 
-__device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+// ---- Blackwell primitives (inline PTX) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
 }
-
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(gptr), "r"(src_bytes));
+// Bounded wait: gives up after ~1 s (or as soon as another role gave up),
+// raising the block's abort flag and the launch's error word.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err, int code) {
+  const long long t0 = clock64();
+  for (int it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 63) {
+      if (*abort) return false;
+      if (clock64() - t0 > OZ_WAIT_CYCLES) {
+        *abort = 1;
+        atomicCAS(err, 0, code);
+        return false;
+      }
+    }
+  }
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-// Stage the 16 digit-slice tiles (A_1..A_8 rows tm.., B_1..B_8 rows tn..) of
-// the k step starting at k0: 16 x 64 rows x 64 bytes, 16-byte copies; rows
-// past M (N) are zero-filled.
-__device__ __forceinline__ void oz_stage(const OzTask& t, uint32_t sbase, int k0) {
-  const int kw = t.Kp >> 1;
-  const uint32_t* gA = reinterpret_cast<const uint32_t*>(t.A);
-  const uint32_t* gB = reinterpret_cast<const uint32_t*>(t.B);
-  for (int c = threadIdx.x; c < OZ_ROWS * 4; c += OZ_THREADS) {
-    const int srow = c >> 2, part = c & 3;
-    const int sl = srow / OZ_TM, row = srow % OZ_TM;
-    const bool isA = sl < OZ_Q;
-    const int q = isA ? sl : sl - OZ_Q;
-    const int gi = (isA ? t.tm : t.tn) + row, lim = isA ? t.M : t.N;
-    const uint32_t* base = isA ? gA : gB;
-    const int64_t slice = (int64_t)lim * kw;
-    const bool ok = gi < lim;
-    const uint32_t* src = base + (ok ? q * slice + (int64_t)gi * kw + (k0 >> 1) + part * 4 : 0);
-    cp_async16(sbase + (uint32_t)((srow * OZ_LDW + part * 4) * 4), src, ok ? 16 : 0);
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {   // bounded, no flags
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity) && clock64() - t0 < OZ_WAIT_CYCLES) {
   }
 }
 
-// One 64 x 64 tile of C = A B^T from the digit slices: 16 warps of 16 x 16
-// (1 x 2 mma tiles of 16 x 8), eight float32 accumulator sets (one per
-// weight group), k steps double-buffered through cp.async.
-__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzTask* __restrict__ tasks) {
-  extern __shared__ __align__(16) uint32_t oz_smem[];
+// 4-D TMA box (8 k, rows, 2 groups of 8 k, 8 slices) into shared memory; completes on bar.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(dst), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major: start, leading (k
+// direction) and stride (8-row direction) byte offsets, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem), "l"(adesc), "l"(bdesc),
+      "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+
+// 32 lanes x 8 consecutive float32 columns of tensor memory (this warp's lane quarter).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// c_a 128 + c_b from two group sums (exact integers in float32; |result| < 2^31)
+__device__ __forceinline__ int join2(uint32_t a, uint32_t b) {
+  return __float2int_rn(__uint_as_float(a)) * 128 + __float2int_rn(__uint_as_float(b));
+}
+
+// One 128 x 64 tile of C = A B^T from the digit slices.
+//   warp 0, one lane: TMA producer over the k steps (stage ring with full /
+//           empty barriers);
+//   warp 1: allocates the 512 tensor-memory columns; one lane issues the MMAs
+//           (group g = q + r at columns 64 g; the first k step of a chunk
+//           overwrites);
+//   warps 2..9: drain each chunk's group sums into the exact integers hi / lo
+//           (lo carried into hi above 2^28, so lo stays 32-bit) and write the tile.
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_gemm_tc_kernel(const OzTask* __restrict__ tasks, const OzMap* __restrict__ maps, int* __restrict__ err) {
+  extern __shared__ uint8_t oz_dyn[];
+  __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_accf, bar_acce, bar_fin;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag, issued, consumed;
   const OzTask t = tasks[blockIdx.x];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = (warp >> 2) * 16, wn = (warp & 3) * 16;
-  const int g = lane >> 2, tq = lane & 3;
-  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(oz_smem);
-  float acc[OZ_NG][2][4];
-  double acc64[2][4];
-#pragma unroll
-  for (int b = 0; b < 2; ++b)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      acc64[b][c] = 0.0;
-#pragma unroll
-      for (int s = 0; s < OZ_NG; ++s) acc[s][b][c] = 0.f;
-    }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t sbase = (smem_u32(oz_dyn) + 1023u) & ~1023u;
   const int nks = t.Kp / OZ_TK;
-  oz_stage(t, sbase, 0);
-  cp_async_commit();
-  for (int ks = 0; ks < nks; ++ks) {
-    if (ks + 1 < nks) {
-      oz_stage(t, sbase + (uint32_t)(((ks + 1) & 1) * OZ_STAGE_WORDS * 4), (ks + 1) * OZ_TK);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+  const int nch = (nks + OZ_CHUNK_STEPS - 1) / OZ_CHUNK_STEPS;
+  volatile int* abort = &abort_flag;
+  if (tid == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    __syncthreads();
-    const uint32_t* S = oz_smem + (ks & 1) * OZ_STAGE_WORDS;
-#pragma unroll
-    for (int kk = 0; kk < OZ_TK / 2; kk += 8) {      // two k16 mma steps (8 words each)
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        uint32_t bf[OZ_Q][2];
-        const int cn = wn + nt * 8 + g;
-#pragma unroll
-        for (int r = 0; r < OZ_Q; ++r) {
-          const uint32_t* Br = S + ((OZ_Q + r) * OZ_TM + cn) * OZ_LDW + kk + tq;
-          bf[r][0] = Br[0];
-          bf[r][1] = Br[4];
+    mbar_init(smem_u32(&bar_accf), 1);
+    mbar_init(smem_u32(&bar_acce), OZ_DRAIN_WARPS);
+    mbar_init(smem_u32(&bar_fin), 1);
+    abort_flag = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const void* ma = &maps[2 * t.ia];        // A role: 128-row boxes
+      const void* mb = &maps[2 * t.ib + 1];    // B role: 64-row boxes
+      bool ok = true;
+      for (int ks = 0; ks < nks; ++ks) {
+        const int s = ks % OZ_STAGES;
+        if (ks >= OZ_STAGES && !(ok = mbar_wait(smem_u32(&bar_empty[s]), ((ks / OZ_STAGES) - 1) & 1, abort, err, 1)))
+          break;
+        const uint32_t full = smem_u32(&bar_full[s]);
+        const uint32_t sa = sbase + s * OZ_STAGE_BYTES;
+        mbar_expect_tx(full, OZ_STAGE_BYTES);
+        tma_load_4d(sa, ma, 0, t.tm, 2 * ks, 0, full);
+        tma_load_4d(sa + OZ_A_BYTES, mb, 0, t.tn, 2 * ks, 0, full);
+        issued = ks + 1;
+      }
+      // every stage's release (an MMA commit) has landed before the block's shared memory is given up
+      for (int ks = max(nks - OZ_STAGES, 0); ok && ks < nks; ++ks)
+        ok = mbar_wait(smem_u32(&bar_empty[ks % OZ_STAGES]), (ks / OZ_STAGES) & 1, abort, err, 5);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // kind::f16 instruction descriptor: f32 accumulator, bf16 A and B, both K-major, N = 64, M = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TILE_N >> 3) << 17) |
+                             ((uint32_t)(OZ_TILE_M >> 4) << 24);
+      // stage layout: slice q, k group c, row i, k % 8 at ((q * 2 + c) * rows + i) * 16 + 2 (k % 8) bytes
+      const uint64_t a0 = smem_desc(sbase, OZ_TILE_M * 16, 128);
+      const uint64_t b0 = smem_desc(sbase + OZ_A_BYTES, OZ_TILE_N * 16, 128);
+      for (int ks = 0; ks < nks; ++ks) {
+        const int s = ks % OZ_STAGES, kc = ks % OZ_CHUNK_STEPS;
+        if (kc == 0 && ks > 0) {               // the drain of the previous chunk has read the accumulators
+          if (!mbar_wait(smem_u32(&bar_acce), (ks / OZ_CHUNK_STEPS - 1) & 1, abort, err, 2)) break;
+          tc_fence_after();
         }
+        if (!mbar_wait(smem_u32(&bar_full[s]), (ks / OZ_STAGES) & 1, abort, err, 3)) break;
+        tc_fence_after();
+        const uint64_t soff = (uint64_t)((s * OZ_STAGE_BYTES) >> 4);
 #pragma unroll
-        for (int q = 0; q < OZ_Q; ++q) {
-          uint32_t af[4];
-          const uint32_t* Aq = S + (q * OZ_TM + wm + g) * OZ_LDW + kk + tq;
-          af[0] = Aq[0];
-          af[1] = Aq[8 * OZ_LDW];
-          af[2] = Aq[4];
-          af[3] = Aq[8 * OZ_LDW + 4];
+        for (int q = 0; q < OZ_Q; ++q)
 #pragma unroll
-          for (int r = 0; r < OZ_Q; ++r)
-            if (q + r + 2 <= OZ_SMAX) mma_bf16_16816(acc[q + r][nt], af, bf[r][0], bf[r][1]);
+          for (int r = 0; r < OZ_Q - q; ++r)
+            tc_mma(tbase + (uint32_t)((q + r) * OZ_TILE_N), a0 + soff + (uint64_t)(q * (OZ_TILE_M * 2)),
+                   b0 + soff + (uint64_t)(r * (OZ_TILE_N * 2)), idesc, (kc != 0 || q != 0) ? 1 : 0);
+        tc_commit(smem_u32(&bar_empty[s]));    // the stage is free once these MMAs have read it
+        if (kc == OZ_CHUNK_STEPS - 1 || ks == nks - 1) tc_commit(smem_u32(&bar_accf));
+        consumed = ks + 1;
+      }
+    }
+  } else {
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t trow = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+    long long hi[32];
+    int lo[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+      // every lane waits; the warp continues together (tcgen05.ld is warp-collective)
+      if (!(ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_accf), c & 1, abort, err, 4)))) break;
+      tc_fence_after();
+#pragma unroll
+      for (int sub = 0; sub < 4; ++sub) {
+        uint32_t v[4][8];
+        int p0[8], p1[8];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) tmem_ld8(trow + g * OZ_TILE_N + sub * 8, v[g]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { p0[j] = join2(v[0][j], v[1][j]); p1[j] = join2(v[2][j], v[3][j]); }
+#pragma unroll
+        for (int g = 0; g < 4; ++g) tmem_ld8(trow + (g + 4) * OZ_TILE_N + sub * 8, v[g]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int p2 = join2(v[0][j], v[1][j]), p3 = join2(v[2][j], v[3][j]);
+          const long long hc = ((long long)p0[j] << 14) + p1[j];       // sum_{s<=5} c_s 128^{5-s}
+          const long long lt = ((long long)p2 << 14) + p3 + lo[sub * 8 + j];
+          const long long carry = lt >> 28;                            // floor(lt / 2^28)
+          lo[sub * 8 + j] = (int)(lt - (carry << 28));
+          hi[sub * 8 + j] += hc + carry;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_acce));
+    }
+    if (ok && !*abort) {
+      const int i = t.tm + quarter * 32 + lane;
+      if (i < t.M) {
+        const int ea = t.ea[i];
+        double* crow = t.C + (int64_t)i * t.ldc;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int jj = t.tn + half * 32 + j;
+          if (jj < t.N) crow[jj] = ldexp(fma((double)hi[j], 0x1p-35, (double)lo[j] * 0x1p-63), ea + t.eb[jj]);
         }
       }
     }
-    const int kend = (ks + 1) * OZ_TK;
-    if (kend % OZ_CHUNK == 0 || ks + 1 == nks) {
-      // the group sums are exact integers below 2^24: join them exactly in two
-      // 46-bit integers and add to the float64 accumulator
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          long long hi = 0, lo = 0;
-#pragma unroll
-          for (int s = 0; s < 4; ++s) hi = hi * 128 + __float2int_rn(acc[s][b][c]);
-#pragma unroll
-          for (int s = 4; s < OZ_NG; ++s) lo = lo * 128 + __float2int_rn(acc[s][b][c]);
-          acc64[b][c] = fma((double)hi, 0x1p-35, acc64[b][c]);
-          acc64[b][c] = fma((double)lo, 0x1p-63, acc64[b][c]);
-#pragma unroll
-          for (int s = 0; s < OZ_NG; ++s) acc[s][b][c] = 0.f;
-        }
-    }
-    __syncthreads();                                 // stage (ks & 1) is refilled next iteration
   }
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int i = t.tm + wm + g + (c >= 2 ? 8 : 0);
-      const int j = t.tn + wn + nt * 8 + 2 * tq + (c & 1);
-      if (i < t.M && j < t.N) t.C[(int64_t)i * t.ldc + j] = ldexp(acc64[nt][c], t.ea[i] + t.eb[j]);
+  __syncthreads();
+  if (*abort) {
+    // let the copies and MMAs in flight finish before the memory is released (bounded)
+    if (tid == 0)
+      for (int ks = consumed; ks < issued; ++ks) mbar_drain(smem_u32(&bar_full[ks % OZ_STAGES]), (ks / OZ_STAGES) & 1);
+    if (tid == 32) {                           // the MMA-issuing thread: its commit covers all its MMAs
+      tc_commit(smem_u32(&bar_fin));
+      mbar_drain(smem_u32(&bar_fin), 0);
     }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  __syncwarp();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tbase));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
 }
 
 }  // namespace
 
 int oz_slices() { return OZ_Q; }
-int oz_kpad(int K) { return (K + OZ_TK - 1) / OZ_TK * OZ_TK; }
+int oz_kpad(int K) { return (K + 31) / 32 * 32; }
+
+cudaError_t oz_encode_maps(const std::vector<OzSplitTask>& ops, std::vector<OzMap>& maps) {
+  static_assert(sizeof(OzMap) == sizeof(CUtensorMap), "tensor map size");
+  maps.assign(2 * ops.size(), OzMap{});
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  for (size_t o = 0; o < ops.size(); ++o) {
+    const OzSplitTask& t = ops[o];
+    if (t.M < 0 || t.Kp < 0 || t.Kp % 32 != 0 || (reinterpret_cast<uintptr_t>(t.out) & 15)) return cudaErrorInvalidValue;
+    // dims innermost first: k % 8, row, k / 8, slice; byte strides of dims 1..3.  An empty
+    // operand (no rows or no k) gets a one-element extent: no tile reads it (K = 0 runs no k step).
+    const cuuint64_t M = (cuuint64_t)std::max(t.M, 1), G = (cuuint64_t)std::max(t.Kp / 8, 1);
+    const cuuint64_t dims[4] = {8, M, G, (cuuint64_t)OZ_Q};
+    const cuuint64_t strides[3] = {16, M * 16, M * G * 16};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int role = 0; role < 2; ++role) {
+      const cuuint32_t box[4] = {8, (cuuint32_t)(role == 0 ? OZ_TILE_M : OZ_TILE_N), 2, (cuuint32_t)OZ_Q};
+      CUresult r = enc(reinterpret_cast<CUtensorMap*>(&maps[2 * o + role]), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                       const_cast<uint16_t*>(t.out), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, int maxKp, cudaStream_t st) {
   if (ntasks == 0) return cudaSuccess;
@@ -273,11 +438,11 @@ cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, cudaStream_t st) {
+cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, const OzMap* d_maps, int* d_err, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
-  const int smem = (int)(2 * OZ_STAGE_WORDS * sizeof(uint32_t));
-  cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (reinterpret_cast<uintptr_t>(d_maps) & 63) return cudaErrorInvalidValue;   // tensor maps: 64-byte aligned
+  cudaError_t e = cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
   if (e != cudaSuccess) return e;
-  oz_gemm_kernel<<<ntiles, OZ_THREADS, smem, st>>>(d_tasks);
+  oz_gemm_tc_kernel<<<ntiles, OZ_THREADS, OZ_SMEM, st>>>(d_tasks, d_maps, d_err);
   return cudaGetLastError();
 }
