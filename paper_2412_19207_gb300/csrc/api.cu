@@ -595,7 +595,7 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
       int maxKp = 0;
       for (int j = 0; j < J; ++j) {
         const int Kp = oz_kpad(h->subs[j].N);
-        soff += (int64_t)nsl * m * Kp;
+        soff += (int64_t)nsl * oz_mpad(m) * Kp;
         maxKp = std::max(maxKp, Kp);
       }
       CK(dalloc(h, (void**)&d_sl, sizeof(uint16_t) * (size_t)soff));
@@ -605,13 +605,13 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
         const SubDev& S = h->subs[j];
         OzSplitTask& t = sp[j];
         t.X = h->d_Psi + S.row0 * m; t.si = 1; t.sk = m;       // row i of Psi_j^T
-        t.M = m; t.K = S.N; t.Kp = oz_kpad(S.N); t.e = d_e + (size_t)m * j; t.out = d_sl + soff;
+        t.M = m; t.K = S.N; t.Kp = oz_kpad(S.N); t.Mp = oz_mpad(m); t.e = d_e + (size_t)m * j; t.out = d_sl + soff;
         OzTask g{};
         g.ia = j; g.ib = j; g.ea = t.e; g.eb = t.e; g.C = h->d_V + mm * j;
         g.M = m; g.N = m; g.Kp = t.Kp; g.ldc = m;
         for (int tm = 0; tm < m; tm += OZ_TILE_M)      // tiles meeting the upper triangle
           for (int tn = tm; tn < m; tn += OZ_TILE_N) { g.tm = tm; g.tn = tn; gt.push_back(g); }
-        soff += (int64_t)nsl * m * t.Kp;
+        soff += (int64_t)nsl * t.Mp * t.Kp;
       }
       std::vector<OzMap> maps;
       CK(oz_encode_maps(sp, maps));
@@ -712,24 +712,27 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   CK(cudaMemsetAsync(h->d_B, 0, sizeof(double) * (size_t)boff, h->st));
   if (h->inner_df) {        // B_j = H_j V_{p_j} from digit slices of H_j and V_{p_j}^T
     const int nsl = oz_slices(), Kp = oz_kpad(m);
-    int64_t sumP = 0;
-    for (int j = 0; j < J; ++j) sumP += h->subs[j].p;
+    int64_t sumP = 0, srows = 0;          // slice rows: every operand padded to oz_mpad rows
+    for (int j = 0; j < J; ++j) { sumP += h->subs[j].p; srows += oz_mpad(h->subs[j].N) + oz_mpad(h->subs[j].p); }
     uint16_t* d_sl; int* d_e;
     const int64_t nrows = h->rows_total + sumP;
-    CK(dalloc(h, (void**)&d_sl, sizeof(uint16_t) * (size_t)(nsl * Kp) * (size_t)nrows));
+    CK(dalloc(h, (void**)&d_sl, sizeof(uint16_t) * (size_t)(nsl * Kp) * (size_t)srows));
     CK(dalloc(h, (void**)&d_e, sizeof(int) * (size_t)nrows));
     std::vector<OzSplitTask> sp(2 * J);
     std::vector<OzTask> gt;
-    int64_t vrow = h->rows_total;       // rows of the V^T operands follow the rows of H
+    int64_t vrow = h->rows_total;       // exponents of the V^T operands follow those of H
+    int64_t srow = 0;
     int maxM = m;
     for (int j = 0; j < J; ++j) {
       const SubDev& S = h->subs[j];
       OzSplitTask& a = sp[2 * j];
       a.X = h->d_H + S.row0 * m; a.si = m; a.sk = 1;
-      a.M = S.N; a.K = m; a.Kp = Kp; a.e = d_e + S.row0; a.out = d_sl + (size_t)nsl * Kp * S.row0;
+      a.M = S.N; a.K = m; a.Kp = Kp; a.Mp = oz_mpad(S.N); a.e = d_e + S.row0; a.out = d_sl + (size_t)nsl * Kp * srow;
+      srow += a.Mp;
       OzSplitTask& b = sp[2 * j + 1];
       b.X = h->d_V + mm * j; b.si = 1; b.sk = m;                // row c of V_{p_j}^T
-      b.M = S.p; b.K = m; b.Kp = Kp; b.e = d_e + vrow; b.out = d_sl + (size_t)nsl * Kp * vrow;
+      b.M = S.p; b.K = m; b.Kp = Kp; b.Mp = oz_mpad(S.p); b.e = d_e + vrow; b.out = d_sl + (size_t)nsl * Kp * srow;
+      srow += b.Mp;
       vrow += S.p;
       maxM = std::max(maxM, S.N);
       OzTask g{};
@@ -989,10 +992,10 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
       OzSplitTask o{};
       o.X = h->d_B + S[k].boff; o.si = 1; o.sk = S[k].P;
       o.gather = d_ridx + start;
-      o.M = S[k].p; o.K = K; o.Kp = oz_kpad(K);
+      o.M = S[k].p; o.K = K; o.Kp = oz_kpad(K); o.Mp = oz_mpad(o.M);
       o.e = reinterpret_cast<int*>(eoff);                    // patched below
       o.out = reinterpret_cast<uint16_t*>(soff);
-      soff += (int64_t)nsl * o.M * o.Kp;
+      soff += (int64_t)nsl * o.Mp * o.Kp;
       eoff += o.M;
       maxM = std::max(maxM, o.M);
       maxKp = std::max(maxKp, o.Kp);

@@ -86,9 +86,9 @@ struct OzSplitTask {         // one operand: rows i < M of x(i, k) = X[i * si + 
   const double* X;
   const int* gather;         // g(k) = gather[k], or k when null
   int64_t si, sk;
-  int M, K, Kp, pad_;        // Kp = oz_kpad(K)
+  int M, K, Kp, Mp;          // Kp = oz_kpad(K), Mp = oz_mpad(M) (rows M..Mp-1 of the slices are zero)
   int* e;                    // [M] row exponents (out)
-  uint16_t* out;             // [oz_slices()][Kp/8][M][8] bf16 digit slices (out), 16-byte aligned
+  uint16_t* out;             // [oz_slices()][Kp/8][Mp][8] bf16 digit slices (out), 16-byte aligned
 };
 constexpr int OZ_TILE_M = 128, OZ_TILE_N = 64;   // C tile of one block (rows of A x rows of B)
 struct alignas(64) OzMap { unsigned char bytes[128]; };   // a TMA tensor map of one operand's slices
@@ -102,6 +102,7 @@ struct OzTask {              // one OZ_TILE_M x OZ_TILE_N tile of C = A B^T (A: 
 };
 int oz_slices();
 int oz_kpad(int K);
+inline int oz_mpad(int M) { return (M + 31) / 32 * 32; }
 // Host: the two TMA tensor maps (A role, B role) of each operand's slices,
 // from the device addresses in ops[].out (no device work).
 cudaError_t oz_encode_maps(const std::vector<OzSplitTask>& ops, std::vector<OzMap>& maps);

@@ -29,9 +29,10 @@
 // Blackwell mapping of one 128 x 64 tile of C: the eight group accumulators
 // (8 x 64 float32 columns) fill the 512 columns of tensor memory; a 4-stage
 // ring of k steps of 16 is filled by 4-D TMA boxes (all eight slices of the
-// tile's 128 A rows and 64 B rows, landing in the no-swizzle K-major
-// core-matrix layout); one thread issues the 36 tcgen05.mma of a k step; eight
-// warps drain the accumulators to the integer chunk sums through tcgen05.ld.
+// tile's 128 A rows and 64 B rows; each box row is a 32-row group, 512
+// contiguous bytes, landing in the no-swizzle K-major core-matrix layout); one
+// thread issues the 36 tcgen05.mma of a k step; eight warps drain the
+// accumulators to the integer chunk sums through tcgen05.ld.
 #include "common.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -102,51 +103,66 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const OzSplitTask* __rest
   }
 }
 
-// Digit slices of a 32 x 32 tile.  Slice q of row i, column k sits at
-// out[q M Kp + ((k / 8) M + i) 8 + k % 8] (8 k of a row contiguous, then the
-// rows, then the groups of 8 k, then the slices), zero for k >= K.
+// Digit slices of a 32-row x 64-k tile.  Slice q of row i, column k sits at
+// out[q Mp Kp + ((k / 8) Mp + i) 8 + k % 8]: 8 k of a row contiguous, then the
+// rows (32-row groups are 512 contiguous bytes), then the groups of 8 k, then
+// the slices; zero for k >= K and for the padding rows M <= i < Mp.
 __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitTask* __restrict__ tasks) {
   const OzSplitTask t = tasks[blockIdx.z];
-  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
-  if (i0 >= t.M || k0 >= t.Kp) return;
-  __shared__ long long tile[32][33];
+  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  if (i0 >= t.Mp || k0 >= t.Kp) return;
+  __shared__ long long tile[32][65];
   const long long* X = reinterpret_cast<const long long*>(t.X);
-  const bool kfast = (t.sk == 1 && !t.gather);
-  for (int e = threadIdx.x; e < 1024; e += 256) {
-    const int a = e & 31, b = e >> 5;
-    const int ii = kfast ? b : a, kk = kfast ? a : b;
-    const int i = i0 + ii, k = k0 + kk;
-    long long v = 0;
-    if (i < t.M && k < t.K) v = X[(int64_t)i * t.si + (int64_t)(t.gather ? t.gather[k] : k) * t.sk];
-    tile[ii][kk] = v;
+  if (t.sk == 1 && !t.gather) {                      // rows contiguous in k
+    for (int e = threadIdx.x; e < 2048; e += 256) {
+      const int kk = e & 63, ii = e >> 6, i = i0 + ii, k = k0 + kk;
+      tile[ii][kk] = (i < t.M && k < t.K) ? X[(int64_t)i * t.si + k] : 0;
+    }
+  } else {                                           // columns contiguous in i (or gathered k)
+    for (int e = threadIdx.x; e < 2048; e += 256) {
+      const int ii = e & 31, kk = e >> 5, i = i0 + ii, k = k0 + kk;
+      tile[ii][kk] = (i < t.M && k < t.K) ? X[(int64_t)i * t.si + (int64_t)(t.gather ? t.gather[k] : k) * t.sk] : 0;
+    }
   }
   __syncthreads();
-  const int64_t slice = (int64_t)t.M * t.Kp;
-  for (int e = threadIdx.x; e < 1024; e += 256) {
-    // a warp covers 8 k x 4 rows: 64 contiguous bytes of every slice
-    const int k8 = e & 7, ii = (e >> 3) & 31, kk = (e >> 8) * 8 + k8;
-    const int i = i0 + ii, k = k0 + kk;
-    if (i >= t.M) continue;
+  // thread: row i0 + (tid % 32), 8 k starting at k0 + 8 (tid / 32); a warp writes 512
+  // contiguous bytes of every slice
+  const int ii = threadIdx.x & 31, kc = threadIdx.x >> 5, i = i0 + ii;
+  if (k0 + 8 * kc >= t.Kp) return;
+  const int ei = (i < t.M) ? t.e[i] : 0;
+  uint32_t w[OZ_Q][4];
+#pragma unroll
+  for (int k8 = 0; k8 < 8; ++k8) {
     // X = round(|x| 2^{56 - e_i}) with the sign of x, from the float64 fields
-    const long long bits = tile[ii][kk];
+    const long long bits = tile[ii][8 * kc + k8];
     const int E = (int)((bits >> 52) & 0x7ff);
     long long v = 0;
     if (E != 0) {                                    // zero and subnormals give 0
       const long long mant = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
-      const int sh = E - 1075 + 56 - t.e[i];         // <= 4 since |x| <= 2^{e_i}
+      const int sh = E - 1075 + 56 - ei;             // <= 4 since |x| <= 2^{e_i}
       if (sh >= 0) v = mant << sh;
       else if (sh > -60) v = (mant + (1ll << (-sh - 1))) >> (-sh);
       if (bits < 0) v = -v;
     }
-    uint16_t* o = t.out + ((int64_t)(k >> 3) * t.M + i) * 8 + k8;
+    uint32_t d16[OZ_Q];
 #pragma unroll
     for (int q = OZ_Q - 1; q >= 1; --q) {            // balanced base-128 digits, least significant first
       const long long d = ((v + 64) & 127) - 64;
       v = (v - d) >> 7;                              // exact: v - d is a multiple of 128
-      o[q * slice] = bf16_of_small_int((int)d);
+      d16[q] = bf16_of_small_int((int)d);
     }
-    o[0] = bf16_of_small_int((int)v);                // leading digit, |v| <= 128
+    d16[0] = bf16_of_small_int((int)v);              // leading digit, |v| <= 128
+#pragma unroll
+    for (int q = 0; q < OZ_Q; ++q) {
+      if (k8 & 1) w[q][k8 >> 1] |= d16[q] << 16;
+      else w[q][k8 >> 1] = d16[q];
+    }
   }
+  const int64_t slice = (int64_t)t.Mp * t.Kp;
+  uint16_t* o = t.out + ((int64_t)((k0 >> 3) + kc) * t.Mp + i) * 8;
+#pragma unroll
+  for (int q = 0; q < OZ_Q; ++q)
+    *reinterpret_cast<uint4*>(o + q * slice) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
 }
 
 // ---- Blackwell primitives (inline PTX) ----
@@ -190,7 +206,8 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {   //
   }
 }
 
-// 4-D TMA box (8 k, rows, 2 groups of 8 k, 8 slices) into shared memory; completes on bar.
+// 4-D TMA box (32-row groups of 8 k, groups, 2 groups of 8 k, 8 slices) into shared memory;
+// completes on bar.
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* map, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
   asm volatile(
@@ -285,8 +302,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const uint32_t full = smem_u32(&bar_full[s]);
         const uint32_t sa = sbase + s * OZ_STAGE_BYTES;
         mbar_expect_tx(full, OZ_STAGE_BYTES);
-        tma_load_4d(sa, ma, 0, t.tm, 2 * ks, 0, full);
-        tma_load_4d(sa + OZ_A_BYTES, mb, 0, t.tn, 2 * ks, 0, full);
+        tma_load_4d(sa, ma, 0, t.tm / 32, 2 * ks, 0, full);
+        tma_load_4d(sa + OZ_A_BYTES, mb, 0, t.tn / 32, 2 * ks, 0, full);
         issued = ks + 1;
       }
       // every stage's release (an MMA commit) has landed before the block's shared memory is given up
@@ -367,7 +384,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int jj = t.tn + half * 32 + j;
-          if (jj < t.N) crow[jj] = ldexp(fma((double)hi[j], 0x1p-35, (double)lo[j] * 0x1p-63), ea + t.eb[jj]);
+          if (jj < t.N) {
+            const double v = fma((double)hi[j], 0x1p-35, (double)lo[j] * 0x1p-63);   // the one rounding
+            const int ex = ea + t.eb[jj];
+            // times 2^ex: a power-of-two factor built from its exponent field when it is normal
+            crow[jj] = (ex >= -1022 && ex <= 1023) ? v * __longlong_as_double((long long)(ex + 1023) << 52)
+                                                   : ldexp(v, ex);
+          }
         }
       }
     }
@@ -413,15 +436,17 @@ cudaError_t oz_encode_maps(const std::vector<OzSplitTask>& ops, std::vector<OzMa
   if (!enc) return cudaErrorNotSupported;
   for (size_t o = 0; o < ops.size(); ++o) {
     const OzSplitTask& t = ops[o];
-    if (t.M < 0 || t.Kp < 0 || t.Kp % 32 != 0 || (reinterpret_cast<uintptr_t>(t.out) & 15)) return cudaErrorInvalidValue;
-    // dims innermost first: k % 8, row, k / 8, slice; byte strides of dims 1..3.  An empty
-    // operand (no rows or no k) gets a one-element extent: no tile reads it (K = 0 runs no k step).
-    const cuuint64_t M = (cuuint64_t)std::max(t.M, 1), G = (cuuint64_t)std::max(t.Kp / 8, 1);
-    const cuuint64_t dims[4] = {8, M, G, (cuuint64_t)OZ_Q};
-    const cuuint64_t strides[3] = {16, M * 16, M * G * 16};
+    if (t.M < 0 || t.Kp < 0 || t.Kp % 32 != 0 || t.Mp != oz_mpad(t.M) || (reinterpret_cast<uintptr_t>(t.out) & 15))
+      return cudaErrorInvalidValue;
+    // dims innermost first: (row % 32, k % 8) as 256 contiguous elements, row / 32, k / 8,
+    // slice; byte strides of dims 1..3.  An empty operand (no rows or no k) gets a
+    // one-element extent: no tile reads it (K = 0 runs no k step).
+    const cuuint64_t G32 = (cuuint64_t)std::max(t.Mp / 32, 1), G8 = (cuuint64_t)std::max(t.Kp / 8, 1);
+    const cuuint64_t dims[4] = {256, G32, G8, (cuuint64_t)OZ_Q};
+    const cuuint64_t strides[3] = {512, G32 * 512, G32 * G8 * 512};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     for (int role = 0; role < 2; ++role) {
-      const cuuint32_t box[4] = {8, (cuuint32_t)(role == 0 ? OZ_TILE_M : OZ_TILE_N), 2, (cuuint32_t)OZ_Q};
+      const cuuint32_t box[4] = {256, (cuuint32_t)((role == 0 ? OZ_TILE_M : OZ_TILE_N) / 32), 2, (cuuint32_t)OZ_Q};
       CUresult r = enc(reinterpret_cast<CUtensorMap*>(&maps[2 * o + role]), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                        const_cast<uint16_t*>(t.out), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -434,7 +459,7 @@ cudaError_t oz_encode_maps(const std::vector<OzSplitTask>& ops, std::vector<OzMa
 cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, int maxKp, cudaStream_t st) {
   if (ntasks == 0) return cudaSuccess;
   oz_scale_kernel<<<dim3((maxM + 31) / 32, ntasks), 256, 0, st>>>(d_tasks);
-  oz_split_kernel<<<dim3((maxKp + 31) / 32, (maxM + 31) / 32, ntasks), 256, 0, st>>>(d_tasks);
+  oz_split_kernel<<<dim3((maxKp + 63) / 64, (maxM + 31) / 32, ntasks), 256, 0, st>>>(d_tasks);
   return cudaGetLastError();
 }
 
