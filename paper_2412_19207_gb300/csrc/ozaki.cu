@@ -53,10 +53,12 @@ constexpr int OZ_THREADS = 32 * (2 + OZ_DRAIN_WARPS);
 constexpr long long OZ_WAIT_CYCLES = 2000000000ll;          // ~1 s: a wait this long is a fault
 static_assert(OZ_NG * OZ_TILE_N == 512, "the group accumulators fill tensor memory");
 
-__device__ __forceinline__ uint16_t bf16_of_small_int(int d) {
-  // |d| <= 128: exactly representable in bf16 (8 significant bits); the bf16
-  // pattern is the upper half of the float32 pattern.
-  return (uint16_t)(__float_as_uint((float)d) >> 16);
+__device__ __forceinline__ uint32_t bf16_of_small_int(int d) {
+  // |d| <= 128: exactly representable in bf16 (8 significant bits), whose
+  // pattern is the upper half of the float32 one.  The float32 value comes
+  // without a conversion instruction: 1.5 2^23 + d has d in its low mantissa
+  // bits (|d| < 2^22), and subtracting 1.5 2^23 leaves d exactly.
+  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
 }
 
 // e_i of 32 rows of one operand per block (deterministic integer max of |x|'s bits).
@@ -144,14 +146,14 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitTask* __rest
       else if (sh > -60) v = (mant + (1ll << (-sh - 1))) >> (-sh);
       if (bits < 0) v = -v;
     }
+    // balanced base-128 digits: adding 64 (1 + 128 + ... + 128^6) makes the seven
+    // low digits d + 64 in [0, 127] plain base-128 digits of u, and the leading
+    // digit u >> 49 (|lead| <= 128)
+    const long long u = v + 0x1020408102040ll;
     uint32_t d16[OZ_Q];
+    d16[0] = bf16_of_small_int((int)(u >> 49));
 #pragma unroll
-    for (int q = OZ_Q - 1; q >= 1; --q) {            // balanced base-128 digits, least significant first
-      const long long d = ((v + 64) & 127) - 64;
-      v = (v - d) >> 7;                              // exact: v - d is a multiple of 128
-      d16[q] = bf16_of_small_int((int)d);
-    }
-    d16[0] = bf16_of_small_int((int)v);              // leading digit, |v| <= 128
+    for (int q = 1; q < OZ_Q; ++q) d16[q] = bf16_of_small_int((int)((u >> (7 * (OZ_Q - 1 - q))) & 127) - 64);
 #pragma unroll
     for (int q = 0; q < OZ_Q; ++q) {
       if (k8 & 1) w[q][k8 >> 1] |= d16[q] << 16;
@@ -223,11 +225,30 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
+// D (+)= A B^T; COL selects the A collector buffer: 0 none, 1 fill (keep A for the
+// next MMAs), 2 use (A as kept), 3 last use (A as kept, then released).
+template <int COL>
 __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem), "l"(adesc), "l"(bdesc),
-      "r"(idesc), "r"(acc));
+  if constexpr (COL == 0)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem), "l"(adesc), "l"(bdesc),
+        "r"(idesc), "r"(acc));
+  else if constexpr (COL == 1)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  else if constexpr (COL == 2)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
@@ -327,12 +348,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (!mbar_wait(smem_u32(&bar_full[s]), (ks / OZ_STAGES) & 1, abort, err, 3)) break;
         tc_fence_after();
         const uint64_t soff = (uint64_t)((s * OZ_STAGE_BYTES) >> 4);
+        // A slice q meets B slices r = 0..7-q back to back: it is read from shared
+        // memory once and kept in the collector buffer for the following MMAs
 #pragma unroll
-        for (int q = 0; q < OZ_Q; ++q)
+        for (int q = 0; q < OZ_Q; ++q) {
+          const uint64_t ad = a0 + soff + (uint64_t)(q * (OZ_TILE_M * 2));
+          const int acc = (kc != 0 || q != 0) ? 1 : 0;
 #pragma unroll
-          for (int r = 0; r < OZ_Q - q; ++r)
-            tc_mma(tbase + (uint32_t)((q + r) * OZ_TILE_N), a0 + soff + (uint64_t)(q * (OZ_TILE_M * 2)),
-                   b0 + soff + (uint64_t)(r * (OZ_TILE_N * 2)), idesc, (kc != 0 || q != 0) ? 1 : 0);
+          for (int r = 0; r < OZ_Q - q; ++r) {
+            const uint32_t d = tbase + (uint32_t)((q + r) * OZ_TILE_N);
+            const uint64_t bd = b0 + soff + (uint64_t)(r * (OZ_TILE_N * 2));
+            if (q == OZ_Q - 1) tc_mma<0>(d, ad, bd, idesc, acc);
+            else if (r == 0) tc_mma<1>(d, ad, bd, idesc, acc);
+            else if (r == OZ_Q - 1 - q) tc_mma<3>(d, ad, bd, idesc, acc);
+            else tc_mma<2>(d, ad, bd, idesc, acc);
+          }
+        }
         tc_commit(smem_u32(&bar_empty[s]));    // the stage is free once these MMAs have read it
         if (kc == OZ_CHUNK_STEPS - 1 || ks == nks - 1) tc_commit(smem_u32(&bar_accf));
         consumed = ks + 1;
