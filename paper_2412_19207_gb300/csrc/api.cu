@@ -41,7 +41,8 @@ int schwarz_apply_max_subs();
 cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
                                     const int* d_set_sub, const SubDev* d_sub, const double* d_r,
                                     const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
-                                    int wkind, const int* d_inc_ptr, cudaStream_t st);
+                                    int* d_done, int wkind, const int* d_inc_ptr, int ckind, double* d_z,
+                                    cudaStream_t st);
 cudaError_t launch_trmv_lower_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
                                  const float2* d_g2, float2* d_y2, cudaStream_t st);
 cudaError_t launch_trmv_upper_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
@@ -214,6 +215,7 @@ struct rann_dd_handle {
   int64_t* d_p_off32 = nullptr;   // per set: offset of its 32-row-block partial sums
   int max_set_size = 0;           // most subdomains in one extended set
   double* d_tpart32 = nullptr;
+  int* d_adone = nullptr;          // per set: row blocks of the fused apply finished (reset by the last)
   bool prec_df = false;           // the set-up kept only double-float factors
   double* d_Xmats = nullptr;
   float2* d_X2mats = nullptr;
@@ -917,8 +919,9 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
                   (void*)h->d_inc_set, (void*)h->d_inc_pos, (void*)h->d_s_off, (void*)h->d_s,
                   (void*)h->d_Amats, (void*)h->d_Xmats, (void*)h->d_g, (void*)h->d_y, (void*)h->d_tpart,
                   (void*)h->d_p_off, (void*)h->d_X2mats, (void*)h->d_g2, (void*)h->d_ys2, (void*)h->d_A2mats,
-                  (void*)h->d_p_off32, (void*)h->d_tpart32})
+                  (void*)h->d_p_off32, (void*)h->d_tpart32, (void*)h->d_adone})
     dfree(h, p);
+  h->d_adone = nullptr;
   h->d_mats = nullptr; h->d_Amats = nullptr; h->d_Xmats = nullptr; h->d_X2mats = nullptr; h->d_A2mats = nullptr;
   for (void* p : h->gram_allocs) dfree(h, p);
   h->gram_allocs.clear();
@@ -1066,9 +1069,9 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     for (int q = h->set_ptr[i]; q < h->set_ptr[i + 1]; ++q) { boffs.push_back(n); n += S[h->set_sub[q]].p; }
     boffs.push_back(n);
     boff_ptr.push_back((int)boffs.size());
-    mats[i].n = n; mats[i].ld = n;
+    mats[i].n = n; mats[i].ld = (n + 3) & ~3;       // rows start 32-byte aligned in double-float
     mats[i].A = reinterpret_cast<double*>(aoff);   // patched below
-    aoff += (int64_t)n * n;
+    aoff += (int64_t)n * mats[i].ld;
     s_off[i + 1] = s_off[i] + n;
     h->maxn = std::max(h->maxn, n);
     for (int q = h->set_ptr[i]; q < h->set_ptr[i + 1]; ++q)
@@ -1171,6 +1174,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     for (int i = 0; i < J; ++i) p32[i + 1] = p32[i] + (int64_t)((mats[i].n + ar - 1) / ar) * mats[i].n;
     CK(dupload(h, &h->d_p_off32, p32));
     CK(dalloc(h, (void**)&h->d_tpart32, sizeof(double) * (size_t)std::max<int64_t>(p32[J], 1)));
+    CK(dalloc(h, (void**)&h->d_adone, sizeof(int) * (size_t)J));
+    CK(cudaMemsetAsync(h->d_adone, 0, sizeof(int) * (size_t)J, h->st));
   }
   // incidence lists for the combine step: sets containing each subdomain, with its block offset
   std::vector<int> inc_ptr(1, 0), inc_set, inc_pos;
@@ -1185,6 +1190,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     inc_ptr.push_back((int)inc_set.size());
   }
   CK(dupload(h, &h->d_set_ptr, h->set_ptr)); CK(dupload(h, &h->d_set_sub, h->set_sub));
+  for (int k = 0; k < J; ++k)
+    REQUIRE(inc_ptr[k + 1] - inc_ptr[k] <= 64, RANN_EINVAL, "subdomain %d lies in more than 64 extended sets", k);
   CK(dupload(h, &h->d_inc_ptr, inc_ptr)); CK(dupload(h, &h->d_inc_set, inc_set)); CK(dupload(h, &h->d_inc_pos, inc_pos));
   CK(dupload(h, &h->d_s_off, s_off));
   CK(dalloc(h, (void**)&h->d_s, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
@@ -1220,10 +1227,12 @@ static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, boo
                              h->st));
   } else if (fast) {
     // s_i = X_i^T X_i R_i r with X_i = L_i^{-1} read from HBM once (fused, with the gather)
-    KLA(h, K_SCHWARZ_DF, 2, 4.0 * (h->sum_n2 + h->sum_n) + 8.0 * h->sum_n + 8.0 * h->dof,
+    KLA(h, K_SCHWARZ_DF, 1, 4.0 * (h->sum_n2 + h->sum_n) + 8.0 * h->sum_n + 8.0 * h->dof,
         2.0 * (h->sum_n2 + h->sum_n),
         launch_schwarz_apply_df(h->d_mats, h->nsets, h->maxn, h->d_set_ptr, h->d_set_sub, h->d_sub, r, h->d_s_off,
-                                h->d_p_off32, h->d_tpart32, h->d_s, wkind, h->d_inc_ptr, h->st));
+                                h->d_p_off32, h->d_tpart32, h->d_s, h->d_adone, wkind, h->d_inc_ptr, ckind, z,
+                                h->st));
+    if (ckind == RANN_PREC_RAS) return RANN_OK;                // the restricted combine ran in the apply
   }
   if (fast) {
     KLA(h, K_COMBINE, 1, 8.0 * (h->sum_n + h->dof), 0, launch_schwarz_combine(h->d_sub, h->J, h->d_inc_ptr,

@@ -502,15 +502,18 @@ __global__ void schwarz_combine_kernel(const SubDev* __restrict__ subs, int J,
                                        double* __restrict__ z) {
   const int k = blockIdx.x;
   const SubDev& S = subs[k];
-  const int q0 = inc_ptr[k], q1 = inc_ptr[k + 1];
-  const double scale = (kind == RANN_PREC_SAS) ? 1.0 / (double)(q1 - q0) : 1.0;
+  const int q0 = inc_ptr[k], nq = min(inc_ptr[k + 1] - q0, 64);
+  __shared__ int64_t base[64];                        // s_i offsets of k's block (-1: skipped)
+  if ((int)threadIdx.x < nq) {
+    const int i = inc_set[q0 + threadIdx.x];
+    base[threadIdx.x] = (kind == RANN_PREC_RAS && i != k) ? -1 : s_off[i] + inc_pos[q0 + threadIdx.x];
+  }
+  __syncthreads();
+  const double scale = (kind == RANN_PREC_SAS) ? 1.0 / (double)(inc_ptr[k + 1] - q0) : 1.0;
   for (int c = threadIdx.x; c < S.p; c += blockDim.x) {
     double acc = 0.0;
-    for (int q = q0; q < q1; ++q) {
-      int i = inc_set[q];
-      if (kind == RANN_PREC_RAS && i != k) continue;
-      acc += s_all[s_off[i] + inc_pos[q] + c];
-    }
+    for (int q = 0; q < nq; ++q)
+      if (base[q] >= 0) acc += s_all[base[q] + c];
     z[S.woff + c] = acc * scale;
   }
 }
@@ -685,25 +688,36 @@ __global__ void __launch_bounds__(256) trmv_upper_df_partial_kernel(const CholMa
 // blocks of X_i: the block's y rows are formed from the rows just loaded, and
 // the same rows (re-read from L2) give the block's share of X_i^T y, so X_i
 // crosses HBM once per apply.  part[rb][c] holds the share of row block rb;
-// schwarz_reduce32_kernel adds them in a fixed order.  The set's residual
-// entries are split to double-float and staged in shared memory in one flat
-// pass (a small table maps each column to its subdomain).
+// the last block of a set to finish adds them in a fixed order (rb ascending)
+// into s_i.  The set's residual entries are split to double-float and staged
+// in shared memory in one flat pass (a small table maps each column to its
+// subdomain).  Rows are read as 16-byte pairs of columns (ld is a multiple of
+// 4, so every row starts 32-byte aligned); the parts of the triangle away
+// from the diagonal run without bounds tests.
 constexpr int AR = 32;             // rows per block of the fused apply
 constexpr int AMAX_SUB = 27;       // most subdomains in an extended set (3^3)
-constexpr int ANT = 512;           // threads per block of the fused apply
-__global__ void __launch_bounds__(ANT, 2) schwarz_apply_df_kernel(const CholMat* __restrict__ mats,
+constexpr int ANT = 256;           // threads per block of the fused apply (four blocks per SM)
+__device__ __forceinline__ void df_mac2(float& h0, float& l0, float& h1, float& l1, float4 a, float4 x) {
+  df_mac(h0, l0, make_float2(a.x, a.y), make_float2(x.x, x.y));
+  df_mac(h1, l1, make_float2(a.z, a.w), make_float2(x.z, x.w));
+}
+__global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat* __restrict__ mats,
                                                                const int* __restrict__ set_ptr,
                                                                const int* __restrict__ set_sub,
                                                                const SubDev* __restrict__ subs,
                                                                const double* __restrict__ r,
                                                                const int64_t* __restrict__ p_off32,
                                                                double* __restrict__ part, int wkind,
-                                                               const int* __restrict__ inc_ptr) {
-  extern __shared__ float2 gs[];
-  __shared__ float2 ys[AR];
+                                                               const int* __restrict__ inc_ptr,
+                                                               const int64_t* __restrict__ s_off,
+                                                               double* __restrict__ s, int* __restrict__ done,
+                                                               int ckind, double* __restrict__ z) {
+  extern __shared__ float4 gs4[];                     // (g_2c, g_2c+1) as double-float pairs
+  __shared__ float4 ys4[AR / 2];                      // (y_2q, y_2q+1)
   __shared__ int seg_c[AMAX_SUB + 1], seg_p[AMAX_SUB];
   __shared__ int64_t seg_w[AMAX_SUB];
   __shared__ double seg_d[AMAX_SUB];
+  __shared__ int last, own_q;
   const int i = blockIdx.y;
   const CholMat M = mats[i];
   const int nb = (M.n + AR - 1) / AR;
@@ -711,41 +725,72 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_df_kernel(const CholMat*
   const int rb = nb - 1 - (int)blockIdx.x;            // the long bottom row blocks start first
   const int r0 = rb * AR;
   const int r1 = min(M.n, r0 + AR);
+  const int nr = r1 - r0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int q0 = set_ptr[i], nq = set_ptr[i + 1] - q0;
+  if (tid < nq) {                                     // the set's subdomains, one thread each
+    const int k = set_sub[q0 + tid];
+    seg_p[tid] = subs[k].p;
+    seg_w[tid] = subs[k].woff;
+    seg_d[tid] = input_weight(wkind, k, i, inc_ptr);
+    if (k == i) own_q = tid;
+  }
+  __syncthreads();
   if (tid == 0) {
     int c = 0;
-    for (int q = 0; q < nq; ++q) {
-      const SubDev& S = subs[set_sub[q0 + q]];
-      seg_c[q] = c; seg_p[q] = S.p; seg_w[q] = S.woff;
-      seg_d[q] = input_weight(wkind, set_sub[q0 + q], i, inc_ptr);
-      c += S.p;
-    }
+    for (int q = 0; q < nq; ++q) { seg_c[q] = c; c += seg_p[q]; }
     seg_c[nq] = c;
   }
   __syncthreads();
-  for (int c = tid; c < r1; c += blockDim.x) {       // columns < r1 are all this block uses
-    int q = 0;
-    while (q + 1 < nq && seg_c[q + 1] <= c) ++q;
-    gs[c] = df_split(seg_d[q] * r[seg_w[q] + (c - seg_c[q])]);
-  }
-  if (tid < AR) ys[tid] = make_float2(0.f, 0.f);
-  __syncthreads();
-  // y rows: one warp per row, eight independent loads per lane in flight
-  for (int rr = warp; rr < r1 - r0; rr += ANT / 32) {
-    const int row = r0 + rr;
-    const float2* xr = M.X2 + (int64_t)row * M.ld;
-    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
-    constexpr int U = 8;
-    for (int c0 = lane; c0 <= row; c0 += 32 * U) {
-      float2 a[U];
+  const int np = (r1 + 1) >> 1;                       // column pairs below column r1 (all this block uses)
+  for (int c2 = tid; c2 < np; c2 += ANT) {
+    float2 v[2];
 #pragma unroll
-      for (int u = 0; u < U; ++u) a[u] = (c0 + 32 * u <= row) ? xr[c0 + 32 * u] : make_float2(0.f, 0.f);
+    for (int e = 0; e < 2; ++e) {
+      const int c = 2 * c2 + e;
+      v[e] = make_float2(0.f, 0.f);
+      if (c < r1) {
+        int q = 0;
+        while (q + 1 < nq && seg_c[q + 1] <= c) ++q;
+        v[e] = df_split(seg_d[q] * r[seg_w[q] + (c - seg_c[q])]);
+      }
+    }
+    gs4[c2] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  }
+  if (tid < AR / 2) ys4[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  float2* ys = reinterpret_cast<float2*>(ys4);
+  const int ldq = M.ld >> 1;                          // row stride in float4
+  // y rows: one warp per row, lane pairs c2 = lane + 32 k; pairs with 2 c2 + 1 <= row are
+  // wholly in the triangle, the pair holding the diagonal of an even row has its upper
+  // element masked
+  for (int rr = warp; rr < nr; rr += ANT / 32) {
+    const int row = r0 + rr;
+    const float4* xr = reinterpret_cast<const float4*>(M.X2 + (int64_t)row * M.ld);
+    const int nfull = (row + 1) >> 1, nall = (row >> 1) + 1;
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+    constexpr int U = 4;
+    int c2 = lane;
+    for (; c2 + 32 * (U - 1) < nfull; c2 += 32 * U) {
+      float4 a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) a[u] = xr[c2 + 32 * u];
+#pragma unroll
+      for (int u = 0; u < U; ++u) df_mac2(h[(2 * u) & 3], l[(2 * u) & 3], h[(2 * u + 1) & 3], l[(2 * u + 1) & 3], a[u],
+                                          gs4[c2 + 32 * u]);
+    }
+    if (c2 < nall) {
+      float4 a[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (c0 + 32 * u > row) break;
-        df_mac(h[u & 3], l[u & 3], a[u], gs[c0 + 32 * u]);
+        const int pc = c2 + 32 * u;
+        a[u] = (pc < nall) ? xr[pc] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (2 * pc + 1 > row) { a[u].z = 0.f; a[u].w = 0.f; }
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c2 + 32 * u < nall)
+          df_mac2(h[(2 * u) & 3], l[(2 * u) & 3], h[(2 * u + 1) & 3], l[(2 * u + 1) & 3], a[u], gs4[c2 + 32 * u]);
     }
     df_add(h[0], l[0], h[1], l[1]);
     df_add(h[2], l[2], h[3], l[3]);
@@ -754,39 +799,70 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_df_kernel(const CholMat*
     if (lane == 0) ys[rr] = make_float2(h[0], l[0]);
   }
   __syncthreads();
-  // the block's share of X^T y: thread per column, the block's rows r >= c
-  for (int c = tid; c < r1; c += blockDim.x) {
-    // eight of the block's rows of column c in flight at a time (rows r < c are zero in X)
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    for (int q = max(0, c - r0) & ~7; q < r1 - r0; q += 8) {
-      float2 a[8];
+  // the block's share of X^T y: thread per column pair (c, c + 1), the block's rows r >= c
+  for (int c2 = tid; c2 < np; c2 += ANT) {
+    const int c = 2 * c2;
+    const float4* xc = reinterpret_cast<const float4*>(M.X2 + (int64_t)r0 * M.ld + c);
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
+    if (nr == AR && c + 1 < r0) {                     // every row of the block is below both columns
+#pragma unroll 2
+      for (int q = 0; q < AR; q += 4) {
+        float4 a[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int row = r0 + q + u;
-        a[u] = (row < r1 && row >= c) ? M.X2[(int64_t)row * M.ld + c] : make_float2(0.f, 0.f);
+        for (int u = 0; u < 4; ++u) a[u] = xc[(q + u) * ldq];
+#pragma unroll
+        for (int u = 0; u < 4; u += 2) {
+          const float4 y = ys4[(q + u) >> 1];
+          df_mac2(h0, l0, h1, l1, a[u], make_float4(y.x, y.y, y.x, y.y));
+          df_mac2(h2, l2, h3, l3, a[u + 1], make_float4(y.z, y.w, y.z, y.w));
+        }
       }
+    } else {                                          // diagonal block or short last block
+      for (int q = 0; q < nr; q += 4) {
+        float4 a[4];
 #pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        df_mac(h0, l0, a[u], ys[q + u]);
-        df_mac(h1, l1, a[u + 1], ys[q + u + 1]);
+        for (int u = 0; u < 4; ++u) {
+          const int row = r0 + q + u;
+          a[u] = (q + u < nr && row >= c) ? xc[(q + u) * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row < c + 1) { a[u].z = 0.f; a[u].w = 0.f; }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u += 2) {
+          const float4 y = ys4[(q + u) >> 1];
+          df_mac2(h0, l0, h1, l1, a[u], make_float4(y.x, y.y, y.x, y.y));
+          df_mac2(h2, l2, h3, l3, a[u + 1], make_float4(y.z, y.w, y.z, y.w));
+        }
       }
     }
-    df_add(h0, l0, h1, l1);
-    part[p_off32[i] + (int64_t)rb * M.n + c] = df_to_double(h0, l0);
+    df_add(h0, l0, h2, l2);
+    df_add(h1, l1, h3, l3);
+    double* pr = part + p_off32[i] + (int64_t)rb * M.n;
+    pr[c] = df_to_double(h0, l0);
+    if (c + 1 < r1) pr[c + 1] = df_to_double(h1, l1);
   }
-}
-
-// s_i[c] = sum over the row blocks rb >= c / 32 of part[rb][c] (fixed order).
-__global__ void schwarz_reduce32_kernel(const CholMat* __restrict__ mats, const int64_t* __restrict__ s_off,
-                                        const int64_t* __restrict__ p_off32, const double* __restrict__ part,
-                                        double* __restrict__ s) {
-  const CholMat M = mats[blockIdx.y];
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= M.n) return;
-  const int nb = (M.n + AR - 1) / AR;
-  double acc = 0.0;
-  for (int rb = c / AR; rb < nb; ++rb) acc += part[p_off32[blockIdx.y] + (int64_t)rb * M.n + c];
-  s[s_off[blockIdx.y] + c] = acc;
+  // the last row block of the set to finish adds the parts
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(&done[i], 1) == nb - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (ckind == RANN_PREC_RAS) {
+    // restricted combine: z_i = (s_i) restricted to subdomain i's own block, written here
+    const int c0 = seg_c[own_q], pc = seg_p[own_q];
+    for (int c = c0 + tid; c < c0 + pc; c += ANT) {
+      double acc = 0.0;
+      for (int b = c / AR; b < nb; ++b) acc += __ldcg(part + p_off32[i] + (int64_t)b * M.n + c);
+      z[seg_w[own_q] + (c - c0)] = acc;
+    }
+  } else {
+    for (int c = tid; c < M.n; c += ANT) {
+      double acc = 0.0;
+      for (int b = c / AR; b < nb; ++b) acc += __ldcg(part + p_off32[i] + (int64_t)b * M.n + c);
+      s[s_off[i] + c] = acc;
+    }
+  }
+  if (tid == 0) done[i] = 0;                           // ready for the next apply (stream order)
 }
 
 // X2 = split(X) on the lower triangles.
@@ -922,14 +998,13 @@ int schwarz_apply_max_subs() { return AMAX_SUB; }
 cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
                                     const int* d_set_sub, const SubDev* d_sub, const double* d_r,
                                     const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
-                                    int wkind, const int* d_inc_ptr, cudaStream_t st) {
+                                    int* d_done, int wkind, const int* d_inc_ptr, int ckind, double* d_z,
+                                    cudaStream_t st) {
   if (nsets == 0) return cudaSuccess;
-  const int smem = (int)(sizeof(float2) * (size_t)maxn);
+  const int smem = (int)(sizeof(float4) * (size_t)((maxn + 1) / 2));
   cudaError_t e = cudaFuncSetAttribute(schwarz_apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  schwarz_apply_df_kernel<<<dim3((maxn + AR - 1) / AR, nsets), ANT, smem, st>>>(d_mats, d_set_ptr, d_set_sub, d_sub,
-                                                                               d_r, d_p_off32, d_part, wkind,
-                                                                               d_inc_ptr);
-  schwarz_reduce32_kernel<<<dim3((maxn + 255) / 256, nsets), 256, 0, st>>>(d_mats, d_s_off, d_p_off32, d_part, d_s);
+  schwarz_apply_df_kernel<<<dim3((maxn + AR - 1) / AR, nsets), ANT, smem, st>>>(
+      d_mats, d_set_ptr, d_set_sub, d_sub, d_r, d_p_off32, d_part, wkind, d_inc_ptr, d_s_off, d_s, d_done, ckind, d_z);
   return cudaGetLastError();
 }
