@@ -34,6 +34,7 @@
 // thread issues the 36 tcgen05.mma of a k step; eight warps drain the
 // accumulators to the integer chunk sums through tcgen05.ld.
 #include "common.cuh"
+#include "mbar.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -50,7 +51,6 @@ constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024; // + alignment slack
 constexpr int OZ_DRAIN_WARPS = 8;   // warps 2..9: lane quarter w % 4, column half (w - 2) / 4
 constexpr int OZ_THREADS = 32 * (2 + OZ_DRAIN_WARPS);
-constexpr long long OZ_WAIT_CYCLES = 2000000000ll;          // ~1 s: a wait this long is a fault
 static_assert(OZ_NG * OZ_TILE_N == 512, "the group accumulators fill tensor memory");
 
 __device__ __forceinline__ uint32_t bf16_of_small_int(int d) {
@@ -167,47 +167,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitTask* __rest
     *reinterpret_cast<uint4*>(o + q * slice) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
 }
 
-// ---- Blackwell primitives (inline PTX) ----
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after ~1 s (or as soon as another role gave up),
-// raising the block's abort flag and the launch's error word.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err, int code) {
-  const long long t0 = clock64();
-  for (int it = 0;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 63) == 63) {
-      if (*abort) return false;
-      if (clock64() - t0 > OZ_WAIT_CYCLES) {
-        *abort = 1;
-        atomicCAS(err, 0, code);
-        return false;
-      }
-    }
-  }
-}
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {   // bounded, no flags
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity) && clock64() - t0 < OZ_WAIT_CYCLES) {
-  }
-}
-
+// ---- Blackwell primitives (inline PTX; barriers in mbar.cuh) ----
 // 4-D TMA box (32-row groups of 8 k, groups, 2 groups of 8 k, 8 slices) into shared memory;
 // completes on bar.
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* map, int c0, int c1, int c2, int c3,
