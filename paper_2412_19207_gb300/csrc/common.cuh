@@ -178,7 +178,7 @@ struct SyevBatch {
   int* ranks;
   int mode;
   double thr;
-  int bisect;
+  int bisect;                // precision mode 1: bisection eigenvalues, double-float Gram-Schmidt
 };
 int64_t syevd_work_doubles(int m);
 cudaError_t launch_syev_phase(const SyevBatch& b, int phase, cudaStream_t st);

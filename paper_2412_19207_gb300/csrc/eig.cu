@@ -574,6 +574,79 @@ __global__ void __launch_bounds__(NT) syev_orth_kernel(int m, double* __restrict
   }
 }
 
+// The same Gram-Schmidt (same order, two passes) in double-float for precision
+// mode 1: GB300 issues float32 at 64x its float64 rate, and one block per
+// matrix was float64-bound.  Finished vectors are kept as double-float pairs
+// in the inverse-iteration workspace (free by now) next to their float64
+// copies in Z; coefficients, the current vector and the norm are
+// double-float, the final 1/||z|| scaling float64.
+__global__ void __launch_bounds__(NT) syev_orth_df_kernel(int m, double* __restrict__ work_all, int64_t work_stride,
+                                                          const int* __restrict__ ranks) {
+  extern __shared__ float2 smf[];
+  float2* coef = smf;          // [m]
+  float2* zs = coef + m;       // [m] current vector
+  __shared__ float2 red2[NW];
+  __shared__ double inv_s;
+  SyevWork W(work_all + blockIdx.x * work_stride, m);
+  double* Z = W.Z;
+  float2* Z2 = reinterpret_cast<float2*>(W.LU);   // [p][m] double-float copies of the finished vectors
+  const int p = ranks[blockIdx.x], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (p > 0)
+    for (int i = tid; i < m; i += NT) Z2[i] = df_split(Z[i]);
+  for (int k = 1; k < p; ++k) {
+    double* zk = Z + (int64_t)k * m;
+    for (int i = tid; i < m; i += NT) zs[i] = df_split(zk[i]);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = warp; j < k; j += NW) {
+        const float2* zj = Z2 + (int64_t)j * m;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        int i = lane;
+        for (; i + 32 < m; i += 64) {
+          df_mac(h0, l0, zj[i], zs[i]);
+          df_mac(h1, l1, zj[i + 32], zs[i + 32]);
+        }
+        if (i < m) df_mac(h0, l0, zj[i], zs[i]);
+        df_add(h0, l0, h1, l1);
+        df_warp_sum(h0, l0);
+        if (lane == 0) coef[j] = make_float2(-h0, -l0);
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += NT) {
+        float h0 = zs[i].x, l0 = zs[i].y, h1 = 0.f, l1 = 0.f;
+        int j = 0;
+        for (; j + 1 < k; j += 2) {
+          df_mac(h0, l0, coef[j], Z2[(int64_t)j * m + i]);
+          df_mac(h1, l1, coef[j + 1], Z2[(int64_t)(j + 1) * m + i]);
+        }
+        if (j < k) df_mac(h0, l0, coef[j], Z2[(int64_t)j * m + i]);
+        df_add(h0, l0, h1, l1);
+        zs[i] = make_float2(h0, l0);
+      }
+      __syncthreads();
+    }
+    float h = 0.f, l = 0.f;
+    for (int i = tid; i < m; i += NT) df_mac(h, l, zs[i], zs[i]);
+    df_warp_sum(h, l);
+    if (lane == 0) red2[warp] = make_float2(h, l);
+    __syncthreads();
+    if (tid == 0) {
+      float hh = red2[0].x, ll = red2[0].y;
+      for (int w = 1; w < NW; ++w) df_add(hh, ll, red2[w].x, red2[w].y);
+      const double nn = df_to_double(hh, ll);
+      inv_s = (nn > 0.0) ? 1.0 / sqrt(nn) : 0.0;
+    }
+    __syncthreads();
+    const double inv = inv_s;
+    for (int i = tid; i < m; i += NT) {
+      const double v = df_to_double(zs[i].x, zs[i].y) * inv;
+      zk[i] = v;
+      Z2[(int64_t)k * m + i] = df_split(v);
+    }
+    __syncthreads();
+  }
+}
+
 // ---- 5. back-transformation V = H_0 H_1 ... H_{m-3} Z, one warp per vector ----
 constexpr int BW = 8;          // warps (vectors) per block
 __global__ void __launch_bounds__(BW * 32) syev_back_kernel(const double* __restrict__ Aall, int m,
@@ -657,7 +730,10 @@ cudaError_t launch_syev_phase(const SyevBatch& b, int phase, cudaStream_t st) {
     }
     case 3: {
       const int smem = (int)(sizeof(double) * 2 * m);
-      syev_orth_kernel<<<b.batch, NT, smem, st>>>(m, b.work, ws, b.ranks);
+      if (b.bisect)     // precision mode 1: double-float Gram-Schmidt
+        syev_orth_df_kernel<<<b.batch, NT, smem, st>>>(m, b.work, ws, b.ranks);
+      else
+        syev_orth_kernel<<<b.batch, NT, smem, st>>>(m, b.work, ws, b.ranks);
       break;
     }
     case 4: {
