@@ -671,6 +671,63 @@ __global__ void __launch_bounds__(BW * 32) syev_back_kernel(const double* __rest
   }
 }
 
+// The same back-transformation in double-float for precision mode 1.  The
+// reflectors (upper part of A, row k from column k + 1) are split once into
+// the workspace (LU + m^2, row k at k m); then one warp per vector keeps z in
+// registers (entry lane + 32 t in slot t) and, for k = m - 3 .. 0, forms
+// s = beta_k v_k . z and z -= s v_k with double-float products (float32 pipe).
+__global__ void __launch_bounds__(256) syev_back_split_kernel(const double* __restrict__ Aall, int m,
+                                                              double* __restrict__ work_all, int64_t work_stride) {
+  SyevWork W(work_all + blockIdx.y * work_stride, m);
+  const double* A = Aall + blockIdx.y * (int64_t)m * m;
+  float2* V2 = reinterpret_cast<float2*>(W.LU + (int64_t)m * m);
+  const int64_t tot = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / m), j = (int)(e % m);
+    if (k + 1 + j < m) V2[e] = df_split(A[(int64_t)k * m + k + 1 + j]);
+  }
+}
+
+template <int SL>
+__global__ void __launch_bounds__(BW * 32) syev_back_df_kernel(int m, double* __restrict__ work_all,
+                                                               int64_t work_stride, const int* __restrict__ ranks) {
+  SyevWork W(work_all + blockIdx.x * work_stride, m);
+  const float2* V2 = reinterpret_cast<const float2*>(W.LU + (int64_t)m * m);
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.y * BW + (threadIdx.x >> 5);
+  if (c >= ranks[blockIdx.x]) return;
+  double* z = W.Z + (int64_t)c * m;
+  float2 zr[SL];
+#pragma unroll
+  for (int t = 0; t < SL; ++t) {
+    const int i = lane + 32 * t;
+    zr[t] = (i < m) ? df_split(z[i]) : make_float2(0.f, 0.f);
+  }
+  for (int k = m - 3; k >= 0; --k) {
+    const double bt = W.beta[k];
+    if (bt == 0.0) continue;
+    const float2* vk = V2 + (int64_t)k * m - (k + 1);       // vk[i] = v_k entry of z_i, i >= k + 1
+    float2 vr[SL];
+    float h = 0.f, l = 0.f;
+#pragma unroll
+    for (int t = 0; t < SL; ++t) {
+      const int i = lane + 32 * t;
+      vr[t] = (i > k && i < m) ? vk[i] : make_float2(0.f, 0.f);
+      df_mac(h, l, vr[t], zr[t]);
+    }
+    df_warp_sum(h, l);
+    // s = -beta_k (v_k . z) as a double-float
+    const float2 sb = df_split(-bt * df_to_double(h, l));
+#pragma unroll
+    for (int t = 0; t < SL; ++t) df_mac(zr[t].x, zr[t].y, sb, vr[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < SL; ++t) {
+    const int i = lane + 32 * t;
+    if (i < m) z[i] = df_to_double(zr[t].x, zr[t].y);
+  }
+}
+
 // G <- V: column c of G is eigenvector c (c < p), zero beyond; 32 x 32 tiles.
 __global__ void __launch_bounds__(256) syev_output_kernel(double* __restrict__ Aall, int m,
                                                           const double* __restrict__ work_all, int64_t work_stride,
@@ -737,7 +794,21 @@ cudaError_t launch_syev_phase(const SyevBatch& b, int phase, cudaStream_t st) {
       break;
     }
     case 4: {
-      syev_back_kernel<<<dim3(b.batch, (m + BW - 1) / BW), BW * 32, 0, st>>>(b.A, m, b.work, ws, b.ranks);
+      if (b.bisect) {   // precision mode 1: double-float back-transformation
+        const int64_t tot = (int64_t)m * m;
+        syev_back_split_kernel<<<dim3((int)std::min<int64_t>((tot + 255) / 256, 512), b.batch), 256, 0, st>>>(
+            b.A, m, b.work, ws);
+        const dim3 g(b.batch, (m + BW - 1) / BW);
+        const int sl = (m + 31) / 32;
+        if (sl <= 4) syev_back_df_kernel<4><<<g, BW * 32, 0, st>>>(m, b.work, ws, b.ranks);
+        else if (sl <= 8) syev_back_df_kernel<8><<<g, BW * 32, 0, st>>>(m, b.work, ws, b.ranks);
+        else if (sl <= 12) syev_back_df_kernel<12><<<g, BW * 32, 0, st>>>(m, b.work, ws, b.ranks);
+        else if (sl <= 16) syev_back_df_kernel<16><<<g, BW * 32, 0, st>>>(m, b.work, ws, b.ranks);
+        else if (sl <= 24) syev_back_df_kernel<24><<<g, BW * 32, 0, st>>>(m, b.work, ws, b.ranks);
+        else syev_back_df_kernel<32><<<g, BW * 32, 0, st>>>(m, b.work, ws, b.ranks);
+      } else {
+        syev_back_kernel<<<dim3(b.batch, (m + BW - 1) / BW), BW * 32, 0, st>>>(b.A, m, b.work, ws, b.ranks);
+      }
       const int nt = (m + 31) / 32;
       syev_output_kernel<<<dim3(nt, nt, b.batch), 256, 0, st>>>(b.A, m, b.work, ws, b.ranks);
       break;
