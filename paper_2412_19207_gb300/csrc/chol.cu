@@ -95,52 +95,76 @@ __global__ void trsm_panel_kernel(const CholMat* __restrict__ mats, int c0) {
 // trailing update A22 -= L21 L21^T and the block-column inverse run on the
 // float32 pipe with no conversions.
 
-// Diagonal block c0 of A2: L11 (float64 Cholesky, pivots checked as in the
-// float64 path) back to A2, L11^{-1} (one thread per column) to X2.
+// Diagonal block c0 of A2: L11 back to A2 and L11^{-1} to X2, in double-float
+// on the float32 pipe (the block is stored in double-float, so float64 here
+// would add no accuracy, while GB300's float64 unit makes the serial
+// sqrt / divide / update chain of the 32 columns its bottleneck).  Pivots are
+// checked against the same tolerance as the float64 path.  Entries accumulate
+// their updates unnormalised and are renormalised when read as a pivot or
+// column entry.  The inverse: thread c forms column c by forward substitution
+// in registers (every index static).
 __global__ void potrf_diag_df_kernel(const CholMat* __restrict__ mats, int c0, int* __restrict__ fail,
                                      const double* __restrict__ dmax) {
   const CholMat M = mats[blockIdx.x];
   if (M.n <= c0) return;
   const int nb = min(NB, M.n - c0);
-  __shared__ double a[NB][NB + 1];
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    const float2 v = M.A2[(int64_t)(c0 + r) * M.ld + c0 + c];
-    a[r][c] = df_to_double(v.x, v.y);
+  __shared__ float2 a[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    a[r][c] = (r < nb && c <= r) ? M.A2[(int64_t)(c0 + r) * M.ld + c0 + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const double tol = 1e-15 * dmax[blockIdx.x];
   for (int j = 0; j < nb; ++j) {
     if (threadIdx.x == 0) {
-      double piv = a[j][j];
-      if (!(piv > tol)) {
+      float2 piv = df_fast(a[j][j].x, a[j][j].y);
+      if (!(df_to_double(piv.x, piv.y) > tol)) {
         fail[blockIdx.x] = 1;
-        piv = fmax(fabs(piv), tol > 0.0 ? tol : 1e-300);
+        piv = df_split(fmax(fabs(df_to_double(piv.x, piv.y)), tol > 0.0 ? tol : 1e-300));
       }
-      a[j][j] = sqrt(piv);
+      a[j][j] = df_sqrt(piv);
     }
     __syncthreads();
-    for (int r = j + 1 + threadIdx.x; r < nb; r += blockDim.x) a[r][j] /= a[j][j];
+    for (int r = j + 1 + threadIdx.x; r < nb; r += blockDim.x) {
+      float2 v = a[r][j];
+      df_renorm(v.x, v.y);
+      a[r][j] = df_div(v, a[j][j]);
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-      const int r = e / nb, c = e % nb;
-      if (c > j && r >= c) a[r][c] -= a[r][j] * a[c][j];
+    // a[r][c] -= l_rj l_cj for j < c <= r: thread per entry of the trailing triangle
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      const int r = e / NB, c = e % NB;
+      if (c > j && r >= c && r < nb) {
+        const float2 lr = a[r][j], lc = a[c][j];
+        float h = a[r][c].x, l = a[r][c].y;
+        df_mac(h, l, make_float2(-lr.x, -lr.y), lc);
+        a[r][c] = make_float2(h, l);
+      }
     }
     __syncthreads();
   }
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     const int r = e / nb, c = e % nb;
-    if (r >= c) M.A2[(int64_t)(c0 + r) * M.ld + c0 + c] = df_split(a[r][c]);
+    if (r >= c) M.A2[(int64_t)(c0 + r) * M.ld + c0 + c] = a[r][c];
   }
   const int c = threadIdx.x;
   if (c < nb) {
-    double x[NB];
-    for (int r = c; r < nb; ++r) {
-      double sacc = (r == c) ? 1.0 : 0.0;
-      for (int k = c; k < r; ++k) sacc = fma(-a[r][k], x[k], sacc);
-      x[r] = sacc / a[r][r];
-      M.X2[(int64_t)(c0 + r) * M.ld + c0 + c] = df_split(x[r]);
+    float2 x[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      float h0 = (q == c) ? 1.f : 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < q; ++k) {
+        const float2 lq = a[q][k];
+        if (k & 1) df_mac(h1, l1, make_float2(-lq.x, -lq.y), x[k]);
+        else df_mac(h0, l0, make_float2(-lq.x, -lq.y), x[k]);
+      }
+      df_add(h0, l0, h1, l1);
+      x[q] = (c <= q && q < nb) ? df_div(make_float2(h0, l0), a[q][q]) : make_float2(0.f, 0.f);
     }
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (c <= q && q < nb) M.X2[(int64_t)(c0 + q) * M.ld + c0 + c] = x[q];
   }
 }
 

@@ -60,3 +60,33 @@ __device__ __forceinline__ void df_warp_sum(float& h, float& l) {
     df_add(h, l, oh, ol);
   }
 }
+
+// fast two-sum (|a| >= |b| or a == 0): s + e = a + b exactly
+__device__ __forceinline__ float2 df_fast(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+// a / b in double-float (Dekker 1971): q1 = a_h / b_h, r = a - q1 b formed with
+// an exact product, q2 = r_h / b_h; about 2^-46 relative.
+__device__ __forceinline__ float2 df_div(float2 a, float2 b) {
+  const float q1 = __fdiv_rn(a.x, b.x);
+  const float p = __fmul_rn(q1, b.x);
+  const float pe = __fmaf_rn(q1, b.x, -p);             // q1 b_h = p + pe exactly
+  float rh, re;
+  df_two_sum(a.x, -p, rh, re);
+  const float r = __fadd_rn(rh, __fsub_rn(__fadd_rn(re, a.y), __fmaf_rn(q1, b.y, pe)));
+  return df_fast(q1, __fdiv_rn(r, b.x));
+}
+
+// sqrt(a) in double-float, a >= 0: y = sqrt(a_h) (float32), then one Heron step
+// y + (a - y^2) / (2 y) with the residual formed exactly (Karp & Markstein,
+// "High-precision division and square root", ACM TOMS 23, 1997).
+__device__ __forceinline__ float2 df_sqrt(float2 a) {
+  if (!(a.x > 0.f)) return make_float2(0.f, 0.f);
+  const float y = __fsqrt_rn(a.x);
+  const float p = __fmul_rn(y, y);
+  const float pe = __fmaf_rn(y, y, -p);                // y^2 = p + pe exactly
+  const float e = __fadd_rn(__fsub_rn(__fsub_rn(a.x, p), pe), a.y);
+  return df_fast(y, __fdiv_rn(e, __fmul_rn(2.f, y)));
+}
