@@ -161,7 +161,8 @@ constexpr int TC = 2;          // blocks per matrix (cluster size; one block per
 
 template <int SL>
 __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ Aall, int m,
-                                                          double* __restrict__ work_all, int64_t work_stride) {
+                                                          double* __restrict__ work_all, int64_t work_stride,
+                                                          int use_dp) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double sm[];
@@ -170,6 +171,10 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
   double* wl = w + m;          // [m] this block's partial product (read by the cluster)
   double* wdot = wl + m;       // [m] dot products of the rows this block owns
   double* part = wdot + m;     // [NW][m] per-warp partials
+  // [NW][SR][33] lane partials of the row dots (SR rows per warp, padded rows);
+  // summed by one thread per row instead of a 32-lane shuffle reduction
+  const int SR = (m - 1 + TC * NW - 1) / (TC * NW);
+  double* dpart = part + (int64_t)NW * m;
   __shared__ double red[33];
   const int mat = blockIdx.x / TC;
   const int rank = (int)cluster.block_rank();
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
       double acc[SL];
 #pragma unroll
       for (int t = 0; t < SL; ++t) acc[t] = 0.0;
-      for (int c = gw; c < n1; c += TC * NW) {
+      for (int c = gw, si = 0; c < n1; c += TC * NW, ++si) {
         const double* R = Ak + (int64_t)c * m;
         const int tmax = c >> 5;               // last slot holding part of row c (warp-uniform)
         double x[SL];
@@ -219,8 +224,12 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
           acc[t] = fma(vc, x[t], acc[t]);
           dot = fma(x[t], (j < c) ? v[j] : 0.0, dot);
         }
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        if (lane == 0) wdot[c] = dot;          // row c belongs to this warp alone
+        if (use_dp) {
+          dpart[((int64_t)warp * SR + si) * 33 + lane] = dot;
+        } else {
+          for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+          if (lane == 0) wdot[c] = dot;        // row c belongs to this warp alone
+        }
       }
 #pragma unroll
       for (int t = 0; t < SL; ++t)
@@ -229,7 +238,18 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
       for (int j = tid; j < n1; j += NT) {
         double s = 0.0;
         for (int q = 0; q < NW; ++q) s += part[q * m + j];
-        if ((j % (TC * NW)) / NW == rank) s += wdot[j];   // dot of a row this block owns
+        const int gj = j % (TC * NW);
+        if (gj / NW == rank) {                 // dot of a row this block owns
+          if (use_dp) {
+            const double* dp = dpart + ((int64_t)(gj % NW) * SR + j / (TC * NW)) * 33;
+            double d0 = 0.0, d1 = 0.0;
+#pragma unroll
+            for (int l = 0; l < 32; l += 2) { d0 += dp[l]; d1 += dp[l + 1]; }
+            s += d0 + d1;
+          } else {
+            s += wdot[j];
+          }
+        }
         wl[j] = s;
       }
       cluster.sync();                          // partials visible to the cluster
@@ -292,7 +312,16 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
 
 template <int SL>
 cudaError_t launch_tridiag(double* A, int m, int batch, double* work, int64_t ws, cudaStream_t st) {
-  const int smem = (int)(sizeof(double) * (size_t)(4 + NW) * m);
+  const int SR = (m - 1 + TC * NW - 1) / (TC * NW);
+  int smem = (int)(sizeof(double) * ((size_t)(4 + NW) * m + (size_t)NW * SR * 33));
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int use_dp = 1;
+  if (smem > optin - 1024) {                 // large m: shuffle-reduced row dots
+    use_dp = 0;
+    smem = (int)(sizeof(double) * (size_t)(4 + NW) * m);
+  }
   cudaError_t e = cudaFuncSetAttribute(syev_tridiag_kernel<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -307,7 +336,7 @@ cudaError_t launch_tridiag(double* A, int m, int batch, double* work, int64_t ws
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, syev_tridiag_kernel<SL>, A, m, work, ws);
+  return cudaLaunchKernelEx(&cfg, syev_tridiag_kernel<SL>, A, m, work, ws, use_dp);
 }
 
 // ---- 2. eigenvalues, grid (matrix, part of the spectrum) ----
