@@ -129,7 +129,9 @@ static const char* const KNAMES[K_COUNT] = {
 static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1,
                                      0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1, 0, 0, 2, 0};
 
-static bool family_is_df(int k) { return k == K_PAIRGRAM || k == K_CHOL || k == K_TRTRI; }
+static bool family_is_df(int k) {
+  return k == K_PAIRGRAM || k == K_CHOL || k == K_TRTRI || k == K_EIG_ORTH || k == K_EIG_BACK;
+}
 
 struct Prof {
   bool on = false;

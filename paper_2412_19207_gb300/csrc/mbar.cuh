@@ -48,15 +48,3 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
   while (!mbar_try(bar, parity) && clock64() - t0 < MBAR_WAIT_CYCLES) {
   }
 }
-
-// 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16); completes on bar.
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-// Named barrier over the first `count` threads of the block (count a multiple of 32).
-__device__ __forceinline__ void named_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
-}
