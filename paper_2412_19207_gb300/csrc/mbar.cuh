@@ -1,5 +1,5 @@
-// mbarrier and bulk-copy primitives (inline PTX, sm_100 family) shared by the
-// pipelined kernels.  Every wait is bounded: after about a second it raises a
+// mbarrier primitives (inline PTX, sm_100 family) shared by the pipelined
+// kernels.  Every wait is bounded: after about a second it raises a
 // block-local abort flag and a launch-wide error word and returns false, so a
 // lost arrival ends the kernel with an error status instead of a hang.
 #pragma once
