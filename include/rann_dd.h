@@ -207,9 +207,13 @@ rann_status rann_dd_solve_backward(rann_dd_handle* h, const double* gW_dev, doub
  * blocks B_j and every residual that decides a restart or convergence stay
  * float64-accurate, so the solve is an iterative refinement converging to the
  * float64 solution.  In mode 1 the two dense products of the PCA (the Gram
- * matrices Psi_j^T Psi_j and B_j = H_j V_{p_j}) are formed on the bf16 tensor
- * cores from exact 7-bit digit slices of float64 operands (Ozaki splitting),
- * with an error of the float64 product's order.  Mode 0: float64 SIMT
+ * matrices Psi_j^T Psi_j and B_j = H_j V_{p_j}) and the neighbour Gram blocks
+ * are formed on the bf16 tensor cores (tcgen05) from exact 7-bit digit slices
+ * of float64 operands (Ozaki splitting), with an error of the float64
+ * product's order; the Gram-Schmidt and back-transformation of the kept
+ * eigenvectors and the 32 x 32 diagonal blocks of the local Cholesky factors
+ * are double-float (the eigenvalues, hence the PCA ranks, stay float64).
+ * Mode 0: float64 SIMT
  * arithmetic throughout (needed where the preconditioner must be exact to
  * float64 rounding, e.g. the unreduced system with PCA off).  Affects the
  * next pca, setup_precond and solve. */
