@@ -101,8 +101,7 @@ __global__ void trsm_panel_kernel(const CholMat* __restrict__ mats, int c0) {
 // sqrt / divide / update chain of the 32 columns its bottleneck).  Pivots are
 // checked against the same tolerance as the float64 path.  Entries accumulate
 // their updates unnormalised and are renormalised when read as a pivot or
-// column entry.  The inverse: thread c forms column c by forward substitution
-// in registers (every index static).
+// column entry.  The inverse: thread c forms column c by forward substitution.
 __global__ void potrf_diag_df_kernel(const CholMat* __restrict__ mats, int c0, int* __restrict__ fail,
                                      const double* __restrict__ dmax) {
   const CholMat M = mats[blockIdx.x];
@@ -131,10 +130,10 @@ __global__ void potrf_diag_df_kernel(const CholMat* __restrict__ mats, int c0, i
       a[r][j] = df_div(v, a[j][j]);
     }
     __syncthreads();
-    // a[r][c] -= l_rj l_cj for j < c <= r: thread per entry of the trailing triangle
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-      const int r = e / NB, c = e % NB;
-      if (c > j && r >= c && r < nb) {
+    // a[r][c] -= l_rj l_cj for j < c <= r: thread per entry of the rows below j
+    for (int e = threadIdx.x; e < (nb - j - 1) * NB; e += blockDim.x) {
+      const int r = j + 1 + e / NB, c = e % NB;
+      if (c > j && r >= c) {
         const float2 lr = a[r][j], lc = a[c][j];
         float h = a[r][c].x, l = a[r][c].y;
         df_mac(h, l, make_float2(-lr.x, -lr.y), lc);
@@ -147,29 +146,33 @@ __global__ void potrf_diag_df_kernel(const CholMat* __restrict__ mats, int c0, i
     const int r = e / nb, c = e % nb;
     if (r >= c) M.A2[(int64_t)(c0 + r) * M.ld + c0 + c] = a[r][c];
   }
+  // thread c: column c of L11^{-1} by forward substitution (column kept in shared memory)
+  __shared__ float2 xs[NB][NB + 1];
   const int c = threadIdx.x;
   if (c < nb) {
-    float2 x[NB];
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
+    for (int q = 0; q < nb; ++q) {
       float h0 = (q == c) ? 1.f : 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-#pragma unroll
-      for (int k = 0; k < q; ++k) {
-        const float2 lq = a[q][k];
-        if (k & 1) df_mac(h1, l1, make_float2(-lq.x, -lq.y), x[k]);
-        else df_mac(h0, l0, make_float2(-lq.x, -lq.y), x[k]);
+      int k = c;                                     // x_kc = 0 for k < c
+      for (; k + 1 < q; k += 2) {
+        const float2 la = a[q][k], lb = a[q][k + 1];
+        df_mac(h0, l0, make_float2(-la.x, -la.y), xs[k][c]);
+        df_mac(h1, l1, make_float2(-lb.x, -lb.y), xs[k + 1][c]);
+      }
+      if (k < q) {
+        const float2 la = a[q][k];
+        df_mac(h0, l0, make_float2(-la.x, -la.y), xs[k][c]);
       }
       df_add(h0, l0, h1, l1);
-      x[q] = (c <= q && q < nb) ? df_div(make_float2(h0, l0), a[q][q]) : make_float2(0.f, 0.f);
+      const float2 v = (c <= q) ? df_div(make_float2(h0, l0), a[q][q]) : make_float2(0.f, 0.f);
+      xs[q][c] = v;
+      if (c <= q) M.X2[(int64_t)(c0 + q) * M.ld + c0 + c] = v;
     }
-#pragma unroll
-    for (int q = 0; q < NB; ++q)
-      if (c <= q && q < nb) M.X2[(int64_t)(c0 + q) * M.ld + c0 + c] = x[q];
   }
 }
 
-// L21 = A21 L11^{-T}: row r of the panel times the stored inverse block, one
-// thread per row, in double-float.
+// L21 = A21 L11^{-T}: row r of the panel times the stored inverse block, in
+// double-float; four threads per row, each forming eight of its 32 columns
+// (the k loop is not unrolled, so the code stays small).
 __global__ void __launch_bounds__(128) trsm_panel_df_kernel(const CholMat* __restrict__ mats, int c0) {
   const CholMat M = mats[blockIdx.y];
   if (M.n <= c0 + NB) return;
@@ -179,23 +182,29 @@ __global__ void __launch_bounds__(128) trsm_panel_df_kernel(const CholMat* __res
     li[r][c] = (c <= r) ? M.X2[(int64_t)(c0 + r) * M.ld + c0 + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int r = c0 + NB + blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= M.n) return;
-  float2* row = M.A2 + (int64_t)r * M.ld + c0;
-  float ah[NB], al[NB];
+  const int r = c0 + NB + blockIdx.x * (blockDim.x / 4) + (threadIdx.x >> 2);
+  const int j0 = (threadIdx.x & 3) * 8;
+  const bool valid = r < M.n;                       // the four threads of a row share it
+  float2* row = M.A2 + (int64_t)(valid ? r : 0) * M.ld + c0;
+  float ah[8], al[8];
 #pragma unroll
-  for (int j = 0; j < NB; ++j) { ah[j] = 0.f; al[j] = 0.f; }
+  for (int u = 0; u < 8; ++u) { ah[u] = 0.f; al[u] = 0.f; }
+  if (valid) {
+#pragma unroll 1
+    for (int k = 0; k < j0 + 8; ++k) {               // columns j >= k only: L11^{-1} is lower triangular
+      const float2 xk = row[k];
 #pragma unroll
-  for (int k = 0; k < NB; ++k) {
-    const float2 xk = row[k];
-#pragma unroll
-    for (int j = k; j < NB; ++j) df_mac(ah[j], al[j], xk, li[j][k]);
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u >= k) df_mac(ah[u], al[u], xk, li[j0 + u][k]);
+    }
   }
+  __syncwarp();                                      // the row's reads of columns < 32 precede its writes
+  if (valid)
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    df_renorm(ah[j], al[j]);
-    row[j] = make_float2(ah[j], al[j]);
-  }
+    for (int u = 0; u < 8; ++u) {
+      df_renorm(ah[u], al[u]);
+      row[j0 + u] = make_float2(ah[u], al[u]);
+    }
 }
 
 // A22 -= L21 L21^T on the lower triangle of A2, 64 x 64 tiles, double-float.
@@ -959,7 +968,7 @@ cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, 
   if (df) {
     potrf_diag_df_kernel<<<nmat, NB * 8, 0, st>>>(d_mats, c0, d_fail, d_dmax);
     if (rest > 0) {
-      trsm_panel_df_kernel<<<dim3((rest + 127) / 128, nmat), 128, 0, st>>>(d_mats, c0);
+      trsm_panel_df_kernel<<<dim3((rest + 31) / 32, nmat), 128, 0, st>>>(d_mats, c0);
       syrk_update_df_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
     }
   } else {
