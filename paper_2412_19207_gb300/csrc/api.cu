@@ -42,7 +42,7 @@ cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, 
                                     const int* d_set_sub, const SubDev* d_sub, const double* d_r,
                                     const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
                                     int* d_done, int wkind, const int* d_inc_ptr, int ckind, double* d_z,
-                                    cudaStream_t st);
+                                    cudaStream_t st, const float2* d_r2 = nullptr);
 cudaError_t launch_trmv_lower_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
                                  const float2* d_g2, float2* d_y2, cudaStream_t st);
 cudaError_t launch_trmv_upper_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
@@ -68,7 +68,8 @@ cudaError_t launch_add_combination(const double* V, int64_t ldv, int nv, const d
 cudaError_t launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t st);
 cudaError_t launch_cg_update(double a, const double* p, const double* q, double* x, double* r, int64_t n,
                              cudaStream_t st);
-cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, cudaStream_t st);
+cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, cudaStream_t st,
+                              float2* y2 = nullptr);
 cudaError_t launch_assemble_local(const double* d_pairbuf, const int64_t* d_tab, const int* d_tab_ptr,
                                   const int* d_boff, const int* d_boff_ptr, const CholMat* d_mats, int nsets,
                                   int maxn, double* d_dmax, cudaStream_t st);
@@ -832,11 +833,14 @@ extern "C" rann_status rann_dd_normal_matvec(rann_dd_handle* h, const double* x_
 }
 
 // Inner-iteration operator: z = H^T H x with double-float blocks.
-static rann_status normal_matvec_fast(rann_dd_handle* h, const double* x, double* z) {
+// x2 / z2 (optional): double-float splits of x (read instead of x) and of z
+// (written), used only on the block-row path (gram_ready).
+static rann_status normal_matvec_fast(rann_dd_handle* h, const double* x, double* z, const float2* x2 = nullptr,
+                                      float2* z2 = nullptr) {
   if (h->gram_ready) {
     // z_k = sum_l G_kl x_l from the block rows of H^T H
     KLA(h, K_GRAMOP, 1, 8.0 * (h->gram_entries + h->dof), 2.0 * h->gram_entries,
-        launch_gram_matvec(h->gram, h->J, h->d_gtile, h->ngtile, h->gram_maxn2, x, z, h->st));
+        launch_gram_matvec(h->gram, h->J, h->d_gtile, h->ngtile, h->gram_maxn2, x, z, h->st, x2, z2));
     return RANN_OK;
   }
   // y_j = B_j x_j row by row (per block), then z_j = B_j^T y with y summed over the blocks holding each point
@@ -1211,7 +1215,7 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
 // z = M^{-1} r, or with transpose z = M^{-T} r = sum_i R_i^T A_i^{-1} D_i R_i r
 // (D_i moves to the gather, the combine sums unweighted).
 static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, bool fast = false,
-                              bool transpose = false) {
+                              bool transpose = false, const float2* r2 = nullptr) {
   if (h->prec_kind == RANN_PREC_NONE) {
     CK(cudaMemcpyAsync(z, r, sizeof(double) * h->dof, cudaMemcpyDeviceToDevice, h->st));
     return RANN_OK;
@@ -1233,7 +1237,7 @@ static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, boo
         2.0 * (h->sum_n2 + h->sum_n),
         launch_schwarz_apply_df(h->d_mats, h->nsets, h->maxn, h->d_set_ptr, h->d_set_sub, h->d_sub, r, h->d_s_off,
                                 h->d_p_off32, h->d_tpart32, h->d_s, h->d_adone, wkind, h->d_inc_ptr, ckind, z,
-                                h->st));
+                                h->st, r2));
     if (ckind == RANN_PREC_RAS) return RANN_OK;                // the restricted combine ran in the apply
   }
   if (fast) {
@@ -1289,8 +1293,8 @@ struct Workspace {
 static rann_status op_inner(rann_dd_handle* h, const double* x, double* z) {
   return h->inner_df ? normal_matvec_fast(h, x, z) : rann_dd_normal_matvec(h, x, z);
 }
-static rann_status prec_inner(rann_dd_handle* h, const double* r, double* z) {
-  return prec_apply(h, r, z, h->inner_df != 0 || h->prec_df);
+static rann_status prec_inner(rann_dd_handle* h, const double* r, double* z, const float2* r2 = nullptr) {
+  return prec_apply(h, r, z, h->inner_df != 0 || h->prec_df, false, r2);
 }
 
 // CG on H^T H W = b with b = H^T F (F_dev) or b given (b_dev).
@@ -1571,7 +1575,14 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
   double *b = ws.get(n), *t = ws.get(n), *V = ws.get((size_t)(k + 1) * n), *hv = ws.get(2 * (k + 2));
   const size_t nstate = (size_t)(k + 1) * k + 2 * k + (k + 1) + 3 * (k + 2) + 4;
   double* state = ws.get(nstate);
-  REQUIRE(b && t && V && hv && state, RANN_ENOMEM, "workspace allocation failed");
+  // double-float splits of the basis vectors and of A v_j, written by their producers
+  // when the inner operator is the block-row product (its consumers then skip the split)
+  const bool split2 = h->inner_df && h->gram_ready;
+  double* V2d = split2 ? ws.get((size_t)(k + 1) * n) : nullptr;
+  double* t2d = split2 ? ws.get(n) : nullptr;
+  REQUIRE(b && t && V && hv && state && (!split2 || (V2d && t2d)), RANN_ENOMEM, "workspace allocation failed");
+  float2* V2 = reinterpret_cast<float2*>(V2d);
+  float2* t2 = reinterpret_cast<float2*>(t2d);
   GmresDev sd{};
   sd.H = state;
   sd.cs = sd.H + (size_t)(k + 1) * k;
@@ -1625,7 +1636,7 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
     if (!std::isfinite(rel)) { st = RANN_BREAKDOWN; break; }
     if (rel <= rtol) { st = RANN_OK; break; }
     if (it >= maxit) break;
-    KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_copy(1.0 / beta, V, V, n, h->st));
+    KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_copy(1.0 / beta, V, V, n, h->st, V2));
     // Arnoldi steps with the Givens bookkeeping on the device; the host stays at
     // most two steps ahead and stops enqueueing once the device reports done
     CK(cudaMemsetAsync(sd.g, 0, sizeof(double) * (k + 1), h->st));
@@ -1639,8 +1650,13 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
         if (*(volatile int*)hdone) break;
       }
       double* w = V + (size_t)(j + 1) * n;
-      TRY(op_inner(h, V + (size_t)j * n, t));
-      TRY(prec_inner(h, t, w));
+      if (split2) {
+        TRY(normal_matvec_fast(h, V + (size_t)j * n, t, V2 + (size_t)j * n, t2));
+        TRY(prec_inner(h, t, w, t2));
+      } else {
+        TRY(op_inner(h, V + (size_t)j * n, t));
+        TRY(prec_inner(h, t, w));
+      }
       // classical Gram-Schmidt, twice
       for (int pass = 0; pass < 2; ++pass) {
         KLA(h, K_DOT, 1, 8.0 * n * (j + 2), 2.0 * n * (j + 1),
@@ -1650,7 +1666,8 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
       }
       KLA(h, K_DOT, 1, 8.0 * n, 2.0 * n, launch_multidot(w, 0, 1, w, n, h->d_red, sd.ww, h->st));
       KLA(h, K_VEC, 1, 0, 0, launch_gmres_givens(sd, j, k, mbnorm, rtol, h->st));
-      KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_dev(w, sd.inv, n, h->st));
+      KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n,
+          launch_scale_dev(w, sd.inv, n, h->st, split2 ? V2 + (size_t)(j + 1) * n : nullptr));
       CK(cudaMemcpyAsync(hdone, sd.done, sizeof(int), cudaMemcpyDeviceToHost, h->st));
       CK(cudaEventRecord(evs[j % 3], h->st));
     }

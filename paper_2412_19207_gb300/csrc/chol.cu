@@ -744,7 +744,8 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
                                                                const int* __restrict__ inc_ptr,
                                                                const int64_t* __restrict__ s_off,
                                                                double* __restrict__ s, int* __restrict__ done,
-                                                               int ckind, double* __restrict__ z) {
+                                                               int ckind, double* __restrict__ z,
+                                                               const float2* __restrict__ r2) {
   extern __shared__ float4 gs4[];                     // (g_2c, g_2c+1) as double-float pairs
   __shared__ float4 ys4[AR / 2];                      // (y_2q, y_2q+1)
   __shared__ int seg_c[AMAX_SUB + 1], seg_p[AMAX_SUB];
@@ -785,7 +786,8 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
       if (c < r1) {
         int q = 0;
         while (q + 1 < nq && seg_c[q + 1] <= c) ++q;
-        v[e] = df_split(seg_d[q] * r[seg_w[q] + (c - seg_c[q])]);
+        // unit weights (the forward apply): the producer's double-float split of r
+        v[e] = r2 ? r2[seg_w[q] + (c - seg_c[q])] : df_split(seg_d[q] * r[seg_w[q] + (c - seg_c[q])]);
       }
     }
     gs4[c2] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
@@ -1032,12 +1034,13 @@ cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, 
                                     const int* d_set_sub, const SubDev* d_sub, const double* d_r,
                                     const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
                                     int* d_done, int wkind, const int* d_inc_ptr, int ckind, double* d_z,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, const float2* d_r2) {
   if (nsets == 0) return cudaSuccess;
   const int smem = (int)(sizeof(float4) * (size_t)((maxn + 1) / 2));
   cudaError_t e = cudaFuncSetAttribute(schwarz_apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   schwarz_apply_df_kernel<<<dim3((maxn + AR - 1) / AR, nsets), ANT, smem, st>>>(
-      d_mats, d_set_ptr, d_set_sub, d_sub, d_r, d_p_off32, d_part, wkind, d_inc_ptr, d_s_off, d_s, d_done, ckind, d_z);
+      d_mats, d_set_ptr, d_set_sub, d_sub, d_r, d_p_off32, d_part, wkind, d_inc_ptr, d_s_off, d_s, d_done, ckind, d_z,
+      wkind == RANN_PREC_AS ? d_r2 : nullptr);
   return cudaGetLastError();
 }

@@ -140,7 +140,8 @@ cudaError_t launch_cg_update_dev(const double* p, const double* q, double* x, do
                                  int ph, cudaStream_t st);
 cudaError_t launch_cg_check(const CgDev& s, double bnorm, double rtol, cudaStream_t st);
 cudaError_t launch_cg_direction(const double* z, double* p, int64_t n, const CgDev& s, int ph, cudaStream_t st);
-cudaError_t launch_scale_dev(double* y, const double* a, int64_t n, cudaStream_t st);
+// y *= *a; y2 (optional): the double-float split of the result
+cudaError_t launch_scale_dev(double* y, const double* a, int64_t n, cudaStream_t st, float2* y2 = nullptr);
 
 // gramop.cu -- the normal matrix as double-float block rows R_k = [G_kl]_l
 constexpr int GRAM_TILE_ROWS = 8;    // rows of R_k per block of the row-dot kernel (one warp each)
@@ -160,8 +161,11 @@ struct GramRows {                    // device arrays
 };
 cudaError_t launch_gramrows_build(const GramRows& g, const double* d_pairbuf, int J, int maxp, int maxn2,
                                   cudaStream_t st);
+// z = (H^T H) x from the block rows; x2 (optional): the double-float split of x
+// (staged instead of splitting x); z2 (optional): the split of z is written too
 cudaError_t launch_gram_matvec(const GramRows& g, int J, const int* d_rtile, int nrtile, int maxn2,
-                               const double* d_x, double* d_z, cudaStream_t st);
+                               const double* d_x, double* d_z, cudaStream_t st, const float2* d_x2 = nullptr,
+                               float2* d_z2 = nullptr);
 
 // eig.cu -- batched symmetric eigen-decomposition (float64)
 // Eigenpairs of `batch` m x m symmetric matrices A; ranks by the PCA rule (mode, thr);

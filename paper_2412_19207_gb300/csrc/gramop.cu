@@ -39,7 +39,8 @@ __global__ void gramrows_build_kernel(const GramRows g, const double* __restrict
 // to its neighbour), then one warp per row with 16-byte loads and two chains
 // per lane.
 __global__ void __launch_bounds__(256) gram_rowdot_kernel(const GramRows g, const int* __restrict__ rtile,
-                                                          const double* __restrict__ x, double* __restrict__ z) {
+                                                          const double* __restrict__ x, const float2* __restrict__ x2,
+                                                          double* __restrict__ z, float2* __restrict__ z2) {
   extern __shared__ float4 xs[];
   __shared__ int seg_c4[GRAM_MAX_NBR + 1], seg_p[GRAM_MAX_NBR];
   __shared__ int64_t seg_w[GRAM_MAX_NBR];
@@ -58,9 +59,16 @@ __global__ void __launch_bounds__(256) gram_rowdot_kernel(const GramRows g, cons
     int q = 0;
     while (q + 1 < nq && seg_c4[q + 1] <= i) ++q;
     const int e = 2 * (i - seg_c4[q]);
-    const double* xl = x + seg_w[q];
-    const float2 a = df_split(xl[e]);
-    const float2 b = (e + 1 < seg_p[q]) ? df_split(xl[e + 1]) : make_float2(0.f, 0.f);
+    float2 a, b;
+    if (x2) {                                      // the producer's double-float split of x
+      const float2* xl = x2 + seg_w[q];
+      a = xl[e];
+      b = (e + 1 < seg_p[q]) ? xl[e + 1] : make_float2(0.f, 0.f);
+    } else {
+      const double* xl = x + seg_w[q];
+      a = df_split(xl[e]);
+      b = (e + 1 < seg_p[q]) ? df_split(xl[e + 1]) : make_float2(0.f, 0.f);
+    }
     xs[i] = make_float4(a.x, a.y, b.x, b.y);
   }
   __syncthreads();
@@ -84,7 +92,11 @@ __global__ void __launch_bounds__(256) gram_rowdot_kernel(const GramRows g, cons
   }
   df_add(h0, l0, h1, l1);
   df_warp_sum(h0, l0);
-  if (lane == 0) z[g.woff[k] + c] = df_to_double(h0, l0);
+  if (lane == 0) {
+    const double v = df_to_double(h0, l0);
+    z[g.woff[k] + c] = v;
+    if (z2) z2[g.woff[k] + c] = df_split(v);
+  }
 }
 
 }  // namespace
@@ -103,11 +115,11 @@ cudaError_t launch_gramrows_build(const GramRows& g, const double* d_pairbuf, in
 }
 
 cudaError_t launch_gram_matvec(const GramRows& g, int J, const int* d_rtile, int nrtile, int maxn2,
-                               const double* d_x, double* d_z, cudaStream_t st) {
+                               const double* d_x, double* d_z, cudaStream_t st, const float2* d_x2, float2* d_z2) {
   if (J == 0) return cudaSuccess;
   const int smem = (int)(sizeof(float2) * (size_t)maxn2);
   cudaError_t e = cudaFuncSetAttribute(gram_rowdot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  gram_rowdot_kernel<<<nrtile, 32 * GRAM_TILE_ROWS, smem, st>>>(g, d_rtile, d_x, d_z);
+  gram_rowdot_kernel<<<nrtile, 32 * GRAM_TILE_ROWS, smem, st>>>(g, d_rtile, d_x, d_x2, d_z, d_z2);
   return cudaGetLastError();
 }

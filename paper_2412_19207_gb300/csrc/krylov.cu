@@ -2,6 +2,7 @@
 // equations, Sec. 3/5), float64.  Reductions are deterministic: each dot
 // product is one block reduction with a fixed summation order.
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace {
 
@@ -64,9 +65,14 @@ __global__ void cg_update_kernel(double a, const double* __restrict__ p, const d
   }
 }
 
-__global__ void scale_copy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-    y[t] = a * x[t];
+// y = a x (and its double-float split into y2 when given)
+__global__ void scale_copy_kernel(double a, const double* __restrict__ x, double* __restrict__ y,
+                                  float2* __restrict__ y2, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a * x[t];
+    y[t] = v;
+    if (y2) y2[t] = df_split(v);
+  }
 }
 
 // x += V^T y for GMRES: x[t] += sum_i y[i] V[i][t]
@@ -126,11 +132,15 @@ __global__ void __launch_bounds__(128) gmres_givens_kernel(GmresDev s, int j, in
   for (int i = t; i <= j; i += blockDim.x) s.H[(int64_t)i * k + j] = hj[i];
 }
 
-// y *= *a (a device scalar)
-__global__ void scale_dev_kernel(double* __restrict__ y, const double* __restrict__ a, int64_t n) {
+// y *= *a (a device scalar), and the double-float split of the result into y2 when given
+__global__ void scale_dev_kernel(double* __restrict__ y, const double* __restrict__ a, float2* __restrict__ y2,
+                                 int64_t n) {
   const double f = *a;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-    y[t] *= f;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double v = y[t] * f;
+    y[t] = v;
+    if (y2) y2[t] = df_split(v);
+  }
 }
 
 // Preconditioned CG steps with the scalars on the device (Hestenes & Stiefel):
@@ -212,8 +222,8 @@ cudaError_t launch_cg_update(double a, const double* p, const double* q, double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, cudaStream_t st) {
-  scale_copy_kernel<<<grid_for(n), 256, 0, st>>>(a, x, y, n);
+cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, cudaStream_t st, float2* y2) {
+  scale_copy_kernel<<<grid_for(n), 256, 0, st>>>(a, x, y, y2, n);
   return cudaGetLastError();
 }
 
@@ -222,8 +232,8 @@ cudaError_t launch_gmres_givens(const GmresDev& s, int j, int k, double mbnorm, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale_dev(double* y, const double* a, int64_t n, cudaStream_t st) {
-  scale_dev_kernel<<<grid_for(n), 256, 0, st>>>(y, a, n);
+cudaError_t launch_scale_dev(double* y, const double* a, int64_t n, cudaStream_t st, float2* y2) {
+  scale_dev_kernel<<<grid_for(n), 256, 0, st>>>(y, a, y2, n);
   return cudaGetLastError();
 }
 
