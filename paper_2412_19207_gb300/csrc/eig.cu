@@ -42,8 +42,12 @@ namespace {
 constexpr int NT = 512;
 constexpr int NW = NT / 32;
 
-__device__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+// n_active: only threads tid < n_active hold non-zero values; warps wholly beyond
+// it skip their shuffle tree (their partial is zero either way, so the sum and
+// its order are unchanged).
+__device__ double block_sum(double v, double* red, int n_active = NT) {
+  if ((threadIdx.x & ~31) < n_active)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
       v[c] = x;
       loc += x * x;
     }
-    const double sig2 = block_sum(loc, red);
+    const double sig2 = block_sum(loc, red, n1);
     const double sigma = sqrt(sig2);
     const double x0 = v[0];
     const double alpha = (x0 >= 0.0) ? -sigma : sigma;
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
         w[j] = s;
         pv = fma(s, v[j], pv);
       }
-      const double K = 0.5 * bt * block_sum(pv, red);
+      const double K = 0.5 * bt * block_sum(pv, red, n1);
       for (int j = tid; j < n1; j += NT) w[j] = fma(-K, v[j], w[j]);
       __syncthreads();
       // A' -= v w^T + w v^T on the lower rows
