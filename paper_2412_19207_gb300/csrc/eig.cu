@@ -499,8 +499,10 @@ __global__ void __launch_bounds__(VT) syev_vectors_kernel(int m, double* __restr
   double* xv = ml + mm;
   const double lam = ev[k];
   // LU of T - lam I with partial pivoting.  A row swap at step i is coded
-  // in the multiplier as -(mult + 4) (|mult| <= 1 either way).
+  // in the multiplier as -(mult + 4) (|mult| <= 1 either way).  u0 keeps the
+  // reciprocal of each pivot: one division per step, and the solves multiply.
   double cd = d[0] - lam, cs = (m > 1) ? e[0] : 0.0;
+#pragma unroll 4
   for (int i = 0; i + 1 < m; ++i) {
     const double sub = e[i];
     const double nd = d[i + 1] - lam, ns = (i + 2 < m) ? e[i + 1] : 0.0;
@@ -508,13 +510,15 @@ __global__ void __launch_bounds__(VT) syev_vectors_kernel(int m, double* __restr
     const bool swap = fabs(sub) > fabs(cd);
     if (!swap) {
       if (fabs(cd) < tolp) cd = (cd < 0.0) ? -tolp : tolp;
-      mult = sub / cd;
-      a0 = cd; a1 = cs; a2 = 0.0;
+      a0 = 1.0 / cd;
+      mult = sub * a0;
+      a1 = cs; a2 = 0.0;
       cd = nd - mult * cs;
       cs = ns;
     } else {
-      mult = cd / sub;
-      a0 = sub; a1 = nd; a2 = ns;
+      a0 = 1.0 / sub;
+      mult = cd * a0;
+      a1 = nd; a2 = ns;
       cd = cs - mult * nd;
       cs = -mult * ns;
     }
@@ -524,9 +528,10 @@ __global__ void __launch_bounds__(VT) syev_vectors_kernel(int m, double* __restr
     ml[(int64_t)i * m] = swap ? -(mult + 4.0) : mult;
   }
   if (fabs(cd) < tolp) cd = (cd < 0.0) ? -tolp : tolp;
-  u0[(int64_t)(m - 1) * m] = cd;
+  u0[(int64_t)(m - 1) * m] = 1.0 / cd;
   for (int i = 0; i < m; ++i) xv[(int64_t)i * m] = start_entry(i, k);
   for (int it = 0; it < 2; ++it) {
+#pragma unroll 4
     for (int i = 0; i + 1 < m; ++i) {      // apply the row swaps and L^{-1}
       double mc = ml[(int64_t)i * m];
       double xi = xv[(int64_t)i * m], xn = xv[(int64_t)(i + 1) * m];
@@ -538,11 +543,12 @@ __global__ void __launch_bounds__(VT) syev_vectors_kernel(int m, double* __restr
       xv[(int64_t)(i + 1) * m] = xn - mc * xi;
     }
     double x1 = 0.0, x2 = 0.0, amax = 0.0;
+#pragma unroll 4
     for (int i = m - 1; i >= 0; --i) {      // U^{-1}
       double s = xv[(int64_t)i * m];
       if (i + 1 < m) s -= u1[(int64_t)i * m] * x1;
       if (i + 2 < m) s -= u2[(int64_t)i * m] * x2;
-      const double xi = s / u0[(int64_t)i * m];
+      const double xi = s * u0[(int64_t)i * m];
       xv[(int64_t)i * m] = xi;
       x2 = x1;
       x1 = xi;
