@@ -232,7 +232,42 @@ def bench_ours(args, rank, world):
                 "h2d_bytes_per_step": int(R.nbytes + b.nbytes), "d2h_bytes_per_step": int(W.numel() * 8)},
         "clocks": clocks,
     }
+    if args.multi_rhs > 0:
+        out["multi_rhs"] = multi_rhs_timing(g, p, R, b, args.multi_rhs)
     return out
+
+
+def multi_rhs_timing(g, p, R, b, k):
+    """AS-preconditioned CG on k right-hand sides of the workload (F scaled by
+    1..k, so every column runs the same iterations): k one-column solves one
+    after another against one lockstep solve of all k (every launch serves all
+    columns).  Both after a warm-up solve; wall time with the device
+    synchronised on both sides (the solves include their host round trips)."""
+    import torch
+    s = g.RannDD(p, R, b)
+    s.assemble()
+    F = s.rhs()
+    s.pca(p.pca_mode, p.pca_thr)
+    s.setup_precond("as")
+    Fs = torch.stack([F * float(c + 1) for c in range(k)])
+    s.solve_cg_as(F, p.rtol, 4000)
+    s.solve_cg_as_multi(Fs[:1].contiguous(), p.rtol, 4000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = []
+    for c in range(k):
+        _, st = s.solve_cg_as(Fs[c].contiguous(), p.rtol, 4000)
+        iters.append(st["iters"])
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, sts = s.solve_cg_as_multi(Fs, p.rtol, 4000)
+    torch.cuda.synchronize()
+    t_multi = time.perf_counter() - t0
+    s.close()
+    return {"nrhs": k, "solver": "AS-CG", "iters": iters[0], "ms_one_at_a_time": round(t_one * 1e3, 3),
+            "ms_lockstep": round(t_multi * 1e3, 3), "ms_per_rhs_lockstep": round(t_multi * 1e3 / k, 3),
+            "speedup": round(t_one / t_multi, 3), "all_converged": all(x["rel_res_true"] <= p.rtol for x in sts)}
 
 
 def cpu_sample(args):
@@ -280,6 +315,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--iters-hint", type=int, default=71)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--multi-rhs", type=int, default=0,
+                    help="also time AS-CG on this many right-hand sides in lockstep against one at a time")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -238,6 +238,25 @@ rann_status rann_dd_precond_apply(rann_dd_handle* h, const double* r_dev, double
  * preconditioner of Sec. 3; equals M^{-1} for AS). */
 rann_status rann_dd_precond_apply_t(rann_dd_handle* h, const double* r_dev, double* z_dev);
 
+/* Many right-hand sides per launch (the batching the weak-scaling runs of
+ * Sec. 5 / Table 2 call for; the operator and the local factors are shared).
+ * Vectors of one call are stored one after another: R_dev, Z_dev [nrhs][DoF],
+ * F_dev [nrhs][N], W_dev [nrhs][DoF], device, caller-owned; stats: nrhs
+ * entries or NULL.
+ * rann_dd_precond_apply_multi: Z_c = M^{-1} R_c for c < nrhs; every column
+ * equals rann_dd_precond_apply of that column.
+ * rann_dd_solve_cg_as_multi: rann_dd_solve_cg_as for every column, in
+ * lockstep: each step reads the local factors and the block rows of H^T H
+ * once for (up to four) columns at a time; every column keeps its own
+ * scalars, convergence flag and refinement decisions, with the arithmetic
+ * of the one-column solve (same iterates while a column is below its own
+ * maxit).  The return value is the first non-OK column status (RANN_OK if
+ * all converged).  With the float64 factors (precision mode 0) or without
+ * the block-row operator the columns are solved one after another. */
+rann_status rann_dd_precond_apply_multi(rann_dd_handle* h, const double* R_dev, double* Z_dev, int nrhs);
+rann_status rann_dd_solve_cg_as_multi(rann_dd_handle* h, const double* F_dev, double* W_dev, int nrhs,
+                                      double rtol, int maxit, rann_dd_stats* stats);
+
 /* Inspection (synchronising copies to host memory).
  * which = 0: Psi_j, 1: H_j (both N_j x m, after assemble, before pca);
  *         2: reduced block B_j = H_j V_{p_j} (N_j x p_j, after pca).

@@ -97,6 +97,8 @@ SIGNATURES = {
     "rann_dd_normal_matvec": (_I, [_P, _P, _P]),
     "rann_dd_precond_apply": (_I, [_P, _P, _P]),
     "rann_dd_precond_apply_t": (_I, [_P, _P, _P]),
+    "rann_dd_precond_apply_multi": (_I, [_P, _P, _P, _I]),
+    "rann_dd_solve_cg_as_multi": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Stats)]),
     "rann_dd_block_info": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_I)]),
     "rann_dd_get_block": (_I, [_P, _I, _I, _P, _P]),
     "rann_dd_get_pca": (_I, [_P, _I, _P, _P]),
@@ -277,6 +279,16 @@ class RannDD:
         _check(s, "rann_dd_solve_cg_as", allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return W, st.as_dict() | {"status": STATUS[s]}
 
+    def solve_cg_as_multi(self, F, rtol=1e-10, maxit=2000, W=None, allow_not_converged=False):
+        """AS-preconditioned CG for the rows of F ([nrhs][N], device float64) in
+        lockstep; returns W [nrhs][DoF] and one stats dict per row."""
+        nrhs = int(F.shape[0])
+        W = W if W is not None else self._empty(nrhs * self.sizes()["dof"]).reshape(nrhs, -1)
+        st = (Stats * max(nrhs, 1))()
+        s = self._lib.rann_dd_solve_cg_as_multi(self._h, _dptr(F), _dptr(W), nrhs, rtol, maxit, st)
+        _check(s, "rann_dd_solve_cg_as_multi", allow=(NOT_CONVERGED,) if allow_not_converged else ())
+        return W, [st[c].as_dict() for c in range(nrhs)]
+
     def solve_gmres_ras(self, F, rtol=1e-10, restart=50, maxit=2000, W=None, allow_not_converged=False):
         W = W if W is not None else self._empty(self.sizes()["dof"])
         st = Stats()
@@ -344,6 +356,13 @@ class RannDD:
         z = z if z is not None else self._empty(self.sizes()["dof"])
         _check(self._lib.rann_dd_precond_apply(self._h, _dptr(r), _dptr(z)), "rann_dd_precond_apply")
         return z
+
+    def precond_apply_multi(self, R, Z=None):
+        """Z[c] = M^{-1} R[c] for the rows of R ([nrhs][DoF], device float64)."""
+        Z = Z if Z is not None else self._empty(R.numel()).reshape(R.shape)
+        _check(self._lib.rann_dd_precond_apply_multi(self._h, _dptr(R), _dptr(Z), int(R.shape[0])),
+               "rann_dd_precond_apply_multi")
+        return Z
 
     def precond_apply_t(self, r, z=None):
         z = z if z is not None else self._empty(self.sizes()["dof"])

@@ -38,6 +38,12 @@ cudaError_t launch_schwarz_gather_df(int nsets, const int* d_set_ptr, const int*
                                      const int* d_inc_ptr, cudaStream_t st);
 int schwarz_apply_rows();
 int schwarz_apply_max_subs();
+cudaError_t launch_schwarz_apply_multi(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
+                                       const int* d_set_sub, const SubDev* d_sub, const double* d_r, int64_t ldr,
+                                       const int64_t* d_p_off32, double* d_part, int64_t pstride,
+                                       const int64_t* d_s_off, double* d_s, int64_t lds, int* d_done, int nrhs,
+                                       const int* d_inc_ptr, const int* d_inc_set, const int* d_inc_pos, int J,
+                                       int ckind, double* d_z, int64_t ldz, cudaStream_t st);
 cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
                                     const int* d_set_sub, const SubDev* d_sub, const double* d_r,
                                     const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
@@ -219,6 +225,8 @@ struct rann_dd_handle {
   int max_set_size = 0;           // most subdomains in one extended set
   double* d_tpart32 = nullptr;
   int* d_adone = nullptr;          // per set: row blocks of the fused apply finished (reset by the last)
+  int64_t p32_total = 0;           // doubles of the fused apply's row-block sums (one right-hand side)
+  int64_t s_total = 0;             // entries of the stacked set vectors s_i (sum of n_i)
   bool prec_df = false;           // the set-up kept only double-float factors
   double* d_Xmats = nullptr;
   float2* d_X2mats = nullptr;
@@ -1179,6 +1187,7 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     std::vector<int64_t> p32(J + 1, 0);
     for (int i = 0; i < J; ++i) p32[i + 1] = p32[i] + (int64_t)((mats[i].n + ar - 1) / ar) * mats[i].n;
     CK(dupload(h, &h->d_p_off32, p32));
+    h->p32_total = p32[J];
     CK(dalloc(h, (void**)&h->d_tpart32, sizeof(double) * (size_t)std::max<int64_t>(p32[J], 1)));
     CK(dalloc(h, (void**)&h->d_adone, sizeof(int) * (size_t)J));
     CK(cudaMemsetAsync(h->d_adone, 0, sizeof(int) * (size_t)J, h->st));
@@ -1201,6 +1210,7 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   CK(dupload(h, &h->d_inc_ptr, inc_ptr)); CK(dupload(h, &h->d_inc_set, inc_set)); CK(dupload(h, &h->d_inc_pos, inc_pos));
   CK(dupload(h, &h->d_s_off, s_off));
   CK(dalloc(h, (void**)&h->d_s, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
+  h->s_total = s_off[J];
   CK(dalloc(h, (void**)&h->d_g, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
   CK(dalloc(h, (void**)&h->d_y, sizeof(double) * (size_t)std::max<int64_t>(s_off[J], 1)));
   CK(dalloc(h, (void**)&h->d_g2, sizeof(float2) * (size_t)std::max<int64_t>(s_off[J], 1)));
@@ -1721,6 +1731,195 @@ extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_de
                                            int maxit, rann_dd_stats* stats) {
   REQUIRE(F_dev, RANN_EINVAL, "null F");
   return solve_cg_impl(h, F_dev, nullptr, W_dev, rtol, maxit, stats);
+}
+
+// ------------------------------------------------ many right-hand sides --
+// The batched path needs the double-float factors with the fused apply and the
+// block-row inner operator (precision mode 1); otherwise the right-hand sides
+// are handled one after another by the one-vector routines.
+static bool multi_batched(rann_dd_handle* h) {
+  return h->prec_df && h->inner_df && h->gram_ready && h->prec_kind != RANN_PREC_NONE &&
+         h->max_set_size <= schwarz_apply_max_subs();
+}
+
+// Z_c = M^{-1} R_c for c < nr (vectors [nr][DoF]); each column equals prec_apply's.
+static rann_status prec_apply_multi(rann_dd_handle* h, const double* R, double* Z, int nr, Workspace& ws) {
+  const int64_t n = h->dof;
+  if (!multi_batched(h)) {
+    for (int c = 0; c < nr; ++c) TRY(prec_apply(h, R + c * n, Z + c * n, h->prec_df));
+    return RANN_OK;
+  }
+  const int64_t stot = std::max<int64_t>(h->s_total, 1);
+  double* sbuf = ws.get((size_t)nr * stot);
+  double* pbuf = ws.get((size_t)4 * std::max<int64_t>(h->p32_total, 1));
+  REQUIRE(sbuf && pbuf, RANN_ENOMEM, "workspace allocation failed");
+  KLA(h, K_SCHWARZ_DF, (nr + 3) / 4 + 1, nr * (4.0 * (h->sum_n2 + h->sum_n) / std::min(nr, 4) + 16.0 * h->sum_n),
+      nr * 2.0 * (h->sum_n2 + h->sum_n),
+      launch_schwarz_apply_multi(h->d_mats, h->nsets, h->maxn, h->d_set_ptr, h->d_set_sub, h->d_sub, R, n,
+                                 h->d_p_off32, pbuf, std::max<int64_t>(h->p32_total, 1), h->d_s_off, sbuf, stot,
+                                 h->d_adone, nr, h->d_inc_ptr, h->d_inc_set, h->d_inc_pos, h->J, h->prec_kind, Z, n,
+                                 h->st));
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_precond_apply_multi(rann_dd_handle* h, const double* R_dev, double* Z_dev, int nrhs) {
+  REQUIRE(h && R_dev && Z_dev && nrhs >= 0, RANN_EINVAL, "null argument or nrhs < 0");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "precond_apply before setup_precond");
+  Workspace ws{h, {}};
+  return prec_apply_multi(h, R_dev, Z_dev, nrhs, ws);
+}
+
+// Preconditioned CG (AS) for nr right-hand sides in lockstep: every launch
+// serves all columns (the factor rows and the block rows of H^T H are read
+// once per step for all of them), each column has its own scalars, done flag
+// and iterative-refinement decisions, with the arithmetic of solve_cg_impl.
+static rann_status solve_cg_multi_impl(rann_dd_handle* h, const double* F_dev, double* W_dev, int nr, double rtol,
+                                       int maxit, rann_dd_stats* stats) {
+  REQUIRE(h && F_dev && W_dev && nr >= 0, RANN_EINVAL, "null argument or nrhs < 0");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve before setup_precond");
+  REQUIRE(h->prec_kind == RANN_PREC_AS || h->prec_kind == RANN_PREC_NONE, RANN_EINVAL,
+          "CG needs a symmetric preconditioner (AS or none)");
+  REQUIRE(rtol > 0 && maxit >= 0, RANN_EINVAL, "bad rtol/maxit");
+  const int64_t n = h->dof, N = h->N;
+  if (nr == 0) return RANN_OK;
+  if (!multi_batched(h)) {                         // one right-hand side after another
+    rann_status worst = RANN_OK;
+    for (int c = 0; c < nr; ++c) {
+      const rann_status st = solve_cg_impl(h, F_dev + c * N, nullptr, W_dev + c * n, rtol, maxit,
+                                           stats ? stats + c : nullptr);
+      if (st != RANN_OK && worst == RANN_OK) worst = st;
+    }
+    return worst;
+  }
+  Workspace ws{h, {}};
+  const size_t nv = (size_t)nr * n;
+  double *b = ws.get(nv), *r = ws.get(nv), *z = ws.get(nv), *p = ws.get(nv), *q = ws.get(nv);
+  double* sc = ws.get((size_t)8 * nr + 8);
+  REQUIRE(b && r && z && p && q && sc, RANN_ENOMEM, "workspace allocation failed");
+  CgMulti sd{};
+  sd.pq = sc; sd.rr = sc + nr; sd.rz = sc + 2 * nr; sd.rel = sc + 4 * nr;
+  double* d_bnorm = sc + 5 * nr;
+  sd.bnorm = d_bnorm;
+  sd.done = reinterpret_cast<int*>(sc + 6 * nr);    // nr ints
+  sd.it = reinterpret_cast<int*>(sc + 7 * nr);      // nr ints
+  sd.nr = nr;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, h->st));
+  for (int c = 0; c < nr; ++c) TRY(rann_dd_matvec_t(h, F_dev + c * N, b + c * n));
+  CK(cudaMemsetAsync(W_dev, 0, sizeof(double) * nv, h->st));
+  CK(cudaMemcpyAsync(r, b, sizeof(double) * nv, cudaMemcpyDeviceToDevice, h->st));
+  std::vector<double> bb(nr), bn(nr), rel(nr, 1.0), true_rel(nr, 1.0), hrr(nr);
+  std::vector<int> it(nr, 0), active(nr, 1), hd(nr), hit(nr);
+  std::vector<rann_status> st(nr, RANN_NOT_CONVERGED);
+  KLA(h, K_DOT, 1, 16.0 * nv, 2.0 * nv, launch_dot_multi(b, n, b, n, n, nr, sd.rr, h->st));
+  CK(cudaMemcpyAsync(bb.data(), sd.rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->st));
+  CK(stream_sync(h));
+  for (int c = 0; c < nr; ++c) {
+    bn[c] = std::sqrt(bb[c]);
+    if (!(bn[c] > 0.0)) {
+      st[c] = std::isfinite(bb[c]) ? RANN_OK : RANN_BREAKDOWN;
+      rel[c] = true_rel[c] = 0.0;
+      active[c] = 0;
+    }
+  }
+  CK(cudaMemcpyAsync(d_bnorm, bn.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, h->st));
+  struct Events {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~Events() { for (auto x : e) if (x) cudaEventDestroy(x); }
+  } evh;
+  for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&evh.e[i], cudaEventDisableTiming));
+  int* hdone = reinterpret_cast<int*>(h->h_scal + 128);        // pinned: nr flags (host side)
+  std::vector<int> hdv(nr);
+  auto any_active = [&]() { for (int c = 0; c < nr; ++c) if (active[c]) return true; return false; };
+  for (int cycle = 0; cycle < 30 && any_active(); ++cycle) {
+    TRY(prec_apply_multi(h, r, z, nr, ws));
+    CK(cudaMemcpyAsync(p, z, sizeof(double) * nv, cudaMemcpyDeviceToDevice, h->st));
+    KLA(h, K_DOT, 1, 16.0 * nv, 2.0 * nv, launch_dot_multi(r, n, z, n, n, nr, sd.rz, h->st));
+    for (int c = 0; c < nr; ++c) hd[c] = active[c] ? 0 : 1;
+    CK(cudaMemcpyAsync(sd.done, hd.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemsetAsync(sd.it, 0, sizeof(int) * nr, h->st));
+    int kmax = 0;
+    for (int c = 0; c < nr; ++c) if (active[c]) kmax = std::max(kmax, maxit - it[c]);
+    bool all_done = false;
+    int ph = 0;
+    for (int i = 0; i < kmax; ++i) {
+      if (i >= 2) {
+        CK(cudaEventSynchronize(evh.e[(i - 2) % 3]));
+        if (*(volatile int*)hdone) break;
+      }
+      KLA(h, K_GRAMOP, 1, 8.0 * (h->gram_entries + nv), 2.0 * h->gram_entries * nr,
+          launch_gram_matvec_multi(h->gram, h->J, h->d_gtile, h->ngtile, h->gram_maxn2, p, n, q, n, nr, h->st));
+      KLA(h, K_DOT, 1, 16.0 * nv, 2.0 * nv, launch_dot_multi(p, n, q, n, n, nr, sd.pq, h->st));
+      KLA(h, K_VEC, 1, 40.0 * nv, 4.0 * nv, launch_cg_update_multi(p, q, W_dev, r, n, n, sd, ph, h->st));
+      KLA(h, K_DOT, 1, 8.0 * nv, 2.0 * nv, launch_dot_multi(r, n, r, n, n, nr, sd.rr, h->st));
+      KLA(h, K_VEC, 1, 0, 0, launch_cg_check_multi(sd, rtol, h->st));
+      TRY(prec_apply_multi(h, r, z, nr, ws));
+      KLA(h, K_DOT, 1, 16.0 * nv, 2.0 * nv, launch_dot_multi(r, n, z, n, n, nr, sd.rz + (ph ^ 1) * nr, h->st));
+      KLA(h, K_VEC, 1, 24.0 * nv, 3.0 * nv, launch_cg_direction_multi(z, p, n, n, sd, ph, h->st));
+      ph ^= 1;
+      KLA(h, K_VEC, 1, 0, 0, launch_all_done(sd.done, nr, h->d_scal + 64, h->st));
+      CK(cudaMemcpyAsync(hdone, h->d_scal + 64, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaEventRecord(evh.e[i % 3], h->st));
+    }
+    (void)all_done;
+    CK(cudaMemcpyAsync(hdv.data(), sd.done, sizeof(int) * nr, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(hit.data(), sd.it, sizeof(int) * nr, cudaMemcpyDeviceToHost, h->st));
+    std::vector<double> hrel(nr);
+    CK(cudaMemcpyAsync(hrel.data(), sd.rel, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->st));
+    CK(stream_sync(h));
+    std::vector<int> inner_ok(nr, 0);
+    for (int c = 0; c < nr; ++c) {
+      if (!active[c]) continue;
+      it[c] += hit[c];
+      rel[c] = hrel[c];
+      inner_ok[c] = hdv[c] == 1;
+      if (hdv[c] == 2) { st[c] = RANN_BREAKDOWN; active[c] = 0; }
+    }
+    // float64 residual of each accumulated W_c
+    for (int c = 0; c < nr; ++c) {
+      if (!active[c]) continue;
+      TRY(rann_dd_normal_matvec(h, W_dev + c * n, q + c * n));
+      CK(cudaMemcpyAsync(r + c * n, b + c * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+      KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(-1.0, q + c * n, 1.0, r + c * n, n, h->st));
+    }
+    KLA(h, K_DOT, 1, 8.0 * nv, 2.0 * nv, launch_dot_multi(r, n, r, n, n, nr, sd.rr, h->st));
+    CK(cudaMemcpyAsync(hrr.data(), sd.rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->st));
+    CK(stream_sync(h));
+    for (int c = 0; c < nr; ++c) {
+      if (!active[c]) continue;
+      const double prev = true_rel[c];
+      true_rel[c] = std::sqrt(hrr[c]) / bn[c];
+      if (!std::isfinite(true_rel[c])) { st[c] = RANN_BREAKDOWN; active[c] = 0; continue; }
+      if (true_rel[c] <= rtol) { st[c] = RANN_OK; active[c] = 0; continue; }
+      if (!inner_ok[c] || it[c] >= maxit) { active[c] = 0; continue; }
+      if (true_rel[c] >= prev) active[c] = 0;    // refinement no longer reduces the float64 residual
+    }
+  }
+  CK(cudaEventRecord(e1, h->st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  rann_status worst = RANN_OK;
+  for (int c = 0; c < nr; ++c) {
+    if (stats) {
+      stats[c].iters = it[c];
+      stats[c].rel_res_true = true_rel[c];
+      stats[c].rel_res_rec = rel[c];
+      stats[c].rel_res_prec = -1.0;
+      stats[c].ms_solve = ms;
+      stats[c].n_shifted = h->n_shifted;
+    }
+    if (st[c] != RANN_OK && worst == RANN_OK) worst = st[c];
+  }
+  if (worst == RANN_NOT_CONVERGED) rann_set_error("CG (many right-hand sides) reached maxit=%d", maxit);
+  return worst;
+}
+
+extern "C" rann_status rann_dd_solve_cg_as_multi(rann_dd_handle* h, const double* F_dev, double* W_dev, int nrhs,
+                                                 double rtol, int maxit, rann_dd_stats* stats) {
+  return solve_cg_multi_impl(h, F_dev, W_dev, nrhs, rtol, maxit, stats);
 }
 
 extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,

@@ -900,6 +900,195 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
   if (tid == 0) done[i] = 0;                           // ready for the next apply (stream order)
 }
 
+// schwarz_apply_df_kernel for NR right-hand sides r_c = r + c ldr (c < NR) with
+// unit input weights and the plain combine (s_c = s + c lds, row-block sums in
+// part + c pstride): each row of X_i is read once for all of them; per
+// right-hand side the same chains in the same order, so every column is
+// bit-identical to the one-vector apply.
+template <int NR>
+__global__ void __launch_bounds__(ANT, 2) schwarz_apply_multi_kernel(
+    const CholMat* __restrict__ mats, const int* __restrict__ set_ptr, const int* __restrict__ set_sub,
+    const SubDev* __restrict__ subs, const double* __restrict__ r, int64_t ldr, const int64_t* __restrict__ p_off32,
+    double* __restrict__ part, int64_t pstride, const int64_t* __restrict__ s_off, double* __restrict__ s,
+    int64_t lds, int* __restrict__ done) {
+  extern __shared__ float4 gsm[];                      // [NR][np]
+  __shared__ float4 ysm[NR][AR / 2];
+  __shared__ int seg_c[AMAX_SUB + 1], seg_p[AMAX_SUB];
+  __shared__ int64_t seg_w[AMAX_SUB];
+  __shared__ int last;
+  const int i = blockIdx.y;
+  const CholMat M = mats[i];
+  const int nb = (M.n + AR - 1) / AR;
+  if ((int)blockIdx.x >= nb) return;
+  const int rb = nb - 1 - (int)blockIdx.x;
+  const int r0 = rb * AR;
+  const int r1 = min(M.n, r0 + AR);
+  const int nr = r1 - r0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q0 = set_ptr[i], nq = set_ptr[i + 1] - q0;
+  if (tid < nq) {
+    const int k = set_sub[q0 + tid];
+    seg_p[tid] = subs[k].p;
+    seg_w[tid] = subs[k].woff;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int c = 0;
+    for (int q = 0; q < nq; ++q) { seg_c[q] = c; c += seg_p[q]; }
+    seg_c[nq] = c;
+  }
+  __syncthreads();
+  const int np = (r1 + 1) >> 1;
+  const int npmax = (M.n + 1) >> 1;                    // row stride of gsm (fits the dynamic allocation)
+  for (int c2 = tid; c2 < np; c2 += ANT) {
+#pragma unroll
+    for (int rc = 0; rc < NR; ++rc) {
+      float2 v[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int c = 2 * c2 + e;
+        v[e] = make_float2(0.f, 0.f);
+        if (c < r1) {
+          int q = 0;
+          while (q + 1 < nq && seg_c[q + 1] <= c) ++q;
+          v[e] = df_split(1.0 * r[rc * ldr + seg_w[q] + (c - seg_c[q])]);
+        }
+      }
+      gsm[rc * npmax + c2] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    }
+  }
+  if (tid < AR / 2)
+#pragma unroll
+    for (int rc = 0; rc < NR; ++rc) ysm[rc][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  const int ldq = M.ld >> 1;
+  for (int rr = warp; rr < nr; rr += ANT / 32) {
+    const int row = r0 + rr;
+    const float4* xr = reinterpret_cast<const float4*>(M.X2 + (int64_t)row * M.ld);
+    const int nfull = (row + 1) >> 1, nall = (row >> 1) + 1;
+    float h[NR][4], l[NR][4];
+#pragma unroll
+    for (int rc = 0; rc < NR; ++rc)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) { h[rc][t] = 0.f; l[rc][t] = 0.f; }
+    constexpr int U = 4;
+    int c2 = lane;
+    for (; c2 + 32 * (U - 1) < nfull; c2 += 32 * U) {
+      float4 a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) a[u] = xr[c2 + 32 * u];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int rc = 0; rc < NR; ++rc)
+          df_mac2(h[rc][(2 * u) & 3], l[rc][(2 * u) & 3], h[rc][(2 * u + 1) & 3], l[rc][(2 * u + 1) & 3], a[u],
+                  gsm[rc * npmax + c2 + 32 * u]);
+    }
+    if (c2 < nall) {
+      float4 a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int pc = c2 + 32 * u;
+        a[u] = (pc < nall) ? xr[pc] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (2 * pc + 1 > row) { a[u].z = 0.f; a[u].w = 0.f; }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c2 + 32 * u < nall)
+#pragma unroll
+          for (int rc = 0; rc < NR; ++rc)
+            df_mac2(h[rc][(2 * u) & 3], l[rc][(2 * u) & 3], h[rc][(2 * u + 1) & 3], l[rc][(2 * u + 1) & 3], a[u],
+                    gsm[rc * npmax + c2 + 32 * u]);
+    }
+#pragma unroll
+    for (int rc = 0; rc < NR; ++rc) {
+      df_add(h[rc][0], l[rc][0], h[rc][1], l[rc][1]);
+      df_add(h[rc][2], l[rc][2], h[rc][3], l[rc][3]);
+      df_add(h[rc][0], l[rc][0], h[rc][2], l[rc][2]);
+      df_warp_sum(h[rc][0], l[rc][0]);
+      if (lane == 0) reinterpret_cast<float2*>(ysm[rc])[rr] = make_float2(h[rc][0], l[rc][0]);
+    }
+  }
+  __syncthreads();
+  for (int c2 = tid; c2 < np; c2 += ANT) {
+    const int c = 2 * c2;
+    const float4* xc = reinterpret_cast<const float4*>(M.X2 + (int64_t)r0 * M.ld + c);
+    float acc[NR][8];
+#pragma unroll
+    for (int rc = 0; rc < NR; ++rc)
+#pragma unroll
+      for (int t = 0; t < 8; ++t) acc[rc][t] = 0.f;
+    const bool fast = (nr == AR && c + 1 < r0);
+    for (int q = 0; q < nr; q += 4) {
+      float4 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int row = r0 + q + u;
+        if (fast) {
+          a[u] = xc[(q + u) * ldq];
+        } else {
+          a[u] = (q + u < nr && row >= c) ? xc[(q + u) * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row < c + 1) { a[u].z = 0.f; a[u].w = 0.f; }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u += 2)
+#pragma unroll
+        for (int rc = 0; rc < NR; ++rc) {
+          const float4 y = ysm[rc][(q + u) >> 1];
+          df_mac2(acc[rc][0], acc[rc][1], acc[rc][2], acc[rc][3], a[u], make_float4(y.x, y.y, y.x, y.y));
+          df_mac2(acc[rc][4], acc[rc][5], acc[rc][6], acc[rc][7], a[u + 1], make_float4(y.z, y.w, y.z, y.w));
+        }
+    }
+#pragma unroll
+    for (int rc = 0; rc < NR; ++rc) {
+      df_add(acc[rc][0], acc[rc][1], acc[rc][4], acc[rc][5]);
+      df_add(acc[rc][2], acc[rc][3], acc[rc][6], acc[rc][7]);
+      double* pr = part + rc * pstride + p_off32[i] + (int64_t)rb * M.n;
+      pr[c] = df_to_double(acc[rc][0], acc[rc][1]);
+      if (c + 1 < r1) pr[c + 1] = df_to_double(acc[rc][2], acc[rc][3]);
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(&done[i], 1) == nb - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int c = tid; c < M.n; c += ANT)
+#pragma unroll
+    for (int rc = 0; rc < NR; ++rc) {
+      double a = 0.0;
+      for (int b = c / AR; b < nb; ++b) a += __ldcg(part + rc * pstride + p_off32[i] + (int64_t)b * M.n + c);
+      s[rc * lds + s_off[i] + c] = a;
+    }
+  if (tid == 0) done[i] = 0;
+}
+
+// schwarz_combine_kernel for column blockIdx.y (s_c = s_all + c lds, z_c = z + c ldz)
+__global__ void schwarz_combine_multi_kernel(const SubDev* __restrict__ subs, const int* __restrict__ inc_ptr,
+                                             const int* __restrict__ inc_set, const int* __restrict__ inc_pos,
+                                             const int64_t* __restrict__ s_off, const double* __restrict__ s_all,
+                                             int64_t lds, int kind, double* __restrict__ z, int64_t ldz) {
+  const int k = blockIdx.x, col = blockIdx.y;
+  const SubDev& S = subs[k];
+  const int q0 = inc_ptr[k], nq = min(inc_ptr[k + 1] - q0, 64);
+  __shared__ int64_t base[64];
+  if ((int)threadIdx.x < nq) {
+    const int i = inc_set[q0 + threadIdx.x];
+    base[threadIdx.x] = (kind == RANN_PREC_RAS && i != k) ? -1 : s_off[i] + inc_pos[q0 + threadIdx.x];
+  }
+  __syncthreads();
+  const double scale = (kind == RANN_PREC_SAS) ? 1.0 / (double)(inc_ptr[k + 1] - q0) : 1.0;
+  const double* sc = s_all + col * lds;
+  for (int c = threadIdx.x; c < S.p; c += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < nq; ++q)
+      if (base[q] >= 0) acc += sc[base[q] + c];
+    z[col * ldz + S.woff + c] = acc * scale;
+  }
+}
+
 // X2 = split(X) on the lower triangles.
 __global__ void split_lower_kernel(const CholMat* __restrict__ mats) {
   const CholMat M = mats[blockIdx.y];
@@ -1024,6 +1213,46 @@ cudaError_t launch_schwarz_combine(const SubDev* d_sub, int J, const int* d_inc_
   if (J == 0) return cudaSuccess;
   schwarz_combine_kernel<<<J, 256, 0, st>>>(d_sub, J, d_inc_ptr, d_inc_set, d_inc_pos, d_s_off, d_s,
                                              kind, d_z);
+  return cudaGetLastError();
+}
+
+template <int NR>
+static cudaError_t apply_multi_launch(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
+                                      const int* d_set_sub, const SubDev* d_sub, const double* d_r, int64_t ldr,
+                                      const int64_t* d_p_off32, double* d_part, int64_t pstride,
+                                      const int64_t* d_s_off, double* d_s, int64_t lds, int* d_done, cudaStream_t st) {
+  const int smem = (int)(sizeof(float4) * (size_t)((maxn + 1) / 2) * NR);
+  cudaError_t e = cudaFuncSetAttribute(schwarz_apply_multi_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+  if (e != cudaSuccess) return e;
+  schwarz_apply_multi_kernel<NR><<<dim3((maxn + AR - 1) / AR, nsets), ANT, smem, st>>>(
+      d_mats, d_set_ptr, d_set_sub, d_sub, d_r, ldr, d_p_off32, d_part, pstride, d_s_off, d_s, lds, d_done);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schwarz_apply_multi(const CholMat* d_mats, int nsets, int maxn, const int* d_set_ptr,
+                                       const int* d_set_sub, const SubDev* d_sub, const double* d_r, int64_t ldr,
+                                       const int64_t* d_p_off32, double* d_part, int64_t pstride,
+                                       const int64_t* d_s_off, double* d_s, int64_t lds, int* d_done, int nrhs,
+                                       const int* d_inc_ptr, const int* d_inc_set, const int* d_inc_pos, int J,
+                                       int ckind, double* d_z, int64_t ldz, cudaStream_t st) {
+  if (nsets == 0 || nrhs == 0) return cudaSuccess;
+  for (int c0 = 0; c0 < nrhs; c0 += 4) {              // four right-hand sides per launch
+    const int k = nrhs - c0 < 4 ? nrhs - c0 : 4;
+    const double* r = d_r + c0 * ldr;
+    double* s = d_s + c0 * lds;
+    cudaError_t e = k == 4 ? apply_multi_launch<4>(d_mats, nsets, maxn, d_set_ptr, d_set_sub, d_sub, r, ldr, d_p_off32,
+                                                   d_part, pstride, d_s_off, s, lds, d_done, st)
+                  : k == 3 ? apply_multi_launch<3>(d_mats, nsets, maxn, d_set_ptr, d_set_sub, d_sub, r, ldr, d_p_off32,
+                                                   d_part, pstride, d_s_off, s, lds, d_done, st)
+                  : k == 2 ? apply_multi_launch<2>(d_mats, nsets, maxn, d_set_ptr, d_set_sub, d_sub, r, ldr, d_p_off32,
+                                                   d_part, pstride, d_s_off, s, lds, d_done, st)
+                           : apply_multi_launch<1>(d_mats, nsets, maxn, d_set_ptr, d_set_sub, d_sub, r, ldr, d_p_off32,
+                                                   d_part, pstride, d_s_off, s, lds, d_done, st);
+    if (e != cudaSuccess) return e;
+  }
+  schwarz_combine_multi_kernel<<<dim3(J, nrhs), 256, 0, st>>>(d_sub, d_inc_ptr, d_inc_set, d_inc_pos, d_s_off, d_s,
+                                                              lds, ckind, d_z, ldz);
   return cudaGetLastError();
 }
 

@@ -140,6 +140,26 @@ cudaError_t launch_cg_update_dev(const double* p, const double* q, double* x, do
                                  int ph, cudaStream_t st);
 cudaError_t launch_cg_check(const CgDev& s, double bnorm, double rtol, cudaStream_t st);
 cudaError_t launch_cg_direction(const double* z, double* p, int64_t n, const CgDev& s, int ph, cudaStream_t st);
+// many right-hand sides in lockstep: one scalar set per column c < nr
+struct CgMulti {
+  double* pq;                // [nr]
+  double* rr;                // [nr]
+  double* rz;                // [2][nr]
+  double* rel;               // [nr]
+  int* done;                 // [nr] 0 running, 1 converged, 2 breakdown
+  int* it;                   // [nr] updates made
+  const double* bnorm;       // [nr] ||b_c||
+  int nr;
+};
+cudaError_t launch_dot_multi(const double* x, int64_t ldx, const double* y, int64_t ldy, int64_t n, int nr,
+                             double* d_out, cudaStream_t st);
+cudaError_t launch_cg_update_multi(const double* p, const double* q, double* x, double* r, int64_t n, int64_t ld,
+                                   const CgMulti& s, int ph, cudaStream_t st);
+cudaError_t launch_cg_check_multi(const CgMulti& s, double rtol, cudaStream_t st);
+cudaError_t launch_cg_direction_multi(const double* z, double* p, int64_t n, int64_t ld, const CgMulti& s, int ph,
+                                      cudaStream_t st);
+// *(int*)d_out = 1 when done[c] != 0 for every c < nr
+cudaError_t launch_all_done(const int* d_done, int nr, double* d_out, cudaStream_t st);
 // y *= *a; y2 (optional): the double-float split of the result
 cudaError_t launch_scale_dev(double* y, const double* a, int64_t n, cudaStream_t st, float2* y2 = nullptr);
 
@@ -166,6 +186,11 @@ cudaError_t launch_gramrows_build(const GramRows& g, const double* d_pairbuf, in
 cudaError_t launch_gram_matvec(const GramRows& g, int J, const int* d_rtile, int nrtile, int maxn2,
                                const double* d_x, double* d_z, cudaStream_t st, const float2* d_x2 = nullptr,
                                float2* d_z2 = nullptr);
+// the same for nr right-hand sides x_c = d_x + c ldx -> z_c = d_z + c ldz (each column
+// bit-identical to launch_gram_matvec of that column)
+cudaError_t launch_gram_matvec_multi(const GramRows& g, int J, const int* d_rtile, int nrtile, int maxn2,
+                                     const double* d_x, int64_t ldx, double* d_z, int64_t ldz, int nr,
+                                     cudaStream_t st);
 
 // eig.cu -- batched symmetric eigen-decomposition (float64)
 // Eigenpairs of `batch` m x m symmetric matrices A; ranks by the PCA rule (mode, thr);

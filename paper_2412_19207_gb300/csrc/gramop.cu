@@ -99,6 +99,72 @@ __global__ void __launch_bounds__(256) gram_rowdot_kernel(const GramRows g, cons
   }
 }
 
+// gram_rowdot_kernel for NR right-hand sides x_c = x + c ldx (c < NR): each row
+// of R_k is read once for all of them; per right-hand side the same chains in
+// the same order as the one-vector kernel, so every column is bit-identical
+// to a one-vector product.
+template <int NR>
+__global__ void __launch_bounds__(256) gram_rowdot_multi_kernel(const GramRows g, const int* __restrict__ rtile,
+                                                                const double* __restrict__ x, int64_t ldx,
+                                                                double* __restrict__ z, int64_t ldz) {
+  extern __shared__ float4 xsm[];                 // [NR][n4]
+  __shared__ int seg_c4[GRAM_MAX_NBR + 1], seg_p[GRAM_MAX_NBR];
+  __shared__ int64_t seg_w[GRAM_MAX_NBR];
+  const int k = rtile[2 * blockIdx.x], c0 = rtile[2 * blockIdx.x + 1];
+  const int p = g.p[k], n4 = g.n2[k] >> 1;
+  const int q0 = g.nbr_ptr[k], nq = g.nbr_ptr[k + 1] - q0;
+  if (threadIdx.x < nq) {
+    const int l = g.nbr_l[q0 + threadIdx.x];
+    seg_c4[threadIdx.x] = g.nbr_col[q0 + threadIdx.x] >> 1;
+    seg_p[threadIdx.x] = g.p[l];
+    seg_w[threadIdx.x] = g.woff[l];
+  }
+  if (threadIdx.x == 0) seg_c4[nq] = n4;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+    int q = 0;
+    while (q + 1 < nq && seg_c4[q + 1] <= i) ++q;
+    const int e = 2 * (i - seg_c4[q]);
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const double* xl = x + c * ldx + seg_w[q];
+      const float2 a = df_split(xl[e]);
+      const float2 b = (e + 1 < seg_p[q]) ? df_split(xl[e + 1]) : make_float2(0.f, 0.f);
+      xsm[c * n4 + i] = make_float4(a.x, a.y, b.x, b.y);
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rr = c0 + warp;
+  if (rr >= min(c0 + GRAM_TILE_ROWS, p)) return;
+  const float4* row = reinterpret_cast<const float4*>(g.R2 + g.roff[k] + (int64_t)rr * g.n2[k]);
+  float h0[NR], l0[NR], h1[NR], l1[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) { h0[c] = 0.f; l0[c] = 0.f; h1[c] = 0.f; l1[c] = 0.f; }
+  constexpr int U = 8;
+  for (int i0 = lane; i0 < n4; i0 += 32 * U) {
+    float4 a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = (i0 + 32 * u < n4) ? row[i0 + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (i0 + 32 * u >= n4) break;
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        const float4 xv = xsm[c * n4 + i0 + 32 * u];
+        df_mac(h0[c], l0[c], make_float2(a[u].x, a[u].y), make_float2(xv.x, xv.y));
+        df_mac(h1[c], l1[c], make_float2(a[u].z, a[u].w), make_float2(xv.z, xv.w));
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NR; ++c) {
+    df_add(h0[c], l0[c], h1[c], l1[c]);
+    df_warp_sum(h0[c], l0[c]);
+    if (lane == 0) z[c * ldz + g.woff[k] + rr] = df_to_double(h0[c], l0[c]);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_gramrows_build(const GramRows& g, const double* d_pairbuf, int J, int maxp, int maxn2,
@@ -122,4 +188,31 @@ cudaError_t launch_gram_matvec(const GramRows& g, int J, const int* d_rtile, int
   if (e != cudaSuccess) return e;
   gram_rowdot_kernel<<<nrtile, 32 * GRAM_TILE_ROWS, smem, st>>>(g, d_rtile, d_x, d_x2, d_z, d_z2);
   return cudaGetLastError();
+}
+
+template <int NR>
+static cudaError_t gram_multi_launch(const GramRows& g, const int* d_rtile, int nrtile, int maxn2, const double* d_x,
+                                     int64_t ldx, double* d_z, int64_t ldz, cudaStream_t st) {
+  const int smem = (int)(sizeof(float2) * (size_t)maxn2 * NR);
+  cudaError_t e = cudaFuncSetAttribute(gram_rowdot_multi_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  gram_rowdot_multi_kernel<NR><<<nrtile, 32 * GRAM_TILE_ROWS, smem, st>>>(g, d_rtile, d_x, ldx, d_z, ldz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_matvec_multi(const GramRows& g, int J, const int* d_rtile, int nrtile, int maxn2,
+                                     const double* d_x, int64_t ldx, double* d_z, int64_t ldz, int nr,
+                                     cudaStream_t st) {
+  if (J == 0) return cudaSuccess;
+  for (int c0 = 0; c0 < nr; c0 += 4) {            // four right-hand sides per launch
+    const int k = std::min(4, nr - c0);
+    const double* x = d_x + c0 * ldx;
+    double* z = d_z + c0 * ldz;
+    cudaError_t e = k == 4 ? gram_multi_launch<4>(g, d_rtile, nrtile, maxn2, x, ldx, z, ldz, st)
+                  : k == 3 ? gram_multi_launch<3>(g, d_rtile, nrtile, maxn2, x, ldx, z, ldz, st)
+                  : k == 2 ? gram_multi_launch<2>(g, d_rtile, nrtile, maxn2, x, ldx, z, ldz, st)
+                           : gram_multi_launch<1>(g, d_rtile, nrtile, maxn2, x, ldx, z, ldz, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }

@@ -180,6 +180,70 @@ __global__ void cg_direction_kernel(const double* __restrict__ z, double* __rest
     p[t] = fma(beta, p[t], z[t]);
 }
 
+// ---- many right-hand sides in lockstep (vectors [nr][ld], one scalar set per column) ----
+// out[c] = x_c . y_c: the same block reduction as multidot_rows, one block per column
+__global__ void __launch_bounds__(RT) dot_multi_kernel(const double* __restrict__ x, int64_t ldx,
+                                                       const double* __restrict__ y, int64_t ldy, int64_t n,
+                                                       double* __restrict__ out) {
+  const double* v = x + blockIdx.x * ldx;
+  const double* w = y + blockIdx.x * ldy;
+  double s0 = 0.0, s1 = 0.0;
+  int64_t t = threadIdx.x;
+  for (; t + RT < n; t += 2 * RT) { s0 = fma(v[t], w[t], s0); s1 = fma(v[t + RT], w[t + RT], s1); }
+  if (t < n) s0 = fma(v[t], w[t], s0);
+  const double s = block_sum(s0 + s1);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// cg_update_dev_kernel for column blockIdx.y
+__global__ void cg_update_multi_kernel(const double* __restrict__ p, const double* __restrict__ q,
+                                       double* __restrict__ x, double* __restrict__ r, int64_t n, int64_t ld,
+                                       CgMulti s, int ph) {
+  const int c = blockIdx.y;
+  if (s.done[c]) return;
+  const double pq = s.pq[c], rz = s.rz[ph * s.nr + c];
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.done[c] = 2;
+    return;
+  }
+  const double alpha = rz / pq;
+  const int64_t o = c * ld;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    x[o + t] = fma(alpha, p[o + t], x[o + t]);
+    r[o + t] = fma(-alpha, q[o + t], r[o + t]);
+  }
+}
+
+// cg_check_kernel for every column (thread per column)
+__global__ void cg_check_multi_kernel(CgMulti s, double rtol) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= s.nr || s.done[c]) return;
+  const double rel = sqrt(s.rr[c]) / s.bnorm[c];
+  s.rel[c] = rel;
+  s.it[c] += 1;
+  if (!isfinite(rel)) s.done[c] = 2;
+  else if (rel <= rtol) s.done[c] = 1;
+}
+
+// cg_direction_kernel for column blockIdx.y
+__global__ void cg_direction_multi_kernel(const double* __restrict__ z, double* __restrict__ p, int64_t n, int64_t ld,
+                                          CgMulti s, int ph) {
+  const int c = blockIdx.y;
+  if (s.done[c]) return;
+  const double beta = s.rz[(ph ^ 1) * s.nr + c] / s.rz[ph * s.nr + c];
+  const int64_t o = c * ld;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    p[o + t] = fma(beta, p[o + t], z[o + t]);
+}
+
+// *out = 1 when every column is done (one warp)
+__global__ void all_done_kernel(const int* __restrict__ done, int nr, int* __restrict__ out) {
+  int all = 1;
+  for (int c = threadIdx.x; c < nr; c += 32) all &= (done[c] != 0);
+  all = __all_sync(0xffffffffu, all);
+  if (threadIdx.x == 0) *out = all;
+}
+
 inline unsigned grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   return (unsigned)(g > 1216 ? 1216 : (g < 1 ? 1 : g));
@@ -208,6 +272,35 @@ cudaError_t launch_sub_combination(const double* V, int64_t ldv, int nv, const d
 cudaError_t launch_add_combination(const double* V, int64_t ldv, int nv, const double* d_y, double* x,
                                    int64_t n, cudaStream_t st) {
   add_combination<<<grid_for(n), 256, 0, st>>>(V, ldv, nv, d_y, x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_multi(const double* x, int64_t ldx, const double* y, int64_t ldy, int64_t n, int nr,
+                             double* d_out, cudaStream_t st) {
+  if (nr <= 0) return cudaSuccess;
+  dot_multi_kernel<<<nr, RT, 0, st>>>(x, ldx, y, ldy, n, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update_multi(const double* p, const double* q, double* x, double* r, int64_t n, int64_t ld,
+                                   const CgMulti& s, int ph, cudaStream_t st) {
+  cg_update_multi_kernel<<<dim3(grid_for(n), s.nr), 256, 0, st>>>(p, q, x, r, n, ld, s, ph);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_check_multi(const CgMulti& s, double rtol, cudaStream_t st) {
+  cg_check_multi_kernel<<<(s.nr + 127) / 128, 128, 0, st>>>(s, rtol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_direction_multi(const double* z, double* p, int64_t n, int64_t ld, const CgMulti& s, int ph,
+                                      cudaStream_t st) {
+  cg_direction_multi_kernel<<<dim3(grid_for(n), s.nr), 256, 0, st>>>(z, p, n, ld, s, ph);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_all_done(const int* d_done, int nr, double* d_out, cudaStream_t st) {
+  all_done_kernel<<<1, 32, 0, st>>>(d_done, nr, reinterpret_cast<int*>(d_out));
   return cudaGetLastError();
 }
 
