@@ -343,60 +343,89 @@ cudaError_t launch_tridiag(double* A, int m, int batch, double* work, int64_t ws
   return cudaLaunchKernelEx(&cfg, syev_tridiag_kernel<SL>, A, m, work, ws, use_dp);
 }
 
-// ---- 2. eigenvalues, grid (matrix, part of the spectrum) ----
-constexpr int VT = 128;        // threads (eigenvalues) per block of the bisection
-__global__ void __launch_bounds__(VT) syev_values_kernel(int m, double* __restrict__ work_all, int64_t work_stride,
-                                                         double* __restrict__ wall, int* __restrict__ info,
-                                                         int bisect) {
-  extern __shared__ double sm[];
+// ---- 2. eigenvalues ----
+// Bisection: one thread per eigenvalue over the whole batch, flattened
+// ((matrix, k) pairs in order, BT per block), so the grid is a single wave
+// with at most BT threads on any SM (the float64 counts keep the SM's
+// float64 pipe busy, so an SM holding two blocks would take twice as long);
+// a block stages the scaled T of every matrix its range touches.
+constexpr int BT = 128;        // eigenvalues per block of the bisection
+__host__ __device__ inline int bisect_mats_per_block(int m) { return (BT - 1) / m + 2; }
+
+__global__ void __launch_bounds__(BT) syev_bisect_kernel(int m, int batch, double* __restrict__ work_all,
+                                                         int64_t work_stride, double* __restrict__ wall,
+                                                         int* __restrict__ info) {
+  extern __shared__ double sm[];   // per matrix: ds[m], e2s[m] (double), dh, dl, eh, el [m] (float)
   const int tid = threadIdx.x;
-  SyevWork W(work_all + blockIdx.x * work_stride, m);
-  double* ev = wall + blockIdx.x * (int64_t)m;
-  const double tnorm = W.meta[0];
-  if (bisect) {
-    double* ds = sm;             // [m] scaled diagonal
-    double* e2s = ds + m;        // [m] scaled squared off-diagonal
-    float* dh = reinterpret_cast<float*>(e2s + m);   // [m] x 4: double-float copies of ds, e2s
+  const int64_t total = (int64_t)batch * m;
+  const int64_t g0 = (int64_t)blockIdx.x * BT;
+  const int64_t g1 = (g0 + BT < total) ? g0 + BT : total;
+  const int mat0 = (int)(g0 / m);
+  const int nmat = (int)((g1 - 1) / m) - mat0 + 1;
+  for (int lm = 0; lm < nmat; ++lm) {
+    SyevWork W(work_all + (mat0 + lm) * work_stride, m);
+    const double tnorm = W.meta[0];
+    // scale T by 2^-sc (exact) so that its norm is at most 1
+    const int sc = (tnorm > 0.0) ? ilogb(tnorm) + 1 : 0;
+    double* ds = sm + (int64_t)lm * 4 * m;
+    double* e2s = ds + m;
+    float* dh = reinterpret_cast<float*>(e2s + m);
     float* dl = dh + m;
     float* eh = dl + m;
     float* el = eh + m;
-    // scale T by 2^-sc (exact) so that its norm is at most 1
-    const int sc = (tnorm > 0.0) ? ilogb(tnorm) + 1 : 0;
-    for (int i = tid; i < m; i += VT) {
+    for (int i = tid; i < m; i += BT) {
       const double di = ldexp(W.d[i], -sc), ei = ldexp(W.e[i], -sc);
       ds[i] = di;
       e2s[i] = ei * ei;
       const float2 a = df_split(di), b = df_split(ei * ei);
       dh[i] = a.x; dl[i] = a.y; eh[i] = b.x; el[i] = b.y;
     }
-    __syncthreads();
-    const double glo = ldexp(W.meta[1], -sc) - 0x1p-40, ghi = ldexp(W.meta[2], -sc) + 0x1p-40;
-    const int k = blockIdx.y * VT + tid;          // k-th smallest eigenvalue
-    if (k < m) {
-      double lo = glo, hi = ghi;
-      for (int it = 0; it < 48; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (sturm_count_df(dh, dl, eh, el, m, mid) > k) hi = mid; else lo = mid;
-      }
-      // float64 polish: widen, re-verify the bracket with float64 counts, halve
-      double wd = 0x1p-44;
-      lo -= wd;
-      for (int r = 0; r < 40 && lo > glo && sturm_count_f64(ds, e2s, m, lo) > k; ++r) { wd *= 2.0; lo = fmax(lo - wd, glo); }
-      wd = 0x1p-44;
-      hi += wd;
-      for (int r = 0; r < 40 && hi < ghi && sturm_count_f64(ds, e2s, m, hi) <= k; ++r) { wd *= 2.0; hi = fmin(hi + wd, ghi); }
-      for (int it = 0; it < 10; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (!(mid > lo && mid < hi)) break;
-        if (sturm_count_f64(ds, e2s, m, mid) > k) hi = mid; else lo = mid;
-      }
-      ev[m - 1 - k] = ldexp(0.5 * (lo + hi), sc);
-    }
-    if (blockIdx.y == 0 && tid == 0) info[blockIdx.x] = 0;
-    return;
   }
-  // reference path: implicit QL without vectors (one thread), then a rank sort
-  if (blockIdx.y != 0) return;
+  __syncthreads();
+  const int64_t g = g0 + tid;
+  if (g >= g1) return;
+  const int mat = (int)(g / m), k = (int)(g % m);   // k-th smallest eigenvalue of matrix mat
+  SyevWork W(work_all + mat * work_stride, m);
+  const double tnorm = W.meta[0];
+  const int sc = (tnorm > 0.0) ? ilogb(tnorm) + 1 : 0;
+  const double* ds = sm + (int64_t)(mat - mat0) * 4 * m;
+  const double* e2s = ds + m;
+  const float* dh = reinterpret_cast<const float*>(e2s + m);
+  const float* dl = dh + m;
+  const float* eh = dl + m;
+  const float* el = eh + m;
+  const double glo = ldexp(W.meta[1], -sc) - 0x1p-40, ghi = ldexp(W.meta[2], -sc) + 0x1p-40;
+  double lo = glo, hi = ghi;
+  for (int it = 0; it < 48; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count_df(dh, dl, eh, el, m, mid) > k) hi = mid; else lo = mid;
+  }
+  // float64 polish: widen, re-verify the bracket with float64 counts, halve
+  double wd = 0x1p-44;
+  lo -= wd;
+  for (int r = 0; r < 40 && lo > glo && sturm_count_f64(ds, e2s, m, lo) > k; ++r) { wd *= 2.0; lo = fmax(lo - wd, glo); }
+  wd = 0x1p-44;
+  hi += wd;
+  for (int r = 0; r < 40 && hi < ghi && sturm_count_f64(ds, e2s, m, hi) <= k; ++r) { wd *= 2.0; hi = fmin(hi + wd, ghi); }
+  for (int it = 0; it < 10; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (sturm_count_f64(ds, e2s, m, mid) > k) hi = mid; else lo = mid;
+  }
+  wall[(int64_t)mat * m + m - 1 - k] = ldexp(0.5 * (lo + hi), sc);
+  if (k == 0) info[mat] = 0;
+}
+
+// Reference path (precision mode 0): implicit QL without vectors (one
+// thread per matrix), then a rank sort.
+constexpr int VT = 128;        // threads per block of the QL rank sort
+__global__ void __launch_bounds__(VT) syev_values_kernel(int m, double* __restrict__ work_all, int64_t work_stride,
+                                                         double* __restrict__ wall, int* __restrict__ info) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  SyevWork W(work_all + blockIdx.x * work_stride, m);
+  double* ev = wall + blockIdx.x * (int64_t)m;
+  const double tnorm = W.meta[0];
   double* v = sm;
   double* w = v + m;
   __shared__ int ql_fail;
@@ -471,7 +500,11 @@ __device__ int pca_rank_rule(const double* ev, int m, int mode, double thr) {
 }
 
 // ---- 3./4. rank rule and inverse iteration, grid (matrix, part of the vectors) ----
-__global__ void __launch_bounds__(VT) syev_vectors_kernel(int m, double* __restrict__ work_all, int64_t work_stride,
+// One thread per kept vector; blocks of VV threads over (matrix, vector
+// range), so the few hundred busy threads of a batch spread over the SMs
+// (each thread's LU chain loads the SM's float64 pipe).
+constexpr int VV = 64;
+__global__ void __launch_bounds__(VV) syev_vectors_kernel(int m, double* __restrict__ work_all, int64_t work_stride,
                                                           const double* __restrict__ wall, int* __restrict__ ranks,
                                                           int mode, double thr) {
   extern __shared__ double sm[];
@@ -485,10 +518,10 @@ __global__ void __launch_bounds__(VT) syev_vectors_kernel(int m, double* __restr
     prank = pca_rank_rule(ev, m, mode, thr);
     if (blockIdx.y == 0) ranks[blockIdx.x] = prank;
   }
-  for (int i = tid; i < m; i += VT) { d[i] = W.d[i]; e[i] = W.e[i]; }
+  for (int i = tid; i < m; i += VV) { d[i] = W.d[i]; e[i] = W.e[i]; }
   __syncthreads();
   const int p = prank;
-  const int k = blockIdx.y * VT + tid;
+  const int k = blockIdx.y * VV + tid;
   if (k >= p) return;
   const double tolp = 2.2e-16 * W.meta[0] + 1e-300;
   const int64_t mm = (int64_t)m * m;
@@ -811,16 +844,23 @@ cudaError_t launch_syev_phase(const SyevBatch& b, int phase, cudaStream_t st) {
       break;
     }
     case 1: {
-      const int smem = (int)(sizeof(double) * 4 * m);
-      if ((e = cudaFuncSetAttribute(syev_values_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-        return e;
-      syev_values_kernel<<<dim3(b.batch, b.bisect ? (m + VT - 1) / VT : 1), VT, smem, st>>>(m, b.work, ws, b.w,
-                                                                                          b.info, b.bisect);
+      if (b.bisect) {
+        const int64_t total = (int64_t)b.batch * m;
+        const int nmat = std::min(b.batch, bisect_mats_per_block(m));
+        const int smem = (int)(sizeof(double) * 4 * (size_t)m * nmat);
+        if ((e = cudaFuncSetAttribute(syev_bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+            cudaSuccess)
+          return e;
+        syev_bisect_kernel<<<(unsigned)((total + BT - 1) / BT), BT, smem, st>>>(m, b.batch, b.work, ws, b.w, b.info);
+      } else {
+        const int smem = (int)(sizeof(double) * 2 * m);
+        syev_values_kernel<<<b.batch, VT, smem, st>>>(m, b.work, ws, b.w, b.info);
+      }
       break;
     }
     case 2: {
       const int smem = (int)(sizeof(double) * 2 * m);
-      syev_vectors_kernel<<<dim3(b.batch, (m + VT - 1) / VT), VT, smem, st>>>(m, b.work, ws, b.w, b.ranks, b.mode,
+      syev_vectors_kernel<<<dim3(b.batch, (m + VV - 1) / VV), VV, smem, st>>>(m, b.work, ws, b.w, b.ranks, b.mode,
                                                                              b.thr);
       break;
     }
