@@ -22,8 +22,10 @@ cudaError_t launch_matvec_HT2(const ProbDev& P, const SubDev* d_sub, int J, cons
                               int nrtiles, const int* d_tile0, const double* d_B, const double* d_y,
                               double* d_part, double* d_z, int maxP, cudaStream_t st);
 cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, int* d_fail,
-                             const double* d_dmax, int df, cudaStream_t st);
+                             const double* d_dmax, cudaStream_t st);
 cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, int df, cudaStream_t st);
+cudaError_t launch_chol_df_lookahead(const CholMat* d_mats, int nmat, int maxn, int* d_fail, const double* d_dmax,
+                                     cudaStream_t st, cudaStream_t st2, cudaEvent_t* ev, int* nlaunch);
 cudaError_t launch_split(const double* d_x, float2* d_x2, int64_t n, cudaStream_t st);
 cudaError_t launch_split_pad(const SubDev* d_sub, int J, const double* d_x, float2* d_x2p, cudaStream_t st);
 cudaError_t launch_rowdot_df(const SubDev* d_sub, const int* d_rtiles, int nrtiles, int tile_rows,
@@ -155,6 +157,8 @@ struct Prof {
 
 struct rann_dd_handle {
   cudaStream_t st = nullptr;
+  cudaStream_t st_la = nullptr;   // high-priority stream of the Cholesky lookahead (created on first use)
+  cudaEvent_t ev_la[5] = {};
   ProbDev P{};
   int J = 0, m = 0, dim = 0, Gmax = 0;
   int64_t N = 0, rows_total = 0;
@@ -525,6 +529,12 @@ extern "C" void rann_dd_destroy(rann_dd_handle* h) {
   if (h->h_stage) cudaFreeHost(h->h_stage);
   prof_resolve(h);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+  if (h->st_la) {
+    cudaStreamSynchronize(h->st_la);
+    cudaStreamDestroy(h->st_la);
+  }
+  for (cudaEvent_t e : h->ev_la)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 
@@ -1140,9 +1150,21 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   for (int i = 0; i < J; ++i) chol_flops += (double)mats[i].n * mats[i].n * mats[i].n / 3.0;
   for (int attempt = 0; attempt < 6; ++attempt) {
     CK(cudaMemsetAsync(d_fail, 0, sizeof(int) * J, h->st));
-    for (int c0 = 0; c0 < h->maxn; c0 += 32)
-      KLA(h, K_CHOL, (h->maxn - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
-          launch_chol_step(h->d_mats, J, h->maxn, c0, d_fail, d_dmax, h->prec_df, h->st));
+    if (h->prec_df) {
+      if (!h->st_la) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&h->st_la, cudaStreamNonBlocking, greatest));
+        for (cudaEvent_t& e : h->ev_la) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      }
+      int nl = 0;
+      KLA(h, K_CHOL, nl, 0, chol_flops,
+          launch_chol_df_lookahead(h->d_mats, J, h->maxn, d_fail, d_dmax, h->st, h->st_la, h->ev_la, &nl));
+    } else {
+      for (int c0 = 0; c0 < h->maxn; c0 += 32)
+        KLA(h, K_CHOL, (h->maxn - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
+            launch_chol_step(h->d_mats, J, h->maxn, c0, d_fail, d_dmax, h->st));
+    }
     std::vector<int> f(J);
     int ozerr = 0;
     CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));

@@ -208,17 +208,32 @@ __global__ void __launch_bounds__(128) trsm_panel_df_kernel(const CholMat* __res
 }
 
 // A22 -= L21 L21^T on the lower triangle of A2, 64 x 64 tiles, double-float.
-__global__ void __launch_bounds__(256) syrk_update_df_kernel(const CholMat* __restrict__ mats, int c0) {
+// The panel is columns [c0, c0 + NB); the updated region starts at
+// s0 = c0 + NB + skip.  colpart = 0: the whole lower triangle from s0 (one
+// block per lower tile).  colpart = 1: only block column [s0, s0 + NB), rows
+// >= s0 (one block per 64-row tile).  Each entry is the same fixed-order sum
+// over the panel whichever tile holds it, so splitting the update into the
+// next block column and the rest changes no result.
+__global__ void __launch_bounds__(256) syrk_update_df_kernel(const CholMat* __restrict__ mats, int c0, int skip,
+                                                             int colpart) {
   const CholMat M = mats[blockIdx.y];
-  const int s0 = c0 + NB;
+  const int s0 = c0 + NB + skip;
   if (M.n <= s0) return;
   const int T = (M.n - s0 + 63) / 64;
   const int t = blockIdx.x;
-  if (t >= T * (T + 1) / 2) return;
-  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while (ti * (ti + 1) / 2 > t) --ti;
-  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-  const int tj = t - ti * (ti + 1) / 2;
+  int ti, tj;
+  if (colpart) {
+    if (t >= T) return;
+    ti = t;
+    tj = 0;
+  } else {
+    if (t >= T * (T + 1) / 2) return;
+    ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (ti * (ti + 1) / 2 > t) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    tj = t - ti * (ti + 1) / 2;
+  }
+  const int cend = colpart ? s0 + NB : M.n;       // columns written: c < cend
   const int r0 = s0 + ti * 64, q0 = s0 + tj * 64;
   __shared__ float2 sa[NB][65];
   __shared__ float2 sb[NB][65];
@@ -255,7 +270,7 @@ __global__ void __launch_bounds__(256) syrk_update_df_kernel(const CholMat* __re
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = r0 + ty + 16 * p, c = q0 + tx + 16 * q;
-      if (r < M.n && c <= r) {
+      if (r < M.n && c <= r && c < cend) {
         float2 v = M.A2[(int64_t)r * M.ld + c];
         df_add(v.x, v.y, -ah[p][q], -al[p][q]);
         M.A2[(int64_t)r * M.ld + c] = v;
@@ -1152,23 +1167,67 @@ cudaError_t launch_add_diag(const CholMat* d_mats, const int* d_which, int nwhic
   return cudaGetLastError();
 }
 
+// One serial step of the float64 factorisation (precision mode 0).
 cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, int* d_fail,
-                             const double* d_dmax, int df, cudaStream_t st) {
+                             const double* d_dmax, cudaStream_t st) {
   const int rest = maxn - c0 - NB;
   const int T = (rest + 63) / 64;
-  if (df) {
-    potrf_diag_df_kernel<<<nmat, NB * 8, 0, st>>>(d_mats, c0, d_fail, d_dmax);
-    if (rest > 0) {
-      trsm_panel_df_kernel<<<dim3((rest + 31) / 32, nmat), 128, 0, st>>>(d_mats, c0);
-      syrk_update_df_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
-    }
-  } else {
-    potrf_diag_kernel<<<nmat, 256, 0, st>>>(d_mats, c0, d_fail, d_dmax);
-    if (rest > 0) {
-      trsm_panel_kernel<<<dim3((rest + 127) / 128, nmat), 128, 0, st>>>(d_mats, c0);
-      syrk_update_f64_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
-    }
+  potrf_diag_kernel<<<nmat, 256, 0, st>>>(d_mats, c0, d_fail, d_dmax);
+  if (rest > 0) {
+    trsm_panel_kernel<<<dim3((rest + 127) / 128, nmat), 128, 0, st>>>(d_mats, c0);
+    syrk_update_f64_kernel<<<dim3(T * (T + 1) / 2, nmat), 256, 0, st>>>(d_mats, c0);
   }
+  return cudaGetLastError();
+}
+
+// The whole double-float factorisation with one block column of lookahead.
+// Step s (c0 = s NB) splits its trailing update into block column s + 1 and
+// the rest (columns >= c0 + 2 NB).  The critical path -- block column s + 1,
+// its diagonal block, its panel -- runs on st2 (high priority) while the
+// rest of step s runs on st, so the latency-bound diagonal factorisations
+// overlap the throughput-bound updates.  Order per entry is the serial one:
+// block column s + 1 is updated by step s only after the rest of step s - 1
+// (event evR), and the rest of step s starts only after panel s (event evT);
+// the regions written concurrently are disjoint.  ev: five events (fork /
+// join, two for panels, two for the rests).  *nlaunch: kernels launched.
+cudaError_t launch_chol_df_lookahead(const CholMat* d_mats, int nmat, int maxn, int* d_fail, const double* d_dmax,
+                                     cudaStream_t st, cudaStream_t st2, cudaEvent_t* ev, int* nlaunch) {
+  int n = 0;
+  cudaError_t e;
+  auto potrf = [&](int c0) {
+    potrf_diag_df_kernel<<<nmat, NB * 8, 0, st2>>>(d_mats, c0, d_fail, d_dmax);
+    ++n;
+  };
+  auto trsm = [&](int c0) {
+    trsm_panel_df_kernel<<<dim3((maxn - c0 - NB + 31) / 32, nmat), 128, 0, st2>>>(d_mats, c0);
+    ++n;
+  };
+  auto syrk = [&](int c0, int skip, int colpart, cudaStream_t s) {
+    const int T = (maxn - c0 - NB - skip + 63) / 64;
+    syrk_update_df_kernel<<<dim3(colpart ? T : T * (T + 1) / 2, nmat), 256, 0, s>>>(d_mats, c0, skip, colpart);
+    ++n;
+  };
+  const int nsteps = (maxn + NB - 1) / NB;
+  if ((e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(st2, ev[0], 0)) != cudaSuccess) return e;
+  potrf(0);
+  if (nsteps > 1) trsm(0);
+  if ((e = cudaEventRecord(ev[1], st2)) != cudaSuccess) return e;
+  for (int s = 0; s + 1 < nsteps; ++s) {
+    const int c0 = s * NB;
+    const bool more = maxn > c0 + 2 * NB;          // columns beyond block column s + 1
+    if ((e = cudaStreamWaitEvent(st, ev[1 + (s & 1)], 0)) != cudaSuccess) return e;   // panel s
+    if (more) syrk(c0, NB, 0, st);
+    if ((e = cudaEventRecord(ev[3 + (s & 1)], st)) != cudaSuccess) return e;
+    if (s >= 1 && (e = cudaStreamWaitEvent(st2, ev[3 + ((s - 1) & 1)], 0)) != cudaSuccess) return e;   // rest s - 1
+    syrk(c0, 0, 1, st2);
+    potrf(c0 + NB);
+    if (more) trsm(c0 + NB);
+    if ((e = cudaEventRecord(ev[1 + ((s + 1) & 1)], st2)) != cudaSuccess) return e;
+  }
+  if ((e = cudaEventRecord(ev[0], st2)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(st, ev[0], 0)) != cudaSuccess) return e;
+  *nlaunch = n;
   return cudaGetLastError();
 }
 
