@@ -23,9 +23,10 @@ cudaError_t launch_matvec_HT2(const ProbDev& P, const SubDev* d_sub, int J, cons
                               double* d_part, double* d_z, int maxP, cudaStream_t st);
 cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, int* d_fail,
                              const double* d_dmax, cudaStream_t st);
-cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, int df, cudaStream_t st);
+cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st);
 cudaError_t launch_chol_df_lookahead(const CholMat* d_mats, int nmat, int maxn, int* d_fail, const double* d_dmax,
-                                     cudaStream_t st, cudaStream_t st2, cudaEvent_t* ev, int* nlaunch);
+                                     cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaEvent_t* ev,
+                                     int* nlaunch);
 cudaError_t launch_split(const double* d_x, float2* d_x2, int64_t n, cudaStream_t st);
 cudaError_t launch_split_pad(const SubDev* d_sub, int J, const double* d_x, float2* d_x2p, cudaStream_t st);
 cudaError_t launch_rowdot_df(const SubDev* d_sub, const int* d_rtiles, int nrtiles, int tile_rows,
@@ -158,7 +159,8 @@ struct Prof {
 struct rann_dd_handle {
   cudaStream_t st = nullptr;
   cudaStream_t st_la = nullptr;   // high-priority stream of the Cholesky lookahead (created on first use)
-  cudaEvent_t ev_la[5] = {};
+  cudaStream_t st_inv = nullptr;  // stream of the row-block inverse inside the factorisation
+  cudaEvent_t ev_la[7] = {};
   ProbDev P{};
   int J = 0, m = 0, dim = 0, Gmax = 0;
   int64_t N = 0, rows_total = 0;
@@ -529,10 +531,11 @@ extern "C" void rann_dd_destroy(rann_dd_handle* h) {
   if (h->h_stage) cudaFreeHost(h->h_stage);
   prof_resolve(h);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
-  if (h->st_la) {
-    cudaStreamSynchronize(h->st_la);
-    cudaStreamDestroy(h->st_la);
-  }
+  for (cudaStream_t* sp : {&h->st_la, &h->st_inv})
+    if (*sp) {
+      cudaStreamSynchronize(*sp);
+      cudaStreamDestroy(*sp);
+    }
   for (cudaEvent_t e : h->ev_la)
     if (e) cudaEventDestroy(e);
   delete h;
@@ -1155,11 +1158,13 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
         int least = 0, greatest = 0;
         CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
         CK(cudaStreamCreateWithPriority(&h->st_la, cudaStreamNonBlocking, greatest));
+        CK(cudaStreamCreateWithPriority(&h->st_inv, cudaStreamNonBlocking, least));
         for (cudaEvent_t& e : h->ev_la) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       }
       int nl = 0;
-      KLA(h, K_CHOL, nl, 0, chol_flops,
-          launch_chol_df_lookahead(h->d_mats, J, h->maxn, d_fail, d_dmax, h->st, h->st_la, h->ev_la, &nl));
+      KLA(h, K_CHOL, nl, 0, chol_flops + h->sum_n3 / 3.0,
+          launch_chol_df_lookahead(h->d_mats, J, h->maxn, d_fail, d_dmax, h->st, h->st_la, h->st_inv, h->ev_la,
+                                   &nl));
     } else {
       for (int c0 = 0; c0 < h->maxn; c0 += 32)
         KLA(h, K_CHOL, (h->maxn - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
@@ -1197,8 +1202,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     dfree(h, d_fm); dfree(h, d_which); dfree(h, d_shift);
   }
   for (int i = 0; i < J; ++i) h->n_shifted += shifted[i];
-  // X_i = L_i^{-1} for the parallel apply
-  KLA(h, K_TRTRI, h->prec_df ? 1 : 2, 0, h->sum_n3 / 3.0, launch_trtri(h->d_mats, J, h->maxn, h->prec_df, h->st));
+  // X_i = L_i^{-1} for the parallel apply (precision mode 1 formed it inside the factorisation)
+  if (!h->prec_df) KLA(h, K_TRTRI, 2, 0, h->sum_n3 / 3.0, launch_trtri(h->d_mats, J, h->maxn, h->st));
   if (!h->prec_df) KLA(h, K_SPLIT, 1, 6.0 * h->sum_n2, 0, launch_split_lower(h->d_mats, J, h->maxn, h->st));
   std::vector<int64_t> p_off(J + 1, 0);
   for (int i = 0; i < J; ++i) p_off[i + 1] = p_off[i] + (int64_t)((mats[i].n + 255) / 256) * mats[i].n;

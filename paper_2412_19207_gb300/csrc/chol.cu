@@ -89,11 +89,10 @@ __global__ void trsm_panel_kernel(const CholMat* __restrict__ mats, int c0) {
 
 // ---- double-float resident factorisation (precision mode 1) ----
 // A_i, L_i and L_i^{-1} stay double-float (A2, X2): the 32 x 32 diagonal
-// block is factored in float64 (converted on load and store) together with
-// its inverse, which goes to the diagonal block of X2; the panel is then
-// L21 = A21 L11^{-T} as a double-float product with that inverse, and the
-// trailing update A22 -= L21 L21^T and the block-column inverse run on the
-// float32 pipe with no conversions.
+// block is factored together with its inverse, which goes to the diagonal
+// block of X2; the panel is then L21 = A21 L11^{-T} as a double-float product
+// with that inverse, and the trailing update A22 -= L21 L21^T and the
+// block-column inverse run on the float32 pipe with no conversions.
 
 // Diagonal block c0 of A2: L11 back to A2 and L11^{-1} to X2, in double-float
 // on the float32 pipe (the block is stored in double-float, so float64 here
@@ -171,40 +170,42 @@ __global__ void potrf_diag_df_kernel(const CholMat* __restrict__ mats, int c0, i
 }
 
 // L21 = A21 L11^{-T}: row r of the panel times the stored inverse block, in
-// double-float; four threads per row, each forming eight of its 32 columns
-// (the k loop is not unrolled, so the code stays small).
+// double-float.  A block takes 32 rows (staged in shared memory); warp w forms
+// columns 8w .. 8w + 7 of every row (lane = row), so the triangular bound
+// on k is the same for the whole warp and no lane idles through it.
 __global__ void __launch_bounds__(128) trsm_panel_df_kernel(const CholMat* __restrict__ mats, int c0) {
   const CholMat M = mats[blockIdx.y];
   if (M.n <= c0 + NB) return;
   __shared__ float2 li[NB][NB + 1];
+  __shared__ float2 ar[32][NB + 1];
+  const int rbase = c0 + NB + blockIdx.x * 32;
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
     li[r][c] = (c <= r) ? M.X2[(int64_t)(c0 + r) * M.ld + c0 + c] : make_float2(0.f, 0.f);
+    ar[r][c] = (rbase + r < M.n) ? M.A2[(int64_t)(rbase + r) * M.ld + c0 + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int r = c0 + NB + blockIdx.x * (blockDim.x / 4) + (threadIdx.x >> 2);
-  const int j0 = (threadIdx.x & 3) * 8;
-  const bool valid = r < M.n;                       // the four threads of a row share it
-  float2* row = M.A2 + (int64_t)(valid ? r : 0) * M.ld + c0;
+  const int lane = threadIdx.x & 31;
+  const int j0 = (threadIdx.x >> 5) * 8;
   float ah[8], al[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) { ah[u] = 0.f; al[u] = 0.f; }
-  if (valid) {
 #pragma unroll 1
-    for (int k = 0; k < j0 + 8; ++k) {               // columns j >= k only: L11^{-1} is lower triangular
-      const float2 xk = row[k];
+  for (int k = 0; k < j0 + 8; ++k) {                 // columns j >= k only: L11^{-1} is lower triangular
+    const float2 xk = ar[lane][k];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (j0 + u >= k) df_mac(ah[u], al[u], xk, li[j0 + u][k]);
-    }
+    for (int u = 0; u < 8; ++u)
+      if (j0 + u >= k) df_mac(ah[u], al[u], xk, li[j0 + u][k]);
   }
-  __syncwarp();                                      // the row's reads of columns < 32 precede its writes
-  if (valid)
+  const int r = rbase + lane;
+  if (r < M.n) {
+    float2* row = M.A2 + (int64_t)r * M.ld + c0;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       df_renorm(ah[u], al[u]);
       row[j0 + u] = make_float2(ah[u], al[u]);
     }
+  }
 }
 
 // A22 -= L21 L21^T on the lower triangle of A2, 64 x 64 tiles, double-float.
@@ -304,65 +305,64 @@ __global__ void trtri_diag_kernel(const CholMat* __restrict__ mats) {
   for (int r = c; r < nb; ++r) M.X[(int64_t)(b0 + r) * M.ld + b0 + c] = x[r];
 }
 
-// Block column j of X2 = L^{-1} (double-float, L from A2): for i > j,
-// X_ij = -X_ii sum_{j <= k < i} L_ik X_kj; the diagonal blocks X_ii were
-// written by the factorisation.
-__global__ void __launch_bounds__(256) trtri_col_df_kernel(const CholMat* __restrict__ mats) {
+// Row block i of X2 = L^{-1} (double-float, L from A2): for every j < i,
+// X_ij = -X_ii sum_{j <= k < i} L_ik X_kj (k in increasing order, each block
+// product renormalised); the diagonal blocks X_ii were written by the
+// factorisation.  Row block i needs only L's rows of block i (final once
+// diagonal block i is factored) and X's row blocks below i, so it runs inside
+// the factorisation's pipeline, one launch per i; grid (j, matrix).
+__global__ void __launch_bounds__(256) trtri_row_df_kernel(const CholMat* __restrict__ mats, int i) {
   const CholMat M = mats[blockIdx.y];
   const int nblk = (M.n + NB - 1) / NB;
   const int j = blockIdx.x;
-  if (j >= nblk) return;
+  if (i >= nblk || j >= i) return;
   __shared__ float2 sl[NB][NB + 1];
   __shared__ float2 sx[NB][NB + 1];
   const int t = threadIdx.x, r = t % NB, cg = (t / NB) * 4;   // row r, columns cg..cg+3
-  const int cj = j * NB;
+  const int cj = j * NB, ri = i * NB;
   const float2 zero = make_float2(0.f, 0.f);
-  for (int i = j + 1; i < nblk; ++i) {
-    const int ri = i * NB;
-    float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k = j; k < i; ++k) {
-      const int ck = k * NB;
-      for (int e = t; e < NB * NB; e += 256) {
-        const int a = e / NB, b = e % NB;
-        sl[a][b] = (ri + a < M.n) ? M.A2[(int64_t)(ri + a) * M.ld + ck + b] : zero;   // L_ik
-        // X_kj (the diagonal block X_jj is lower triangular: its upper part is never written)
-        sx[a][b] = (ck + a < M.n && cj + b < M.n && (k > j || b <= a)) ? M.X2[(int64_t)(ck + a) * M.ld + cj + b]
-                                                                       : zero;
-      }
-      __syncthreads();
-#pragma unroll 8
-      for (int q = 0; q < NB; ++q) {
-        const float2 lv = sl[r][q];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) df_mac(ah[u], al[u], lv, sx[q][cg + u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) df_renorm(ah[u], al[u]);
-      __syncthreads();
-    }
-    // X_ij = -X_ii acc
+  float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k = j; k < i; ++k) {
+    const int ck = k * NB;
     for (int e = t; e < NB * NB; e += 256) {
       const int a = e / NB, b = e % NB;
-      sl[a][b] = (ri + a < M.n && b <= a) ? M.X2[(int64_t)(ri + a) * M.ld + ri + b] : zero;   // X_ii
+      sl[a][b] = (ri + a < M.n) ? M.A2[(int64_t)(ri + a) * M.ld + ck + b] : zero;   // L_ik
+      // X_kj (the diagonal block X_jj is lower triangular: its upper part is never written)
+      sx[a][b] = (ck + a < M.n && cj + b < M.n && (k > j || b <= a)) ? M.X2[(int64_t)(ck + a) * M.ld + cj + b]
+                                                                     : zero;
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) sx[r][cg + u] = make_float2(ah[u], al[u]);
     __syncthreads();
-    float oh[4] = {0.f, 0.f, 0.f, 0.f}, ol[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int q = 0; q <= r; ++q) {
+#pragma unroll 8
+    for (int q = 0; q < NB; ++q) {
       const float2 lv = sl[r][q];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) df_mac(oh[u], ol[u], lv, sx[q][cg + u]);
+      for (int u = 0; u < 4; ++u) df_mac(ah[u], al[u], lv, sx[q][cg + u]);
     }
-    if (ri + r < M.n)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (cj + cg + u >= M.n) continue;
-        df_renorm(oh[u], ol[u]);
-        M.X2[(int64_t)(ri + r) * M.ld + cj + cg + u] = make_float2(-oh[u], -ol[u]);
-      }
-    __syncthreads();   // X_ij visible to the next i (same block)
+    for (int u = 0; u < 4; ++u) df_renorm(ah[u], al[u]);
+    __syncthreads();
   }
+  // X_ij = -X_ii acc
+  for (int e = t; e < NB * NB; e += 256) {
+    const int a = e / NB, b = e % NB;
+    sl[a][b] = (ri + a < M.n && b <= a) ? M.X2[(int64_t)(ri + a) * M.ld + ri + b] : zero;   // X_ii
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) sx[r][cg + u] = make_float2(ah[u], al[u]);
+  __syncthreads();
+  float oh[4] = {0.f, 0.f, 0.f, 0.f}, ol[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int q = 0; q <= r; ++q) {
+    const float2 lv = sl[r][q];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) df_mac(oh[u], ol[u], lv, sx[q][cg + u]);
+  }
+  if (ri + r < M.n)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (cj + cg + u >= M.n) continue;
+      df_renorm(oh[u], ol[u]);
+      M.X2[(int64_t)(ri + r) * M.ld + cj + cg + u] = make_float2(-oh[u], -ol[u]);
+    }
 }
 
 // Float64 variant of the trailing update (precision mode 0).
@@ -1180,18 +1180,23 @@ cudaError_t launch_chol_step(const CholMat* d_mats, int nmat, int maxn, int c0, 
   return cudaGetLastError();
 }
 
-// The whole double-float factorisation with one block column of lookahead.
-// Step s (c0 = s NB) splits its trailing update into block column s + 1 and
-// the rest (columns >= c0 + 2 NB).  The critical path -- block column s + 1,
-// its diagonal block, its panel -- runs on st2 (high priority) while the
-// rest of step s runs on st, so the latency-bound diagonal factorisations
-// overlap the throughput-bound updates.  Order per entry is the serial one:
+// The whole double-float factorisation with one block column of lookahead,
+// and X = L^{-1} by row blocks inside the same pipeline.  Step s (c0 = s NB)
+// splits its trailing update into block column s + 1 and the rest (columns
+// >= c0 + 2 NB).  The critical path -- block column s + 1, its diagonal
+// block, its panel -- runs on st2 (high priority) while the rest of step s
+// runs on st; row block s + 1 of X runs on st3 once diagonal block s + 1 is
+// factored.  So the latency-bound diagonal factorisations overlap the
+// throughput-bound updates and inverse.  Order per entry is the serial one:
 // block column s + 1 is updated by step s only after the rest of step s - 1
-// (event evR), and the rest of step s starts only after panel s (event evT);
-// the regions written concurrently are disjoint.  ev: five events (fork /
-// join, two for panels, two for the rests).  *nlaunch: kernels launched.
+// (evR), the rest of step s starts only after panel s (evT), row block i of
+// X after diagonal block i (evP; L's rows of block i are final by then) and
+// after row block i - 1 (stream order); the regions written concurrently are
+// disjoint.  ev: seven events (fork / join, two each for panels, rests and
+// diagonal blocks).  *nlaunch: kernels launched.
 cudaError_t launch_chol_df_lookahead(const CholMat* d_mats, int nmat, int maxn, int* d_fail, const double* d_dmax,
-                                     cudaStream_t st, cudaStream_t st2, cudaEvent_t* ev, int* nlaunch) {
+                                     cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaEvent_t* ev,
+                                     int* nlaunch) {
   int n = 0;
   cudaError_t e;
   auto potrf = [&](int c0) {
@@ -1210,6 +1215,7 @@ cudaError_t launch_chol_df_lookahead(const CholMat* d_mats, int nmat, int maxn, 
   const int nsteps = (maxn + NB - 1) / NB;
   if ((e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(st2, ev[0], 0)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(st3, ev[0], 0)) != cudaSuccess) return e;
   potrf(0);
   if (nsteps > 1) trsm(0);
   if ((e = cudaEventRecord(ev[1], st2)) != cudaSuccess) return e;
@@ -1222,24 +1228,28 @@ cudaError_t launch_chol_df_lookahead(const CholMat* d_mats, int nmat, int maxn, 
     if (s >= 1 && (e = cudaStreamWaitEvent(st2, ev[3 + ((s - 1) & 1)], 0)) != cudaSuccess) return e;   // rest s - 1
     syrk(c0, 0, 1, st2);
     potrf(c0 + NB);
+    if ((e = cudaEventRecord(ev[5 + (s & 1)], st2)) != cudaSuccess) return e;
     if (more) trsm(c0 + NB);
     if ((e = cudaEventRecord(ev[1 + ((s + 1) & 1)], st2)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st3, ev[5 + (s & 1)], 0)) != cudaSuccess) return e;   // diagonal block s + 1
+    trtri_row_df_kernel<<<dim3(s + 1, nmat), 256, 0, st3>>>(d_mats, s + 1);
+    ++n;
   }
   if ((e = cudaEventRecord(ev[0], st2)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(st, ev[0], 0)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(ev[0], st3)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(st, ev[0], 0)) != cudaSuccess) return e;
   *nlaunch = n;
   return cudaGetLastError();
 }
 
-cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, int df, cudaStream_t st) {
+// X = L^{-1} in float64 (precision mode 0; mode 1 forms it inside the
+// factorisation's pipeline).
+cudaError_t launch_trtri(const CholMat* d_mats, int nmat, int maxn, cudaStream_t st) {
   if (nmat == 0) return cudaSuccess;
   int nblk = (maxn + NB - 1) / NB;
-  if (df) {            // the diagonal blocks of X2 come from the factorisation
-    trtri_col_df_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
-  } else {
-    trtri_diag_kernel<<<dim3(nblk, nmat), NB, 0, st>>>(d_mats);
-    trtri_col_f64_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
-  }
+  trtri_diag_kernel<<<dim3(nblk, nmat), NB, 0, st>>>(d_mats);
+  trtri_col_f64_kernel<<<dim3(nblk, nmat), 256, 0, st>>>(d_mats);
   return cudaGetLastError();
 }
 
