@@ -38,7 +38,11 @@ DF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12   # double-float multiply-
 # DRAM bytes of one launch of the kernel family (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu --set full capture of the same kernel code
 # on this workload); a family missing here reports null
-TRAFFIC = {"eig_tridiag": 28.43e6}
+TRAFFIC = {"eig_tridiag": 28.35e6}
+# families whose profiled bracket spans a multi-stream pipeline of many kernels
+# (the Cholesky with lookahead and the row-block inverse): no single launch
+# duration, so they are reported as pipelines, not as the roofline kernel
+PIPELINED = {"cholesky"}
 
 
 def workload():
@@ -178,7 +182,7 @@ def bench_ours(args, rank, world):
             e2e.append(time.perf_counter() - t0)
     pk = peaks()
     launches = sum(v["launches"] for v in prof.values()) // prof_steps
-    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dom_name, dom = max(((k, v) for k, v in prof.items() if k not in PIPELINED), key=lambda kv: kv[1]["ms"])
     bound = dom["bound"]
     if bound == "hbm":
         ach = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
@@ -225,6 +229,12 @@ def bench_ours(args, rank, world):
                    "H_f64": gbps(["matvec_H"]), "HT_f64": gbps(["matvec_HT"]),
                    "H_df32": gbps(["matvec_H_df32"]), "HT_df32": gbps(["matvec_HT_df32"]),
                    "schwarz_apply_df32": gbps(["schwarz_apply_df32", "trmv_lower_df32", "trmv_upper_df32"])},
+        "pipelines": {k: {"ms_per_step": round(prof[k]["ms"] / prof_steps, 3),
+                          "launches_per_step": prof[k]["launches"] // prof_steps,
+                          "achieved_tflops": round(prof[k]["flops"] / (prof[k]["ms"] * 1e-3) / 1e12, 3),
+                          "frac_of_df32_peak": round(prof[k]["flops"] / (prof[k]["ms"] * 1e-3) / 1e12
+                                                     / DF32_PEAK_TFLOPS, 4)}
+                      for k in sorted(PIPELINED) if prof.get(k, {}).get("ms")},
         "kernels": kernels,
         "gpu_launches": int(launches) * args.steps,
         "gpu_launches_per_step": int(launches),
