@@ -100,72 +100,79 @@ __global__ void trsm_panel_kernel(const CholMat* __restrict__ mats, int c0) {
 // sqrt / divide / update chain of the 32 columns its bottleneck).  Pivots are
 // checked against the same tolerance as the float64 path.  Entries accumulate
 // their updates unnormalised and are renormalised when read as a pivot or
-// column entry.  The inverse: thread c forms column c by forward substitution.
-__global__ void potrf_diag_df_kernel(const CholMat* __restrict__ mats, int c0, int* __restrict__ fail,
-                                     const double* __restrict__ dmax) {
+// column entry.  Per column j: every thread of rows r >= j forms the pivot's
+// square root itself (identical values; the diagonal goes to dg) and rows
+// r > j scale their entry; then warps 1..7 update the trailing entries while
+// warp 0 forms row j of L11^{-1} (lane c: x_jc by forward substitution, which
+// needs only rows <= j of L11), so the inverse runs inside the column loop.
+__global__ void __launch_bounds__(256) potrf_diag_df_kernel(const CholMat* __restrict__ mats, int c0,
+                                                            int* __restrict__ fail, const double* __restrict__ dmax) {
   const CholMat M = mats[blockIdx.x];
   if (M.n <= c0) return;
   const int nb = min(NB, M.n - c0);
+  const int tid = threadIdx.x;
   __shared__ float2 a[NB][NB + 1];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+  __shared__ float2 xs[NB][NB + 1];   // xs[q][c]: row q of L11^{-1} (lane c of warp 0 owns column c)
+  __shared__ float2 dg[NB];
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
     a[r][c] = (r < nb && c <= r) ? M.A2[(int64_t)(c0 + r) * M.ld + c0 + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const double tol = 1e-15 * dmax[blockIdx.x];
   for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
+    if (tid >= j && tid < nb) {
       float2 piv = df_fast(a[j][j].x, a[j][j].y);
       if (!(df_to_double(piv.x, piv.y) > tol)) {
-        fail[blockIdx.x] = 1;
+        if (tid == j) fail[blockIdx.x] = 1;
         piv = df_split(fmax(fabs(df_to_double(piv.x, piv.y)), tol > 0.0 ? tol : 1e-300));
       }
-      a[j][j] = df_sqrt(piv);
-    }
-    __syncthreads();
-    for (int r = j + 1 + threadIdx.x; r < nb; r += blockDim.x) {
-      float2 v = a[r][j];
-      df_renorm(v.x, v.y);
-      a[r][j] = df_div(v, a[j][j]);
-    }
-    __syncthreads();
-    // a[r][c] -= l_rj l_cj for j < c <= r: thread per entry of the rows below j
-    for (int e = threadIdx.x; e < (nb - j - 1) * NB; e += blockDim.x) {
-      const int r = j + 1 + e / NB, c = e % NB;
-      if (c > j && r >= c) {
-        const float2 lr = a[r][j], lc = a[c][j];
-        float h = a[r][c].x, l = a[r][c].y;
-        df_mac(h, l, make_float2(-lr.x, -lr.y), lc);
-        a[r][c] = make_float2(h, l);
+      const float2 ljj = df_sqrt(piv);
+      if (tid == j) {
+        dg[j] = ljj;
+      } else {
+        float2 v = a[tid][j];
+        df_renorm(v.x, v.y);
+        a[tid][j] = df_div(v, ljj);
       }
     }
     __syncthreads();
-  }
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    if (r >= c) M.A2[(int64_t)(c0 + r) * M.ld + c0 + c] = a[r][c];
-  }
-  // thread c: column c of L11^{-1} by forward substitution (column kept in shared memory)
-  __shared__ float2 xs[NB][NB + 1];
-  const int c = threadIdx.x;
-  if (c < nb) {
-    for (int q = 0; q < nb; ++q) {
-      float h0 = (q == c) ? 1.f : 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-      int k = c;                                     // x_kc = 0 for k < c
-      for (; k + 1 < q; k += 2) {
-        const float2 la = a[q][k], lb = a[q][k + 1];
+    if (tid >= 32) {
+      // a[r][c] -= l_rj l_cj for j < c <= r
+      for (int e = tid - 32; e < (nb - j - 1) * NB; e += blockDim.x - 32) {
+        const int r = j + 1 + e / NB, c = e % NB;
+        if (c > j && r >= c) {
+          const float2 lr = a[r][j], lc = a[c][j];
+          float h = a[r][c].x, l = a[r][c].y;
+          df_mac(h, l, make_float2(-lr.x, -lr.y), lc);
+          a[r][c] = make_float2(h, l);
+        }
+      }
+    } else if (tid <= j) {
+      // x_jc = (delta_jc - sum_{c <= k < j} l_jk x_kc) / l_jj
+      const int c = tid;
+      float h0 = (j == c) ? 1.f : 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+      int k = c;
+      for (; k + 1 < j; k += 2) {
+        const float2 la = a[j][k], lb = a[j][k + 1];
         df_mac(h0, l0, make_float2(-la.x, -la.y), xs[k][c]);
         df_mac(h1, l1, make_float2(-lb.x, -lb.y), xs[k + 1][c]);
       }
-      if (k < q) {
-        const float2 la = a[q][k];
+      if (k < j) {
+        const float2 la = a[j][k];
         df_mac(h0, l0, make_float2(-la.x, -la.y), xs[k][c]);
       }
       df_add(h0, l0, h1, l1);
-      const float2 v = (c <= q) ? df_div(make_float2(h0, l0), a[q][q]) : make_float2(0.f, 0.f);
-      xs[q][c] = v;
-      if (c <= q) M.X2[(int64_t)(c0 + q) * M.ld + c0 + c] = v;
+      const float2 v = df_div(make_float2(h0, l0), dg[j]);
+      xs[j][c] = v;
+      M.X2[(int64_t)(c0 + j) * M.ld + c0 + c] = v;
     }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int r = e / nb, c = e % nb;
+    if (r > c) M.A2[(int64_t)(c0 + r) * M.ld + c0 + c] = a[r][c];
+    else if (r == c) M.A2[(int64_t)(c0 + r) * M.ld + c0 + c] = dg[r];
   }
 }
 
@@ -208,15 +215,17 @@ __global__ void __launch_bounds__(128) trsm_panel_df_kernel(const CholMat* __res
   }
 }
 
-// A22 -= L21 L21^T on the lower triangle of A2, 64 x 64 tiles, double-float.
-// The panel is columns [c0, c0 + NB); the updated region starts at
-// s0 = c0 + NB + skip.  colpart = 0: the whole lower triangle from s0 (one
-// block per lower tile).  colpart = 1: only block column [s0, s0 + NB), rows
-// >= s0 (one block per 64-row tile).  Each entry is the same fixed-order sum
-// over the panel whichever tile holds it, so splitting the update into the
-// next block column and the rest changes no result.
-__global__ void __launch_bounds__(256) syrk_update_df_kernel(const CholMat* __restrict__ mats, int c0, int skip,
-                                                             int colpart) {
+// A22 -= L21 L21^T on the lower triangle of A2, double-float.  The panel is
+// columns [c0, c0 + NB); the updated region starts at s0 = c0 + NB + skip.
+// QN = 4: the whole lower triangle from s0 in 64 x 64 tiles (one block per
+// lower tile).  QN = 2: only block column [s0, s0 + NB), rows >= s0, in
+// 64 x 32 tiles (one block per 64-row tile; a thread holds QN of the tile's
+// 16-column groups).  Each entry is the same fixed-order sum over the panel
+// whichever tile holds it, so splitting the update into the next block
+// column and the rest changes no result.
+template <int QN>
+__global__ void __launch_bounds__(256) syrk_update_df_kernel(const CholMat* __restrict__ mats, int c0, int skip) {
+  constexpr bool colpart = QN == 2;
   const CholMat M = mats[blockIdx.y];
   const int s0 = c0 + NB + skip;
   if (M.n <= s0) return;
@@ -242,34 +251,36 @@ __global__ void __launch_bounds__(256) syrk_update_df_kernel(const CholMat* __re
     const int rr = e / NB, k = e % NB;
     const int r = r0 + rr, q = q0 + rr;
     sa[k][rr] = (r < M.n) ? M.A2[(int64_t)r * M.ld + c0 + k] : make_float2(0.f, 0.f);
-    sb[k][rr] = (q < M.n) ? M.A2[(int64_t)q * M.ld + c0 + k] : make_float2(0.f, 0.f);
+    if (rr < 16 * QN) sb[k][rr] = (q < M.n) ? M.A2[(int64_t)q * M.ld + c0 + k] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float ah[4][4], al[4][4];
+  float ah[4][QN], al[4][QN];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { ah[p][q] = 0.f; al[p][q] = 0.f; }
+    for (int q = 0; q < QN; ++q) { ah[p][q] = 0.f; al[p][q] = 0.f; }
 #pragma unroll 4
   for (int k = 0; k < NB; ++k) {
-    float2 a[4], b[4];
+    float2 a[4], b[QN];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) { a[p] = sa[k][ty + 16 * p]; b[p] = sb[k][tx + 16 * p]; }
+    for (int p = 0; p < 4; ++p) a[p] = sa[k][ty + 16 * p];
+#pragma unroll
+    for (int q = 0; q < QN; ++q) b[q] = sb[k][tx + 16 * q];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) df_mac(ah[p][q], al[p][q], a[p], b[q]);
+      for (int q = 0; q < QN; ++q) df_mac(ah[p][q], al[p][q], a[p], b[q]);
     if ((k & 15) == 15)
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) df_renorm(ah[p][q], al[p][q]);
+        for (int q = 0; q < QN; ++q) df_renorm(ah[p][q], al[p][q]);
   }
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < QN; ++q) {
       const int r = r0 + ty + 16 * p, c = q0 + tx + 16 * q;
       if (r < M.n && c <= r && c < cend) {
         float2 v = M.A2[(int64_t)r * M.ld + c];
@@ -1209,7 +1220,10 @@ cudaError_t launch_chol_df_lookahead(const CholMat* d_mats, int nmat, int maxn, 
   };
   auto syrk = [&](int c0, int skip, int colpart, cudaStream_t s) {
     const int T = (maxn - c0 - NB - skip + 63) / 64;
-    syrk_update_df_kernel<<<dim3(colpart ? T : T * (T + 1) / 2, nmat), 256, 0, s>>>(d_mats, c0, skip, colpart);
+    if (colpart)
+      syrk_update_df_kernel<2><<<dim3(T, nmat), 256, 0, s>>>(d_mats, c0, skip);
+    else
+      syrk_update_df_kernel<4><<<dim3(T * (T + 1) / 2, nmat), 256, 0, s>>>(d_mats, c0, skip);
     ++n;
   };
   const int nsteps = (maxn + NB - 1) / NB;
