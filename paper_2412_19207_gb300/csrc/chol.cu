@@ -760,6 +760,25 @@ __device__ __forceinline__ void df_mac2(float& h0, float& l0, float& h1, float& 
   df_mac(h0, l0, make_float2(a.x, a.y), make_float2(x.x, x.y));
   df_mac(h1, l1, make_float2(a.z, a.w), make_float2(x.z, x.w));
 }
+// The sums of nv vectors of 32 lane partials lp[v * vstride + l], each with
+// the pairing of the xor-shuffle warp sum (level o: entry l += entry l + o
+// for l < o, o = 16 .. 1; df_add is symmetric, so this is bit for bit the
+// value every lane of the shuffle sum ends with), left in entry 0.  The
+// calling warp's lanes share the nv * o additions of each level.
+__device__ __forceinline__ void df_tree_sum32(float2* lp, int vstride, int nv, int lane) {
+  __syncwarp();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int it = lane; it < nv * o; it += 32) {
+      float2* e = lp + (it / o) * vstride + (it % o);
+      float2 a = e[0];
+      const float2 b = e[o];
+      df_add(a.x, a.y, b.x, b.y);
+      e[0] = a;
+    }
+    __syncwarp();
+  }
+}
 __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat* __restrict__ mats,
                                                                const int* __restrict__ set_ptr,
                                                                const int* __restrict__ set_sub,
@@ -774,6 +793,7 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
                                                                const float2* __restrict__ r2) {
   extern __shared__ float4 gs4[];                     // (g_2c, g_2c+1) as double-float pairs
   __shared__ float4 ys4[AR / 2];                      // (y_2q, y_2q+1)
+  __shared__ float2 lp[AR][33];                       // lane partials of the y rows (row rr at rr / 8 of warp rr % 8)
   __shared__ int seg_c[AMAX_SUB + 1], seg_p[AMAX_SUB];
   __shared__ int64_t seg_w[AMAX_SUB];
   __shared__ double seg_d[AMAX_SUB];
@@ -856,8 +876,13 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
     df_add(h[0], l[0], h[1], l[1]);
     df_add(h[2], l[2], h[3], l[3]);
     df_add(h[0], l[0], h[2], l[2]);
-    df_warp_sum(h[0], l[0]);
-    if (lane == 0) ys[rr] = make_float2(h[0], l[0]);
+    lp[rr][lane] = make_float2(h[0], l[0]);
+  }
+  // each warp sums the lane partials of its rows (warp, warp + 8, ...)
+  if (warp < nr) {
+    const int nv = (nr - warp + ANT / 32 - 1) / (ANT / 32);
+    df_tree_sum32(&lp[warp][0], (ANT / 32) * 33, nv, lane);
+    if (lane < nv) ys[warp + (ANT / 32) * lane] = lp[warp + (ANT / 32) * lane][0];
   }
   __syncthreads();
   // the block's share of X^T y: thread per column pair (c, c + 1), the block's rows r >= c
@@ -939,6 +964,7 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_multi_kernel(
     int64_t lds, int* __restrict__ done) {
   extern __shared__ float4 gsm[];                      // [NR][np]
   __shared__ float4 ysm[NR][AR / 2];
+  __shared__ float2 lpm[NR][AR][33];                   // lane partials of the y rows per right-hand side
   __shared__ int seg_c[AMAX_SUB + 1], seg_p[AMAX_SUB];
   __shared__ int64_t seg_w[AMAX_SUB];
   __shared__ int last;
@@ -1031,8 +1057,15 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_multi_kernel(
       df_add(h[rc][0], l[rc][0], h[rc][1], l[rc][1]);
       df_add(h[rc][2], l[rc][2], h[rc][3], l[rc][3]);
       df_add(h[rc][0], l[rc][0], h[rc][2], l[rc][2]);
-      df_warp_sum(h[rc][0], l[rc][0]);
-      if (lane == 0) reinterpret_cast<float2*>(ysm[rc])[rr] = make_float2(h[rc][0], l[rc][0]);
+      lpm[rc][rr][lane] = make_float2(h[rc][0], l[rc][0]);
+    }
+  }
+  if (warp < nr) {
+    const int nv = (nr - warp + ANT / 32 - 1) / (ANT / 32);
+#pragma unroll
+    for (int rc = 0; rc < NR; ++rc) {
+      df_tree_sum32(&lpm[rc][warp][0], (ANT / 32) * 33, nv, lane);
+      if (lane < nv) reinterpret_cast<float2*>(ysm[rc])[warp + (ANT / 32) * lane] = lpm[rc][warp + (ANT / 32) * lane][0];
     }
   }
   __syncthreads();
