@@ -44,8 +44,9 @@ constexpr int NW = NT / 32;
 
 // n_active: only threads tid < n_active hold non-zero values; warps wholly beyond
 // it skip their shuffle tree (their partial is zero either way, so the sum and
-// its order are unchanged).
-__device__ double block_sum(double v, double* red, int n_active = NT) {
+// its order are unchanged).  Returns scale * sum, the product formed once by
+// thread 0 (1.0 * sum is the sum itself).
+__device__ double block_sum(double v, double* red, int n_active = NT, double scale = 1.0) {
   if ((threadIdx.x & ~31) < n_active)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();
@@ -54,7 +55,7 @@ __device__ double block_sum(double v, double* red, int n_active = NT) {
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < NW; ++w) s += red[w];
-    red[32] = s;
+    red[32] = scale * s;
   }
   __syncthreads();
   return red[32];
@@ -180,6 +181,8 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
   const int SR = (m - 1 + TC * NW - 1) / (TC * NW);
   double* dpart = part + (int64_t)NW * m;
   __shared__ double red[33];
+  __shared__ double sbt;       // 2 / (v^T v) of the current reflector
+  __shared__ int sbt_nz;
   const int mat = blockIdx.x / TC;
   const int rank = (int)cluster.block_rank();
   double* A = Aall + (int64_t)mat * m * m;
@@ -195,17 +198,22 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
       loc += x * x;
     }
     const double sig2 = block_sum(loc, red, n1);
-    const double sigma = sqrt(sig2);
-    const double x0 = v[0];
-    const double alpha = (x0 >= 0.0) ? -sigma : sigma;
-    const double bt = (sigma > 0.0) ? 1.0 / (sig2 + fabs(x0) * sigma) : 0.0;   // 2 / (v^T v)
-    __syncthreads();
+    // the reflector's scalars once per block (thread 0), shared: GB300's
+    // float64 pipe would otherwise run the square root and the division for
+    // every warp
     if (tid == 0) {
+      const double sigma = sqrt(sig2);
+      const double x0 = v[0];
+      const double alpha = (x0 >= 0.0) ? -sigma : sigma;
+      const double b2 = (sigma > 0.0) ? 1.0 / (sig2 + fabs(x0) * sigma) : 0.0;   // 2 / (v^T v)
       v[0] = x0 - alpha;
-      if (rank == 0) { W.d[k] = A[(int64_t)k * m + k]; W.e[k] = alpha; W.beta[k] = bt; }
+      sbt = b2;
+      sbt_nz = b2 != 0.0;
+      if (rank == 0) { W.d[k] = A[(int64_t)k * m + k]; W.e[k] = alpha; W.beta[k] = b2; }
     }
     __syncthreads();
-    if (bt != 0.0) {
+    const double bt = sbt;
+    if (sbt_nz) {
       double* Ak = A + (int64_t)(k + 1) * m + (k + 1);       // A'[c][j] = Ak[c * m + j]
       double acc[SL];
 #pragma unroll
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(NT) syev_tridiag_kernel(double* __restrict__ A
         w[j] = s;
         pv = fma(s, v[j], pv);
       }
-      const double K = 0.5 * bt * block_sum(pv, red, n1);
+      const double K = block_sum(pv, red, n1, 0.5 * bt);
       for (int j = tid; j < n1; j += NT) w[j] = fma(-K, v[j], w[j]);
       __syncthreads();
       // A' -= v w^T + w v^T on the lower rows
