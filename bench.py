@@ -38,7 +38,7 @@ DF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12   # double-float multiply-
 # DRAM bytes of one launch of the kernel family (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu --set full capture of the same kernel code
 # on this workload); a family missing here reports null
-TRAFFIC = {}
+TRAFFIC = {"eig_tridiag": 28.54e6}
 # families whose profiled bracket spans a multi-stream pipeline of many kernels
 # (the Cholesky with lookahead and the row-block inverse): no single launch
 # duration, so they are reported as pipelines, not as the roofline kernel

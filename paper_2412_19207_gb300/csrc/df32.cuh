@@ -67,6 +67,15 @@ __device__ __forceinline__ float2 df_fast(float a, float b) {
   return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 
+// a * b in double-float (Dekker 1971): exact product of the high parts, the
+// cross terms added to its error, one fast renormalisation.
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = __fmaf_rn(a.x, b.x, -p);
+  const float t = __fadd_rn(e, __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+  return df_fast(p, t);
+}
+
 // a / b in double-float (Dekker 1971): q1 = a_h / b_h, r = a - q1 b formed with
 // an exact product, q2 = r_h / b_h; about 2^-46 relative.
 __device__ __forceinline__ float2 df_div(float2 a, float2 b) {

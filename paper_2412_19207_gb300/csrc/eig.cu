@@ -753,9 +753,13 @@ __global__ void __launch_bounds__(BW * 32) syev_back_kernel(const double* __rest
 
 // The same back-transformation in double-float for precision mode 1.  The
 // reflectors (upper part of A, row k from column k + 1) are split once into
-// the workspace (LU + m^2, row k at k m); then one warp per vector keeps z in
-// registers (entry lane + 32 t in slot t) and, for k = m - 3 .. 0, forms
-// s = beta_k v_k . z and z -= s v_k with double-float products (float32 pipe).
+// the workspace (LU + m^2, row k at k m), and so are the beta_k (after them;
+// a beta outside [1e-30, 1e30] is marked NaN and scaled in float64 instead);
+// then one warp per vector keeps z in registers (entry lane + 32 t in slot t)
+// and, for k = m - 3 .. 0, forms s = -beta_k v_k . z and z += s v_k with
+// double-float products (float32 pipe; GB300's float64 unit would otherwise
+// carry a conversion, product and split per reflector and vector).  Slots
+// wholly above row k + 1 hold zeros of v_k and are skipped.
 __global__ void __launch_bounds__(256) syev_back_split_kernel(const double* __restrict__ Aall, int m,
                                                               double* __restrict__ work_all, int64_t work_stride) {
   SyevWork W(work_all + blockIdx.y * work_stride, m);
@@ -765,6 +769,26 @@ __global__ void __launch_bounds__(256) syev_back_split_kernel(const double* __re
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(e / m), j = (int)(e % m);
     if (k + 1 + j < m) V2[e] = df_split(A[(int64_t)k * m + k + 1 + j]);
+  }
+  if (blockIdx.x == 0) {
+    float2* B2 = V2 + tot;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+      const double bt = W.beta[k];
+      const bool ok = bt == 0.0 || (fabs(bt) >= 1e-30 && fabs(bt) <= 1e30);
+      B2[k] = ok ? df_split(bt) : make_float2(__int_as_float(0x7fc00000), 0.f);
+    }
+  }
+}
+
+// Slot t of reflector k (entry lane + 32 t, zero outside k < i < m).
+template <int SL>
+__device__ __forceinline__ void back_load_reflector(const float2* __restrict__ V2, int m, int k, int lane,
+                                                    float2 (&v)[SL]) {
+  const float2* vk = V2 + (int64_t)k * m - (k + 1);       // vk[i] = v_k entry of z_i, i >= k + 1
+#pragma unroll
+  for (int t = 0; t < SL; ++t) {
+    const int i = lane + 32 * t;
+    v[t] = (i > k && i < m) ? vk[i] : make_float2(0.f, 0.f);
   }
 }
 
@@ -783,23 +807,45 @@ __global__ void __launch_bounds__(BW * 32) syev_back_df_kernel(int m, double* __
     const int i = lane + 32 * t;
     zr[t] = (i < m) ? df_split(z[i]) : make_float2(0.f, 0.f);
   }
+  const float2* B2 = V2 + (int64_t)m * m;
+  // reflector k - 1 is loaded while k is applied (the loop's only memory traffic)
+  float2 vn[SL];
+  float2 bn = make_float2(0.f, 0.f);
+  if (m >= 3) {
+    back_load_reflector<SL>(V2, m, m - 3, lane, vn);
+    bn = B2[m - 3];
+  }
   for (int k = m - 3; k >= 0; --k) {
-    const double bt = W.beta[k];
-    if (bt == 0.0) continue;
-    const float2* vk = V2 + (int64_t)k * m - (k + 1);       // vk[i] = v_k entry of z_i, i >= k + 1
     float2 vr[SL];
+#pragma unroll
+    for (int t = 0; t < SL; ++t) vr[t] = vn[t];
+    const float2 b2 = bn;
+    if (k > 0) {
+      back_load_reflector<SL>(V2, m, k - 1, lane, vn);
+      bn = B2[k - 1];
+    }
+    if (b2.x == 0.f) continue;                              // beta_k = 0
+    const int t0 = (k + 1) >> 5;                            // slots t < t0 lie above the reflector
     float h = 0.f, l = 0.f;
 #pragma unroll
     for (int t = 0; t < SL; ++t) {
-      const int i = lane + 32 * t;
-      vr[t] = (i > k && i < m) ? vk[i] : make_float2(0.f, 0.f);
+      if (t < t0) continue;
       df_mac(h, l, vr[t], zr[t]);
     }
     df_warp_sum(h, l);
     // s = -beta_k (v_k . z) as a double-float
-    const float2 sb = df_split(-bt * df_to_double(h, l));
+    float2 sb;
+    if (b2.x == b2.x) {
+      sb = df_mul(b2, make_float2(h, l));
+      sb = make_float2(-sb.x, -sb.y);
+    } else {
+      sb = df_split(-W.beta[k] * df_to_double(h, l));
+    }
 #pragma unroll
-    for (int t = 0; t < SL; ++t) df_mac(zr[t].x, zr[t].y, sb, vr[t]);
+    for (int t = 0; t < SL; ++t) {
+      if (t < t0) continue;
+      df_mac(zr[t].x, zr[t].y, sb, vr[t]);
+    }
   }
 #pragma unroll
   for (int t = 0; t < SL; ++t) {
