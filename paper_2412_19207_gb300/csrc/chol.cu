@@ -320,7 +320,7 @@ __global__ void trtri_diag_kernel(const CholMat* __restrict__ mats) {
 // X_ij = -X_ii sum_{j <= k < i} L_ik X_kj (k in increasing order, each block
 // product renormalised); the diagonal blocks X_ii were written by the
 // factorisation.  Row block i needs only L's rows of block i (final once
-// diagonal block i is factored) and X's row blocks below i, so it runs inside
+// diagonal block i is factored) and X's row blocks k < i, so it runs inside
 // the factorisation's pipeline, one launch per i; grid (j, matrix).
 __global__ void __launch_bounds__(256) trtri_row_df_kernel(const CholMat* __restrict__ mats, int i) {
   const CholMat M = mats[blockIdx.y];
