@@ -198,6 +198,21 @@ rann_status rann_dd_solve_bicg(rann_dd_handle* h, const double* F_dev, double* W
 rann_status rann_dd_solve_backward(rann_dd_handle* h, const double* gW_dev, double* lam_dev,
                                    double rtol, int maxit, rann_dd_stats* stats);
 
+/* Derivative of a loss through the solve with respect to the reaction
+ * coefficient c0 of the Poisson operator -Lap u + c0 u (the coefficient
+ * enters Sec. 2 Eq. (sum) linearly, and Psi_j, hence the PCA basis, does not
+ * depend on it): dH/dc0 = L Psi V and, for F from rann_dd_rhs, dF/dc0 = -G.
+ * Given F_dev [N] (the right-hand side the solve used), the solution W_dev
+ * [DoF] and lam_dev [DoF] = (H^T H)^{-1} dl/dW from rann_dd_solve_backward,
+ * *grad_host receives
+ *   dl/dc0 = r . (H_c lam) - (H lam) . G - (H lam) . (H_c W),   r = F - H W,
+ * for a loss that depends on c0 only through W.  H_c x is formed as
+ * u_hat(x) - G at the collocation points (rann_dd_eval).  All device
+ * pointers are the caller's; synchronises the stream.  RANN_EINVAL for other
+ * operators, RANN_EORDER before rann_dd_pca. */
+rann_status rann_dd_grad_c0(rann_dd_handle* h, const double* F_dev, const double* W_dev, const double* lam_dev,
+                            double* grad_host);
+
 /* Precision policy.  Mode 1 (default): the work that only shapes the
  * preconditioner or the Krylov iterates -- the neighbour Gram blocks of A_i,
  * the Cholesky trailing updates, L_i^{-1}, and every operator and

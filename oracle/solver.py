@@ -17,6 +17,9 @@ baseline use this package; the product path never does.
     overlap_level = 0 it selects subdomain i's own unknowns only.
   * Sec. 5: u_hat = L sum_j omega_j (V_{p_j}^T Phi_j) . W_j + G (Eq. (netdd)),
     relative L2 error and normalised L1 error at test points.
+  * Differentiation through the least-squares solve (an extension; the
+    paper does not differentiate): grad_c0, the derivative of a loss l(W)
+    with respect to the reaction coefficient c0 of -Lap u + c0 u.
 """
 from __future__ import annotations
 
@@ -227,6 +230,35 @@ def solve_qr(S: System) -> Solution:
     bvec = S.HT(S.F)
     return Solution(W, 0, [], np.linalg.norm(S.HT(res)) / np.linalg.norm(bvec),
                     np.linalg.norm(res))
+
+
+# ---------------------------------------------------------- differentiation --
+
+def grad_c0(S: System, W: np.ndarray, lam: np.ndarray) -> float:
+    """dl/dc0 of a loss l(W) through W(c0) = argmin ||H W - F|| (Sec. 2 Eq.
+    (system), normal equations), given lam = (H^T H)^{-1} dl/dW, for the
+    operator -Lap u + c0 u.  Psi_j and hence the PCA basis V do not depend on
+    c0; the reaction term adds c0 L omega_j phi_j to the entries of H_j
+    (Sec. 2 Eq. (sum)) and -c0 G to F = f - A[G], so dH/dc0 = H_c with
+    (H_c)_j = L Psi_j V_j and dF/dc0 = -G.  Differentiating
+    H^T H W = H^T F gives, with r = F - H W,
+        dl/dc0 = r . (H_c lam) + (H lam) . (-G) - (H lam) . (H_c W).
+    """
+    p = S.problem
+    xs = asm._coords(ri.grid_points(p), -1)
+    Lx = asm.constraint_L(p, xs).a
+    Gx = asm.constraint_G(p, xs).a
+    Psis = [asm.block(p, S.R, S.b, j)[1] for j in range(len(S.B))]
+
+    def Hc(x: np.ndarray) -> np.ndarray:
+        y = np.zeros(S.n_rows)
+        for j, Psi in enumerate(Psis):
+            np.add.at(y, S.rows[j], Psi @ (S.pcas[j].V @ x[S.offsets[j]:S.offsets[j + 1]]))
+        return Lx * y
+
+    r = S.F - S.H(W)
+    Hl = S.H(lam)
+    return float(r @ Hc(lam) - Hl @ Gx - Hl @ Hc(W))
 
 
 # --------------------------------------------------------------- evaluation --

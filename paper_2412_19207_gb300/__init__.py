@@ -91,6 +91,7 @@ SIGNATURES = {
     "rann_dd_solve_bicg": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
     "rann_dd_eval": (_I, [_P, _P, _P, _L, _P]),
     "rann_dd_solve_backward": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
+    "rann_dd_grad_c0": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D)]),
     "rann_dd_set_precision": (_I, [_P, _I]),
     "rann_dd_matvec": (_I, [_P, _P, _P]),
     "rann_dd_matvec_t": (_I, [_P, _P, _P]),
@@ -318,6 +319,14 @@ class RannDD:
         s = self._lib.rann_dd_solve_backward(self._h, _dptr(gW), _dptr(lam), rtol, maxit, ctypes.byref(st))
         _check(s, "rann_dd_solve_backward")
         return lam, st.as_dict() | {"status": STATUS[s]}
+
+    def grad_c0(self, F, W, lam) -> float:
+        """dl/dc0 through the solve for -Lap u + c0 u, given the right-hand side F,
+        the solution W and lam = (H^T H)^{-1} dl/dW (rann_dd_grad_c0)."""
+        out = _D(0.0)
+        _check(self._lib.rann_dd_grad_c0(self._h, _dptr(F), _dptr(W), _dptr(lam), ctypes.byref(out)),
+               "rann_dd_grad_c0")
+        return out.value
 
     def solve(self, F, rtol=1e-10, maxit=2000, restart=50):
         """The solve matching the preconditioner: AS-CG for AS/none, GMRES otherwise."""

@@ -1968,6 +1968,42 @@ extern "C" rann_status rann_dd_solve_backward(rann_dd_handle* h, const double* g
   return solve_gmres_impl(h, nullptr, gW_dev, lam_dev, rtol, 50, maxit, stats);
 }
 
+// dl/dc0 of a loss l(W) through the least-squares solve, for -Lap u + c0 u
+// (the coefficient enters H linearly: dH/dc0 = L Psi V, dF/dc0 = -G).  With
+// r = F - H W and lam = (H^T H)^{-1} dl/dW (rann_dd_solve_backward),
+//   dl/dc0 = r . (H_c lam) - (H lam) . G - (H lam) . (H_c W),
+// where H_c x = u_hat(x) - G at the collocation points (u_hat of Eq. (netdd)
+// with weights x), so every term comes from the evaluation kernel, the block
+// matvec and fixed-order dot products.
+extern "C" rann_status rann_dd_grad_c0(rann_dd_handle* h, const double* F_dev, const double* W_dev,
+                                       const double* lam_dev, double* grad_host) {
+  REQUIRE(h && F_dev && W_dev && lam_dev && grad_host, RANN_EINVAL, "null argument");
+  REQUIRE(h->reduced, RANN_EORDER, "grad_c0 before pca");
+  REQUIRE(h->P.op == RANN_OP_POISSON, RANN_EINVAL, "grad_c0: c0 is a coefficient of the Poisson operator only");
+  const int64_t N = h->N, dof = h->dof;
+  double *x, *zero, *g0, *eW, *eL, *r, *hl;
+  CK(dalloc(h, (void**)&x, sizeof(double) * (size_t)N * h->dim));
+  CK(dalloc(h, (void**)&zero, sizeof(double) * (size_t)std::max<int64_t>(dof, 1)));
+  for (double** q : {&g0, &eW, &eL, &r, &hl}) CK(dalloc(h, (void**)q, sizeof(double) * (size_t)N));
+  CK(cudaMemsetAsync(zero, 0, sizeof(double) * (size_t)std::max<int64_t>(dof, 1), h->st));
+  TRY(rann_dd_points(h, x));
+  TRY(rann_dd_eval(h, zero, x, N, g0));                       // G
+  TRY(rann_dd_eval(h, W_dev, x, N, eW));
+  TRY(rann_dd_eval(h, lam_dev, x, N, eL));
+  KL(h, K_VEC, 1, launch_axpby(-1.0, g0, 1.0, eW, N, h->st));   // H_c W
+  KL(h, K_VEC, 1, launch_axpby(-1.0, g0, 1.0, eL, N, h->st));   // H_c lam
+  TRY(rann_dd_matvec(h, W_dev, r));
+  KL(h, K_VEC, 1, launch_axpby(1.0, F_dev, -1.0, r, N, h->st));  // r = F - H W
+  TRY(rann_dd_matvec(h, lam_dev, hl));                           // H lam
+  double d1 = 0.0, d2 = 0.0, d3 = 0.0;
+  TRY(dot_host(h, r, eL, N, &d1));
+  TRY(dot_host(h, hl, g0, N, &d2));
+  TRY(dot_host(h, hl, eW, N, &d3));
+  *grad_host = d1 - d2 - d3;
+  for (double* q : {x, zero, g0, eW, eL, r, hl}) dfree(h, q);
+  return RANN_OK;
+}
+
 extern "C" rann_status rann_dd_set_precision(rann_dd_handle* h, int mode) {
   REQUIRE(h, RANN_EINVAL, "null handle");
   REQUIRE(mode == 0 || mode == 1, RANN_EINVAL, "precision mode must be 0 (float64) or 1 (double-float)");

@@ -103,3 +103,71 @@ def test_backward_needs_a_preconditioner(g):
     with pytest.raises(g.RannError) as e:
         s.solve_backward(z)
     assert e.value.status == g.EORDER
+
+
+# ---- derivative with respect to the reaction coefficient c0 (rann_dd_grad_c0) ----
+
+def _poisson_c0(g, c0, mode, rtol):
+    import dataclasses
+    p = dataclasses.replace(ri.config("poisson2d_2x2", small=True), c0=c0, g_kind=ri.G_SINPROD)
+    s = g.RannDD(p)
+    s.set_precision(mode)
+    s.assemble()
+    F = s.rhs()
+    s.pca(p.pca_mode, p.pca_thr)
+    s.setup_precond("as")
+    W, st = s.solve_cg_as(F, rtol, 200)
+    assert st["status"] == "RANN_OK"
+    return p, s, F, W
+
+
+def test_grad_c0_matches_central_differences(g):
+    """l = c . W(c0), c = H^T v, in float64 (precision mode 0): on the 2x2 layout AS-CG
+    solves to rounding in a step or two, so central differences of the GPU
+    solves resolve dl/dc0 (the PCA basis does not depend on c0)."""
+    p, s, F, W = _poisson_c0(g, 0.7, 0, 1e-12)
+    v = torch.tensor(np.random.default_rng(21).standard_normal(F.numel()), device="cuda")
+    c = s.matvec_t(v)                                      # dl/dW in range(H^T), as above
+    lam, st = s.solve_backward(c, 1e-12, 200)
+    grad = s.grad_c0(F, W, lam)
+    h = 1e-4
+    lp = float((c * _poisson_c0(g, 0.7 + h, 0, 1e-12)[3]).sum())
+    lm = float((c * _poisson_c0(g, 0.7 - h, 0, 1e-12)[3]).sum())
+    fd = (lp - lm) / (2 * h)
+    assert abs(grad - fd) <= 1e-4 * abs(fd), (grad, fd)
+
+
+def test_grad_c0_matches_the_oracle_formula(g):
+    """The same formula in the oracle (dense blocks, L Psi V from the oracle's
+    assembly) at the GPU's W, lam and PCA basis."""
+    from oracle import assembly as asm
+    from oracle import solver as sv
+    p, s, F, W = _poisson_c0(g, 0.4, 1, 1e-9)
+    v = torch.tensor(np.random.default_rng(22).standard_normal(F.numel()), device="cuda")
+    c = s.matvec_t(v)
+    lam, st = s.solve_backward(c, 1e-9, 200)
+    grad = s.grad_c0(F, W, lam)
+    R, b = ri.weights(p)
+    rows, Bs, pcas = [], [], []
+    for j in range(p.J):
+        r, Psi, Hj = asm.block(p, R, b, j)
+        eig, V = s.pca_of(j)
+        rows.append(r)
+        Bs.append(Hj @ V)
+        pcas.append(sv.PCA(np.sqrt(np.maximum(eig, 0.0)), V, V.shape[1], False))
+    offs = np.concatenate([[0], np.cumsum([B.shape[1] for B in Bs])]).astype(np.int64)
+    Sg = sv.System(p, R, b, rows, Bs, pcas, asm.rhs(p), offs)
+    expect = sv.grad_c0(Sg, W.cpu().numpy(), lam.cpu().numpy())
+    assert abs(grad - expect) <= 1e-7 * abs(expect), (grad, expect)
+
+
+def test_grad_c0_needs_the_poisson_operator(g):
+    p = ri.config("multiscale2d", small=True)
+    s = g.RannDD(p)
+    s.assemble()
+    F = s.rhs()
+    s.pca(p.pca_mode, p.pca_thr)
+    W = torch.zeros(int(s.sizes()["dof"]), dtype=torch.float64, device="cuda")
+    with pytest.raises(g.RannError) as e:
+        s.grad_c0(F, W, W)
+    assert e.value.status == g.EINVAL

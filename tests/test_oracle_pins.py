@@ -508,6 +508,52 @@ def test_manufactured_solution_accuracy():
     assert e2 < 1e-3 and e1 < 1e-3
 
 
+# ------------------------------------------------------- differentiation --
+
+def _lstsq_and_adjoint(S, c):
+    """W = H^+ F and lam = (H^T H)^{-1} c from one SVD of the dense H."""
+    U, sg, Vt = np.linalg.svd(S.dense(), full_matrices=False)
+    W = Vt.T @ ((U.T @ S.F) / sg)
+    lam = Vt.T @ ((Vt @ c) / sg ** 2)
+    return W, lam
+
+
+@pytest.mark.parametrize("c0,loss_kind,g_kind", [(0.0, "linear", ri.G_ZERO), (0.7, "linear", ri.G_SINPROD),
+                                                  (0.3, "quadratic", ri.G_SINPROD)])
+def test_grad_c0_is_the_derivative_of_the_least_squares_solution(c0, loss_kind, g_kind):
+    """grad_c0 against central differences of l(W(c0)) for a loss that depends
+    on c0 only through the least-squares solution W(c0) of -Lap u + c0 u:
+    l = c . W, or l = 1/2 ||W - w0||^2 (dl/dW = W - w0); with G = 0 and with
+    G = prod sin(pi x_i) (so each of the formula's three terms is exercised).
+    The PCA basis does not depend on c0, which the test checks."""
+    import dataclasses
+    p = dataclasses.replace(ri.config("poisson2d_2x2", small=True), c0=c0, g_kind=g_kind)
+    R, b = ri.weights(p)
+    S = sv.build_system(p, R, b)
+    rng = np.random.default_rng(11)
+    c = rng.standard_normal(S.dof)
+    w0 = rng.standard_normal(S.dof)
+
+    def loss_and_grad(W):
+        if loss_kind == "linear":
+            return float(c @ W), c
+        return 0.5 * float(np.sum((W - w0) ** 2)), W - w0
+
+    W, _ = _lstsq_and_adjoint(S, c)
+    _, lam = _lstsq_and_adjoint(S, loss_and_grad(W)[1])
+    grad = sv.grad_c0(S, W, lam)
+    h = 1e-4
+
+    def loss(c0v):
+        S2 = sv.build_system(dataclasses.replace(p, c0=c0v), R, b)
+        for pa, pb in zip(S.pcas, S2.pcas):
+            np.testing.assert_array_equal(pa.V, pb.V)
+        return loss_and_grad(_lstsq_and_adjoint(S2, c)[0])[0]
+
+    fd = (loss(c0 + h) - loss(c0 - h)) / (2 * h)
+    assert abs(grad - fd) <= 2e-5 * abs(fd)
+
+
 # ------------------------------------------------------ planted mistakes --
 
 def test_planted_dropped_window_normalisation_is_caught(monkeypatch):
