@@ -243,41 +243,53 @@ def bench_ours(args, rank, world):
         "clocks": clocks,
     }
     if args.multi_rhs > 0:
-        out["multi_rhs"] = multi_rhs_timing(g, p, R, b, args.multi_rhs)
+        out["multi_rhs"] = [multi_rhs_timing(g, p, R, b, args.multi_rhs, "cg"),
+                            multi_rhs_timing(g, p, R, b, args.multi_rhs, "gmres")]
     return out
 
 
-def multi_rhs_timing(g, p, R, b, k):
-    """AS-preconditioned CG on k right-hand sides of the workload (F scaled by
-    1..k, so every column runs the same iterations): k one-column solves one
-    after another against one lockstep solve of all k (every launch serves all
-    columns).  Both after a warm-up solve; wall time with the device
-    synchronised on both sides (the solves include their host round trips)."""
+def multi_rhs_timing(g, p, R, b, k, solver="cg"):
+    """k right-hand sides of the workload (F scaled by 1..k, so every column
+    runs the same iterations): k one-column solves one after another against
+    one lockstep solve of all k (every operator and preconditioner launch
+    serves all columns).  solver "cg": AS-preconditioned CG; "gmres": the
+    workload's SAS-preconditioned GMRES(50).  Both after a warm-up solve; wall
+    time with the device synchronised on both sides (the solves include their
+    host round trips)."""
     import torch
     s = g.RannDD(p, R, b)
     s.assemble()
     F = s.rhs()
     s.pca(p.pca_mode, p.pca_thr)
-    s.setup_precond("as")
+    s.setup_precond("as" if solver == "cg" else p.precond)
     Fs = torch.stack([F * float(c + 1) for c in range(k)])
-    s.solve_cg_as(F, p.rtol, 4000)
-    s.solve_cg_as_multi(Fs[:1].contiguous(), p.rtol, 4000)
+    if solver == "cg":
+        one = lambda f: s.solve_cg_as(f, p.rtol, 4000)
+        multi = lambda fs: s.solve_cg_as_multi(fs, p.rtol, 4000)
+        ok = lambda st: st["rel_res_true"] <= p.rtol
+    else:
+        one = lambda f: s.solve_gmres_ras(f, p.rtol, p.restart, 4000)
+        multi = lambda fs: s.solve_gmres_ras_multi(fs, p.rtol, p.restart, 4000)
+        ok = lambda st: st["rel_res_prec"] <= p.rtol
+    one(F)
+    multi(Fs[:1].contiguous())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     iters = []
     for c in range(k):
-        _, st = s.solve_cg_as(Fs[c].contiguous(), p.rtol, 4000)
+        _, st = one(Fs[c].contiguous())
         iters.append(st["iters"])
     torch.cuda.synchronize()
     t_one = time.perf_counter() - t0
     t0 = time.perf_counter()
-    _, sts = s.solve_cg_as_multi(Fs, p.rtol, 4000)
+    _, sts = multi(Fs)
     torch.cuda.synchronize()
     t_multi = time.perf_counter() - t0
     s.close()
-    return {"nrhs": k, "solver": "AS-CG", "iters": iters[0], "ms_one_at_a_time": round(t_one * 1e3, 3),
+    return {"nrhs": k, "solver": "AS-CG" if solver == "cg" else f"{p.precond.upper()}-GMRES({p.restart})",
+            "iters": iters[0], "ms_one_at_a_time": round(t_one * 1e3, 3),
             "ms_lockstep": round(t_multi * 1e3, 3), "ms_per_rhs_lockstep": round(t_multi * 1e3 / k, 3),
-            "speedup": round(t_one / t_multi, 3), "all_converged": all(x["rel_res_true"] <= p.rtol for x in sts)}
+            "speedup": round(t_one / t_multi, 3), "all_converged": all(ok(x) for x in sts)}
 
 
 def cpu_sample(args):
@@ -326,7 +338,8 @@ def main():
     ap.add_argument("--iters-hint", type=int, default=71)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--multi-rhs", type=int, default=0,
-                    help="also time AS-CG on this many right-hand sides in lockstep against one at a time")
+                    help="also time AS-CG and the workload's GMRES on this many right-hand sides in lockstep "
+                         "against one at a time")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

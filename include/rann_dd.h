@@ -267,10 +267,19 @@ rann_status rann_dd_precond_apply_t(rann_dd_handle* h, const double* r_dev, doub
  * of the one-column solve (same iterates while a column is below its own
  * maxit).  The return value is the first non-OK column status (RANN_OK if
  * all converged).  With the float64 factors (precision mode 0) or without
- * the block-row operator the columns are solved one after another. */
+ * the block-row operator the columns are solved one after another.
+ * rann_dd_solve_gmres_ras_multi: rann_dd_solve_gmres_ras for every column in
+ * the same way: each Arnoldi step applies the block-row operator and the
+ * Schwarz preconditioner to all columns' current basis vectors at once; the
+ * Gram-Schmidt passes, the Givens bookkeeping, the restarts and the float64
+ * residual decisions are per column, so every column equals the one-column
+ * solve (a column that converged keeps stepping with a frozen Hessenberg
+ * matrix while others run). */
 rann_status rann_dd_precond_apply_multi(rann_dd_handle* h, const double* R_dev, double* Z_dev, int nrhs);
 rann_status rann_dd_solve_cg_as_multi(rann_dd_handle* h, const double* F_dev, double* W_dev, int nrhs,
                                       double rtol, int maxit, rann_dd_stats* stats);
+rann_status rann_dd_solve_gmres_ras_multi(rann_dd_handle* h, const double* F_dev, double* W_dev, int nrhs,
+                                          double rtol, int restart, int maxit, rann_dd_stats* stats);
 
 /* Inspection (synchronising copies to host memory).
  * which = 0: Psi_j, 1: H_j (both N_j x m, after assemble, before pca);

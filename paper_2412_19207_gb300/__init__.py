@@ -100,6 +100,7 @@ SIGNATURES = {
     "rann_dd_precond_apply_t": (_I, [_P, _P, _P]),
     "rann_dd_precond_apply_multi": (_I, [_P, _P, _P, _I]),
     "rann_dd_solve_cg_as_multi": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Stats)]),
+    "rann_dd_solve_gmres_ras_multi": (_I, [_P, _P, _P, _I, _D, _I, _I, ctypes.POINTER(Stats)]),
     "rann_dd_block_info": (_I, [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_I)]),
     "rann_dd_get_block": (_I, [_P, _I, _I, _P, _P]),
     "rann_dd_get_pca": (_I, [_P, _I, _P, _P]),
@@ -288,6 +289,16 @@ class RannDD:
         st = (Stats * max(nrhs, 1))()
         s = self._lib.rann_dd_solve_cg_as_multi(self._h, _dptr(F), _dptr(W), nrhs, rtol, maxit, st)
         _check(s, "rann_dd_solve_cg_as_multi", allow=(NOT_CONVERGED,) if allow_not_converged else ())
+        return W, [st[c].as_dict() for c in range(nrhs)]
+
+    def solve_gmres_ras_multi(self, F, rtol=1e-10, restart=50, maxit=2000, W=None, allow_not_converged=False):
+        """Left-preconditioned GMRES(restart) for the rows of F ([nrhs][N], device
+        float64) in lockstep; returns W [nrhs][DoF] and one stats dict per row."""
+        nrhs = int(F.shape[0])
+        W = W if W is not None else self._empty(nrhs * self.sizes()["dof"]).reshape(nrhs, -1)
+        st = (Stats * max(nrhs, 1))()
+        s = self._lib.rann_dd_solve_gmres_ras_multi(self._h, _dptr(F), _dptr(W), nrhs, rtol, restart, maxit, st)
+        _check(s, "rann_dd_solve_gmres_ras_multi", allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return W, [st[c].as_dict() for c in range(nrhs)]
 
     def solve_gmres_ras(self, F, rtol=1e-10, restart=50, maxit=2000, W=None, allow_not_converged=False):

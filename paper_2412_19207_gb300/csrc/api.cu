@@ -1955,6 +1955,215 @@ extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* 
   return solve_gmres_impl(h, F_dev, nullptr, W_dev, rtol, restart, maxit, stats);
 }
 
+// Left-preconditioned GMRES(k) for nr right-hand sides in lockstep: each
+// Arnoldi step applies the block-row operator and the Schwarz preconditioner
+// to every column's current basis vector in one launch each (block rows and
+// factor rows read once per step for up to four columns); the Gram-Schmidt
+// passes, the Givens bookkeeping (own device state and done flag per column),
+// the restarts and the float64 residual decisions are per column with the
+// arithmetic of solve_gmres_impl, so every column equals the one-column
+// solve.  A column that converged keeps stepping while others run; its
+// Givens step is then a no-op and zeroes its next basis vector.
+static rann_status solve_gmres_multi_impl(rann_dd_handle* h, const double* F_dev, double* W_dev, int nr,
+                                          double rtol, int restart, int maxit, rann_dd_stats* stats) {
+  REQUIRE(h && F_dev && W_dev && nr >= 0, RANN_EINVAL, "null argument or nrhs < 0");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve before setup_precond");
+  REQUIRE(rtol > 0 && maxit >= 0 && restart >= 1 && restart <= GMRES_MAX_RESTART, RANN_EINVAL,
+          "bad rtol/restart/maxit");
+  const int64_t n = h->dof, N = h->N;
+  if (nr == 0) return RANN_OK;
+  if (!multi_batched(h)) {                         // one right-hand side after another
+    rann_status worst = RANN_OK;
+    for (int c = 0; c < nr; ++c) {
+      const rann_status st = solve_gmres_impl(h, F_dev + c * N, nullptr, W_dev + c * n, rtol, restart, maxit,
+                                              stats ? stats + c : nullptr);
+      if (st != RANN_OK && worst == RANN_OK) worst = st;
+    }
+    return worst;
+  }
+  const int k = restart;
+  const size_t nv = (size_t)nr * n, lv = (size_t)(k + 1) * n;      // lv: one column's basis
+  const size_t nstate = (size_t)(k + 1) * k + 2 * k + (k + 1) + 3 * (k + 2) + 4;
+  Workspace ws{h, {}};
+  double *b = ws.get(nv), *t = ws.get(nv), *z = ws.get(nv), *V = ws.get(nr * lv);
+  double *state = ws.get(nr * nstate), *hvy = ws.get((size_t)nr * (k + 2)), *sc = ws.get((size_t)2 * nr + 2);
+  REQUIRE(b && t && z && V && state && hvy && sc, RANN_ENOMEM, "workspace allocation failed");
+  int* d_done = reinterpret_cast<int*>(sc);                // nr flags, then nr step counts
+  int* d_jdone = d_done + nr;
+  std::vector<GmresDev> sd(nr);
+  for (int c = 0; c < nr; ++c) {
+    GmresDev& q = sd[c];
+    q.H = state + c * nstate;
+    q.cs = q.H + (size_t)(k + 1) * k;
+    q.sn = q.cs + k;
+    q.g = q.sn + k;
+    q.hv = q.g + (k + 1);
+    q.hcol = q.hv + 2 * (k + 2);
+    q.ww = q.hcol + (k + 2);
+    q.inv = q.ww + 1;
+    q.rel = q.inv + 1;
+    q.done = d_done + c;
+    q.jdone = d_jdone + c;
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, h->st));
+  for (int c = 0; c < nr; ++c) TRY(rann_dd_matvec_t(h, F_dev + c * N, b + c * n));
+  CK(cudaMemsetAsync(W_dev, 0, sizeof(double) * nv, h->st));
+  // ||M^{-1} b|| per column
+  TRY(prec_apply_multi(h, b, z, nr, ws));
+  std::vector<double> mbb(nr), mbnorm(nr), bb(nr), beta(nr), rel(nr, 1.0), Hm((size_t)(k + 1) * k), g(k + 1), y(k);
+  KLA(h, K_DOT, 1, 16.0 * nv, 2.0 * nv, launch_dot_multi(z, n, z, n, n, nr, t, h->st));
+  CK(cudaMemcpyAsync(mbb.data(), t, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->st));
+  CK(stream_sync(h));
+  std::vector<int> it(nr, 0), active(nr, 1), first(nr, 1), jmaxc(nr, 0), hd(nr), hj(nr);
+  std::vector<rann_status> st(nr, RANN_NOT_CONVERGED);
+  for (int c = 0; c < nr; ++c) {
+    mbnorm[c] = std::sqrt(mbb[c]);
+    if (!(mbnorm[c] > 0.0)) {
+      st[c] = std::isfinite(mbb[c]) ? RANN_OK : RANN_BREAKDOWN;
+      rel[c] = 0.0;
+      active[c] = 0;
+    }
+  }
+  struct Events {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~Events() { for (auto x : e) if (x) cudaEventDestroy(x); }
+  } evh;
+  for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&evh.e[i], cudaEventDisableTiming));
+  int* hdone = reinterpret_cast<int*>(h->h_scal + 128);
+  auto any_active = [&]() { for (int c = 0; c < nr; ++c) if (active[c]) return true; return false; };
+  while (any_active()) {
+    // r_c = M^{-1}(b_c - A W_c) with the float64 operator (W_c = 0 on a column's first cycle)
+    for (int c = 0; c < nr; ++c) {
+      if (!active[c]) continue;
+      if (first[c]) {
+        CK(cudaMemcpyAsync(t + c * n, b + c * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+      } else {
+        TRY(rann_dd_normal_matvec(h, W_dev + c * n, t + c * n));
+        KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b + c * n, -1.0, t + c * n, n, h->st));
+      }
+      first[c] = 0;
+    }
+    TRY(prec_apply_multi(h, t, z, nr, ws));
+    KLA(h, K_DOT, 1, 16.0 * nv, 2.0 * nv, launch_dot_multi(z, n, z, n, n, nr, t, h->st));
+    CK(cudaMemcpyAsync(bb.data(), t, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->st));
+    CK(stream_sync(h));
+    int jmax = 0;
+    for (int c = 0; c < nr; ++c) {
+      hd[c] = 1;
+      if (!active[c]) continue;
+      beta[c] = std::sqrt(bb[c]);
+      rel[c] = beta[c] / mbnorm[c];
+      if (!std::isfinite(rel[c])) { st[c] = RANN_BREAKDOWN; active[c] = 0; continue; }
+      if (rel[c] <= rtol) { st[c] = RANN_OK; active[c] = 0; continue; }
+      if (it[c] >= maxit) { active[c] = 0; continue; }
+      double* Vc = V + c * lv;
+      KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_copy(1.0 / beta[c], z + c * n, Vc, n, h->st));
+      CK(cudaMemsetAsync(sd[c].g, 0, sizeof(double) * (k + 1), h->st));
+      CK(cudaMemcpyAsync(sd[c].g, &beta[c], sizeof(double), cudaMemcpyHostToDevice, h->st));
+      hd[c] = 0;
+      jmaxc[c] = std::min(k, maxit - it[c]);         // a column past its step count launches nothing
+      jmax = std::max(jmax, jmaxc[c]);
+    }
+    if (!any_active()) break;
+    CK(cudaMemcpyAsync(d_done, hd.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemsetAsync(d_jdone, 0, sizeof(int) * nr, h->st));
+    *hdone = 0;
+    for (int j = 0; j < jmax; ++j) {
+      if (j >= 2) {
+        CK(cudaEventSynchronize(evh.e[(j - 2) % 3]));
+        if (*(volatile int*)hdone) break;
+      }
+      KLA(h, K_GRAMOP, 1, 8.0 * (h->gram_entries + nv), 2.0 * h->gram_entries * nr,
+          launch_gram_matvec_multi(h->gram, h->J, h->d_gtile, h->ngtile, h->gram_maxn2, V + (size_t)j * n, lv, t,
+                                   n, nr, h->st));
+      TRY(prec_apply_multi(h, t, z, nr, ws));
+      for (int c = 0; c < nr; ++c) {
+        if (!active[c] || j >= jmaxc[c]) continue;
+        double* Vc = V + c * lv;
+        double* w = Vc + (size_t)(j + 1) * n;
+        CK(cudaMemcpyAsync(w, z + c * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+        for (int pass = 0; pass < 2; ++pass) {
+          KLA(h, K_DOT, 1, 8.0 * n * (j + 2), 2.0 * n * (j + 1),
+              launch_multidot(Vc, n, j + 1, w, n, h->d_red, sd[c].hv + pass * (k + 2), h->st));
+          KLA(h, K_VEC, 1, 8.0 * n * (j + 3), 2.0 * n * (j + 1),
+              launch_sub_combination(Vc, n, j + 1, sd[c].hv + pass * (k + 2), w, n, h->st));
+        }
+        KLA(h, K_DOT, 1, 8.0 * n, 2.0 * n, launch_multidot(w, 0, 1, w, n, h->d_red, sd[c].ww, h->st));
+        KLA(h, K_VEC, 1, 0, 0, launch_gmres_givens(sd[c], j, k, mbnorm[c], rtol, h->st));
+        KLA(h, K_VEC, 1, 16.0 * n, 1.0 * n, launch_scale_dev(w, sd[c].inv, n, h->st));
+      }
+      KLA(h, K_VEC, 1, 0, 0, launch_all_done(d_done, nr, h->d_scal + 64, h->st));
+      CK(cudaMemcpyAsync(hdone, h->d_scal + 64, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaEventRecord(evh.e[j % 3], h->st));
+    }
+    std::vector<double> hrel(nr);
+    std::vector<double> state_rel(nr);
+    CK(cudaMemcpyAsync(hd.data(), d_done, sizeof(int) * nr, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(hj.data(), d_jdone, sizeof(int) * nr, cudaMemcpyDeviceToHost, h->st));
+    for (int c = 0; c < nr; ++c)
+      if (active[c]) CK(cudaMemcpyAsync(&state_rel[c], sd[c].rel, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(stream_sync(h));
+    for (int c = 0; c < nr; ++c) {
+      if (!active[c]) continue;
+      const int jdone = hj[c];
+      it[c] += jdone;
+      rel[c] = jdone == 0 ? beta[c] / mbnorm[c] : state_rel[c];
+      if (hd[c] == 2) { st[c] = RANN_BREAKDOWN; active[c] = 0; continue; }
+      if (jdone == 0) { active[c] = 0; continue; }
+      CK(cudaMemcpyAsync(Hm.data(), sd[c].H, sizeof(double) * (size_t)jdone * k, cudaMemcpyDeviceToHost, h->st));
+      CK(cudaMemcpyAsync(g.data(), sd[c].g, sizeof(double) * jdone, cudaMemcpyDeviceToHost, h->st));
+      CK(stream_sync(h));
+      for (int i = jdone - 1; i >= 0; --i) {
+        double sacc = g[i];
+        for (int q = i + 1; q < jdone; ++q) sacc -= Hm[(size_t)i * k + q] * y[q];
+        y[i] = Hm[(size_t)i * k + i] != 0.0 ? sacc / Hm[(size_t)i * k + i] : 0.0;
+      }
+      double* yc = hvy + (size_t)c * (k + 2);
+      CK(cudaMemcpyAsync(yc, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, h->st));
+      KLA(h, K_VEC, 1, 8.0 * n * (jdone + 2), 2.0 * n * jdone,
+          launch_add_combination(V + c * lv, n, jdone, yc, W_dev + c * n, n, h->st));
+      CK(stream_sync(h));
+    }
+  }
+  // the float64 relative residual of every column
+  std::vector<double> bb2(nr), tr(nr);
+  KLA(h, K_DOT, 1, 16.0 * nv, 2.0 * nv, launch_dot_multi(b, n, b, n, n, nr, t, h->st));
+  CK(cudaMemcpyAsync(bb2.data(), t, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->st));
+  CK(stream_sync(h));
+  for (int c = 0; c < nr; ++c) {
+    TRY(rann_dd_normal_matvec(h, W_dev + c * n, z + c * n));
+    KLA(h, K_VEC, 1, 24.0 * n, 3.0 * n, launch_axpby(1.0, b + c * n, -1.0, z + c * n, n, h->st));
+  }
+  KLA(h, K_DOT, 1, 16.0 * nv, 2.0 * nv, launch_dot_multi(z, n, z, n, n, nr, t, h->st));
+  CK(cudaMemcpyAsync(tr.data(), t, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaEventRecord(e1, h->st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  rann_status worst = RANN_OK;
+  for (int c = 0; c < nr; ++c) {
+    if (stats) {
+      stats[c].iters = it[c];
+      stats[c].rel_res_true = bb2[c] > 0 ? std::sqrt(tr[c] / bb2[c]) : 0.0;
+      stats[c].rel_res_rec = rel[c];
+      stats[c].rel_res_prec = rel[c];
+      stats[c].ms_solve = ms;
+      stats[c].n_shifted = h->n_shifted;
+    }
+    if (st[c] != RANN_OK && worst == RANN_OK) worst = st[c];
+  }
+  if (worst == RANN_NOT_CONVERGED) rann_set_error("GMRES (many right-hand sides) reached maxit=%d", maxit);
+  return worst;
+}
+
+extern "C" rann_status rann_dd_solve_gmres_ras_multi(rann_dd_handle* h, const double* F_dev, double* W_dev, int nrhs,
+                                                     double rtol, int restart, int maxit, rann_dd_stats* stats) {
+  return solve_gmres_multi_impl(h, F_dev, W_dev, nrhs, rtol, restart, maxit, stats);
+}
+
 // Adjoint of the least-squares solve.  W = (H^T H)^{-1} H^T F, so for a loss
 // l(W) the sensitivity to F is H lam with (H^T H) lam = dl/dW: the same
 // symmetric normal matrix, solved with the stored preconditioner (CG when it

@@ -85,3 +85,23 @@ def test_cg_multi_solution_matches_the_oracle(g):
         # u_hat is affine in W through the boundary term G: compare the W-linear parts
         g0 = s.eval(torch.zeros_like(W[c]), torch.tensor(X, device="cuda")).cpu().numpy()
         assert np.linalg.norm((ug - g0) - f * (uo - g0)) <= 1e-5 * f * np.linalg.norm(uo - g0)
+
+
+@pytest.mark.parametrize("kind,mode", [("sas", 1), ("ras", 1), ("ras", 0)])
+def test_gmres_multi_columns_equal_single(g, kind, mode):
+    """Lockstep GMRES(50): every column equals the one-column solve bit for
+    bit (columns that stop at different steps and restarts, a zero column)."""
+    p, s, F = handle(g, "multiscale2d", kind, mode)
+    rng = np.random.default_rng(7)
+    noise = torch.tensor(rng.standard_normal(F.numel()) * 1e-2, device="cuda")
+    Fs = torch.stack([F, torch.zeros_like(F), F + noise, -2.0 * F])
+    W, stats = s.solve_gmres_ras_multi(Fs, 1e-10, 50, 3000)
+    iters = []
+    for c in range(Fs.shape[0]):
+        w1, st1 = s.solve_gmres_ras(Fs[c].contiguous(), 1e-10, 50, 3000)
+        assert torch.equal(W[c], w1), (kind, mode, c, float((W[c] - w1).abs().max()))
+        assert stats[c]["iters"] == st1["iters"]
+        assert stats[c]["rel_res_true"] == st1["rel_res_true"]
+        iters.append(st1["iters"])
+    assert torch.count_nonzero(W[1]) == 0 and stats[1]["iters"] == 0
+    assert len(set(iters)) > 1
