@@ -113,6 +113,18 @@ def run_step(g, s, p, F):
     return W, st, ranks
 
 
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The largest value over the ranks of the process group (the job's time
+    per step is its slowest replica's); the value itself when world == 1."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def bench_ours(args, rank, world):
     import torch
     import paper_2412_19207_gb300 as g
@@ -158,12 +170,7 @@ def bench_ours(args, rank, world):
     prof = s.profile_read()
     s.profile(False)
     prof_steps = 1
-    ms = float(np.mean(times))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)), world)
     # end to end through the public API with host buffers: weights in, W out
     Rh = torch.tensor(R).pin_memory()
     bh = torch.tensor(b).pin_memory()
