@@ -19,6 +19,7 @@ from oracle import linalg as la
 from oracle import solver as sv
 
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")))
+BANDS = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_bands.json")))
 SMALL = ["poisson2d_2x2", "multiscale2d", "heat3d", "poisson3d", "piecewise2d"]
 
 
@@ -506,6 +507,36 @@ def test_manufactured_solution_accuracy():
     X = ri.test_points(p, 50)
     e2, e1 = sv.errors(sv.evaluate(S, sol.W, X), ri.exact_solution(p, X))
     assert e2 < 1e-3 and e1 < 1e-3
+
+
+# ------------------------------------------------------------- Table 1 --
+
+def test_table1_largest_eigenvalues_of_the_preconditioned_normal_matrix():
+    """Sec. 5, Example 1, Table 1 (4x4 subdomains, 40x40 points, delta = 2,
+    m = 16, no PCA): the largest real part of the eigenvalues of
+    M^{-1} H^T H for AS, SAS and RAS within the band of the paper's values
+    (another random draw), and for AS at most 4^2 = 16, the bound the paper
+    gives: a collocation point lies in at most 4 subdomains (checked here on
+    the geometry), squared by the least-squares form."""
+    import dataclasses
+    p = dataclasses.replace(ri.example1_paper(), pca_mode=ri.PCA_NONE)
+    counts = np.zeros(p.n_points(), dtype=int)
+    for j in range(p.J):
+        counts[asm.box_rows(p, j)] += 1
+    assert counts.max() == 4
+    S = sv.build_system(p)
+    A = S.dense()
+    A = A.T @ A
+    n = A.shape[0]
+    assert n == 256 and S.n_rows == 1600
+    band = BANDS["table1_lambda_max"]
+    for kind, ref in band["value"].items():
+        M = sv.schwarz(S, kind)
+        Minv = np.column_stack([M.apply(e) for e in np.eye(n)])
+        lmax = float(np.linalg.eigvals(Minv @ A).real.max())
+        assert abs(lmax - ref) <= band["rel_band"] * ref, (kind, lmax, ref)
+        if kind == "as":
+            assert lmax <= 16.0 * (1 + 1e-9)
 
 
 # ------------------------------------------------------- differentiation --
