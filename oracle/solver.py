@@ -55,18 +55,28 @@ def pca_rank(sigma: np.ndarray, mode: int, thr: float) -> int:
     raise ValueError(mode)
 
 
-def pca(Psi: np.ndarray, mode: int, thr: float) -> PCA:
+def pca(Psi: np.ndarray, mode: int, thr: float, rank: Optional[int] = None) -> PCA:
+    """Sec. 4: the p_j leading right singular vectors of Psi_j, p_j by the
+    rank rule, or the given rank (a rank that another implementation chose
+    at a borderline cut; borderline still refers to the rule)."""
     m = Psi.shape[1]
     if mode == ri.PCA_NONE:
         return PCA(np.linalg.svd(Psi, compute_uv=False), np.eye(m), m, False)
     _, s, Vt = np.linalg.svd(Psi, full_matrices=False)
     p = pca_rank(s, mode, thr)
+    if rank is not None:
+        if not 1 <= rank <= Vt.shape[0]:
+            raise ValueError(f"rank {rank} outside 1..{Vt.shape[0]}")
+        rule = p
+        p = rank
+    else:
+        rule = p
     # borderline: does a 1e-6 relative wobble of the singular values move the rank?
     lo = pca_rank(s * (1 - 1e-6), mode, thr) if mode == ri.PCA_ABS else pca_rank(
-        np.concatenate([s[:p] * (1 - 1e-6), s[p:] * (1 + 1e-6)]), mode, thr)
+        np.concatenate([s[:rule] * (1 - 1e-6), s[rule:] * (1 + 1e-6)]), mode, thr)
     hi = pca_rank(s * (1 + 1e-6), mode, thr) if mode == ri.PCA_ABS else pca_rank(
-        np.concatenate([s[:p] * (1 + 1e-6), s[p:] * (1 - 1e-6)]), mode, thr)
-    return PCA(s, Vt[:p].T.copy(), p, lo != p or hi != p)
+        np.concatenate([s[:rule] * (1 + 1e-6), s[rule:] * (1 - 1e-6)]), mode, thr)
+    return PCA(s, Vt[:p].T.copy(), p, lo != rule or hi != rule)
 
 
 @dataclasses.dataclass
@@ -108,15 +118,16 @@ class System:
         return Hd
 
 
-def build_system(p: ri.Problem, R=None, b=None, blocks_subset=None) -> System:
-    """Algorithm 1 steps 1-5: geometry, networks, windows and C, PCA, reduced system."""
+def build_system(p: ri.Problem, R=None, b=None, blocks_subset=None, ranks=None) -> System:
+    """Algorithm 1 steps 1-5: geometry, networks, windows and C, PCA, reduced system.
+    ranks: optional p_j per subdomain in place of the rank rule."""
     if R is None:
         R, b = ri.weights(p)
     js = range(p.J) if blocks_subset is None else blocks_subset
     rows, Bs, pcas = [], [], []
     for j in js:
         r, Psi, Hj = asm.block(p, R, b, j)
-        pc = pca(Psi, p.pca_mode, p.pca_thr)
+        pc = pca(Psi, p.pca_mode, p.pca_thr, None if ranks is None else int(ranks[j]))
         rows.append(r)
         Bs.append(Hj @ pc.V)
         pcas.append(pc)

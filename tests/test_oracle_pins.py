@@ -509,6 +509,36 @@ def test_manufactured_solution_accuracy():
     assert e2 < 1e-3 and e1 < 1e-3
 
 
+def test_forced_ranks_reproduce_the_rule_and_extend_the_basis():
+    """build_system(ranks=...): the rule's own ranks give the same system; one
+    more column on a subdomain appends Psi_j's next right singular vector and
+    cannot raise the least-squares minimum; ranks outside 1..min(N_j, m) are
+    rejected."""
+    p = ri.config("poisson2d_2x2", small=True)
+    R, b = ri.weights(p)
+    S = sv.build_system(p, R, b)
+    ranks = [pc.rank for pc in S.pcas]
+    S1 = sv.build_system(p, R, b, ranks=ranks)
+    for B0, B1 in zip(S.B, S1.B):
+        np.testing.assert_array_equal(B0, B1)
+    j = next(j for j in range(p.J) if ranks[j] < min(S.B[j].shape[0], p.neurons))
+    r2 = list(ranks)
+    r2[j] += 1
+    S2 = sv.build_system(p, R, b, ranks=r2)
+    np.testing.assert_array_equal(S2.pcas[j].V[:, :ranks[j]], S.pcas[j].V)
+    _, Psi, _ = asm.block(p, R, b, j)
+    Vt = np.linalg.svd(Psi, full_matrices=False)[2]
+    np.testing.assert_allclose(np.abs(S2.pcas[j].V[:, -1]), np.abs(Vt[ranks[j]]), atol=1e-12)
+    assert S2.pcas[j].borderline == S.pcas[j].borderline
+
+    def ls_min(Sx):
+        return np.linalg.norm(Sx.F - Sx.H(np.linalg.lstsq(Sx.dense(), Sx.F, rcond=None)[0]))
+
+    assert ls_min(S2) <= ls_min(S) * (1 + 1e-12)
+    with pytest.raises(ValueError):
+        sv.build_system(p, R, b, ranks=[0] * p.J)
+
+
 # ------------------------------------------------------------- Table 1 --
 
 def test_table1_largest_eigenvalues_of_the_preconditioned_normal_matrix():
