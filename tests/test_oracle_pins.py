@@ -569,6 +569,20 @@ def test_table1_largest_eigenvalues_of_the_preconditioned_normal_matrix():
             assert lmax <= 16.0 * (1 + 1e-9)
 
 
+def test_table1_error_of_the_as_preconditioned_gmres_solution():
+    """Sec. 5, Example 1, Table 1: the relative L2 error of u_hat on 350 x 350
+    test points after AS-preconditioned GMRES to 1e-5 (no PCA, m = 16),
+    within the band of the paper's value."""
+    import dataclasses
+    p = dataclasses.replace(ri.example1_paper(), pca_mode=ri.PCA_NONE)
+    S = sv.build_system(p)
+    sol = sv.solve(S, "gmres", sv.schwarz(S, "as"), 1e-5, 50, 3000)
+    X = ri.test_points(p, 350)
+    e2, _ = sv.errors(sv.evaluate(S, sol.W, X), ri.exact_solution(p, X))
+    band = BANDS["table1_eL2_as"]
+    assert abs(e2 - band["value"]) <= band["rel_band"] * band["value"], e2
+
+
 # ------------------------------------------------------- differentiation --
 
 def _lstsq_and_adjoint(S, c):
