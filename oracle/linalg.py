@@ -18,7 +18,14 @@ baseline use this package; the product path never does.
     1976), preconditioned as in Barrett et al., "Templates for the Solution of
     Linear Systems" (1994), Figs. 2.9 and 2.8; BiCG also applies A^T and M^T.
     Both stop on ||b - A x|| / ||b||.
-No LAPACK: every factorisation here is written out.
+  * jacobi_svd: the reduced SVD that the PCA of Sec. 4 (Eq. (pca)) needs --
+    singular values and right singular vectors by one-sided Jacobi rotations
+    (Hestenes 1958; Golub & Van Loan Sec. 8.6.3) applied to the triangular
+    factor of a Householder QR (the QR-preconditioned form of Drmac and
+    Veselic 2008), with the pairs of each sweep visited in round-robin order
+    so that the m/2 rotations of one round touch disjoint columns.
+No LAPACK: every factorisation here is written out (numpy supplies only
+vector arithmetic, norms and products).
 """
 from __future__ import annotations
 
@@ -259,3 +266,97 @@ def bicg(apply_A, apply_AT, b: np.ndarray, apply_M=None, apply_MT=None, rtol=1e-
         if rel <= rtol:
             break
     return x, it, hist
+
+
+def apply_q(V: np.ndarray, beta: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """Q Y for the reflectors of householder_qr (reflectors applied in reverse
+    order); Y has V.shape[0] rows."""
+    Y = np.array(Y, dtype=np.float64, copy=True)
+    for c in range(V.shape[1] - 1, -1, -1):
+        if beta[c] != 0.0:
+            v = V[c:, c]
+            Y[c:] -= beta[c] * np.outer(v, v @ Y[c:])
+    return Y
+
+
+def _round_robin(m: int):
+    """The m - 1 rounds (m even) of a round-robin tournament on 0..m-1: each
+    round pairs every index with exactly one other, and over all rounds every
+    pair meets once."""
+    idx = list(range(m))
+    rounds = []
+    for _ in range(m - 1):
+        rounds.append((np.array(idx[: m // 2]), np.array(idx[m // 2:][::-1])))
+        idx = [idx[0], idx[-1]] + idx[1:-1]
+    return rounds
+
+
+def _one_sided_jacobi(G: np.ndarray, tol: float, max_sweeps: int):
+    """Orthogonalise the columns of G (n x m) by plane rotations G <- G J_pq,
+    accumulating V = prod J_pq: for the pair (p, q) with a = |g_p|^2,
+    b = |g_q|^2, c = g_p . g_q the rotation that diagonalises [[a, c], [c, b]]
+    (zeta = (b - a)/(2c), t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)),
+    cs = 1/sqrt(1 + t^2), sn = cs t).  Pairs with |c| <= tol sqrt(a b) are
+    left alone; the sweeps stop when a whole sweep rotates nothing.  The
+    columns are held as the rows of G^T and V^T (contiguous).  Returns
+    (G V, V, sweeps)."""
+    Gt = np.array(np.asarray(G, dtype=np.float64).T, copy=True, order="C")
+    m, n = Gt.shape
+    pad = m % 2
+    if pad:
+        Gt = np.concatenate([Gt, np.zeros((1, n))], axis=0)
+    mm = m + pad
+    Vt = np.eye(mm)
+    rounds = _round_robin(mm)
+    sweep = 0
+    for sweep in range(1, max_sweeps + 1):
+        rotated = 0
+        for P, Q in rounds:
+            gp, gq = Gt[P], Gt[Q]
+            a = np.einsum("ij,ij->i", gp, gp)
+            b = np.einsum("ij,ij->i", gq, gq)
+            c = np.einsum("ij,ij->i", gp, gq)
+            act = np.abs(c) > tol * np.sqrt(a * b)
+            if not np.any(act):
+                continue
+            rotated += int(act.sum())
+            P, Q, a, b, c = P[act], Q[act], a[act], b[act], c[act]
+            zeta = (b - a) / (2.0 * c)
+            t = np.where(zeta >= 0, 1.0, -1.0) / (np.abs(zeta) + np.sqrt(1.0 + zeta * zeta))
+            cs = (1.0 / np.sqrt(1.0 + t * t))[:, None]
+            sn = cs * t[:, None]
+            for M in (Gt, Vt):
+                mp, mq = M[P], M[Q]
+                M[P] = cs * mp - sn * mq
+                M[Q] = sn * mp + cs * mq
+        if rotated == 0:
+            break
+    return Gt[:m].T, Vt[:m, :m].T, sweep
+
+
+def jacobi_svd(A: np.ndarray, max_sweeps: int = 60):
+    """Reduced SVD data of A (n x m): singular values in descending order
+    (min(n, m) of them) and the matching right singular vectors as the rows of
+    Vt (min(n, m) x m), so that A = U diag(s) Vt with orthonormal U.
+
+    Tall case (n >= m): A = Q R by householder_qr; R (m x m) has the singular
+    values and right singular vectors of A, and one-sided Jacobi on R's
+    columns gives R V = U_R diag(s).  Wide case (n < m): A^T = Q R, so
+    A = R^T Q^T; one-sided Jacobi on R^T (n x n) gives R^T W = U diag(s) and
+    the right singular vectors of A are the columns of Q W.  The singular
+    values are the column norms of the rotated matrix."""
+    A = np.asarray(A, dtype=np.float64)
+    n, m = A.shape
+    eps = np.finfo(np.float64).eps
+    if n >= m:
+        _, _, Rf = householder_qr(A)
+        Gv, V, _ = _one_sided_jacobi(Rf, m * eps, max_sweeps)
+        s = np.sqrt(np.einsum("ij,ij->j", Gv, Gv))
+        order = np.argsort(-s, kind="stable")
+        return s[order], V[:, order].T.copy()
+    Vq, bq, Rf = householder_qr(A.T)
+    Gv, W, _ = _one_sided_jacobi(Rf.T, n * eps, max_sweeps)
+    s = np.sqrt(np.einsum("ij,ij->j", Gv, Gv))
+    order = np.argsort(-s, kind="stable")
+    QW = apply_q(Vq, bq, np.concatenate([W, np.zeros((m - n, n))], axis=0))
+    return s[order], QW[:, order].T.copy()

@@ -3,8 +3,9 @@
 TEST INFRASTRUCTURE: only tests/, __graft_entry__.smoke() and bench.py's CPU
 baseline use this package; the product path never does.
 
-  * Sec. 4 Eq. (pca)/(pca_net): reduced SVD Psi_j = U S V^T (numpy's SVD as a
-    library step); keep p_j columns of V, by the absolute threshold
+  * Sec. 4 Eq. (pca)/(pca_net): reduced SVD Psi_j = U S V^T (the oracle's own
+    one-sided Jacobi SVD, linalg.jacobi_svd); keep p_j columns of V, by the
+    absolute threshold
     sigma_k > tau (Sec. 4) or by the variance rule: the smallest p with
     sum_{k<=p} sigma_k^2 >= (1 - eps) sum_k sigma_k^2.
     Reduced block B_j = H_j V_{p_j} (Eq. (system_new)).
@@ -60,9 +61,9 @@ def pca(Psi: np.ndarray, mode: int, thr: float, rank: Optional[int] = None) -> P
     rank rule, or the given rank (a rank that another implementation chose
     at a borderline cut; borderline still refers to the rule)."""
     m = Psi.shape[1]
+    s, Vt = la.jacobi_svd(Psi)
     if mode == ri.PCA_NONE:
-        return PCA(np.linalg.svd(Psi, compute_uv=False), np.eye(m), m, False)
-    _, s, Vt = np.linalg.svd(Psi, full_matrices=False)
+        return PCA(s, np.eye(m), m, False)
     p = pca_rank(s, mode, thr)
     if rank is not None:
         if not 1 <= rank <= Vt.shape[0]:

@@ -281,6 +281,79 @@ def test_svd_brute_force_small():
     assert pc.rank == 3
 
 
+def test_jacobi_svd_2x2_closed_form():
+    """A 2 x 2 matrix [[a, b], [c, d]] has singular values
+    s1 = sqrt((S + sqrt(S^2 - 4 D^2)) / 2) and s2 = |D| / s1 with
+    S = a^2 + b^2 + c^2 + d^2, D = ad - bc (s1 s2 = |det A|)."""
+    for a, b, c, d in [(3.0, 1.0, -2.0, 4.0), (1.0, 2.0, 2.0, 4.0), (0.0, 5.0, 0.0, 0.0), (1e-3, 7.0, -2.0, 1e5)]:
+        A = np.array([[a, b], [c, d]])
+        S, D = a * a + b * b + c * c + d * d, a * d - b * c
+        disc = np.sqrt(max(S * S - 4 * D * D, 0.0))
+        s1 = np.sqrt((S + disc) / 2)
+        want = np.array([s1, abs(D) / s1])
+        s, Vt = la.jacobi_svd(A)
+        np.testing.assert_allclose(s, want, rtol=1e-13, atol=4e-16 * want[0])
+        np.testing.assert_allclose(Vt @ Vt.T, np.eye(2), atol=1e-15)
+        # A^T A v_k = s_k^2 v_k
+        for k in range(2):
+            np.testing.assert_allclose(A.T @ (A @ Vt[k]), s[k] ** 2 * Vt[k], atol=1e-12 * want[0] ** 2)
+
+
+@pytest.mark.parametrize("n,m", [(40, 12), (12, 12), (7, 30), (300, 41)])
+def test_jacobi_svd_on_a_planted_spectrum(n, m):
+    """A = U diag(s) V^T with orthonormal U, V and a known spectrum spanning 14
+    orders of magnitude (tall, square and wide, odd m): the oracle's Jacobi SVD
+    returns s to rounding of the largest value and the planted right singular
+    vectors up to sign."""
+    rng = np.random.default_rng(n * 131 + m)
+    k = min(n, m)
+    U, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    V, _ = np.linalg.qr(rng.standard_normal((m, k)))
+    s = 10.0 ** -np.linspace(0, 14, k)
+    A = U @ np.diag(s) @ V.T
+    sg, Vt = la.jacobi_svd(A)
+    assert sg.shape == (k,) and Vt.shape == (k, m)
+    np.testing.assert_allclose(sg, s, rtol=0, atol=64 * max(n, m) * 2.2e-16)
+    np.testing.assert_allclose(Vt @ Vt.T, np.eye(k), atol=1e-13)
+    # vectors whose singular value is separated from the rest by a gap g are
+    # fixed to an angle of about eps ||A|| / g (A itself carries rounding):
+    # those with g > 1e-3 equal the planted ones up to sign
+    for j in range(k):
+        gap = min(abs(s[j] - s[i]) for i in range(k) if i != j) if k > 1 else 1.0
+        if gap > 1e-3:
+            assert abs(abs(Vt[j] @ V[:, j]) - 1.0) < 1e-12
+    # reconstruction: A = (A V) V^T on the row space
+    np.testing.assert_allclose((A @ Vt.T) @ Vt, A, atol=1e-13)
+
+
+def test_jacobi_svd_rank_deficient_and_zero_columns():
+    """Duplicate and zero columns: exactly zero singular values beyond the
+    rank, and the kept vectors still orthonormal."""
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((20, 3))
+    A = np.concatenate([B, B[:, :1], np.zeros((20, 2))], axis=1)     # rank 3 of 6 columns
+    s, Vt = la.jacobi_svd(A)
+    assert np.all(s[3:] <= 1e-14 * s[0])
+    np.testing.assert_allclose(Vt @ Vt.T, np.eye(6), atol=1e-13)
+    np.testing.assert_allclose(s[:3] ** 2, np.sort(np.linalg.eigvalsh(A.T @ A))[::-1][:3], rtol=1e-12)
+    assert sv.pca(A, ri.PCA_ABS, 1e-8).rank == 3
+
+
+def test_errors_closed_form():
+    """Sec. 5 error measures on a case with known values: u = (1, -1, 1, -1)
+    (mean 0, population std 1, ||u|| = 2) and u_hat = u + 1/2 give
+    e_L2 = ||1/2||/||u|| = 1/2 and e_L1 = mean |1/2| / std(u) = 1/2; a sign or
+    normalisation slip changes one of them."""
+    u = np.array([1.0, -1.0, 1.0, -1.0])
+    e2, e1 = sv.errors(u + 0.5, u)
+    assert e2 == pytest.approx(0.5, rel=1e-15)
+    assert e1 == pytest.approx(0.5, rel=1e-15)
+    # u + 2 = (3, 1, 3, 1) has std 1 still; the error (-1, -2, -2, -2)
+    e2, e1 = sv.errors(np.array([2.0, -1.0, 1.0, -1.0]), u + 2.0)
+    assert e1 == pytest.approx(7.0 / 4.0, rel=1e-15)
+    assert e2 == pytest.approx(np.sqrt(13.0 / 20.0), rel=1e-15)
+
+
 # ---------------------------------------------------------- linear algebra --
 
 def _exact_normal_solution(H, F):
