@@ -1,20 +1,28 @@
 """Benchmark: time to relative residual 1e-10 of the RaNN domain-decomposition
-solver on the 2D multiscale diffusion workload.
+solver, and the bandwidth of its block matrix-vector products.
 
-Workload: -div(a grad u) = 1 on [0,1]^2, a = 2 + sin(2 pi x/eps) sin(2 pi y/eps),
-eps = 1/16; 8 x 8 subdomains, overlap 0.05; 300 tanh neurons per subdomain,
-weights U[-2, 2] (seeded); 40 x 40 collocation points per subdomain cell
-(320 x 320 global); PCA keeping 1 - 1e-12 of the variance; restricted additive
-Schwarz GMRES(50) on the normal equations (scaled partition of unity D_i),
-rtol 1e-10.  One step = the whole hot path: assembly, right-hand side, PCA and
-reduction, preconditioner set-up, Krylov solve.  Synthetic, seeded inputs.
+Headline workload (the largest configured problem that one GPU holds): the
+space-time heat equation u_t = 0.1 Lap u on [0,1]^2 x [0,1], u(0) =
+sin(pi x) sin(pi y) (exact solution known); 8 x 8 x 4 space-time subdomains
+(overlap ratio 1.4), 400 tanh neurons per subdomain with weights U[-1, 1]
+(seeded), 16 x 16 x 8 collocation points per subdomain cell (128 x 128 x 32
+global); PCA keeping 1 - 1e-12 of the variance; additive-Schwarz
+preconditioned CG on the normal equations to rtol 1e-10.  One step = the
+whole hot path: assembly, right-hand side, PCA and reduction, preconditioner
+set-up, Krylov solve.  Synthetic, seeded inputs.
+
+The line also carries the 2D multiscale workload (8 x 8 subdomains, m = 300,
+SAS-preconditioned GMRES(50)) in both precision modes: plain float64
+(mode 0) and the double-float preconditioner and inner iterations with
+float64 refinement (mode 1).
 
 Prints one JSON line.  --impl reference times the CPU oracle (float64 numpy)
-on a bounded sample of the same workload, scaled to a whole step.
+on a bounded sample of the workload.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -30,25 +38,48 @@ sys.path.insert(0, ROOT)
 
 import rann_inputs as ri  # noqa: E402
 
-METRIC = "time to rel. residual 1e-10 (RAS-GMRES, full hot path)"
-WORKLOAD_DESC = ("multiscale2d 8x8 subdomains, m=300, 40x40 pts/subdomain (320x320), overlap 0.05, "
-                 "PCA 1-1e-12, RAS(scaled D_i)-GMRES(50), rtol 1e-10")
+METRIC = "time to rel. residual 1e-10 (AS-CG, RAS-GMRES) & block-matvec HBM GB/s"
+WORKLOAD_DESC = ("heat3d (space-time heat u_t = 0.1 Lap u) 8x8x4 subdomains, m=400, 16x16x8 pts/subdomain "
+                 "(128x128x32), overlap ratio 1.4, PCA 1-1e-12, AS-CG on the normal equations, rtol 1e-10")
+DTYPE = ("mixed: f64 residuals, PCA eigenvalues and reduced blocks; df32 (float32 hi+lo) local factors, "
+         "Schwarz apply and inner Krylov operator; bf16 digit-slice (Ozaki) tensor-core products, f64-accurate")
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 float64 FMA/clk x 2 flop x 2.07 GHz
 DF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12   # double-float multiply-add: 12 float32 instructions
-# DRAM bytes of one launch of the kernel family (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu --set full capture of the same kernel code
-# on this workload); a family missing here reports null
-TRAFFIC = {"eig_tridiag": 28.54e6}
+CSRC = os.path.join(ROOT, "paper_2412_19207_gb300", "csrc")
+# DRAM bytes per launch of a kernel family (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture on this workload, scaled as the
+# profiles/ summary states), valid only for the kernel source it was taken
+# on: the sha256 prefix of that .cu file.  A changed source reports null.
+TRAFFIC = {}
 # families whose profiled bracket spans a multi-stream pipeline of many kernels
 # (the Cholesky with lookahead and the row-block inverse): no single launch
 # duration, so they are reported as pipelines, not as the roofline kernel
 PIPELINED = {"cholesky"}
 
 
-def workload():
-    p = ri.multiscale2d()
+def headline_workload():
+    p = ri.config("heat3d")
+    p.solver, p.precond = "cg_as", "as"
+    return p
+
+
+def multiscale_workload():
+    p = ri.config("multiscale2d")
     p.precond = "sas"
     return p
+
+
+def source_sha(fname):
+    with open(os.path.join(CSRC, fname), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+def traffic_of(family):
+    t = TRAFFIC.get(family)
+    if not t:
+        return None
+    bytes_per_launch, fname, sha = t
+    return bytes_per_launch if source_sha(fname) == sha else None
 
 
 def peaks():
@@ -56,6 +87,18 @@ def peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+
+
+def local_gpu_index():
+    """The nvidia-smi index of this rank's GPU: entry LOCAL_RANK of
+    CUDA_VISIBLE_DEVICES, or LOCAL_RANK itself when the variable is unset."""
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if ids:
+            return ids[min(lr, len(ids) - 1)]
+    return str(lr)
 
 
 class Clocks:
@@ -70,7 +113,7 @@ class Clocks:
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0],
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", local_gpu_index(),
                                           f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
@@ -104,12 +147,23 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def run_step(g, s, p, F):
+def run_step(s, p, F, events=None):
+    """One pass of the hot path; with events (5 CUDA events) the phase
+    boundaries are recorded on the handle's stream."""
+    rec = (lambda i: events[i].record(s.stream)) if events else (lambda i: None)
+    rec(0)
     s.assemble()
     s.rhs(F)
+    rec(1)
     ranks = s.pca(p.pca_mode, p.pca_thr)
+    rec(2)
     s.setup_precond(p.precond)
-    W, st = s.solve_gmres_ras(F, p.rtol, p.restart, p.maxit)
+    rec(3)
+    if p.solver == "cg_as":
+        W, st = s.solve_cg_as(F, p.rtol, p.maxit)
+    else:
+        W, st = s.solve_gmres_ras(F, p.rtol, p.restart, p.maxit)
+    rec(4)
     return W, st, ranks
 
 
@@ -125,6 +179,87 @@ def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
+def roofline(prof, pk):
+    """The roofline object of the dominant single kernel of a profiled step."""
+    dom_name, dom = max(((k, v) for k, v in prof.items() if k not in PIPELINED and v["ms"] > 0),
+                        key=lambda kv: kv[1]["ms"])
+    bound = dom["bound"]
+    if bound == "hbm":
+        ach = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+        peak, unit = pk["hbm_gbs"], "GB/s"
+        note = "measured HBM copy (MEASURED_PEAKS.json)"
+    elif bound == "tensor":
+        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
+        peak, unit = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")), "TFLOP/s"
+        note = "measured cuBLAS bf16, sustained (MEASURED_PEAKS.json); flops of the digit-slice products"
+    elif bound == "alu_df32":
+        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
+        peak, unit = DF32_PEAK_TFLOPS, "TFLOP/s"
+        note = ("double-float multiply-add: 152 SMs x 128 float32 lanes x 2.07 GHz / 12 float32 "
+                "instructions x 2 flops (unit counts x max clock), float64-equivalent flops")
+        bound = "alu"
+    else:
+        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
+        peak, unit = FP64_PEAK_TFLOPS, "TFLOP/s"
+        note = "float64 FMA: 152 SMs x 2 FMA/clk x 2.07 GHz (unit counts x max clock)"
+    tr = traffic_of(dom_name)
+    return {"kernel": dom_name, "bound": bound, "achieved": round(ach, 3), "peak": peak, "unit": unit,
+            "frac": round(ach / peak, 4), "traffic": (tr if tr is None else round(tr)),
+            "launches": dom["launches"], "ms_per_launch": round(dom["ms"] / max(dom["launches"], 1), 4),
+            "alg_bytes_per_launch": round(dom["bytes"] / max(dom["launches"], 1)),
+            "peak_source": note}
+
+
+def bandwidths(prof, pk):
+    def gbps(names):
+        fam = [prof[n] for n in names if prof.get(n, {}).get("ms")]
+        if not fam:
+            return None
+        by, t = sum(f["bytes"] for f in fam), sum(f["ms"] for f in fam)
+        return {"GBps": round(by / (t * 1e-3) / 1e9, 1), "frac_of_hbm": round(by / (t * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                "launches_per_step": sum(f["launches"] for f in fam), "ms_per_step": round(t, 3)}
+    return {"normal_rows_df32": gbps(["gramop_df32"]), "H_f64": gbps(["matvec_H"]), "HT_f64": gbps(["matvec_HT"]),
+            "schwarz_apply_df32": gbps(["schwarz_apply_df32", "trmv_lower_df32", "trmv_upper_df32"]),
+            "schwarz_apply_f64": gbps(["trmv_lower", "trmv_upper"])}
+
+
+def time_steps(torch, s, p, F, n):
+    """Mean CUDA-event time of n steps (after the caller's warm-up)."""
+    stream = torch.cuda.current_stream()
+    out = []
+    for _ in range(n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        W, st, ranks = run_step(s, p, F)
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out, W, st, ranks
+
+
+def multiscale_arms(g, torch, steps=3):
+    """The 2D multiscale workload (SAS-GMRES(50)) in precision mode 0 (plain
+    float64) and mode 1 (double-float preconditioner and inner iterations,
+    float64 refinement), each after one warm-up step."""
+    p = multiscale_workload()
+    R, b = ri.weights(p)
+    out = {"workload": "multiscale2d 8x8 subdomains, m=300, 40x40 pts/subdomain (320x320), overlap 0.05, "
+                       "PCA 1-1e-12, SAS-GMRES(50), rtol 1e-10"}
+    for mode in (0, 1):
+        s = g.RannDD(p, R, b)
+        s.set_precision(mode)
+        F = s._empty(s.sizes()["n_points"])
+        run_step(s, p, F)
+        times, W, st, ranks = time_steps(torch, s, p, F, steps)
+        out[f"mode{mode}"] = {"precision": "f64" if mode == 0 else "df32 preconditioner+inner, f64 refinement",
+                              "ms_per_step": round(float(np.mean(times)), 3), "iters": st["iters"],
+                              "rel_res_true": st["rel_res_true"], "rel_res_prec": st["rel_res_prec"],
+                              "dof": int(np.sum(ranks))}
+        s.close()
+    out["mode1_speedup_over_mode0"] = round(out["mode0"]["ms_per_step"] / out["mode1"]["ms_per_step"], 3)
+    return out
+
+
 def bench_ours(args, rank, world):
     import torch
     import paper_2412_19207_gb300 as g
@@ -136,11 +271,10 @@ def bench_ours(args, rank, world):
         dist.barrier()
     g.load_library()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    p = workload()
+    p = headline_workload()
     R, b = ri.weights(p)
     s = g.RannDD(p, R, b)
     F = s._empty(s.sizes()["n_points"])
-    stream = torch.cuda.current_stream()
 
     def barrier():
         torch.cuda.synchronize()
@@ -149,95 +283,60 @@ def bench_ours(args, rank, world):
             dist.barrier()
 
     for _ in range(args.warmup):
-        W, st, ranks = run_step(g, s, p, F)
+        W, st, ranks = run_step(s, p, F)
     barrier()
-    times = []
     with Clocks() as clk:
-        for _ in range(args.steps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            W, st, ranks = run_step(g, s, p, F)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
+        times, W, st, ranks = time_steps(torch, s, p, F, args.steps)
         barrier()
-    # one further step with every launch bracketed by CUDA events on the handle's
-    # stream: the kernel breakdown and the roofline (not part of the timed steps)
+    ms = max_over_ranks(float(np.mean(times)), world)
+    # one further step with the phase boundaries on CUDA events, and one with
+    # every launch bracketed by CUDA events on the handle's stream (kernel
+    # breakdown and roofline); neither is part of the timed steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    run_step(s, p, F, ev)
+    torch.cuda.synchronize()
+    phases = {k: round(ev[i].elapsed_time(ev[i + 1]), 3)
+              for i, k in enumerate(["assemble_rhs", "pca", "setup_precond", "solve"])}
     s.profile(True)
-    run_step(g, s, p, F)
+    run_step(s, p, F)
     torch.cuda.synchronize()
     prof = s.profile_read()
     s.profile(False)
-    prof_steps = 1
-    ms = max_over_ranks(float(np.mean(times)), world)
+    s.close()
     # end to end through the public API with host buffers: weights in, W out
     Rh = torch.tensor(R).pin_memory()
     bh = torch.tensor(b).pin_memory()
     e2e = []
-    for rep in range(max(2, min(args.steps, 3)) + 1):
+    for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = g.RannDD(p, Rh.numpy(), bh.numpy())
         F2 = s2._empty(s2.sizes()["n_points"])
-        W2, st2, _ = run_step(g, s2, p, F2)
+        W2, st2, _ = run_step(s2, p, F2)
         Wh = torch.empty(W2.shape, dtype=torch.float64).pin_memory()
         Wh.copy_(W2)
         torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
         s2.close()
-        if rep > 0:
-            e2e.append(time.perf_counter() - t0)
+        del s2, F2, W2
     pk = peaks()
-    launches = sum(v["launches"] for v in prof.values()) // prof_steps
-    dom_name, dom = max(((k, v) for k, v in prof.items() if k not in PIPELINED), key=lambda kv: kv[1]["ms"])
-    bound = dom["bound"]
-    if bound == "hbm":
-        ach = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
-        peak, unit = pk["hbm_gbs"], "GB/s"
-        peak_note = "measured HBM copy (MEASURED_PEAKS.json)"
-    elif bound == "tensor":
-        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
-        peak, unit = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")), "TFLOP/s"
-        peak_note = "measured cuBLAS bf16, sustained (MEASURED_PEAKS.json); flops of the digit-slice products"
-    elif bound == "alu_df32":
-        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
-        peak, unit = DF32_PEAK_TFLOPS, "TFLOP/s"
-        peak_note = ("double-float multiply-add: 152 SMs x 128 float32 lanes x 2.07 GHz / 12 float32 "
-                     "instructions x 2 flops (unit counts x max clock), float64-equivalent flops")
-        bound = "alu"
-    else:
-        ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
-        peak, unit = FP64_PEAK_TFLOPS, "TFLOP/s"
-        peak_note = "float64 FMA: 152 SMs x 2 FMA/clk x 2.07 GHz (unit counts x max clock)"
-    # the block products: the inner iterations' normal-matrix block rows (double-float) and the float64
-    # two-pass B^T (B x) of the residuals that decide convergence
-    def gbps(names):
-        fam = [prof[n] for n in names if prof.get(n, {}).get("ms")]
-        if not fam:
-            return None
-        by, t = sum(f["bytes"] for f in fam), sum(f["ms"] for f in fam)
-        return {"GBps": round(by / (t * 1e-3) / 1e9, 1), "frac_of_hbm": round(by / (t * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
-                "launches_per_step": sum(f["launches"] for f in fam) // prof_steps}
-    kernels = {k: {"ms_per_step": round(v["ms"] / prof_steps, 3), "launches_per_step": v["launches"] // prof_steps}
+    launches = sum(v["launches"] for v in prof.values())
+    kernels = {k: {"ms_per_step": round(v["ms"], 3), "launches_per_step": v["launches"]}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]}
-    clocks = clk.summary()
     out = {
         "metric": METRIC, "value": round(ms / 1e3, 6), "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded SplitMix64 weights, manufactured PDE data)",
-        "config": {"workload": WORKLOAD_DESC,
-                   "dof": int(np.sum(ranks)), "iters": st["iters"], "rel_res_true": st["rel_res_true"],
-                   "rel_res_prec": st["rel_res_prec"], "parallelism": f"replicas x{world}",
-                   "l2": "working set > L2 (reduced blocks 8*sum N_j p_j bytes, factors), no flush"},
-        "roofline": {"kernel": dom_name, "bound": bound, "achieved": round(ach, 3), "peak": peak,
-                     "unit": unit, "frac": round(ach / peak, 4), "traffic": TRAFFIC.get(dom_name),
-                     "peak_source": peak_note},
-        "matvec": {"normal_rows_df32": gbps(["gramop_df32"]),
-                   "H_f64": gbps(["matvec_H"]), "HT_f64": gbps(["matvec_HT"]),
-                   "H_df32": gbps(["matvec_H_df32"]), "HT_df32": gbps(["matvec_HT_df32"]),
-                   "schwarz_apply_df32": gbps(["schwarz_apply_df32", "trmv_lower_df32", "trmv_upper_df32"])},
-        "pipelines": {k: {"ms_per_step": round(prof[k]["ms"] / prof_steps, 3),
-                          "launches_per_step": prof[k]["launches"] // prof_steps,
+        "vs_baseline": None, "dtype": DTYPE,
+        "data": "synthetic (seeded SplitMix64 weights, manufactured PDE data)",
+        "config": {"workload": WORKLOAD_DESC, "solver": "AS-CG", "precision_mode": 1,
+                   "dof": int(np.sum(ranks)), "J": p.J, "m": p.neurons, "iters": st["iters"],
+                   "rel_res_true": st["rel_res_true"], "rel_res_rec": st["rel_res_rec"],
+                   "n_shifted": st["n_shifted"], "parallelism": f"replicas x{world}",
+                   "l2": "working set > L2 (reduced blocks 8*sum N_j p_j bytes, local factors), no flush"},
+        "phases_ms": phases,
+        "roofline": roofline(prof, pk),
+        "matvec": bandwidths(prof, pk),
+        "pipelines": {k: {"ms_per_step": round(prof[k]["ms"], 3), "launches_per_step": prof[k]["launches"],
                           "achieved_tflops": round(prof[k]["flops"] / (prof[k]["ms"] * 1e-3) / 1e12, 3),
                           "frac_of_df32_peak": round(prof[k]["flops"] / (prof[k]["ms"] * 1e-3) / 1e12
                                                      / DF32_PEAK_TFLOPS, 4)}
@@ -246,24 +345,28 @@ def bench_ours(args, rank, world):
         "gpu_launches": int(launches) * args.steps,
         "gpu_launches_per_step": int(launches),
         "e2e": {"value": round(float(np.median(e2e)), 6), "unit": "s",
-                "h2d_bytes_per_step": int(R.nbytes + b.nbytes), "d2h_bytes_per_step": int(W.numel() * 8)},
-        "clocks": clocks,
+                "h2d_bytes_per_step": int(R.nbytes + b.nbytes), "d2h_bytes_per_step": int(W.numel() * 8),
+                "what": "fresh handle from pinned host weights R, b; full hot path; W copied to pinned host memory"},
+        "clocks": clk.summary(),
     }
+    if not args.no_multiscale:
+        out["multiscale2d"] = multiscale_arms(g, torch)
     if args.multi_rhs > 0:
-        out["multi_rhs"] = [multi_rhs_timing(g, p, R, b, args.multi_rhs, "cg"),
-                            multi_rhs_timing(g, p, R, b, args.multi_rhs, "gmres")]
+        out["multi_rhs"] = [multi_rhs_timing(g, args.multi_rhs, "cg"), multi_rhs_timing(g, args.multi_rhs, "gmres")]
     return out
 
 
-def multi_rhs_timing(g, p, R, b, k, solver="cg"):
-    """k right-hand sides of the workload (F scaled by 1..k, so every column
-    runs the same iterations): k one-column solves one after another against
-    one lockstep solve of all k (every operator and preconditioner launch
-    serves all columns).  solver "cg": AS-preconditioned CG; "gmres": the
-    workload's SAS-preconditioned GMRES(50).  Both after a warm-up solve; wall
-    time with the device synchronised on both sides (the solves include their
-    host round trips)."""
+def multi_rhs_timing(g, k, solver="cg"):
+    """k right-hand sides of the multiscale workload (F scaled by 1..k, so every
+    column runs the same iterations): k one-column solves one after another
+    against one lockstep solve of all k (every operator and preconditioner
+    launch serves all columns).  solver "cg": AS-preconditioned CG; "gmres":
+    SAS-preconditioned GMRES(50).  Both after a warm-up solve; wall time with
+    the device synchronised on both sides (the solves include their host
+    round trips)."""
     import torch
+    p = multiscale_workload()
+    R, b = ri.weights(p)
     s = g.RannDD(p, R, b)
     s.assemble()
     F = s.rhs()
@@ -299,41 +402,110 @@ def multi_rhs_timing(g, p, R, b, k, solver="cg"):
             "speedup": round(t_one / t_multi, 3), "all_converged": all(ok(x) for x in sts)}
 
 
-def cpu_sample(args):
-    """The oracle, as it stands, on a bounded sample of the workload scaled to
-    a whole step: the 3 x 3 neighbourhood of an interior subdomain is built
-    with the oracle's own assembly and PCA (time per subdomain x J), the
-    centre's extended-set matrix A_i is formed and factored by the oracle's
-    Householder QR (x J sets), and one preconditioned normal-matrix product
-    over the sample is timed (x J/9 for the products, x J local solves, x the
-    GPU's Krylov iteration count)."""
+# --------------------------------------------------------------- CPU oracle --
+
+def oracle_sample_problem():
+    """A scaled-down instance of the headline workload that the oracle solves
+    completely in seconds: the same space-time heat problem, overlap ratio,
+    weight range and rank rule on 3 x 3 x 2 subdomains (one interior
+    subdomain, so the Schwarz sets overlap as in the full grid) with
+    6 x 6 x 4 points per cell and 40 neurons."""
+    p = ri.heat3d(sub=(3, 3, 2), pts=(6, 6, 4), neurons=40)
+    p.solver, p.precond = "cg_as", "as"
+    return p
+
+
+def oracle_pass(p):
+    """The oracle's whole hot path on problem p (assembly and PCA, AS set-up
+    by Householder QR of every A_i, AS-CG to rtol); seconds per phase."""
+    from oracle import solver as sv
+    t0 = time.perf_counter()
+    S = sv.build_system(p)
+    t1 = time.perf_counter()
+    M = sv.schwarz(S, "as")
+    t2 = time.perf_counter()
+    sol = sv.solve(S, "cg", M, p.rtol, p.restart, p.maxit)
+    t3 = time.perf_counter()
+    return {"build": t1 - t0, "setup": t2 - t1, "solve": t3 - t2, "total": t3 - t0, "iters": sol.iters,
+            "dof": S.dof, "rel_res": sol.rel_res_normal}
+
+
+def oracle_extrapolation(iters):
+    """The oracle's time for one step of the full headline workload, scaled
+    from measured units of that workload: the assembly and PCA of one full
+    subdomain (x J), one Householder QR of a 1200 x 1200 local matrix scaled
+    by (n_i / 1200)^3 over the J extended sets (n_i from the full workload's
+    sizes at the measured ranks), and one normal product over that subdomain
+    and one local solve per set per iteration (x the GPU's iteration count).
+    Returns (seconds, description)."""
+    from oracle import assembly as asm
     from oracle import linalg as la
     from oracle import solver as sv
-    p = workload()
+    p = headline_workload()
     R, b = ri.weights(p)
-    J, l = p.J, p.sub[0]
-    c = (l // 2) * l + l // 2
-    hood = [c + dy * l + dx for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    j = 4 + 8 * 4 + 64 * 2
     t0 = time.perf_counter()
-    S = sv.build_system(p, R, b, blocks_subset=hood)
-    t_build = (time.perf_counter() - t0) / len(hood)
+    rows, Psi, Hj = asm.block(p, R, b, j)
+    pc = sv.pca(Psi, p.pca_mode, p.pca_thr)
+    B = Hj @ pc.V
+    t_block = time.perf_counter() - t0
+    x = np.random.default_rng(1).standard_normal(B.shape[1])
     t0 = time.perf_counter()
-    A = sv.local_matrix(S, list(range(len(hood))))
-    qr = la.householder_qr(A)
-    t_setup = time.perf_counter() - t0
-    x = np.random.default_rng(1).standard_normal(S.dof)
-    t0 = time.perf_counter()
-    y = S.normal(x)
+    B.T @ (B @ x)
     t_mv = time.perf_counter() - t0
+    n0 = 1200
+    A = np.random.default_rng(2).standard_normal((n0, n0))
+    A = A @ A.T + n0 * np.eye(n0)
+    t0 = time.perf_counter()
+    qr = la.householder_qr(A)
+    t_qr = time.perf_counter() - t0
+    y = np.ones(n0)
     t0 = time.perf_counter()
     la.back_substitute(qr[2], la.apply_qt(qr[0], qr[1], y))
     t_ls = time.perf_counter() - t0
-    iters = args.iters_hint
-    total = J * (t_build + t_setup) + iters * (t_mv * J / len(hood) + t_ls * J)
-    return total, (f"oracle on the 3x3 neighbourhood of subdomain {c}: assembly+PCA "
-                   f"{t_build:.2f} s/subdomain, A_i ({A.shape[0]}x{A.shape[0]}) + Householder QR {t_setup:.2f} s, "
-                   f"normal product {t_mv * 1e3:.1f} ms/9 blocks, local solve {t_ls * 1e3:.1f} ms; "
-                   f"scaled by J={J} and {iters} Krylov iterations (extrapolated)")
+    # extended-set sizes of the full workload at this block's rank
+    l = p.sub
+    n3 = n2 = 0.0
+    for k2 in range(l[2]):
+        for k1 in range(l[1]):
+            for k0 in range(l[0]):
+                cnt = 1
+                for k, L in ((k0, l[0]), (k1, l[1]), (k2, l[2])):
+                    cnt *= (1 + (k > 0) + (k < L - 1))
+                n = cnt * pc.rank
+                n3 += n ** 3
+                n2 += n ** 2
+    total = p.J * t_block + t_qr * n3 / n0 ** 3 + iters * (p.J * t_mv + t_ls * n2 / n0 ** 2)
+    desc = (f"oracle units of the full workload: assembly+PCA of subdomain {j} ({Hj.shape[0]}x{p.neurons}, rank "
+            f"{pc.rank}) {t_block:.2f} s x J={p.J}; Householder QR {n0}x{n0} {t_qr:.2f} s scaled by sum n_i^3; "
+            f"per iteration: normal product {t_mv * 1e3:.2f} ms x J and QR solve {t_ls * 1e3:.1f} ms scaled by "
+            f"sum n_i^2, x {iters} iterations (extrapolated)")
+    return total, desc
+
+
+def reference_arm(args):
+    """The oracle as it stands, on the host cores: each step is one complete
+    pass of the hot path on the scaled-down instance (a measured time); the
+    full workload's time, extrapolated from measured units, is reported
+    beside it."""
+    p = oracle_sample_problem()
+    vals = []
+    for _ in range(args.steps):
+        r = oracle_pass(p)
+        vals.append(r["total"])
+    v = float(np.mean(vals))
+    ext, ext_desc = oracle_extrapolation(args.iters_hint)
+    cores = os.cpu_count()
+    sample = (f"complete oracle pass (assembly+PCA, AS set-up by Householder QR, AS-CG to 1e-10) on heat3d "
+              f"3x3x2 subdomains, 6x6x4 pts/cell, m=40 (DoF {r['dof']}, {r['iters']} CG iterations): "
+              f"build {r['build']:.2f} s, setup {r['setup']:.2f} s, solve {r['solve']:.2f} s; numpy default threads")
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": 0, "ms_per_step": round(v * 1e3, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "sample": "scaled-down instance (see cpu_baseline.sample)"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "extrapolated_full_workload": {"value": round(ext, 2), "unit": "s", "how": ext_desc},
+            "e2e": {"value": round(v, 4), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
@@ -342,11 +514,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--iters-hint", type=int, default=71)
+    ap.add_argument("--iters-hint", type=int, default=377)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-multiscale", action="store_true", help="skip the multiscale precision-mode arms")
     ap.add_argument("--multi-rhs", type=int, default=0,
                     help="also time AS-CG and the workload's GMRES on this many right-hand sides in lockstep "
-                         "against one at a time")
+                         "against one at a time (multiscale workload)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -355,20 +528,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        vals = []
-        for _ in range(args.steps):
-            v, sample = cpu_sample(args)
-            vals.append(v)
-        v = float(np.mean(vals))
-        cores = os.cpu_count()
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "s",
-                          "n_gpus": args.gpus, "steps": args.steps, "warmup": 0, "ms_per_step": round(v * 1e3, 1),
-                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": WORKLOAD_DESC},
-                          "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": cores, "kind": "oracle",
-                                           "sample": sample},
-                          "e2e": {"value": round(v, 4), "unit": "s", "h2d_bytes_per_step": 0,
-                                  "d2h_bytes_per_step": 0}}))
+        print(json.dumps(reference_arm(args)))
         return
     if world > 1:
         import torch.distributed as dist
@@ -376,8 +536,7 @@ def main():
     out = bench_ours(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:
-            args.iters_hint = out["config"]["iters"]
-            v, sample = cpu_sample(args)
+            v, sample = oracle_extrapolation(out["config"]["iters"])
             out["cpu_baseline"] = {"value": round(v, 3), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
                                    "sample": sample}
         print(json.dumps(out))

@@ -322,7 +322,10 @@ def _one_sided_jacobi(G: np.ndarray, tol: float, max_sweeps: int):
             rotated += int(act.sum())
             P, Q, a, b, c = P[act], Q[act], a[act], b[act], c[act]
             zeta = (b - a) / (2.0 * c)
-            t = np.where(zeta >= 0, 1.0, -1.0) / (np.abs(zeta) + np.sqrt(1.0 + zeta * zeta))
+            big = np.abs(zeta) > 1e150               # t = 1/(2 zeta) to rounding; avoids zeta^2 overflow
+            zs = np.where(big, 0.0, zeta)
+            t = np.where(big, 0.5 / np.where(big, zeta, 1.0),
+                         np.where(zeta >= 0, 1.0, -1.0) / (np.abs(zs) + np.sqrt(1.0 + zs * zs)))
             cs = (1.0 / np.sqrt(1.0 + t * t))[:, None]
             sn = cs * t[:, None]
             for M in (Gt, Vt):

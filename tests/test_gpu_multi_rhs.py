@@ -15,6 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import rann_inputs as ri
+from solution_bounds import GpuReduced
 
 
 @pytest.fixture(scope="module")
@@ -77,14 +78,13 @@ def test_cg_multi_solution_matches_the_oracle(g):
     R, b = ri.weights(p)
     S = sv.build_system(p, R, b)
     W, stats = s.solve_cg_as_multi(torch.stack([F, 3.0 * F]), 1e-10, 3000)
-    sol = sv.solve(S, "cg", sv.schwarz(S, "as"), 1e-10, 50, 3000)
+    gr = GpuReduced(p, s, s.ranks, F)
+    qr = sv.solve_qr(S)
     X = ri.test_points(p, 21)
-    uo = sv.evaluate(S, sol.W, X)
     for c, f in enumerate([1.0, 3.0]):
-        ug = s.eval(W[c].contiguous(), torch.tensor(X, device="cuda")).cpu().numpy()
-        # u_hat is affine in W through the boundary term G: compare the W-linear parts
-        g0 = s.eval(torch.zeros_like(W[c]), torch.tensor(X, device="cuda")).cpu().numpy()
-        assert np.linalg.norm((ug - g0) - f * (uo - g0)) <= 1e-5 * f * np.linalg.norm(uo - g0)
+        gr.check(W[c], scale=f)
+        res = np.linalg.norm(s.matvec(W[c].contiguous()).cpu().numpy() - f * S.F)
+        assert abs(res - f * qr.res_ls) <= 1e-8 * f * np.linalg.norm(S.F)
 
 
 @pytest.mark.parametrize("kind,mode", [("sas", 1), ("ras", 1), ("ras", 0)])
