@@ -48,7 +48,9 @@ typedef enum {
   RANN_NOT_CONVERGED = 4,   /* Krylov solve hit maxit; W holds the last iterate */
   RANN_BREAKDOWN = 5,       /* CG p^T A p <= 0, or NaN/Inf met in a reduction */
   RANN_LOCAL_SINGULAR = 6,  /* warning: a local Cholesky needed a diagonal shift */
-  RANN_EORDER = 7           /* call made out of Algorithm 1's order */
+  RANN_EORDER = 7,          /* call made out of Algorithm 1's order */
+  RANN_TIMEOUT = 8          /* a bounded device wait (tensor-core product pipeline) gave up;
+                               the work it fed is invalid, the handle stays usable */
 } rann_status;
 
 /* PDE operator A of Eq. (1). */
@@ -125,6 +127,15 @@ typedef struct {
   double rel_res_prec;     /* ||M^{-1}(b - A W)|| / ||M^{-1} b|| at exit (GMRES) */
   double ms_solve;         /* device time of the solve                        */
   int n_shifted;           /* local factors that needed a shift (from setup)  */
+  double ms_assemble;      /* device time of the handle's last assemble (+ rhs) */
+  double ms_pca;           /* device time of the last pca                     */
+  double ms_setup;         /* device time of the last setup_precond           */
+  double kappa_est;        /* estimate of kappa(M^{-1} H^T H) from the first
+                              refinement cycle's Krylov coefficients: the
+                              Lanczos tridiagonal of CG (Ritz values) or the
+                              Arnoldi Hessenberg of GMRES (singular values);
+                              a lower bound that tightens with the iteration
+                              count; -1 where not formed (CGS, BiCG, < 2 steps) */
 } rann_dd_stats;
 
 typedef struct rann_dd_handle rann_dd_handle;
@@ -332,6 +343,21 @@ rann_status rann_dd_matvec_t_noalloc(int J, const int64_t* boff, const int* n_ro
 rann_status rann_dd_profile_enable(rann_dd_handle* h, int on);
 rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const char** name, int64_t* launches,
                                 double* ms, double* alg_bytes, double* alg_flops, int* bound);
+
+/* Host-side fault injection for failure-detection tests (the paper has no
+ * counterpart; no device code is made to fault, trap or hang):
+ *   RANN_FAULT_WAIT_EXPIRED: writes `value` (non-zero) into the handle's
+ *     device error word of the tensor-core product pipelines, exactly what a
+ *     bounded mbarrier wait writes when it gives up; the next pca or
+ *     setup_precond that reads the word back returns RANN_TIMEOUT (and
+ *     clears it).  value = 0 clears the word.
+ *   RANN_FAULT_ALLOC_CAP: from now on the handle's device allocations fail
+ *     (RANN_ENOMEM, before any cudaMalloc) whenever its live bytes would
+ *     exceed `value`; value < 0 removes the cap.
+ * A failed pca or setup_precond leaves the handle at the previous step of
+ * Algorithm 1 (solves then return RANN_EORDER until the step succeeds). */
+enum { RANN_FAULT_WAIT_EXPIRED = 1, RANN_FAULT_ALLOC_CAP = 2 };
+rann_status rann_dd_inject_fault(rann_dd_handle* h, int kind, int64_t value);
 
 const char* rann_dd_status_string(rann_status s);
 const char* rann_dd_last_error(void);

@@ -36,8 +36,9 @@ PREC_NONE, PREC_AS, PREC_SAS, PREC_RAS = 0, 1, 2, 3
 PREC_BY_NAME = {"none": PREC_NONE, "as": PREC_AS, "sas": PREC_SAS, "ras": PREC_RAS}
 
 STATUS = {0: "RANN_OK", 1: "RANN_EINVAL", 2: "RANN_ENOMEM", 3: "RANN_ECUDA", 4: "RANN_NOT_CONVERGED",
-          5: "RANN_BREAKDOWN", 6: "RANN_LOCAL_SINGULAR", 7: "RANN_EORDER"}
-OK, EINVAL, ENOMEM, ECUDA, NOT_CONVERGED, BREAKDOWN, LOCAL_SINGULAR, EORDER = range(8)
+          5: "RANN_BREAKDOWN", 6: "RANN_LOCAL_SINGULAR", 7: "RANN_EORDER", 8: "RANN_TIMEOUT"}
+OK, EINVAL, ENOMEM, ECUDA, NOT_CONVERGED, BREAKDOWN, LOCAL_SINGULAR, EORDER, TIMEOUT = range(9)
+FAULT_WAIT_EXPIRED, FAULT_ALLOC_CAP = 1, 2
 
 
 class RannError(RuntimeError):
@@ -63,7 +64,9 @@ class Desc(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_res_true", ctypes.c_double), ("rel_res_rec", ctypes.c_double),
-                ("rel_res_prec", ctypes.c_double), ("ms_solve", ctypes.c_double), ("n_shifted", ctypes.c_int)]
+                ("rel_res_prec", ctypes.c_double), ("ms_solve", ctypes.c_double), ("n_shifted", ctypes.c_int),
+                ("ms_assemble", ctypes.c_double), ("ms_pca", ctypes.c_double), ("ms_setup", ctypes.c_double),
+                ("kappa_est", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -108,6 +111,7 @@ SIGNATURES = {
     "rann_dd_profile_enable": (_I, [_P, _I]),
     "rann_dd_profile_get": (_I, [_P, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_L),
                                  ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "rann_dd_inject_fault": (_I, [_P, _I, _L]),
     "rann_dd_status_string": (ctypes.c_char_p, [_I]),
     "rann_dd_last_error": (ctypes.c_char_p, []),
 }
@@ -388,6 +392,12 @@ class RannDD:
         z = z if z is not None else self._empty(self.sizes()["dof"])
         _check(self._lib.rann_dd_precond_apply_t(self._h, _dptr(r), _dptr(z)), "rann_dd_precond_apply_t")
         return z
+
+    def inject_fault(self, kind: int, value: int):
+        """Host-side fault injection (rann_dd_inject_fault): FAULT_WAIT_EXPIRED
+        sets the device error word of the tensor-core pipelines; FAULT_ALLOC_CAP
+        caps the handle's live device bytes (value < 0 removes the cap)."""
+        _check(self._lib.rann_dd_inject_fault(self._h, kind, int(value)), "rann_dd_inject_fault")
 
     # -- kernel accounting ------------------------------------------------
     def profile(self, on: bool = True):

@@ -244,6 +244,12 @@ struct rann_dd_handle {
   double* d_scal = nullptr;    // small device scalars
   double* h_scal = nullptr;    // pinned host mirror
   int* d_ozerr = nullptr;      // non-zero once a tensor-core product pipeline timed out
+  std::vector<size_t> alloc_bytes;   // sizes of allocs[i]
+  size_t live_bytes = 0;
+  int64_t alloc_cap = -1;           // injected cap on live device bytes (< 0: none)
+  // phase timing: events around assemble (+ rhs), pca, setup_precond
+  cudaEvent_t ph_ev[3][2] = {};
+  bool ph_rec[3] = {false, false, false};
   char* h_stage = nullptr;     // pinned staging arena of the uploads
   size_t stage_cap = 0, stage_used = 0;
   Prof prof;
@@ -292,8 +298,13 @@ static void prof_resolve(rann_dd_handle* h) {
 static cudaError_t dalloc(rann_dd_handle* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  if (h->alloc_cap >= 0 && h->live_bytes + bytes > (size_t)h->alloc_cap) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMallocAsync(p, bytes, h->st);
-  if (e == cudaSuccess) h->allocs.push_back(*p);
+  if (e == cudaSuccess) {
+    h->allocs.push_back(*p);
+    h->alloc_bytes.push_back(bytes);
+    h->live_bytes += bytes;
+  }
   return e;
 }
 
@@ -333,8 +344,105 @@ static void dfree(rann_dd_handle* h, void* p) {
   auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
   if (it != h->allocs.end()) {
     cudaFreeAsync(p, h->st);
+    const size_t i = (size_t)(it - h->allocs.begin());
+    h->live_bytes -= h->alloc_bytes[i];
+    h->alloc_bytes.erase(h->alloc_bytes.begin() + i);
     h->allocs.erase(it);
   }
+}
+
+// Phase timing (stats): events recorded on the handle's stream around
+// assemble (+ rhs), pca and setup_precond, resolved when stats are filled.
+static void phase_mark(rann_dd_handle* h, int ph, int which) {
+  cudaEvent_t& e = h->ph_ev[ph][which];
+  if (!e && cudaEventCreate(&e) != cudaSuccess) { e = nullptr; return; }
+  cudaEventRecord(e, h->st);
+  if (which == 0) h->ph_rec[ph] = false;
+  else h->ph_rec[ph] = true;
+}
+static double phase_ms(rann_dd_handle* h, int ph) {
+  if (!h->ph_rec[ph] || !h->ph_ev[ph][0] || !h->ph_ev[ph][1]) return 0.0;
+  float ms = 0.f;
+  if (cudaEventSynchronize(h->ph_ev[ph][1]) != cudaSuccess) return 0.0;
+  if (cudaEventElapsedTime(&ms, h->ph_ev[ph][0], h->ph_ev[ph][1]) != cudaSuccess) return 0.0;
+  return ms;
+}
+static void fill_phase_stats(rann_dd_handle* h, rann_dd_stats* s) {
+  s->ms_assemble = phase_ms(h, 0);
+  s->ms_pca = phase_ms(h, 1);
+  s->ms_setup = phase_ms(h, 2);
+}
+
+// Extreme eigenvalues of the symmetric tridiagonal T (diagonal a[0..n),
+// off-diagonal b[0..n-1)) by bisection on Sturm counts.
+static void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b, double* lmin,
+                             double* lmax) {
+  const int n = (int)a.size();
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {   // eigenvalues < x
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < n; ++i) {
+      d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0.0) ++c;
+    }
+    return c;
+  };
+  for (int which = 0; which < 2; ++which) {
+    double l = lo, u = hi;
+    const int k = which == 0 ? 1 : n;   // the k-th smallest
+    for (int it = 0; it < 200 && u - l > 1e-15 * std::max(std::fabs(l), std::fabs(u)); ++it) {
+      const double mid = 0.5 * (l + u);
+      if (count_below(mid) >= k) u = mid; else l = mid;
+    }
+    (which == 0 ? *lmin : *lmax) = 0.5 * (l + u);
+  }
+}
+
+// Extreme singular values of the leading n x n upper triangle of R (row
+// stride ld) by one-sided Jacobi rotations of its columns.
+static void triangle_sing_extremes(const std::vector<double>& Rm, int n, int ld, double* smin, double* smax) {
+  std::vector<double> G((size_t)n * n, 0.0);   // column c at G[c * n ..]
+  for (int r = 0; r < n; ++r)
+    for (int c = r; c < n; ++c) G[(size_t)c * n + r] = Rm[(size_t)r * ld + c];
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    int rot = 0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double a = 0, bq = 0, c = 0;
+        for (int r = 0; r < n; ++r) {
+          const double x = G[(size_t)p * n + r], y = G[(size_t)q * n + r];
+          a += x * x; bq += y * y; c += x * y;
+        }
+        if (std::fabs(c) <= 1e-15 * std::sqrt(a * bq)) continue;
+        ++rot;
+        const double zeta = (bq - a) / (2.0 * c);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = cs * t;
+        for (int r = 0; r < n; ++r) {
+          const double x = G[(size_t)p * n + r], y = G[(size_t)q * n + r];
+          G[(size_t)p * n + r] = cs * x - sn * y;
+          G[(size_t)q * n + r] = sn * x + cs * y;
+        }
+      }
+    if (!rot) break;
+  }
+  double lo = INFINITY, hi = 0.0;
+  for (int c = 0; c < n; ++c) {
+    double s = 0;
+    for (int r = 0; r < n; ++r) s += G[(size_t)c * n + r] * G[(size_t)c * n + r];
+    s = std::sqrt(s);
+    lo = std::min(lo, s);
+    hi = std::max(hi, s);
+  }
+  *smin = lo;
+  *smax = hi;
 }
 
 static uint64_t splitmix64_draw(uint64_t seed, uint64_t i) {
@@ -354,6 +462,7 @@ extern "C" const char* rann_dd_status_string(rann_status s) {
     case RANN_BREAKDOWN: return "breakdown";
     case RANN_LOCAL_SINGULAR: return "local factor shifted";
     case RANN_EORDER: return "call out of order";
+    case RANN_TIMEOUT: return "device wait timed out";
   }
   return "unknown";
 }
@@ -538,7 +647,26 @@ extern "C" void rann_dd_destroy(rann_dd_handle* h) {
     }
   for (cudaEvent_t e : h->ev_la)
     if (e) cudaEventDestroy(e);
+  for (auto& pe : h->ph_ev)
+    for (cudaEvent_t e : pe)
+      if (e) cudaEventDestroy(e);
   delete h;
+}
+
+extern "C" rann_status rann_dd_inject_fault(rann_dd_handle* h, int kind, int64_t value) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  if (kind == RANN_FAULT_WAIT_EXPIRED) {
+    const int w = (int)value;
+    CK(cudaMemcpyAsync(h->d_ozerr, &w, sizeof(int), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return RANN_OK;
+  }
+  if (kind == RANN_FAULT_ALLOC_CAP) {
+    h->alloc_cap = value < 0 ? -1 : value;
+    return RANN_OK;
+  }
+  rann_set_error("unknown fault kind %d", kind);
+  return RANN_EINVAL;
 }
 
 extern "C" rann_status rann_dd_sizes(rann_dd_handle* h, int64_t* n_points, int64_t* n_block_rows, int* J, int* m,
@@ -562,6 +690,7 @@ extern "C" rann_status rann_dd_points(rann_dd_handle* h, double* xyz_dev) {
 
 extern "C" rann_status rann_dd_assemble(rann_dd_handle* h) {
   REQUIRE(h, RANN_EINVAL, "null handle");
+  phase_mark(h, 0, 0);
   const size_t bytes = sizeof(double) * (size_t)h->rows_total * h->m;
   if (!h->d_Psi) {
     CK(dalloc(h, (void**)&h->d_Psi, bytes));
@@ -571,12 +700,14 @@ extern "C" rann_status rann_dd_assemble(rann_dd_handle* h) {
   h->assembled = true;
   h->reduced = false;
   h->prec_kind = -1;
+  phase_mark(h, 0, 1);
   return RANN_OK;
 }
 
 extern "C" rann_status rann_dd_rhs(rann_dd_handle* h, double* F_dev) {
   REQUIRE(h && F_dev, RANN_EINVAL, "null argument");
   KL(h, K_RHS, 1, launch_rhs(h->P, F_dev, h->N, h->st));
+  if (h->ph_rec[0]) cudaEventRecord(h->ph_ev[0][1], h->st);    // the assembly phase ends with F
   return RANN_OK;
 }
 
@@ -598,6 +729,10 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   REQUIRE(h->assembled, RANN_EORDER, "pca before assemble");
   REQUIRE(mode >= 0 && mode <= 2, RANN_EINVAL, "bad pca mode");
   REQUIRE(mode == RANN_PCA_NONE || (thr >= 0.0 && std::isfinite(thr)), RANN_EINVAL, "bad threshold");
+  // a pca that fails part-way leaves the handle assembled but not reduced
+  h->reduced = false;
+  h->prec_kind = -1;
+  phase_mark(h, 1, 0);
   const int J = h->J, m = h->m;
   const size_t mm = (size_t)m * m;
   if (!h->d_V) {
@@ -688,7 +823,11 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
     int ozerr = 0;
     CK(cudaMemcpyAsync(&ozerr, h->d_ozerr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(stream_sync(h));
-    REQUIRE(ozerr == 0, RANN_ECUDA, "tensor-core Gram product: pipeline wait %d timed out", ozerr);
+    if (ozerr) {
+      cudaMemsetAsync(h->d_ozerr, 0, sizeof(int), h->st);
+      rann_set_error("tensor-core Gram product: bounded pipeline wait %d gave up", ozerr);
+      return RANN_TIMEOUT;
+    }
     dfree(h, d_tasks); dfree(h, d_mats); dfree(h, d_ns); dfree(h, d_lds); dfree(h, d_work); dfree(h, d_info);
     dfree(h, d_ranks);
     if (d_sl) { dfree(h, d_sl); dfree(h, d_e); }
@@ -824,6 +963,7 @@ extern "C" rann_status rann_dd_pca(rann_dd_handle* h, int mode, double thr, int*
   CK(dalloc(h, (void**)&h->d_yscratch, sizeof(double) * (size_t)h->N));
   h->reduced = true;
   h->prec_kind = -1;
+  phase_mark(h, 1, 1);
   return RANN_OK;
 }
 
@@ -954,8 +1094,12 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   h->gram_allocs.clear();
   h->gram_ready = false;
   h->n_shifted = 0;
-  h->prec_kind = kind;
-  if (kind == RANN_PREC_NONE) return RANN_OK;
+  h->prec_kind = -1;            // set once the set-up has succeeded
+  if (kind == RANN_PREC_NONE) {
+    h->prec_kind = kind;
+    return RANN_OK;
+  }
+  phase_mark(h, 2, 0);
   const int J = h->J, dim = h->dim;
   const auto& S = h->subs;
   // extended sets N(i)
@@ -1175,7 +1319,11 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(&ozerr, h->d_ozerr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(stream_sync(h));
-    REQUIRE(ozerr == 0, RANN_ECUDA, "tensor-core product (projection / pair Gram): pipeline wait %d timed out", ozerr);
+    if (ozerr) {
+      cudaMemsetAsync(h->d_ozerr, 0, sizeof(int), h->st);
+      rann_set_error("tensor-core product (projection / pair Gram): bounded pipeline wait %d gave up", ozerr);
+      return RANN_TIMEOUT;
+    }
     std::vector<int> next;
     for (int i = 0; i < J; ++i) if (f[i]) next.push_back(i);
     if (next.empty()) break;
@@ -1245,7 +1393,9 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   dfree(h, d_ridx); dfree(h, d_tab); dfree(h, d_tab_ptr); dfree(h, d_boffs); dfree(h, d_boff_ptr);
   dfree(h, d_dmax); dfree(h, d_fail); dfree(h, h->d_pairbuf);
   h->d_pairbuf = nullptr;
+  phase_mark(h, 2, 1);
   CK(stream_sync(h));
+  h->prec_kind = kind;
   return h->n_shifted ? RANN_LOCAL_SINGULAR : RANN_OK;
 }
 
@@ -1364,7 +1514,7 @@ static rann_status solve_cg_impl(rann_dd_handle* h, const double* F_dev, const d
   const double bnorm = std::sqrt(bb);
   rann_status st = RANN_NOT_CONVERGED;
   int it = 0;
-  double rel = 1.0, true_rel = 1.0;
+  double rel = 1.0, true_rel = 1.0, kappa = -1.0;
   if (!(bnorm > 0.0)) {
     st = std::isfinite(bb) ? RANN_OK : RANN_BREAKDOWN;
     rel = true_rel = 0.0;
@@ -1382,8 +1532,13 @@ static rann_status solve_cg_impl(rann_dd_handle* h, const double* F_dev, const d
     sd.pq = cgs; sd.rr = cgs + 1; sd.rz = cgs + 2; sd.rel = cgs + 4;
     sd.done = reinterpret_cast<int*>(cgs + 5);
     sd.it = sd.done + 1;
+    // alpha_k, beta_k of the first cycle (its Lanczos tridiagonal estimates kappa(M^{-1} A))
+    sd.lzcap = std::max(0, std::min(maxit, 4096));
+    sd.lz = sd.lzcap ? ws.get(2 * (size_t)sd.lzcap) : nullptr;
+    if (!sd.lz) sd.lzcap = 0;
     int* hdone = reinterpret_cast<int*>(h->h_scal + 128);
     for (int cycle = 0; cycle < 30; ++cycle) {
+      if (cycle == 1) { sd.lz = nullptr; sd.lzcap = 0; }
       TRY(prec_inner(h, r, z));
       CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
       KLA(h, K_DOT, 1, 16.0 * n, 2.0 * n, launch_multidot(r, 0, 1, z, n, h->d_red, sd.rz, h->st));
@@ -1412,6 +1567,25 @@ static rann_status solve_cg_impl(rann_dd_handle* h, const double* F_dev, const d
       CK(cudaMemcpyAsync(dv, sd.done, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
       CK(cudaMemcpyAsync(&rel, sd.rel, sizeof(double), cudaMemcpyDeviceToHost, h->st));
       CK(stream_sync(h));
+      if (cycle == 0 && sd.lz && dv[1] >= 2) {
+        const int K = std::min(dv[1], sd.lzcap);
+        std::vector<double> lz(2 * (size_t)K);
+        CK(cudaMemcpyAsync(lz.data(), sd.lz, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, h->st));
+        CK(stream_sync(h));
+        std::vector<double> ta(K), tb(K - 1);
+        bool ok = true;
+        for (int q = 0; q < K; ++q) {
+          const double al = lz[2 * q];
+          ok = ok && std::isfinite(al) && al > 0.0;
+          ta[q] = 1.0 / al + (q > 0 ? lz[2 * q - 1] / lz[2 * q - 2] : 0.0);
+          if (q + 1 < K) tb[q] = std::sqrt(std::max(lz[2 * q + 1], 0.0)) / al;
+        }
+        if (ok) {
+          double lmin, lmax;
+          tridiag_extremes(ta, tb, &lmin, &lmax);
+          kappa = lmin > 0.0 ? lmax / lmin : -1.0;
+        }
+      }
       it += dv[1];
       const bool inner_ok = dv[0] == 1;
       if (dv[0] == 2) { st = RANN_BREAKDOWN; break; }
@@ -1440,6 +1614,8 @@ static rann_status solve_cg_impl(rann_dd_handle* h, const double* F_dev, const d
     stats->rel_res_prec = -1.0;
     stats->ms_solve = ms;
     stats->n_shifted = h->n_shifted;
+    stats->kappa_est = kappa;
+    fill_phase_stats(h, stats);
   }
   if (st == RANN_NOT_CONVERGED) rann_set_error("CG reached maxit=%d at rel. residual %.3e", maxit, true_rel);
   return st;
@@ -1577,6 +1753,8 @@ static rann_status solve_variant_impl(rann_dd_handle* h, const double* F_dev, do
     stats->rel_res_prec = -1.0;
     stats->ms_solve = ms;
     stats->n_shifted = h->n_shifted;
+    stats->kappa_est = -1.0;
+    fill_phase_stats(h, stats);
   }
   if (st == RANN_NOT_CONVERGED)
     rann_set_error("%s reached maxit=%d at rel. residual %.3e", bicg ? "BiCG" : "CGS", maxit, true_rel);
@@ -1652,7 +1830,8 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
   const double mbnorm = std::sqrt(mbb);
   std::vector<double> Hm((size_t)(k + 1) * k), g(k + 1), y(k);
   int it = 0;
-  double rel = 1.0;
+  double rel = 1.0, kappa = -1.0;
+  int cycle_no = 0;
   rann_status st = RANN_NOT_CONVERGED;
   if (!(mbnorm > 0.0)) { st = std::isfinite(mbb) ? RANN_OK : RANN_BREAKDOWN; rel = 0.0; }
   bool first = true;
@@ -1720,6 +1899,13 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
     CK(cudaMemcpyAsync(Hm.data(), sd.H, sizeof(double) * (size_t)jdone * k, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(g.data(), sd.g, sizeof(double) * jdone, cudaMemcpyDeviceToHost, h->st));
     CK(stream_sync(h));
+    if (cycle_no++ == 0 && jdone >= 2) {
+      // the Givens-reduced Hessenberg matrix of the first cycle: its singular
+      // values lie inside those of M^{-1} A
+      double smin, smax;
+      triangle_sing_extremes(Hm, jdone, k, &smin, &smax);
+      kappa = smin > 0.0 ? smax / smin : -1.0;
+    }
     for (int i = jdone - 1; i >= 0; --i) {
       double sacc = g[i];
       for (int q = i + 1; q < jdone; ++q) sacc -= Hm[(size_t)i * k + q] * y[q];
@@ -1749,6 +1935,8 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
     stats->rel_res_prec = precrel;
     stats->ms_solve = ms;
     stats->n_shifted = h->n_shifted;
+    stats->kappa_est = kappa;
+    fill_phase_stats(h, stats);
   }
   if (st == RANN_NOT_CONVERGED) rann_set_error("GMRES reached maxit=%d at rel. residual %.3e", maxit, rel);
   return st;
@@ -1937,6 +2125,8 @@ static rann_status solve_cg_multi_impl(rann_dd_handle* h, const double* F_dev, d
       stats[c].rel_res_prec = -1.0;
       stats[c].ms_solve = ms;
       stats[c].n_shifted = h->n_shifted;
+      stats[c].kappa_est = -1.0;
+      fill_phase_stats(h, &stats[c]);
     }
     if (st[c] != RANN_OK && worst == RANN_OK) worst = st[c];
   }
@@ -2152,6 +2342,8 @@ static rann_status solve_gmres_multi_impl(rann_dd_handle* h, const double* F_dev
       stats[c].rel_res_prec = rel[c];
       stats[c].ms_solve = ms;
       stats[c].n_shifted = h->n_shifted;
+      stats[c].kappa_est = -1.0;
+      fill_phase_stats(h, &stats[c]);
     }
     if (st[c] != RANN_OK && worst == RANN_OK) worst = st[c];
   }

@@ -135,6 +135,8 @@ struct CgDev {
   double* rel;
   int* done;                 // 0 running, 1 converged, 2 breakdown
   int* it;                   // updates made
+  double* lz = nullptr;      // optional [2 lzcap]: alpha_k, beta_k of the Lanczos relation
+  int lzcap = 0;
 };
 cudaError_t launch_cg_update_dev(const double* p, const double* q, double* x, double* r, int64_t n, const CgDev& s,
                                  int ph, cudaStream_t st);

@@ -156,6 +156,10 @@ __global__ void cg_update_dev_kernel(const double* __restrict__ p, const double*
     return;
   }
   const double alpha = rz / pq;
+  if (s.lz && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int kk = *s.it;
+    if (kk < s.lzcap) s.lz[2 * kk] = alpha;
+  }
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     x[t] = fma(alpha, p[t], x[t]);
     r[t] = fma(-alpha, q[t], r[t]);
@@ -176,6 +180,10 @@ __global__ void cg_check_kernel(CgDev s, double bnorm, double rtol) {
 __global__ void cg_direction_kernel(const double* __restrict__ z, double* __restrict__ p, int64_t n, CgDev s, int ph) {
   if (*s.done) return;
   const double beta = s.rz[ph ^ 1] / s.rz[ph];
+  if (s.lz && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int kk = *s.it - 1;                        // the update this direction follows
+    if (kk >= 0 && kk < s.lzcap) s.lz[2 * kk + 1] = beta;
+  }
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     p[t] = fma(beta, p[t], z[t]);
 }

@@ -23,12 +23,10 @@ blocks the checks need (in worker processes; it is seconds per block).
     m = 300, against the oracle's Householder QR of the same A_i, to the
     factor accuracy kappa(A_i) u (u = 2^-53 for float64 factors, 2^-48 for
     double-float ones), with kappa(A_i) measured;
-  * the full multiscale workload solved end to end (SAS-GMRES(50), as the
-    benchmark runs it, and AS-CG) against the oracle's own Krylov solve of
-    the same reduced system (the GPU's ranks): the least-squares residuals
-    agree to 1e-8 ||F||, and the fitted values H W and u_hat agree to the
-    bound the normal-equation residuals allow (printed with the measured
-    difference).
+  * the full multiscale workload solved end to end (SAS-GMRES(50) and
+    AS-CG) against the oracle's own Krylov solve at the GPU's ranks: the
+    least-squares residuals agree to 1e-8 ||F||, and the u_hat difference is
+    printed with the condition estimate and held to 1e-6 (see the test).
 """
 import numpy as np
 import pytest
@@ -176,14 +174,18 @@ def test_fullsize_local_solve(g, mode, kind):
 
 
 def test_fullsize_multiscale_solve(g):
-    """Sec. 5: the full multiscale workload, GPU against the oracle's Krylov
-    solve of the same reduced problem.  Two solutions W1, W2 whose float64
-    normal residuals are r1, r2 satisfy ||H (W1 - W2)|| <= (||r1|| + ||r2||) /
-    sigma_min(H); sigma_min is bounded below through the principal
-    submatrices (interlacing: lambda_min(H^T H) <= lambda_min(A_i)) only in
-    the wrong direction, so the fitted values are held to the bound with
-    sigma_min(H)^2 replaced by the smallest eigenvalue of the centre set's
-    A_i divided by 100, and the measured differences are printed beside it."""
+    """Sec. 5: the full multiscale workload (DoF ~ 6300, 102400 collocation
+    points), GPU against the oracle's own AS-CG solve (float64 assembly,
+    Jacobi-SVD PCA at the GPU's ranks, Householder-QR local solves).  The two
+    reduced bases differ at rounding level (Gram eigen-decomposition against
+    Jacobi SVD), so the solutions are compared as functions: the collocated
+    residuals H W - F (each side's own H) and u_hat at 101^2 test points.
+    The least-squares residual norms agree to 1e-8 ||F|| (both minimise it
+    to second order in their normal residuals); the u_hat difference has no
+    a-priori bound here (sigma_min of the 102400 x 6300 H is beyond the
+    oracle), so it is printed with the GPU's condition estimate and held to
+    1e-6, ten times the difference that the small multiscale problem shows
+    between the exact solutions of the two bases (7.9e-7)."""
     name = "multiscale2d"
     p, s, F, ranks = reduced(g, name)
     R, b = ri.weights(p)
@@ -198,29 +200,23 @@ def test_fullsize_multiscale_solve(g):
     idx = [np.concatenate([np.arange(So.offsets[k], So.offsets[k + 1]) for k in ks]) for ks in sets]
     M = sv.Schwarz("as", sets, idx, [np.ones(ix.shape[0]) for ix in idx], qrs)
     sol = sv.solve(So, "cg", M, 1e-10, 50, 3000)
-    bnorm = np.linalg.norm(So.HT(So.F))
-    lam_min_centre = float(np.linalg.eigvalsh(mats[4 * 8 + 4])[0])
     X = ri.test_points(p, 101)
     uo = sv.evaluate(So, sol.W, X)
     Fn = np.linalg.norm(So.F)
+    fo = So.H(sol.W)
     for kind, solver in (("sas", "gmres"), ("as", "cg")):
         s.setup_precond(kind)
         if solver == "gmres":
             W, st = s.solve_gmres_ras(F, 1e-10, 50, 3000)
         else:
             W, st = s.solve_cg_as(F, 1e-10, 3000)
-        Wn = W.cpu().numpy()
-        res_g = np.linalg.norm(So.H(Wn) - So.F)
-        rn_g = np.linalg.norm(So.HT(So.F - So.H(Wn)))
-        rn_o = sol.rel_res_normal * bnorm
-        fit = np.linalg.norm(So.H(Wn) - So.H(sol.W))
-        bound = (rn_g + rn_o) / np.sqrt(lam_min_centre / 100.0)
+        fg = s.matvec(W).cpu().numpy()
+        res_g = np.linalg.norm(fg - So.F)
         ug = s.eval(W, torch.tensor(X, device="cuda")).cpu().numpy()
         du = np.linalg.norm(ug - uo) / np.linalg.norm(uo)
-        print(f"\n{name} {kind}-{solver}: GPU iters {st['iters']}, oracle AS-CG iters {sol.iters}; "
-              f"||HW-F|| GPU {res_g:.6e} oracle {sol.res_ls:.6e}; normal residual GPU {rn_g / bnorm:.2e} "
-              f"oracle {sol.rel_res_normal:.2e}; ||H(W_gpu - W_oracle)||/||F|| = {fit / Fn:.3e} "
-              f"(bound {bound / Fn:.3e}, lambda_min(A_centre) {lam_min_centre:.3e}); "
-              f"u_hat relative difference {du:.3e}")
+        print(f"\n{name} {kind}-{solver}: GPU iters {st['iters']} (normal residual {st['rel_res_true']:.2e}, "
+              f"kappa_est(M^-1 A) {st['kappa_est']:.3e}), oracle AS-CG iters {sol.iters} (normal residual "
+              f"{sol.rel_res_normal:.2e}); ||HW-F|| GPU {res_g:.9e} oracle {sol.res_ls:.9e}; "
+              f"||H_g W_g - H_o W_o|| / ||F|| = {np.linalg.norm(fg - fo) / Fn:.3e}; u_hat difference {du:.3e}")
         assert abs(res_g - sol.res_ls) <= 1e-8 * Fn
-        assert fit <= bound
+        assert du <= 1e-6
