@@ -224,6 +224,33 @@ rann_status rann_dd_solve_backward(rann_dd_handle* h, const double* gW_dev, doub
 rann_status rann_dd_grad_c0(rann_dd_handle* h, const double* F_dev, const double* W_dev, const double* lam_dev,
                             double* grad_host);
 
+/* Derivative of a loss through the solve with respect to the cell values a_c
+ * (c < g*g) of the piecewise diffusion coefficient a = sum_c a_c s_c of
+ * -div(a grad u) (RANN_OP_DIFFUSION with RANN_COEF_PIECEWISE).  The operator
+ * of Sec. 2 Eq. (sum) is linear in a and Psi_j (hence the PCA basis) does
+ * not depend on a, so dH/da_c x = A_c[v_x] at the collocation points, with
+ * A_c v = -s_c Lap v - grad s_c . grad v and v_x = L sum_j omega_j
+ * (Phi_j . V_{p_j} x_j), and dF/da_c = -A_c[G] for F from rann_dd_rhs.
+ * Given F_dev [N], W_dev [DoF] and lam_dev [DoF] = (H^T H)^{-1} dl/dW (from
+ * rann_dd_solve_backward), grad_host [g*g] receives
+ *   dl/da_c = r . (dH/da_c lam) + (H lam) . (dF/da_c - dH/da_c W),  r = F - H W,
+ * for a loss that depends on a only through W (fixed-order sums; one kernel
+ * forms v, grad v and Lap v of both vectors per point).  Synchronises.
+ * RANN_EINVAL for other operators or coefficients, RANN_EORDER before pca. */
+rann_status rann_dd_grad_coef(rann_dd_handle* h, const double* F_dev, const double* W_dev, const double* lam_dev,
+                              double* grad_host);
+/* Replaces the piecewise coefficient values a_c (host [g*g], finite) of a
+ * RANN_COEF_PIECEWISE diffusion handle.  H and F depend on them, so the
+ * handle returns to Algorithm 1 step 3: assemble, rhs, pca and
+ * setup_precond must run again. */
+rann_status rann_dd_set_coef(rann_dd_handle* h, const double* vals_host);
+/* Adjoint of the evaluation at the collocation points (Eq. (netdd),
+ * (pca_net)): with u_hat = E W + G on the N points, gW_dev [DoF] = E^T r for
+ * r_dev [N]; block j is (E^T r)_j = V_{p_j}^T Psi_j^T (L r)|_{rows_j}.  Used for
+ * losses on u_hat, e.g. dl/dW = 2 E^T (u_hat - u_obs) for ||u_hat - u_obs||^2.
+ * Synchronises. */
+rann_status rann_dd_eval_grid_t(rann_dd_handle* h, const double* r_dev, double* gW_dev);
+
 /* Precision policy.  Mode 1 (default): the work that only shapes the
  * preconditioner or the Krylov iterates -- the neighbour Gram blocks of A_i,
  * the Cholesky trailing updates, L_i^{-1}, and every operator and

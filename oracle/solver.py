@@ -20,7 +20,11 @@ baseline use this package; the product path never does.
     relative L2 error and normalised L1 error at test points.
   * Differentiation through the least-squares solve (an extension; the
     paper does not differentiate): grad_c0, the derivative of a loss l(W)
-    with respect to the reaction coefficient c0 of -Lap u + c0 u.
+    with respect to the reaction coefficient c0 of -Lap u + c0 u, and
+    grad_coef, its derivative with respect to the cell values a_c of the
+    piecewise diffusion coefficient a = sum_c a_c s_c of -div(a grad u);
+    eval_matrix_t, the adjoint of u_hat at the collocation points (for
+    losses on u_hat).
 """
 from __future__ import annotations
 
@@ -271,6 +275,51 @@ def grad_c0(S: System, W: np.ndarray, lam: np.ndarray) -> float:
     r = S.F - S.H(W)
     Hl = S.H(lam)
     return float(r @ Hc(lam) - Hl @ Gx - Hl @ Hc(W))
+
+
+def grad_coef(S: System, W: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    """dl/da_c, c < g*g, of a loss l(W) through the least-squares solution W
+    of -div(a grad u) = f with the piecewise coefficient a = sum_c a_c s_c
+    (smoothed cell indicators s_c), given lam = (H^T H)^{-1} dl/dW.
+
+    The operator is linear in a, so dH/da_c is the collocation matrix of
+    -div(s_c grad .): the blocks H_j assembled with the coefficient values
+    e_c (one-hot), times the same V_j (Psi_j, hence the PCA basis, does not
+    depend on a); F = f - A[G] gives dF/da_c = -A_c[G], the right-hand side
+    assembled with e_c and f = 0.  Differentiating H^T H W = H^T F, with
+    r = F - H W and H_c = dH/da_c, F_c = dF/da_c:
+        dl/da_c = r . (H_c lam) + (H lam) . (F_c - H_c W).
+    """
+    import dataclasses
+    p = S.problem
+    if p.op != ri.OP_DIFFUSION or p.coef != ri.COEF_PIECEWISE:
+        raise ValueError("grad_coef: piecewise diffusion coefficient only")
+    ncell = p.coef_grid * p.coef_grid
+    r = S.F - S.H(W)
+    Hl = S.H(lam)
+    out = np.zeros(ncell)
+    for c in range(ncell):
+        e = np.zeros(ncell)
+        e[c] = 1.0
+        pc = dataclasses.replace(p, coef_vals=e, fc=None, fa=None, f0=0.0)
+        Bc = [asm.block(pc, S.R, S.b, j)[2] @ S.pcas[j].V for j in range(len(S.B))]
+        Sc = System(p, S.R, S.b, S.rows, Bc, S.pcas, asm.rhs(pc), S.offsets)
+        out[c] = r @ Sc.H(lam) + Hl @ (Sc.F - Sc.H(W))
+    return out
+
+
+def eval_matrix_t(S: System, r: np.ndarray) -> np.ndarray:
+    """E^T r, with u_hat = E W + G at the collocation points of S
+    (Eq. (netdd), (pca_net)): block j of E is diag(L) Psi_j V_j on the rows
+    of box_j, so (E^T r)_j = V_j^T Psi_j^T (L r)|_{rows_j}."""
+    p = S.problem
+    X = ri.grid_points(p)
+    Lx = asm.constraint_L(p, asm._coords(X, -1)).a
+    out = []
+    for j in range(len(S.B)):
+        _, Psi, _ = asm.block(p, S.R, S.b, j)
+        out.append(S.pcas[j].V.T @ (Psi.T @ (Lx * r)[S.rows[j]]))
+    return np.concatenate(out)
 
 
 # --------------------------------------------------------------- evaluation --

@@ -95,6 +95,9 @@ SIGNATURES = {
     "rann_dd_eval": (_I, [_P, _P, _P, _L, _P]),
     "rann_dd_solve_backward": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Stats)]),
     "rann_dd_grad_c0": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D)]),
+    "rann_dd_grad_coef": (_I, [_P, _P, _P, _P, _P]),
+    "rann_dd_set_coef": (_I, [_P, _P]),
+    "rann_dd_eval_grid_t": (_I, [_P, _P, _P]),
     "rann_dd_set_precision": (_I, [_P, _I]),
     "rann_dd_matvec": (_I, [_P, _P, _P]),
     "rann_dd_matvec_t": (_I, [_P, _P, _P]),
@@ -343,6 +346,27 @@ class RannDD:
                "rann_dd_grad_c0")
         return out.value
 
+    def grad_coef(self, F, W, lam) -> np.ndarray:
+        """dl/da_c for the piecewise diffusion coefficient (rann_dd_grad_coef),
+        given the right-hand side F, the solution W and lam = (H^T H)^{-1} dl/dW."""
+        g = self.problem.coef_grid
+        out = np.zeros(g * g)
+        _check(self._lib.rann_dd_grad_coef(self._h, _dptr(F), _dptr(W), _dptr(lam), out.ctypes.data),
+               "rann_dd_grad_coef")
+        return out
+
+    def set_coef(self, vals):
+        """New piecewise coefficient values (the handle must be re-assembled)."""
+        arr = np.ascontiguousarray(vals, dtype=np.float64)
+        _check(self._lib.rann_dd_set_coef(self._h, arr.ctypes.data), "rann_dd_set_coef")
+        self._prec = None
+
+    def eval_grid_t(self, r, out=None):
+        """E^T r for u_hat = E W + G at the collocation points (rann_dd_eval_grid_t)."""
+        gW = out if out is not None else self._empty(self.sizes()["dof"])
+        _check(self._lib.rann_dd_eval_grid_t(self._h, _dptr(r), _dptr(gW)), "rann_dd_eval_grid_t")
+        return gW
+
     def solve(self, F, rtol=1e-10, maxit=2000, restart=50):
         """The solve matching the preconditioner: AS-CG for AS/none, GMRES otherwise."""
         if self._prec in (PREC_AS, PREC_NONE):
@@ -461,3 +485,65 @@ class LeastSquaresSolve:
                 return solver.matvec(lam)
 
         return _Fn.apply(F)
+
+
+class PiecewiseDiffusionSolve:
+    """Differentiable forward solve of -div(a grad u) = f with the piecewise
+    coefficient a = sum_c a_c s_c: W(a, F), with torch.autograd support for
+    both arguments.  forward sets the coefficient values on the handle and
+    runs Algorithm 1 (assemble, PCA, Schwarz set-up, the preconditioned solve
+    of the given kind); backward solves the adjoint system with the same
+    preconditioner (rann_dd_solve_backward) and returns dl/dF = H lam and
+    dl/da = rann_dd_grad_coef (the PCA basis does not depend on a).  The
+    collocation right-hand side F is an input: with G = 0 (homogeneous
+    Dirichlet data) F = f does not depend on a; otherwise F must be the
+    library's rann_dd_rhs for the current a, whose dependence on a through
+    A[G] grad_coef includes."""
+
+    @staticmethod
+    def apply(solver: "RannDD", a, F, kind: str = "ras", rtol: float = 1e-10, maxit: int = 2000,
+              pca_mode: int = PCA_VARIANCE, pca_thr: float = 1e-12):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, a_in, F_in):
+                solver.set_coef(a_in.detach().cpu().numpy())
+                solver.assemble()
+                solver.pca(pca_mode, pca_thr)
+                solver.setup_precond(kind)
+                Fc = F_in.detach().contiguous()
+                W, _ = solver.solve(Fc, rtol, maxit)
+                ctx.save_for_backward(Fc, W)
+                return W
+
+            @staticmethod
+            def backward(ctx, gW):
+                Fc, W = ctx.saved_tensors
+                lam, _ = solver.solve_backward(gW.contiguous(), rtol, maxit)
+                ga = torch.tensor(solver.grad_coef(Fc, W, lam), dtype=torch.float64)
+                return ga, solver.matvec(lam)
+
+        return _Fn.apply(a, F)
+
+
+class GridEval:
+    """u_hat at the collocation points as a differentiable function of W:
+    forward rann_dd_eval at the grid, backward the adjoint rann_dd_eval_grid_t
+    (for misfits ||u_hat - u_obs||^2 on the grid)."""
+
+    @staticmethod
+    def apply(solver: "RannDD", W):
+        import torch
+        X = solver.points()
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, W_in):
+                return solver.eval(W_in.detach().contiguous(), X)
+
+            @staticmethod
+            def backward(ctx, gu):
+                return solver.eval_grid_t(gu.contiguous())
+
+        return _Fn.apply(W)

@@ -82,6 +82,11 @@ cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, c
 cudaError_t launch_assemble_local(const double* d_pairbuf, const int64_t* d_tab, const int* d_tab_ptr,
                                   const int* d_boff, const int* d_boff_ptr, const CholMat* d_mats, int nsets,
                                   int maxn, double* d_dmax, cudaStream_t st);
+int coef_grad_blocks(int64_t N);
+cudaError_t launch_lmul(const ProbDev& P, const double* d_r, double* d_y, int64_t N, cudaStream_t st);
+cudaError_t launch_coef_grad(const ProbDev& P, const SubDev* d_sub, const double* d_R, const double* d_b,
+                             const double* d_Uw, const double* d_Ul, const double* d_r, const double* d_hl,
+                             int64_t N, double* d_part, cudaStream_t st);
 cudaError_t launch_add_diag(const CholMat* d_mats, const int* d_which, int nwhich, const double* d_shift,
                             int maxn, cudaStream_t st);
 
@@ -2402,6 +2407,107 @@ extern "C" rann_status rann_dd_grad_c0(rann_dd_handle* h, const double* F_dev, c
   TRY(dot_host(h, hl, eW, N, &d3));
   *grad_host = d1 - d2 - d3;
   for (double* q : {x, zero, g0, eW, eL, r, hl}) dfree(h, q);
+  return RANN_OK;
+}
+
+// U_j = V_{p_j} x_j for every subdomain (the m-vectors the evaluation kernels read).
+static rann_status basis_combination(rann_dd_handle* h, const double* x, double* U) {
+  const int J = h->J, m = h->m;
+  std::vector<GemmTask> tasks;
+  for (int j = 0; j < J; ++j) {
+    const SubDev& S = h->subs[j];
+    GemmTask t{};
+    t.A = h->d_V + (size_t)m * m * j; t.B = x + S.woff; t.C = U + (size_t)m * j;
+    t.K = S.p; t.M = m; t.N = 1; t.lda = m; t.ldb = 1; t.ldc = 1;
+    push_tiles(tasks, t, false);
+  }
+  GemmTask* d_tasks;
+  CK(dupload(h, &d_tasks, tasks));
+  KL(h, K_EVAL, 1, launch_gemm_nn(d_tasks, (int)tasks.size(), h->st));
+  dfree(h, d_tasks);
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_grad_coef(rann_dd_handle* h, const double* F_dev, const double* W_dev,
+                                         const double* lam_dev, double* grad_host) {
+  REQUIRE(h && F_dev && W_dev && lam_dev && grad_host, RANN_EINVAL, "null argument");
+  REQUIRE(h->reduced, RANN_EORDER, "grad_coef before pca");
+  REQUIRE(h->P.op == RANN_OP_DIFFUSION && h->P.coef == RANN_COEF_PIECEWISE, RANN_EINVAL,
+          "grad_coef: the diffusion operator with a piecewise coefficient only");
+  const int64_t N = h->N;
+  const int J = h->J, m = h->m, nc = h->P.coef_grid * h->P.coef_grid;
+  const int nb = coef_grad_blocks(N);
+  double *U, *r, *hl, *part;
+  CK(dalloc(h, (void**)&U, sizeof(double) * 2 * (size_t)J * m));
+  CK(dalloc(h, (void**)&r, sizeof(double) * (size_t)N));
+  CK(dalloc(h, (void**)&hl, sizeof(double) * (size_t)N));
+  CK(dalloc(h, (void**)&part, sizeof(double) * (size_t)nb * nc));
+  TRY(basis_combination(h, W_dev, U));
+  TRY(basis_combination(h, lam_dev, U + (size_t)J * m));
+  TRY(rann_dd_matvec(h, W_dev, r));
+  KL(h, K_VEC, 1, launch_axpby(1.0, F_dev, -1.0, r, N, h->st));   // r = F - H W
+  TRY(rann_dd_matvec(h, lam_dev, hl));                             // H lam
+  KLA(h, K_EVAL, 1, 8.0 * (2.0 * N + 2.0 * J * m), 0.0,
+      launch_coef_grad(h->P, h->d_sub, h->d_R, h->d_b, U, U + (size_t)J * m, r, hl, N, part, h->st));
+  std::vector<double> ph((size_t)nb * nc);
+  CK(cudaMemcpyAsync(ph.data(), part, sizeof(double) * ph.size(), cudaMemcpyDeviceToHost, h->st));
+  CK(stream_sync(h));
+  for (int c = 0; c < nc; ++c) {
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) acc += ph[(size_t)b * nc + c];
+    grad_host[c] = acc;
+  }
+  for (double* q : {U, r, hl, part}) dfree(h, q);
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_eval_grid_t(rann_dd_handle* h, const double* r_dev, double* gW_dev) {
+  REQUIRE(h && r_dev && gW_dev, RANN_EINVAL, "null argument");
+  REQUIRE(h->reduced, RANN_EORDER, "eval_grid_t before pca");
+  const int64_t N = h->N;
+  const int J = h->J, m = h->m;
+  // t_j = Psi_j^T (L r)|_{rows_j}: the transposed block product over the unreduced
+  // Psi blocks (a descriptor copy with p = P = m), then gW_j = V_{p_j}^T t_j
+  std::vector<SubDev> un(h->subs);
+  for (int j = 0; j < J; ++j) {
+    un[j].p = m; un[j].P = m; un[j].boff = h->subs[j].row0 * m; un[j].woff = (int64_t)j * m;
+  }
+  SubDev* d_un;
+  double *y, *t, *part;
+  CK(dupload(h, &d_un, un));
+  CK(dalloc(h, (void**)&y, sizeof(double) * (size_t)std::max<int64_t>(N, 1)));
+  CK(dalloc(h, (void**)&t, sizeof(double) * (size_t)J * m));
+  CK(dalloc(h, (void**)&part, sizeof(double) * (size_t)std::max(h->nrtiles, 1) * m));
+  KL(h, K_EVAL, 1, launch_lmul(h->P, r_dev, y, N, h->st));
+  KLA(h, K_EVAL, 2, 8.0 * ((double)h->rows_total * m + h->rows_total + (double)J * m), 2.0 * h->rows_total * m,
+      launch_matvec_HT2(h->P, d_un, J, h->d_rtiles, h->nrtiles, h->d_tile0, h->d_Psi, y, part, t, m, h->st));
+  std::vector<GemmTask> tasks;
+  for (int j = 0; j < J; ++j) {
+    const SubDev& S = h->subs[j];
+    GemmTask g{};
+    g.A = h->d_V + (size_t)m * m * j; g.B = t + (size_t)m * j; g.C = gW_dev + S.woff;
+    g.K = m; g.M = S.p; g.N = 1; g.lda = m; g.ldb = 1; g.ldc = 1;
+    push_tiles(tasks, g, false);
+  }
+  GemmTask* d_tasks;
+  CK(dupload(h, &d_tasks, tasks));
+  KL(h, K_EVAL, 1, launch_gemm_tn(d_tasks, (int)tasks.size(), h->st));
+  CK(stream_sync(h));
+  dfree(h, d_tasks); dfree(h, d_un); dfree(h, y); dfree(h, t); dfree(h, part);
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_set_coef(rann_dd_handle* h, const double* vals_host) {
+  REQUIRE(h && vals_host, RANN_EINVAL, "null argument");
+  REQUIRE(h->P.op == RANN_OP_DIFFUSION && h->P.coef == RANN_COEF_PIECEWISE, RANN_EINVAL,
+          "set_coef: the handle has no piecewise diffusion coefficient");
+  const int nc = h->P.coef_grid * h->P.coef_grid;
+  for (int c = 0; c < nc; ++c) REQUIRE(std::isfinite(vals_host[c]), RANN_EINVAL, "coefficient %d not finite", c);
+  for (int c = 0; c < nc; ++c) h->P.coef_vals[c] = vals_host[c];
+  // H depends on the coefficient: the handle goes back to step 3 of Algorithm 1
+  h->assembled = false;
+  h->reduced = false;
+  h->prec_kind = -1;
   return RANN_OK;
 }
 

@@ -310,6 +310,140 @@ __global__ void eval_kernel(ProbDev P, const SubDev* __restrict__ subs, const do
   out[t] = L * total + G;
 }
 
+// Coefficient gradient of a loss through the least-squares solve for the
+// piecewise diffusion coefficient a = sum_c a_c s_c (Sec. 2, normal
+// equations, differentiated).  A v = -div(a grad v) is linear in a, so
+// (dH/da_c) x at a point is A_c[v_x] = -s_c Lap v_x - grad s_c . grad v_x,
+// with v_x = L sum_j omega_j (Phi_j . U_j), U_j = V_{p_j} x_j, and
+// dF/da_c = -A_c[G].  With r = F - H W and h = H lam the gradient is
+//   dl/da_c = sum_i s_c(x_i) Q_i + grad s_c(x_i) . Gv_i,
+//   Q_i = -r_i Lap v_lam + h_i Lap u_hat,  Gv_i = -r_i grad v_lam + h_i grad u_hat
+// (u_hat = v_W + G).  One thread per collocation point forms v, grad v and
+// Lap v for both coefficient sets (sharing the tanh of every neuron), then
+// the block sums of the g^2 cell terms go to part[block][c] (fixed order).
+constexpr int CG_T = 128;
+__global__ void __launch_bounds__(CG_T) coef_grad_kernel(ProbDev P, const SubDev* __restrict__ subs,
+                                                         const double* __restrict__ R,
+                                                         const double* __restrict__ bias,
+                                                         const double* __restrict__ Uw,
+                                                         const double* __restrict__ Ul,
+                                                         const double* __restrict__ res,
+                                                         const double* __restrict__ hl, int64_t N,
+                                                         double* __restrict__ part) {
+  __shared__ double wsum[CG_T / 32][64];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int d = P.dim, m = P.m, ns = P.ns, gq = P.coef_grid, nc = gq * gq;
+  double Q = 0.0, Gv[3] = {0.0, 0.0, 0.0};
+  double xs[3] = {0.5, 0.5, 0.5};
+  if (t < N) {
+    int64_t rem = t;
+    for (int i = 0; i < d; ++i) { xs[i] = ((double)(rem % P.G[i]) + 0.5) / (double)P.G[i]; rem /= P.G[i]; }
+    // v, grad v, Lap_S v for the two coefficient sets
+    double va[4] = {0, 0, 0, 0}, la = 0.0;       // W: grad (up to 3), Lap
+    double vb[4] = {0, 0, 0, 0}, lb = 0.0;       // lam
+    D3 lf[3];
+    for (int i = 0; i < d; ++i) lf[i] = lfun(P, i, xs[i]);
+    int k0[3] = {0, 0, 0}, k1[3] = {0, 0, 0};
+    for (int i = 0; i < d; ++i) cover_range(P, i, xs[i], &k0[i], &k1[i]);
+    for (int c2 = k0[2]; c2 <= (d > 2 ? k1[2] : 0); ++c2)
+      for (int c1 = k0[1]; c1 <= k1[1]; ++c1)
+        for (int c0 = k0[0]; c0 <= k1[0]; ++c0) {
+          const int kk[3] = {c0, c1, c2};
+          D3 e[3];
+          bool zero = false;
+          for (int i = 0; i < d; ++i) {
+            const D3 nu = nu_fun(P, i, xs[i], kk[i]);
+            if (nu.v == 0.0 && nu.d1 == 0.0 && nu.d2 == 0.0) { zero = true; break; }
+            e[i] = {lf[i].v * nu.v, lf[i].d1 * nu.v + lf[i].v * nu.d1,
+                    lf[i].d2 * nu.v + 2.0 * lf[i].d1 * nu.d1 + lf[i].v * nu.d2};
+          }
+          if (zero) continue;
+          // g = L omega_j and its derivatives
+          double gv = 1.0, dg[3], lapg = 0.0;
+          for (int i = 0; i < d; ++i) gv *= e[i].v;
+          for (int i = 0; i < d; ++i) {
+            double rest = 1.0;
+            for (int l = 0; l < d; ++l) if (l != i) rest *= e[l].v;
+            dg[i] = e[i].d1 * rest;
+            if (i < ns) lapg += e[i].d2 * rest;
+          }
+          const int j = c0 + P.nsub[0] * (c1 + P.nsub[1] * c2);
+          const SubDev& S = subs[j];
+          // Phi . U, grad, Lap_S for both sets
+          double pa = 0, pb = 0, ga[3] = {0, 0, 0}, gb[3] = {0, 0, 0}, qa = 0, qb = 0;
+          for (int k = 0; k < m; ++k) {
+            double z = bias[(int64_t)j * m + k];
+            double sk[3], n2 = 0.0;
+            for (int i = 0; i < d; ++i) {
+              sk[i] = R[((int64_t)j * m + k) * d + i] / P.sig[i];
+              z = fma(sk[i], xs[i] - S.mu[i], z);
+              if (i < ns) n2 += sk[i] * sk[i];
+            }
+            const double ph = tanh(z), php = 1.0 - ph * ph, lap = -2.0 * ph * php * n2;
+            const double uw = Uw[(int64_t)j * m + k], ul = Ul[(int64_t)j * m + k];
+            pa = fma(uw, ph, pa);
+            pb = fma(ul, ph, pb);
+            for (int i = 0; i < d; ++i) { ga[i] = fma(uw * php, sk[i], ga[i]); gb[i] = fma(ul * php, sk[i], gb[i]); }
+            qa = fma(uw, lap, qa);
+            qb = fma(ul, lap, qb);
+          }
+          double cross_a = 0.0, cross_b = 0.0;
+          for (int i = 0; i < ns; ++i) { cross_a += dg[i] * ga[i]; cross_b += dg[i] * gb[i]; }
+          for (int i = 0; i < d; ++i) {
+            va[i] += dg[i] * pa + gv * ga[i];
+            vb[i] += dg[i] * pb + gv * gb[i];
+          }
+          la += lapg * pa + 2.0 * cross_a + gv * qa;
+          lb += lapg * pb + 2.0 * cross_b + gv * qb;
+        }
+    // u_hat = v_W + G
+    if (P.g_kind == RANN_G_SINPROD) {
+      double s[3], c[3], G = 1.0;
+      for (int i = 0; i < ns; ++i) { sincospi(xs[i], &s[i], &c[i]); G *= s[i]; }
+      for (int i = 0; i < ns; ++i) {
+        double rest = 1.0;
+        for (int l = 0; l < ns; ++l) if (l != i) rest *= s[l];
+        va[i] += RANN_PI * c[i] * rest;
+      }
+      la += -(double)ns * RANN_PI * RANN_PI * G;
+    }
+    const double ri = res[t], hi = hl[t];
+    Q = -ri * lb + hi * la;
+    for (int i = 0; i < ns; ++i) Gv[i] = -ri * vb[i] + hi * va[i];
+  }
+  // cell terms s_c Q + grad s_c . Gv, summed over the block (warp shuffles, then warps in order)
+  double sx[8], dx[8], sy[8], dy[8];
+  for (int c = 0; c < gq; ++c) { sbox(xs[0], c, gq, &sx[c], &dx[c]); sbox(xs[1], c, gq, &sy[c], &dy[c]); }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = 0; c < nc; ++c) {
+    const int cx = c % gq, cy = c / gq;
+    double v = (t < N) ? (sx[cx] * sy[cy] * Q + dx[cx] * sy[cy] * Gv[0] + sx[cx] * dy[cy] * Gv[1]) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[warp][c] = v;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    double acc = 0.0;
+    for (int w = 0; w < CG_T / 32; ++w) acc += wsum[w][c];
+    part[(int64_t)blockIdx.x * nc + c] = acc;
+  }
+}
+
+// y_i = L(x_i) r_i at the collocation points (the diagonal factor of the
+// evaluation matrix, u_hat = L sum_j omega_j Phi_j V_{p_j} W_j + G).
+__global__ void lmul_kernel(ProbDev P, const double* __restrict__ r, double* __restrict__ y, int64_t N) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  int64_t rem = g;
+  double L = 1.0;
+  for (int i = 0; i < P.dim; ++i) {
+    const double x = ((double)(rem % P.G[i]) + 0.5) / (double)P.G[i];
+    rem /= P.G[i];
+    L *= lfun(P, i, x).v;
+  }
+  y[g] = L * r[g];
+}
+
 }  // namespace
 
 cudaError_t launch_assemble(const ProbDev& P, const SubDev* d_sub, const int* d_tiles, int ntiles,
@@ -342,5 +476,21 @@ cudaError_t launch_eval(const ProbDev& P, const SubDev* d_sub, const double* d_R
                         cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   eval_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(P, d_sub, d_R, d_b, d_U, d_x, n, d_u);
+  return cudaGetLastError();
+}
+
+int coef_grad_blocks(int64_t N) { return (int)((N + CG_T - 1) / CG_T); }
+
+cudaError_t launch_coef_grad(const ProbDev& P, const SubDev* d_sub, const double* d_R, const double* d_b,
+                             const double* d_Uw, const double* d_Ul, const double* d_r, const double* d_hl,
+                             int64_t N, double* d_part, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  coef_grad_kernel<<<coef_grad_blocks(N), CG_T, 0, st>>>(P, d_sub, d_R, d_b, d_Uw, d_Ul, d_r, d_hl, N, d_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lmul(const ProbDev& P, const double* d_r, double* d_y, int64_t N, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  lmul_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P, d_r, d_y, N);
   return cudaGetLastError();
 }

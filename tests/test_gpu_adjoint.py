@@ -171,3 +171,129 @@ def test_grad_c0_needs_the_poisson_operator(g):
     with pytest.raises(g.RannError) as e:
         s.grad_c0(F, W, W)
     assert e.value.status == g.EINVAL
+
+
+# ---- the piecewise diffusion coefficient (gradients w.r.t. a_c) ----
+
+def _piecewise(g, g_kind=None, sub=None, mode=0, kind="as"):
+    import dataclasses
+    p = ri.config("piecewise2d", small=True) if sub is None else ri.piecewise2d(0, sub=sub, pts=8, neurons=20)
+    if g_kind is not None:
+        p = dataclasses.replace(p, g_kind=g_kind)
+    R, b = ri.weights(p)
+    s = g.RannDD(p, R, b)
+    s.set_precision(mode)
+    s.assemble()
+    F = s.rhs()
+    ranks = s.pca(p.pca_mode, p.pca_thr)
+    s.setup_precond(kind)
+    return p, R, b, s, F, ranks
+
+
+def _oracle_on_gpu_basis(p, R, b, s, ranks):
+    """The oracle's system with the oracle's blocks projected on the GPU's basis."""
+    from oracle import assembly as asm
+    from oracle import solver as sv
+    rows, Bs, pcas = [], [], []
+    for j in range(p.J):
+        r, _, H = asm.block(p, R, b, j)
+        V = s.pca_of(j)[1]
+        rows.append(r)
+        Bs.append(H @ V)
+        pcas.append(sv.PCA(np.zeros(1), V, int(ranks[j]), False))
+    offs = np.concatenate([[0], np.cumsum(ranks)]).astype(np.int64)
+    return sv.System(p, R, b, rows, Bs, pcas, asm.rhs(p), offs)
+
+
+@pytest.mark.parametrize("g_kind", [ri.G_ZERO, ri.G_SINPROD])
+def test_grad_coef_matches_the_oracle(g, g_kind):
+    """rann_dd_grad_coef against the oracle's grad_coef (one-hot hyper-dual
+    assembly of dH/da_c) at the same W, lam and basis; with G = sin sin the
+    dF/da_c = -A_c[G] term is exercised too."""
+    from oracle import solver as sv
+    p, R, b, s, F, ranks = _piecewise(g, g_kind)
+    W, _ = s.solve_cg_as(F, 1e-12, 5000, allow_not_converged=True)
+    c = torch.tensor(np.random.default_rng(4).standard_normal(int(ranks.sum())), device="cuda")
+    lam, _ = s.solve_backward(c, 1e-12, 5000)
+    got = s.grad_coef(F, W, lam)
+    So = _oracle_on_gpu_basis(p, R, b, s, ranks)
+    want = sv.grad_coef(So, W.cpu().numpy(), lam.cpu().numpy())
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-9 * np.abs(want).max())
+
+
+def test_grad_coef_against_central_differences(g):
+    """dl/da_c of l = c . W(a) against central differences of the GPU solves
+    (2 x 2 subdomains: the AS solve is exact in one step, float64 mode)."""
+    p, R, b, s, F, ranks = _piecewise(g, sub=2)
+    W, _ = s.solve_cg_as(F, 1e-13, 100, allow_not_converged=True)
+    cvec = torch.tensor(np.random.default_rng(6).standard_normal(int(ranks.sum())), device="cuda")
+    lam, _ = s.solve_backward(cvec, 1e-13, 100)
+    grad = s.grad_coef(F, W, lam)
+    a0 = p.coef_vals.copy()
+    h = 1e-5
+
+    def loss(vals):
+        s.set_coef(vals)
+        s.assemble()
+        Fv = s.rhs()
+        s.pca(p.pca_mode, p.pca_thr)
+        s.setup_precond("as")
+        Wv, _ = s.solve_cg_as(Fv, 1e-13, 100, allow_not_converged=True)
+        return float(cvec @ Wv)
+
+    for cell in (0, 6, 15):
+        e = np.zeros_like(a0)
+        e[cell] = h
+        fd = (loss(a0 + e) - loss(a0 - e)) / (2 * h)
+        assert abs(grad[cell] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(grad).max()), (cell, grad[cell], fd)
+
+
+def test_eval_grid_transpose_matches_the_oracle(g):
+    from oracle import solver as sv
+    p = ri.config("heat3d", small=True)
+    R, b = ri.weights(p)
+    s = g.RannDD(p, R, b)
+    s.assemble()
+    ranks = s.pca(p.pca_mode, p.pca_thr)
+    So = _oracle_on_gpu_basis(p, R, b, s, ranks)
+    r = np.random.default_rng(3).standard_normal(p.n_points())
+    got = s.eval_grid_t(torch.tensor(r, device="cuda")).cpu().numpy()
+    want = sv.eval_matrix_t(So, r)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+    # adjoint identity with the forward evaluation at the grid
+    w = torch.tensor(np.random.default_rng(4).standard_normal(int(ranks.sum())), device="cuda")
+    X = s.points()
+    u = s.eval(w, X) - s.eval(torch.zeros_like(w), X)
+    assert abs(float(u @ torch.tensor(r, device="cuda")) - float(w @ torch.tensor(got, device="cuda"))) <= \
+        1e-11 * float(u.norm() * np.linalg.norm(r))
+
+
+def test_misfit_gradients_through_autograd(g):
+    """l = ||u_hat(a, F) - u_obs||^2 on the collocation grid, through
+    PiecewiseDiffusionSolve and GridEval: dl/da_c against central differences
+    and dl/dF along a direction against a central difference (RAS-GMRES
+    forward and adjoint, as the piecewise workload runs)."""
+    p, R, b, s, F, ranks = _piecewise(g, sub=2, kind="ras")
+    a = torch.tensor(p.coef_vals, dtype=torch.float64, requires_grad=True)
+    Fv = F.clone().requires_grad_(True)
+    u_obs = torch.tensor(np.random.default_rng(2).standard_normal(F.numel()) * 0.01, device="cuda")
+
+    def misfit(av, Fin):
+        W = g.PiecewiseDiffusionSolve.apply(s, av, Fin, kind="ras", rtol=1e-13, maxit=200)
+        u = g.GridEval.apply(s, W)
+        return ((u - u_obs) ** 2).sum()
+
+    l = misfit(a, Fv)
+    l.backward()
+    ga, gF = a.grad.numpy().copy(), Fv.grad.clone()
+    with torch.no_grad():
+        h = 1e-5
+        for cell in (3, 9):
+            e = torch.zeros_like(a)
+            e[cell] = h
+            fd = (float(misfit(a + e, F)) - float(misfit(a - e, F))) / (2 * h)
+            assert abs(ga[cell] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(ga).max()), (cell, ga[cell], fd)
+        dF = torch.tensor(np.random.default_rng(9).standard_normal(F.numel()), device="cuda")
+        hF = 1e-4
+        fd = (float(misfit(a, F + hF * dF)) - float(misfit(a, F - hF * dF))) / (2 * hF)
+        assert abs(float(gF @ dF) - fd) <= 1e-5 * abs(fd)

@@ -702,6 +702,55 @@ def test_grad_c0_is_the_derivative_of_the_least_squares_solution(c0, loss_kind, 
     assert abs(grad - fd) <= 2e-5 * abs(fd)
 
 
+@pytest.mark.parametrize("loss_kind,g_kind", [("linear", ri.G_ZERO), ("quadratic", ri.G_SINPROD)])
+def test_grad_coef_is_the_derivative_of_the_least_squares_solution(loss_kind, g_kind):
+    """grad_coef against central differences of l(W(a)) in three cell values
+    a_c of the piecewise diffusion coefficient (a 2 x 2 grid of subdomains,
+    4 x 4 coefficient cells); G = 0 and G = sin(pi x) sin(pi y) (then
+    dF/da_c = -A_c[G] is not zero, so each term of the formula is exercised).
+    The PCA basis does not depend on a, which the test checks."""
+    import dataclasses
+    p = dataclasses.replace(ri.piecewise2d(0, sub=2, pts=8, neurons=20), g_kind=g_kind)
+    R, b = ri.weights(p)
+    S = sv.build_system(p, R, b)
+    rng = np.random.default_rng(5)
+    c = rng.standard_normal(S.dof)
+    w0 = rng.standard_normal(S.dof)
+
+    def loss_and_grad(W):
+        if loss_kind == "linear":
+            return float(c @ W), c
+        return 0.5 * float(np.sum((W - w0) ** 2)), W - w0
+
+    W, _ = _lstsq_and_adjoint(S, c)
+    _, lam = _lstsq_and_adjoint(S, loss_and_grad(W)[1])
+    grad = sv.grad_coef(S, W, lam)
+    assert grad.shape == (16,)
+    h = 1e-5
+    for cell in (0, 5, 14):
+        def loss(delta):
+            vals = p.coef_vals.copy()
+            vals[cell] += delta
+            S2 = sv.build_system(dataclasses.replace(p, coef_vals=vals), R, b)
+            for pa, pb in zip(S.pcas, S2.pcas):
+                np.testing.assert_array_equal(pa.V, pb.V)
+            return loss_and_grad(_lstsq_and_adjoint(S2, c)[0])[0]
+        fd = (loss(h) - loss(-h)) / (2 * h)
+        assert abs(grad[cell] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(grad).max()), (cell, grad[cell], fd)
+
+
+def test_eval_matrix_transpose_is_the_adjoint_of_u_hat():
+    """E^T r equals the brute-force transpose of the evaluation matrix at the
+    collocation points (columns from evaluate on unit coefficient vectors)."""
+    p = ri.config("heat3d", small=True)
+    S = sv.build_system(p)
+    X = ri.grid_points(p)
+    g0 = sv.evaluate(S, np.zeros(S.dof), X)
+    E = np.stack([sv.evaluate(S, np.eye(S.dof)[c], X) - g0 for c in range(S.dof)], axis=1)
+    r = np.random.default_rng(8).standard_normal(X.shape[0])
+    np.testing.assert_allclose(sv.eval_matrix_t(S, r), E.T @ r, rtol=0, atol=1e-12 * np.abs(E.T @ r).max())
+
+
 # ------------------------------------------------------ planted mistakes --
 
 def test_planted_dropped_window_normalisation_is_caught(monkeypatch):
