@@ -47,14 +47,15 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 float64 FMA/clk x 2 f
 DF32_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12   # double-float multiply-add: 12 float32 instructions
 CSRC = os.path.join(ROOT, "paper_2412_19207_gb300", "csrc")
 # DRAM bytes per launch of a kernel family (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture on this workload, scaled as the
+# dram__bytes_write.sum from one ncu capture on this workload, as the
 # profiles/ summary states), valid only for the kernel source it was taken
-# on: the sha256 prefix of that .cu file.  A changed source reports null.
+# on: (bytes, file, kernel, sha256 prefix of the kernel's source text).  A
+# changed kernel reports null.
 TRAFFIC = {}
 # families whose profiled bracket spans a multi-stream pipeline of many kernels
 # (the Cholesky with lookahead and the row-block inverse): no single launch
 # duration, so they are reported as pipelines, not as the roofline kernel
-PIPELINED = {"cholesky"}
+PIPELINED = {"cholesky", "cholesky_tc"}
 
 
 def headline_workload():
@@ -69,17 +70,21 @@ def multiscale_workload():
     return p
 
 
-def source_sha(fname):
-    with open(os.path.join(CSRC, fname), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:12]
+def kernel_source_sha(fname, kernel):
+    """sha256 prefix of one kernel's source text: from the line that declares
+    `kernel` to the first line holding only a closing brace."""
+    lines = open(os.path.join(CSRC, fname)).read().split("\n")
+    start = next(i for i, l in enumerate(lines) if kernel + "(" in l and "__global__" in l)
+    end = next(i for i in range(start, len(lines)) if lines[i] == "}")
+    return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()[:12]
 
 
 def traffic_of(family):
     t = TRAFFIC.get(family)
     if not t:
         return None
-    bytes_per_launch, fname, sha = t
-    return bytes_per_launch if source_sha(fname) == sha else None
+    bytes_per_launch, fname, kernel, sha = t
+    return bytes_per_launch if kernel_source_sha(fname, kernel) == sha else None
 
 
 def peaks():
@@ -210,6 +215,21 @@ def roofline(prof, pk):
             "peak_source": note}
 
 
+def pipeline_entry(f, pk):
+    """A multi-stream pipeline family: its time per step and its rate against
+    the peak of its class (double-float pipe, or the bf16 tensor cores for the
+    digit-slice products; the tensor pipeline also runs its 32-column panel
+    steps on the float32 pipe, inside the same bracket)."""
+    ach = f["flops"] / (f["ms"] * 1e-3) / 1e12
+    if f["bound"] == "tensor":
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        return {"ms_per_step": round(f["ms"], 3), "launches_per_step": f["launches"], "achieved_tflops": round(ach, 3),
+                "peak_tflops": peak, "frac_of_bf16_sustained": round(ach / peak, 4),
+                "flops": "digit-slice products (36 per float64-accurate product)"}
+    return {"ms_per_step": round(f["ms"], 3), "launches_per_step": f["launches"], "achieved_tflops": round(ach, 3),
+            "frac_of_df32_peak": round(ach / DF32_PEAK_TFLOPS, 4)}
+
+
 def bandwidths(prof, pk):
     def gbps(names):
         fam = [prof[n] for n in names if prof.get(n, {}).get("ms")]
@@ -336,11 +356,7 @@ def bench_ours(args, rank, world):
         "phases_ms": phases,
         "roofline": roofline(prof, pk),
         "matvec": bandwidths(prof, pk),
-        "pipelines": {k: {"ms_per_step": round(prof[k]["ms"], 3), "launches_per_step": prof[k]["launches"],
-                          "achieved_tflops": round(prof[k]["flops"] / (prof[k]["ms"] * 1e-3) / 1e12, 3),
-                          "frac_of_df32_peak": round(prof[k]["flops"] / (prof[k]["ms"] * 1e-3) / 1e12
-                                                     / DF32_PEAK_TFLOPS, 4)}
-                      for k in sorted(PIPELINED) if prof.get(k, {}).get("ms")},
+        "pipelines": {k: pipeline_entry(prof[k], pk) for k in sorted(PIPELINED) if prof.get(k, {}).get("ms")},
         "kernels": kernels,
         "gpu_launches": int(launches) * args.steps,
         "gpu_launches_per_step": int(launches),
@@ -353,6 +369,47 @@ def bench_ours(args, rank, world):
         out["multiscale2d"] = multiscale_arms(g, torch)
     if args.multi_rhs > 0:
         out["multi_rhs"] = [multi_rhs_timing(g, args.multi_rhs, "cg"), multi_rhs_timing(g, args.multi_rhs, "gmres")]
+    return out
+
+
+def piecewise_batch(g, torch, kind="ras"):
+    """The differentiable batch of the piecewise-coefficient diffusion
+    workload: 64 instances (subdomain grids 4x4 .. 16x16 by instance, 200
+    neurons, 24x24 points per cell, a smoothed 4x4 piecewise coefficient with
+    cell values U[0.5, 2] and an 8-mode Fourier source, all seeded), each run
+    forward (assembly, PCA, Schwarz set-up, preconditioned GMRES(50) to
+    1e-10) and backward for l = ||u_hat - u_obs||^2 on its collocation grid
+    (u_obs = 0.01 sin(pi x) sin(pi y)): dl/dW through the grid evaluation's
+    adjoint, the adjoint solve, dl/da_c (16 cells) and dl/dF.  Wall time of
+    the whole batch with the device synchronised on both sides."""
+    out = {"instances": 64, "solver": f"{kind.upper()}-GMRES(50)", "rtol": 1e-10}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters, conv, adj = [], 0, 0
+    for i in range(64):
+        p = ri.piecewise2d(i)
+        s = g.RannDD(p)
+        s.assemble()
+        F = s.rhs()
+        s.pca(p.pca_mode, p.pca_thr)
+        s.setup_precond(kind)
+        W, st = s.solve_gmres_ras(F, 1e-10, 50, 3000, allow_not_converged=True)
+        X = s.points()
+        u = s.eval(W, X)
+        uobs = 0.01 * torch.sin(np.pi * X[:, 0]) * torch.sin(np.pi * X[:, 1])
+        gW = s.eval_grid_t(2.0 * (u - uobs))
+        lam, sb = s.solve_backward(gW, 1e-10, 3000)
+        s.grad_coef(F, W, lam)
+        s.matvec(lam)
+        iters.append(st["iters"])
+        conv += st["status"] == "RANN_OK"
+        adj += sb["status"] == "RANN_OK"
+        s.close()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out.update({"s_per_batch": round(t, 3), "ms_per_instance": round(t * 1e3 / 64, 2),
+                "forward_converged": conv, "adjoint_converged": adj,
+                "iters_min_max": [int(min(iters)), int(max(iters))]})
     return out
 
 

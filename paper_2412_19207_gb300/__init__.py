@@ -330,12 +330,12 @@ class RannDD:
         """Biconjugate gradients on the normal equations (Sec. 5, Table 1b)."""
         return self._solve_variant("rann_dd_solve_bicg", F, rtol, maxit, W, allow_not_converged)
 
-    def solve_backward(self, gW, rtol=1e-10, maxit=2000, lam=None):
+    def solve_backward(self, gW, rtol=1e-10, maxit=2000, lam=None, allow_not_converged=False):
         """lam = (H^T H)^{-1} gW with the stored preconditioner (adjoint of the solve)."""
         lam = lam if lam is not None else self._empty(self.sizes()["dof"])
         st = Stats()
         s = self._lib.rann_dd_solve_backward(self._h, _dptr(gW), _dptr(lam), rtol, maxit, ctypes.byref(st))
-        _check(s, "rann_dd_solve_backward")
+        _check(s, "rann_dd_solve_backward", allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return lam, st.as_dict() | {"status": STATUS[s]}
 
     def grad_c0(self, F, W, lam) -> float:

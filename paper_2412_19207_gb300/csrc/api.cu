@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "chol_tc.h"
 
 // launchers from the other translation units
 cudaError_t launch_matvec_H2(const ProbDev& P, const SubDev* d_sub, const int* d_cov, int Gmax,
@@ -81,7 +82,7 @@ cudaError_t launch_scale_copy(double a, const double* x, double* y, int64_t n, c
                               float2* y2 = nullptr);
 cudaError_t launch_assemble_local(const double* d_pairbuf, const int64_t* d_tab, const int* d_tab_ptr,
                                   const int* d_boff, const int* d_boff_ptr, const CholMat* d_mats, int nsets,
-                                  int maxn, double* d_dmax, cudaStream_t st);
+                                  int maxn, double* d_dmax, cudaStream_t st, const int* d_which = nullptr);
 int coef_grad_blocks(int64_t N);
 cudaError_t launch_lmul(const ProbDev& P, const double* d_r, double* d_y, int64_t N, cudaStream_t st);
 cudaError_t launch_coef_grad(const ProbDev& P, const SubDev* d_sub, const double* d_R, const double* d_b,
@@ -127,14 +128,14 @@ enum KId {
   K_CHOL, K_TRTRI, K_GATHER, K_TRMV_L, K_TRMV_U, K_COMBINE, K_MATVEC_H, K_MATVEC_HT, K_DOT, K_VEC, K_EVAL,
   K_SPLIT, K_MATVEC_H_DF, K_MATVEC_HT_DF, K_GATHER_DF, K_TRMV_L_DF, K_TRMV_U_DF, K_OZ_SPLIT, K_GRAM_OZ,
   K_PROJECT_OZ, K_EIG_VAL, K_EIG_VEC, K_EIG_ORTH, K_EIG_BACK, K_GRAMROWS, K_GRAMOP, K_PAIRGRAM_OZ, K_SCHWARZ_DF,
-  K_COUNT
+  K_CHOL_TC, K_COUNT
 };
 static const char* const KNAMES[K_COUNT] = {
   "points", "assemble", "rhs", "gram", "symmetrize", "eig_tridiag", "project", "pair_gram", "local_assemble",
   "add_diag", "cholesky", "trtri", "schwarz_gather", "trmv_lower", "trmv_upper", "schwarz_combine",
   "matvec_H", "matvec_HT", "dot", "vector", "eval", "split_df32", "matvec_H_df32", "matvec_HT_df32",
   "schwarz_gather_df32", "trmv_lower_df32", "trmv_upper_df32", "ozaki_split", "gram_ozaki", "project_ozaki", "eig_values", "eig_vectors", "eig_orth", "eig_back", "gram_rows", "gramop_df32",
-  "pair_gram_ozaki", "schwarz_apply_df32"};
+  "pair_gram_ozaki", "schwarz_apply_df32", "cholesky_tc"};
 
 // Roofline class of each family: 0 = HBM-bound (algorithmic bytes count),
 // 1 = float64-ALU-bound (algorithmic flops count), 2 = bf16-tensor-core-bound
@@ -142,7 +143,7 @@ static const char* const KNAMES[K_COUNT] = {
 // on the float32 pipe (float64-equivalent flops count; the families marked in
 // KDF below run that way in precision mode 1).
 static const int KBOUND[K_COUNT] = {0, 1, 0, 1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 1,
-                                     0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1, 0, 0, 2, 0};
+                                     0, 0, 0, 0, 0, 0, 0, 2, 2, 1, 1, 1, 1, 0, 0, 2, 0, 2};
 
 static bool family_is_df(int k) {
   return k == K_PAIRGRAM || k == K_CHOL || k == K_TRTRI || k == K_EIG_ORTH || k == K_EIG_BACK;
@@ -1293,14 +1294,36 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   CK(dalloc(h, (void**)&d_dmax, sizeof(double) * J));
   CK(dalloc(h, (void**)&d_fail, sizeof(int) * J));
   KLA(h, K_LOCALASM, 2, 8.0 * h->sum_n2, 0, launch_assemble_local(h->d_pairbuf, d_tab, d_tab_ptr, d_boffs, d_boff_ptr, h->d_mats, J, h->maxn, d_dmax, h->st));
-  // Cholesky with shift-and-retry for failed pivots: every attempt factors all
-  // J matrices (a retry reassembles them all); the largest diagonal entries
-  // stay on the device and reach the host only when a shift is needed
+  // Cholesky with shift-and-retry for failed pivots: the first attempt factors
+  // all J matrices; a retry reassembles only the failed ones, adds a growing
+  // diagonal shift and refactors them alone (a compacted matrix list with its
+  // own failure flags and diagonal maxima).  The largest diagonal entries
+  // stay on the device and reach the host only when a shift is needed.
   std::vector<double> dmax;
   std::vector<int> shifted(J, 0);
-  double chol_flops = 0.0;
-  for (int i = 0; i < J; ++i) chol_flops += (double)mats[i].n * mats[i].n * mats[i].n / 3.0;
+  std::vector<int> active(J);
+  for (int i = 0; i < J; ++i) active[i] = i;
+  const CholMat* d_act = h->d_mats;
+  const double* d_act_dmax = d_dmax;
+  int act_maxn = h->maxn;
+  std::vector<void*> retry_allocs;
+  struct Frees {
+    rann_dd_handle* h; std::vector<void*>* v;
+    ~Frees() { for (void* p : *v) dfree(h, p); }
+  } frees{h, &retry_allocs};
+  std::vector<void*> tc_allocs;          // work areas of one big-panel attempt
+  struct Frees2 {
+    rann_dd_handle* h; std::vector<void*>* v;
+    ~Frees2() { for (void* p : *v) dfree(h, p); }
+  } frees2{h, &tc_allocs};
   for (int attempt = 0; attempt < 6; ++attempt) {
+    const int nact = (int)active.size();
+    double chol_flops = 0.0, inv_flops = 0.0;
+    for (int i : active) {
+      const double n = mats[i].n;
+      chol_flops += n * n * n / 3.0;
+      inv_flops += n * n * n / 3.0;
+    }
     CK(cudaMemsetAsync(d_fail, 0, sizeof(int) * J, h->st));
     if (h->prec_df) {
       if (!h->st_la) {
@@ -1311,26 +1334,56 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
         for (cudaEvent_t& e : h->ev_la) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       }
       int nl = 0;
-      KLA(h, K_CHOL, nl, 0, chol_flops + h->sum_n3 / 3.0,
-          launch_chol_df_lookahead(h->d_mats, J, h->maxn, d_fail, d_dmax, h->st, h->st_la, h->st_inv, h->ev_la,
-                                   &nl));
+      if (act_maxn >= TC_MIN_N) {
+        // big panels with the trailing updates and the inverse's products on the tensor cores
+        std::vector<CholMat> am;
+        for (int i : active) am.push_back(mats[i]);
+        CholTcPlan plan;
+        CK(chol_tc_build(am, plan, nullptr, nullptr, nullptr, nullptr));
+        uint16_t *l21a, *l21b, *invb, *xib;
+        int* eb;
+        CK(dalloc(h, (void**)&l21a, 2 * (size_t)std::max<int64_t>(plan.l21_elems, 8)));
+        CK(dalloc(h, (void**)&l21b, 2 * (size_t)std::max<int64_t>(plan.l21_elems, 8)));
+        CK(dalloc(h, (void**)&invb, 2 * (size_t)std::max<int64_t>(plan.inv_elems, 8)));
+        CK(dalloc(h, (void**)&xib, 2 * (size_t)std::max<int64_t>(plan.xi_elems, 8)));
+        CK(dalloc(h, (void**)&eb, 4 * (size_t)std::max<int64_t>(plan.e_ints, 1)));
+        for (void* p : {(void*)l21a, (void*)l21b, (void*)invb, (void*)xib, (void*)eb}) tc_allocs.push_back(p);
+        uint16_t* const l21[2] = {l21a, l21b};
+        CK(chol_tc_build(am, plan, l21, invb, xib, eb));
+        OzSplitTask* d_split; OzGroup* d_groups; OzMap* d_maps;
+        CK(dupload(h, &d_split, plan.split)); CK(dupload(h, &d_groups, plan.groups)); CK(dupload(h, &d_maps, plan.maps));
+        for (void* p : {(void*)d_split, (void*)d_groups, (void*)d_maps}) tc_allocs.push_back(p);
+        for (const CholMat& M : am)        // the inverse accumulates in X2 and reads its upper triangles as zeros
+          CK(cudaMemsetAsync(M.X2, 0, sizeof(float2) * (size_t)M.n * M.ld, h->st));
+        KLA(h, K_CHOL_TC, nl, 0, plan.flops,
+            chol_tc_enqueue(plan, d_act, nact, d_fail, d_act_dmax, d_split, d_groups, d_maps, h->d_ozerr, h->st,
+                            h->st_inv, &nl));
+      } else {
+        KLA(h, K_CHOL, nl, 0, chol_flops + inv_flops,
+            launch_chol_df_lookahead(d_act, nact, act_maxn, d_fail, d_act_dmax, h->st, h->st_la, h->st_inv, h->ev_la,
+                                     &nl));
+      }
     } else {
-      for (int c0 = 0; c0 < h->maxn; c0 += 32)
-        KLA(h, K_CHOL, (h->maxn - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
-            launch_chol_step(h->d_mats, J, h->maxn, c0, d_fail, d_dmax, h->st));
+      for (int c0 = 0; c0 < act_maxn; c0 += 32)
+        KLA(h, K_CHOL, (act_maxn - c0 > 32) ? 3 : 1, 0, c0 == 0 ? chol_flops : 0.0,
+            launch_chol_step(d_act, nact, act_maxn, c0, d_fail, d_act_dmax, h->st));
+      KLA(h, K_TRTRI, 2, 0, inv_flops, launch_trtri(d_act, nact, act_maxn, h->st));
+      KLA(h, K_SPLIT, 1, 6.0 * h->sum_n2, 0, launch_split_lower(d_act, nact, act_maxn, h->st));
     }
-    std::vector<int> f(J);
+    std::vector<int> f(nact);
     int ozerr = 0;
-    CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * J, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(f.data(), d_fail, sizeof(int) * nact, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(&ozerr, h->d_ozerr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(stream_sync(h));
+    for (void* p : tc_allocs) dfree(h, p);
+    tc_allocs.clear();
     if (ozerr) {
       cudaMemsetAsync(h->d_ozerr, 0, sizeof(int), h->st);
-      rann_set_error("tensor-core product (projection / pair Gram): bounded pipeline wait %d gave up", ozerr);
+      rann_set_error("tensor-core product (pair Gram / local factors): bounded pipeline wait %d gave up", ozerr);
       return RANN_TIMEOUT;
     }
     std::vector<int> next;
-    for (int i = 0; i < J; ++i) if (f[i]) next.push_back(i);
+    for (int q = 0; q < nact; ++q) if (f[q]) next.push_back(active[q]);
     if (next.empty()) break;
     if (attempt == 5) { rann_set_error("local Cholesky failed after shifts"); return RANN_ECUDA; }
     if (dmax.empty()) {
@@ -1338,26 +1391,36 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
       CK(cudaMemcpyAsync(dmax.data(), d_dmax, sizeof(double) * J, cudaMemcpyDeviceToHost, h->st));
       CK(stream_sync(h));
     }
-    // rebuild all matrices and add a growing diagonal shift to the failed ones
+    // reassemble the failed matrices and add a growing diagonal shift
     std::vector<CholMat> fm;
-    std::vector<int> which;
-    std::vector<double> shift;
+    std::vector<int> which, widx;
+    std::vector<double> shift, fdmax;
+    act_maxn = 0;
     for (int i : next) {
       shifted[i] = 1;
-      which.push_back((int)fm.size());
+      widx.push_back((int)fm.size());
       fm.push_back(mats[i]);
+      which.push_back(i);
       shift.push_back(dmax[i] * std::pow(10.0, -14 + 2 * attempt));
+      fdmax.push_back(dmax[i]);
+      act_maxn = std::max(act_maxn, mats[i].n);
     }
-    KLA(h, K_LOCALASM, 2, 8.0 * h->sum_n2, 0, launch_assemble_local(h->d_pairbuf, d_tab, d_tab_ptr, d_boffs, d_boff_ptr, h->d_mats, J, h->maxn, d_dmax, h->st));
-    CholMat* d_fm; int* d_which; double* d_shift;
-    CK(dupload(h, &d_fm, fm)); CK(dupload(h, &d_which, which)); CK(dupload(h, &d_shift, shift));
-    KL(h, K_ADDDIAG, 1, launch_add_diag(d_fm, d_which, (int)which.size(), d_shift, h->maxn, h->st));
-    dfree(h, d_fm); dfree(h, d_which); dfree(h, d_shift);
+    int* d_which; CholMat* d_fm; int* d_widx; double* d_shift; double* d_fdmax;
+    CK(dupload(h, &d_which, which)); CK(dupload(h, &d_fm, fm)); CK(dupload(h, &d_widx, widx));
+    CK(dupload(h, &d_shift, shift)); CK(dupload(h, &d_fdmax, fdmax));
+    for (void* p : {(void*)d_which, (void*)d_fm, (void*)d_widx, (void*)d_shift, (void*)d_fdmax}) retry_allocs.push_back(p);
+    double s2 = 0.0;
+    for (int i : next) s2 += (double)mats[i].n * mats[i].n;
+    KLA(h, K_LOCALASM, 2, 8.0 * s2, 0, launch_assemble_local(h->d_pairbuf, d_tab, d_tab_ptr, d_boffs, d_boff_ptr,
+                                                             h->d_mats, (int)next.size(), act_maxn, d_dmax, h->st,
+                                                             d_which));
+    KL(h, K_ADDDIAG, 1, launch_add_diag(d_fm, d_widx, (int)next.size(), d_shift, act_maxn, h->st));
+    active = next;
+    d_act = d_fm;
+    d_act_dmax = d_fdmax;
   }
   for (int i = 0; i < J; ++i) h->n_shifted += shifted[i];
-  // X_i = L_i^{-1} for the parallel apply (precision mode 1 formed it inside the factorisation)
-  if (!h->prec_df) KLA(h, K_TRTRI, 2, 0, h->sum_n3 / 3.0, launch_trtri(h->d_mats, J, h->maxn, h->st));
-  if (!h->prec_df) KLA(h, K_SPLIT, 1, 6.0 * h->sum_n2, 0, launch_split_lower(h->d_mats, J, h->maxn, h->st));
+  // (X_i = L_i^{-1} for the parallel apply was formed with each factorisation attempt)
   std::vector<int64_t> p_off(J + 1, 0);
   for (int i = 0; i < J; ++i) p_off[i + 1] = p_off[i] + (int64_t)((mats[i].n + 255) / 256) * mats[i].n;
   CK(dupload(h, &h->d_p_off, p_off));

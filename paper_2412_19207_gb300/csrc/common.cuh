@@ -89,6 +89,7 @@ struct OzSplitTask {         // one operand: rows i < M of x(i, k) = X[i * si + 
   int M, K, Kp, Mp;          // Kp = oz_kpad(K), Mp = oz_mpad(M) (rows M..Mp-1 of the slices are zero)
   int* e;                    // [M] row exponents (out)
   uint16_t* out;             // [oz_slices()][Kp/8][Mp][8] bf16 digit slices (out), 16-byte aligned
+  int df;                    // 1: X holds double-float pairs (float2, value hi + lo) at the same indices
 };
 constexpr int OZ_TILE_M = 128, OZ_TILE_N = 64;   // C tile of one block (rows of A x rows of B)
 struct alignas(64) OzMap { unsigned char bytes[128]; };   // a TMA tensor map of one operand's slices
@@ -100,6 +101,32 @@ struct OzTask {              // one OZ_TILE_M x OZ_TILE_N tile of C = A B^T (A: 
   int M, N, Kp, ldc;
   int tm, tn;                // tile origin in C
 };
+// A batch of tiles of one product C (op)= A B^T for the grouped launch: the
+// tiles of a group are enumerated in the kernel (row tiles of OZ_TILE_M, column
+// tiles of OZ_TILE_N; with lower = 1 only the tiles that meet the lower
+// triangle i >= j, and no entry above it is written).  mode: OZ_OUT_F64
+// writes float64 C; OZ_OUT_DF_SUB subtracts the product from double-float C
+// (float2); OZ_OUT_DF_SET writes it to double-float C.
+enum { OZ_OUT_F64 = 0, OZ_OUT_DF_SUB = 1, OZ_OUT_DF_SET = 2 };
+struct OzGroup {
+  int ia, ib;
+  const int* ea;
+  const int* eb;
+  void* C;
+  int M, N, Kp, ldc;
+  int mode, lower;
+  int first;                 // index of the group's first tile in the launch
+  int tiles;                 // oz_group_tiles(M, N, lower)
+};
+inline int oz_group_tiles(int M, int N, int lower) {
+  const int RT = (M + OZ_TILE_M - 1) / OZ_TILE_M, CT = (N + OZ_TILE_N - 1) / OZ_TILE_N;
+  if (!lower) return RT * CT;
+  int n = 0;
+  for (int r = 0; r < RT; ++r) n += CT < 2 * r + 2 ? CT : 2 * r + 2;
+  return n;
+}
+cudaError_t launch_oz_gemm_groups(const OzGroup* d_groups, int ngroups, int ntiles, const OzMap* d_maps, int* d_err,
+                                  cudaStream_t st);
 int oz_slices();
 int oz_kpad(int K);
 inline int oz_mpad(int M) { return (M + 31) / 32 * 32; }

@@ -100,10 +100,10 @@ extern "C" rann_status rann_dd_matvec_t_noalloc(int J, const int64_t* boff, cons
       rann_set_error("matvec_t_noalloc: bad descriptor for block %d", j);
       return RANN_EINVAL;
     }
-    tiles += (n_rows[j] + NA_ROWS - 1) / NA_ROWS;
+    tiles += ((int64_t)n_rows[j] + NA_ROWS - 1) / NA_ROWS;   // 64-bit: no wrap for n_rows near INT_MAX
     maxcols = std::max(maxcols, n_cols[j]);
   }
-  if ((int64_t)tiles * maxcols > NA_MAX_SCRATCH) {
+  if (tiles * maxcols > NA_MAX_SCRATCH) {   // also bounds every tile index below by 2^20
     rann_set_error("matvec_t_noalloc: %lld row tiles x %d columns exceed the %lld-double scratch array",
                    (long long)tiles, maxcols, (long long)NA_MAX_SCRATCH);
     return RANN_EINVAL;

@@ -34,6 +34,7 @@
 // thread issues the 36 tcgen05.mma of a k step; eight warps drain the
 // accumulators to the integer chunk sums through tcgen05.ld.
 #include "common.cuh"
+#include "df32.cuh"
 #include "mbar.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -61,6 +62,16 @@ __device__ __forceinline__ uint32_t bf16_of_small_int(int d) {
   return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
 }
 
+// The float64 bit pattern of operand entry idx (a double-float pair is read
+// as the float64 value hi + lo).
+__device__ __forceinline__ long long oz_bits(const OzSplitTask& t, int64_t idx) {
+  if (t.df) {
+    const float2 v = reinterpret_cast<const float2*>(t.X)[idx];
+    return __double_as_longlong((double)v.x + (double)v.y);
+  }
+  return reinterpret_cast<const long long*>(t.X)[idx];
+}
+
 // e_i of 32 rows of one operand per block (deterministic integer max of |x|'s bits).
 __global__ void __launch_bounds__(256) oz_scale_kernel(const OzSplitTask* __restrict__ tasks) {
   const OzSplitTask t = tasks[blockIdx.y];
@@ -68,7 +79,6 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const OzSplitTask* __rest
   if (i0 >= t.M) return;
   __shared__ long long red[8][33];
   const int a = threadIdx.x & 31, b = threadIdx.x >> 5;
-  const long long* X = reinterpret_cast<const long long*>(t.X);
   const long long ABS = 0x7FFFFFFFFFFFFFFFll;
   if (t.sk == 1 && !t.gather) {   // rows contiguous in k: warp b owns rows i0 + b + 8c, lanes stride k
 #pragma unroll
@@ -76,7 +86,7 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const OzSplitTask* __rest
       const int i = i0 + b + 8 * c;
       long long mx = 0;
       if (i < t.M)
-        for (int k = a; k < t.K; k += 32) mx = max(mx, X[(int64_t)i * t.si + k] & ABS);
+        for (int k = a; k < t.K; k += 32) mx = max(mx, oz_bits(t, (int64_t)i * t.si + k) & ABS);
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if (a == 0) red[0][b + 8 * c] = mx;
     }
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const OzSplitTask* __rest
     if (i < t.M)
       for (int k = b; k < t.K; k += 8) {
         const int64_t kk = t.gather ? t.gather[k] : k;
-        mx = max(mx, X[(int64_t)i * t.si + kk * t.sk] & ABS);
+        mx = max(mx, oz_bits(t, (int64_t)i * t.si + kk * t.sk) & ABS);
       }
     red[b][a] = mx;
     __syncthreads();
@@ -114,16 +124,16 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitTask* __rest
   const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   if (i0 >= t.Mp || k0 >= t.Kp) return;
   __shared__ long long tile[32][65];
-  const long long* X = reinterpret_cast<const long long*>(t.X);
   if (t.sk == 1 && !t.gather) {                      // rows contiguous in k
     for (int e = threadIdx.x; e < 2048; e += 256) {
       const int kk = e & 63, ii = e >> 6, i = i0 + ii, k = k0 + kk;
-      tile[ii][kk] = (i < t.M && k < t.K) ? X[(int64_t)i * t.si + k] : 0;
+      tile[ii][kk] = (i < t.M && k < t.K) ? oz_bits(t, (int64_t)i * t.si + k) : 0;
     }
   } else {                                           // columns contiguous in i (or gathered k)
     for (int e = threadIdx.x; e < 2048; e += 256) {
       const int ii = e & 31, kk = e >> 5, i = i0 + ii, k = k0 + kk;
-      tile[ii][kk] = (i < t.M && k < t.K) ? X[(int64_t)i * t.si + (int64_t)(t.gather ? t.gather[k] : k) * t.sk] : 0;
+      tile[ii][kk] = (i < t.M && k < t.K) ? oz_bits(t, (int64_t)i * t.si + (int64_t)(t.gather ? t.gather[k] : k) * t.sk)
+                                          : 0;
     }
   }
   __syncthreads();
@@ -237,13 +247,46 @@ __device__ __forceinline__ int join2(uint32_t a, uint32_t b) {
 //           overwrites);
 //   warps 2..9: drain each chunk's group sums into the exact integers hi / lo
 //           (lo carried into hi above 2^28, so lo stays 32-bit) and write the tile.
-__global__ void __launch_bounds__(OZ_THREADS, 1)
-    oz_gemm_tc_kernel(const OzTask* __restrict__ tasks, const OzMap* __restrict__ maps, int* __restrict__ err) {
+struct OzTile {               // one tile: operands, their row exponents, sizes, origin in C
+  int ia, ib;
+  const int* ea;
+  const int* eb;
+  int M, N, Kp, tm, tn;
+};
+// Output of the grouped launch: float64 C, or double-float C minus (plus) the product.
+struct OzEpi {
+  void* C;
+  int ldc, mode, lower;
+  __device__ __forceinline__ void operator()(int i, int j, double v) const {
+    if (mode == OZ_OUT_F64) {
+      reinterpret_cast<double*>(C)[(int64_t)i * ldc + j] = v;
+      return;
+    }
+    if (lower && j > i) return;
+    float2* p = reinterpret_cast<float2*>(C) + (int64_t)i * ldc + j;
+    const float2 s = df_split(v);
+    if (mode == OZ_OUT_DF_SET) {
+      *p = s;
+    } else {
+      float2 c = *p;
+      df_add(c.x, c.y, -s.x, -s.y);
+      *p = c;
+    }
+  }
+};
+struct OzEpiF64 {
+  double* C;
+  int ldc;
+  __device__ __forceinline__ void operator()(int i, int j, double v) const { C[(int64_t)i * ldc + j] = v; }
+};
+
+template <class Epi>
+__device__ __forceinline__ void oz_tile_run(const OzTile& t, const OzMap* __restrict__ maps, int* __restrict__ err,
+                                            const Epi& epi) {
   extern __shared__ uint8_t oz_dyn[];
   __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_accf, bar_acce, bar_fin;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, issued, consumed;
-  const OzTask t = tasks[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t sbase = (smem_u32(oz_dyn) + 1023u) & ~1023u;
   const int nks = t.Kp / OZ_TK;
@@ -371,7 +414,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int i = t.tm + quarter * 32 + lane;
       if (i < t.M) {
         const int ea = t.ea[i];
-        double* crow = t.C + (int64_t)i * t.ldc;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int jj = t.tn + half * 32 + j;
@@ -379,8 +421,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const double v = fma((double)hi[j], 0x1p-35, (double)lo[j] * 0x1p-63);   // the one rounding
             const int ex = ea + t.eb[jj];
             // times 2^ex: a power-of-two factor built from its exponent field when it is normal
-            crow[jj] = (ex >= -1022 && ex <= 1023) ? v * __longlong_as_double((long long)(ex + 1023) << 52)
-                                                   : ldexp(v, ex);
+            epi(i, jj, (ex >= -1022 && ex <= 1023) ? v * __longlong_as_double((long long)(ex + 1023) << 52)
+                                                   : ldexp(v, ex));
           }
         }
       }
@@ -401,6 +443,38 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   tc_fence_after();
   __syncwarp();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tbase));
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_gemm_tc_kernel(const OzTask* __restrict__ tasks, const OzMap* __restrict__ maps, int* __restrict__ err) {
+  const OzTask& q = tasks[blockIdx.x];
+  const OzTile t{q.ia, q.ib, q.ea, q.eb, q.M, q.N, q.Kp, q.tm, q.tn};
+  oz_tile_run(t, maps, err, OzEpiF64{q.C, q.ldc});
+}
+
+// Grouped launch: block b finds its group (largest first <= b) and its tile
+// in the group's enumeration (row tiles in order; in a lower group row tile r
+// has min(CT, 2 r + 2) column tiles, those meeting j <= i).
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_gemm_grp_kernel(const OzGroup* __restrict__ groups, int ngroups, const OzMap* __restrict__ maps,
+                       int* __restrict__ err) {
+  const int b = (int)blockIdx.x;
+  int lo = 0, hi = ngroups - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (groups[mid].first <= b) lo = mid; else hi = mid - 1;
+  }
+  const OzGroup& G = groups[lo];
+  int id = b - G.first;
+  const int RT = (G.M + OZ_TILE_M - 1) / OZ_TILE_M, CT = (G.N + OZ_TILE_N - 1) / OZ_TILE_N;
+  int r = 0;
+  for (; r < RT; ++r) {
+    const int cnt = G.lower ? min(CT, 2 * r + 2) : CT;
+    if (id < cnt) break;
+    id -= cnt;
+  }
+  const OzTile t{G.ia, G.ib, G.ea, G.eb, G.M, G.N, G.Kp, r * OZ_TILE_M, id * OZ_TILE_N};
+  oz_tile_run(t, maps, err, OzEpi{G.C, G.ldc, G.mode, G.lower});
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -460,5 +534,15 @@ cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, const OzMap* d_map
   cudaError_t e = cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
   if (e != cudaSuccess) return e;
   oz_gemm_tc_kernel<<<ntiles, OZ_THREADS, OZ_SMEM, st>>>(d_tasks, d_maps, d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_gemm_groups(const OzGroup* d_groups, int ngroups, int ntiles, const OzMap* d_maps, int* d_err,
+                                  cudaStream_t st) {
+  if (ntiles == 0 || ngroups == 0) return cudaSuccess;
+  if (reinterpret_cast<uintptr_t>(d_maps) & 63) return cudaErrorInvalidValue;   // tensor maps: 64-byte aligned
+  cudaError_t e = cudaFuncSetAttribute(oz_gemm_grp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+  if (e != cudaSuccess) return e;
+  oz_gemm_grp_kernel<<<ntiles, OZ_THREADS, OZ_SMEM, st>>>(d_groups, ngroups, d_maps, d_err);
   return cudaGetLastError();
 }

@@ -209,12 +209,13 @@ def _oracle_on_gpu_basis(p, R, b, s, ranks):
 def test_grad_coef_matches_the_oracle(g, g_kind):
     """rann_dd_grad_coef against the oracle's grad_coef (one-hot hyper-dual
     assembly of dH/da_c) at the same W, lam and basis; with G = sin sin the
-    dF/da_c = -A_c[G] term is exercised too."""
+    dF/da_c = -A_c[G] term is exercised too.  The formula is an identity in
+    W and lam, so the solves need not be converged far."""
     from oracle import solver as sv
     p, R, b, s, F, ranks = _piecewise(g, g_kind)
-    W, _ = s.solve_cg_as(F, 1e-12, 5000, allow_not_converged=True)
-    c = torch.tensor(np.random.default_rng(4).standard_normal(int(ranks.sum())), device="cuda")
-    lam, _ = s.solve_backward(c, 1e-12, 5000)
+    W, _ = s.solve_cg_as(F, 1e-8, 3000, allow_not_converged=True)
+    v = torch.tensor(np.random.default_rng(4).standard_normal(F.numel()), device="cuda")
+    lam, _ = s.solve_backward(s.eval_grid_t(v), 1e-8, 3000, allow_not_converged=True)
     got = s.grad_coef(F, W, lam)
     So = _oracle_on_gpu_basis(p, R, b, s, ranks)
     want = sv.grad_coef(So, W.cpu().numpy(), lam.cpu().numpy())
@@ -222,12 +223,15 @@ def test_grad_coef_matches_the_oracle(g, g_kind):
 
 
 def test_grad_coef_against_central_differences(g):
-    """dl/da_c of l = c . W(a) against central differences of the GPU solves
-    (2 x 2 subdomains: the AS solve is exact in one step, float64 mode)."""
+    """dl/da_c of l = v . u_hat(a) on the collocation grid (a linear functional
+    of the solution, well determined where W itself is not) against central
+    differences of the GPU solves (2 x 2 subdomains: the AS solve is exact in
+    one step; float64 mode); dl/dW = E^T v through rann_dd_eval_grid_t."""
     p, R, b, s, F, ranks = _piecewise(g, sub=2)
-    W, _ = s.solve_cg_as(F, 1e-13, 100, allow_not_converged=True)
-    cvec = torch.tensor(np.random.default_rng(6).standard_normal(int(ranks.sum())), device="cuda")
-    lam, _ = s.solve_backward(cvec, 1e-13, 100)
+    v = torch.tensor(np.random.default_rng(6).standard_normal(F.numel()), device="cuda")
+    X = s.points()
+    W, _ = s.solve_cg_as(F, 1e-10, 100, allow_not_converged=True)
+    lam, _ = s.solve_backward(s.eval_grid_t(v), 1e-10, 100, allow_not_converged=True)
     grad = s.grad_coef(F, W, lam)
     a0 = p.coef_vals.copy()
     h = 1e-5
@@ -238,8 +242,8 @@ def test_grad_coef_against_central_differences(g):
         Fv = s.rhs()
         s.pca(p.pca_mode, p.pca_thr)
         s.setup_precond("as")
-        Wv, _ = s.solve_cg_as(Fv, 1e-13, 100, allow_not_converged=True)
-        return float(cvec @ Wv)
+        Wv, _ = s.solve_cg_as(Fv, 1e-10, 100, allow_not_converged=True)
+        return float(v @ s.eval(Wv, X))
 
     for cell in (0, 6, 15):
         e = np.zeros_like(a0)
