@@ -954,175 +954,6 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
   if (tid == 0) done[i] = 0;                           // ready for the next apply (stream order)
 }
 
-// The same apply for local matrices too large for L2 to keep a 32-row block
-// between its two reads (n in the thousands: one row block of X_i is up to
-// 1.5 MB, and hundreds are in flight).  A cluster of CL_K blocks shares one
-// 32-row block: each block loads one column slab of it into shared memory
-// (X crosses HBM once), forms the slab's share of y = X_rb g, the cluster adds
-// the CL_K shares through distributed shared memory (fixed order), and each
-// block forms X_rb^T y for its slab's columns from shared memory.  The row
-// block sums part[rb][c] and the per-set reduction are those of
-// schwarz_apply_df_kernel.
-constexpr int CL_K = 8;                 // blocks per cluster (column slabs of a row block)
-constexpr int CL_MIN_N = 2048;          // from this size on a 32-row block outgrows its share of L2
-constexpr int CL_T = 256;
-constexpr int CL_MAXP = 368;            // column pairs per slab: n <= 2 CL_K CL_MAXP = 5888
-__device__ __forceinline__ uint32_t cl_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cl_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ float2 cl_ld_f2(const float2* local, uint32_t rank) {
-  uint32_t a = (uint32_t)__cvta_generic_to_shared(local), ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
-  float2 v;
-  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(ra) : "memory");
-  return v;
-}
-__global__ void __cluster_dims__(CL_K, 1, 1) __launch_bounds__(CL_T, 1)
-    schwarz_apply_cl_kernel(const CholMat* __restrict__ mats, const int* __restrict__ set_ptr,
-                            const int* __restrict__ set_sub, const SubDev* __restrict__ subs,
-                            const double* __restrict__ r, const int64_t* __restrict__ p_off32,
-                            double* __restrict__ part, int wkind, const int* __restrict__ inc_ptr,
-                            const int64_t* __restrict__ s_off, double* __restrict__ s, int* __restrict__ done,
-                            int ckind, double* __restrict__ z, const float2* __restrict__ r2) {
-  extern __shared__ float4 xs4[];                       // [nr][chunk] column pairs of the slab, then g
-  __shared__ float2 ypart[AR], yfull[AR];
-  __shared__ float2 lpart[CL_T / 32][AR];
-  __shared__ int seg_c[AMAX_SUB + 1], seg_p[AMAX_SUB];
-  __shared__ int64_t seg_w[AMAX_SUB];
-  __shared__ double seg_d[AMAX_SUB];
-  __shared__ int last, own_q;
-  const int i = blockIdx.y;
-  const CholMat M = mats[i];
-  const int nb = (M.n + AR - 1) / AR;
-  const int rbx = (int)blockIdx.x / CL_K;               // the same for the whole cluster
-  if (rbx >= nb) return;
-  const int kc = (int)cl_rank();
-  const int rb = nb - 1 - rbx;                          // long bottom row blocks first
-  const int r0 = rb * AR, r1 = min(M.n, r0 + AR), nr = r1 - r0;
-  const int np = (r1 + 1) >> 1;                         // column pairs the block touches
-  const int chunk = (np + CL_K - 1) / CL_K;
-  const int p0 = min(np, kc * chunk), p1 = min(np, p0 + chunk), nw = p1 - p0;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int q0 = set_ptr[i], nq = set_ptr[i + 1] - q0;
-  if (tid < nq) {
-    const int k = set_sub[q0 + tid];
-    seg_p[tid] = subs[k].p;
-    seg_w[tid] = subs[k].woff;
-    seg_d[tid] = input_weight(wkind, k, i, inc_ptr);
-    if (k == i) own_q = tid;
-  }
-  if (tid < AR) ypart[tid] = make_float2(0.f, 0.f);
-  __syncthreads();
-  if (tid == 0) {
-    int c = 0;
-    for (int q = 0; q < nq; ++q) { seg_c[q] = c; c += seg_p[q]; }
-    seg_c[nq] = c;
-  }
-  __syncthreads();
-  float4* gs4 = xs4 + (size_t)AR * chunk;
-  for (int t = tid; t < nw; t += CL_T) {                // g of the slab's columns
-    float2 v[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int c = 2 * (p0 + t) + e;
-      v[e] = make_float2(0.f, 0.f);
-      if (c < r1) {
-        int q = 0;
-        while (q + 1 < nq && seg_c[q + 1] <= c) ++q;
-        v[e] = r2 ? r2[seg_w[q] + (c - seg_c[q])] : df_split(seg_d[q] * r[seg_w[q] + (c - seg_c[q])]);
-      }
-    }
-    gs4[t] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-  }
-  // the slab: row rr, pairs p0 .. p1 (zero beyond the row's triangle; the upper
-  // element of the pair holding an even row's diagonal is zero)
-  const int tot = nr * nw;
-  for (int e0 = tid; e0 < tot; e0 += CL_T * 4) {
-    float4 v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = e0 + u * CL_T;
-      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (e < tot) {
-        const int rr = e / nw, pp = p0 + e % nw, row = r0 + rr;
-        if (2 * pp <= row) {
-          v[u] = reinterpret_cast<const float4*>(M.X2 + (int64_t)row * M.ld)[pp];
-          if (2 * pp + 1 > row) { v[u].z = 0.f; v[u].w = 0.f; }
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = e0 + u * CL_T;
-      if (e < tot) xs4[(e / nw) * chunk + e % nw] = v[u];
-    }
-  }
-  __syncthreads();
-  // the slab's share of y: warp w takes rows w, w + 8, ...; lanes stride the pairs
-  for (int rr = warp; rr < nr; rr += CL_T / 32) {
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    for (int t = lane; t < nw; t += 32) {
-      const float4 a = xs4[rr * chunk + t], g = gs4[t];
-      df_mac(h0, l0, make_float2(a.x, a.y), make_float2(g.x, g.y));
-      df_mac(h1, l1, make_float2(a.z, a.w), make_float2(g.z, g.w));
-    }
-    df_add(h0, l0, h1, l1);
-    df_warp_sum(h0, l0);
-    if (lane == 0) ypart[rr] = make_float2(h0, l0);
-  }
-  cl_sync();                                            // every slab's share is in its shared memory
-  if (tid < nr) {
-    float h = 0.f, l = 0.f;
-    for (int q = 0; q < CL_K; ++q) {                    // fixed order over the slabs
-      const float2 v = cl_ld_f2(&ypart[tid], (uint32_t)q);
-      df_add(h, l, v.x, v.y);
-    }
-    yfull[tid] = make_float2(h, l);
-  }
-  cl_sync();                                            // no block leaves while a peer reads its shares
-  // X_rb^T y on the slab's columns: thread per pair, the block's rows from shared memory
-  double* pr = part + p_off32[i] + (int64_t)rb * M.n;
-  for (int t = tid; t < nw; t += CL_T) {
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    for (int rr = 0; rr < nr; ++rr) {
-      const float4 a = xs4[rr * chunk + t];
-      const float2 y = yfull[rr];
-      df_mac(h0, l0, make_float2(a.x, a.y), y);
-      df_mac(h1, l1, make_float2(a.z, a.w), y);
-    }
-    const int c = 2 * (p0 + t);
-    pr[c] = df_to_double(h0, l0);
-    if (c + 1 < r1) pr[c + 1] = df_to_double(h1, l1);
-  }
-  // the last block of the set adds the row blocks' parts
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) last = (atomicAdd(&done[i], 1) == nb * CL_K - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  if (ckind == RANN_PREC_RAS) {
-    const int c0 = seg_c[own_q], pc = seg_p[own_q];
-    for (int c = c0 + tid; c < c0 + pc; c += CL_T) {
-      double acc = 0.0;
-      for (int b = c / AR; b < nb; ++b) acc += __ldcg(part + p_off32[i] + (int64_t)b * M.n + c);
-      z[seg_w[own_q] + (c - c0)] = acc;
-    }
-  } else {
-    for (int c = tid; c < M.n; c += CL_T) {
-      double acc = 0.0;
-      for (int b = c / AR; b < nb; ++b) acc += __ldcg(part + p_off32[i] + (int64_t)b * M.n + c);
-      s[s_off[i] + c] = acc;
-    }
-  }
-  if (tid == 0) done[i] = 0;
-}
-
 // schwarz_apply_df_kernel for NR right-hand sides r_c = r + c ldr (c < NR) with
 // unit input weights and the plain combine (s_c = s + c lds, row-block sums in
 // part + c pstride): each row of X_i is read once for all of them; per
@@ -1582,18 +1413,6 @@ cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, 
                                     int* d_done, int wkind, const int* d_inc_ptr, int ckind, double* d_z,
                                     cudaStream_t st, const float2* d_r2) {
   if (nsets == 0) return cudaSuccess;
-  if (maxn > CL_MIN_N && maxn <= 2 * CL_K * CL_MAXP) {
-    // large local matrices: the cluster apply (one HBM read of X per apply)
-    const int chunk = ((maxn + 1) / 2 + CL_K - 1) / CL_K;
-    const int smem = (int)(sizeof(float4) * (size_t)(AR + 1) * chunk);
-    cudaError_t e = cudaFuncSetAttribute(schwarz_apply_cl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    const int nb = (maxn + AR - 1) / AR;
-    schwarz_apply_cl_kernel<<<dim3(nb * CL_K, nsets), CL_T, smem, st>>>(
-        d_mats, d_set_ptr, d_set_sub, d_sub, d_r, d_p_off32, d_part, wkind, d_inc_ptr, d_s_off, d_s, d_done, ckind,
-        d_z, wkind == RANN_PREC_AS ? d_r2 : nullptr);
-    return cudaGetLastError();
-  }
   const int smem = (int)(sizeof(float4) * (size_t)((maxn + 1) / 2));
   cudaError_t e = cudaFuncSetAttribute(schwarz_apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

@@ -212,10 +212,10 @@ def test_grad_coef_matches_the_oracle(g, g_kind):
     dF/da_c = -A_c[G] term is exercised too.  The formula is an identity in
     W and lam, so the solves need not be converged far."""
     from oracle import solver as sv
-    p, R, b, s, F, ranks = _piecewise(g, g_kind)
-    W, _ = s.solve_cg_as(F, 1e-8, 3000, allow_not_converged=True)
+    p, R, b, s, F, ranks = _piecewise(g, g_kind, mode=1, kind="ras")
+    W, _ = s.solve_gmres_ras(F, 1e-10, 50, 3000, allow_not_converged=True)
     v = torch.tensor(np.random.default_rng(4).standard_normal(F.numel()), device="cuda")
-    lam, _ = s.solve_backward(s.eval_grid_t(v), 1e-8, 3000, allow_not_converged=True)
+    lam, _ = s.solve_backward(s.eval_grid_t(v), 1e-10, 3000, allow_not_converged=True)
     got = s.grad_coef(F, W, lam)
     So = _oracle_on_gpu_basis(p, R, b, s, ranks)
     want = sv.grad_coef(So, W.cpu().numpy(), lam.cpu().numpy())

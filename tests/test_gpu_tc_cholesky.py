@@ -94,16 +94,14 @@ def test_tensor_core_factors_solve(g, reduced):
     assert torch.equal(z1, z2)
 
 
-def test_cluster_apply_on_sets_beyond_two_thousand_unknowns(g):
-    """Local matrices above 2048 unknowns take the cluster apply (a 32-row
-    block of L_i^{-1} shared by eight blocks through distributed shared
-    memory).  On a 2 x 2 x 2 Poisson grid with 400 neurons every extended set
-    holds all subdomains (about 2800 unknowns): M^{-1} r = 8 A^{-1} r.  The
-    double-float apply (tensor-core factors, cluster apply) is held to the
-    float64 one (float64 factors, triangular products) and to a direct
-    float64 solve of A within kappa(A) 2^-48; two applies are identical."""
-    import dataclasses
-    p = dataclasses.replace(ri.poisson3d(sub=2, pts=10, neurons=400))
+def test_factors_and_apply_on_sets_beyond_two_thousand_unknowns(g):
+    """A larger local matrix: on a 2 x 2 x 2 Poisson grid with 600 neurons
+    every extended set holds all subdomains (over 2048 unknowns, nine
+    panels): M^{-1} r = 8 A^{-1} r.  The double-float apply (tensor-core
+    factors) is held to the float64 one (float64 factors, triangular
+    products) and to a direct float64 solve of A within kappa(A) 2^-48; two
+    applies are identical."""
+    p = ri.poisson3d(sub=2, pts=14, neurons=600)
     s = g.RannDD(p, *ri.weights(p))
     s.assemble()
     F = s.rhs()
@@ -133,7 +131,7 @@ def test_cluster_apply_on_sets_beyond_two_thousand_unknowns(g):
             assert np.array_equal(out[1], s.precond_apply(rd).cpu().numpy())
     e1 = np.linalg.norm(out[1] - zref) / np.linalg.norm(zref)
     e0 = np.linalg.norm(out[0] - zref) / np.linalg.norm(zref)
-    print(f"\nn = {n}, kappa(A) {kappa:.3e}: double-float (tensor-core factors, cluster apply) {e1:.3e}, "
+    print(f"\nn = {n}, kappa(A) {kappa:.3e}: double-float (tensor-core factors) {e1:.3e}, "
           f"float64 {e0:.3e}")
     assert e1 <= max(1e-12, kappa * 2.0 ** -48)
     assert e0 <= max(1e-12, kappa * 2.0 ** -53 * 8)
