@@ -14,7 +14,9 @@ set-up, Krylov solve.  Synthetic, seeded inputs.
 The line also carries the 2D multiscale workload (8 x 8 subdomains, m = 300,
 SAS-preconditioned GMRES(50)) in both precision modes: plain float64
 (mode 0) and the double-float preconditioner and inner iterations with
-float64 refinement (mode 1).
+float64 refinement (mode 1); and the differentiable batch of 64
+piecewise-coefficient diffusion instances (forward RAS-GMRES, adjoint
+solve, gradients with respect to the coefficient cells and the source).
 
 Prints one JSON line.  --impl reference times the CPU oracle (float64 numpy)
 on a bounded sample of the workload.
@@ -367,6 +369,8 @@ def bench_ours(args, rank, world):
     }
     if not args.no_multiscale:
         out["multiscale2d"] = multiscale_arms(g, torch)
+    if not args.no_batch:
+        out["piecewise_batch"] = piecewise_batch(g, torch)
     if args.multi_rhs > 0:
         out["multi_rhs"] = [multi_rhs_timing(g, args.multi_rhs, "cg"), multi_rhs_timing(g, args.multi_rhs, "gmres")]
     return out
@@ -574,6 +578,7 @@ def main():
     ap.add_argument("--iters-hint", type=int, default=377)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multiscale", action="store_true", help="skip the multiscale precision-mode arms")
+    ap.add_argument("--no-batch", action="store_true", help="skip the piecewise-coefficient differentiable batch")
     ap.add_argument("--multi-rhs", type=int, default=0,
                     help="also time AS-CG and the workload's GMRES on this many right-hand sides in lockstep "
                          "against one at a time (multiscale workload)")

@@ -116,17 +116,31 @@ __device__ __forceinline__ void coef_fun(const ProbDev& P, const double* x, doub
     ga[1] = RANN_PI * k * sx * cy;
     return;
   }
-  int g = P.coef_grid;
+  // the cell factors stay in registers: loops over the largest grid (8),
+  // fully unrolled, with the cells beyond g skipped
+  const int g = P.coef_grid;
   double vx[8], dx[8], vy[8], dy[8];
-  for (int c = 0; c < g; ++c) { sbox(x[0], c, g, &vx[c], &dx[c]); sbox(x[1], c, g, &vy[c], &dy[c]); }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    vx[c] = dx[c] = vy[c] = dy[c] = 0.0;
+    if (c < g) { sbox(x[0], c, g, &vx[c], &dx[c]); sbox(x[1], c, g, &vy[c], &dy[c]); }
+  }
   double s = 0, sx = 0, sy = 0;
-  for (int cy = 0; cy < g; ++cy)
-    for (int cx = 0; cx < g; ++cx) {
-      double v = P.coef_vals[cy * g + cx];
-      s += v * vx[cx] * vy[cy];
-      sx += v * dx[cx] * vy[cy];
-      sy += v * vx[cx] * dy[cy];
+#pragma unroll
+  for (int cy = 0; cy < 8; ++cy) {
+    if (cy >= g) break;
+    double rv = 0, rd = 0;                    // sum_cx v vx, sum_cx v dx along row cy
+#pragma unroll
+    for (int cx = 0; cx < 8; ++cx) {
+      if (cx >= g) break;
+      const double v = P.coef_vals[cy * g + cx];
+      rv += v * vx[cx];
+      rd += v * dx[cx];
     }
+    s += rv * vy[cy];
+    sx += rd * vy[cy];
+    sy += rv * dy[cy];
+  }
   *a = s; ga[0] = sx; ga[1] = sy;
 }
 
@@ -248,17 +262,17 @@ __global__ void rhs_kernel(ProbDev P, double* __restrict__ F, int64_t N) {
   }
   double AG = 0.0;
   if (P.g_kind == RANN_G_SINPROD) {
-    double s[3], c[3], G = 1.0;
-    for (int i = 0; i < P.ns; ++i) { sincospi(x[i], &s[i], &c[i]); G *= s[i]; }
+    // A G for G = prod_i sin(pi x_i): Lap_S G = -ns pi^2 G, d_i G = pi cos(pi x_i) prod_{l != i} sin(pi x_l)
     double alpha, beta[3], c0;
     op_coefs(P, x, &alpha, beta, &c0);
-    double lap = -(double)P.ns * RANN_PI * RANN_PI * G;
-    double bg = 0.0;
-    for (int i = 0; i < P.ns; ++i) {
-      double rest = 1.0;
-      for (int l = 0; l < P.ns; ++l) if (l != i) rest *= s[l];
-      bg += beta[i] * RANN_PI * c[i] * rest;
-    }
+    double s[3] = {1.0, 1.0, 1.0}, c[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (i < P.ns) sincospi(x[i], &s[i], &c[i]);
+    const double G = s[0] * s[1] * s[2];
+    const double lap = -(double)P.ns * RANN_PI * RANN_PI * G;
+    const double bg = RANN_PI * (beta[0] * c[0] * s[1] * s[2] + beta[1] * s[0] * c[1] * s[2] +
+                                 beta[2] * s[0] * s[1] * c[2]);
     AG = -alpha * lap + bg + c0 * G;
   }
   F[g] = f - AG;
@@ -398,14 +412,14 @@ __global__ void __launch_bounds__(CG_T) coef_grad_kernel(ProbDev P, const SubDev
         }
     // u_hat = v_W + G
     if (P.g_kind == RANN_G_SINPROD) {
-      double s[3], c[3], G = 1.0;
-      for (int i = 0; i < ns; ++i) { sincospi(xs[i], &s[i], &c[i]); G *= s[i]; }
-      for (int i = 0; i < ns; ++i) {
-        double rest = 1.0;
-        for (int l = 0; l < ns; ++l) if (l != i) rest *= s[l];
-        va[i] += RANN_PI * c[i] * rest;
-      }
-      la += -(double)ns * RANN_PI * RANN_PI * G;
+      double s[3] = {1.0, 1.0, 1.0}, c[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < ns) sincospi(xs[i], &s[i], &c[i]);
+      va[0] += RANN_PI * c[0] * s[1] * s[2];
+      va[1] += RANN_PI * s[0] * c[1] * s[2];
+      va[2] += RANN_PI * s[0] * s[1] * c[2];
+      la += -(double)ns * RANN_PI * RANN_PI * (s[0] * s[1] * s[2]);
     }
     const double ri = res[t], hi = hl[t];
     Q = -ri * lb + hi * la;
@@ -413,13 +427,22 @@ __global__ void __launch_bounds__(CG_T) coef_grad_kernel(ProbDev P, const SubDev
   }
   // cell terms s_c Q + grad s_c . Gv, summed over the block (warp shuffles, then warps in order)
   double sx[8], dx[8], sy[8], dy[8];
-  for (int c = 0; c < gq; ++c) { sbox(xs[0], c, gq, &sx[c], &dx[c]); sbox(xs[1], c, gq, &sy[c], &dy[c]); }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    sx[c] = dx[c] = sy[c] = dy[c] = 0.0;
+    if (c < gq) { sbox(xs[0], c, gq, &sx[c], &dx[c]); sbox(xs[1], c, gq, &sy[c], &dy[c]); }
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c = 0; c < nc; ++c) {
-    const int cx = c % gq, cy = c / gq;
-    double v = (t < N) ? (sx[cx] * sy[cy] * Q + dx[cx] * sy[cy] * Gv[0] + sx[cx] * dy[cy] * Gv[1]) : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) wsum[warp][c] = v;
+#pragma unroll
+  for (int cy = 0; cy < 8; ++cy) {
+    if (cy >= gq) break;
+#pragma unroll
+    for (int cx = 0; cx < 8; ++cx) {
+      if (cx >= gq) break;
+      double v = (t < N) ? (sx[cx] * sy[cy] * Q + dx[cx] * sy[cy] * Gv[0] + sx[cx] * dy[cy] * Gv[1]) : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) wsum[warp][cy * gq + cx] = v;
+    }
   }
   __syncthreads();
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {

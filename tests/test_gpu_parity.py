@@ -86,6 +86,24 @@ def test_rhs_parity(g, name):
     np.testing.assert_allclose(F.cpu().numpy(), Fo, rtol=0, atol=1e-13 * max(1.0, np.abs(Fo).max()))
 
 
+@pytest.mark.parametrize("g_kind", [ri.G_ZERO, ri.G_SINPROD])
+@pytest.mark.parametrize("name,coef", [("poisson2d_2x2", None), ("poisson3d", None), ("heat3d", None),
+                                       ("multiscale2d", None), ("piecewise2d", None),
+                                       ("piecewise2d", ri.COEF_CONST)])
+def test_rhs_every_operator_and_lift(g, name, coef, g_kind):
+    """F = f - A G (Eq. (cons1)/(cons2): u = L v + G) for every operator and
+    coefficient, with and without the lift G = prod_i sin(pi x_i)."""
+    import dataclasses
+    p = dataclasses.replace(ri.config(name, small=True), g_kind=g_kind)
+    if coef is not None:
+        p = dataclasses.replace(p, coef=coef, coef_value=1.7)
+    s = g.RannDD(p, *ri.weights(p))
+    F = s.rhs().cpu().numpy()
+    Fo = asm.rhs(p)
+    assert np.all(np.isfinite(F))
+    np.testing.assert_allclose(F, Fo, rtol=0, atol=1e-13 * max(1.0, np.abs(Fo).max()))
+
+
 @pytest.mark.parametrize("name", SMALL)
 def test_assembly_parity(g, name):
     p, s, F, blocks, *_ = pipeline(g, name)
