@@ -371,13 +371,90 @@ rann_status rann_dd_profile_enable(rann_dd_handle* h, int on);
 rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const char** name, int64_t* launches,
                                 double* ms, double* alg_bytes, double* alg_flops, int* bound);
 
+/* Schwarz apply configurations (precision mode 1).  0: the fused kernel that
+ * reads 32-row blocks of L_i^{-1} twice (the second time from L2); 1..3: the
+ * streaming kernel that reads every row of L_i^{-1} once through shared
+ * memory, with row chunks of about 1/2, 1/6, 1/12 of an SM's share of the
+ * factor entries (sets of at most 6144 unknowns).  setup_precond picks 2 for
+ * sets of 2048 unknowns and more, else 0.  The configurations differ only in
+ * the summation order (results agree to the double-float factor accuracy);
+ * each is deterministic.
+ * rann_dd_set_apply_config: after setup_precond; RANN_EINVAL for a
+ * configuration this set-up cannot run (or out of range).
+ * rann_dd_tune_apply: times every configuration this set-up can run (one
+ * warm-up and `reps` timed applies each, CUDA events on the handle's
+ * stream), keeps the fastest; best_out gets it, ms_out [RANN_APPLY_NCFG] (or
+ * NULL) the ms per apply, -1 where a configuration cannot run.
+ * Synchronises. */
+#define RANN_APPLY_NCFG 4
+rann_status rann_dd_set_apply_config(rann_dd_handle* h, int cfg);
+rann_status rann_dd_get_apply_config(rann_dd_handle* h, int* cfg);
+rann_status rann_dd_tune_apply(rann_dd_handle* h, int reps, int* best_out, float* ms_out);
+
+/* Moves the handle's work to another CUDA stream (0 = legacy default):
+ * waits for the current stream's work first. */
+rann_status rann_dd_set_stream(rann_dd_handle* h, void* cuda_stream);
+
+/* ---- Batches of instances (Sec. 5, Table 2: many independent problems) ----
+ * rann_dd_batch_run takes n instances (handles of any problem and grid size,
+ * created and left unassembled or assembled, in any precision mode) through
+ * the whole path -- assemble, F, PCA, Schwarz set-up, the preconditioned
+ * solve and, with backward set, the gradient of the grid misfit
+ * l = ||u_hat - u_obs||^2 over the collocation points: dl/dW = 2 E^T (u_hat -
+ * u_obs), the adjoint solve, dl/dF = H lam and, for the piecewise
+ * coefficient, dl/da_c (rann_dd_grad_coef).  A batch owns `nworkers` host
+ * threads (1..64), each with its own CUDA stream; a worker moves an
+ * instance's handle onto its stream for the run and back afterwards, so the
+ * kernels of different instances overlap on the device while every worker
+ * drives its instance's host-side control (rank decisions, Krylov
+ * convergence checks).  Instances start largest first (points x neurons).
+ * With autotune set, the first instance of each size class (subdomain
+ * count, largest extended set rounded up to 64 unknowns) runs
+ * rann_dd_tune_apply(reps 2) and the others of the class wait for and reuse
+ * its choice.
+ * Per instance (arrays of n pointers, device buffers caller-owned):
+ *   F_dev [n_points] written; W_dev with room for J*m entries, dof written;
+ *   backward only: u_obs_dev [n_points] read, grad_F_dev [n_points] written
+ *   (or NULL), grad_coef_host [g*g] written for RANN_COEF_PIECEWISE handles
+ *   (or NULL).
+ * out[k]: the first failing step's status (RANN_NOT_CONVERGED of a solve is
+ * recorded, not failing), dof, the apply configuration used, the loss, and
+ * the forward and adjoint statistics.  Returns RANN_OK when every instance
+ * succeeded, else the first failing instance's status (the others still
+ * run).  A handle must not be used by the caller while the call runs. */
+typedef struct rann_dd_batch rann_dd_batch;
+typedef struct {
+  int pca_mode;           /* RANN_PCA_*                                     */
+  double pca_thr;
+  int prec_kind;          /* RANN_PREC_*                                    */
+  int solver;             /* 0: CG (prec AS or NONE), 1: GMRES(restart)     */
+  double rtol;
+  int restart;
+  int maxit;
+  int autotune;           /* 1: tune the Schwarz apply per size class       */
+  int backward;           /* 1: also the misfit gradient                    */
+} rann_dd_pipeline;
+typedef struct {
+  rann_status status;
+  int64_t dof;
+  int apply_config;
+  double loss;
+  rann_dd_stats forward, adjoint;
+} rann_dd_pipeline_out;
+rann_status rann_dd_batch_create(int nworkers, rann_dd_batch** out);
+void rann_dd_batch_destroy(rann_dd_batch* b);
+rann_status rann_dd_batch_run(rann_dd_batch* b, int n, rann_dd_handle* const* hs, const rann_dd_pipeline* cfg,
+                              double* const* F_dev, double* const* W_dev, const double* const* u_obs_dev,
+                              double* const* grad_F_dev, double* const* grad_coef_host, rann_dd_pipeline_out* out);
+
+
 /* Host-side fault injection for failure-detection tests (the paper has no
  * counterpart; no device code is made to fault, trap or hang):
  *   RANN_FAULT_WAIT_EXPIRED: writes `value` (non-zero) into the handle's
  *     device error word of the tensor-core product pipelines, exactly what a
- *     bounded mbarrier wait writes when it gives up; the next pca or
- *     setup_precond that reads the word back returns RANN_TIMEOUT (and
- *     clears it).  value = 0 clears the word.
+ *     bounded mbarrier wait writes when it gives up; the next pca,
+ *     setup_precond or solve that reads the word back returns RANN_TIMEOUT
+ *     (and clears it).  value = 0 clears the word.
  *   RANN_FAULT_ALLOC_CAP: from now on the handle's device allocations fail
  *     (RANN_ENOMEM, before any cudaMalloc) whenever its live bytes would
  *     exceed `value`; value < 0 removes the cap.

@@ -72,6 +72,17 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Pipeline(ctypes.Structure):
+    _fields_ = [("pca_mode", ctypes.c_int), ("pca_thr", ctypes.c_double), ("prec_kind", ctypes.c_int),
+                ("solver", ctypes.c_int), ("rtol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("maxit", ctypes.c_int), ("autotune", ctypes.c_int), ("backward", ctypes.c_int)]
+
+
+class PipelineOut(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("dof", ctypes.c_int64), ("apply_config", ctypes.c_int),
+                ("loss", ctypes.c_double), ("forward", Stats), ("adjoint", Stats)]
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -115,6 +126,15 @@ SIGNATURES = {
     "rann_dd_profile_get": (_I, [_P, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_L),
                                  ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "rann_dd_inject_fault": (_I, [_P, _I, _L]),
+    "rann_dd_set_apply_config": (_I, [_P, _I]),
+    "rann_dd_get_apply_config": (_I, [_P, ctypes.POINTER(_I)]),
+    "rann_dd_tune_apply": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
+    "rann_dd_set_stream": (_I, [_P, _P]),
+    "rann_dd_batch_create": (_I, [_I, ctypes.POINTER(_P)]),
+    "rann_dd_batch_destroy": (None, [_P]),
+    "rann_dd_batch_run": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(Pipeline), ctypes.POINTER(_P),
+                               ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                               ctypes.POINTER(PipelineOut)]),
     "rann_dd_status_string": (ctypes.c_char_p, [_I]),
     "rann_dd_last_error": (ctypes.c_char_p, []),
 }
@@ -297,6 +317,23 @@ class RannDD:
         s = self._lib.rann_dd_solve_cg_as_multi(self._h, _dptr(F), _dptr(W), nrhs, rtol, maxit, st)
         _check(s, "rann_dd_solve_cg_as_multi", allow=(NOT_CONVERGED,) if allow_not_converged else ())
         return W, [st[c].as_dict() for c in range(nrhs)]
+
+    def set_apply_config(self, cfg: int):
+        """Schwarz apply configuration (0: fused 32-row blocks; 1..3: streaming rows)."""
+        _check(self._lib.rann_dd_set_apply_config(self._h, int(cfg)), "rann_dd_set_apply_config")
+
+    def get_apply_config(self) -> int:
+        c = _I()
+        _check(self._lib.rann_dd_get_apply_config(self._h, ctypes.byref(c)), "rann_dd_get_apply_config")
+        return c.value
+
+    def tune_apply(self, reps: int = 3):
+        """Times every Schwarz apply configuration, keeps the fastest; returns
+        (best, ms per configuration, None where it cannot run)."""
+        best = _I()
+        ms = (ctypes.c_float * APPLY_NCFG)()
+        _check(self._lib.rann_dd_tune_apply(self._h, int(reps), ctypes.byref(best), ms), "rann_dd_tune_apply")
+        return best.value, [None if v < 0 else float(v) for v in ms]
 
     def solve_gmres_ras_multi(self, F, rtol=1e-10, restart=50, maxit=2000, W=None, allow_not_converged=False):
         """Left-preconditioned GMRES(restart) for the rows of F ([nrhs][N], device
@@ -547,3 +584,75 @@ class GridEval:
                 return solver.eval_grid_t(gu.contiguous())
 
         return _Fn.apply(W)
+
+
+APPLY_NCFG = 4
+SOLVER_CG, SOLVER_GMRES = 0, 1
+
+
+class Batch:
+    """Many instances through the whole path at once (rann_dd_batch_run): a pool
+    of native worker threads, one CUDA stream each; instances of any grid size
+    overlap on the device.  run() takes RannDD handles (fresh or assembled) and
+    returns one dict per instance: F, W (dof entries), the statistics, the
+    Schwarz apply configuration used and, with u_obs given, the misfit
+    l = ||u_hat - u_obs||^2 with dl/dF and dl/da_c."""
+
+    def __init__(self, nworkers: int = 8):
+        self._lib = load_library()
+        b = ctypes.c_void_p()
+        _check(self._lib.rann_dd_batch_create(int(nworkers), ctypes.byref(b)), "rann_dd_batch_create")
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.rann_dd_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, handles, pca_mode, pca_thr, prec="ras", solver=SOLVER_GMRES, rtol=1e-10, restart=50,
+            maxit=3000, autotune=False, u_obs=None, allow_not_converged=True):
+        import torch
+        n = len(handles)
+        cfg = Pipeline(int(pca_mode), float(pca_thr), PREC_BY_NAME[prec] if isinstance(prec, str) else int(prec),
+                       int(solver), float(rtol), int(restart), int(maxit), int(bool(autotune)), int(u_obs is not None))
+        sizes = [h.sizes() for h in handles]
+        F = [torch.empty(sz["n_points"], dtype=torch.float64, device="cuda") for sz in sizes]
+        W = [torch.empty(sz["J"] * sz["m"], dtype=torch.float64, device="cuda") for sz in sizes]
+        gF = [torch.empty(sz["n_points"], dtype=torch.float64, device="cuda") for sz in sizes] if u_obs is not None else None
+        ncell = [h.problem.coef_grid ** 2 if getattr(h.problem, "coef", 0) == 2 else 0 for h in handles]
+        gc = [np.zeros(max(c, 1)) for c in ncell]
+        arr = lambda xs: (_P * max(n, 1))(*[_dptr(x) for x in xs])
+        hs = (_P * max(n, 1))(*[h._h.value for h in handles])
+        out = (PipelineOut * max(n, 1))()
+        uo = arr(u_obs) if u_obs is not None else None
+        gfp = arr(gF) if gF is not None else None
+        gcp = (_P * max(n, 1))(*[g.ctypes.data if c else None for g, c in zip(gc, ncell)])
+        torch.cuda.synchronize()
+        s = self._lib.rann_dd_batch_run(self._b, n, hs, ctypes.byref(cfg), arr(F), arr(W), uo, gfp,
+                                        gcp if u_obs is not None else None, out)
+        _check(s, "rann_dd_batch_run", allow=(NOT_CONVERGED,) if allow_not_converged else ())
+        res = []
+        for k in range(n):
+            o = out[k]
+            if o.status != OK and not (allow_not_converged and o.status == NOT_CONVERGED):
+                raise RannError(o.status, f"batch instance {k}")
+            h = handles[k]
+            nr, nc = _L(), _I()
+            rk = []
+            for j in range(sizes[k]["J"]):
+                _check(self._lib.rann_dd_block_info(h._h, j, ctypes.byref(nr), ctypes.byref(nc)), "rann_dd_block_info")
+                rk.append(nc.value)
+            h.ranks = np.array(rk, dtype=np.int64)
+            r = {"status": STATUS.get(o.status, o.status), "dof": int(o.dof), "apply_config": int(o.apply_config),
+                 "F": F[k], "W": W[k][: int(o.dof)], "forward": o.forward.as_dict()}
+            if u_obs is not None:
+                r.update({"loss": float(o.loss), "adjoint": o.adjoint.as_dict(), "grad_F": gF[k],
+                          "grad_coef": gc[k][: ncell[k]].copy() if ncell[k] else None})
+            res.append(r)
+        return res

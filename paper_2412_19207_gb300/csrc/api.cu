@@ -238,6 +238,14 @@ struct rann_dd_handle {
   double* d_tpart32 = nullptr;
   int* d_adone = nullptr;          // per set: row blocks of the fused apply finished (reset by the last)
   int64_t p32_total = 0;           // doubles of the fused apply's row-block sums (one right-hand side)
+  // streaming apply (sets of up to schwarz_rows_nmax() unknowns): row chunks and their column sums
+  SrChunk* d_sr_chunks = nullptr;
+  int* d_sr_order = nullptr;
+  int* d_sr_ckptr = nullptr;
+  double* d_sr_part = nullptr;
+  int sr_nchunks = 0;
+  int apply_cfg = 0;               // Schwarz apply configuration (0: fused 32-row blocks; >= 1: streaming)
+  std::vector<int> set_n;          // n_i of the extended sets (for re-planning the streaming apply)
   int64_t s_total = 0;             // entries of the stacked set vectors s_i (sum of n_i)
   bool prec_df = false;           // the set-up kept only double-float factors
   double* d_Xmats = nullptr;
@@ -1082,6 +1090,42 @@ static rann_status build_gram_rows(rann_dd_handle* h, const std::vector<int64_t>
   return RANN_OK;
 }
 
+// ------------------------------------------------ Schwarz apply configurations --
+// 0: the fused 32-row-block kernel (precision mode 1, sets of up to 27 subdomains);
+// c >= 1: the streaming kernel with chunks of about 1/APPLY_CHUNKS[c] of an SM's
+// share of the triangles' entries (sets of up to schwarz_rows_nmax() unknowns).
+static const int APPLY_CHUNKS[RANN_APPLY_NCFG] = {0, 2, 6, 12};
+
+static bool streaming_ok(const rann_dd_handle* h) {
+  return h->prec_df && h->maxn <= schwarz_rows_nmax() && h->max_set_size <= schwarz_apply_max_subs();
+}
+
+static rann_status set_apply_config(rann_dd_handle* h, int cfg) {
+  REQUIRE(cfg >= 0 && cfg < RANN_APPLY_NCFG, RANN_EINVAL, "apply configuration %d out of range", cfg);
+  REQUIRE(cfg == 0 || streaming_ok(h), RANN_EINVAL,
+          "streaming apply needs precision mode 1 and sets of at most %d unknowns", schwarz_rows_nmax());
+  for (void* p : {(void*)h->d_sr_chunks, (void*)h->d_sr_order, (void*)h->d_sr_ckptr, (void*)h->d_sr_part}) dfree(h, p);
+  h->d_sr_chunks = nullptr; h->d_sr_order = nullptr; h->d_sr_ckptr = nullptr; h->d_sr_part = nullptr;
+  h->sr_nchunks = 0;
+  h->apply_cfg = 0;
+  if (cfg > 0) {
+    int64_t tri = 0;
+    for (int n : h->set_n) tri += (int64_t)n * (n + 1) / 2;
+    const int64_t target = std::max<int64_t>(65536, tri / ((int64_t)h->nsm * APPLY_CHUNKS[cfg]));
+    std::vector<SrChunk> chunks;
+    std::vector<int> ck_ptr, order;
+    int64_t ptot = 0;
+    schwarz_rows_plan(h->set_n, target, chunks, ck_ptr, order, ptot);
+    CK(dupload(h, &h->d_sr_chunks, chunks));
+    CK(dupload(h, &h->d_sr_order, order));
+    CK(dupload(h, &h->d_sr_ckptr, ck_ptr));
+    CK(dalloc(h, (void**)&h->d_sr_part, sizeof(double) * (size_t)std::max<int64_t>(ptot, 1)));
+    h->sr_nchunks = (int)chunks.size();
+  }
+  h->apply_cfg = cfg;
+  return RANN_OK;
+}
+
 extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int overlap_level) {
   REQUIRE(h, RANN_EINVAL, "null handle");
   REQUIRE(h->reduced, RANN_EORDER, "setup_precond before pca");
@@ -1092,9 +1136,12 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
                   (void*)h->d_inc_set, (void*)h->d_inc_pos, (void*)h->d_s_off, (void*)h->d_s,
                   (void*)h->d_Amats, (void*)h->d_Xmats, (void*)h->d_g, (void*)h->d_y, (void*)h->d_tpart,
                   (void*)h->d_p_off, (void*)h->d_X2mats, (void*)h->d_g2, (void*)h->d_ys2, (void*)h->d_A2mats,
-                  (void*)h->d_p_off32, (void*)h->d_tpart32, (void*)h->d_adone})
+                  (void*)h->d_p_off32, (void*)h->d_tpart32, (void*)h->d_adone, (void*)h->d_sr_chunks,
+                  (void*)h->d_sr_order, (void*)h->d_sr_ckptr, (void*)h->d_sr_part})
     dfree(h, p);
   h->d_adone = nullptr;
+  h->d_sr_chunks = nullptr; h->d_sr_order = nullptr; h->d_sr_ckptr = nullptr; h->d_sr_part = nullptr;
+  h->sr_nchunks = 0;
   h->d_mats = nullptr; h->d_Amats = nullptr; h->d_Xmats = nullptr; h->d_X2mats = nullptr; h->d_A2mats = nullptr;
   for (void* p : h->gram_allocs) dfree(h, p);
   h->gram_allocs.clear();
@@ -1435,6 +1482,11 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     CK(dalloc(h, (void**)&h->d_adone, sizeof(int) * (size_t)J));
     CK(cudaMemsetAsync(h->d_adone, 0, sizeof(int) * (size_t)J, h->st));
   }
+  h->set_n.resize(J);
+  for (int i = 0; i < J; ++i) h->set_n[i] = mats[i].n;
+  // default Schwarz apply: the streaming kernel for sets of 2048 unknowns and more (long rows), the
+  // fused 32-row kernel below; rann_dd_tune_apply times them all
+  TRY(set_apply_config(h, streaming_ok(h) && h->maxn >= 2048 ? 2 : 0));
   // incidence lists for the combine step: sets containing each subdomain, with its block offset
   std::vector<int> inc_ptr(1, 0), inc_set, inc_pos;
   for (int k = 0; k < J; ++k) {
@@ -1486,6 +1538,14 @@ static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, boo
     KLA(h, K_TRMV_U_DF, 2, 4.0 * (h->sum_n2 + h->sum_n) + 16.0 * h->sum_n, h->sum_n2 + h->sum_n,
         launch_trmv_upper_df(h->d_mats, h->nsets, h->maxn, h->d_s_off, h->d_p_off, h->d_ys2, h->d_tpart, h->d_s,
                              h->st));
+  } else if (fast && h->sr_nchunks > 0) {
+    // s_i = X_i^T X_i R_i r, the rows of X_i = L_i^{-1} streamed through shared memory once
+    KLA(h, K_SCHWARZ_DF, 1, 4.0 * (h->sum_n2 + h->sum_n) + 8.0 * h->sum_n + 8.0 * h->dof,
+        2.0 * (h->sum_n2 + h->sum_n),
+        launch_schwarz_apply_rows_df(h->d_mats, h->d_sr_chunks, h->d_sr_order, h->sr_nchunks, h->d_sr_ckptr,
+                                     h->d_set_ptr, h->d_set_sub, h->d_sub, r, r2, wkind, h->d_inc_ptr, h->d_sr_part,
+                                     h->d_s_off, h->d_s, h->d_adone, ckind, z, h->d_ozerr, h->st));
+    if (ckind == RANN_PREC_RAS) return RANN_OK;                // the restricted combine ran in the apply
   } else if (fast) {
     // s_i = X_i^T X_i R_i r with X_i = L_i^{-1} read from HBM once (fused, with the gather)
     KLA(h, K_SCHWARZ_DF, 1, 4.0 * (h->sum_n2 + h->sum_n) + 8.0 * h->sum_n + 8.0 * h->dof,
@@ -1509,6 +1569,78 @@ static rann_status prec_apply(rann_dd_handle* h, const double* r, double* z, boo
   return RANN_OK;
 }
 
+extern "C" rann_status rann_dd_set_apply_config(rann_dd_handle* h, int cfg) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "set_apply_config before setup_precond");
+  return set_apply_config(h, cfg);
+}
+
+extern "C" rann_status rann_dd_get_apply_config(rann_dd_handle* h, int* cfg) {
+  REQUIRE(h && cfg, RANN_EINVAL, "null argument");
+  *cfg = h->apply_cfg;
+  return RANN_OK;
+}
+
+extern "C" rann_status rann_dd_tune_apply(rann_dd_handle* h, int reps, int* best_out, float* ms_out) {
+  REQUIRE(h && best_out, RANN_EINVAL, "null argument");
+  REQUIRE(h->prec_kind >= 0, RANN_EORDER, "tune_apply before setup_precond");
+  REQUIRE(reps >= 1 && reps <= 100, RANN_EINVAL, "reps must be in 1..100");
+  const int64_t n = std::max<int64_t>(h->dof, 1);
+  double *r = nullptr, *z = nullptr;
+  CK(dalloc(h, (void**)&r, sizeof(double) * (size_t)n));
+  CK(dalloc(h, (void**)&z, sizeof(double) * (size_t)n));
+  {
+    std::vector<double> ones((size_t)n, 1.0);
+    CK(cudaMemcpyAsync(r, ones.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->st));
+    CK(stream_sync(h));
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool fused_ok = h->prec_df && h->max_set_size <= schwarz_apply_max_subs();
+  int best = h->apply_cfg;
+  float best_ms = -1.f;
+  rann_status st = RANN_OK;
+  for (int cfg = 0; cfg < RANN_APPLY_NCFG && st == RANN_OK; ++cfg) {
+    if (ms_out) ms_out[cfg] = -1.f;
+    if (cfg == 0 ? !fused_ok : !streaming_ok(h)) continue;
+    if ((st = set_apply_config(h, cfg)) != RANN_OK) break;
+    if ((st = prec_apply(h, r, z, h->prec_df)) != RANN_OK) break;
+    cudaEventRecord(e0, h->st);
+    for (int k = 0; k < reps && st == RANN_OK; ++k) st = prec_apply(h, r, z, h->prec_df);
+    cudaEventRecord(e1, h->st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = RANN_ECUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)reps;
+    if (ms_out) ms_out[cfg] = ms;
+    if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = cfg; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dfree(h, r);
+  dfree(h, z);
+  TRY(st);
+  TRY(set_apply_config(h, best));
+  CK(stream_sync(h));
+  *best_out = best;
+  return RANN_OK;
+}
+
+cudaStream_t rann_handle_stream(const rann_dd_handle* h) { return h->st; }
+int rann_handle_dim(const rann_dd_handle* h) { return h->dim; }
+int rann_handle_maxn(const rann_dd_handle* h) { return h->prec_kind >= 0 ? h->maxn : 0; }
+bool rann_handle_piecewise(const rann_dd_handle* h) {
+  return h->P.op == RANN_OP_DIFFUSION && h->P.coef == RANN_COEF_PIECEWISE;
+}
+
+extern "C" rann_status rann_dd_set_stream(rann_dd_handle* h, void* stream) {
+  REQUIRE(h, RANN_EINVAL, "null handle");
+  CK(stream_sync(h));
+  h->st = (cudaStream_t)stream;
+  return RANN_OK;
+}
+
 extern "C" rann_status rann_dd_precond_apply(rann_dd_handle* h, const double* r_dev, double* z_dev) {
   REQUIRE(h && r_dev && z_dev, RANN_EINVAL, "null argument");
   REQUIRE(h->prec_kind >= 0, RANN_EORDER, "precond_apply before setup_precond");
@@ -1517,6 +1649,23 @@ extern "C" rann_status rann_dd_precond_apply(rann_dd_handle* h, const double* r_
 }
 
 // -------------------------------------------------------------- solves --
+
+// After a solve: an expired bounded wait of the streaming Schwarz apply left
+// its error word set (the apply then skipped its arithmetic); report it as
+// RANN_TIMEOUT and clear the word, so the handle stays usable.
+static rann_status solve_done(rann_dd_handle* h, rann_status st) {
+  if (!h || !h->d_ozerr) return st;
+  int w = 0;
+  if (cudaMemcpyAsync(&w, h->d_ozerr, sizeof(int), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+      stream_sync(h) != cudaSuccess)
+    return st;
+  if (w) {
+    cudaMemsetAsync(h->d_ozerr, 0, sizeof(int), h->st);
+    rann_set_error("Schwarz apply: bounded pipeline wait %d gave up", w);
+    return RANN_TIMEOUT;
+  }
+  return st;
+}
 
 static rann_status dot_host(rann_dd_handle* h, const double* x, const double* y, int64_t n, double* out) {
   KLA(h, K_DOT, 1, 16.0 * n, 2.0 * n, launch_multidot(x, 0, 1, y, n, h->d_red, h->d_scal, h->st));
@@ -1831,12 +1980,12 @@ static rann_status solve_variant_impl(rann_dd_handle* h, const double* F_dev, do
 
 extern "C" rann_status rann_dd_solve_cgs(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
                                          int maxit, rann_dd_stats* stats) {
-  return solve_variant_impl(h, F_dev, W_dev, rtol, maxit, stats, false);
+  return solve_done(h, solve_variant_impl(h, F_dev, W_dev, rtol, maxit, stats, false));
 }
 
 extern "C" rann_status rann_dd_solve_bicg(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
                                           int maxit, rann_dd_stats* stats) {
-  return solve_variant_impl(h, F_dev, W_dev, rtol, maxit, stats, true);
+  return solve_done(h, solve_variant_impl(h, F_dev, W_dev, rtol, maxit, stats, true));
 }
 
 extern "C" rann_status rann_dd_precond_apply_t(rann_dd_handle* h, const double* r_dev, double* z_dev) {
@@ -2013,7 +2162,7 @@ static rann_status solve_gmres_impl(rann_dd_handle* h, const double* F_dev, cons
 extern "C" rann_status rann_dd_solve_cg_as(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
                                            int maxit, rann_dd_stats* stats) {
   REQUIRE(F_dev, RANN_EINVAL, "null F");
-  return solve_cg_impl(h, F_dev, nullptr, W_dev, rtol, maxit, stats);
+  return solve_done(h, solve_cg_impl(h, F_dev, nullptr, W_dev, rtol, maxit, stats));
 }
 
 // ------------------------------------------------ many right-hand sides --
@@ -2028,7 +2177,8 @@ static bool multi_batched(rann_dd_handle* h) {
 // Z_c = M^{-1} R_c for c < nr (vectors [nr][DoF]); each column equals prec_apply's.
 static rann_status prec_apply_multi(rann_dd_handle* h, const double* R, double* Z, int nr, Workspace& ws) {
   const int64_t n = h->dof;
-  if (!multi_batched(h)) {
+  // the streaming apply serves one column at a time (each column bit for bit the one-vector apply)
+  if (!multi_batched(h) || h->sr_nchunks > 0) {
     for (int c = 0; c < nr; ++c) TRY(prec_apply(h, R + c * n, Z + c * n, h->prec_df));
     return RANN_OK;
   }
@@ -2204,19 +2354,20 @@ static rann_status solve_cg_multi_impl(rann_dd_handle* h, const double* F_dev, d
 
 extern "C" rann_status rann_dd_solve_cg_as_multi(rann_dd_handle* h, const double* F_dev, double* W_dev, int nrhs,
                                                  double rtol, int maxit, rann_dd_stats* stats) {
-  return solve_cg_multi_impl(h, F_dev, W_dev, nrhs, rtol, maxit, stats);
+  return solve_done(h, solve_cg_multi_impl(h, F_dev, W_dev, nrhs, rtol, maxit, stats));
 }
 
 extern "C" rann_status rann_dd_solve_gmres_ras(rann_dd_handle* h, const double* F_dev, double* W_dev, double rtol,
                                                int restart, int maxit, rann_dd_stats* stats) {
   REQUIRE(F_dev, RANN_EINVAL, "null F");
-  return solve_gmres_impl(h, F_dev, nullptr, W_dev, rtol, restart, maxit, stats);
+  return solve_done(h, solve_gmres_impl(h, F_dev, nullptr, W_dev, rtol, restart, maxit, stats));
 }
 
 // Left-preconditioned GMRES(k) for nr right-hand sides in lockstep: each
 // Arnoldi step applies the block-row operator and the Schwarz preconditioner
-// to every column's current basis vector in one launch each (block rows and
-// factor rows read once per step for up to four columns); the Gram-Schmidt
+// to every column's current basis vector (block rows read once per step for
+// up to four columns; the factors by the streaming apply once per column, by
+// the fused apply once per four columns); the Gram-Schmidt
 // passes, the Givens bookkeeping (own device state and done flag per column),
 // the restarts and the float64 residual decisions are per column with the
 // arithmetic of solve_gmres_impl, so every column equals the one-column
@@ -2421,7 +2572,7 @@ static rann_status solve_gmres_multi_impl(rann_dd_handle* h, const double* F_dev
 
 extern "C" rann_status rann_dd_solve_gmres_ras_multi(rann_dd_handle* h, const double* F_dev, double* W_dev, int nrhs,
                                                      double rtol, int restart, int maxit, rann_dd_stats* stats) {
-  return solve_gmres_multi_impl(h, F_dev, W_dev, nrhs, rtol, restart, maxit, stats);
+  return solve_done(h, solve_gmres_multi_impl(h, F_dev, W_dev, nrhs, rtol, restart, maxit, stats));
 }
 
 // Adjoint of the least-squares solve.  W = (H^T H)^{-1} H^T F, so for a loss
@@ -2433,8 +2584,8 @@ extern "C" rann_status rann_dd_solve_backward(rann_dd_handle* h, const double* g
   REQUIRE(h && gW_dev && lam_dev, RANN_EINVAL, "null argument");
   REQUIRE(h->prec_kind >= 0, RANN_EORDER, "solve_backward before setup_precond");
   if (h->prec_kind == RANN_PREC_AS || h->prec_kind == RANN_PREC_NONE)
-    return solve_cg_impl(h, nullptr, gW_dev, lam_dev, rtol, maxit, stats);
-  return solve_gmres_impl(h, nullptr, gW_dev, lam_dev, rtol, 50, maxit, stats);
+    return solve_done(h, solve_cg_impl(h, nullptr, gW_dev, lam_dev, rtol, maxit, stats));
+  return solve_done(h, solve_gmres_impl(h, nullptr, gW_dev, lam_dev, rtol, 50, maxit, stats));
 }
 
 // dl/dc0 of a loss l(W) through the least-squares solve, for -Lap u + c0 u

@@ -475,8 +475,8 @@ cudaError_t launch_assemble(const ProbDev& P, const SubDev* d_sub, const int* d_
   if (ntiles == 0) return cudaSuccess;
   size_t smem = sizeof(double) * ((size_t)TR * (3 + P.dim) + (size_t)TR * P.dim + (size_t)P.m * (P.dim + 2));
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static const cudaError_t lim = smem_limit_max(assemble_kernel);
+    if (lim != cudaSuccess) return lim;
   }
   assemble_kernel<<<ntiles, NT, smem, st>>>(P, d_sub, d_tiles, d_R, d_b, d_Psi, d_H);
   return cudaGetLastError();

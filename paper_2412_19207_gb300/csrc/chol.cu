@@ -1370,9 +1370,8 @@ static cudaError_t apply_multi_launch(const CholMat* d_mats, int nsets, int maxn
                                       const int64_t* d_p_off32, double* d_part, int64_t pstride,
                                       const int64_t* d_s_off, double* d_s, int64_t lds, int* d_done, cudaStream_t st) {
   const int smem = (int)(sizeof(float4) * (size_t)((maxn + 1) / 2) * NR);
-  cudaError_t e = cudaFuncSetAttribute(schwarz_apply_multi_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem);
-  if (e != cudaSuccess) return e;
+  static const cudaError_t lim = smem_limit_max(schwarz_apply_multi_kernel<NR>);
+  if (lim != cudaSuccess) return lim;
   schwarz_apply_multi_kernel<NR><<<dim3((maxn + AR - 1) / AR, nsets), ANT, smem, st>>>(
       d_mats, d_set_ptr, d_set_sub, d_sub, d_r, ldr, d_p_off32, d_part, pstride, d_s_off, d_s, lds, d_done);
   return cudaGetLastError();
@@ -1414,8 +1413,8 @@ cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, 
                                     cudaStream_t st, const float2* d_r2) {
   if (nsets == 0) return cudaSuccess;
   const int smem = (int)(sizeof(float4) * (size_t)((maxn + 1) / 2));
-  cudaError_t e = cudaFuncSetAttribute(schwarz_apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  static const cudaError_t lim = smem_limit_max(schwarz_apply_df_kernel);
+  if (lim != cudaSuccess) return lim;
   schwarz_apply_df_kernel<<<dim3((maxn + AR - 1) / AR, nsets), ANT, smem, st>>>(
       d_mats, d_set_ptr, d_set_sub, d_sub, d_r, d_p_off32, d_part, wkind, d_inc_ptr, d_s_off, d_s, d_done, ckind, d_z,
       wkind == RANN_PREC_AS ? d_r2 : nullptr);

@@ -45,8 +45,29 @@ struct SubDev {
 };
 
 
+// Lifts a kernel's dynamic shared-memory limit to the most this device allows
+// (once per kernel, from a function-local static in the launcher).  The limit
+// is a per-kernel setting shared by every host thread: setting it per launch
+// to the launch's own size would race with concurrent launches of larger
+// sizes from other threads (handles driven in parallel by a batch).
+template <typename K>
+inline cudaError_t smem_limit_max(K kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes a{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+  return e;
+}
+
 // Host-side helpers (api.cu).
 void rann_set_error(const char* fmt, ...);
+cudaStream_t rann_handle_stream(const rann_dd_handle* h);
+int rann_handle_dim(const rann_dd_handle* h);
+int rann_handle_maxn(const rann_dd_handle* h);        // largest extended set after setup_precond (else 0)
+bool rann_handle_piecewise(const rann_dd_handle* h);  // RANN_COEF_PIECEWISE diffusion
 
 static inline double host_mu(int layout, int k, int l) {
   return layout == RANN_LAYOUT_PAPER ? (double)k / (double)(l - 1) : ((double)k + 0.5) / (double)l;
@@ -250,3 +271,19 @@ struct CholMat {
   int n;
   int ld;
 };
+
+// apply.cu -- streaming double-float Schwarz apply (rows of X_i = L_i^{-1} read once)
+struct SrChunk {             // consecutive rows [r0, r1) of set `set`, its k-th chunk, in nst stages
+  int set, r0, r1, k, nst;
+  int64_t poff;              // offset of the chunk's column sums (n_set doubles)
+};
+int schwarz_rows_nmax();
+int schwarz_rows_stage();
+void schwarz_rows_plan(const std::vector<int>& nvec, int64_t target, std::vector<SrChunk>& chunks,
+                       std::vector<int>& ck_ptr, std::vector<int>& order, int64_t& part_total);
+cudaError_t launch_schwarz_apply_rows_df(const CholMat* d_mats, const SrChunk* d_chunks, const int* d_order,
+                                         int nchunks, const int* d_ck_ptr, const int* d_set_ptr,
+                                         const int* d_set_sub, const SubDev* d_sub, const double* d_r,
+                                         const float2* d_r2, int wkind, const int* d_inc_ptr, double* d_part,
+                                         const int64_t* d_s_off, double* d_s, int* d_done, int ckind, double* d_z,
+                                         int* d_err, cudaStream_t st);

@@ -35,6 +35,18 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float2 a, float2 x)
   sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e, e2), __fmaf_rn(a.x, x.y, __fmul_rn(a.y, x.x))));
 }
 
+// (sh, sl) += a * x with the low-order terms added by FMAs straight into sl:
+// the same terms as df_mac (exact product error, exact two-sum error, the two
+// cross products), 12 float32 instructions instead of 13.
+__device__ __forceinline__ void df_mac_f(float& sh, float& sl, float2 a, float2 x) {
+  const float p = __fmul_rn(a.x, x.x);
+  const float e = __fmaf_rn(a.x, x.x, -p);
+  float t, e2;
+  df_two_sum(sh, p, t, e2);
+  sh = t;
+  sl = __fmaf_rn(a.x, x.y, __fmaf_rn(a.y, x.x, __fadd_rn(sl, __fadd_rn(e, e2))));
+}
+
 // Fold the low part into the high part (fast two-sum, |sh| >= |sl| not required
 // for the exactness of the sum, only for normalisation).
 __device__ __forceinline__ void df_renorm(float& sh, float& sl) {

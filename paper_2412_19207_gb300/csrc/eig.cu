@@ -334,7 +334,8 @@ cudaError_t launch_tridiag(double* A, int m, int batch, double* work, int64_t ws
     use_dp = 0;
     smem = (int)(sizeof(double) * (size_t)(4 + NW) * m);
   }
-  cudaError_t e = cudaFuncSetAttribute(syev_tridiag_kernel<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  static const cudaError_t lim = smem_limit_max(syev_tridiag_kernel<SL>);
+  cudaError_t e = lim;
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(batch * TC);
@@ -902,9 +903,8 @@ cudaError_t launch_syev_phase(const SyevBatch& b, int phase, cudaStream_t st) {
         const int64_t total = (int64_t)b.batch * m;
         const int nmat = std::min(b.batch, bisect_mats_per_block(m));
         const int smem = (int)(sizeof(double) * 4 * (size_t)m * nmat);
-        if ((e = cudaFuncSetAttribute(syev_bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
-            cudaSuccess)
-          return e;
+        static const cudaError_t lim = smem_limit_max(syev_bisect_kernel);
+        if ((e = lim) != cudaSuccess) return e;
         syev_bisect_kernel<<<(unsigned)((total + BT - 1) / BT), BT, smem, st>>>(m, b.batch, b.work, ws, b.w, b.info);
       } else {
         const int smem = (int)(sizeof(double) * 2 * m);

@@ -184,8 +184,8 @@ cudaError_t launch_gram_matvec(const GramRows& g, int J, const int* d_rtile, int
                                const double* d_x, double* d_z, cudaStream_t st, const float2* d_x2, float2* d_z2) {
   if (J == 0) return cudaSuccess;
   const int smem = (int)(sizeof(float2) * (size_t)maxn2);
-  cudaError_t e = cudaFuncSetAttribute(gram_rowdot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  static const cudaError_t lim = smem_limit_max(gram_rowdot_kernel);
+  if (lim != cudaSuccess) return lim;
   gram_rowdot_kernel<<<nrtile, 32 * GRAM_TILE_ROWS, smem, st>>>(g, d_rtile, d_x, d_x2, d_z, d_z2);
   return cudaGetLastError();
 }
@@ -194,8 +194,8 @@ template <int NR>
 static cudaError_t gram_multi_launch(const GramRows& g, const int* d_rtile, int nrtile, int maxn2, const double* d_x,
                                      int64_t ldx, double* d_z, int64_t ldz, cudaStream_t st) {
   const int smem = (int)(sizeof(float2) * (size_t)maxn2 * NR);
-  cudaError_t e = cudaFuncSetAttribute(gram_rowdot_multi_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  static const cudaError_t lim = smem_limit_max(gram_rowdot_multi_kernel<NR>);
+  if (lim != cudaSuccess) return lim;
   gram_rowdot_multi_kernel<NR><<<nrtile, 32 * GRAM_TILE_ROWS, smem, st>>>(g, d_rtile, d_x, ldx, d_z, ldz);
   return cudaGetLastError();
 }

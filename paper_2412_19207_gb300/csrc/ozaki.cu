@@ -531,8 +531,8 @@ cudaError_t launch_oz_split(const OzSplitTask* d_tasks, int ntasks, int maxM, in
 cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, const OzMap* d_maps, int* d_err, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
   if (reinterpret_cast<uintptr_t>(d_maps) & 63) return cudaErrorInvalidValue;   // tensor maps: 64-byte aligned
-  cudaError_t e = cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
-  if (e != cudaSuccess) return e;
+  static const cudaError_t lim = smem_limit_max(oz_gemm_tc_kernel);
+  if (lim != cudaSuccess) return lim;
   oz_gemm_tc_kernel<<<ntiles, OZ_THREADS, OZ_SMEM, st>>>(d_tasks, d_maps, d_err);
   return cudaGetLastError();
 }
@@ -541,8 +541,8 @@ cudaError_t launch_oz_gemm_groups(const OzGroup* d_groups, int ngroups, int ntil
                                   cudaStream_t st) {
   if (ntiles == 0 || ngroups == 0) return cudaSuccess;
   if (reinterpret_cast<uintptr_t>(d_maps) & 63) return cudaErrorInvalidValue;   // tensor maps: 64-byte aligned
-  cudaError_t e = cudaFuncSetAttribute(oz_gemm_grp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
-  if (e != cudaSuccess) return e;
+  static const cudaError_t lim = smem_limit_max(oz_gemm_grp_kernel);
+  if (lim != cudaSuccess) return lim;
   oz_gemm_grp_kernel<<<ntiles, OZ_THREADS, OZ_SMEM, st>>>(d_groups, ngroups, d_maps, d_err);
   return cudaGetLastError();
 }

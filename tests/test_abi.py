@@ -52,14 +52,13 @@ def test_binding_covers_the_header():
 
 def test_struct_layouts_match_the_c_compiler():
     import paper_2412_19207_gb300 as g
-    fields_d = [f for f, _ in g.Desc._fields_]
-    fields_s = [f for f, _ in g.Stats._fields_]
+    structs = [("rann_dd_desc", g.Desc), ("rann_dd_stats", g.Stats), ("rann_dd_pipeline", g.Pipeline),
+               ("rann_dd_pipeline_out", g.PipelineOut)]
     prog = ['#include <stdio.h>', '#include <stddef.h>', '#include "rann_dd.h"', "int main(void){"]
-    prog.append('printf("%zu %zu\\n", sizeof(rann_dd_desc), sizeof(rann_dd_stats));')
-    for f in fields_d:
-        prog.append(f'printf("%zu\\n", offsetof(rann_dd_desc, {f}));')
-    for f in fields_s:
-        prog.append(f'printf("%zu\\n", offsetof(rann_dd_stats, {f}));')
+    for cname, py in structs:
+        prog.append(f'printf("%zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            prog.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
     prog.append("return 0;}")
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "l.c")
@@ -67,10 +66,11 @@ def test_struct_layouts_match_the_c_compiler():
         exe = os.path.join(d, "l")
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
-    assert vals[0] == ctypes.sizeof(g.Desc) and vals[1] == ctypes.sizeof(g.Stats)
-    offs = vals[2:]
-    assert offs[: len(fields_d)] == [getattr(g.Desc, f).offset for f in fields_d]
-    assert offs[len(fields_d):] == [getattr(g.Stats, f).offset for f in fields_s]
+    want = []
+    for _, py in structs:
+        want.append(ctypes.sizeof(py))
+        want += [getattr(py, f).offset for f, _ in py._fields_]
+    assert vals == want
 
 
 @pytest.mark.parametrize("field,value", [("dim", 4), ("neurons", 0), ("neurons", 2000), ("rho", 0.0),

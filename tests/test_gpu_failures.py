@@ -109,6 +109,14 @@ def test_expired_pipeline_wait_is_a_timeout(g):
     s.setup_precond("as")
     W, st = s.solve_cg_as(F)
     assert st["status"] == "RANN_OK"
+    # the streaming Schwarz apply's waits report through the same word at the end of a solve
+    s.inject_fault(g.FAULT_WAIT_EXPIRED, 7)
+    with pytest.raises(g.RannError) as e:
+        s.solve_cg_as(F)
+    assert e.value.status == g.TIMEOUT
+    W2, st = s.solve_cg_as(F)
+    assert st["status"] == "RANN_OK"
+    assert torch.equal(W, W2)
 
 
 def test_allocation_cap_is_out_of_memory(g):

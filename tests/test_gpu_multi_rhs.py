@@ -2,8 +2,9 @@
 the batching over subdomains): every column of the multi-RHS Schwarz apply and
 of the lockstep AS-preconditioned CG equals the one-column routine bit for bit
 (the batched kernels keep the one-column arithmetic per column, reading the
-local factors and the block rows of H^T H once per step for up to four
-columns).  Edge cases: one column, a column count that is not a multiple of
+block rows of H^T H once per step for up to four columns; the local factors
+are read once per column by the streaming Schwarz apply, and once per four
+columns where a set is too large for it).  Edge cases: one column, a column count that is not a multiple of
 the four-column launch group, a zero right-hand side, columns converging at
 different steps, and the float64 factors of precision mode 0 (handled column
 by column).
