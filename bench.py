@@ -53,15 +53,18 @@ CSRC = os.path.join(ROOT, "paper_2412_19207_gb300", "csrc")
 # profiles/ summary states), valid only for the kernel source it was taken
 # on: (bytes, file, kernel, sha256 prefix of the kernel's source text).  A
 # changed kernel reports null.
-TRAFFIC = {}
+TRAFFIC = {"schwarz_apply_df32": (17894.3e6, "apply.cu", "schwarz_apply_rows_df_kernel", "d079c76b8aa4")}
 # families whose profiled bracket spans a multi-stream pipeline of many kernels
 # (the Cholesky with lookahead and the row-block inverse): no single launch
 # duration, so they are reported as pipelines, not as the roofline kernel
 PIPELINED = {"cholesky", "cholesky_tc"}
 
 
+SMALL = False          # --small: the headline problem on 3 x 3 x 2 subdomains (12 x 12 x 6 points each), for profiling
+
+
 def headline_workload():
-    p = ri.config("heat3d")
+    p = ri.heat3d(sub=(3, 3, 2), pts=(12, 12, 6), neurons=400) if SMALL else ri.config("heat3d")
     p.solver, p.precond = "cg_as", "as"
     return p
 
@@ -201,14 +204,15 @@ def roofline(prof, pk):
         note = "measured cuBLAS bf16, sustained (MEASURED_PEAKS.json); flops of the digit-slice products"
     elif bound == "alu_df32":
         ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
-        peak, unit = DF32_PEAK_TFLOPS, "TFLOP/s"
-        note = ("double-float multiply-add: 152 SMs x 128 float32 lanes x 2.07 GHz / 12 float32 "
-                "instructions x 2 flops (unit counts x max clock), float64-equivalent flops")
+        peak, unit = pk["df32_tflops"], "TFLOP/s"
+        note = ("double-float multiply-add rate measured by rann_dd_device_rates (float64-equivalent flops)"
+                if pk.get("rates_measured") else "double-float multiply-add: unit counts x max clock / 12 instructions")
         bound = "alu"
     else:
         ach = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
-        peak, unit = FP64_PEAK_TFLOPS, "TFLOP/s"
-        note = "float64 FMA: 152 SMs x 2 FMA/clk x 2.07 GHz (unit counts x max clock)"
+        peak, unit = pk["fp64_tflops"], "TFLOP/s"
+        note = ("float64 FMA rate measured by rann_dd_device_rates" if pk.get("rates_measured")
+                else "float64 FMA: 152 SMs x 2 FMA/clk x 2.07 GHz (unit counts x max clock)")
     tr = traffic_of(dom_name)
     return {"kernel": dom_name, "bound": bound, "achieved": round(ach, 3), "peak": peak, "unit": unit,
             "frac": round(ach / peak, 4), "traffic": (tr if tr is None else round(tr)),
@@ -229,7 +233,7 @@ def pipeline_entry(f, pk):
                 "peak_tflops": peak, "frac_of_bf16_sustained": round(ach / peak, 4),
                 "flops": "digit-slice products (36 per float64-accurate product)"}
     return {"ms_per_step": round(f["ms"], 3), "launches_per_step": f["launches"], "achieved_tflops": round(ach, 3),
-            "frac_of_df32_peak": round(ach / DF32_PEAK_TFLOPS, 4)}
+            "frac_of_df32_rate": round(ach / pk["df32_tflops"], 4)}
 
 
 def bandwidths(prof, pk):
@@ -342,6 +346,11 @@ def bench_ours(args, rank, world):
         s2.close()
         del s2, F2, W2
     pk = peaks()
+    try:                                  # measured double-float and float64 rates of this GPU
+        pk["df32_tflops"], pk["fp64_tflops"] = g.device_rates()
+        pk["rates_measured"] = True
+    except Exception:
+        pk["df32_tflops"], pk["fp64_tflops"], pk["rates_measured"] = DF32_PEAK_TFLOPS, FP64_PEAK_TFLOPS, False
     launches = sum(v["launches"] for v in prof.values())
     kernels = {k: {"ms_per_step": round(v["ms"], 3), "launches_per_step": v["launches"]}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]}
@@ -359,6 +368,8 @@ def bench_ours(args, rank, world):
         "roofline": roofline(prof, pk),
         "matvec": bandwidths(prof, pk),
         "pipelines": {k: pipeline_entry(prof[k], pk) for k in sorted(PIPELINED) if prof.get(k, {}).get("ms")},
+        "device_rates": {"df32_tflops": round(pk["df32_tflops"], 2), "fp64_tflops": round(pk["fp64_tflops"], 3),
+                         "measured": pk["rates_measured"]},
         "kernels": kernels,
         "gpu_launches": int(launches) * args.steps,
         "gpu_launches_per_step": int(launches),
@@ -604,10 +615,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multiscale", action="store_true", help="skip the multiscale precision-mode arms")
     ap.add_argument("--no-batch", action="store_true", help="skip the piecewise-coefficient differentiable batch")
+    ap.add_argument("--small", action="store_true",
+                    help="headline problem on 3x3x2 subdomains with 12x12x6 points (a few GB, for ncu captures)")
     ap.add_argument("--multi-rhs", type=int, default=0,
                     help="also time AS-CG and the workload's GMRES on this many right-hand sides in lockstep "
                          "against one at a time (multiscale workload)")
     args = ap.parse_args()
+    if args.small:
+        global SMALL, WORKLOAD_DESC
+        SMALL = True
+        WORKLOAD_DESC = ("heat3d (space-time heat u_t = 0.1 Lap u) 3x3x2 subdomains, m=400, 12x12x6 pts/subdomain "
+                         "(profiling case), overlap ratio 1.4, PCA 1-1e-12, AS-CG on the normal equations, rtol 1e-10")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.warmup < 3:

@@ -448,6 +448,13 @@ rann_status rann_dd_batch_run(rann_dd_batch* b, int n, rann_dd_handle* const* hs
                               double* const* grad_F_dev, double* const* grad_coef_host, rann_dd_pipeline_out* out);
 
 
+/* Measured device rates for roofline denominators (TFLOP/s, 2 flops per
+ * multiply-add): df32_tflops, the double-float multiply-add of the Schwarz
+ * apply and the inner operator on the float32 pipe; fp64_tflops, float64
+ * FMAs.  Each is a timed loop of independent chains on every SM (legacy
+ * default stream, synchronises).  Either pointer may be NULL. */
+rann_status rann_dd_device_rates(double* df32_tflops, double* fp64_tflops);
+
 /* Host-side fault injection for failure-detection tests (the paper has no
  * counterpart; no device code is made to fault, trap or hang):
  *   RANN_FAULT_WAIT_EXPIRED: writes `value` (non-zero) into the handle's

@@ -126,6 +126,7 @@ SIGNATURES = {
     "rann_dd_profile_get": (_I, [_P, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_L),
                                  ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "rann_dd_inject_fault": (_I, [_P, _I, _L]),
+    "rann_dd_device_rates": (_I, [ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "rann_dd_set_apply_config": (_I, [_P, _I]),
     "rann_dd_get_apply_config": (_I, [_P, ctypes.POINTER(_I)]),
     "rann_dd_tune_apply": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
@@ -584,6 +585,14 @@ class GridEval:
                 return solver.eval_grid_t(gu.contiguous())
 
         return _Fn.apply(W)
+
+
+def device_rates():
+    """Measured (df32, fp64) TFLOP/s of this device (rann_dd_device_rates)."""
+    lib = load_library()
+    a, b = _D(), _D()
+    _check(lib.rann_dd_device_rates(ctypes.byref(a), ctypes.byref(b)), "rann_dd_device_rates")
+    return a.value, b.value
 
 
 APPLY_NCFG = 4

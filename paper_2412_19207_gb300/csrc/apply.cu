@@ -30,12 +30,14 @@ namespace {
 
 constexpr int SR_C = 512;                       // consumer threads
 constexpr int SR_W = SR_C / 32;
-constexpr int SR_WP = SR_W <= 16 ? 16 : 32;     // SR_W rounded up to a power of two
+constexpr int SR_G = 2;                         // consumer groups, taking the stages in turn
+constexpr int SR_GC = SR_C / SR_G;              // threads of a group
+constexpr int SR_GW = SR_W / SR_G;              // warps of a group
 constexpr int SR_T = SR_C + 32;                 // and one producer warp
-constexpr int SR_PPT = 6;                       // column pairs per thread in the column-sum pass
-constexpr int SR_NMAX = 2 * SR_C * SR_PPT;      // longest row (6144 columns)
-constexpr int SR_STAGE = 10752;                 // double-float entries per stage (84 KB)
-constexpr int SR_NST = 2;                       // stages in the ring
+constexpr int SR_PPT = 12;                      // column pairs per thread in the column-sum pass
+constexpr int SR_NMAX = 2 * SR_GC * SR_PPT;     // longest row (6144 columns)
+constexpr int SR_STAGE = 7168;                  // double-float entries per stage (56 KB)
+constexpr int SR_NST = 3;                       // stages in the ring
 constexpr int SR_MAXROWS = 32;                  // rows per stage
 constexpr int SR_MAXSUB = 27;                   // subdomains per extended set (3^3)
 constexpr int SR_ERR_WAIT = 0x5A00;             // error word: a stage wait gave up
@@ -53,16 +55,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-// barrier over the consumer warps only (named barrier `id`, SR_C threads)
-__device__ __forceinline__ void consumers_sync(int id) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "n"(SR_C) : "memory");
+// barrier over `n` consumer threads (named barrier `id`)
+__device__ __forceinline__ void consumers_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
 }
-// the same barrier, returning whether v holds in every consumer thread
-__device__ __forceinline__ bool consumers_all(int id, bool v) {
+// the same barrier, returning whether v holds in every participating thread
+__device__ __forceinline__ bool consumers_all(int id, int n, bool v) {
   int r;
   asm volatile(
       "{\n .reg .pred p, q;\n setp.ne.s32 q, %1, 0;\n bar.red.and.pred p, %2, %3, q;\n selp.s32 %0, 1, 0, p;\n}\n"
-      : "=r"(r) : "r"((int)v), "r"(id), "n"(SR_C) : "memory");
+      : "=r"(r) : "r"((int)v), "r"(id), "r"(n) : "memory");
   return r != 0;
 }
 
@@ -85,8 +87,8 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
   extern __shared__ __align__(128) float4 sr_buf[];   // g_i (SR_NMAX entries), then SR_NST stages
   __shared__ __align__(8) uint64_t full[SR_NST], empty[SR_NST];
   __shared__ SrPlan plan[SR_NST];
-  __shared__ float2 wp[SR_MAXROWS][SR_W];             // per row: the warps' sums of their pieces
-  __shared__ float2 ysm[SR_MAXROWS];                  // y_r of the stage's rows
+  __shared__ float2 wp[SR_G][SR_MAXROWS][SR_GW];      // per group and row: the warps' sums of their pieces
+  __shared__ float2 ysm[SR_G][SR_MAXROWS];            // y_r of the group's current stage
   __shared__ int seg_c[SR_MAXSUB + 1], seg_p[SR_MAXSUB];
   __shared__ int64_t seg_w[SR_MAXSUB];
   __shared__ double seg_d[SR_MAXSUB];
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
     issued = 0;
     for (int st = 0; st < SR_NST; ++st) {
       mbar_init(smem_u32(&full[st]), 1);
-      mbar_init(smem_u32(&empty[st]), SR_W);
+      mbar_init(smem_u32(&empty[st]), SR_GW);
     }
     mbar_fence_init();
   }
@@ -125,13 +127,16 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
   }
   __syncthreads();
 
-  // phase-2 teams: GS threads own the column pairs c2 = lt + GS k (k < SR_PPT)
+  // consumer group grp takes stages grp, grp + SR_G, ...; in the column-sum pass its
+  // teams of GS threads own the column pairs c2 = lt + GS k (k < SR_PPT)
+  const int grp = warp / SR_GW, gw = warp - grp * SR_GW, gtid = tid - grp * SR_GC;
   int tw = 1;                                         // warps per team: the fewest that divide the
-  while (tw < SR_W && (SR_W % tw != 0 || 64 * tw * SR_PPT < n)) ++tw;   // consumers and cover n columns
-  const int GS = 32 * tw, nt = SR_C / GS, tau = tid / GS, lt = tid - tau * GS;
-  float ah0[SR_PPT], al0[SR_PPT], ah1[SR_PPT], al1[SR_PPT];
+  while (tw < SR_GW && (SR_GW % tw != 0 || 64 * tw * SR_PPT < n)) ++tw;   // group and cover n columns
+  const int GS = 32 * tw, nt = SR_GC / GS, tau = gtid / GS, lt = gtid - tau * GS;
+  const int team = grp * nt + tau, nteams = SR_G * nt;
+  float2 ah[SR_PPT], al[SR_PPT];                      // column sums of the pairs (2 c2, 2 c2 + 1)
 #pragma unroll
-  for (int k = 0; k < SR_PPT; ++k) ah0[k] = al0[k] = ah1[k] = al1[k] = 0.f;
+  for (int k = 0; k < SR_PPT; ++k) ah[k] = al[k] = make_float2(0.f, 0.f);
 
   if (warp == SR_W) {
     // ---- producer warp: stage the chunk's rows, SR_NST stages ahead of the consumers
@@ -190,17 +195,19 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
       }
       g2[c] = v;
     }
-    for (int st = 0; st < NS; ++st) {
+    consumers_sync(1, SR_C);                          // g_i staged for both groups
+    const int bar_a = 2 + 2 * grp, bar_b = 3 + 2 * grp;
+    for (int st = grp; st < NS; st += SR_G) {
       const int slot = st % SR_NST;
       const bool got = mbar_wait(smem_u32(&full[slot]), (uint32_t)(st / SR_NST) & 1u, &abort_flag, err,
                                  SR_ERR_WAIT + 1);
-      if (!consumers_all(2, got)) break;              // (also publishes g_i before the first stage)
+      if (!consumers_all(bar_a, SR_GC, got)) break;
       const SrPlan& P = plan[slot];
       const float4* stage = stages + (size_t)slot * (SR_STAGE / 2);
       const int R = P.nr, TP = P.pfx[R];
       // (1) dot products over the warps' shares of the stage's column pairs
       {
-        const int a = (int)(((int64_t)warp * TP) / SR_W), b = (int)(((int64_t)(warp + 1) * TP) / SR_W);
+        const int a = (int)(((int64_t)gw * TP) / SR_GW), b = (int)(((int64_t)(gw + 1) * TP) / SR_GW);
         for (int j = 0; j < R; ++j) {
           const int p0 = P.pfx[j], p1 = P.pfx[j + 1];
           const int lo = max(a, p0) - p0, hi = min(b, p1) - p0;
@@ -208,59 +215,62 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
           if (lo < hi) {
             const int row = P.r0 + j;
             const float4* xr = stage + (P.off[j] >> 1);
-            float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
+              // accumulators (even column, odd column) of two pairs per lane, packed
+            float2 H0 = make_float2(0.f, 0.f), L0 = H0, H1 = H0, L1 = H0;
             int c2 = lo + lane;
             for (; c2 + 32 < hi; c2 += 64) {          // two pairs per lane in flight; only the
               const float4 x0 = xr[c2], y0 = gsm[c2]; // row's last pair can reach above the diagonal
               float4 x1 = xr[c2 + 32];
               const float4 y1 = gsm[c2 + 32];
               if (2 * (c2 + 32) + 1 > row) { x1.z = 0.f; x1.w = 0.f; }
-              df_mac_f(h, l, make_float2(x0.x, x0.y), make_float2(y0.x, y0.y));
-              df_mac_f(h1, l1, make_float2(x0.z, x0.w), make_float2(y0.z, y0.w));
-              df_mac_f(h2, l2, make_float2(x1.x, x1.y), make_float2(y1.x, y1.y));
-              df_mac_f(h3, l3, make_float2(x1.z, x1.w), make_float2(y1.z, y1.w));
+              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.z),
+                          make_float2(y0.y, y0.w));
+              df_mac_f_x2(H1, L1, make_float2(x1.x, x1.z), make_float2(x1.y, x1.w), make_float2(y1.x, y1.z),
+                          make_float2(y1.y, y1.w));
             }
             if (c2 < hi) {
               float4 x0 = xr[c2];
               const float4 y0 = gsm[c2];
               if (2 * c2 + 1 > row) { x0.z = 0.f; x0.w = 0.f; }
-              df_mac_f(h, l, make_float2(x0.x, x0.y), make_float2(y0.x, y0.y));
-              df_mac_f(h1, l1, make_float2(x0.z, x0.w), make_float2(y0.z, y0.w));
+              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.z),
+                          make_float2(y0.y, y0.w));
             }
-            df_add(h, l, h1, l1);
-            df_add(h2, l2, h3, l3);
+            h = H0.x; l = L0.x;
+            float h2 = H1.x, l2 = L1.x;
+            df_add(h, l, H0.y, L0.y);
+            df_add(h2, l2, H1.y, L1.y);
             df_add(h, l, h2, l2);
             df_warp_sum(h, l);
           }
-          if (lane == 0) wp[j][warp] = make_float2(h, l);
+          if (lane == 0) wp[grp][j][gw] = make_float2(h, l);
         }
       }
-      consumers_sync(1);
-      // y_r = the row's pieces added in warp order: warp w takes rows w, w + SR_W
-      for (int j = warp; j < R; j += SR_W) {
-        float2 v = lane < SR_W ? wp[j][lane] : make_float2(0.f, 0.f);
+      consumers_sync(bar_b, SR_GC);
+      // y_r = the row's pieces added in warp order: warp w of the group takes rows w, w + SR_GW
+      for (int j = gw; j < R; j += SR_GW) {
+        float2 v = lane < SR_GW ? wp[grp][j][lane] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int o = SR_WP / 2; o > 0; o >>= 1) {
+        for (int o = SR_GW / 2; o > 0; o >>= 1) {
           const float oh = __shfl_xor_sync(0xffffffffu, v.x, o);
           const float ol = __shfl_xor_sync(0xffffffffu, v.y, o);
           df_add(v.x, v.y, oh, ol);
         }
-        if (lane == 0) ysm[j] = v;
+        if (lane == 0) ysm[grp][j] = v;
       }
-      consumers_sync(1);
+      consumers_sync(bar_b, SR_GC);
       // (2) column sums: team tau takes rows tau, tau + nt, ...
       for (int j = tau; j < R; j += nt) {
         const int row = P.r0 + j, nall = (row >> 1) + 1;
         const float4* xr = stage + (P.off[j] >> 1);
-        const float2 y = ysm[j];
+        const float2 y = ysm[grp][j];
 #pragma unroll
         for (int k = 0; k < SR_PPT; ++k) {
           const int c2 = lt + GS * k;
           if (c2 < nall) {
             float4 x = xr[c2];
             if (2 * c2 + 1 > row) { x.z = 0.f; x.w = 0.f; }
-            df_mac_f(ah0[k], al0[k], make_float2(x.x, x.y), y);
-            df_mac_f(ah1[k], al1[k], make_float2(x.z, x.w), y);
+            df_mac_f_x2(ah[k], al[k], make_float2(x.x, x.z), make_float2(x.y, x.w), make_float2(y.x, y.x),
+                        make_float2(y.y, y.y));
           }
         }
       }
@@ -274,27 +284,21 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
     for (int st = 0; st < issued; ++st) mbar_drain(smem_u32(&full[st % SR_NST]), (uint32_t)(st / SR_NST) & 1u);
   }
   __syncthreads();
-  // the chunk's column sums (columns < C.r1): the teams' sums added in team order
+  // the chunk's column sums (columns < C.r1): the teams' sums (group 0's, then group 1's)
+  // added in team order
   double* pr = part + C.poff;
   if (!abort_flag && tid < SR_C) {
-    if (nt == 1) {
-#pragma unroll
-      for (int k = 0; k < SR_PPT; ++k) {
-        const int c = 2 * (lt + GS * k);
-        if (c < C.r1) pr[c] = df_to_double(ah0[k], al0[k]);
-        if (c + 1 < C.r1) pr[c + 1] = df_to_double(ah1[k], al1[k]);
-      }
-    } else {
+    {
       const int np = (C.r1 + 1) >> 1;
 #pragma unroll
       for (int k = 0; k < SR_PPT; ++k) {
         const int c2 = lt + GS * k;
-        if (c2 < np) stages[(size_t)tau * np + c2] = make_float4(ah0[k], al0[k], ah1[k], al1[k]);
+        if (c2 < np) stages[(size_t)team * np + c2] = make_float4(ah[k].x, al[k].x, ah[k].y, al[k].y);
       }
-      consumers_sync(1);
+      consumers_sync(1, SR_C);
       for (int c2 = tid; c2 < np; c2 += SR_C) {
         float4 v = stages[c2];
-        for (int t2 = 1; t2 < nt; ++t2) {
+        for (int t2 = 1; t2 < nteams; ++t2) {
           const float4 u = stages[(size_t)t2 * np + c2];
           df_add(v.x, v.y, u.x, u.y);
           df_add(v.z, v.w, u.z, u.w);

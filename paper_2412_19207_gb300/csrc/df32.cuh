@@ -47,6 +47,24 @@ __device__ __forceinline__ void df_mac_f(float& sh, float& sl, float2 a, float2 
   sl = __fmaf_rn(a.x, x.y, __fmaf_rn(a.y, x.x, __fadd_rn(sl, __fadd_rn(e, e2))));
 }
 
+// df_mac_f for two independent accumulators at once, lanes .x and .y of each
+// float2 (sh, sl: the accumulators' high and low parts; ah, al and xh, xl:
+// the two products' operands), with the packed float32x2 operations of
+// sm_100 and later (__fmul2_rn, __ffma2_rn, __fadd2_rn: one issue slot per
+// pair of float32 operations).  Every lane takes the same IEEE
+// round-to-nearest steps in the same order as df_mac_f (a - b as a + (-b),
+// exact), so the results are bit for bit those of two df_mac_f calls.
+__device__ __forceinline__ float2 df_neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void df_mac_f_x2(float2& sh, float2& sl, float2 ah, float2 al, float2 xh, float2 xl) {
+  const float2 p = __fmul2_rn(ah, xh);
+  const float2 e = __ffma2_rn(ah, xh, df_neg2(p));
+  const float2 t = __fadd2_rn(sh, p);
+  const float2 bp = __fadd2_rn(t, df_neg2(sh));
+  const float2 e2 = __fadd2_rn(__fadd2_rn(sh, df_neg2(__fadd2_rn(t, df_neg2(bp)))), __fadd2_rn(p, df_neg2(bp)));
+  sh = t;
+  sl = __ffma2_rn(ah, xl, __ffma2_rn(al, xh, __fadd2_rn(sl, __fadd2_rn(e, e2))));
+}
+
 // Fold the low part into the high part (fast two-sum, |sh| >= |sl| not required
 // for the exactness of the sum, only for normalisation).
 __device__ __forceinline__ void df_renorm(float& sh, float& sl) {
