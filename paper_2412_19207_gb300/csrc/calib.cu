@@ -1,8 +1,9 @@
 // Device calibration: the measured rates of the arithmetic the double-float
 // and float64 kernels are bound by, for their roofline denominators.
 //   df32: the double-float multiply-add of the Schwarz apply and the inner
-//         operator (df_mac_f: exact product, two-sum, low-order terms by
-//         FMAs), counted as 2 flops each;
+//         operator (df_mac_f_x2: exact product, two-sum, low-order terms by
+//         FMAs, two at a time in packed float32x2 operations), counted as 2
+//         flops each;
 //   fp64: float64 FMAs, 2 flops each.
 // Each thread runs 8 independent chains (enough to cover the pipelines'
 // latency at full occupancy); the grid fills every SM several times over.
@@ -14,19 +15,23 @@ namespace {
 constexpr int CAL_T = 256;
 constexpr int CAL_CHAINS = 8;
 
+// the packed form the kernels use (df_mac_f_x2: two chains per call)
 __global__ void __launch_bounds__(CAL_T) df_rate_kernel(int iters, float seed, float* __restrict__ sink) {
-  float h[CAL_CHAINS], l[CAL_CHAINS];
-  const float2 a = make_float2(1.0f + seed * 1e-7f, seed * 1e-15f);
-  const float2 x = make_float2(0.999999f, 1e-9f * seed);
+  float2 h[CAL_CHAINS / 2], l[CAL_CHAINS / 2];
+  const float2 ah = make_float2(1.0f + seed * 1e-7f, 1.0f - seed * 1e-7f), al = make_float2(seed * 1e-15f, 0.f);
+  const float2 xh = make_float2(0.999999f, 0.999998f), xl = make_float2(1e-9f * seed, -1e-9f * seed);
 #pragma unroll
-  for (int c = 0; c < CAL_CHAINS; ++c) { h[c] = (float)(threadIdx.x + c) * 1e-3f; l[c] = 0.f; }
+  for (int c = 0; c < CAL_CHAINS / 2; ++c) {
+    h[c] = make_float2((float)(threadIdx.x + c) * 1e-3f, (float)(threadIdx.x - c) * 1e-3f);
+    l[c] = make_float2(0.f, 0.f);
+  }
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int c = 0; c < CAL_CHAINS; ++c) df_mac_f(h[c], l[c], a, x);
+    for (int c = 0; c < CAL_CHAINS / 2; ++c) df_mac_f_x2(h[c], l[c], ah, al, xh, xl);
   }
   float s = 0.f;
 #pragma unroll
-  for (int c = 0; c < CAL_CHAINS; ++c) s += h[c] + l[c];
+  for (int c = 0; c < CAL_CHAINS / 2; ++c) s += h[c].x + l[c].x + h[c].y + l[c].y;
   if (s == 1234.5f) sink[blockIdx.x] = s;     // never true in practice: keeps the chains live
 }
 

@@ -270,7 +270,8 @@ __global__ void __launch_bounds__(256) syrk_update_df_kernel(const CholMat* __re
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int q = 0; q < QN; ++q) df_mac(ah[p][q], al[p][q], a[p], b[q]);
+      for (int q = 0; q < QN; q += 2)             // packed float32x2, two columns at a time
+        df_mac_2(ah[p][q], al[p][q], ah[p][q + 1], al[p][q + 1], a[p], b[q], a[p], b[q + 1]);
     if ((k & 15) == 15)
 #pragma unroll
       for (int p = 0; p < 4; ++p)
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(256) trtri_row_df_kernel(const CholMat* __rest
     for (int q = 0; q < NB; ++q) {
       const float2 lv = sl[r][q];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) df_mac(ah[u], al[u], lv, sx[q][cg + u]);
+      for (int u = 0; u < 4; u += 2) df_mac_2(ah[u], al[u], ah[u + 1], al[u + 1], lv, sx[q][cg + u], lv, sx[q][cg + u + 1]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) df_renorm(ah[u], al[u]);
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(256) trtri_row_df_kernel(const CholMat* __rest
   for (int q = 0; q <= r; ++q) {
     const float2 lv = sl[r][q];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) df_mac(oh[u], ol[u], lv, sx[q][cg + u]);
+    for (int u = 0; u < 4; u += 2) df_mac_2(oh[u], ol[u], oh[u + 1], ol[u + 1], lv, sx[q][cg + u], lv, sx[q][cg + u + 1]);
   }
   if (ri + r < M.n)
 #pragma unroll
@@ -760,8 +761,7 @@ constexpr int AR = 32;             // rows per block of the fused apply
 constexpr int AMAX_SUB = 27;       // most subdomains in an extended set (3^3)
 constexpr int ANT = 256;           // threads per block of the fused apply (four blocks per SM)
 __device__ __forceinline__ void df_mac2(float& h0, float& l0, float& h1, float& l1, float4 a, float4 x) {
-  df_mac(h0, l0, make_float2(a.x, a.y), make_float2(x.x, x.y));
-  df_mac(h1, l1, make_float2(a.z, a.w), make_float2(x.z, x.w));
+  df_mac_pair(h0, l0, h1, l1, a, x);              // packed float32x2
 }
 // The sums of nv vectors of 32 lane partials lp[v * vstride + l], each with
 // the pairing of the xor-shuffle warp sum (level o: entry l += entry l + o

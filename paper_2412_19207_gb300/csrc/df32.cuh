@@ -65,6 +65,28 @@ __device__ __forceinline__ void df_mac_f_x2(float2& sh, float2& sl, float2 ah, f
   sl = __ffma2_rn(ah, xl, __ffma2_rn(al, xh, __fadd2_rn(sl, __fadd2_rn(e, e2))));
 }
 
+// (h0, l0) += a0 x0 and (h1, l1) += a1 x1: df_mac_f_x2 on two scalar accumulators.
+__device__ __forceinline__ void df_mac_2(float& h0, float& l0, float& h1, float& l1, float2 a0, float2 x0, float2 a1,
+                                         float2 x1) {
+  float2 H = make_float2(h0, h1), L = make_float2(l0, l1);
+  df_mac_f_x2(H, L, make_float2(a0.x, a1.x), make_float2(a0.y, a1.y), make_float2(x0.x, x1.x), make_float2(x0.y, x1.y));
+  h0 = H.x;
+  h1 = H.y;
+  l0 = L.x;
+  l1 = L.y;
+}
+
+// The two double-float entries of a float4 (h0, l0, h1, l1) times those of
+// x, accumulated into (h0, l0) and (h1, l1): df_mac_f_x2 on the pair.
+__device__ __forceinline__ void df_mac_pair(float& h0, float& l0, float& h1, float& l1, float4 a, float4 x) {
+  float2 H = make_float2(h0, h1), L = make_float2(l0, l1);
+  df_mac_f_x2(H, L, make_float2(a.x, a.z), make_float2(a.y, a.w), make_float2(x.x, x.z), make_float2(x.y, x.w));
+  h0 = H.x;
+  h1 = H.y;
+  l0 = L.x;
+  l1 = L.y;
+}
+
 // Fold the low part into the high part (fast two-sum, |sh| >= |sl| not required
 // for the exactness of the sum, only for normalisation).
 __device__ __forceinline__ void df_renorm(float& sh, float& sl) {

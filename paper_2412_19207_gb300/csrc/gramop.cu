@@ -86,8 +86,7 @@ __global__ void __launch_bounds__(256) gram_rowdot_kernel(const GramRows g, cons
     for (int u = 0; u < U; ++u) {
       if (i0 + 32 * u >= n4) break;
       const float4 xv = xs[i0 + 32 * u];
-      df_mac(h0, l0, make_float2(a[u].x, a[u].y), make_float2(xv.x, xv.y));
-      df_mac(h1, l1, make_float2(a[u].z, a[u].w), make_float2(xv.z, xv.w));
+      df_mac_pair(h0, l0, h1, l1, a[u], xv);
     }
   }
   df_add(h0, l0, h1, l1);
@@ -152,8 +151,7 @@ __global__ void __launch_bounds__(256) gram_rowdot_multi_kernel(const GramRows g
 #pragma unroll
       for (int c = 0; c < NR; ++c) {
         const float4 xv = xsm[c * n4 + i0 + 32 * u];
-        df_mac(h0[c], l0[c], make_float2(a[u].x, a[u].y), make_float2(xv.x, xv.y));
-        df_mac(h1[c], l1[c], make_float2(a[u].z, a[u].w), make_float2(xv.z, xv.w));
+        df_mac_pair(h0[c], l0[c], h1[c], l1[c], a[u], xv);
       }
     }
   }

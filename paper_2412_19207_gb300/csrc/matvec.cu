@@ -122,8 +122,7 @@ __global__ void __launch_bounds__(256) rowdot_df_kernel(const SubDev* __restrict
       for (int c = sl; c < P2; c += 8) {
         const float4 b = rp[c];
         const float4 xv = xs[c];
-        df_mac(h0, l0, make_float2(b.x, b.y), make_float2(xv.x, xv.y));
-        df_mac(h1, l1, make_float2(b.z, b.w), make_float2(xv.z, xv.w));
+        df_mac_pair(h0, l0, h1, l1, b, xv);
       }
       df_add(h0, l0, h1, l1);
     }
@@ -191,16 +190,13 @@ __global__ void __launch_bounds__(256) matvec_HT_df_partial_kernel(ProbDev P, co
       for (; t + G < nr; t += 2 * G) {
         const float4 u = col[(int64_t)t * P2], w = col[(int64_t)(t + G) * P2];
         const float2 yu = yl[t], yw = yl[t + G];
-        df_mac(a0, a1, make_float2(u.x, u.y), yu);
-        df_mac(b0, b1, make_float2(u.z, u.w), yu);
-        df_mac(e0, e1, make_float2(w.x, w.y), yw);
-        df_mac(f0, f1, make_float2(w.z, w.w), yw);
+        df_mac_pair(a0, a1, b0, b1, u, make_float4(yu.x, yu.y, yu.x, yu.y));
+        df_mac_pair(e0, e1, f0, f1, w, make_float4(yw.x, yw.y, yw.x, yw.y));
         if ((++cnt & 7) == 0) { df_renorm(a0, a1); df_renorm(b0, b1); df_renorm(e0, e1); df_renorm(f0, f1); }
       }
       if (t < nr) {
         const float4 u = col[(int64_t)t * P2];
-        df_mac(a0, a1, make_float2(u.x, u.y), yl[t]);
-        df_mac(b0, b1, make_float2(u.z, u.w), yl[t]);
+        df_mac_pair(a0, a1, b0, b1, u, make_float4(yl[t].x, yl[t].y, yl[t].x, yl[t].y));
       }
       df_add(a0, a1, e0, e1);
       df_add(b0, b1, f0, f1);
