@@ -253,18 +253,47 @@ struct OzTile {               // one tile: operands, their row exponents, sizes,
   const int* eb;
   int M, N, Kp, tm, tn;
 };
+// The tile entry (hi 2^-35 + lo 2^-63) 2^ex from the exact integer sums, in float64: one rounding.
+__device__ __forceinline__ double oz_f64_of(long long hi, int lo, int ex) {
+  const double v = fma((double)hi, 0x1p-35, (double)lo * 0x1p-63);
+  // times 2^ex: a power-of-two factor built from its exponent field when it is normal
+  return (ex >= -1022 && ex <= 1023) ? v * __longlong_as_double((long long)(ex + 1023) << 52) : ldexp(v, ex);
+}
+// The same entry as a double-float without float64 arithmetic (GB300's float64 pipe runs at
+// 1/64 of float32): hi = c2 2^48 + c1 2^24 + c0 with c1, c0 in [0, 2^24) converts to floats
+// exactly; the pieces (and lo, rounded to 24 bits: far below the product's error) are added
+// with error-free float32 steps, then scaled by 2^(ex - 35).  About 2^-47 relative, the
+// double-float format's own accuracy.
+__device__ __forceinline__ float2 oz_df_of(long long hi, int lo, int ex) {
+  const float a = __int2float_rn((int)(hi >> 48)) * 0x1p48f;
+  const float b = __int2float_rn((int)((hi >> 24) & 0xFFFFFF)) * 0x1p24f;
+  const float c = __int2float_rn((int)(hi & 0xFFFFFF));
+  const float d = __int2float_rn(lo) * 0x1p-28f;
+  float s, e;
+  df_two_sum(a, b, s, e);
+  df_add(s, e, c, 0.f);
+  df_add(s, e, d, 0.f);
+  const int k = ex - 35;
+  if (k >= -126 && k <= 127) {
+    const float f = __int_as_float((k + 127) << 23);
+    return make_float2(s * f, e * f);
+  }
+  return make_float2(ldexpf(s, k), ldexpf(e, k));
+}
 // Output of the grouped launch: float64 C, or double-float C minus (plus) the product.
 struct OzEpi {
   void* C;
   int ldc, mode, lower;
-  __device__ __forceinline__ void operator()(int i, int j, double v) const {
+  __device__ __forceinline__ void operator()(int i, int j, long long hi, int lo, int ex) const {
     if (mode == OZ_OUT_F64) {
-      reinterpret_cast<double*>(C)[(int64_t)i * ldc + j] = v;
+      reinterpret_cast<double*>(C)[(int64_t)i * ldc + j] = oz_f64_of(hi, lo, ex);
       return;
     }
+    put_df(i, j, oz_df_of(hi, lo, ex));
+  }
+  __device__ __forceinline__ void put_df(int i, int j, float2 s) const {
     if (lower && j > i) return;
     float2* p = reinterpret_cast<float2*>(C) + (int64_t)i * ldc + j;
-    const float2 s = df_split(v);
     if (mode == OZ_OUT_DF_SET) {
       *p = s;
     } else {
@@ -277,7 +306,9 @@ struct OzEpi {
 struct OzEpiF64 {
   double* C;
   int ldc;
-  __device__ __forceinline__ void operator()(int i, int j, double v) const { C[(int64_t)i * ldc + j] = v; }
+  __device__ __forceinline__ void operator()(int i, int j, long long hi, int lo, int ex) const {
+    C[(int64_t)i * ldc + j] = oz_f64_of(hi, lo, ex);
+  }
 };
 
 template <class Epi>
@@ -417,13 +448,7 @@ __device__ __forceinline__ void oz_tile_run(const OzTile& t, const OzMap* __rest
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int jj = t.tn + half * 32 + j;
-          if (jj < t.N) {
-            const double v = fma((double)hi[j], 0x1p-35, (double)lo[j] * 0x1p-63);   // the one rounding
-            const int ex = ea + t.eb[jj];
-            // times 2^ex: a power-of-two factor built from its exponent field when it is normal
-            epi(i, jj, (ex >= -1022 && ex <= 1023) ? v * __longlong_as_double((long long)(ex + 1023) << 52)
-                                                   : ldexp(v, ex));
-          }
+          if (jj < t.N) epi(i, jj, hi[j], lo[j], ea + t.eb[jj]);
         }
       }
     }
