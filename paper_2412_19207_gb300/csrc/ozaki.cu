@@ -282,6 +282,7 @@ __device__ __forceinline__ float2 oz_df_of(long long hi, int lo, int ex) {
 }
 // Output of the grouped launch: float64 C, or double-float C minus (plus) the product.
 struct OzEpi {
+  static constexpr bool kDf = true;         // can write double-float outputs
   void* C;
   int ldc, mode, lower;
   __device__ __forceinline__ void operator()(int i, int j, long long hi, int lo, int ex) const {
@@ -291,6 +292,7 @@ struct OzEpi {
     }
     put_df(i, j, oz_df_of(hi, lo, ex));
   }
+  __device__ __forceinline__ bool df() const { return mode != OZ_OUT_F64; }
   __device__ __forceinline__ void put_df(int i, int j, float2 s) const {
     if (lower && j > i) return;
     float2* p = reinterpret_cast<float2*>(C) + (int64_t)i * ldc + j;
@@ -304,12 +306,49 @@ struct OzEpi {
   }
 };
 struct OzEpiF64 {
+  static constexpr bool kDf = false;
   double* C;
   int ldc;
   __device__ __forceinline__ void operator()(int i, int j, long long hi, int lo, int ex) const {
     C[(int64_t)i * ldc + j] = oz_f64_of(hi, lo, ex);
   }
+  __device__ __forceinline__ bool df() const { return false; }
 };
+constexpr int OZ_EP_LD = OZ_TILE_N + 1;   // row stride of the staged double-float tile (2-way banks)
+constexpr int OZ_EP_BATCH = 8;            // rows of C each drain warp reads before it updates them
+
+// Double-float output of a tile through shared memory: every drain thread stages its 32 entries
+// (the operand ring is free, all MMAs have completed); then each drain warp takes rows rr = w,
+// w + 8, ... and, OZ_EP_BATCH rows at a time, first loads the rows' 64-entry segments of C
+// (coalesced; up to 16 loads in flight per lane), then updates and stores them.
+__device__ __forceinline__ void oz_epilogue_df(const OzTile& t, const OzEpi& epi, float2* tile, int dw, int lane) {
+  const bool sub = epi.mode == OZ_OUT_DF_SUB;
+  for (int r0 = dw; r0 < OZ_TILE_M; r0 += OZ_DRAIN_WARPS * OZ_EP_BATCH) {
+    float2 cv[OZ_EP_BATCH][2];
+#pragma unroll
+    for (int b = 0; b < OZ_EP_BATCH; ++b)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rr = r0 + b * OZ_DRAIN_WARPS, i = t.tm + rr, j = t.tn + lane + 32 * h;
+        cv[b][h] = make_float2(0.f, 0.f);
+        if (sub && rr < OZ_TILE_M && i < t.M && j < t.N && !(epi.lower && j > i))
+          cv[b][h] = reinterpret_cast<const float2*>(epi.C)[(int64_t)i * epi.ldc + j];
+      }
+#pragma unroll
+    for (int b = 0; b < OZ_EP_BATCH; ++b)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rr = r0 + b * OZ_DRAIN_WARPS, i = t.tm + rr, j = t.tn + lane + 32 * h;
+        if (rr < OZ_TILE_M && i < t.M && j < t.N && !(epi.lower && j > i)) {
+          const float2 v = tile[rr * OZ_EP_LD + lane + 32 * h];
+          float2 c = cv[b][h];
+          if (sub) df_add(c.x, c.y, -v.x, -v.y);
+          else c = v;
+          reinterpret_cast<float2*>(epi.C)[(int64_t)i * epi.ldc + j] = c;
+        }
+      }
+  }
+}
 
 template <class Epi>
 __device__ __forceinline__ void oz_tile_run(const OzTile& t, const OzMap* __restrict__ maps, int* __restrict__ err,
@@ -441,9 +480,31 @@ __device__ __forceinline__ void oz_tile_run(const OzTile& t, const OzMap* __rest
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_acce));
     }
-    if (ok && !*abort) {
+    // one decision for all drain warps (the staged epilogue synchronises them)
+    int go = (ok && !*abort) ? 1 : 0;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.s32 q, %0, 0;\n bar.red.and.pred p, 2, %1, q;\n selp.s32 %0, 1, 0, p;\n}\n"
+        : "+r"(go) : "n"(OZ_DRAIN_WARPS * 32) : "memory");
+    if (go) {
       const int i = t.tm + quarter * 32 + lane;
-      if (i < t.M) {
+      bool staged = false;
+      if constexpr (Epi::kDf) {
+        if (epi.df()) {
+          staged = true;
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          float2* tile = reinterpret_cast<float2*>(oz_dyn + (sbase - smem_u32(oz_dyn)));
+          const int rl = quarter * 32 + lane, ea = (i < t.M) ? t.ea[i] : 0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int jj = t.tn + half * 32 + j;
+            tile[rl * OZ_EP_LD + half * 32 + j] =
+                (i < t.M && jj < t.N) ? oz_df_of(hi[j], lo[j], ea + t.eb[jj]) : make_float2(0.f, 0.f);
+          }
+          asm volatile("bar.sync 1, %0;\n" ::"n"(OZ_DRAIN_WARPS * 32) : "memory");
+          oz_epilogue_df(t, epi, tile, warp - 2, lane);
+        }
+      }
+      if (!staged && i < t.M) {
         const int ea = t.ea[i];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
