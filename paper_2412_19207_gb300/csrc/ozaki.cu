@@ -45,11 +45,11 @@ constexpr int OZ_Q = 8;             // digit slices per operand
 constexpr int OZ_NG = 8;            // weight groups s = 2..9 (g = s - 2 = q + r, zero-based)
 constexpr int OZ_TK = 16;           // k of one stage (one tcgen05.mma step)
 constexpr int OZ_CHUNK_STEPS = 16;  // 256 k per exact float32 accumulation
-constexpr int OZ_STAGES = 4;
+constexpr int OZ_STAGES = 3;
 constexpr int OZ_A_BYTES = OZ_Q * OZ_TILE_M * OZ_TK * 2;   // 32 KB
 constexpr int OZ_B_BYTES = OZ_Q * OZ_TILE_N * OZ_TK * 2;   // 16 KB
 constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024; // + alignment slack
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + OZ_TILE_M * (OZ_TILE_N + 1) * 8 + 1024;   // ring, output staging, alignment slack
 constexpr int OZ_DRAIN_WARPS = 8;   // warps 2..9: lane quarter w % 4, column half (w - 2) / 4
 constexpr int OZ_THREADS = 32 * (2 + OZ_DRAIN_WARPS);
 static_assert(OZ_NG * OZ_TILE_N == 512, "the group accumulators fill tensor memory");
@@ -350,17 +350,22 @@ __device__ __forceinline__ void oz_epilogue_df(const OzTile& t, const OzEpi& epi
   }
 }
 
-template <class Epi>
-__device__ __forceinline__ void oz_tile_run(const OzTile& t, const OzMap* __restrict__ maps, int* __restrict__ err,
-                                            const Epi& epi) {
+// Persistent tile loop: block b takes tiles b, b + gridDim.x, ... (fetch(i, t, epi) fills
+// tile i's operands and output).  The roles of one tile (above) run over the whole
+// sequence with running stage and chunk counters, so the producer streams the next tile's
+// operands and the MMA thread starts its products as soon as the drain warps have read the
+// accumulators, while the drain warps still finish the previous tile's output.  The output
+// staging area of the double-float epilogue follows the operand ring.
+template <class Fetch>
+__device__ __forceinline__ void oz_tiles_run(const Fetch& fetch, int ntiles, const OzMap* __restrict__ maps,
+                                             int* __restrict__ err) {
+  using Epi = typename Fetch::Epi;
   extern __shared__ uint8_t oz_dyn[];
   __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_accf, bar_acce, bar_fin;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, issued, consumed;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t sbase = (smem_u32(oz_dyn) + 1023u) & ~1023u;
-  const int nks = t.Kp / OZ_TK;
-  const int nch = (nks + OZ_CHUNK_STEPS - 1) / OZ_CHUNK_STEPS;
   volatile int* abort = &abort_flag;
   if (tid == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -386,23 +391,30 @@ __device__ __forceinline__ void oz_tile_run(const OzTile& t, const OzMap* __rest
 
   if (warp == 0) {
     if (lane == 0) {
-      const void* ma = &maps[2 * t.ia];        // A role: 128-row boxes
-      const void* mb = &maps[2 * t.ib + 1];    // B role: 64-row boxes
       bool ok = true;
-      for (int ks = 0; ks < nks; ++ks) {
-        const int s = ks % OZ_STAGES;
-        if (ks >= OZ_STAGES && !(ok = mbar_wait(smem_u32(&bar_empty[s]), ((ks / OZ_STAGES) - 1) & 1, abort, err, 1)))
-          break;
-        const uint32_t full = smem_u32(&bar_full[s]);
-        const uint32_t sa = sbase + s * OZ_STAGE_BYTES;
-        mbar_expect_tx(full, OZ_STAGE_BYTES);
-        tma_load_4d(sa, ma, 0, t.tm / 32, 2 * ks, 0, full);
-        tma_load_4d(sa + OZ_A_BYTES, mb, 0, t.tn / 32, 2 * ks, 0, full);
-        issued = ks + 1;
+      int g = 0;                                  // stages issued so far (all tiles)
+      for (int b = (int)blockIdx.x; ok && b < ntiles; b += (int)gridDim.x) {
+        OzTile t;
+        Epi epi;
+        fetch(b, t, epi);
+        const void* ma = &maps[2 * t.ia];        // A role: 128-row boxes
+        const void* mb = &maps[2 * t.ib + 1];    // B role: 64-row boxes
+        const int nks = t.Kp / OZ_TK;
+        for (int ks = 0; ks < nks; ++ks, ++g) {
+          const int s = g % OZ_STAGES;
+          if (g >= OZ_STAGES && !(ok = mbar_wait(smem_u32(&bar_empty[s]), ((g / OZ_STAGES) - 1) & 1, abort, err, 1)))
+            break;
+          const uint32_t full = smem_u32(&bar_full[s]);
+          const uint32_t sa = sbase + s * OZ_STAGE_BYTES;
+          mbar_expect_tx(full, OZ_STAGE_BYTES);
+          tma_load_4d(sa, ma, 0, t.tm / 32, 2 * ks, 0, full);
+          tma_load_4d(sa + OZ_A_BYTES, mb, 0, t.tn / 32, 2 * ks, 0, full);
+          issued = g + 1;
+        }
       }
       // every stage's release (an MMA commit) has landed before the block's shared memory is given up
-      for (int ks = max(nks - OZ_STAGES, 0); ok && ks < nks; ++ks)
-        ok = mbar_wait(smem_u32(&bar_empty[ks % OZ_STAGES]), (ks / OZ_STAGES) & 1, abort, err, 5);
+      for (int q = max(g - OZ_STAGES, 0); ok && q < g; ++q)
+        ok = mbar_wait(smem_u32(&bar_empty[q % OZ_STAGES]), (q / OZ_STAGES) & 1, abort, err, 5);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -412,96 +424,113 @@ __device__ __forceinline__ void oz_tile_run(const OzTile& t, const OzMap* __rest
       // stage layout: slice q, k group c, row i, k % 8 at ((q * 2 + c) * rows + i) * 16 + 2 (k % 8) bytes
       const uint64_t a0 = smem_desc(sbase, OZ_TILE_M * 16, 128);
       const uint64_t b0 = smem_desc(sbase + OZ_A_BYTES, OZ_TILE_N * 16, 128);
-      for (int ks = 0; ks < nks; ++ks) {
-        const int s = ks % OZ_STAGES, kc = ks % OZ_CHUNK_STEPS;
-        if (kc == 0 && ks > 0) {               // the drain of the previous chunk has read the accumulators
-          if (!mbar_wait(smem_u32(&bar_acce), (ks / OZ_CHUNK_STEPS - 1) & 1, abort, err, 2)) break;
-          tc_fence_after();
-        }
-        if (!mbar_wait(smem_u32(&bar_full[s]), (ks / OZ_STAGES) & 1, abort, err, 3)) break;
-        tc_fence_after();
-        const uint64_t soff = (uint64_t)((s * OZ_STAGE_BYTES) >> 4);
-        // A slice q meets B slices r = 0..7-q back to back: it is read from shared
-        // memory once and kept in the collector buffer for the following MMAs
-#pragma unroll
-        for (int q = 0; q < OZ_Q; ++q) {
-          const uint64_t ad = a0 + soff + (uint64_t)(q * (OZ_TILE_M * 2));
-          const int acc = (kc != 0 || q != 0) ? 1 : 0;
-#pragma unroll
-          for (int r = 0; r < OZ_Q - q; ++r) {
-            const uint32_t d = tbase + (uint32_t)((q + r) * OZ_TILE_N);
-            const uint64_t bd = b0 + soff + (uint64_t)(r * (OZ_TILE_N * 2));
-            if (q == OZ_Q - 1) tc_mma<0>(d, ad, bd, idesc, acc);
-            else if (r == 0) tc_mma<1>(d, ad, bd, idesc, acc);
-            else if (r == OZ_Q - 1 - q) tc_mma<3>(d, ad, bd, idesc, acc);
-            else tc_mma<2>(d, ad, bd, idesc, acc);
+      bool ok = true;
+      int g = 0, cg = 0;                          // stages and accumulation chunks consumed so far
+      for (int b = (int)blockIdx.x; ok && b < ntiles; b += (int)gridDim.x) {
+        OzTile t;
+        Epi epi;
+        fetch(b, t, epi);
+        const int nks = t.Kp / OZ_TK;
+        for (int ks = 0; ks < nks; ++ks, ++g) {
+          const int s = g % OZ_STAGES, kc = ks % OZ_CHUNK_STEPS;
+          if (kc == 0 && cg > 0) {                // the drain has read the previous chunk's accumulators
+            if (!(ok = mbar_wait(smem_u32(&bar_acce), (cg - 1) & 1, abort, err, 2))) break;
+            tc_fence_after();
           }
+          if (!(ok = mbar_wait(smem_u32(&bar_full[s]), (g / OZ_STAGES) & 1, abort, err, 3))) break;
+          tc_fence_after();
+          const uint64_t soff = (uint64_t)((s * OZ_STAGE_BYTES) >> 4);
+          // A slice q meets B slices r = 0..7-q back to back: it is read from shared
+          // memory once and kept in the collector buffer for the following MMAs
+#pragma unroll
+          for (int q = 0; q < OZ_Q; ++q) {
+            const uint64_t ad = a0 + soff + (uint64_t)(q * (OZ_TILE_M * 2));
+            const int acc = (kc != 0 || q != 0) ? 1 : 0;
+#pragma unroll
+            for (int r = 0; r < OZ_Q - q; ++r) {
+              const uint32_t d = tbase + (uint32_t)((q + r) * OZ_TILE_N);
+              const uint64_t bd = b0 + soff + (uint64_t)(r * (OZ_TILE_N * 2));
+              if (q == OZ_Q - 1) tc_mma<0>(d, ad, bd, idesc, acc);
+              else if (r == 0) tc_mma<1>(d, ad, bd, idesc, acc);
+              else if (r == OZ_Q - 1 - q) tc_mma<3>(d, ad, bd, idesc, acc);
+              else tc_mma<2>(d, ad, bd, idesc, acc);
+            }
+          }
+          tc_commit(smem_u32(&bar_empty[s]));    // the stage is free once these MMAs have read it
+          if (kc == OZ_CHUNK_STEPS - 1 || ks == nks - 1) {
+            tc_commit(smem_u32(&bar_accf));
+            ++cg;
+          }
+          consumed = g + 1;
         }
-        tc_commit(smem_u32(&bar_empty[s]));    // the stage is free once these MMAs have read it
-        if (kc == OZ_CHUNK_STEPS - 1 || ks == nks - 1) tc_commit(smem_u32(&bar_accf));
-        consumed = ks + 1;
       }
     }
   } else {
     const int quarter = warp & 3, half = (warp - 2) >> 2;
     const uint32_t trow = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
-    long long hi[32];
-    int lo[32];
+    float2* const stage_out = reinterpret_cast<float2*>(oz_dyn + (sbase - smem_u32(oz_dyn)) + OZ_STAGES * OZ_STAGE_BYTES);
+    int cg = 0;                                   // accumulation chunks drained so far
+    for (int b = (int)blockIdx.x; b < ntiles; b += (int)gridDim.x) {
+      OzTile t;
+      Epi epi;
+      fetch(b, t, epi);
+      const int nch = (t.Kp / OZ_TK + OZ_CHUNK_STEPS - 1) / OZ_CHUNK_STEPS;
+      long long hi[32];
+      int lo[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
-    bool ok = true;
-    for (int c = 0; c < nch; ++c) {
-      // every lane waits; the warp continues together (tcgen05.ld is warp-collective)
-      if (!(ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_accf), c & 1, abort, err, 4)))) break;
-      tc_fence_after();
+      for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
+      bool ok = true;
+      for (int c = 0; c < nch; ++c, ++cg) {
+        // every lane waits; the warp continues together (tcgen05.ld is warp-collective)
+        if (!(ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_accf), cg & 1, abort, err, 4)))) break;
+        tc_fence_after();
 #pragma unroll
-      for (int sub = 0; sub < 4; ++sub) {
-        uint32_t v[4][8];
-        int p0[8], p1[8];
+        for (int sub = 0; sub < 4; ++sub) {
+          uint32_t v[4][8];
+          int p0[8], p1[8];
 #pragma unroll
-        for (int g = 0; g < 4; ++g) tmem_ld8(trow + g * OZ_TILE_N + sub * 8, v[g]);
-        tmem_wait_ld();
+          for (int g = 0; g < 4; ++g) tmem_ld8(trow + g * OZ_TILE_N + sub * 8, v[g]);
+          tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) { p0[j] = join2(v[0][j], v[1][j]); p1[j] = join2(v[2][j], v[3][j]); }
+          for (int j = 0; j < 8; ++j) { p0[j] = join2(v[0][j], v[1][j]); p1[j] = join2(v[2][j], v[3][j]); }
 #pragma unroll
-        for (int g = 0; g < 4; ++g) tmem_ld8(trow + (g + 4) * OZ_TILE_N + sub * 8, v[g]);
-        tmem_wait_ld();
+          for (int g = 0; g < 4; ++g) tmem_ld8(trow + (g + 4) * OZ_TILE_N + sub * 8, v[g]);
+          tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int p2 = join2(v[0][j], v[1][j]), p3 = join2(v[2][j], v[3][j]);
-          const long long hc = ((long long)p0[j] << 14) + p1[j];       // sum_{s<=5} c_s 128^{5-s}
-          const long long lt = ((long long)p2 << 14) + p3 + lo[sub * 8 + j];
-          const long long carry = lt >> 28;                            // floor(lt / 2^28)
-          lo[sub * 8 + j] = (int)(lt - (carry << 28));
-          hi[sub * 8 + j] += hc + carry;
+          for (int j = 0; j < 8; ++j) {
+            const int p2 = join2(v[0][j], v[1][j]), p3 = join2(v[2][j], v[3][j]);
+            const long long hc = ((long long)p0[j] << 14) + p1[j];       // sum_{s<=5} c_s 128^{5-s}
+            const long long lt = ((long long)p2 << 14) + p3 + lo[sub * 8 + j];
+            const long long carry = lt >> 28;                            // floor(lt / 2^28)
+            lo[sub * 8 + j] = (int)(lt - (carry << 28));
+            hi[sub * 8 + j] += hc + carry;
+          }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_acce));
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bar_acce));
-    }
-    // one decision for all drain warps (the staged epilogue synchronises them)
-    int go = (ok && !*abort) ? 1 : 0;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.s32 q, %0, 0;\n bar.red.and.pred p, 2, %1, q;\n selp.s32 %0, 1, 0, p;\n}\n"
-        : "+r"(go) : "n"(OZ_DRAIN_WARPS * 32) : "memory");
-    if (go) {
+      // one decision for all drain warps (the staged epilogue synchronises them)
+      int go = (ok && !*abort) ? 1 : 0;
+      asm volatile(
+          "{\n .reg .pred p, q;\n setp.ne.s32 q, %0, 0;\n bar.red.and.pred p, 2, %1, q;\n selp.s32 %0, 1, 0, p;\n}\n"
+          : "+r"(go) : "n"(OZ_DRAIN_WARPS * 32) : "memory");
+      if (!go) break;
       const int i = t.tm + quarter * 32 + lane;
       bool staged = false;
       if constexpr (Epi::kDf) {
         if (epi.df()) {
           staged = true;
-          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-          float2* tile = reinterpret_cast<float2*>(oz_dyn + (sbase - smem_u32(oz_dyn)));
           const int rl = quarter * 32 + lane, ea = (i < t.M) ? t.ea[i] : 0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int jj = t.tn + half * 32 + j;
-            tile[rl * OZ_EP_LD + half * 32 + j] =
+            stage_out[rl * OZ_EP_LD + half * 32 + j] =
                 (i < t.M && jj < t.N) ? oz_df_of(hi[j], lo[j], ea + t.eb[jj]) : make_float2(0.f, 0.f);
           }
           asm volatile("bar.sync 1, %0;\n" ::"n"(OZ_DRAIN_WARPS * 32) : "memory");
-          oz_epilogue_df(t, epi, tile, warp - 2, lane);
+          oz_epilogue_df(t, epi, stage_out, warp - 2, lane);
+          asm volatile("bar.sync 1, %0;\n" ::"n"(OZ_DRAIN_WARPS * 32) : "memory");   // staging free again
         }
       }
       if (!staged && i < t.M) {
@@ -518,7 +547,7 @@ __device__ __forceinline__ void oz_tile_run(const OzTile& t, const OzMap* __rest
   if (*abort) {
     // let the copies and MMAs in flight finish before the memory is released (bounded)
     if (tid == 0)
-      for (int ks = consumed; ks < issued; ++ks) mbar_drain(smem_u32(&bar_full[ks % OZ_STAGES]), (ks / OZ_STAGES) & 1);
+      for (int q = consumed; q < issued; ++q) mbar_drain(smem_u32(&bar_full[q % OZ_STAGES]), (q / OZ_STAGES) & 1);
     if (tid == 32) {                           // the MMA-issuing thread: its commit covers all its MMAs
       tc_commit(smem_u32(&bar_fin));
       mbar_drain(smem_u32(&bar_fin), 0);
@@ -531,36 +560,53 @@ __device__ __forceinline__ void oz_tile_run(const OzTile& t, const OzMap* __rest
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tbase));
 }
 
+struct OzFetchTasks {                             // one task per tile (float64 output)
+  using Epi = OzEpiF64;
+  const OzTask* tasks;
+  __device__ __forceinline__ void operator()(int b, OzTile& t, OzEpiF64& epi) const {
+    const OzTask& q = tasks[b];
+    t = OzTile{q.ia, q.ib, q.ea, q.eb, q.M, q.N, q.Kp, q.tm, q.tn};
+    epi = OzEpiF64{q.C, q.ldc};
+  }
+};
+
+// Grouped launch: tile b belongs to the group with the largest first <= b; within
+// the group row tiles come in order, and in a lower group row tile r has
+// min(CT, 2 r + 2) column tiles (those meeting j <= i).
+struct OzFetchGroups {
+  using Epi = OzEpi;
+  const OzGroup* groups;
+  int ngroups;
+  __device__ __forceinline__ void operator()(int b, OzTile& t, OzEpi& epi) const {
+    int lo = 0, hi = ngroups - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (groups[mid].first <= b) lo = mid; else hi = mid - 1;
+    }
+    const OzGroup& G = groups[lo];
+    int id = b - G.first;
+    const int RT = (G.M + OZ_TILE_M - 1) / OZ_TILE_M, CT = (G.N + OZ_TILE_N - 1) / OZ_TILE_N;
+    int r = 0;
+    for (; r < RT; ++r) {
+      const int cnt = G.lower ? min(CT, 2 * r + 2) : CT;
+      if (id < cnt) break;
+      id -= cnt;
+    }
+    t = OzTile{G.ia, G.ib, G.ea, G.eb, G.M, G.N, G.Kp, r * OZ_TILE_M, id * OZ_TILE_N};
+    epi = OzEpi{G.C, G.ldc, G.mode, G.lower};
+  }
+};
+
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    oz_gemm_tc_kernel(const OzTask* __restrict__ tasks, const OzMap* __restrict__ maps, int* __restrict__ err) {
-  const OzTask& q = tasks[blockIdx.x];
-  const OzTile t{q.ia, q.ib, q.ea, q.eb, q.M, q.N, q.Kp, q.tm, q.tn};
-  oz_tile_run(t, maps, err, OzEpiF64{q.C, q.ldc});
+    oz_gemm_tc_kernel(const OzTask* __restrict__ tasks, int ntiles, const OzMap* __restrict__ maps,
+                      int* __restrict__ err) {
+  oz_tiles_run(OzFetchTasks{tasks}, ntiles, maps, err);
 }
 
-// Grouped launch: block b finds its group (largest first <= b) and its tile
-// in the group's enumeration (row tiles in order; in a lower group row tile r
-// has min(CT, 2 r + 2) column tiles, those meeting j <= i).
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    oz_gemm_grp_kernel(const OzGroup* __restrict__ groups, int ngroups, const OzMap* __restrict__ maps,
+    oz_gemm_grp_kernel(const OzGroup* __restrict__ groups, int ngroups, int ntiles, const OzMap* __restrict__ maps,
                        int* __restrict__ err) {
-  const int b = (int)blockIdx.x;
-  int lo = 0, hi = ngroups - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (groups[mid].first <= b) lo = mid; else hi = mid - 1;
-  }
-  const OzGroup& G = groups[lo];
-  int id = b - G.first;
-  const int RT = (G.M + OZ_TILE_M - 1) / OZ_TILE_M, CT = (G.N + OZ_TILE_N - 1) / OZ_TILE_N;
-  int r = 0;
-  for (; r < RT; ++r) {
-    const int cnt = G.lower ? min(CT, 2 * r + 2) : CT;
-    if (id < cnt) break;
-    id -= cnt;
-  }
-  const OzTile t{G.ia, G.ib, G.ea, G.eb, G.M, G.N, G.Kp, r * OZ_TILE_M, id * OZ_TILE_N};
-  oz_tile_run(t, maps, err, OzEpi{G.C, G.ldc, G.mode, G.lower});
+  oz_tiles_run(OzFetchGroups{groups, ngroups}, ntiles, maps, err);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -578,6 +624,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }  // namespace
 
 int oz_slices() { return OZ_Q; }
+
+// blocks of the persistent tile kernels: one per SM (each holds the SM's whole tensor memory)
+static int oz_resident_blocks() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    n = sms > 0 ? sms : 1;
+  }
+  return n;
+}
 int oz_kpad(int K) { return (K + 31) / 32 * 32; }
 
 cudaError_t oz_encode_maps(const std::vector<OzSplitTask>& ops, std::vector<OzMap>& maps) {
@@ -619,7 +677,7 @@ cudaError_t launch_oz_gemm(const OzTask* d_tasks, int ntiles, const OzMap* d_map
   if (reinterpret_cast<uintptr_t>(d_maps) & 63) return cudaErrorInvalidValue;   // tensor maps: 64-byte aligned
   static const cudaError_t lim = smem_limit_max(oz_gemm_tc_kernel);
   if (lim != cudaSuccess) return lim;
-  oz_gemm_tc_kernel<<<ntiles, OZ_THREADS, OZ_SMEM, st>>>(d_tasks, d_maps, d_err);
+  oz_gemm_tc_kernel<<<std::min(ntiles, oz_resident_blocks()), OZ_THREADS, OZ_SMEM, st>>>(d_tasks, ntiles, d_maps, d_err);
   return cudaGetLastError();
 }
 
@@ -629,6 +687,7 @@ cudaError_t launch_oz_gemm_groups(const OzGroup* d_groups, int ngroups, int ntil
   if (reinterpret_cast<uintptr_t>(d_maps) & 63) return cudaErrorInvalidValue;   // tensor maps: 64-byte aligned
   static const cudaError_t lim = smem_limit_max(oz_gemm_grp_kernel);
   if (lim != cudaSuccess) return lim;
-  oz_gemm_grp_kernel<<<ntiles, OZ_THREADS, OZ_SMEM, st>>>(d_groups, ngroups, d_maps, d_err);
+  oz_gemm_grp_kernel<<<std::min(ntiles, oz_resident_blocks()), OZ_THREADS, OZ_SMEM, st>>>(d_groups, ngroups, ntiles,
+                                                                                          d_maps, d_err);
   return cudaGetLastError();
 }
