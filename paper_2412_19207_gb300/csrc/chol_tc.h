@@ -6,7 +6,7 @@
 #include "common.cuh"
 
 constexpr int TC_NB = 256;          // panel width: one exact 256-long chunk of the digit-slice products
-constexpr int TC_MIN_N = 1024;      // local matrices from this size on take the big-panel path
+constexpr int TC_MIN_N = 512;       // local matrices from this size on take the big-panel path
 
 struct CholTcPlan {
   struct Step {

@@ -1,5 +1,5 @@
 """The big-panel local factorisation with tensor-core updates (precision mode 1,
-local matrices of 1024 unknowns and more: the extended sets of a 2 x 2 x 2
+local matrices of 512 unknowns and more: the extended sets of a 2 x 2 x 2
 space-time grid with 240 neurons hold about 1300 unknowns, so the
 factorisation runs five 256-column panels, the lower-triangle trailing
 updates, and the inverse's two products per panel).
