@@ -344,8 +344,8 @@ rann_status rann_dd_get_pca(rann_dd_handle* h, int j, double* eig_host, double* 
  * z_dev[zoff[j] ..].  RANN_EINVAL if J is outside 1..4096, a pointer is NULL,
  * a descriptor is negative or n_cols > ld, or (number of 256-row tiles) x
  * (largest n_cols) exceeds 2^20.  The first call on a device looks up the
- * arrays' device addresses (with that device current); make it before any
- * stream capture.  All calls share the arrays, which keep the last call's
+ * arrays' device addresses (with that device current).  All calls share
+ * the arrays, which keep the last call's
  * contents; every value a call reads is written earlier by the same call.
  * Calls that overlap on the GPU race.  Enqueued on `cuda_stream`. */
 rann_status rann_dd_matvec_t_noalloc(int J, const int64_t* boff, const int* n_rows, const int* n_cols,
