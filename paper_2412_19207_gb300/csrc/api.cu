@@ -1316,6 +1316,9 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
     CK(dalloc(h, (void**)&h->d_Xmats, sizeof(double) * (size_t)std::max<int64_t>(aoff, 1)));
   }
   CK(dalloc(h, (void**)&h->d_X2mats, sizeof(float2) * (size_t)std::max<int64_t>(aoff, 1)));
+  // the factorisations write only the lower triangles of L_i^{-1}; the streaming apply reads the
+  // entry just above the diagonal of even rows (its 16-byte copies) and relies on it being zero
+  CK(cudaMemsetAsync(h->d_X2mats, 0, sizeof(float2) * (size_t)std::max<int64_t>(aoff, 1), h->st));
   h->sum_n = h->sum_n2 = h->sum_n3 = 0;
   for (int i = 0; i < J; ++i) {
     const double n = mats[i].n;

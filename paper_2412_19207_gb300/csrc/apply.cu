@@ -35,6 +35,7 @@ constexpr int SR_GC = SR_C / SR_G;              // threads of a group
 constexpr int SR_GW = SR_W / SR_G;              // warps of a group
 constexpr int SR_T = SR_C + 32;                 // and one producer warp
 constexpr int SR_PPT = 12;                      // column pairs per thread in the column-sum pass
+static_assert(SR_PPT == 12, "the column-sum pass spells out its twelve cases");
 constexpr int SR_NMAX = 2 * SR_GC * SR_PPT;     // longest row (6144 columns)
 constexpr int SR_STAGE = 7168;                  // double-float entries per stage (56 KB)
 constexpr int SR_NST = 3;                       // stages in the ring
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
   int tw = 1;                                         // warps per team: the fewest that divide the
   while (tw < SR_GW && (SR_GW % tw != 0 || 64 * tw * SR_PPT < n)) ++tw;   // group and cover n columns
   const int GS = 32 * tw, nt = SR_GC / GS, tau = gtid / GS, lt = gtid - tau * GS;
+  const int gs_log = 5 + (tw >= 2) + (tw >= 4) + (tw >= 8);   // GS = 2^gs_log (tw divides SR_GW = 8)
   const int team = grp * nt + tau, nteams = SR_G * nt;
   float2 ah[SR_PPT], al[SR_PPT];                      // column sums of the pairs (2 c2, 2 c2 + 1)
 #pragma unroll
@@ -213,25 +215,22 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
           const int lo = max(a, p0) - p0, hi = min(b, p1) - p0;
           float h = 0.f, l = 0.f;
           if (lo < hi) {
-            const int row = P.r0 + j;
             const float4* xr = stage + (P.off[j] >> 1);
-              // accumulators (even column, odd column) of two pairs per lane, packed
+            // accumulators (even column, odd column) of two pairs per lane, packed
             float2 H0 = make_float2(0.f, 0.f), L0 = H0, H1 = H0, L1 = H0;
             int c2 = lo + lane;
-            for (; c2 + 32 < hi; c2 += 64) {          // two pairs per lane in flight; only the
-              const float4 x0 = xr[c2], y0 = gsm[c2]; // row's last pair can reach above the diagonal
-              float4 x1 = xr[c2 + 32];
+            for (; c2 + 32 < hi; c2 += 64) {          // two pairs per lane in flight (the entry above
+              const float4 x0 = xr[c2], y0 = gsm[c2]; // the diagonal in a row's last pair is zero)
+              const float4 x1 = xr[c2 + 32];
               const float4 y1 = gsm[c2 + 32];
-              if (2 * (c2 + 32) + 1 > row) { x1.z = 0.f; x1.w = 0.f; }
               df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.z),
                           make_float2(y0.y, y0.w));
               df_mac_f_x2(H1, L1, make_float2(x1.x, x1.z), make_float2(x1.y, x1.w), make_float2(y1.x, y1.z),
                           make_float2(y1.y, y1.w));
             }
             if (c2 < hi) {
-              float4 x0 = xr[c2];
+              const float4 x0 = xr[c2];
               const float4 y0 = gsm[c2];
-              if (2 * c2 + 1 > row) { x0.z = 0.f; x0.w = 0.f; }
               df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.z),
                           make_float2(y0.y, y0.w));
             }
@@ -258,21 +257,25 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
         if (lane == 0) ysm[grp][j] = v;
       }
       consumers_sync(bar_b, SR_GC);
-      // (2) column sums: team tau takes rows tau, tau + nt, ...
+      // (2) column sums: team tau takes rows tau, tau + nt, ...; a row reaches kact of the thread's
+      // SR_PPT column pairs, entered at the last of them (the bodies fall through down to k = 0)
       for (int j = tau; j < R; j += nt) {
-        const int row = P.r0 + j, nall = (row >> 1) + 1;
-        const float4* xr = stage + (P.off[j] >> 1);
+        const int nall = ((P.r0 + j) >> 1) + 1;
+        const float4* xr = stage + (P.off[j] >> 1) + lt;
         const float2 y = ysm[grp][j];
-#pragma unroll
-        for (int k = 0; k < SR_PPT; ++k) {
-          const int c2 = lt + GS * k;
-          if (c2 < nall) {
-            float4 x = xr[c2];
-            if (2 * c2 + 1 > row) { x.z = 0.f; x.w = 0.f; }
-            df_mac_f_x2(ah[k], al[k], make_float2(x.x, x.z), make_float2(x.y, x.w), make_float2(y.x, y.x),
-                        make_float2(y.y, y.y));
-          }
+        const float2 yh = make_float2(y.x, y.x), yl = make_float2(y.y, y.y);
+        const int kact = nall > lt ? min(SR_PPT, ((nall - lt - 1) >> gs_log) + 1) : 0;
+#define SR_COLSUM(k)                                                                                    \
+  case (k) + 1: {                                                                                       \
+    const float4 x = xr[GS * (k)];                                                                      \
+    df_mac_f_x2(ah[k], al[k], make_float2(x.x, x.z), make_float2(x.y, x.w), yh, yl);                    \
+  }
+        switch (kact) {
+          SR_COLSUM(11) SR_COLSUM(10) SR_COLSUM(9) SR_COLSUM(8) SR_COLSUM(7) SR_COLSUM(6)
+          SR_COLSUM(5) SR_COLSUM(4) SR_COLSUM(3) SR_COLSUM(2) SR_COLSUM(1) SR_COLSUM(0)
+          default: break;
         }
+#undef SR_COLSUM
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[slot]));
