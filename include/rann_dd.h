@@ -374,7 +374,7 @@ rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const char** name, i
 /* Schwarz apply configurations (precision mode 1).  0: the fused kernel that
  * reads 32-row blocks of L_i^{-1} twice (the second time from L2); 1..3: the
  * streaming kernel that reads every row of L_i^{-1} once through shared
- * memory, with row chunks of about 1/2, 1/6, 1/12 of an SM's share of the
+ * memory, with row chunks of about 1/6, 1/12, 1/24 of an SM's share of the
  * factor entries (sets of at most 6144 unknowns).  setup_precond picks 2 for
  * sets of 2048 unknowns and more, else 0.  The configurations differ only in
  * the summation order (results agree to the double-float factor accuracy);

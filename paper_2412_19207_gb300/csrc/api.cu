@@ -1094,7 +1094,7 @@ static rann_status build_gram_rows(rann_dd_handle* h, const std::vector<int64_t>
 // 0: the fused 32-row-block kernel (precision mode 1, sets of up to 27 subdomains);
 // c >= 1: the streaming kernel with chunks of about 1/APPLY_CHUNKS[c] of an SM's
 // share of the triangles' entries (sets of up to schwarz_rows_nmax() unknowns).
-static const int APPLY_CHUNKS[RANN_APPLY_NCFG] = {0, 2, 6, 12};
+static const int APPLY_CHUNKS[RANN_APPLY_NCFG] = {0, 6, 12, 24};
 
 static bool streaming_ok(const rann_dd_handle* h) {
   return h->prec_df && h->maxn <= schwarz_rows_nmax() && h->max_set_size <= schwarz_apply_max_subs();
