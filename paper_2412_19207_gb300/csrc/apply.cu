@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
   const int n = M.n, NS = C.nst;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int q0 = set_ptr[i], nq = set_ptr[i + 1] - q0;
-  float4* const gsm = sr_buf;                         // (g_2c, g_2c+1) as double-float pairs
+  float4* const gsm = sr_buf;                         // g_i by column pairs, high parts then low parts
   float4* const stages = sr_buf + SR_NMAX / 2;
   if (tid < nq) {
     const int k = set_sub[q0 + tid];
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
   } else {
     // ---- consumer warps
     // g_i in shared memory, columns below C.r1 (all the chunk's rows reach)
-    float2* const g2 = reinterpret_cast<float2*>(gsm);
+    float* const gf = reinterpret_cast<float*>(gsm);  // pair c2: (h_2c2, h_2c2+1, l_2c2, l_2c2+1)
     for (int c = tid; c < ((C.r1 + 1) & ~1); c += SR_C) {
       float2 v = make_float2(0.f, 0.f);
       if (c < C.r1) {
@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
         }
         v = r2 ? r2[seg_w[lo] + (c - seg_c[lo])] : df_split(seg_d[lo] * r[seg_w[lo] + (c - seg_c[lo])]);
       }
-      g2[c] = v;
+      gf[4 * (c >> 1) + (c & 1)] = v.x;
+      gf[4 * (c >> 1) + (c & 1) + 2] = v.y;
     }
     consumers_sync(1, SR_C);                          // g_i staged for both groups
     const int bar_a = 2 + 2 * grp, bar_b = 3 + 2 * grp;
@@ -223,16 +224,16 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
               const float4 x0 = xr[c2], y0 = gsm[c2]; // the diagonal in a row's last pair is zero)
               const float4 x1 = xr[c2 + 32];
               const float4 y1 = gsm[c2 + 32];
-              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.z),
-                          make_float2(y0.y, y0.w));
-              df_mac_f_x2(H1, L1, make_float2(x1.x, x1.z), make_float2(x1.y, x1.w), make_float2(y1.x, y1.z),
-                          make_float2(y1.y, y1.w));
+              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.y),
+                          make_float2(y0.z, y0.w));
+              df_mac_f_x2(H1, L1, make_float2(x1.x, x1.z), make_float2(x1.y, x1.w), make_float2(y1.x, y1.y),
+                          make_float2(y1.z, y1.w));
             }
             if (c2 < hi) {
               const float4 x0 = xr[c2];
               const float4 y0 = gsm[c2];
-              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.z),
-                          make_float2(y0.y, y0.w));
+              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.y),
+                          make_float2(y0.z, y0.w));
             }
             h = H0.x; l = L0.x;
             float h2 = H1.x, l2 = L1.x;

@@ -52,15 +52,18 @@ __device__ __forceinline__ void df_mac_f(float& sh, float& sl, float2 a, float2 
 // the two products' operands), with the packed float32x2 operations of
 // sm_100 and later (__fmul2_rn, __ffma2_rn, __fadd2_rn: one issue slot per
 // pair of float32 operations).  Every lane takes the same IEEE
-// round-to-nearest steps in the same order as df_mac_f (a - b as a + (-b),
-// exact), so the results are bit for bit those of two df_mac_f calls.
-__device__ __forceinline__ float2 df_neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// round-to-nearest steps in the same order as df_mac_f, so the results are
+// bit for bit those of two df_mac_f calls; a - b is formed as fma(b, -1, a)
+// (one rounding of the exact a - b, the packed add having no negated
+// operand) and -p as p * -1 (exact).
 __device__ __forceinline__ void df_mac_f_x2(float2& sh, float2& sl, float2 ah, float2 al, float2 xh, float2 xl) {
+  const float2 m1 = make_float2(-1.f, -1.f);
   const float2 p = __fmul2_rn(ah, xh);
-  const float2 e = __ffma2_rn(ah, xh, df_neg2(p));
-  const float2 t = __fadd2_rn(sh, p);
-  const float2 bp = __fadd2_rn(t, df_neg2(sh));
-  const float2 e2 = __fadd2_rn(__fadd2_rn(sh, df_neg2(__fadd2_rn(t, df_neg2(bp)))), __fadd2_rn(p, df_neg2(bp)));
+  const float2 e = __ffma2_rn(ah, xh, __fmul2_rn(p, m1));                  // ah xh - p, exact
+  const float2 t = __fadd2_rn(sh, p);                                      // two-sum of sh and p
+  const float2 bp = __ffma2_rn(sh, m1, t);                                 // t - sh
+  const float2 e2 = __fadd2_rn(__ffma2_rn(__ffma2_rn(bp, m1, t), m1, sh),  // (sh - (t - bp))
+                               __ffma2_rn(bp, m1, p));                     //   + (p - bp)
   sh = t;
   sl = __ffma2_rn(ah, xl, __ffma2_rn(al, xh, __fadd2_rn(sl, __fadd2_rn(e, e2))));
 }
