@@ -586,6 +586,8 @@ def reference_arm(args):
     full workload's time, extrapolated from measured units, is reported
     beside it."""
     p = oracle_sample_problem()
+    for _ in range(args.warmup):                 # untimed, like the GPU arm's warm-up steps
+        oracle_pass(p)
     vals = []
     for _ in range(args.steps):
         r = oracle_pass(p)
@@ -597,7 +599,7 @@ def reference_arm(args):
               f"3x3x2 subdomains, 6x6x4 pts/cell, m=40 (DoF {r['dof']}, {r['iters']} CG iterations): "
               f"build {r['build']:.2f} s, setup {r['setup']:.2f} s, solve {r['solve']:.2f} s; numpy default threads")
     return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": 0, "ms_per_step": round(v * 1e3, 1), "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "sample": "scaled-down instance (see cpu_baseline.sample)"},
             "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
