@@ -53,6 +53,7 @@ cudaError_t launch_schwarz_apply_df(const CholMat* d_mats, int nsets, int maxn, 
                                     const int64_t* d_s_off, const int64_t* d_p_off32, double* d_part, double* d_s,
                                     int* d_done, int wkind, const int* d_inc_ptr, int ckind, double* d_z,
                                     cudaStream_t st, const float2* d_r2 = nullptr);
+cudaError_t launch_x2_pairs(const CholMat* d_mats, int nsets, int maxn, cudaStream_t st);
 cudaError_t launch_trmv_lower_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
                                  const float2* d_g2, float2* d_y2, cudaStream_t st);
 cudaError_t launch_trmv_upper_df(const CholMat* d_mats, int nsets, int maxn, const int64_t* d_s_off,
@@ -1516,6 +1517,8 @@ extern "C" rann_status rann_dd_setup_precond(rann_dd_handle* h, int kind, int ov
   dfree(h, d_ridx); dfree(h, d_tab); dfree(h, d_tab_ptr); dfree(h, d_boffs); dfree(h, d_boff_ptr);
   dfree(h, d_dmax); dfree(h, d_fail); dfree(h, h->d_pairbuf);
   h->d_pairbuf = nullptr;
+  // the applies read L_i^{-1} with each column pair's high parts first
+  if (h->prec_df) KLA(h, K_SPLIT, 1, 8.0 * (h->sum_n2 + h->sum_n), 0, launch_x2_pairs(h->d_mats, J, h->maxn, h->st));
   phase_mark(h, 2, 1);
   CK(stream_sync(h));
   h->prec_kind = kind;

@@ -224,15 +224,15 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
               const float4 x0 = xr[c2], y0 = gsm[c2]; // the diagonal in a row's last pair is zero)
               const float4 x1 = xr[c2 + 32];
               const float4 y1 = gsm[c2 + 32];
-              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.y),
+              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.y), make_float2(x0.z, x0.w), make_float2(y0.x, y0.y),
                           make_float2(y0.z, y0.w));
-              df_mac_f_x2(H1, L1, make_float2(x1.x, x1.z), make_float2(x1.y, x1.w), make_float2(y1.x, y1.y),
+              df_mac_f_x2(H1, L1, make_float2(x1.x, x1.y), make_float2(x1.z, x1.w), make_float2(y1.x, y1.y),
                           make_float2(y1.z, y1.w));
             }
             if (c2 < hi) {
               const float4 x0 = xr[c2];
               const float4 y0 = gsm[c2];
-              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.z), make_float2(x0.y, x0.w), make_float2(y0.x, y0.y),
+              df_mac_f_x2(H0, L0, make_float2(x0.x, x0.y), make_float2(x0.z, x0.w), make_float2(y0.x, y0.y),
                           make_float2(y0.z, y0.w));
             }
             h = H0.x; l = L0.x;
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
 #define SR_COLSUM(k)                                                                                    \
   case (k) + 1: {                                                                                       \
     const float4 x = xr[GS * (k)];                                                                      \
-    df_mac_f_x2(ah[k], al[k], make_float2(x.x, x.z), make_float2(x.y, x.w), yh, yl);                    \
+    df_mac_f_x2(ah[k], al[k], make_float2(x.x, x.y), make_float2(x.z, x.w), yh, yl);                    \
   }
         switch (kact) {
           SR_COLSUM(11) SR_COLSUM(10) SR_COLSUM(9) SR_COLSUM(8) SR_COLSUM(7) SR_COLSUM(6)

@@ -668,6 +668,28 @@ __global__ void schwarz_gather_df_kernel(const int* __restrict__ set_ptr, const 
   }
 }
 
+// Entry c of a row of L^{-1} in the column-pair layout (h_2k, h_2k+1, l_2k, l_2k+1).
+__device__ __forceinline__ float2 x2_entry(const float* row, int c) {
+  const int b = 4 * (c >> 1) + (c & 1);
+  return make_float2(row[b], row[b + 2]);
+}
+
+// After the set-up (precision mode 1): every 16-byte column pair of the lower
+// triangles of L^{-1}, written entry by entry as (h_0, l_0, h_1, l_1), becomes
+// (h_0, h_1, l_0, l_1), the layout the applies read (the packed float32x2
+// operands are then the halves of each load).  Rows are 32-byte aligned
+// (ld a multiple of 4).
+__global__ void __launch_bounds__(256) x2_pairs_kernel(const CholMat* __restrict__ mats) {
+  const CholMat M = mats[blockIdx.y];
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= M.n) return;
+  float4* row = reinterpret_cast<float4*>(M.X2 + (int64_t)r * M.ld);
+  for (int c2 = threadIdx.x & 31; c2 <= (r >> 1); c2 += 32) {
+    const float4 v = row[c2];
+    row[c2] = make_float4(v.x, v.z, v.y, v.w);
+  }
+}
+
 // y2 = X2 g2 (lower triangular) in double-float: one warp per row, four
 // independent accumulator chains per lane.
 __global__ void __launch_bounds__(256) trmv_lower_df_kernel(const CholMat* __restrict__ mats,
@@ -677,14 +699,14 @@ __global__ void __launch_bounds__(256) trmv_lower_df_kernel(const CholMat* __res
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= M.n) return;
-  const float2* row = M.X2 + (int64_t)r * M.ld;
+  const float* row = reinterpret_cast<const float*>(M.X2 + (int64_t)r * M.ld);   // pairs (h, h, l, l)
   const float2* gi = g2 + s_off[blockIdx.y];
   float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
   constexpr int U = 8;                                   // independent loads in flight per lane
   for (int c0 = lane; c0 <= r; c0 += 32 * U) {
     float2 a[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) a[u] = (c0 + 32 * u <= r) ? row[c0 + 32 * u] : make_float2(0.f, 0.f);
+    for (int u = 0; u < U; ++u) a[u] = (c0 + 32 * u <= r) ? x2_entry(row, c0 + 32 * u) : make_float2(0.f, 0.f);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (c0 + 32 * u > r) break;
@@ -728,7 +750,9 @@ __global__ void __launch_bounds__(256) trmv_upper_df_partial_kernel(const CholMa
       float2 a[U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        a[u] = (rr + 4 * u < r1) ? M.X2[(int64_t)(rr + 4 * u) * M.ld + c] : make_float2(0.f, 0.f);
+        a[u] = (rr + 4 * u < r1)
+                   ? x2_entry(reinterpret_cast<const float*>(M.X2 + (int64_t)(rr + 4 * u) * M.ld), c)
+                   : make_float2(0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < U; u += 2) {
         if (rr + 4 * u >= r1) break;
@@ -760,8 +784,17 @@ __global__ void __launch_bounds__(256) trmv_upper_df_partial_kernel(const CholMa
 constexpr int AR = 32;             // rows per block of the fused apply
 constexpr int AMAX_SUB = 27;       // most subdomains in an extended set (3^3)
 constexpr int ANT = 256;           // threads per block of the fused apply (four blocks per SM)
+// (h0, l0) += a_0 x_0 and (h1, l1) += a_1 x_1 for column pairs stored high
+// parts first, (h_0, h_1, l_0, l_1): the layout of L^{-1} after the set-up
+// (x2_pairs_kernel) and of the staged vectors, so the packed float32x2
+// operands are the two halves of each 16-byte load.
 __device__ __forceinline__ void df_mac2(float& h0, float& l0, float& h1, float& l1, float4 a, float4 x) {
-  df_mac_pair(h0, l0, h1, l1, a, x);              // packed float32x2
+  float2 H = make_float2(h0, h1), L = make_float2(l0, l1);
+  df_mac_f_x2(H, L, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(x.x, x.y), make_float2(x.z, x.w));
+  h0 = H.x;
+  h1 = H.y;
+  l0 = L.x;
+  l1 = L.y;
 }
 // The sums of nv vectors of 32 lane partials lp[v * vstride + l], each with
 // the pairing of the xor-shuffle warp sum (level o: entry l += entry l + o
@@ -839,7 +872,7 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
         v[e] = r2 ? r2[seg_w[q] + (c - seg_c[q])] : df_split(seg_d[q] * r[seg_w[q] + (c - seg_c[q])]);
       }
     }
-    gs4[c2] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    gs4[c2] = make_float4(v[0].x, v[1].x, v[0].y, v[1].y);
   }
   if (tid < AR / 2) ys4[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
@@ -869,7 +902,7 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
       for (int u = 0; u < U; ++u) {
         const int pc = c2 + 32 * u;
         a[u] = (pc < nall) ? xr[pc] : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (2 * pc + 1 > row) { a[u].z = 0.f; a[u].w = 0.f; }
+        if (2 * pc + 1 > row) { a[u].y = 0.f; a[u].w = 0.f; }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -902,8 +935,8 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
 #pragma unroll
         for (int u = 0; u < 4; u += 2) {
           const float4 y = ys4[(q + u) >> 1];
-          df_mac2(h0, l0, h1, l1, a[u], make_float4(y.x, y.y, y.x, y.y));
-          df_mac2(h2, l2, h3, l3, a[u + 1], make_float4(y.z, y.w, y.z, y.w));
+          df_mac2(h0, l0, h1, l1, a[u], make_float4(y.x, y.x, y.y, y.y));
+          df_mac2(h2, l2, h3, l3, a[u + 1], make_float4(y.z, y.z, y.w, y.w));
         }
       }
     } else {                                          // diagonal block or short last block
@@ -913,13 +946,13 @@ __global__ void __launch_bounds__(ANT, 4) schwarz_apply_df_kernel(const CholMat*
         for (int u = 0; u < 4; ++u) {
           const int row = r0 + q + u;
           a[u] = (q + u < nr && row >= c) ? xc[(q + u) * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
-          if (row < c + 1) { a[u].z = 0.f; a[u].w = 0.f; }
+          if (row < c + 1) { a[u].y = 0.f; a[u].w = 0.f; }
         }
 #pragma unroll
         for (int u = 0; u < 4; u += 2) {
           const float4 y = ys4[(q + u) >> 1];
-          df_mac2(h0, l0, h1, l1, a[u], make_float4(y.x, y.y, y.x, y.y));
-          df_mac2(h2, l2, h3, l3, a[u + 1], make_float4(y.z, y.w, y.z, y.w));
+          df_mac2(h0, l0, h1, l1, a[u], make_float4(y.x, y.x, y.y, y.y));
+          df_mac2(h2, l2, h3, l3, a[u + 1], make_float4(y.z, y.z, y.w, y.w));
         }
       }
     }
@@ -1009,7 +1042,7 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_multi_kernel(
           v[e] = df_split(1.0 * r[rc * ldr + seg_w[q] + (c - seg_c[q])]);
         }
       }
-      gsm[rc * npmax + c2] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+      gsm[rc * npmax + c2] = make_float4(v[0].x, v[1].x, v[0].y, v[1].y);
     }
   }
   if (tid < AR / 2)
@@ -1045,7 +1078,7 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_multi_kernel(
       for (int u = 0; u < U; ++u) {
         const int pc = c2 + 32 * u;
         a[u] = (pc < nall) ? xr[pc] : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (2 * pc + 1 > row) { a[u].z = 0.f; a[u].w = 0.f; }
+        if (2 * pc + 1 > row) { a[u].y = 0.f; a[u].w = 0.f; }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -1090,7 +1123,7 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_multi_kernel(
           a[u] = xc[(q + u) * ldq];
         } else {
           a[u] = (q + u < nr && row >= c) ? xc[(q + u) * ldq] : make_float4(0.f, 0.f, 0.f, 0.f);
-          if (row < c + 1) { a[u].z = 0.f; a[u].w = 0.f; }
+          if (row < c + 1) { a[u].y = 0.f; a[u].w = 0.f; }
         }
       }
 #pragma unroll
@@ -1098,8 +1131,8 @@ __global__ void __launch_bounds__(ANT, 2) schwarz_apply_multi_kernel(
 #pragma unroll
         for (int rc = 0; rc < NR; ++rc) {
           const float4 y = ysm[rc][(q + u) >> 1];
-          df_mac2(acc[rc][0], acc[rc][1], acc[rc][2], acc[rc][3], a[u], make_float4(y.x, y.y, y.x, y.y));
-          df_mac2(acc[rc][4], acc[rc][5], acc[rc][6], acc[rc][7], a[u + 1], make_float4(y.z, y.w, y.z, y.w));
+          df_mac2(acc[rc][0], acc[rc][1], acc[rc][2], acc[rc][3], a[u], make_float4(y.x, y.x, y.y, y.y));
+          df_mac2(acc[rc][4], acc[rc][5], acc[rc][6], acc[rc][7], a[u + 1], make_float4(y.z, y.z, y.w, y.w));
         }
     }
 #pragma unroll
@@ -1176,6 +1209,12 @@ cudaError_t launch_schwarz_gather_df(int nsets, const int* d_set_ptr, const int*
                                      const int64_t* d_s_off, const double* d_r, float2* d_g2, int wkind,
                                      const int* d_inc_ptr, cudaStream_t st) {
   schwarz_gather_df_kernel<<<nsets, 256, 0, st>>>(d_set_ptr, d_set_sub, d_sub, d_s_off, d_r, d_g2, wkind, d_inc_ptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x2_pairs(const CholMat* d_mats, int nsets, int maxn, cudaStream_t st) {
+  if (nsets == 0 || maxn == 0) return cudaSuccess;
+  x2_pairs_kernel<<<dim3((maxn + 7) / 8, nsets), 256, 0, st>>>(d_mats);
   return cudaGetLastError();
 }
 
