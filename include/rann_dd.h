@@ -383,8 +383,10 @@ rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const char** name, i
  * configuration this set-up cannot run (or out of range).
  * rann_dd_tune_apply: times every configuration this set-up can run (one
  * warm-up and `reps` timed applies each, CUDA events on the handle's
- * stream), keeps the fastest; best_out gets it, ms_out [RANN_APPLY_NCFG] (or
- * NULL) the ms per apply, -1 where a configuration cannot run.
+ * stream; a configuration's time is its fastest apply, robust to other
+ * work sharing the GPU), keeps the fastest; best_out gets it, ms_out
+ * [RANN_APPLY_NCFG] (or NULL) the ms per apply, -1 where a configuration
+ * cannot run.
  * Synchronises. */
 #define RANN_APPLY_NCFG 4
 rann_status rann_dd_set_apply_config(rann_dd_handle* h, int cfg);
@@ -410,7 +412,7 @@ rann_status rann_dd_set_stream(rann_dd_handle* h, void* cuda_stream);
  * convergence checks).  Instances start largest first (points x neurons).
  * With autotune set, the first instance of each size class (subdomain
  * count, largest extended set rounded up to 64 unknowns) runs
- * rann_dd_tune_apply(reps 2) and the others of the class wait for and reuse
+ * rann_dd_tune_apply(reps 5) and the others of the class wait for and reuse
  * its choice.
  * Per instance (arrays of n pointers, device buffers caller-owned):
  *   F_dev [n_points] written; W_dev with room for J*m entries, dof written;

@@ -98,7 +98,7 @@ rann_status run_one(rann_dd_handle* h, cudaStream_t st, const rann_dd_pipeline& 
       tu.busy.insert(key);
       lk.unlock();
       int best = 0;
-      const rann_status ts = rann_dd_tune_apply(h, 2, &best, nullptr);
+      const rann_status ts = rann_dd_tune_apply(h, 5, &best, nullptr);
       if (ts != RANN_OK) rann_dd_get_apply_config(h, &best);
       lk.lock();
       tu.done[key] = best;
