@@ -53,7 +53,7 @@ CSRC = os.path.join(ROOT, "paper_2412_19207_gb300", "csrc")
 # profiles/ summary states), valid only for the kernel source it was taken
 # on: (bytes, file, kernel, sha256 prefix of the kernel's source text).  A
 # changed kernel reports null.
-TRAFFIC = {"schwarz_apply_df32": (17945.1e6, "apply.cu", "schwarz_apply_rows_df_kernel", "f3cff299d8a2")}
+TRAFFIC = {"schwarz_apply_df32": (17946.9e6, "apply.cu", "schwarz_apply_rows_df_kernel", "7c262b33f7dc")}
 # families whose profiled bracket spans a multi-stream pipeline of many kernels
 # (the Cholesky with lookahead and the row-block inverse): no single launch
 # duration, so they are reported as pipelines, not as the roofline kernel

@@ -11,10 +11,12 @@
 // every staged row twice: (1) its dot product with g (kept in shared memory):
 // the stage's column pairs, rows concatenated, are split evenly over the
 // warps, and each warp sums every row piece it holds over its lanes; the
-// pieces of a row are then added in warp order; (2) its share x_r y_r of the
-// column sums: teams of threads own the columns cyclically (a team is as
-// small as the longest row allows, so short rows keep every thread busy) and
-// take the stage's rows in turn, with the sums in registers.  At the end the
+// pieces of a row are then added in warp order (these reductions add the
+// high parts error-free and renormalise once at the end); (2) its share
+// x_r y_r of the column sums: teams of threads own the columns cyclically (a
+// team is as small as the longest row allows, so short rows keep every
+// thread busy) and take the stage's rows in turn, with the sums in registers
+// and each entry loaded one pair ahead of its arithmetic.  At the end the
 // teams' sums are added in team order and written as the chunk's part; the
 // last chunk of a set to finish adds the parts in chunk order into s_i (or,
 // for the restricted combine, into z).  Every sum has a fixed order, so the
@@ -235,12 +237,10 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
               df_mac_f_x2(H0, L0, make_float2(x0.x, x0.y), make_float2(x0.z, x0.w), make_float2(y0.x, y0.y),
                           make_float2(y0.z, y0.w));
             }
+            df_reduce_add_x2(H0, L0, H1, L1);
             h = H0.x; l = L0.x;
-            float h2 = H1.x, l2 = L1.x;
-            df_add(h, l, H0.y, L0.y);
-            df_add(h2, l2, H1.y, L1.y);
-            df_add(h, l, h2, l2);
-            df_warp_sum(h, l);
+            df_reduce_add(h, l, H0.y, L0.y);
+            df_warp_sum_lazy(h, l);
           }
           if (lane == 0) wp[grp][j][gw] = make_float2(h, l);
         }
@@ -253,8 +253,9 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
         for (int o = SR_GW / 2; o > 0; o >>= 1) {
           const float oh = __shfl_xor_sync(0xffffffffu, v.x, o);
           const float ol = __shfl_xor_sync(0xffffffffu, v.y, o);
-          df_add(v.x, v.y, oh, ol);
+          df_reduce_add(v.x, v.y, oh, ol);
         }
+        df_renorm(v.x, v.y);
         if (lane == 0) ysm[grp][j] = v;
       }
       consumers_sync(bar_b, SR_GC);
@@ -264,12 +265,20 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
         const int nall = ((P.r0 + j) >> 1) + 1;
         const float4* xr = stage + (P.off[j] >> 1) + lt;
         const float2 y = ysm[grp][j];
-        const float2 yh = make_float2(y.x, y.x), yl = make_float2(y.y, y.y);
+        const float2 yh = make_float2(y.x, y.x), yl = make_float2(y.y, y.y), nyh = make_float2(-y.x, -y.x);
         const int kact = nall > lt ? min(SR_PPT, ((nall - lt - 1) >> gs_log) + 1) : 0;
+        // the next pair's entry is loaded before this pair's arithmetic (two buffers, by parity)
+        float4 xb0 = make_float4(0.f, 0.f, 0.f, 0.f), xb1 = xb0;
+        if (kact > 0) {
+          if ((kact - 1) & 1) xb1 = xr[GS * (kact - 1)];
+          else xb0 = xr[GS * (kact - 1)];
+        }
+#define SR_BUF(k) (((k) & 1) ? xb1 : xb0)
 #define SR_COLSUM(k)                                                                                    \
   case (k) + 1: {                                                                                       \
-    const float4 x = xr[GS * (k)];                                                                      \
-    df_mac_f_x2(ah[k], al[k], make_float2(x.x, x.y), make_float2(x.z, x.w), yh, yl);                    \
+    if ((k) > 0) SR_BUF((k) + 1) = xr[GS * ((k) > 0 ? (k) - 1 : 0)];                                    \
+    const float4 x = SR_BUF(k);                                                                         \
+    df_mac_f_x2n(ah[k], al[k], make_float2(x.x, x.y), make_float2(x.z, x.w), yh, yl, nyh);              \
   }
         switch (kact) {
           SR_COLSUM(11) SR_COLSUM(10) SR_COLSUM(9) SR_COLSUM(8) SR_COLSUM(7) SR_COLSUM(6)
@@ -277,6 +286,7 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
           default: break;
         }
 #undef SR_COLSUM
+#undef SR_BUF
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[slot]));
@@ -284,8 +294,10 @@ __global__ void __launch_bounds__(SR_T, 1) schwarz_apply_rows_df_kernel(
   }
   __syncthreads();
   if (abort_flag && tid == SR_C) {
-    // let the copies in flight land before the block's shared memory is reused or released
-    for (int st = 0; st < issued; ++st) mbar_drain(smem_u32(&full[st % SR_NST]), (uint32_t)(st / SR_NST) & 1u);
+    // let the copies in flight land before the block's shared memory is reused or released: only
+    // a slot's latest stage can have copies in flight (a slot is refilled after its stage's release)
+    for (int st = max(0, issued - SR_NST); st < issued; ++st)
+      mbar_drain(smem_u32(&full[st % SR_NST]), (uint32_t)(st / SR_NST) & 1u);
   }
   __syncthreads();
   // the chunk's column sums (columns < C.r1): the teams' sums (group 0's, then group 1's)
