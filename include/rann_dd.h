@@ -384,9 +384,12 @@ rann_status rann_dd_profile_get(rann_dd_handle* h, int idx, const char** name, i
  * rann_dd_tune_apply: times every configuration this set-up can run (one
  * warm-up and `reps` timed applies each, CUDA events on the handle's
  * stream; a configuration's time is its fastest apply, robust to other
- * work sharing the GPU), keeps the fastest; best_out gets it, ms_out
- * [RANN_APPLY_NCFG] (or NULL) the ms per apply, -1 where a configuration
- * cannot run.
+ * work sharing the GPU) and keeps the configuration in effect unless
+ * another is more than 10 % faster, in which case it keeps the fastest of
+ * those (work sharing the GPU can slow all of one configuration's samples;
+ * a small gain does not outweigh that noise); best_out gets the choice,
+ * ms_out [RANN_APPLY_NCFG] (or NULL) the ms per apply, -1 where a
+ * configuration cannot run.
  * Synchronises. */
 #define RANN_APPLY_NCFG 4
 rann_status rann_dd_set_apply_config(rann_dd_handle* h, int cfg);

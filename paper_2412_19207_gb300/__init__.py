@@ -329,8 +329,9 @@ class RannDD:
         return c.value
 
     def tune_apply(self, reps: int = 3):
-        """Times every Schwarz apply configuration, keeps the fastest; returns
-        (best, ms per configuration, None where it cannot run)."""
+        """Times every Schwarz apply configuration and keeps the one in effect
+        unless another is more than 10 % faster (then the fastest); returns
+        (chosen, ms per configuration, None where it cannot run)."""
         best = _I()
         ms = (ctypes.c_float * APPLY_NCFG)()
         _check(self._lib.rann_dd_tune_apply(self._h, int(reps), ctypes.byref(best), ms), "rann_dd_tune_apply")

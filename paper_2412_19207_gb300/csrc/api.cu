@@ -1587,6 +1587,8 @@ extern "C" rann_status rann_dd_get_apply_config(rann_dd_handle* h, int* cfg) {
   return RANN_OK;
 }
 
+static const float TUNE_MARGIN = 0.1f;
+
 extern "C" rann_status rann_dd_tune_apply(rann_dd_handle* h, int reps, int* best_out, float* ms_out) {
   REQUIRE(h && best_out, RANN_EINVAL, "null argument");
   REQUIRE(h->prec_kind >= 0, RANN_EORDER, "tune_apply before setup_precond");
@@ -1604,10 +1606,11 @@ extern "C" rann_status rann_dd_tune_apply(rann_dd_handle* h, int reps, int* best
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   const bool fused_ok = h->prec_df && h->max_set_size <= schwarz_apply_max_subs();
-  int best = h->apply_cfg;
-  float best_ms = -1.f;
+  const int cur = h->apply_cfg;
+  float ms_cfg[RANN_APPLY_NCFG];
   rann_status st = RANN_OK;
   for (int cfg = 0; cfg < RANN_APPLY_NCFG && st == RANN_OK; ++cfg) {
+    ms_cfg[cfg] = -1.f;
     if (ms_out) ms_out[cfg] = -1.f;
     if (cfg == 0 ? !fused_ok : !streaming_ok(h)) continue;
     if ((st = set_apply_config(h, cfg)) != RANN_OK) break;
@@ -1626,7 +1629,21 @@ extern "C" rann_status rann_dd_tune_apply(rann_dd_handle* h, int reps, int* best
     }
     if (st != RANN_OK) break;
     if (ms_out) ms_out[cfg] = ms;
-    if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = cfg; }
+    ms_cfg[cfg] = ms;
+  }
+  // another configuration replaces the one in effect only when it is faster by more than
+  // TUNE_MARGIN: work sharing the GPU (a batch's other instances) can slow every sample of
+  // one configuration, and a small gain is not worth a choice that noise may have made
+  int best = cur;
+  float best_ms = st == RANN_OK ? ms_cfg[cur] : -1.f;
+  for (int cfg = 0; cfg < RANN_APPLY_NCFG && st == RANN_OK; ++cfg) {
+    const float m = ms_cfg[cfg];
+    if (m < 0.f || cfg == cur) continue;
+    if (ms_cfg[cur] < 0.f ? (best_ms < 0.f || m < best_ms)
+                          : (m < (1.f - TUNE_MARGIN) * ms_cfg[cur] && m < best_ms)) {
+      best = cfg;
+      best_ms = m;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -2286,7 +2303,6 @@ static rann_status solve_cg_multi_impl(rann_dd_handle* h, const double* F_dev, d
     CK(cudaMemsetAsync(sd.it, 0, sizeof(int) * nr, h->st));
     int kmax = 0;
     for (int c = 0; c < nr; ++c) if (active[c]) kmax = std::max(kmax, maxit - it[c]);
-    bool all_done = false;
     int ph = 0;
     for (int i = 0; i < kmax; ++i) {
       if (i >= 2) {
@@ -2307,7 +2323,6 @@ static rann_status solve_cg_multi_impl(rann_dd_handle* h, const double* F_dev, d
       CK(cudaMemcpyAsync(hdone, h->d_scal + 64, sizeof(int), cudaMemcpyDeviceToHost, h->st));
       CK(cudaEventRecord(evh.e[i % 3], h->st));
     }
-    (void)all_done;
     CK(cudaMemcpyAsync(hdv.data(), sd.done, sizeof(int) * nr, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(hit.data(), sd.it, sizeof(int) * nr, cudaMemcpyDeviceToHost, h->st));
     std::vector<double> hrel(nr);

@@ -11,7 +11,8 @@ on scheduling.  One instance's solution is also held to the bound its normal
 residual allows against the oracle's direct least-squares solution on the
 same reduced blocks.  The tuner: every configuration a set-up can run gives
 the same M^{-1} r to the double-float factor accuracy, each one
-deterministically; the tuner keeps the fastest; instances of one size class
+deterministically; the tuner keeps the configuration in effect unless another
+is more than 10 % faster (then the fastest); instances of one size class
 share the tuned choice.
 """
 import numpy as np
@@ -133,9 +134,15 @@ def test_apply_configurations_agree_and_the_tuner_keeps_the_fastest(g):
         z.append(a.cpu().numpy())
     for a in z[1:]:
         np.testing.assert_allclose(a, z[0], rtol=0, atol=1e-11 * np.abs(z[0]).max())
+    cur = s.get_apply_config()
     best, ms = s.tune_apply(2)
     assert all(v is not None and v > 0 for v in ms)
-    assert ms[best] == min(ms) and s.get_apply_config() == best
+    assert s.get_apply_config() == best
+    faster = [c for c in range(g.APPLY_NCFG) if c != cur and ms[c] < 0.9 * ms[cur]]
+    if faster:
+        assert ms[best] == min(ms[c] for c in faster)
+    else:
+        assert best == cur
     with pytest.raises(g.RannError) as e:
         s.set_apply_config(g.APPLY_NCFG)
     assert e.value.status == g.EINVAL
